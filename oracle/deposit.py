@@ -1,0 +1,115 @@
+"""Spec Q: b2 charge assignment, Sec. II.B.1 eqs. (pg), (Wpc), (b2), in 64-bit fixed point.
+
+Eq. (b2) as printed gives (3/2 - |xi|)^2 for 1/2 < |xi| < 3/2; that branch is
+discontinuous at |xi| = 1/2 and the weights do not sum to one. Reading: the standard
+quadratic B-spline 1/2 (3/2 - |xi|)^2 (Birdsall & Langdon, the reference the paper cites
+for its assignment functions). b2 is assigned to the 3^D cell centres around the particle
+(density lives at cell centres, Sec. II.B).
+
+Fixed-point spec (constants QK = 12, QF = 24):
+  per axis: u = floor(t * 2^QK) (exact), s = 2u + 1 - 2^QK (odd, |s| < 2^QK),
+  integer weights for nodes m = -1, 0, +1:
+    W[-1] = (2^QK - s)^2,  W[0] = 2 (3 * 2^(2 QK) - s^2),  W[+1] = (2^QK + s)^2,
+  which are b2 at the sub-cell centre offset d = s / 2^(QK+1) scaled by 2^(2 QK + 3) and
+  sum to exactly 2^(2 QK + 3).
+  2D node weight: q = (W0[m0] W1[m1] + 2^29) >> 30.
+  3D node weight: q01 = (W0[m0] W1[m1] + 2^29) >> 30, q = (q01 W2[m2] + 2^26) >> 27.
+  The centre node takes 2^QF minus the sum of the other nodes, so each particle deposits
+  exactly 2^QF units (charge conservation is exact, P5).
+  Node cells outside a non-periodic axis fold onto the boundary cell (charge kept);
+  periodic axes wrap.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+QK = 12
+QF = 24
+
+
+def b1(x):
+    """Linear B-spline, eq. (b1)."""
+    ax = np.abs(x)
+    return np.where(ax < 1.0, 1.0 - ax, 0.0)
+
+
+def b2(x):
+    """Quadratic B-spline, eq. (b2) with the 1/2 of the outer branch restored."""
+    ax = np.abs(x)
+    return np.where(ax < 0.5, 0.75 - ax * ax, np.where(ax < 1.5, 0.5 * (1.5 - ax) ** 2, 0.0))
+
+
+def b2_as_printed(x):
+    """Eq. (b2) exactly as printed (outer branch without the 1/2): used only by the test
+    that documents the garbled constant."""
+    ax = np.abs(x)
+    return np.where(ax < 0.5, 0.75 - ax * ax, np.where(ax < 1.5, (1.5 - ax) ** 2, 0.0))
+
+
+def axis_weights(t32: np.ndarray):
+    """Integer per-axis weights W[m+1] (int64 arrays) from float32 offsets t in [0, 1)."""
+    t32 = np.asarray(t32, dtype=np.float32)
+    u = np.floor(t32 * np.float32(1 << QK)).astype(np.int64)
+    s = 2 * u + 1 - (1 << QK)
+    one = np.int64(1 << QK)
+    return [(one - s) ** 2, 2 * (3 * one * one - s * s), (one + s) ** 2]
+
+
+def node_weights(t32: np.ndarray):
+    """Fixed-point node weights for particles with offsets t32 (D, n).
+    Returns dict offset tuple (m0, m1[, m2]) -> int64 array (n,)."""
+    D = t32.shape[0]
+    W = [axis_weights(t32[a]) for a in range(D)]
+    out = {}
+    for m in itertools.product((-1, 0, 1), repeat=D):
+        if all(x == 0 for x in m):
+            continue
+        p = W[0][m[0] + 1] * W[1][m[1] + 1]
+        q = (p + (1 << 29)) >> 30
+        if D == 3:
+            q = (q * W[2][m[2] + 1] + (1 << 26)) >> 27
+        out[m] = q
+    centre = np.full(t32.shape[1], 1 << QF, dtype=np.int64)
+    for q in out.values():
+        centre -= q
+    out[(0,) * D] = centre
+    return out
+
+
+def deposit_fixed(idx: np.ndarray, t32: np.ndarray, n, periodic) -> np.ndarray:
+    """Accumulate int64 charge counts (numpy cell layout) for live particles with per-axis
+    cell indices idx (D, n) and float32 offsets t32 (D, n)."""
+    D = len(n)
+    C = np.zeros(int(np.prod(n)), dtype=np.int64)
+    for m, q in node_weights(t32).items():
+        lin = np.zeros(idx.shape[1], dtype=np.int64)
+        for a in reversed(range(D)):
+            c = idx[a].astype(np.int64) + m[a]
+            if periodic[a]:
+                c = np.mod(c, n[a])
+            else:
+                c = np.clip(c, 0, n[a] - 1)
+            lin = lin * n[a] + c
+        np.add.at(C, lin, q)
+    return C.reshape(tuple(reversed(n)))
+
+
+def deposit_exact(idx: np.ndarray, t: np.ndarray, n, periodic) -> np.ndarray:
+    """FP64 b2 deposit (no quantisation), same folding rules: eq. (pg) numerator with unit
+    charge per particle."""
+    D = len(n)
+    C = np.zeros(int(np.prod(n)), dtype=np.float64)
+    d = np.asarray(t, dtype=np.float64) - 0.5  # offset from the cell centre
+    for m in itertools.product((-1, 0, 1), repeat=D):
+        w = np.ones(idx.shape[1])
+        lin = np.zeros(idx.shape[1], dtype=np.int64)
+        for a in range(D):
+            w = w * b2(d[a] - m[a])
+        for a in reversed(range(D)):
+            c = idx[a].astype(np.int64) + m[a]
+            c = np.mod(c, n[a]) if periodic[a] else np.clip(c, 0, n[a] - 1)
+            lin = lin * n[a] + c
+        np.add.at(C, lin, w)
+    return C.reshape(tuple(reversed(n)))

@@ -1,0 +1,109 @@
+"""Spec I: Maxwellian flux injection at a boundary face (Sec. III.A-B: plasma injected from
+the outer boundary each step with fluxes from a Maxwellian; Sec. III.B: loaded at t = 0).
+
+Readings (the paper gives no formulas):
+  * particles per step from a one-sided Maxwellian flux n vth / sqrt(2 pi) through the
+    face's physical length (2D polyline through the face vertices, summed in vertex order),
+    rate r = n vth / sqrt(2 pi) * A * dt / w; step n (0-based) injects
+    floor((n+1) r) - floor(n r) particles (a deterministic fractional carry);
+  * draws: Philox4x32-10 with key (seed low 32 bits, seed high 32 bits) and counter
+    (p, n, species, 0) for U0..U3 and (p, n, species, 1) for U4..U7, u -> (u + 1/2) 2^-32;
+  * position uniform in the face's logical coordinate: u1 = U0 * N2 (uniform in arc length
+    when the face's arc length is linear in eta, as on the annulus);
+  * velocity: inward normal speed vth sqrt(-2 ln U1) (flux-weighted), tangential and z
+    components vth sqrt(-2 ln U2) (cos 2 pi U3, sin 2 pi U3), plus the drift vector;
+    the inward normal is -+ k^{a.}/|k^{a.}| with k linearly interpolated along the face
+    from its FP64 vertex values; the tangent is the normal rotated by +90 degrees;
+  * partial first push: the particle enters at a uniformly random time within the step:
+    u = u_face + U4 dt (k v) (cell units, FP64, velocity already rounded to FP32); then the
+    split (cell, FP32 offset) with the 1.0 -> next-cell rule, periodic wrap along the face;
+    a particle whose partial push leaves the domain is dropped (not counted).
+Only 2D faces normal to axis 0 are defined here.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .philox import philox4x32_10, uniform01
+
+INV_SQRT_2PI = 1.0 / math.sqrt(2.0 * math.pi)
+
+
+def face_length_2d(X, side):
+    """Physical length of the xi = 0 (side 0) or xi = 1 (side 1) face, summed in order."""
+    col = X[:, 0 if side == 0 else -1, :]
+    acc = 0.0
+    for j in range(col.shape[0] - 1):
+        d = col[j + 1] - col[j]
+        acc += math.sqrt(d[0] * d[0] + d[1] * d[1])
+    return acc
+
+
+def rate_per_step(density, vth, area, dt, w):
+    return (((density * vth) * INV_SQRT_2PI) * area) * dt / w
+
+
+def count_at_step(rate, step):
+    return int(math.floor((step + 1) * rate) - math.floor(step * rate))
+
+
+def draws(count, step, species, seed):
+    p = np.arange(count, dtype=np.uint64)
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint32)
+    out = []
+    for word in (0, 1):
+        ctr = np.zeros((count, 4), dtype=np.uint32)
+        ctr[:, 0] = p.astype(np.uint32)
+        ctr[:, 1] = np.uint32(step & 0xFFFFFFFF)
+        ctr[:, 2] = np.uint32(species)
+        ctr[:, 3] = np.uint32(word)
+        out.append(uniform01(philox4x32_10(ctr, np.broadcast_to(key, (count, 2)))))
+    return np.concatenate(out, axis=1)  # (count, 8)
+
+
+def inject_2d(k64, n, side, count, step, species, seed, vth, drift, dt):
+    """New particles on the face normal to axis 0 (side 0: xi = 0, side 1: xi = 1).
+    k64: FP64 vertex table (N2+1, N1+1, a, alpha). Returns (idx (2, m), t32 (2, m),
+    v32 (3, m), keep mask over the count draws)."""
+    n1, n2 = n
+    U = draws(count, step, species, seed)
+    u1 = U[:, 0] * n2
+    j = np.floor(u1).astype(np.int64)
+    j = np.minimum(j, n2 - 1)
+    s = u1 - j
+    col = 0 if side == 0 else n1
+    kb = (1.0 - s)[:, None, None] * k64[j, col] + s[:, None, None] * k64[j + 1, col]
+    ga = kb[:, 0, :]  # d u^0 / d x
+    gn = np.sqrt(ga[:, 0] * ga[:, 0] + ga[:, 1] * ga[:, 1])
+    sgn = -1.0 if side == 1 else 1.0
+    nin = sgn * ga / gn[:, None]
+    tau = np.stack([-nin[:, 1], nin[:, 0]], axis=1)
+    vn = vth * np.sqrt(-2.0 * np.log(U[:, 1]))
+    rho = vth * np.sqrt(-2.0 * np.log(U[:, 2]))
+    vt = rho * np.cos(2.0 * math.pi * U[:, 3])
+    vz = rho * np.sin(2.0 * math.pi * U[:, 3])
+    v = np.empty((3, count))
+    v[0] = vn * nin[:, 0] + vt * tau[:, 0] + drift[0]
+    v[1] = vn * nin[:, 1] + vt * tau[:, 1] + drift[1]
+    v[2] = vz + drift[2]
+    v32 = v.astype(np.float32)
+    vd = v32.astype(np.float64)
+    du0 = (U[:, 4] * dt) * (kb[:, 0, 0] * vd[0] + kb[:, 0, 1] * vd[1])
+    du1 = (U[:, 4] * dt) * (kb[:, 1, 0] * vd[0] + kb[:, 1, 1] * vd[1])
+    u0 = (0.0 if side == 0 else float(n1)) + du0
+    uu1 = (j + s) + du1
+    out_idx = np.empty((2, count), dtype=np.int64)
+    out_t = np.empty((2, count), dtype=np.float32)
+    for a, u in enumerate((u0, uu1)):
+        c = np.floor(u)
+        f32 = (u - c).astype(np.float32)
+        one = f32 >= np.float32(1.0)
+        f32[one] = np.float32(0.0)
+        c = c + one
+        out_idx[a] = c.astype(np.int64)
+        out_t[a] = f32
+    out_idx[1] = np.mod(out_idx[1], n2)
+    keep = (out_idx[0] >= 0) & (out_idx[0] < n1)
+    return out_idx[:, keep], out_t[:, keep], v32[:, keep], keep

@@ -1,0 +1,171 @@
+"""Hybrid mover in FP64 (Sec. II.B.4) and the ctypes wrapper of the FP32 replay.
+
+Particles keep a logical position (cell index + in-cell offset, cell units) and a
+physical velocity. One push (eqs. (step1)-(step4), unmagnetised):
+  1. b1-gather (eqs. (vvp), (Wvp), (b1)) of the logical field G and of k at xi^n;
+     E^alpha = -sum_a G^a k^{a alpha} (reading: the vertex field is logical and is turned
+     physical at the particle with the same gathered k that the predictor needs);
+  2. v^{n+1/2} = v^{n-1/2} + dt (q/m) E (eq. (step1); B0 = 0, so the Boris rotation is the
+     identity; in 2D E has no z component);
+  3. predictor xi' = xi^n + dt/2 k(xi^n) v^{n+1/2} (eq. (step2)); in 2D only the in-plane
+     velocity moves xi;
+  4. k(xi') by b1 interpolation (eq. (step3));
+  5. corrector xi^{n+1} = xi^n + dt k(xi') v^{n+1/2} (eq. (step4));
+  6. boundaries: periodic axes wrap; on an absorbing axis a cell index < 0 or >= N removes
+     the particle (Sec. II.B.4: leaving the domain means a logical coordinate < 0 or > 1;
+     an offset of exactly 0 on cell 0 is inside, a coordinate of exactly 1 is outside).
+A predictor point outside a non-periodic axis is clamped to the boundary (reading).
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import os
+
+import numpy as np
+
+PBC_PERIODIC, PBC_ABSORB, PBC_REFLECT = 0, 1, 2
+
+
+def _vertex_lookup(table, idx):
+    """table: numpy vertex layout (..., comps); idx: per-axis vertex indices (D, n)."""
+    D = idx.shape[0]
+    return table[tuple(idx[D - 1 - x] for x in range(D))]
+
+
+def gather(table, idx, t):
+    """b1 interpolation of a vertex table at (cell idx, offsets t): sum over the 2^D corners
+    of prod_a b1 weights times the vertex value."""
+    D = idx.shape[0]
+    acc = 0.0
+    for o in itertools.product((0, 1), repeat=D):
+        w = np.ones(idx.shape[1])
+        for a in range(D):
+            w = w * (t[a] if o[a] else 1.0 - t[a])
+        corner = idx + np.asarray(o)[:, None]
+        val = _vertex_lookup(table, corner)
+        acc = acc + w.reshape((-1,) + (1,) * (val.ndim - 1)) * val
+    return acc
+
+
+def _renorm(x):
+    c = np.floor(x)
+    f = x - c
+    one = f >= 1.0
+    f = np.where(one, 0.0, f)
+    c = c + one
+    return c.astype(np.int64), f
+
+
+def push64(idx, t, v, k, G, dt, qm, n, pbc):
+    """One FP64 push. idx (D, n) int, t (D, n), v (3, n); k: vertex table (..., a, alpha);
+    G: vertex table (..., a); qm: q/m per particle (n,) or scalar.
+    Returns (idx, t, v, face) with face = -1 alive or 2a+side for removed particles."""
+    D = idx.shape[0]
+    idx = idx.astype(np.int64)
+    t = np.asarray(t, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    kp = gather(k, idx, t)  # (n, a, alpha)
+    gp = gather(G, idx, t)  # (n, a)
+    E = -np.einsum("pa,pab->pb", gp, kp)  # (n, alpha), alpha < D
+    v[:D] = v[:D] + dt * np.asarray(qm) * E.T
+    # predictor
+    d = np.einsum("pab,bp->ap", kp, v[:D])
+    cpred, tpred = _renorm(t + 0.5 * dt * d)
+    ip = idx + cpred
+    for a in range(D):
+        if pbc[2 * a] == PBC_PERIODIC:
+            ip[a] = np.mod(ip[a], n[a])
+        else:
+            low = ip[a] < 0
+            high = ip[a] >= n[a]
+            ip[a] = np.clip(ip[a], 0, n[a] - 1)
+            tpred[a] = np.where(low, 0.0, np.where(high, 1.0, tpred[a]))
+    kq = gather(k, ip, tpred)
+    d2 = np.einsum("pab,bp->ap", kq, v[:D])
+    cn, tn = _renorm(t + dt * d2)
+    inew = idx + cn
+    face = np.full(idx.shape[1], -1, dtype=np.int64)
+    for a in range(D):
+        if pbc[2 * a] == PBC_PERIODIC:
+            inew[a] = np.mod(inew[a], n[a])
+        else:
+            lo = (inew[a] < 0) & (face < 0)
+            hi = (inew[a] >= n[a]) & (face < 0)
+            face[lo] = 2 * a
+            face[hi] = 2 * a + 1
+    return inew, tn, v, face
+
+
+def kick64(idx, t, v, k, G, coef):
+    """Gather and kick only: v += coef * E (used for the leapfrog start-up half step)."""
+    D = idx.shape[0]
+    v = np.array(v, dtype=np.float64)
+    kp = gather(k, idx.astype(np.int64), np.asarray(t, dtype=np.float64))
+    gp = gather(G, idx.astype(np.int64), np.asarray(t, dtype=np.float64))
+    E = -np.einsum("pa,pab->pb", gp, kp)
+    v[:D] = v[:D] + np.asarray(coef) * E.T
+    return v
+
+
+# ---------------------------------------------------------------------------------------
+# FP32 replay (oracle/replay32.c)
+# ---------------------------------------------------------------------------------------
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        from .build import build_replay
+
+        path = build_replay()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        lib.replay_push.argtypes = [ctypes.c_int, P, P, ctypes.c_long, P, P, P, P, P,
+                                    ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P]
+        lib.replay_push.restype = None
+        lib.replay_kick.argtypes = [ctypes.c_int, P, ctypes.c_long, P, P, P, P, P, ctypes.c_float]
+        lib.replay_kick.restype = None
+        _LIB = lib
+    return _LIB
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def push32(idx, t32, v32, k32, G32, n, pbc, dtqm, hdt, dt):
+    """FP32 replay of one push. Arguments as push64 but float32 tables (numpy vertex
+    layout, k32 (..., a, alpha), G32 (..., a)) and float32 coefficients
+    dtqm = float32(dt q / m), hdt = float32(dt / 2), dt = float32(dt).
+    Returns (idx, t, v, face, ke_fp)."""
+    D = idx.shape[0]
+    np_ = idx.shape[1]
+    idx_c = np.ascontiguousarray(idx, dtype=np.int32).copy()
+    t_c = np.ascontiguousarray(t32, dtype=np.float32).copy()
+    v_c = np.ascontiguousarray(v32, dtype=np.float32).copy()
+    K = np.ascontiguousarray(k32, dtype=np.float32).reshape(-1)
+    G = np.ascontiguousarray(G32, dtype=np.float32).reshape(-1)
+    nn = np.asarray(list(n) + [1] * (3 - D), dtype=np.int32)
+    pb = np.asarray(list(pbc) + [0] * (6 - len(pbc)), dtype=np.int32)
+    face = np.empty(np_, dtype=np.int32)
+    ke = np.empty(np_, dtype=np.int64)
+    _lib().replay_push(D, _ptr(nn), _ptr(pb), np_, _ptr(idx_c), _ptr(t_c), _ptr(v_c), _ptr(K), _ptr(G),
+                       np.float32(dtqm), np.float32(hdt), np.float32(dt), _ptr(face), _ptr(ke))
+    return idx_c, t_c, v_c, face, ke
+
+
+def kick32(idx, t32, v32, k32, G32, n, coef):
+    D = idx.shape[0]
+    idx_c = np.ascontiguousarray(idx, dtype=np.int32)
+    t_c = np.ascontiguousarray(t32, dtype=np.float32)
+    v_c = np.ascontiguousarray(v32, dtype=np.float32).copy()
+    K = np.ascontiguousarray(k32, dtype=np.float32).reshape(-1)
+    G = np.ascontiguousarray(G32, dtype=np.float32).reshape(-1)
+    nn = np.asarray(list(n) + [1] * (3 - D), dtype=np.int32)
+    _lib().replay_kick(D, _ptr(nn), idx.shape[1], _ptr(idx_c), _ptr(t_c), _ptr(v_c), _ptr(K), _ptr(G),
+                       np.float32(coef))
+    return v_c

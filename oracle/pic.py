@@ -1,0 +1,153 @@
+"""The PIC cycle composed from the oracle's steps (Sec. II: mover, P->G, field solve, G->P).
+
+Step order (reading of the four-step cycle of Sec. II and the leapfrog of eq. (step1)):
+state at step n is (xi^n, v^{n-1/2}) for every particle and phi^n;
+  1. G^n = vertex field of phi^n (spec G);
+  2. push every particle (eqs. (step1)-(step4)) to (xi^{n+1}, v^{n+1/2}); remove and tally
+     the absorbed ones; W_K^n = sum_s 1/2 m_s w_s sum_p v^{n-1/2} . v^{n+1/2};
+  3. inject new particles (spec I, step index n);
+  4. deposit rho^{n+1} (eq. (pg)) and solve for phi^{n+1} (spec P);
+  History entry n holds W_E^n = 1/2 sum_c phi^n_c Q^n_c (before the push) and W_K^n.
+Start-up: deposit and solve at xi^0, then v^{-1/2} = v^0 - dt/2 (q/m) E(xi^0).
+
+Two precisions: "fp64" uses the FP64 mover and the exact FP64 b2 deposit; "fp32" replays
+the FP32 operation sequence of spec R with FP32 tables and the fixed-point deposit of
+spec Q (the results a GPU implementation of the same specs must reproduce bit for bit
+given the same potential).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import deposit as dep
+from . import gradient, inject, mover, poisson
+from .geometry import build_geometry
+
+BC_PERIODIC = poisson.BC_PERIODIC
+
+
+def unpack_cells(cell, D):
+    """Per-axis cell indices (D, n) from the packed int32 cell word of the particle format
+    (2D: i | j << 16; 3D: i | j << 10 | k << 20)."""
+    c = np.asarray(cell).astype(np.int64)
+    if D == 2:
+        return np.stack([c & 0xFFFF, c >> 16])
+    return np.stack([c & 0x3FF, (c >> 10) & 0x3FF, c >> 20])
+
+
+@dataclass
+class SpeciesState:
+    q: float
+    m: float
+    w: float
+    idx: np.ndarray  # (D, n) int64
+    t: np.ndarray  # (D, n)
+    v: np.ndarray  # (3, n)
+    absorbed: np.ndarray  # per face counts
+
+
+class OraclePIC:
+    def __init__(self, wl, precision: str = "fp64"):
+        self.wl = wl
+        self.D = wl.dim
+        self.n = tuple(wl.n)
+        self.precision = precision
+        self.bc = list(wl.field_bc)
+        self.bcval = list(wl.field_bc_value)
+        self.pbc = list(wl.particle_bc)
+        periodic = [self.bc[2 * a] == BC_PERIODIC for a in range(self.D)]
+        self.periodic = periodic
+        self.geom = build_geometry(wl.vertices, periodic, axisym=wl.omega_axisym)
+        self.M, self.bbc = poisson.assemble(self.geom, self.bc, self.bcval)
+        self.dt = wl.dt
+        self.step_index = 0
+        self.species = []
+        for s, ps in zip(wl.species, wl.particles):
+            idx = unpack_cells(ps.cell, self.D)
+            if precision == "fp64":
+                t, v = ps.t.astype(np.float64), ps.v.astype(np.float64)
+            else:
+                t, v = ps.t.copy(), ps.v.copy()
+            self.species.append(SpeciesState(s.q, s.m, s.w, idx, t, v, np.zeros(2 * self.D, np.int64)))
+        self.injection = list(wl.injection)
+        self.phi = np.zeros(self.geom.Jc.shape)
+        self.history = []
+        self.injected = [0] * len(self.species)
+
+    # ---- steps ---------------------------------------------------------------------
+    def charge(self):
+        """Q_c (numpy cell layout)."""
+        Q = self.wl.background * self.geom.Jc
+        for sp in self.species:
+            if self.precision == "fp64":
+                C = dep.deposit_exact(sp.idx, sp.t, self.n, self.periodic)
+                Q = Q + (sp.q * sp.w) * C
+            else:
+                C = dep.deposit_fixed(sp.idx, sp.t, self.n, self.periodic)
+                Q = Q + (sp.q * sp.w) * np.ldexp(C.astype(np.float64), -dep.QF)
+        return Q
+
+    def solve(self):
+        self.Q = self.charge()
+        self.phi = poisson.solve(self.geom, self.M, self.bbc, self.Q, self.bc)
+        return self.phi
+
+    def field_tables(self):
+        G = gradient.vertex_gradient(self.phi, self.bc, self.bcval)
+        if self.precision == "fp64":
+            return self.geom.k, G
+        return self.geom.k.astype(np.float32), G.astype(np.float32)
+
+    def initialize(self):
+        self.solve()
+        k, G = self.field_tables()
+        for sp in self.species:
+            qm = sp.q / sp.m
+            if self.precision == "fp64":
+                sp.v = mover.kick64(sp.idx, sp.t, sp.v, k, G, -0.5 * self.dt * qm)
+            else:
+                sp.v = mover.kick32(sp.idx, sp.t, sp.v, k, G, self.n, np.float32(-0.5 * self.dt * qm))
+
+    def step(self):
+        we = 0.5 * float(np.sum(self.phi * self.Q))
+        k, G = self.field_tables()
+        ke = []
+        for s, sp in enumerate(self.species):
+            qm = sp.q / sp.m
+            if self.precision == "fp64":
+                vold = sp.v
+                idx, t, v, face = mover.push64(sp.idx, sp.t, sp.v, k, G, self.dt, qm, self.n, self.pbc)
+                ke.append(0.5 * sp.m * sp.w * float(np.sum(vold * v)))
+            else:
+                idx, t, v, face, kefp = mover.push32(
+                    sp.idx, sp.t, sp.v, k, G, self.n, self.pbc,
+                    np.float32(self.dt * qm), np.float32(0.5 * self.dt), np.float32(self.dt))
+                ke.append(0.5 * sp.m * sp.w * float(np.ldexp(float(kefp.sum()), -24)))
+            alive = face < 0
+            for f in range(2 * self.D):
+                sp.absorbed[f] += int(np.sum(face == f))
+            sp.idx, sp.t, sp.v = idx[:, alive].astype(np.int64), t[:, alive], v[:, alive]
+        for (s, face, dens, vth, seed) in self.injection:
+            sp = self.species[s]
+            side = face % 2
+            area = inject.face_length_2d(self.geom.X, side)
+            rate = inject.rate_per_step(dens, vth, area, self.dt, sp.w)
+            cnt = inject.count_at_step(rate, self.step_index)
+            if cnt == 0:
+                continue
+            idx, t32, v32, _ = inject.inject_2d(self.geom.k, self.n, side, cnt, self.step_index, s, seed,
+                                                vth, (0.0, 0.0, 0.0), self.dt)
+            self.injected[s] += idx.shape[1]
+            if self.precision == "fp64":
+                t32, v32 = t32.astype(np.float64), v32.astype(np.float64)
+            sp.idx = np.concatenate([sp.idx, idx], axis=1)
+            sp.t = np.concatenate([sp.t, t32], axis=1)
+            sp.v = np.concatenate([sp.v, v32], axis=1)
+        self.solve()
+        self.step_index += 1
+        self.history.append({"step": self.step_index, "W_E": we, "W_K": sum(ke),
+                             "n": [sp.idx.shape[1] for sp in self.species],
+                             "absorbed": [sp.absorbed.copy() for sp in self.species]})
+        return self.history[-1]

@@ -1,0 +1,193 @@
+/* FP32 replay of the hybrid mover's operation sequence (spec R). Test infrastructure: only
+ * the test suite, the smoke check and the benchmark's CPU-baseline leg may load it.
+ *
+ * Sec. II.B.4, eqs. (hybridx), (step1)-(step4): full-step kick with the field gathered at
+ * xi^n (eq. (step1); unmagnetised, so the Boris rotation is the identity), predictor
+ * xi' = xi^n + dt/2 k(xi^n) v^{n+1/2} (eq. (step2)), k re-interpolated at xi' with b1
+ * weights (eq. (step3)), corrector xi^{n+1} = xi^n + dt k(xi') v^{n+1/2} (eq. (step4)).
+ * b1 weights and vertex interpolation: Sec. II.B.2 eqs. (vvp), (Wvp), (b1).
+ *
+ * Positions are split: integer cell per axis + float offset t in [0, 1), cell units.
+ * Operation order (every rounding is part of the spec; compile with -ffp-contract=off):
+ *   s_a = 1 - t_a; corner weight w_o = product over axes of (o_a ? t_a : s_a), multiplied
+ *   from axis 0 upwards; corners in order o = 0 .. 2^D - 1 (bit a = offset along axis a);
+ *   gather acc = w_0 * Q_0, then acc = fmaf(w_o, Q_o, acc) for o = 1 ...
+ *   E^al = -(fmaf chain over a of K^{a al} G^a, starting with K^{0 al} * G^0)
+ *   v^al = fmaf(dtqm, E^al, v^al) for al < D
+ *   d_a = fmaf chain over al < D of K^{a al} v^al, starting with K^{a0} * v^0
+ *   t'_a = fmaf(hdt, d_a, t_a); renormalise + clamp (below); K' = gather at (cell', t')
+ *   t_a^{n+1} = fmaf(dt, d'_a, t_a) with d' from K'; renormalise + boundary.
+ * Renormalisation of x on axis a: c = floorf(x), f = x - c, if f >= 1 then f = 0, c += 1;
+ * c is clamped to [-2^24, 2^24] before conversion. Predictor point: periodic axes wrap,
+ * other axes clamp to (0, 0) below and (N-1, 1) above (reading: the paper is silent on a
+ * predictor point outside the domain). Final point: periodic wrap; a cell index below 0 or
+ * at/above N on an absorbing axis removes the particle (Sec. II.B.4: a particle leaves the
+ * domain when a logical coordinate becomes < 0 or > 1); the lowest such axis names the
+ * face. A non-finite final offset also removes the particle (reported separately).
+ */
+#include <math.h>
+#include <stdint.h>
+
+#define PBC_PERIODIC 0
+#define PBC_ABSORB 1
+
+static int wrap(int c, int n) {
+    int r = c % n;
+    return r < 0 ? r + n : r;
+}
+
+static void renorm(float x, float* f, int* c) {
+    float cf = floorf(x);
+    float fr = x - cf;
+    if (fr >= 1.0f) {
+        fr = 0.0f;
+        cf = cf + 1.0f;
+    }
+    if (cf < -16777216.0f) cf = -16777216.0f;
+    if (cf > 16777216.0f) cf = 16777216.0f;
+    *f = fr;
+    *c = (int)cf;
+}
+
+/* vertex table index of vertex (i, j[, k]) with N_a + 1 vertices per axis */
+static long vtx(int D, const int* n, const int* c) {
+    long v = c[D - 1];
+    for (int a = D - 2; a >= 0; --a) v = v * (n[a] + 1) + c[a];
+    return v;
+}
+
+/* gather nq components of table Q (nq floats per vertex) at (cell c, offsets t) */
+static void gather(int D, const int* n, const float* Q, int nq, const int* c, const float* t,
+                   float* out) {
+    float s[3], w[8];
+    int nc = 1 << D;
+    for (int a = 0; a < D; ++a) s[a] = 1.0f - t[a];
+    for (int o = 0; o < nc; ++o) {
+        float ww = (o & 1) ? t[0] : s[0];
+        for (int a = 1; a < D; ++a) ww = ww * (((o >> a) & 1) ? t[a] : s[a]);
+        w[o] = ww;
+    }
+    for (int q = 0; q < nq; ++q) out[q] = 0.0f;
+    for (int o = 0; o < nc; ++o) {
+        int cc[3];
+        for (int a = 0; a < D; ++a) cc[a] = c[a] + ((o >> a) & 1);
+        const float* rec = Q + vtx(D, n, cc) * nq;
+        for (int q = 0; q < nq; ++q) out[q] = (o == 0) ? (w[0] * rec[q]) : fmaf(w[o], rec[q], out[q]);
+    }
+}
+
+/* One push of np particles. idx: (D, np) int32 per-axis cells; t: (D, np); v: (3, np);
+ * K: vertex table of D*D floats [a][al]; G: vertex table of D floats.
+ * pbc[2a+side]: particle boundary kinds. Outputs in place; face[p] = -1 alive, 2a+side
+ * absorbed, 2*D non-finite. ke_fp[p] = llrint((v_old . v_new) * 2^24) (spec D). */
+void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* t, float* v,
+                 const float* K, const float* G, float dtqm, float hdt, float dt, int* face,
+                 long long* ke_fp) {
+    for (long p = 0; p < np; ++p) {
+        int c[3];
+        float tt[3], vv[3], vo[3];
+        for (int a = 0; a < D; ++a) {
+            c[a] = idx[a * np + p];
+            tt[a] = t[a * np + p];
+        }
+        for (int al = 0; al < 3; ++al) vo[al] = vv[al] = v[al * np + p];
+
+        float kp[9], gp[3];
+        gather(D, n, K, D * D, c, tt, kp);
+        gather(D, n, G, D, c, tt, gp);
+        for (int al = 0; al < D; ++al) {
+            float e = kp[0 * D + al] * gp[0];
+            for (int a = 1; a < D; ++a) e = fmaf(kp[a * D + al], gp[a], e);
+            e = -e;
+            vv[al] = fmaf(dtqm, e, vv[al]);
+        }
+        /* predictor */
+        int cp[3];
+        float tp[3];
+        for (int a = 0; a < D; ++a) {
+            float d = kp[a * D + 0] * vv[0];
+            for (int al = 1; al < D; ++al) d = fmaf(kp[a * D + al], vv[al], d);
+            float x = fmaf(hdt, d, tt[a]);
+            if (!isfinite(x)) {
+                cp[a] = c[a];
+                tp[a] = tt[a];
+                continue;
+            }
+            int dc;
+            renorm(x, &tp[a], &dc);
+            int ci = c[a] + dc;
+            if (pbc[2 * a] == PBC_PERIODIC) {
+                ci = wrap(ci, n[a]);
+            } else if (ci < 0) {
+                ci = 0;
+                tp[a] = 0.0f;
+            } else if (ci >= n[a]) {
+                ci = n[a] - 1;
+                tp[a] = 1.0f;
+            }
+            cp[a] = ci;
+        }
+        float kq[9];
+        gather(D, n, K, D * D, cp, tp, kq);
+        /* corrector */
+        int fc = -1;
+        int cn[3];
+        float tn[3];
+        for (int a = 0; a < D; ++a) {
+            float d = kq[a * D + 0] * vv[0];
+            for (int al = 1; al < D; ++al) d = fmaf(kq[a * D + al], vv[al], d);
+            float x = fmaf(dt, d, tt[a]);
+            if (!isfinite(x)) {
+                fc = 2 * D;
+                cn[a] = c[a];
+                tn[a] = tt[a];
+                continue;
+            }
+            int dc;
+            renorm(x, &tn[a], &dc);
+            cn[a] = c[a] + dc;
+        }
+        if (fc < 0) {
+            for (int a = 0; a < D; ++a) {
+                if (pbc[2 * a] == PBC_PERIODIC) {
+                    cn[a] = wrap(cn[a], n[a]);
+                } else if (cn[a] < 0) {
+                    if (fc < 0) fc = 2 * a;
+                } else if (cn[a] >= n[a]) {
+                    if (fc < 0) fc = 2 * a + 1;
+                }
+            }
+        }
+        double ke = ((double)vo[0] * (double)vv[0] + (double)vo[1] * (double)vv[1]) + (double)vo[2] * (double)vv[2];
+        ke_fp[p] = llrint(ldexp(ke, 24));
+        face[p] = fc;
+        for (int a = 0; a < D; ++a) {
+            idx[a * np + p] = fc < 0 ? cn[a] : -1;
+            t[a * np + p] = tn[a];
+        }
+        for (int al = 0; al < 3; ++al) v[al * np + p] = vv[al];
+    }
+}
+
+/* Half kick (leapfrog start-up, v^{-1/2} = v^0 - dt/2 q/m E(xi^0)): only the gather and
+ * kick of the push, with the given (negative) coefficient. */
+void replay_kick(int D, const int* n, long np, const int* idx, const float* t, float* v,
+                 const float* K, const float* G, float coef) {
+    for (long p = 0; p < np; ++p) {
+        int c[3];
+        float tt[3];
+        for (int a = 0; a < D; ++a) {
+            c[a] = idx[a * np + p];
+            tt[a] = t[a * np + p];
+        }
+        float kp[9], gp[3];
+        gather(D, n, K, D * D, c, tt, kp);
+        gather(D, n, G, D, c, tt, gp);
+        for (int al = 0; al < D; ++al) {
+            float e = kp[0 * D + al] * gp[0];
+            for (int a = 1; a < D; ++a) e = fmaf(kp[a * D + al], gp[a], e);
+            e = -e;
+            v[al * np + p] = fmaf(coef, e, v[al * np + p]);
+        }
+    }
+}

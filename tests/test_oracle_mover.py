@@ -1,0 +1,172 @@
+"""Pins of the oracle's hybrid mover (Sec. II.B.4) in FP64 and of its FP32 replay."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import geometry, gradient, mover, poisson
+from paper_1311_2286_gb300 import workloads as wl
+
+P, Dr = poisson.BC_PERIODIC, poisson.BC_DIRICHLET
+PP, PA = mover.PBC_PERIODIC, mover.PBC_ABSORB
+
+
+def _uniform(n1, n2):
+    return geometry.build_geometry(wl.map2_vertices(n1, n2, 0.0), [True, True])
+
+
+def test_free_streaming_on_uniform_map():
+    """With zero field, xi advances by dt k v = dt N v in cell units (eq. (hybridx))."""
+    n = (16, 8)
+    g = _uniform(*n)
+    rng = np.random.default_rng(0)
+    idx = np.stack([rng.integers(0, 16, 100), rng.integers(0, 8, 100)])
+    t = rng.random((2, 100))
+    v = rng.standard_normal((3, 100)) * 0.3
+    G = np.zeros(g.k.shape[:-1])
+    i2, t2, v2, face = mover.push64(idx, t, v, g.k, G, 0.1, -1.0, n, [PP] * 4)
+    for a in range(2):
+        u0 = idx[a] + t[a] + 0.1 * n[a] * v[a]
+        np.testing.assert_allclose(i2[a] + t2[a], np.mod(u0, n[a]), atol=1e-12)
+    np.testing.assert_array_equal(v2, v)
+    assert np.all(face == -1)
+
+
+def test_kick_in_uniform_logical_field():
+    """G = const on the uniform map: E = -k^T G = -N G, v^{n+1/2} = v + dt (q/m) E."""
+    n = (8, 8)
+    g = _uniform(*n)
+    G = np.zeros(g.k.shape[:-1])
+    G[..., 0] = 0.02
+    G[..., 1] = -0.01
+    idx = np.array([[2, 5], [3, 1]])
+    t = np.array([[0.1, 0.9], [0.4, 0.2]])
+    v = np.zeros((3, 2))
+    _, _, v2, _ = mover.push64(idx, t, v, g.k, G, 0.1, -1.0, n, [PP] * 4)
+    np.testing.assert_allclose(v2[0], -1.0 * 0.1 * (-8 * 0.02), rtol=1e-12)
+    np.testing.assert_allclose(v2[1], -1.0 * 0.1 * (-8 * -0.01), rtol=1e-12)
+    assert np.all(v2[2] == 0)
+
+
+def test_reversibility_uniform_map():
+    """P6: on the uniform map with a frozen field the push is time reversible: N steps,
+    then restart from (x^N, -v^{N+1/2}) for N steps, returns to x^0 within 1e-12."""
+    n = (16, 16)
+    g = _uniform(*n)
+    rng = np.random.default_rng(5)
+    phi = wl.random_field(rng, (16, 16), 0.05)
+    G = gradient.vertex_gradient(phi, [P] * 4, [0.0] * 4)
+    npart = 200
+    idx0 = np.stack([rng.integers(0, 16, npart), rng.integers(0, 16, npart)])
+    t0 = rng.random((2, npart))
+    v0 = rng.standard_normal((3, npart)) * 0.05
+    idx, t, v = idx0, t0, v0
+    steps, dt, qm = 40, 0.1, -1.0
+    for _ in range(steps):
+        idx, t, v, _ = mover.push64(idx, t, v, g.k, G, dt, qm, n, [PP] * 4)
+    # v^{N+1/2} from one more kick at x^N
+    vN = mover.kick64(idx, t, v, g.k, G, dt * qm)
+    idx, t, v = idx, t, -vN
+    for _ in range(steps):
+        idx, t, v, _ = mover.push64(idx, t, v, g.k, G, dt, qm, n, [PP] * 4)
+    u_back = idx + t
+    u0 = idx0 + t0
+    dist = np.abs(((u_back - u0) + 8) % 16 - 8)
+    assert np.max(dist) < 1e-12
+
+
+def _map2_x(u, n, eps):
+    xi, eta = u[0] / n, u[1] / n
+    s = eps * np.sin(2 * np.pi * xi) * np.sin(2 * np.pi * eta)
+    return np.stack([xi + s, eta + s])
+
+
+def test_predictor_corrector_second_order_on_distorted_map():
+    """Sec. II.B.4: on a non-orthogonal mesh the predictor-corrector regains second-order
+    accuracy in time. With E = 0 the logical trajectory solves du/dt = k(u) v; against a
+    fine-dt reference on the same grid the error drops 4x when dt halves, and the end point
+    mapped through the exact map lies on the straight physical line x0 + v T up to the
+    metric's O(h^2) error."""
+    n, eps = 512, 0.1
+    g = geometry.build_geometry(wl.map2_vertices(n, n, eps), [True, True])
+    G = np.zeros(g.k.shape[:-1])
+    rng = np.random.default_rng(6)
+    npart = 64
+    u0 = rng.random((2, npart)) * n
+    v = np.zeros((3, npart))
+    v[0] = 0.25
+    v[1] = -0.15
+    T = 0.4
+
+    def run(dt):
+        idx = np.floor(u0).astype(np.int64)
+        t = u0 - idx
+        for _ in range(int(round(T / dt))):
+            idx, t, _, _ = mover.push64(idx, t, v, g.k, G, dt, 0.0, (n, n), [PP] * 4)
+        return idx + t
+
+    ref = run(0.00125)
+    e = []
+    for dt in (0.02, 0.01):
+        d = (run(dt) - ref + n / 2) % n - n / 2
+        e.append(np.max(np.abs(d)))
+    assert 3.6 < e[0] / e[1] < 4.4
+    x_end = _map2_x(ref, n, eps)
+    x_ref = _map2_x(u0, n, eps) + T * v[:2]
+    d = (x_end - x_ref + 0.5) % 1.0 - 0.5
+    assert np.max(np.abs(d)) < 4.0 / n ** 2
+
+
+def test_absorption_faces_and_edge_cases():
+    """Leaving through xi < 0 or xi >= 1 removes the particle (Sec. II.B.4); an offset of
+    exactly 0 on cell 0 stays inside, a coordinate of exactly N leaves."""
+    n = (8, 8)
+    g = _uniform(*n)
+    G = np.zeros(g.k.shape[:-1])
+    pbc = [PA, PA, PP, PP]
+    idx = np.array([[0, 7, 0, 7, 3], [1, 2, 3, 4, 5]])
+    t = np.array([[0.1, 0.9, 0.5, 0.5, 0.5], [0.5, 0.5, 0.5, 0.5, 0.5]])
+    v = np.zeros((3, 5))
+    # displacement dt*N*v in cell units: -0.2, +0.2, exactly -0.5 (lands on 0), +0.5 (lands on 8)
+    v[0] = np.array([-0.25, 0.25, -0.625, 0.625, 0.0])
+    _, t2, _, face = mover.push64(idx, t, v, g.k, G, 0.1, 0.0, n, pbc)
+    assert list(face) == [0, 1, -1, 1, -1]
+    assert t2[0, 2] == 0.0
+
+
+def test_replay32_matches_fp64_single_step():
+    """The FP32 replay of spec R agrees with the FP64 mover to the single-step tolerance
+    (normwise 1e-5 on global xi and on v) on the distorted map with a random field."""
+    n = (32, 32)
+    g = geometry.build_geometry(wl.map2_vertices(32, 32, 0.05), [True, True])
+    rng = np.random.default_rng(7)
+    phi = wl.random_field(rng, (32, 32), 0.3)
+    G = gradient.vertex_gradient(phi, [P] * 4, [0.0] * 4)
+    ps = wl.load_uniform_logical(rng, n, 20000, 0.5)
+    idx = np.stack([ps.cell & 0xFFFF, ps.cell >> 16]).astype(np.int64)
+    i64, t64, v64, f64 = mover.push64(idx, ps.t.astype(np.float64), ps.v.astype(np.float64), g.k, G, 0.1, -1.0, n, [PP] * 4)
+    i32, t32, v32, f32, ke = mover.push32(idx, ps.t, ps.v, g.k.astype(np.float32), G.astype(np.float32), n, [PP] * 4,
+                                          np.float32(-0.1), np.float32(0.05), np.float32(0.1))
+    u64 = (i64 + t64) / 32.0
+    u32 = (i32 + t32.astype(np.float64)) / 32.0
+    du = np.abs(u32 - u64)
+    du = np.minimum(du, 1.0 - du)
+    assert np.max(du) / np.max(np.abs(u64)) < 1e-5
+    assert np.max(np.abs(v32 - v64)) / np.max(np.abs(v64)) < 1e-5
+    ke64 = np.sum(ps.v.astype(np.float64) * v32.astype(np.float64), axis=0)
+    assert np.all(ke == np.rint(np.ldexp(ke64, 24)).astype(np.int64)) or np.max(np.abs(ke - np.ldexp(ke64, 24))) <= 1
+
+
+def test_replay32_deterministic_and_absorbs():
+    n = (16, 16)
+    g = _uniform(*n)
+    G32 = np.zeros(g.k.shape[:-1], np.float32)
+    idx = np.array([[0, 15], [3, 4]])
+    t = np.array([[0.1, 0.9], [0.5, 0.5]], np.float32)
+    v = np.zeros((3, 2), np.float32)
+    v[0] = [-0.5, 0.5]
+    a = mover.push32(idx, t, v, g.k.astype(np.float32), G32, n, [PA, PA, PP, PP], np.float32(0), np.float32(0.05), np.float32(0.1))
+    b = mover.push32(idx, t, v, g.k.astype(np.float32), G32, n, [PA, PA, PP, PP], np.float32(0), np.float32(0.05), np.float32(0.1))
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    assert list(a[3]) == [0, 1] and list(a[0][0]) == [-1, -1]
