@@ -1,0 +1,216 @@
+/*
+ * cpic.h - C ABI of the GB300-native curvilinear particle-in-cell hot path.
+ *
+ * Method: electrostatic PIC in curvilinear geometry (Delzanno et al., CPIC, arXiv 1311.2286).
+ * Particles keep a logical position xi in the unit cube (split into an int32 cell index per
+ * axis and an FP32 offset in [0, 1), "cell units") and a physical velocity (hybrid mover,
+ * Sec. II.B.4, eq. (hybridx)). One PIC step (Sec. II, four-step cycle): vertex field ->
+ * fused gather / push / boundary / deposit -> injection -> (sort) -> field solve.
+ *
+ * Conventions for every call:
+ *  - Return value: CPIC_OK (0) or a negative CPIC_ERR_* code; cpic_last_error() returns a
+ *    message for the calling thread's last failure (static storage, overwritten by the next
+ *    failure on that thread).
+ *  - Layout: logical axis a = 0, 1, 2 (xi, eta, zeta); cell arrays are indexed
+ *    i + N1 (j + N2 k) (i fastest); vertex arrays have N_a + 1 entries per axis (a periodic
+ *    axis repeats vertex 0 as vertex N_a) and are indexed i + (N1+1)(j + (N2+1) k).
+ *    Face f = 2 * axis + side (side 0 = low end, 1 = high end of the logical axis).
+ *  - Particle format (structure of arrays, one species per call): cell = int32 packed
+ *    per-axis cell indices (2D: i | j << 16, 3D: i | j << 10 | k << 20; dead = -1),
+ *    t = FP32 offsets [D][n], v = FP32 physical velocity [3][n] (three components also in
+ *    2D, Sec. III).
+ *  - Pointers marked "host or device" may point to either (unified addressing); every
+ *    other pointer is host memory. Host arrays are copied before the call returns.
+ *  - Work is enqueued on the run's stream (cpic_create / cpic_set_stream) and is
+ *    asynchronous unless the call says it synchronises; cpic_get_* calls synchronise.
+ *  - Ownership: a run owns the device memory it allocates; with a caller arena
+ *    (cpic_create) it allocates nothing and the caller keeps the arena alive until
+ *    cpic_destroy returns. A run is not thread safe: one thread at a time per run.
+ */
+#ifndef CPIC_H
+#define CPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CPIC_ABI_VERSION 1
+#define CPIC_MAX_SPECIES 4
+
+/* status codes */
+#define CPIC_OK 0
+#define CPIC_ERR_INVALID (-1)        /* bad argument or configuration */
+#define CPIC_ERR_OOM (-2)            /* device allocation failed or arena too small */
+#define CPIC_ERR_CUDA (-3)           /* a CUDA runtime call failed */
+#define CPIC_ERR_NOT_CONVERGED (-4)  /* field solve hit its cycle limit */
+#define CPIC_ERR_TIMEOUT (-5)        /* a bounded device wait ran out */
+#define CPIC_ERR_NONFINITE (-6)      /* particles with non-finite positions were removed */
+#define CPIC_ERR_BUSY (-7)           /* not done yet (serving) */
+#define CPIC_ERR_STATE (-8)          /* call out of order (e.g. step before a map is set) */
+#define CPIC_ERR_CAPACITY (-9)       /* particles dropped: species capacity exhausted */
+#define CPIC_ERR_NOT_BUILT (-10)     /* the library was built without the requested part */
+
+/* field boundary conditions (Sec. II.B.3: imposed through ghost cells) */
+#define CPIC_BC_PERIODIC 0
+#define CPIC_BC_DIRICHLET 1
+#define CPIC_BC_NEUMANN 2
+/* particle boundary conditions (Sec. II.B.4, Sec. III.A-B) */
+#define CPIC_PBC_PERIODIC 0
+#define CPIC_PBC_ABSORB 1
+#define CPIC_PBC_REFLECT 2
+
+/* analytic maps evaluated on the device (Sec. II.A eq. (map); Sec. II.B.4 eq. (map2);
+ * Sec. II.B.3 eqs. (r), (z)) */
+#define CPIC_MAP_SINE 1          /* params: eps            x = xi + eps sin(2 pi xi) sin(2 pi eta), y likewise */
+#define CPIC_MAP_ANNULUS 2       /* params: r0, R          r = r0 (R/r0)^xi, theta = 2 pi eta */
+#define CPIC_MAP_SPHERE_AXISYM 3 /* params: r1, r2         (r, z) = [r1 + (r2-r1) xi](sin, cos)(pi (1 - eta)) */
+#define CPIC_MAP_SHELL 4         /* params: r0, R, theta_c 3D: r = r0 (R/r0)^xi, theta = theta_c + (pi - 2 theta_c) eta, phi = 2 pi zeta */
+
+typedef struct cpic_run cpic_run;
+
+/* Run configuration (Sec. II: grid, boundary conditions, species in normalised units,
+ * Sec. II.B). Fixed for the life of a run. */
+typedef struct cpic_config {
+    int32_t dim;                  /* 2 or 3 */
+    int32_t n[3];                 /* cells per logical axis; 2D: n[2] ignored.
+                                     Limits: 2D n[0] < 65536, n[1] < 32768; 3D each < 1024 */
+    int32_t field_bc[6];          /* CPIC_BC_* per face; a periodic axis has both faces periodic */
+    double field_bc_value[6];     /* Dirichlet potential per face */
+    int32_t particle_bc[6];       /* CPIC_PBC_* per face; periodic iff the field axis is */
+    double dt;                    /* time step (normalised to 1/omega_pe) */
+    double background;            /* uniform immobile charge density (e.g. +1: neutralising ions) */
+    int32_t axisymmetric;         /* 1: geometric factor Omega = x^1 in the solver (eq. (poiscurv)) */
+    int32_t n_species;            /* 1 .. CPIC_MAX_SPECIES */
+    double q[CPIC_MAX_SPECIES];   /* charge of a physical particle */
+    double m[CPIC_MAX_SPECIES];   /* mass of a physical particle */
+    double w[CPIC_MAX_SPECIES];   /* physical particles per macro-particle */
+    int64_t capacity[CPIC_MAX_SPECIES]; /* particle slots per species (load + injection) */
+    int32_t sort_interval;        /* cpic_step sorts every this many steps (0 = never) */
+    int32_t mg_max_cycles;        /* V-cycle limit of the solve inside cpic_step (0: 30) */
+    double mg_rtol;               /* relative residual target of that solve (0: 1e-10, the
+                                     paper's tolerance, Sec. II.B.3) */
+} cpic_config;
+
+/* Diagnostics (Sec. III: potential, currents from absorbed particles, particle counts;
+ * Table IV: solver iterations). Energies: W_E = 1/2 sum_c phi_c Q_c at the current time
+ * level, W_K = sum_s 1/2 m_s w_s sum_p v^{n-1/2} . v^{n+1/2} of the last push. */
+typedef struct cpic_diag {
+    int64_t step;                          /* completed pushes */
+    double field_energy;
+    double kinetic_energy;
+    int64_t n_particles[CPIC_MAX_SPECIES]; /* live particles */
+    int64_t absorbed[CPIC_MAX_SPECIES][6]; /* cumulative, per face */
+    int64_t injected[CPIC_MAX_SPECIES];    /* cumulative */
+    int64_t dropped[CPIC_MAX_SPECIES];     /* cumulative, for lack of capacity */
+    int64_t nonfinite;                     /* cumulative */
+    int32_t mg_cycles;                     /* V-cycles of the last solve */
+    double mg_residual;                    /* relative residual of the last solve */
+} cpic_diag;
+
+/* ---------------------------------------------------------------- general */
+
+/* Message for a status code (static string). */
+const char* cpic_status_string(int status);
+/* Message of the calling thread's last failure (static thread-local storage). */
+const char* cpic_last_error(void);
+/* ABI version of the loaded library (CPIC_ABI_VERSION when it matches this header). */
+int cpic_abi_version(void);
+
+/* ---------------------------------------------------------------- setup */
+
+/* Device bytes a run with this configuration needs (the size of a caller arena).
+ * Pure host computation; no GPU work. */
+int cpic_query_footprint(const cpic_config* cfg, size_t* device_bytes);
+
+/* Create a run on the current device. arena: NULL (the run cudaMallocs its memory) or a
+ * device buffer of at least cpic_query_footprint bytes, 256-byte aligned, owned by the
+ * caller. stream: cudaStream_t to enqueue on (NULL = legacy default stream). */
+int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* stream,
+                cpic_run** out);
+/* Synchronise the run's stream and release it (frees what it allocated). NULL is a no-op. */
+int cpic_destroy(cpic_run* run);
+/* Enqueue subsequent work on another stream. */
+int cpic_set_stream(cpic_run* run, void* stream);
+
+/* Map from logical to physical space known at cell vertices (Sec. II.A, eq. (map) and its
+ * last paragraph: metric coefficients by finite differences of the vertex map).
+ * xyz: host or device, FP64 [vertex][D] in the vertex layout above. Computes on the device
+ * (FP64): k = j^-1 at vertices (eqs. (jcov), (jcon)), the cell Jacobians (eq. (jac)), the
+ * face coefficients Omega J g^{ab} (eqs. (gcon), (poiscurv)) for every multigrid level,
+ * and the FP32 vertex table of k used by the mover. */
+int cpic_set_map_vertices(cpic_run* run, const double* xyz);
+/* Same, with the map evaluated on the device from a CPIC_MAP_* formula. */
+int cpic_set_map_analytic(cpic_run* run, int map_id, const double* params, int nparams);
+
+/* ---------------------------------------------------------------- particles */
+
+/* Replace species sp's particles (Sec. III.B: initial load). cell, t, v: host or device,
+ * particle format above, n <= capacity. */
+int cpic_load_particles(cpic_run* run, int sp, int64_t n, const int32_t* cell, const float* t,
+                        const float* v);
+/* Copy species sp's live particles out (synchronises). cell, t, v: host or device with room
+ * for `room` particles; *n receives the count (CPIC_ERR_INVALID if room is too small). The
+ * order is the storage order (cell-sorted after cpic_sort, unspecified within a cell). */
+int cpic_get_particles(cpic_run* run, int sp, int64_t room, int64_t* n, int32_t* cell, float* t,
+                       float* v);
+/* Maxwellian flux injection through face `face` for species sp (Sec. III.A-B): density,
+ * thermal speed vth, drift (host, 3 doubles, may be NULL), Philox4x32-10 key `seed`.
+ * 2D faces normal to axis 0 only. */
+int cpic_set_injection(cpic_run* run, int sp, int face, double density, double vth,
+                       const double* drift, uint64_t seed);
+
+/* ---------------------------------------------------------------- the PIC cycle */
+
+/* Start-up: deposit rho^0 and solve phi^0, then v^{-1/2} = v^0 - dt/2 (q/m) E(xi^0)
+ * (standard leapfrog start-up for eq. (step1)). */
+int cpic_initialize(cpic_run* run);
+/* nsteps full PIC steps (Sec. II cycle): vertex field, push (+ deposit), injection, sort
+ * every sort_interval steps, charge -> RHS, multigrid solve to mg_rtol, diagnostics. */
+int cpic_step(cpic_run* run, int nsteps);
+
+/* Rows of one step, for callers that drive the cycle themselves: */
+/* a1: G = d phi / d u at vertices from the cell potential (Sec. II.B staggering). */
+int cpic_vertex_field(cpic_run* run);
+/* a2-a6: for every live particle: b1 gather of G and k at xi^n (eqs. (vvp), (Wvp), (b1)),
+ * E = -k^T G, kick (eq. (step1)), predictor (eq. (step2)), k re-gather (eq. (step3)),
+ * corrector (eq. (step4)), boundaries (periodic / absorb), then the b2 deposit
+ * (eqs. (pg), (Wpc), (b2)) in 64-bit fixed point into freshly zeroed charge grids.
+ * Advances the step counter. */
+int cpic_push(cpic_run* run);
+/* a6 alone: zero the charge grids and deposit every live particle. */
+int cpic_deposit(cpic_run* run);
+/* Gather and kick only: v += fraction * dt (q/m) E(xi) (fraction = -0.5: start-up). */
+int cpic_kick(cpic_run* run, double fraction);
+/* a8: inject this step's particles (step index = completed pushes - 1) and deposit them. */
+int cpic_inject(cpic_run* run);
+/* a7: counting sort of every species by cell (row-major cell index), dropping dead slots. */
+int cpic_sort(cpic_run* run);
+/* a9: RHS from the charge grids (Omega_c Q_c plus Dirichlet terms), then multigrid
+ * V-cycles (Sec. II.B.3) until ||r||/||b|| <= rtol or max_cycles; synchronises once per
+ * cycle. cycles, residual: host, may be NULL. CPIC_ERR_NOT_CONVERGED if rtol was not met. */
+int cpic_solve_field(cpic_run* run, double rtol, int max_cycles, int* cycles, double* residual);
+
+/* ---------------------------------------------------------------- data out / in */
+
+int cpic_get_diag(cpic_run* run, cpic_diag* out);              /* synchronises */
+int cpic_get_phi(cpic_run* run, double* phi);                  /* host or device, cells */
+int cpic_set_phi(cpic_run* run, const double* phi);            /* host or device, cells */
+int cpic_get_charge(cpic_run* run, int sp, int64_t* counts);   /* host or device, cells;
+                                                                  units of 2^-24 particles */
+/* FP32 vertex tables used by the mover: k [vertex][D][D] (cell units, k[a][alpha]) and
+ * G [vertex][D]; host or device; either may be NULL. */
+int cpic_get_vertex_tables(cpic_run* run, float* k, float* g);
+/* FP64 metric of the finest grid: k [vertex][D][D], cell Jacobians J_c [cell]; host or
+ * device; either may be NULL. */
+int cpic_get_geometry(cpic_run* run, double* k, double* jc);
+/* Wait for the run's stream. */
+int cpic_synchronize(cpic_run* run);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPIC_H */

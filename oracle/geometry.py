@@ -22,6 +22,12 @@ from dataclasses import dataclass
 import numpy as np
 
 
+# A cross coefficient a^{ab} (b != a) no larger than this fraction of the face's a^{aa} is
+# the rounding residue of an orthogonal map and is set to zero, so that orthogonal maps give
+# exact 5-point (2D) / 7-point (3D) operators (reading; applied identically on the device).
+CROSS_ROUNDOFF = 1e-12
+
+
 def _ax(D: int, a: int) -> int:
     return D - 1 - a
 
@@ -204,6 +210,8 @@ def face_coefficients_2d(X, dv, axisym):
     om2 = (X[:, :-1, 0] + X[:, 1:, 0]) * 0.5 if axisym else np.ones(J2.shape)
     a_vv = (om2 * dot(xu2, xu2)) / J2
     a_vu = -((om2 * dot(xu2, xv2)) / J2)
+    a_uv = np.where(np.abs(a_uv) <= CROSS_ROUNDOFF * np.abs(a_uu), 0.0, a_uv)
+    a_vu = np.where(np.abs(a_vu) <= CROSS_ROUNDOFF * np.abs(a_vv), 0.0, a_vu)
     return [[a_uu, a_uv], [a_vu, a_vv]]
 
 
@@ -241,7 +249,11 @@ def face_coefficients_3d(X, dv):
         # contravariant basis times J: A^b = x_{b+1} x x_{b+2}
         A = [cross(d[1], d[2]), cross(d[2], d[0]), cross(d[0], d[1])]
         J = dot(d[0], A[0])
-        out.append([dot(A[a], A[b]) / J for b in range(3)])
+        coef = [dot(A[a], A[b]) / J for b in range(3)]
+        for b in range(3):
+            if b != a:
+                coef[b] = np.where(np.abs(coef[b]) <= CROSS_ROUNDOFF * np.abs(coef[a]), 0.0, coef[b])
+        out.append(coef)
     return out
 
 

@@ -79,7 +79,8 @@ static void gather(int D, const int* n, const float* Q, int nq, const int* c, co
 /* One push of np particles. idx: (D, np) int32 per-axis cells; t: (D, np); v: (3, np);
  * K: vertex table of D*D floats [a][al]; G: vertex table of D floats.
  * pbc[2a+side]: particle boundary kinds. Outputs in place; face[p] = -1 alive, 2a+side
- * absorbed, 2*D non-finite. ke_fp[p] = llrint((v_old . v_new) * 2^24) (spec D). */
+ * absorbed, 2*D non-finite. ke_fp[p] = llrintf(ke * 2^24) with the FP32 product
+ * ke = fmaf(vo2, v2, fmaf(vo1, v1, vo0 * v0)) (spec D). */
 void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* t, float* v,
                  const float* K, const float* G, float dtqm, float hdt, float dt, int* face,
                  long long* ke_fp) {
@@ -158,8 +159,8 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
                 }
             }
         }
-        double ke = ((double)vo[0] * (double)vv[0] + (double)vo[1] * (double)vv[1]) + (double)vo[2] * (double)vv[2];
-        ke_fp[p] = llrint(ldexp(ke, 24));
+        float ke = fmaf(vo[2], vv[2], fmaf(vo[1], vv[1], vo[0] * vv[0]));
+        ke_fp[p] = llrintf(ldexpf(ke, 24));
         face[p] = fc;
         for (int a = 0; a < D; ++a) {
             idx[a * np + p] = fc < 0 ? cn[a] : -1;

@@ -1,0 +1,346 @@
+"""Thin ctypes binding of include/cpic.h (argument marshalling only).
+
+Every function of the C ABI is exposed under the same name and returns the status code;
+``check`` turns a non-zero status into an exception carrying cpic_last_error(). The
+``Run`` class wraps one run handle for convenience (numpy in, numpy out; torch tensors may
+be passed for device pointers). No arithmetic of the method happens here: if the compiled
+library is missing, ``load`` raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcpic.so")
+
+CPIC_OK = 0
+CPIC_ERR_INVALID, CPIC_ERR_OOM, CPIC_ERR_CUDA, CPIC_ERR_NOT_CONVERGED = -1, -2, -3, -4
+CPIC_ERR_TIMEOUT, CPIC_ERR_NONFINITE, CPIC_ERR_BUSY, CPIC_ERR_STATE = -5, -6, -7, -8
+CPIC_ERR_CAPACITY, CPIC_ERR_NOT_BUILT = -9, -10
+CPIC_BC_PERIODIC, CPIC_BC_DIRICHLET, CPIC_BC_NEUMANN = 0, 1, 2
+CPIC_PBC_PERIODIC, CPIC_PBC_ABSORB, CPIC_PBC_REFLECT = 0, 1, 2
+CPIC_MAP_SINE, CPIC_MAP_ANNULUS, CPIC_MAP_SPHERE_AXISYM, CPIC_MAP_SHELL = 1, 2, 3, 4
+MAX_SPECIES = 4
+
+
+class cpic_config(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32),
+        ("n", ctypes.c_int32 * 3),
+        ("field_bc", ctypes.c_int32 * 6),
+        ("field_bc_value", ctypes.c_double * 6),
+        ("particle_bc", ctypes.c_int32 * 6),
+        ("dt", ctypes.c_double),
+        ("background", ctypes.c_double),
+        ("axisymmetric", ctypes.c_int32),
+        ("n_species", ctypes.c_int32),
+        ("q", ctypes.c_double * MAX_SPECIES),
+        ("m", ctypes.c_double * MAX_SPECIES),
+        ("w", ctypes.c_double * MAX_SPECIES),
+        ("capacity", ctypes.c_int64 * MAX_SPECIES),
+        ("sort_interval", ctypes.c_int32),
+        ("mg_max_cycles", ctypes.c_int32),
+        ("mg_rtol", ctypes.c_double),
+    ]
+
+
+class cpic_diag(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64),
+        ("field_energy", ctypes.c_double),
+        ("kinetic_energy", ctypes.c_double),
+        ("n_particles", ctypes.c_int64 * MAX_SPECIES),
+        ("absorbed", (ctypes.c_int64 * 6) * MAX_SPECIES),
+        ("injected", ctypes.c_int64 * MAX_SPECIES),
+        ("dropped", ctypes.c_int64 * MAX_SPECIES),
+        ("nonfinite", ctypes.c_int64),
+        ("mg_cycles", ctypes.c_int32),
+        ("mg_residual", ctypes.c_double),
+    ]
+
+
+_lib = None
+P = ctypes.c_void_p
+_SIGS = {
+    "cpic_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "cpic_last_error": ([], ctypes.c_char_p),
+    "cpic_abi_version": ([], ctypes.c_int),
+    "cpic_query_footprint": ([ctypes.POINTER(cpic_config), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "cpic_create": ([ctypes.POINTER(cpic_config), P, ctypes.c_size_t, P, ctypes.POINTER(P)], ctypes.c_int),
+    "cpic_destroy": ([P], ctypes.c_int),
+    "cpic_set_stream": ([P, P], ctypes.c_int),
+    "cpic_set_map_vertices": ([P, P], ctypes.c_int),
+    "cpic_set_map_analytic": ([P, ctypes.c_int, P, ctypes.c_int], ctypes.c_int),
+    "cpic_load_particles": ([P, ctypes.c_int, ctypes.c_int64, P, P, P], ctypes.c_int),
+    "cpic_get_particles": ([P, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), P, P, P], ctypes.c_int),
+    "cpic_set_injection": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, ctypes.c_uint64],
+                           ctypes.c_int),
+    "cpic_initialize": ([P], ctypes.c_int),
+    "cpic_step": ([P, ctypes.c_int], ctypes.c_int),
+    "cpic_vertex_field": ([P], ctypes.c_int),
+    "cpic_push": ([P], ctypes.c_int),
+    "cpic_deposit": ([P], ctypes.c_int),
+    "cpic_kick": ([P, ctypes.c_double], ctypes.c_int),
+    "cpic_inject": ([P], ctypes.c_int),
+    "cpic_sort": ([P], ctypes.c_int),
+    "cpic_solve_field": ([P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cpic_get_diag": ([P, ctypes.POINTER(cpic_diag)], ctypes.c_int),
+    "cpic_get_phi": ([P, P], ctypes.c_int),
+    "cpic_set_phi": ([P, P], ctypes.c_int),
+    "cpic_get_charge": ([P, ctypes.c_int, P], ctypes.c_int),
+    "cpic_get_vertex_tables": ([P, P, P], ctypes.c_int),
+    "cpic_get_geometry": ([P, P, P], ctypes.c_int),
+    "cpic_synchronize": ([P], ctypes.c_int),
+}
+
+
+class CpicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"cpic status {status}: {msg}")
+        self.status = status
+
+
+def load(path: str | None = None):
+    """Load libcpic.so (built by paper_1311_2286_gb300/build.py). Raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def check(status: int):
+    if status != CPIC_OK:
+        msg = load().cpic_last_error()
+        raise CpicError(status, msg.decode() if msg else "")
+    return status
+
+
+def __getattr__(name):
+    if name.startswith("cpic_") and name in _SIGS:
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+def _ptr(a):
+    """Pointer of a numpy array (host) or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_config(dim, n, field_bc, field_bc_value, particle_bc, dt, species, background=0.0,
+                axisymmetric=False, sort_interval=0, mg_max_cycles=0, mg_rtol=0.0):
+    """species: list of (q, m, w, capacity)."""
+    c = cpic_config()
+    c.dim = dim
+    for a in range(3):
+        c.n[a] = n[a] if a < len(n) else 1
+    for f in range(6):
+        c.field_bc[f] = field_bc[f] if f < len(field_bc) else 0
+        c.field_bc_value[f] = field_bc_value[f] if f < len(field_bc_value) else 0.0
+        c.particle_bc[f] = particle_bc[f] if f < len(particle_bc) else 0
+    c.dt = dt
+    c.background = background
+    c.axisymmetric = 1 if axisymmetric else 0
+    c.n_species = len(species)
+    for s, (q, m, w, cap) in enumerate(species):
+        c.q[s], c.m[s], c.w[s], c.capacity[s] = q, m, w, cap
+    c.sort_interval = sort_interval
+    c.mg_max_cycles = mg_max_cycles
+    c.mg_rtol = mg_rtol
+    return c
+
+
+def config_from_workload(wl, sort_interval=0, mg_max_cycles=0, mg_rtol=0.0):
+    return make_config(wl.dim, wl.n, wl.field_bc, wl.field_bc_value, wl.particle_bc, wl.dt,
+                       [(s.q, s.m, s.w, max(s.capacity, p.n)) for s, p in zip(wl.species, wl.particles)],
+                       background=wl.background, axisymmetric=wl.omega_axisym, sort_interval=sort_interval,
+                       mg_max_cycles=mg_max_cycles, mg_rtol=mg_rtol)
+
+
+class Run:
+    """One simulation run (owns its cpic_run handle)."""
+
+    def __init__(self, cfg: cpic_config, arena=None, stream=None):
+        lib = load()
+        self.cfg = cfg
+        self.D = cfg.dim
+        self.n = tuple(cfg.n[a] for a in range(cfg.dim))
+        self.ncell = int(np.prod(self.n))
+        self.nvert = int(np.prod([x + 1 for x in self.n]))
+        self._arena = arena
+        h = ctypes.c_void_p()
+        nbytes = 0
+        if arena is not None:
+            nbytes = arena.numel() * arena.element_size() if hasattr(arena, "numel") else arena.nbytes
+        check(lib.cpic_create(ctypes.byref(cfg), _ptr(arena), nbytes, stream, ctypes.byref(h)))
+        self.h = h
+
+    @staticmethod
+    def footprint(cfg: cpic_config) -> int:
+        n = ctypes.c_size_t()
+        check(load().cpic_query_footprint(ctypes.byref(cfg), ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(load().cpic_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- setup
+    def set_stream(self, stream):
+        check(load().cpic_set_stream(self.h, stream))
+
+    def set_map_vertices(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        check(load().cpic_set_map_vertices(self.h, _ptr(X)))
+
+    def set_map_analytic(self, map_id, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        check(load().cpic_set_map_analytic(self.h, map_id, _ptr(p), p.size))
+
+    def load_particles(self, sp, cell, t, v):
+        if hasattr(cell, "data_ptr"):
+            n = cell.shape[0]
+            check(load().cpic_load_particles(self.h, sp, n, _ptr(cell), _ptr(t), _ptr(v)))
+            return
+        cell = np.ascontiguousarray(cell, dtype=np.int32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        check(load().cpic_load_particles(self.h, sp, cell.shape[0], _ptr(cell), _ptr(t), _ptr(v)))
+
+    def set_injection(self, sp, face, density, vth, seed, drift=None):
+        d = None if drift is None else np.ascontiguousarray(drift, dtype=np.float64)
+        check(load().cpic_set_injection(self.h, sp, face, density, vth, _ptr(d), seed))
+
+    # ---- cycle
+    def initialize(self):
+        check(load().cpic_initialize(self.h))
+
+    def step(self, nsteps=1):
+        check(load().cpic_step(self.h, nsteps))
+
+    def vertex_field(self):
+        check(load().cpic_vertex_field(self.h))
+
+    def push(self):
+        check(load().cpic_push(self.h))
+
+    def deposit(self):
+        check(load().cpic_deposit(self.h))
+
+    def kick(self, fraction):
+        check(load().cpic_kick(self.h, fraction))
+
+    def inject(self):
+        check(load().cpic_inject(self.h))
+
+    def sort(self):
+        check(load().cpic_sort(self.h))
+
+    def solve_field(self, rtol=1e-10, max_cycles=50, allow_not_converged=False):
+        c = ctypes.c_int()
+        r = ctypes.c_double()
+        st = load().cpic_solve_field(self.h, rtol, max_cycles, ctypes.byref(c), ctypes.byref(r))
+        if not (allow_not_converged and st == CPIC_ERR_NOT_CONVERGED):
+            check(st)
+        return c.value, r.value
+
+    def synchronize(self):
+        check(load().cpic_synchronize(self.h))
+
+    # ---- data out
+    def diag(self) -> dict:
+        d = cpic_diag()
+        check(load().cpic_get_diag(self.h, ctypes.byref(d)))
+        ns = self.cfg.n_species
+        return {
+            "step": d.step, "W_E": d.field_energy, "W_K": d.kinetic_energy,
+            "n": [d.n_particles[s] for s in range(ns)],
+            "absorbed": [[d.absorbed[s][f] for f in range(2 * self.D)] for s in range(ns)],
+            "injected": [d.injected[s] for s in range(ns)], "dropped": [d.dropped[s] for s in range(ns)],
+            "nonfinite": d.nonfinite, "mg_cycles": d.mg_cycles, "mg_residual": d.mg_residual,
+        }
+
+    def phi(self):
+        out = np.empty(self.ncell, np.float64)
+        check(load().cpic_get_phi(self.h, _ptr(out)))
+        return out.reshape(tuple(reversed(self.n)))
+
+    def set_phi(self, phi):
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        check(load().cpic_set_phi(self.h, _ptr(phi)))
+
+    def charge(self, sp):
+        out = np.empty(self.ncell, np.int64)
+        check(load().cpic_get_charge(self.h, sp, _ptr(out)))
+        return out.reshape(tuple(reversed(self.n)))
+
+    def vertex_tables(self):
+        kw = 4 if self.D == 2 else 12
+        gw = 2 if self.D == 2 else 4
+        k = np.empty(self.nvert * kw, np.float32)
+        g = np.empty(self.nvert * gw, np.float32)
+        check(load().cpic_get_vertex_tables(self.h, _ptr(k), _ptr(g)))
+        vshape = tuple(reversed([x + 1 for x in self.n]))
+        k = k.reshape(vshape + (kw,))[..., : self.D * self.D].reshape(vshape + (self.D, self.D))
+        g = g.reshape(vshape + (gw,))[..., : self.D]
+        return k, g
+
+    def geometry(self):
+        k = np.empty(self.nvert * self.D * self.D, np.float64)
+        jc = np.empty(self.ncell, np.float64)
+        check(load().cpic_get_geometry(self.h, _ptr(k), _ptr(jc)))
+        vshape = tuple(reversed([x + 1 for x in self.n]))
+        return k.reshape(vshape + (self.D, self.D)), jc.reshape(tuple(reversed(self.n)))
+
+    def particles(self, sp):
+        cap = int(self.cfg.capacity[sp])
+        cell = np.empty(cap, np.int32)
+        t = np.empty(self.D * cap, np.float32)
+        v = np.empty(3 * cap, np.float32)
+        n = ctypes.c_int64()
+        check(load().cpic_get_particles(self.h, sp, cap, ctypes.byref(n), _ptr(cell), _ptr(t), _ptr(v)))
+        m = n.value
+        return cell[:m].copy(), t[: self.D * m].reshape(self.D, m).copy(), v[: 3 * m].reshape(3, m).copy()
+
+
+def run_from_workload(wl, sort_interval=0, analytic=None, mg_rtol=0.0, mg_max_cycles=0, arena=None, stream=None):
+    """Create a run for a workload (map from its vertex array unless analytic=(id, params)),
+    load its particles and injection sources."""
+    cfg = config_from_workload(wl, sort_interval=sort_interval, mg_rtol=mg_rtol, mg_max_cycles=mg_max_cycles)
+    run = Run(cfg, arena=arena, stream=stream)
+    if analytic is None:
+        run.set_map_vertices(wl.vertices)
+    else:
+        run.set_map_analytic(*analytic)
+    for s, ps in enumerate(wl.particles):
+        run.load_particles(s, ps.cell, ps.t, ps.v)
+    for (s, face, dens, vth, seed) in wl.injection:
+        run.set_injection(s, face, dens, vth, seed)
+    return run

@@ -1,0 +1,687 @@
+// C ABI of include/cpic.h: validation, device-memory planning (one arena per run), the PIC
+// cycle's orchestration on the run's stream, and data transfer. All arithmetic of the
+// method runs in the kernels of geometry.cu, fields.cu, push.cu, inject.cu, sort.cu, mg.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+namespace cpic {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    return e == cudaErrorMemoryAllocation ? CPIC_ERR_OOM : CPIC_ERR_CUDA;
+}
+
+namespace {
+
+// ------------------------------------------------------------------ memory planning
+struct Planner {
+    char* base = nullptr;  // null: dry run
+    size_t used = 0;
+    template <class T>
+    T* take(size_t count) {
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + count * sizeof(T);
+        return base ? reinterpret_cast<T*>(base + off) : nullptr;
+    }
+};
+
+int validate(const cpic_config* c) {
+    if (!c) {
+        set_error("config is NULL");
+        return CPIC_ERR_INVALID;
+    }
+    if (c->dim != 2 && c->dim != 3) {
+        set_error("dim must be 2 or 3 (got %d)", c->dim);
+        return CPIC_ERR_INVALID;
+    }
+    for (int a = 0; a < c->dim; ++a) {
+        int lim = c->dim == 2 ? (a == 0 ? 65535 : 32767) : 1023;
+        if (c->n[a] < 2 || c->n[a] > lim) {
+            set_error("n[%d] = %d outside [2, %d]", a, c->n[a], lim);
+            return CPIC_ERR_INVALID;
+        }
+        bool p0 = c->field_bc[2 * a] == CPIC_BC_PERIODIC, p1 = c->field_bc[2 * a + 1] == CPIC_BC_PERIODIC;
+        if (p0 != p1) {
+            set_error("axis %d: a periodic axis needs both faces periodic", a);
+            return CPIC_ERR_INVALID;
+        }
+        for (int s = 0; s < 2; ++s) {
+            int fb = c->field_bc[2 * a + s], pb = c->particle_bc[2 * a + s];
+            if (fb < 0 || fb > 2 || pb < 0 || pb > 2) {
+                set_error("face %d: unknown boundary kind", 2 * a + s);
+                return CPIC_ERR_INVALID;
+            }
+            if ((fb == CPIC_BC_PERIODIC) != (pb == CPIC_PBC_PERIODIC)) {
+                set_error("face %d: particle boundary must be periodic exactly when the field is", 2 * a + s);
+                return CPIC_ERR_INVALID;
+            }
+            if (pb == CPIC_PBC_REFLECT) {
+                set_error("face %d: specular reflection is not built in this version", 2 * a + s);
+                return CPIC_ERR_NOT_BUILT;
+            }
+        }
+        if (p0 && (c->n[a] & 1)) {
+            set_error("axis %d: a periodic axis needs an even cell count", a);
+            return CPIC_ERR_INVALID;
+        }
+    }
+    if (!(c->dt > 0.0) || !isfinite(c->dt)) {
+        set_error("dt must be positive and finite");
+        return CPIC_ERR_INVALID;
+    }
+    if (c->n_species < 1 || c->n_species > CPIC_MAX_SPECIES) {
+        set_error("n_species must be in [1, %d]", CPIC_MAX_SPECIES);
+        return CPIC_ERR_INVALID;
+    }
+    for (int s = 0; s < c->n_species; ++s) {
+        if (!(c->m[s] > 0.0) || !(c->w[s] > 0.0) || c->capacity[s] < 0 || c->capacity[s] > (1ll << 31) - 64) {
+            set_error("species %d: need m > 0, w > 0, 0 <= capacity < 2^31", s);
+            return CPIC_ERR_INVALID;
+        }
+    }
+    if (c->axisymmetric && c->dim != 2) {
+        set_error("axisymmetric (Omega = r) geometry is 2D only");
+        return CPIC_ERR_INVALID;
+    }
+    return CPIC_OK;
+}
+
+// multigrid levels: halve every axis while all are even, at least 4, and the level has
+// more than 64 cells
+int plan_levels(const cpic_config* c, int lev_n[MAX_LEVELS][3], int* nl) {
+    int n[3] = {c->n[0], c->n[1], c->dim == 3 ? c->n[2] : 1};
+    int l = 0;
+    for (;;) {
+        for (int a = 0; a < 3; ++a) lev_n[l][a] = n[a];
+        long long cells = (long long)n[0] * n[1] * n[2];
+        bool can = cells > 64 && l + 1 < MAX_LEVELS;
+        for (int a = 0; a < c->dim; ++a) can = can && (n[a] % 2 == 0) && n[a] >= 4;
+        ++l;
+        if (!can) break;
+        for (int a = 0; a < c->dim; ++a) n[a] /= 2;
+    }
+    *nl = l;
+    long long last = (long long)lev_n[l - 1][0] * lev_n[l - 1][1] * lev_n[l - 1][2];
+    if (last > DENSE_MAX) {
+        set_error("grid cannot be coarsened to <= %d cells (coarsest %lld cells): use cell counts with more factors of 2",
+                  DENSE_MAX, last);
+        return CPIC_ERR_INVALID;
+    }
+    // every smoothed level needs even counts (colour ordering)
+    for (int k = 0; k + 1 < l; ++k)
+        for (int a = 0; a < c->dim; ++a)
+            if (lev_n[k][a] & 1) {
+                set_error("internal: odd smoothed level");
+                return CPIC_ERR_INVALID;
+            }
+    return CPIC_OK;
+}
+
+void plan(cpic_run* r, Planner& P) {
+    const cpic_config& c = r->cfg;
+    int D = r->D;
+    int S = D == 2 ? 9 : 19;
+    for (int l = 0; l < r->nlevels; ++l) {
+        Level& L = r->lev[l];
+        long long nv = (long long)(L.n[0] + 1) * (L.n[1] + 1) * (D == 3 ? L.n[2] + 1 : 1);
+        L.S = S;
+        L.A = P.take<double>((size_t)S * L.ncell);
+        L.x = P.take<double>(L.ncell);
+        L.b = P.take<double>(L.ncell);
+        L.X = P.take<double>((size_t)nv * D);
+        L.Jc = P.take<double>(L.ncell);
+        L.omega = P.take<double>(L.ncell);
+        L.dv = P.take<double>((size_t)D * nv * D);
+        for (int a = 0; a < 3; ++a) {
+            if (a >= D) {
+                L.face[a] = nullptr;
+                continue;
+            }
+            long long fn[3] = {L.n[0], L.n[1], D == 3 ? L.n[2] : 1};
+            fn[a] += 1;
+            L.face[a] = P.take<double>((size_t)D * fn[0] * fn[1] * fn[2]);
+        }
+    }
+    r->k64 = P.take<double>((size_t)r->nvert * D * D);
+    r->K32 = P.take<float>((size_t)r->nvert * (D == 2 ? 4 : 12));
+    r->G32 = P.take<float>((size_t)r->nvert * (D == 2 ? 2 : 4));
+    r->rhs_bc = P.take<double>(r->ncell);
+    r->charge = P.take<unsigned long long>((size_t)c.n_species * r->ncell);
+    long long total = 0;
+    for (int s = 0; s < c.n_species; ++s) {
+        r->pb.base[s] = total;
+        r->pb.capacity[s] = c.capacity[s];
+        total += (c.capacity[s] + 31) & ~31ll;
+    }
+    for (int s = c.n_species; s < CPIC_MAX_SPECIES; ++s) r->pb.base[s] = r->pb.capacity[s] = 0;
+    if (total == 0) total = 32;
+    r->pb.total = total;
+    for (int b = 0; b < 2; ++b) {
+        r->pb.cell[b] = P.take<int>(total);
+        r->pb.t[b] = P.take<float>((size_t)D * total);
+        r->pb.v[b] = P.take<float>((size_t)3 * total);
+    }
+    r->ctr = P.take<DevCounters>(1);
+    r->red = P.take<double>(2 * 1024 + 8);
+    r->hist = P.take<int>((size_t)c.n_species * r->ncell);
+    r->scan = P.take<long long>((size_t)c.n_species * r->ncell + 1);
+    r->scan_blocks = P.take<long long>(1025);
+    const Level& Lc = r->lev[r->nlevels - 1];
+    long long mm = Lc.ncell + 1;
+    r->dense_inv = P.take<double>((size_t)mm * mm);
+    r->dense_tmp = P.take<double>((size_t)mm * mm);
+}
+
+void init_geometry_sizes(cpic_run* r, const cpic_config* cfg) {
+    r->cfg = *cfg;
+    r->D = cfg->dim;
+    r->ncell = 1;
+    r->nvert = 1;
+    for (int a = 0; a < 3; ++a) {
+        r->n[a] = a < r->D ? cfg->n[a] : 1;
+        r->nvert_axis[a] = a < r->D ? cfg->n[a] + 1 : 1;
+        r->ncell *= r->n[a];
+        r->nvert *= r->nvert_axis[a];
+    }
+    if (r->cfg.mg_max_cycles <= 0) r->cfg.mg_max_cycles = 30;
+    if (!(r->cfg.mg_rtol > 0.0)) r->cfg.mg_rtol = 1e-10;
+    r->singular = true;
+    for (int f = 0; f < 2 * r->D; ++f)
+        if (cfg->field_bc[f] == CPIC_BC_DIRICHLET) r->singular = false;
+}
+
+int setup_levels(cpic_run* r) {
+    int lev_n[MAX_LEVELS][3];
+    int nl = 0;
+    int st = plan_levels(&r->cfg, lev_n, &nl);
+    if (st) return st;
+    r->nlevels = nl;
+    for (int l = 0; l < nl; ++l) {
+        for (int a = 0; a < 3; ++a) r->lev[l].n[a] = lev_n[l][a];
+        r->lev[l].ncell = (long long)lev_n[l][0] * lev_n[l][1] * lev_n[l][2];
+        r->lev[l].cross = 0;
+    }
+    return CPIC_OK;
+}
+
+__global__ void set_count_kernel(DevCounters* ctr, int s, long long n) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        ctr->count[s] = n;
+        ctr->alive[s] = n;
+    }
+}
+
+#define CHECK_RUN(r)                         \
+    do {                                     \
+        if (!(r)) {                          \
+            set_error("run handle is NULL"); \
+            return CPIC_ERR_INVALID;         \
+        }                                    \
+    } while (0)
+#define CHECK_MAP(r)                                            \
+    do {                                                        \
+        if (!(r)->map_set) {                                    \
+            set_error("set the map (cpic_set_map_*) first");   \
+            return CPIC_ERR_STATE;                              \
+        }                                                       \
+    } while (0)
+
+int after_map(cpic_run* r) {
+    int st = launch_geometry(r);
+    if (st) return st;
+    st = mg_setup(r);
+    if (st) return st;
+    // host-side constants: sum of J_c (singular projection) and face lengths (injection rate),
+    // each summed sequentially in index order
+    std::vector<double> jc(r->ncell);
+    CPIC_CUDA(cudaMemcpyAsync(jc.data(), r->lev[0].Jc, sizeof(double) * r->ncell, cudaMemcpyDeviceToHost, r->stream));
+    std::vector<double> X((size_t)r->nvert * r->D);
+    CPIC_CUDA(cudaMemcpyAsync(X.data(), r->lev[0].X, sizeof(double) * X.size(), cudaMemcpyDeviceToHost, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    double sj = 0.0;
+    for (long long c = 0; c < r->ncell; ++c) sj += jc[c];
+    r->sumJ = sj;
+    for (int f = 0; f < 6; ++f) r->face_len[f] = 0.0;
+    if (r->D == 2) {
+        int nv0 = r->n[0] + 1;
+        for (int side = 0; side < 2; ++side) {
+            int col = side == 0 ? 0 : r->n[0];
+            double acc = 0.0;
+            for (int j = 0; j < r->n[1]; ++j) {
+                const double* p0 = &X[((size_t)col + (size_t)nv0 * j) * 2];
+                const double* p1 = &X[((size_t)col + (size_t)nv0 * (j + 1)) * 2];
+                double dx = p1[0] - p0[0], dy = p1[1] - p0[1];
+                acc += sqrt(dx * dx + dy * dy);
+            }
+            r->face_len[side] = acc;
+        }
+    }
+    CPIC_CUDA(cudaMemsetAsync(r->lev[0].x, 0, sizeof(double) * r->ncell, r->stream));
+    r->map_set = true;
+    for (int s = 0; s < CPIC_MAX_SPECIES; ++s)
+        if (r->inj[s].enabled) {
+            const InjectSpec& q = r->inj[s];
+            r->inj[s].rate = (((q.density * q.vth) * (1.0 / sqrt(2.0 * M_PI))) * r->face_len[q.face & 1]) * r->cfg.dt / r->cfg.w[s];
+        }
+    return CPIC_OK;
+}
+
+int step_once(cpic_run* r) {
+    int st = launch_vertex_field(r);
+    if (st) return st;
+    st = launch_push(r);
+    if (st) return st;
+    st = launch_inject(r);
+    if (st) return st;
+    if (r->cfg.sort_interval > 0 && ++r->steps_since_sort >= r->cfg.sort_interval) {
+        st = launch_sort(r);
+        if (st) return st;
+        r->cur_host ^= 1;
+        r->steps_since_sort = 0;
+    }
+    return mg_solve(r, r->cfg.mg_rtol, r->cfg.mg_max_cycles, false, nullptr, nullptr);
+}
+
+}  // namespace
+}  // namespace cpic
+
+using namespace cpic;
+
+extern "C" {
+
+const char* cpic_status_string(int s) {
+    switch (s) {
+        case CPIC_OK: return "ok";
+        case CPIC_ERR_INVALID: return "invalid argument or configuration";
+        case CPIC_ERR_OOM: return "out of device memory";
+        case CPIC_ERR_CUDA: return "CUDA runtime error";
+        case CPIC_ERR_NOT_CONVERGED: return "field solve did not converge";
+        case CPIC_ERR_TIMEOUT: return "bounded device wait ran out";
+        case CPIC_ERR_NONFINITE: return "non-finite particle positions";
+        case CPIC_ERR_BUSY: return "not done yet";
+        case CPIC_ERR_STATE: return "call out of order";
+        case CPIC_ERR_CAPACITY: return "particle capacity exhausted";
+        case CPIC_ERR_NOT_BUILT: return "not built in this version";
+        default: return "unknown status";
+    }
+}
+
+const char* cpic_last_error(void) { return g_err; }
+
+int cpic_abi_version(void) { return CPIC_ABI_VERSION; }
+
+int cpic_query_footprint(const cpic_config* cfg, size_t* bytes) {
+    int st = validate(cfg);
+    if (st) return st;
+    if (!bytes) {
+        set_error("bytes is NULL");
+        return CPIC_ERR_INVALID;
+    }
+    cpic_run tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    init_geometry_sizes(&tmp, cfg);
+    st = setup_levels(&tmp);
+    if (st) return st;
+    Planner P;
+    plan(&tmp, P);
+    *bytes = P.used + 256;
+    return CPIC_OK;
+}
+
+int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* stream, cpic_run** out) {
+    if (!out) {
+        set_error("out is NULL");
+        return CPIC_ERR_INVALID;
+    }
+    *out = nullptr;
+    int st = validate(cfg);
+    if (st) return st;
+    cpic_run* r = new cpic_run;
+    memset(r, 0, sizeof(*r));
+    init_geometry_sizes(r, cfg);
+    st = setup_levels(r);
+    if (st) {
+        delete r;
+        return st;
+    }
+    r->stream = (cudaStream_t)stream;
+    Planner dry;
+    plan(r, dry);
+    size_t need = dry.used + 256;
+    if (arena) {
+        if (arena_bytes < need || (reinterpret_cast<uintptr_t>(arena) & 255)) {
+            set_error("arena too small or misaligned: need %zu bytes, 256-byte aligned", need);
+            delete r;
+            return CPIC_ERR_OOM;
+        }
+        r->arena = (char*)arena;
+        r->own_memory = false;
+    } else {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) {
+            set_error("cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
+            delete r;
+            return CPIC_ERR_OOM;
+        }
+        r->arena = (char*)p;
+        r->own_memory = true;
+    }
+    r->arena_bytes = need;
+    Planner P;
+    P.base = r->arena;
+    plan(r, P);
+    cudaError_t e = cudaMemsetAsync(r->ctr, 0, sizeof(DevCounters), r->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->charge, 0, sizeof(unsigned long long) * r->ncell * cfg->n_species, r->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->pb.cell[0], 0xff, sizeof(int) * r->pb.total, r->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->pb.cell[1], 0xff, sizeof(int) * r->pb.total, r->stream);
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "initial memset", __FILE__, __LINE__);
+        if (r->own_memory) cudaFree(r->arena);
+        delete r;
+        return st;
+    }
+    *out = r;
+    return CPIC_OK;
+}
+
+int cpic_destroy(cpic_run* r) {
+    if (!r) return CPIC_OK;
+    cudaError_t e = cudaStreamSynchronize(r->stream);
+    if (r->own_memory) cudaFree(r->arena);
+    delete r;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+    return CPIC_OK;
+}
+
+int cpic_set_stream(cpic_run* r, void* stream) {
+    CHECK_RUN(r);
+    r->stream = (cudaStream_t)stream;
+    return CPIC_OK;
+}
+
+int cpic_set_map_vertices(cpic_run* r, const double* xyz) {
+    CHECK_RUN(r);
+    if (!xyz) {
+        set_error("xyz is NULL");
+        return CPIC_ERR_INVALID;
+    }
+    CPIC_CUDA(cudaMemcpyAsync(r->lev[0].X, xyz, sizeof(double) * r->nvert * r->D, cudaMemcpyDefault, r->stream));
+    return after_map(r);
+}
+
+int cpic_set_map_analytic(cpic_run* r, int map_id, const double* params, int nparams) {
+    CHECK_RUN(r);
+    int need = map_id == CPIC_MAP_SHELL ? 3 : (map_id == CPIC_MAP_SINE ? 1 : 2);
+    bool dim_ok = map_id == CPIC_MAP_SHELL ? r->D == 3 : r->D == 2;
+    if (map_id < CPIC_MAP_SINE || map_id > CPIC_MAP_SHELL || !dim_ok || !params || nparams < need) {
+        set_error("bad analytic map %d for dim %d (needs %d parameters)", map_id, r->D, need);
+        return CPIC_ERR_INVALID;
+    }
+    int st = launch_map_analytic(r, map_id, params, nparams);
+    if (st) return st;
+    return after_map(r);
+}
+
+int cpic_load_particles(cpic_run* r, int sp, int64_t n, const int32_t* cell, const float* t, const float* v) {
+    CHECK_RUN(r);
+    if (sp < 0 || sp >= r->cfg.n_species || n < 0 || n > r->pb.capacity[sp] || (n > 0 && (!cell || !t || !v))) {
+        set_error("load_particles: bad species, count or pointers (n = %lld, capacity = %lld)", (long long)n,
+                  sp >= 0 && sp < CPIC_MAX_SPECIES ? (long long)r->pb.capacity[sp] : -1ll);
+        return CPIC_ERR_INVALID;
+    }
+    int b = r->cur_host;
+    long long base = r->pb.base[sp], T = r->pb.total;
+    if (n > 0) {
+        CPIC_CUDA(cudaMemcpyAsync(r->pb.cell[b] + base, cell, sizeof(int) * n, cudaMemcpyDefault, r->stream));
+        for (int a = 0; a < r->D; ++a)
+            CPIC_CUDA(cudaMemcpyAsync(r->pb.t[b] + a * T + base, t + a * n, sizeof(float) * n, cudaMemcpyDefault, r->stream));
+        for (int a = 0; a < 3; ++a)
+            CPIC_CUDA(cudaMemcpyAsync(r->pb.v[b] + a * T + base, v + a * n, sizeof(float) * n, cudaMemcpyDefault, r->stream));
+    }
+    set_count_kernel<<<1, 32, 0, r->stream>>>(r->ctr, sp, n);
+    CPIC_CHECK_LAUNCH();
+    // the copies above may read pageable host memory the caller frees after returning
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    return CPIC_OK;
+}
+
+int cpic_get_particles(cpic_run* r, int sp, int64_t room, int64_t* n, int32_t* cell, float* t, float* v) {
+    CHECK_RUN(r);
+    if (sp < 0 || sp >= r->cfg.n_species || !n) {
+        set_error("get_particles: bad species or NULL count");
+        return CPIC_ERR_INVALID;
+    }
+    DevCounters h;
+    CPIC_CUDA(cudaMemcpyAsync(&h, r->ctr, sizeof(h), cudaMemcpyDeviceToHost, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    long long cnt = h.count[sp];
+    int b = h.cur;
+    long long base = r->pb.base[sp], T = r->pb.total;
+    std::vector<int> hc(cnt);
+    std::vector<float> ht((size_t)r->D * cnt), hv((size_t)3 * cnt);
+    if (cnt > 0) {
+        CPIC_CUDA(cudaMemcpy(hc.data(), r->pb.cell[b] + base, sizeof(int) * cnt, cudaMemcpyDeviceToHost));
+        for (int a = 0; a < r->D; ++a)
+            CPIC_CUDA(cudaMemcpy(ht.data() + a * cnt, r->pb.t[b] + a * T + base, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
+        for (int a = 0; a < 3; ++a)
+            CPIC_CUDA(cudaMemcpy(hv.data() + a * cnt, r->pb.v[b] + a * T + base, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
+    }
+    long long live = 0;
+    for (long long i = 0; i < cnt; ++i) live += hc[i] >= 0;
+    *n = live;
+    if (live > room) {
+        set_error("get_particles: room %lld < %lld live particles", (long long)room, live);
+        return CPIC_ERR_INVALID;
+    }
+    if (live == 0) return CPIC_OK;
+    if (!cell || !t || !v) {
+        set_error("get_particles: NULL output array");
+        return CPIC_ERR_INVALID;
+    }
+    std::vector<int> oc(live);
+    std::vector<float> ot((size_t)r->D * live), ov((size_t)3 * live);
+    long long k = 0;
+    for (long long i = 0; i < cnt; ++i) {
+        if (hc[i] < 0) continue;
+        oc[k] = hc[i];
+        for (int a = 0; a < r->D; ++a) ot[a * live + k] = ht[a * cnt + i];
+        for (int a = 0; a < 3; ++a) ov[a * live + k] = hv[a * cnt + i];
+        ++k;
+    }
+    CPIC_CUDA(cudaMemcpy(cell, oc.data(), sizeof(int) * live, cudaMemcpyDefault));
+    CPIC_CUDA(cudaMemcpy(t, ot.data(), sizeof(float) * ot.size(), cudaMemcpyDefault));
+    CPIC_CUDA(cudaMemcpy(v, ov.data(), sizeof(float) * ov.size(), cudaMemcpyDefault));
+    return CPIC_OK;
+}
+
+int cpic_set_injection(cpic_run* r, int sp, int face, double density, double vth, const double* drift, uint64_t seed) {
+    CHECK_RUN(r);
+    if (sp < 0 || sp >= r->cfg.n_species || r->D != 2 || (face != 0 && face != 1) ||
+        r->cfg.particle_bc[face] != CPIC_PBC_ABSORB || !(density >= 0.0) || !(vth > 0.0)) {
+        set_error("set_injection: 2D faces normal to axis 0 with absorbing particle boundaries only");
+        return CPIC_ERR_INVALID;
+    }
+    InjectSpec& q = r->inj[sp];
+    q.enabled = density > 0.0;
+    q.face = face;
+    q.density = density;
+    q.vth = vth;
+    for (int a = 0; a < 3; ++a) q.drift[a] = drift ? drift[a] : 0.0;
+    q.seed = seed;
+    q.rate = r->map_set ? (((density * vth) * (1.0 / sqrt(2.0 * M_PI))) * r->face_len[face & 1]) * r->cfg.dt / r->cfg.w[sp] : 0.0;
+    return CPIC_OK;
+}
+
+int cpic_initialize(cpic_run* r) {
+    CHECK_RUN(r);
+    CHECK_MAP(r);
+    int st = launch_deposit(r);
+    if (st) return st;
+    st = mg_solve(r, r->cfg.mg_rtol, r->cfg.mg_max_cycles, false, nullptr, nullptr);
+    if (st) return st;
+    st = launch_vertex_field(r);
+    if (st) return st;
+    st = launch_kick(r, -0.5);
+    if (st) return st;
+    r->initialized = true;
+    return CPIC_OK;
+}
+
+int cpic_step(cpic_run* r, int nsteps) {
+    CHECK_RUN(r);
+    CHECK_MAP(r);
+    for (int i = 0; i < nsteps; ++i) {
+        int st = step_once(r);
+        if (st) return st;
+    }
+    return CPIC_OK;
+}
+
+int cpic_vertex_field(cpic_run* r) {
+    CHECK_RUN(r);
+    CHECK_MAP(r);
+    return launch_vertex_field(r);
+}
+
+int cpic_push(cpic_run* r) {
+    CHECK_RUN(r);
+    CHECK_MAP(r);
+    return launch_push(r);
+}
+
+int cpic_deposit(cpic_run* r) {
+    CHECK_RUN(r);
+    CHECK_MAP(r);
+    return launch_deposit(r);
+}
+
+int cpic_kick(cpic_run* r, double fraction) {
+    CHECK_RUN(r);
+    CHECK_MAP(r);
+    return launch_kick(r, fraction);
+}
+
+int cpic_inject(cpic_run* r) {
+    CHECK_RUN(r);
+    CHECK_MAP(r);
+    return launch_inject(r);
+}
+
+int cpic_sort(cpic_run* r) {
+    CHECK_RUN(r);
+    int st = launch_sort(r);
+    if (st) return st;
+    r->cur_host ^= 1;
+    r->steps_since_sort = 0;
+    return CPIC_OK;
+}
+
+int cpic_solve_field(cpic_run* r, double rtol, int max_cycles, int* cycles, double* residual) {
+    CHECK_RUN(r);
+    CHECK_MAP(r);
+    if (!(rtol > 0.0) || max_cycles < 0) {
+        set_error("solve_field: rtol must be > 0 and max_cycles >= 0");
+        return CPIC_ERR_INVALID;
+    }
+    int c = 0;
+    double res = 0.0;
+    int st = mg_solve(r, rtol, max_cycles, true, &c, &res);
+    if (cycles) *cycles = c;
+    if (residual) *residual = res;
+    return st;
+}
+
+int cpic_get_diag(cpic_run* r, cpic_diag* out) {
+    CHECK_RUN(r);
+    if (!out) {
+        set_error("out is NULL");
+        return CPIC_ERR_INVALID;
+    }
+    DevCounters h;
+    CPIC_CUDA(cudaMemcpyAsync(&h, r->ctr, sizeof(h), cudaMemcpyDeviceToHost, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    memset(out, 0, sizeof(*out));
+    out->step = h.step;
+    out->field_energy = h.field_energy;
+    double ke = 0.0;
+    for (int s = 0; s < r->cfg.n_species; ++s) {
+        ke += 0.5 * r->cfg.m[s] * r->cfg.w[s] * ldexp((double)h.ke_fp[s], -KE_BITS);
+        out->n_particles[s] = h.alive[s];
+        for (int f = 0; f < 6; ++f) out->absorbed[s][f] = h.absorbed[s][f];
+        out->injected[s] = h.injected[s];
+        out->dropped[s] = h.dropped[s];
+    }
+    out->kinetic_energy = ke;
+    out->nonfinite = h.nonfinite;
+    out->mg_cycles = h.mg_cycles;
+    out->mg_residual = h.mg_residual;
+    return CPIC_OK;
+}
+
+int cpic_get_phi(cpic_run* r, double* phi) {
+    CHECK_RUN(r);
+    CPIC_CUDA(cudaMemcpyAsync(phi, r->lev[0].x, sizeof(double) * r->ncell, cudaMemcpyDefault, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    return CPIC_OK;
+}
+
+int cpic_set_phi(cpic_run* r, const double* phi) {
+    CHECK_RUN(r);
+    CPIC_CUDA(cudaMemcpyAsync(r->lev[0].x, phi, sizeof(double) * r->ncell, cudaMemcpyDefault, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    return CPIC_OK;
+}
+
+int cpic_get_charge(cpic_run* r, int sp, int64_t* counts) {
+    CHECK_RUN(r);
+    if (sp < 0 || sp >= r->cfg.n_species) {
+        set_error("bad species");
+        return CPIC_ERR_INVALID;
+    }
+    CPIC_CUDA(cudaMemcpyAsync(counts, r->charge + (long long)sp * r->ncell, sizeof(int64_t) * r->ncell, cudaMemcpyDefault,
+                              r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    return CPIC_OK;
+}
+
+int cpic_get_vertex_tables(cpic_run* r, float* k, float* g) {
+    CHECK_RUN(r);
+    if (k)
+        CPIC_CUDA(cudaMemcpyAsync(k, r->K32, sizeof(float) * r->nvert * (r->D == 2 ? 4 : 12), cudaMemcpyDefault, r->stream));
+    if (g)
+        CPIC_CUDA(cudaMemcpyAsync(g, r->G32, sizeof(float) * r->nvert * (r->D == 2 ? 2 : 4), cudaMemcpyDefault, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    return CPIC_OK;
+}
+
+int cpic_get_geometry(cpic_run* r, double* k, double* jc) {
+    CHECK_RUN(r);
+    if (k) CPIC_CUDA(cudaMemcpyAsync(k, r->k64, sizeof(double) * r->nvert * r->D * r->D, cudaMemcpyDefault, r->stream));
+    if (jc) CPIC_CUDA(cudaMemcpyAsync(jc, r->lev[0].Jc, sizeof(double) * r->ncell, cudaMemcpyDefault, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    return CPIC_OK;
+}
+
+int cpic_synchronize(cpic_run* r) {
+    CHECK_RUN(r);
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    return CPIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Row a1 (logical field at vertices), the charge -> right-hand side map of row a9, and the
+// field-energy diagnostic of row a10.
+//
+// Staggering (Sec. II.B): phi and rho at cell centres, the field at vertices. The vertex
+// field in cell units is G^a = mean over the 2^(D-1) cell pairs straddling the vertex along
+// a of the cell difference (the paper gives no formula; this is the implementation's
+// reading), with ghost cells from the boundary conditions (Sec. II.B.3): Dirichlet
+// 2 phi_b - phi_in, Neumann phi_in, periodic wrap; the ghost of a ghost applies the rules
+// from axis 0 upwards. FP64 arithmetic in a fixed order (explicit intrinsics), rounded once
+// to FP32 for the mover's table.
+#include "internal.cuh"
+
+namespace cpic {
+namespace {
+
+struct FieldGrid {
+    int D;
+    int n[3];
+    int bc[6];
+    double bcv[6];
+};
+
+__device__ __forceinline__ double phi_ext(const FieldGrid& g, const double* __restrict__ phi, int i, int j, int k) {
+    int c[3] = {i, j, k};
+    int side[3] = {-1, -1, -1};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a >= g.D) break;
+        if (c[a] < 0 || c[a] >= g.n[a]) {
+            int sd = c[a] < 0 ? 0 : 1;
+            if (g.bc[2 * a] == CPIC_BC_PERIODIC) {
+                c[a] = c[a] < 0 ? c[a] + g.n[a] : c[a] - g.n[a];
+            } else {
+                side[a] = sd;
+                c[a] = sd == 0 ? 0 : g.n[a] - 1;
+            }
+        }
+    }
+    double val = phi[c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2])];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a >= g.D) break;
+        if (side[a] >= 0 && g.bc[2 * a + side[a]] == CPIC_BC_DIRICHLET)
+            val = __dsub_rn(__dmul_rn(2.0, g.bcv[2 * a + side[a]]), val);
+    }
+    return val;
+}
+
+__global__ void vertex_field_kernel(FieldGrid g, const double* __restrict__ phi, float* G) {
+    long long nv0 = g.n[0] + 1, nv1 = g.n[1] + 1, nv2 = g.D == 3 ? g.n[2] + 1 : 1;
+    long long nvt = nv0 * nv1 * nv2;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvt;
+         v += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(v % nv0);
+        long long rest = v / nv0;
+        int j = (int)(rest % nv1);
+        int k = (int)(rest / nv1);
+        if (g.D == 2) {
+            double p00 = phi_ext(g, phi, i - 1, j - 1, 0);
+            double p01 = phi_ext(g, phi, i, j - 1, 0);
+            double p10 = phi_ext(g, phi, i - 1, j, 0);
+            double p11 = phi_ext(g, phi, i, j, 0);
+            double g0 = __dmul_rn(__dadd_rn(__dsub_rn(p01, p00), __dsub_rn(p11, p10)), 0.5);
+            double g1 = __dmul_rn(__dadd_rn(__dsub_rn(p10, p00), __dsub_rn(p11, p01)), 0.5);
+            reinterpret_cast<float2*>(G)[v] = make_float2(__double2float_rn(g0), __double2float_rn(g1));
+        } else {
+            double c8[8];  // c8[di + 2 dj + 4 dk] = phi_ext(i-1+di, j-1+dj, k-1+dk)
+#pragma unroll
+            for (int o = 0; o < 8; ++o) c8[o] = phi_ext(g, phi, i - 1 + (o & 1), j - 1 + ((o >> 1) & 1), k - 1 + ((o >> 2) & 1));
+            float out[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int o0 = a == 0 ? 1 : 0, o1 = a == 2 ? 1 : 2;  // the other axes, increasing
+                double acc = 0.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    int oa = q & 1, ob = q >> 1;  // first other axis fastest
+                    int lo = (oa << o0) | (ob << o1);
+                    int hi = lo | (1 << a);
+                    double d = __dsub_rn(c8[hi], c8[lo]);
+                    acc = q == 0 ? d : __dadd_rn(acc, d);
+                }
+                out[a] = __double2float_rn(__dmul_rn(acc, 0.25));
+            }
+            reinterpret_cast<float4*>(G)[v] = make_float4(out[0], out[1], out[2], 0.0f);
+        }
+    }
+}
+
+struct RhsParams {
+    long long ncell;
+    int nsp;
+    double qw[CPIC_MAX_SPECIES];
+    double background;
+    const double* Jc;
+    const double* omega;
+    const double* bbc;
+    const unsigned long long* charge;
+};
+
+// Q_c = background J_c + sum_s q_s w_s C_{s,c} 2^-24 (eq. (pg) with J_c cancelled against
+// the cell volume); b_c = Omega_c Q_c + Dirichlet terms.
+__device__ __forceinline__ double charge_of(const RhsParams& p, long long c) {
+    double Q = __dmul_rn(p.background, p.Jc[c]);
+    for (int s = 0; s < p.nsp; ++s) {
+        double C = (double)(long long)p.charge[(long long)s * p.ncell + c];
+        Q = __dadd_rn(Q, __dmul_rn(p.qw[s], ldexp(C, -QF)));
+    }
+    return Q;
+}
+
+__global__ void rhs_kernel(RhsParams p, double* b) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < p.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        double Q = charge_of(p, c);
+        b[c] = __dadd_rn(__dmul_rn(p.omega[c], Q), p.bbc[c]);
+    }
+}
+
+// deterministic block reduction (fixed shuffle tree, fixed block count)
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    __syncthreads();
+    return r;
+}
+
+__global__ void field_energy_partial(RhsParams p, const double* __restrict__ phi, double* part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < p.ncell;
+         c += (long long)gridDim.x * blockDim.x)
+        acc += phi[c] * charge_of(p, c);
+    double r = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+__global__ void field_energy_final(const double* part, int nb, DevCounters* ctr) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nb; ++i) s += part[i];
+        ctr->field_energy = 0.5 * s;
+    }
+}
+
+FieldGrid make_field_grid(const cpic_run* r) {
+    FieldGrid g;
+    g.D = r->D;
+    for (int a = 0; a < 3; ++a) g.n[a] = a < r->D ? r->n[a] : 1;
+    for (int f = 0; f < 6; ++f) {
+        g.bc[f] = r->cfg.field_bc[f];
+        g.bcv[f] = r->cfg.field_bc_value[f];
+    }
+    return g;
+}
+
+}  // namespace
+
+RhsParams make_rhs_params(const cpic_run* r) {
+    RhsParams p;
+    p.ncell = r->ncell;
+    p.nsp = r->cfg.n_species;
+    for (int s = 0; s < CPIC_MAX_SPECIES; ++s) p.qw[s] = s < p.nsp ? r->cfg.q[s] * r->cfg.w[s] : 0.0;
+    p.background = r->cfg.background;
+    p.Jc = r->lev[0].Jc;
+    p.omega = r->lev[0].omega;
+    p.bbc = r->rhs_bc;
+    p.charge = r->charge;
+    return p;
+}
+
+int launch_vertex_field(cpic_run* r) {
+    FieldGrid g = make_field_grid(r);
+    long long b = (r->nvert + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    vertex_field_kernel<<<(int)b, 256, 0, r->stream>>>(g, r->lev[0].x, r->G32);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
+int launch_rhs(cpic_run* r, double* b) {
+    RhsParams p = make_rhs_params(r);
+    long long nb = (r->ncell + 255) / 256;
+    if (nb > 152 * 8) nb = 152 * 8;
+    rhs_kernel<<<(int)nb, 256, 0, r->stream>>>(p, b);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
+int launch_field_energy(cpic_run* r) {
+    RhsParams p = make_rhs_params(r);
+    const int nb = 256;
+    field_energy_partial<<<nb, 256, 0, r->stream>>>(p, r->lev[0].x, r->red);
+    CPIC_CHECK_LAUNCH();
+    field_energy_final<<<1, 32, 0, r->stream>>>(r->red, nb, r->ctr);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
+}  // namespace cpic

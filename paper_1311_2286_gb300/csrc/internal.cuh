@@ -1,0 +1,168 @@
+// Internal declarations of the CUDA library behind include/cpic.h (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cpic.h"
+
+namespace cpic {
+
+// ---------------------------------------------------------------- constants
+constexpr int QK = 12;  // spec Q: offsets quantised to 2^-QK of a cell
+constexpr int QF = 24;  // spec Q: one particle deposits exactly 2^QF charge units
+constexpr int KE_BITS = 24;  // spec D: kinetic energy products in units of 2^-24
+constexpr int MAX_LEVELS = 16;
+constexpr int COARSE_CELLS = 4096;  // levels at or below this size run in one CTA
+constexpr int DENSE_MAX = 512;      // coarsest level solved densely (inverse) up to this size
+
+// ---------------------------------------------------------------- error handling
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+#define CPIC_CUDA(call)                                                      \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+#define CPIC_CHECK_LAUNCH() CPIC_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------- device-side run state
+// Counters written by kernels (one struct in device memory per run).
+struct DevCounters {
+    long long count[CPIC_MAX_SPECIES];     // occupied slots (live + dead until the next sort)
+    long long alive[CPIC_MAX_SPECIES];     // live particles
+    long long absorbed[CPIC_MAX_SPECIES][6];
+    long long injected[CPIC_MAX_SPECIES];
+    long long dropped[CPIC_MAX_SPECIES];
+    long long nonfinite;
+    long long ke_fp[CPIC_MAX_SPECIES];     // sum of round(v_old . v_new * 2^24) of the last push
+    long long step;                        // completed pushes
+    int cur;                               // current particle buffer (0/1)
+    int pending_inject[CPIC_MAX_SPECIES];  // particles written by the last injection
+    double field_energy;
+    double mg_residual;
+    double mg_bnorm;
+    int mg_cycles;
+    int mg_converged;
+};
+
+// Particle storage: two buffers (sort ping-pong), each a structure of arrays over all
+// species; species s owns slots [base[s], base[s] + capacity[s]).
+struct ParticleBuffers {
+    int* cell[2];
+    float* t[2];  // [D][total] per buffer
+    float* v[2];  // [3][total] per buffer
+    long long total;
+    long long base[CPIC_MAX_SPECIES];
+    long long capacity[CPIC_MAX_SPECIES];
+};
+
+// Everything a particle kernel needs, passed by value.
+struct PushParams {
+    int D;
+    int n[3];
+    int pbc[6];
+    int nsp;
+    float dtqm[CPIC_MAX_SPECIES];  // (float)(dt q/m)
+    float hdt;                     // (float)(dt/2)
+    float dt;                      // (float)dt
+    const float* K;                // vertex k table: 2D float4 [K00 K01 K10 K11]; 3D 3 x float4 (9 used)
+    const float* G;                // vertex G table: 2D float2; 3D float4 (3 used)
+    ParticleBuffers pb;
+    unsigned long long* charge;    // [nsp][ncell]
+    long long ncell;
+    DevCounters* ctr;
+};
+
+// Multigrid level (cell-centred finite volume, rediscretised from the level's vertex map).
+struct Level {
+    int n[3];
+    long long ncell;
+    int S;            // stencil entries stored: 9 (2D) / 19 (3D)
+    int cross;        // 1 if any cross coefficient is non-zero (9/19-point), else 5/7-point
+    double* A;        // [S][ncell]
+    double* x;        // solution (finest: phi) / correction
+    double* b;        // right-hand side
+    double* X;        // vertex map of this level [vertex][D]
+    double* Jc;       // cell Jacobians
+    double* omega;    // cell Omega
+    double* face[3];  // face coefficients per axis: [D][nface_a] (a^{a0}, a^{a1}, a^{a2})
+    double* dv;       // vertex derivatives [D][nvertex][D] (scratch for setup)
+};
+
+struct InjectSpec {
+    int enabled;
+    int face;
+    double density, vth, drift[3];
+    unsigned long long seed;
+    double rate;  // particles per step
+};
+
+}  // namespace cpic
+
+// The run (opaque handle of the ABI).
+struct cpic_run {
+    cpic_config cfg;
+    int D;
+    int n[3];
+    long long ncell, nvert;
+    int nvert_axis[3];
+    cudaStream_t stream;
+    bool own_memory;
+    char* arena;
+    size_t arena_bytes, arena_used;
+    bool map_set;
+    bool initialized;
+    // geometry (finest level lives in levels[0])
+    double* k64;      // [nvert][D][D]
+    float* K32;       // vertex k table (padded records)
+    float* G32;       // vertex G table (padded records)
+    double* rhs_bc;   // Dirichlet part of the right-hand side (finest)
+    unsigned long long* charge;  // [nsp][ncell]
+    cpic::ParticleBuffers pb;
+    cpic::DevCounters* ctr;      // device
+    int cur_host;                // host mirror of ctr->cur (every sort flips both)
+    // multigrid
+    int nlevels;
+    cpic::Level lev[cpic::MAX_LEVELS];
+    double* dense_inv;           // coarsest inverse [(m+1)^2]
+    double* dense_tmp;           // setup scratch [(m+1)^2]
+    int dense_m;                 // coarsest unknowns (+1 row when singular)
+    bool singular;
+    double sumJ;                 // sum of finest J_c (singular projection)
+    double* red;                 // reduction scratch [2 * 1024 + 8]
+    // sort scratch
+    int* hist;                   // [nsp][ncell] counts -> cursors
+    long long* scan;             // [nsp*ncell + 1] exclusive prefix
+    long long* scan_blocks;      // block partials
+    // injection
+    cpic::InjectSpec inj[CPIC_MAX_SPECIES];
+    double face_len[6];
+    int steps_since_sort;
+};
+
+namespace cpic {
+// ---------------------------------------------------------------- launchers (per .cu)
+// geometry.cu
+int launch_map_analytic(cpic_run* r, int map_id, const double* params, int nparams);
+int launch_geometry(cpic_run* r);
+// fields.cu
+int launch_vertex_field(cpic_run* r);
+int launch_rhs(cpic_run* r, double* b);
+int launch_field_energy(cpic_run* r);
+// push.cu
+int launch_push(cpic_run* r);
+int launch_deposit(cpic_run* r);
+int launch_kick(cpic_run* r, double fraction);
+int launch_finalize_step(cpic_run* r);
+// inject.cu
+int launch_inject(cpic_run* r);
+// sort.cu
+int launch_sort(cpic_run* r);
+// mg.cu
+int mg_setup(cpic_run* r);
+int mg_solve(cpic_run* r, double rtol, int max_cycles, bool host_loop, int* cycles, double* res);
+}  // namespace cpic

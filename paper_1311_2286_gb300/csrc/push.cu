@@ -1,0 +1,290 @@
+// Rows a2-a6: the fused hybrid-mover kernel (Sec. II.B.4) with its grid coupling.
+//
+// Per particle (one thread, structure-of-arrays, coalesced):
+//   a2  b1 gather of the logical field G and of k at xi^n (Sec. II.B.2, eqs. (vvp), (Wvp),
+//       (b1)) - both vertex tables are read through the read-only path;
+//   a3  E^alpha = -sum_a G^a k^{a alpha}, v^{n+1/2} = v^{n-1/2} + dt (q/m) E (eq. (step1);
+//       unmagnetised, so the Boris rotation is the identity);
+//   a4  predictor xi' = xi^n + dt/2 k(xi^n) v (eq. (step2)), k re-gathered at xi'
+//       (eq. (step3)), corrector xi^{n+1} = xi^n + dt k(xi') v (eq. (step4)), on the split
+//       (cell, offset) representation in cell units;
+//   a5  boundaries: periodic wrap; absorption when a logical coordinate leaves [0, 1)
+//       (Sec. II.B.4), tallied per face and species;
+//   a6  b2 deposit (eqs. (pg), (Wpc), (b2)) in 64-bit fixed point: integer node weights
+//       from the offset quantised to 2^-12 of a cell, 2^24 units per particle. Lanes of a
+//       warp whose particles share a cell are found with __match_any_sync, their node
+//       weights summed with __reduce_add_sync (each < 2^24, so a warp's sum fits 32 bits),
+//       and one lane per group issues the 3^D global 64-bit reductions.
+//
+// The FP32 operation sequence (explicit __fmaf_rn / __fmul_rn / __fsub_rn, never
+// contracted) is the one the mover is specified with: s = 1 - t; corner weights multiplied
+// from axis 0 upwards; gathers as a fused multiply-add chain over corners in the order
+// 0 .. 2^D - 1 (bit a = +1 along axis a); renormalisation c = floor(x), f = x - c, f == 1
+// -> (0, c + 1); the predictor point is clamped on non-periodic axes.
+#include "particles.cuh"
+
+namespace cpic {
+namespace {
+
+using namespace pk;
+
+// Per-warp tallies of the current species (the species is warp-uniform, so the flush is
+// taken by whole warps): kinetic-energy products, absorbed per face, non-finite.
+struct Tally {
+    long long ke = 0;
+    int gone[7] = {0, 0, 0, 0, 0, 0, 0};  // faces 0..5, 6 = non-finite
+    __device__ __forceinline__ void flush(DevCounters* ctr, int s) {
+        long long k = warp_sum_ll(ke);
+        bool lane0 = (threadIdx.x & 31) == 0;
+        if (lane0 && k != 0) atomicAdd((unsigned long long*)&ctr->ke_fp[s], (unsigned long long)k);
+        long long removed = 0;
+#pragma unroll
+        for (int f = 0; f < 7; ++f) {
+            int c = gone[f];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+            removed += c;
+            if (lane0 && c) {
+                if (f < 6)
+                    atomicAdd((unsigned long long*)&ctr->absorbed[s][f], (unsigned long long)c);
+                else
+                    atomicAdd((unsigned long long*)&ctr->nonfinite, (unsigned long long)c);
+            }
+            gone[f] = 0;
+        }
+        if (lane0 && removed) atomicAdd((unsigned long long*)&ctr->alive[s], (unsigned long long)(-removed));
+        ke = 0;
+    }
+};
+
+// MODE 0: full push + deposit; MODE 1: deposit only; MODE 2: gather + kick only
+template <int D, int MODE>
+__global__ void __launch_bounds__(256) particle_kernel(PushParams p, float kick_coef0, float kick_coef1,
+                                                       float kick_coef2, float kick_coef3) {
+    const SpeciesRanges R = species_ranges(p);
+    const long long total = R.voff[p.nsp];
+    const int cur = p.ctr->cur;
+    int* __restrict__ cellp = p.pb.cell[cur];
+    float* __restrict__ tp = p.pb.t[cur];
+    float* __restrict__ vp = p.pb.v[cur];
+    const long long T = p.pb.total;
+    Tally tally;
+    int s_acc = -1;
+
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += (long long)gridDim.x * blockDim.x) {
+        const long long vi = base + threadIdx.x;
+        const int s = species_of(R, p.nsp, vi);
+        if (MODE == 0 && s != s_acc) {  // warp-uniform
+            if (s_acc >= 0) tally.flush(p.ctr, s_acc);
+            s_acc = s;
+        }
+        const long long local = vi - R.voff[s];
+        bool active = vi < total && local < R.cnt[s];
+        const long long slot = p.pb.base[s] + local;
+        int cw = active ? cellp[slot] : -1;
+        active = active && cw >= 0;
+        int c[3] = {0, 0, 0};
+        float t[3] = {0.f, 0.f, 0.f};
+        float v[3] = {0.f, 0.f, 0.f};
+        if (active) {
+            decode<D>(cw, c);
+#pragma unroll
+            for (int a = 0; a < D; ++a) t[a] = tp[a * T + slot];
+            if (MODE != 1) {
+#pragma unroll
+                for (int al = 0; al < 3; ++al) v[al] = vp[al * T + slot];
+            }
+        }
+        if (MODE == 1) {
+            deposit_warp<D>(p, s, active, c, t);
+            continue;
+        }
+        float kp[9], gp[3];
+        if (active) {
+            Tab<D>::gather(p, vertex_of<D>(p, c), t, kp, gp);
+        }
+        if (MODE == 2) {
+            if (active) {
+                float coef = s == 0 ? kick_coef0 : s == 1 ? kick_coef1 : s == 2 ? kick_coef2 : kick_coef3;
+#pragma unroll
+                for (int al = 0; al < D; ++al) {
+                    float e = __fmul_rn(kp[0 * D + al], gp[0]);
+#pragma unroll
+                    for (int a = 1; a < D; ++a) e = __fmaf_rn(kp[a * D + al], gp[a], e);
+                    e = -e;
+                    vp[al * T + slot] = __fmaf_rn(coef, e, v[al]);
+                }
+            }
+            continue;
+        }
+        // ---- MODE 0: full push
+        bool alive = active;
+        int cn[3] = {0, 0, 0};
+        float tn[3] = {0.f, 0.f, 0.f};
+        if (active) {
+            int face = -1;
+            const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
+            const float dtqm = p.dtqm[s];
+#pragma unroll
+            for (int al = 0; al < D; ++al) {
+                float e = __fmul_rn(kp[0 * D + al], gp[0]);
+#pragma unroll
+                for (int a = 1; a < D; ++a) e = __fmaf_rn(kp[a * D + al], gp[a], e);
+                e = -e;
+                v[al] = __fmaf_rn(dtqm, e, v[al]);
+            }
+            // predictor
+            int cpred[3];
+            float tpred[3];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                float d = __fmul_rn(kp[a * D + 0], v[0]);
+#pragma unroll
+                for (int al = 1; al < D; ++al) d = __fmaf_rn(kp[a * D + al], v[al], d);
+                float x = __fmaf_rn(p.hdt, d, t[a]);
+                if (!isfinite(x)) {
+                    cpred[a] = c[a];
+                    tpred[a] = t[a];
+                    continue;
+                }
+                int dc;
+                renorm(x, tpred[a], dc);
+                int ci = c[a] + dc;
+                if (p.pbc[2 * a] == CPIC_PBC_PERIODIC) {
+                    ci = wrapi(ci, p.n[a]);
+                } else if (ci < 0) {
+                    ci = 0;
+                    tpred[a] = 0.0f;
+                } else if (ci >= p.n[a]) {
+                    ci = p.n[a] - 1;
+                    tpred[a] = 1.0f;
+                }
+                cpred[a] = ci;
+            }
+            float kq[9];
+            Tab<D>::gather(p, vertex_of<D>(p, cpred), tpred, kq, nullptr);
+            // corrector
+            bool bad = false;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                float d = __fmul_rn(kq[a * D + 0], v[0]);
+#pragma unroll
+                for (int al = 1; al < D; ++al) d = __fmaf_rn(kq[a * D + al], v[al], d);
+                float x = __fmaf_rn(p.dt, d, t[a]);
+                if (!isfinite(x)) {
+                    bad = true;
+                    cn[a] = c[a];
+                    tn[a] = t[a];
+                    continue;
+                }
+                int dc;
+                renorm(x, tn[a], dc);
+                cn[a] = c[a] + dc;
+            }
+            if (bad) {
+                face = 6;
+            } else {
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    if (p.pbc[2 * a] == CPIC_PBC_PERIODIC) {
+                        cn[a] = wrapi(cn[a], p.n[a]);
+                    } else if (cn[a] < 0) {
+                        if (face < 0) face = 2 * a;
+                    } else if (cn[a] >= p.n[a]) {
+                        if (face < 0) face = 2 * a + 1;
+                    }
+                }
+            }
+            alive = face < 0;
+            // spec D: v_old . v_new as an FP32 fma chain, then round(x 2^24) to int64 (FP64
+            // throughput on this part is ~1/64 of FP32, so the product stays in FP32)
+            float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
+            tally.ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
+#pragma unroll
+            for (int f = 0; f < 7; ++f) tally.gone[f] += (face == f) ? 1 : 0;
+            // store
+            cellp[slot] = alive ? encode<D>(cn) : -1;
+#pragma unroll
+            for (int a = 0; a < D; ++a) tp[a * T + slot] = tn[a];
+#pragma unroll
+            for (int al = 0; al < 3; ++al) vp[al * T + slot] = v[al];
+        }
+        deposit_warp<D>(p, s, alive, cn, tn);
+    }
+    if (MODE == 0 && s_acc >= 0) tally.flush(p.ctr, s_acc);
+}
+
+__global__ void finalize_step_kernel(DevCounters* ctr) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) ctr->step += 1;
+}
+
+}  // namespace
+
+PushParams make_push_params(cpic_run* r) {
+    PushParams p;
+    p.D = r->D;
+    for (int a = 0; a < 3; ++a) p.n[a] = a < r->D ? r->n[a] : 1;
+    for (int f = 0; f < 6; ++f) p.pbc[f] = r->cfg.particle_bc[f];
+    p.nsp = r->cfg.n_species;
+    for (int s = 0; s < CPIC_MAX_SPECIES; ++s)
+        p.dtqm[s] = s < p.nsp ? (float)(r->cfg.dt * r->cfg.q[s] / r->cfg.m[s]) : 0.0f;
+    p.hdt = (float)(0.5 * r->cfg.dt);
+    p.dt = (float)r->cfg.dt;
+    p.K = r->K32;
+    p.G = r->G32;
+    p.pb = r->pb;
+    p.charge = r->charge;
+    p.ncell = r->ncell;
+    p.ctr = r->ctr;
+    return p;
+}
+
+static int particle_grid(cpic_run* r) {
+    // enough resident blocks for all SMs; grid-stride over the particles
+    long long tot = 0;
+    for (int s = 0; s < r->cfg.n_species; ++s) tot += r->pb.capacity[s] + 32;
+    long long b = (tot + 255) / 256;
+    int dev_blocks = 152 * 8;
+    if (b > dev_blocks) b = dev_blocks;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <int MODE>
+static int launch_particles(cpic_run* r, float c0, float c1, float c2, float c3) {
+    PushParams p = make_push_params(r);
+    int blocks = particle_grid(r);
+    if (r->D == 2)
+        particle_kernel<2, MODE><<<blocks, 256, 0, r->stream>>>(p, c0, c1, c2, c3);
+    else
+        particle_kernel<3, MODE><<<blocks, 256, 0, r->stream>>>(p, c0, c1, c2, c3);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
+int launch_push(cpic_run* r) {
+    CPIC_CUDA(cudaMemsetAsync(r->charge, 0, sizeof(unsigned long long) * r->ncell * r->cfg.n_species, r->stream));
+    CPIC_CUDA(cudaMemsetAsync(&r->ctr->ke_fp[0], 0, sizeof(long long) * CPIC_MAX_SPECIES, r->stream));
+    int st = launch_particles<0>(r, 0, 0, 0, 0);
+    if (st) return st;
+    return launch_finalize_step(r);
+}
+
+int launch_deposit(cpic_run* r) {
+    CPIC_CUDA(cudaMemsetAsync(r->charge, 0, sizeof(unsigned long long) * r->ncell * r->cfg.n_species, r->stream));
+    return launch_particles<1>(r, 0, 0, 0, 0);
+}
+
+int launch_kick(cpic_run* r, double fraction) {
+    float c[4] = {0, 0, 0, 0};
+    for (int s = 0; s < r->cfg.n_species; ++s) c[s] = (float)(fraction * r->cfg.dt * r->cfg.q[s] / r->cfg.m[s]);
+    return launch_particles<2>(r, c[0], c[1], c[2], c[3]);
+}
+
+int launch_finalize_step(cpic_run* r) {
+    finalize_step_kernel<<<1, 32, 0, r->stream>>>(r->ctr);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
+}  // namespace cpic
