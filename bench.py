@@ -1,0 +1,358 @@
+"""Benchmark of the curvilinear PIC hot path on GB300 (one JSON line on rank 0).
+
+Workload (the 2D cylinder-in-plasma configuration): log-polar annulus r = (40)^xi around a
+cylinder of radius 1, 128 x 256 cells, 2M electrons + 2M ions (m_i/m_e = 1836,
+T_i = T_e) loaded uniform in physical space, object at -5 (Dirichlet, absorbing), outer
+boundary at 0 with Maxwellian flux injection, theta periodic, dt = 0.1, synthetic seeded
+inputs. A step is one full PIC cycle through the C ABI (cpic_step): vertex field, fused
+gather/push/boundary/deposit, injection, cell sort every few steps, charge -> right-hand
+side and multigrid solve to the paper's relative tolerance 1e-10, diagnostics.
+
+value: particle-steps/s of the whole step, inputs resident in HBM, per-step CUDA events on
+the run's stream, L2 flushed (256 MB write) between timed steps (state is 96 MB < L2).
+e2e: the same metric through the public API with host buffers: each step loads the
+particle state from pinned host memory (cpic_load_particles), steps, and reads the state
+and diagnostics back (cpic_get_particles, cpic_get_diag), copies inside the timed region.
+roofline: the fused push kernel (the dominant kernel) against the measured HBM copy
+bandwidth, algorithmic bytes = 48 B per particle (state read once, written once).
+--impl reference: the oracle (oracle/, plain FP64 CPU) timed on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+deposit) & % HBM roofline; served p50/p99 latency"
+UNIT = "particle-steps/s"
+BYTES_PER_PARTICLE = 48  # 2D: (4 cell + 8 offsets + 12 velocity) read + written
+WORKLOAD = ("2D cylinder in plasma: annulus r=(40)^xi, 128x256 cells, 2M electrons + 2M ions "
+            "(m_i/m_e=1836, T_i=T_e), phi_obj=-5, Maxwellian flux injection at r=40, dt=0.1, "
+            "sort every {S} steps, multigrid rtol 1e-10")
+KERNEL_SOURCES = ["paper_1311_2286_gb300/csrc/push.cu", "paper_1311_2286_gb300/csrc/particles.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """dram bytes per push launch from the committed ncu summary, if it was taken on the
+    current kernel sources (matching source hash), else None."""
+    path = os.path.join(ROOT, "profiles", "push_cylinder_128x256_4M.md")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_sources_sha256_16") != kernel_hash():
+        return None
+    try:
+        return int(float(kv["dram_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(busy)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(seed, npart):
+    from paper_1311_2286_gb300 import workloads as wl
+
+    return wl.cylinder(n1=128, n2=256, npart_per_species=npart, seed=seed, inject=True)
+
+
+# ------------------------------------------------------------------------------- oracle
+
+def oracle_sample(steps, warmup, seed=1, npart=100_000):
+    """The FP64 oracle (as it stands) on a bounded sample of the workload: the same grid,
+    map, boundaries and injection, npart particles per species. Returns particle-steps/s."""
+    from oracle.pic import OraclePIC
+
+    w = make_workload(seed, npart)
+    pic = OraclePIC(w, "fp64")
+    pic.initialize()
+    for _ in range(warmup):
+        pic.step()
+    t0 = time.perf_counter()
+    ps = 0
+    for _ in range(steps):
+        ps += sum(sp.idx.shape[1] for sp in pic.species)
+        pic.step()
+    dt = time.perf_counter() - t0
+    return ps / dt, dt, f"{steps} full oracle PIC steps (FP64 mover, exact b2 deposit, sparse direct solve) " \
+                        f"on 128x256 cells with {npart}+{npart} particles"
+
+
+# ------------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--particles", type=int, default=2_000_000, help="per species")
+    ap.add_argument("--sort-interval", type=int, default=4)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = max(1, args.steps // 10)
+        v, secs, sample = oracle_sample(steps, min(args.warmup, 1))
+        cores = 1
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": 1000 * secs / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD.format(S=args.sort_interval), "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_1311_2286_gb300 import cpic
+
+    cpic.load()
+    stream = torch.cuda.current_stream()
+    w = make_workload(1 + rank, args.particles)
+    cfg = cpic.config_from_workload(w, sort_interval=args.sort_interval, mg_rtol=1e-10, mg_max_cycles=30)
+    arena = torch.empty(cpic.Run.footprint(cfg), dtype=torch.uint8, device="cuda")
+    run = cpic.Run(cfg, arena=arena, stream=ctypes_stream(stream))
+    run.set_map_analytic(cpic.CPIC_MAP_ANNULUS, [1.0, 40.0])
+    for s, ps in enumerate(w.particles):
+        run.load_particles(s, ps.cell, ps.t, ps.v)
+    for (s, face, dens, vth, seed) in w.injection:
+        run.set_injection(s, face, dens, vth, seed)
+    run.initialize()
+    run.step(args.warmup)
+    run.synchronize()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    run.profile(True)
+    run.profile_read()
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = cpic.load().cpic_kernel_launches()
+    particle_steps = 0
+    cycles = []
+    for k in range(args.steps):
+        d = run.diag()  # synchronises (outside the timed events)
+        particle_steps += sum(d["n"])
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        run.step(1)
+        ev[k][1].record(stream)
+        cycles.append(d["mg_cycles"])
+    torch.cuda.synchronize()
+    launches = cpic.load().cpic_kernel_launches() - launches0
+    clk = clocks.stop()
+    phases = run.profile_read()
+    run.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        ps_t = torch.tensor([particle_steps], dtype=torch.float64, device="cuda")
+        dist.all_reduce(ps_t)
+        particle_steps_all = float(ps_t.item())
+    else:
+        particle_steps_all = float(particle_steps)
+    value = particle_steps_all / (total_ms * 1e-3)
+    push_ms, push_n = phases["push"]
+    push_avg_ms = push_ms / max(push_n, 1)
+    particles_per_push = particle_steps / args.steps
+    achieved = BYTES_PER_PARTICLE * particles_per_push / (push_avg_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(run, cpic, args.steps, stream)
+
+    # ---- CPU baseline (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, secs, sample = oracle_sample(10, 1, npart=250_000)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample + f" ({secs:.1f} s)"}
+    if dist:
+        dist.barrier()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD.format(S=args.sort_interval), "particles_per_gpu": 2 * args.particles,
+                       "cells": 128 * 256, "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world} (independent runs, no collective)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_traffic(), "kernel": "particle_kernel<2,0> (push)",
+                         "peak_kind": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE},
+            "phases_ms_per_step": {p: ms / max(n, 1) for p, (ms, n) in phases.items()},
+            "push_particle_steps_per_s": particles_per_push / (push_avg_ms * 1e-3),
+            "mg_cycles_mean": float(np.mean(cycles)),
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(out))
+    run.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def ctypes_stream(stream):
+    import ctypes
+
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def end_to_end(run, cpic, steps, stream):
+    """Same metric through the public API with host buffers (pinned), copies included."""
+    import torch
+
+    ns = run.cfg.n_species
+    D = run.D
+    bufs = []
+    for s in range(ns):
+        cap = int(run.cfg.capacity[s])
+        bufs.append((torch.empty(cap, dtype=torch.int32).pin_memory(),
+                     torch.empty(D * cap, dtype=torch.float32).pin_memory(),
+                     torch.empty(3 * cap, dtype=torch.float32).pin_memory()))
+    import ctypes
+
+    counts = []
+    for s in range(ns):
+        n = ctypes.c_int64()
+        c, t, v = bufs[s]
+        cpic.check(cpic.load().cpic_get_particles(run.h, s, c.numel(), ctypes.byref(n), cpic._ptr(c), cpic._ptr(t),
+                                                  cpic._ptr(v)))
+        counts.append(n.value)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ps = 0
+    h2d = d2h = 0
+    for _ in range(steps):
+        for s in range(ns):
+            c, t, v = bufs[s]
+            n = counts[s]
+            cpic.check(cpic.load().cpic_load_particles(run.h, s, n, cpic._ptr(c), cpic._ptr(t), cpic._ptr(v)))
+            h2d += n * (4 + 4 * D + 12)
+            ps += n
+        run.step(1)
+        for s in range(ns):
+            c, t, v = bufs[s]
+            n = ctypes.c_int64()
+            cpic.check(cpic.load().cpic_get_particles(run.h, s, c.numel(), ctypes.byref(n), cpic._ptr(c),
+                                                      cpic._ptr(t), cpic._ptr(v)))
+            counts[s] = n.value
+            d2h += n.value * (4 + 4 * D + 12)
+        run.diag()
+        d2h += ctypes.sizeof(cpic.cpic_diag)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    return {"value": ps / secs, "unit": UNIT, "h2d_bytes_per_step": int(h2d / steps),
+            "d2h_bytes_per_step": int(d2h / steps)}
+
+
+if __name__ == "__main__":
+    main()

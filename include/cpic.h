@@ -118,6 +118,8 @@ const char* cpic_status_string(int status);
 const char* cpic_last_error(void);
 /* ABI version of the loaded library (CPIC_ABI_VERSION when it matches this header). */
 int cpic_abi_version(void);
+/* Number of CUDA kernels this library has launched since it was loaded (all runs). */
+int64_t cpic_kernel_launches(void);
 
 /* ---------------------------------------------------------------- setup */
 
@@ -208,6 +210,21 @@ int cpic_get_vertex_tables(cpic_run* run, float* k, float* g);
 int cpic_get_geometry(cpic_run* run, double* k, double* jc);
 /* Wait for the run's stream. */
 int cpic_synchronize(cpic_run* run);
+
+/* ---------------------------------------------------------------- tracing */
+
+/* Phases of cpic_step timed with CUDA events recorded on the run's stream. */
+#define CPIC_PHASE_FIELD 0   /* a1 vertex field */
+#define CPIC_PHASE_PUSH 1    /* a2-a6 fused push + deposit */
+#define CPIC_PHASE_INJECT 2  /* a8 */
+#define CPIC_PHASE_SORT 3    /* a7 */
+#define CPIC_PHASE_SOLVE 4   /* a9 right-hand side + multigrid + field energy */
+#define CPIC_NPHASES 5
+/* Enable (1) or disable (0) per-phase event timing of cpic_step (off by default). */
+int cpic_profile(cpic_run* run, int enable);
+/* Milliseconds per phase (ms[CPIC_NPHASES], host) and timed occurrences (count, host, may
+ * be NULL) accumulated since the last read; synchronises and resets the accumulators. */
+int cpic_profile_read(cpic_run* run, double* ms, int64_t* count);
 
 #ifdef __cplusplus
 }

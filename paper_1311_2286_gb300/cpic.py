@@ -68,6 +68,7 @@ _SIGS = {
     "cpic_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "cpic_last_error": ([], ctypes.c_char_p),
     "cpic_abi_version": ([], ctypes.c_int),
+    "cpic_kernel_launches": ([], ctypes.c_int64),
     "cpic_query_footprint": ([ctypes.POINTER(cpic_config), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "cpic_create": ([ctypes.POINTER(cpic_config), P, ctypes.c_size_t, P, ctypes.POINTER(P)], ctypes.c_int),
     "cpic_destroy": ([P], ctypes.c_int),
@@ -95,7 +96,10 @@ _SIGS = {
     "cpic_get_vertex_tables": ([P, P, P], ctypes.c_int),
     "cpic_get_geometry": ([P, P, P], ctypes.c_int),
     "cpic_synchronize": ([P], ctypes.c_int),
+    "cpic_profile": ([P, ctypes.c_int], ctypes.c_int),
+    "cpic_profile_read": ([P, P, P], ctypes.c_int),
 }
+PHASES = ("field", "push", "inject", "sort", "solve")
 
 
 class CpicError(RuntimeError):
@@ -273,6 +277,16 @@ class Run:
 
     def synchronize(self):
         check(load().cpic_synchronize(self.h))
+
+    def profile(self, enable=True):
+        check(load().cpic_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{phase: (ms, count)} accumulated since the last read."""
+        ms = np.zeros(len(PHASES), np.float64)
+        cnt = np.zeros(len(PHASES), np.int64)
+        check(load().cpic_profile_read(self.h, _ptr(ms), _ptr(cnt)))
+        return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
 
     # ---- data out
     def diag(self) -> dict:

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <vector>
 
 #include "internal.cuh"
@@ -13,6 +14,9 @@
 namespace cpic {
 
 static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -226,6 +230,44 @@ __global__ void set_count_kernel(DevCounters* ctr, int s, long long n) {
     }
 }
 
+// Loaded particles with a cell index outside the grid, an offset outside [0, 1) or a
+// non-finite velocity would make the mover read outside its vertex tables: they are
+// turned into dead slots and counted as dropped.
+__global__ void validate_load_kernel(int D, int n0, int n1, int n2, int* cell, const float* t, const float* v,
+                                     long long T, long long n, DevCounters* ctr, int s) {
+    long long bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int w = cell[i];
+        if (w < 0) {
+            ++bad;
+            continue;
+        }
+        int c0, c1, c2 = 0;
+        if (D == 2) {
+            c0 = w & 0xFFFF;
+            c1 = w >> 16;
+        } else {
+            c0 = w & 1023;
+            c1 = (w >> 10) & 1023;
+            c2 = w >> 20;
+        }
+        bool ok = c0 < n0 && c1 < n1 && (D == 2 || c2 < n2);
+        for (int a = 0; a < D; ++a) {
+            float x = t[a * T + i];
+            ok = ok && (x >= 0.0f) && (x < 1.0f);
+        }
+        for (int a = 0; a < 3; ++a) ok = ok && isfinite(v[a * T + i]);
+        if (!ok) {
+            cell[i] = -1;
+            ++bad;
+        }
+    }
+    if (bad) {
+        atomicAdd((unsigned long long*)&ctr->dropped[s], (unsigned long long)bad);
+        atomicAdd((unsigned long long*)&ctr->alive[s], (unsigned long long)(-bad));
+    }
+}
+
 #define CHECK_RUN(r)                         \
     do {                                     \
         if (!(r)) {                          \
@@ -272,6 +314,7 @@ int after_map(cpic_run* r) {
         }
     }
     CPIC_CUDA(cudaMemsetAsync(r->lev[0].x, 0, sizeof(double) * r->ncell, r->stream));
+    CPIC_CUDA(cudaMemsetAsync(r->G32, 0, sizeof(float) * r->nvert * (r->D == 2 ? 2 : 4), r->stream));
     r->map_set = true;
     for (int s = 0; s < CPIC_MAX_SPECIES; ++s)
         if (r->inj[s].enabled) {
@@ -281,20 +324,44 @@ int after_map(cpic_run* r) {
     return CPIC_OK;
 }
 
+cudaEvent_t pool_event(cpic_run* r) {
+    if (!r->prof_pool->empty()) {
+        cudaEvent_t e = r->prof_pool->back();
+        r->prof_pool->pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// runs `fn` as phase `ph`, bracketed by events on the run's stream when profiling
+template <class F>
+int phase(cpic_run* r, int ph, F fn) {
+    if (!r->profiling) return fn();
+    cudaEvent_t a = pool_event(r), b = pool_event(r);
+    CPIC_CUDA(cudaEventRecord(a, r->stream));
+    int st = fn();
+    CPIC_CUDA(cudaEventRecord(b, r->stream));
+    r->prof_events->push_back({ph, {a, b}});
+    return st;
+}
+
 int step_once(cpic_run* r) {
-    int st = launch_vertex_field(r);
+    int st = phase(r, CPIC_PHASE_FIELD, [&] { return launch_vertex_field(r); });
     if (st) return st;
-    st = launch_push(r);
+    st = phase(r, CPIC_PHASE_PUSH, [&] { return launch_push(r); });
     if (st) return st;
-    st = launch_inject(r);
+    st = phase(r, CPIC_PHASE_INJECT, [&] { return launch_inject(r); });
     if (st) return st;
     if (r->cfg.sort_interval > 0 && ++r->steps_since_sort >= r->cfg.sort_interval) {
-        st = launch_sort(r);
+        st = phase(r, CPIC_PHASE_SORT, [&] { return launch_sort(r); });
         if (st) return st;
         r->cur_host ^= 1;
         r->steps_since_sort = 0;
     }
-    return mg_solve(r, r->cfg.mg_rtol, r->cfg.mg_max_cycles, false, nullptr, nullptr);
+    return phase(r, CPIC_PHASE_SOLVE,
+                 [&] { return mg_solve(r, r->cfg.mg_rtol, r->cfg.mg_max_cycles, true, nullptr, nullptr); });
 }
 
 }  // namespace
@@ -322,6 +389,8 @@ const char* cpic_status_string(int s) {
 }
 
 const char* cpic_last_error(void) { return g_err; }
+
+int64_t cpic_kernel_launches(void) { return g_launches.load(); }
 
 int cpic_abi_version(void) { return CPIC_ABI_VERSION; }
 
@@ -396,6 +465,8 @@ int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* s
         delete r;
         return st;
     }
+    r->prof_events = new std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>();
+    r->prof_pool = new std::vector<cudaEvent_t>();
     *out = r;
     return CPIC_OK;
 }
@@ -404,6 +475,13 @@ int cpic_destroy(cpic_run* r) {
     if (!r) return CPIC_OK;
     cudaError_t e = cudaStreamSynchronize(r->stream);
     if (r->own_memory) cudaFree(r->arena);
+    for (auto& pe : *r->prof_events) {
+        cudaEventDestroy(pe.second.first);
+        cudaEventDestroy(pe.second.second);
+    }
+    for (cudaEvent_t ev : *r->prof_pool) cudaEventDestroy(ev);
+    delete r->prof_events;
+    delete r->prof_pool;
     delete r;
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
     return CPIC_OK;
@@ -456,6 +534,13 @@ int cpic_load_particles(cpic_run* r, int sp, int64_t n, const int32_t* cell, con
     }
     set_count_kernel<<<1, 32, 0, r->stream>>>(r->ctr, sp, n);
     CPIC_CHECK_LAUNCH();
+    if (n > 0) {
+        long long blocks = (n + 255) / 256;
+        if (blocks > 152 * 4) blocks = 152 * 4;
+        validate_load_kernel<<<(int)blocks, 256, 0, r->stream>>>(r->D, r->n[0], r->n[1], r->n[2], r->pb.cell[b] + base,
+                                                                 r->pb.t[b] + base, r->pb.v[b] + base, T, n, r->ctr, sp);
+        CPIC_CHECK_LAUNCH();
+    }
     // the copies above may read pageable host memory the caller frees after returning
     CPIC_CUDA(cudaStreamSynchronize(r->stream));
     return CPIC_OK;
@@ -681,6 +766,35 @@ int cpic_get_geometry(cpic_run* r, double* k, double* jc) {
 int cpic_synchronize(cpic_run* r) {
     CHECK_RUN(r);
     CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    return CPIC_OK;
+}
+
+int cpic_profile(cpic_run* r, int enable) {
+    CHECK_RUN(r);
+    r->profiling = enable != 0;
+    return CPIC_OK;
+}
+
+int cpic_profile_read(cpic_run* r, double* ms, int64_t* count) {
+    CHECK_RUN(r);
+    if (!ms) {
+        set_error("ms is NULL");
+        return CPIC_ERR_INVALID;
+    }
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    for (int p = 0; p < CPIC_NPHASES; ++p) {
+        ms[p] = 0.0;
+        if (count) count[p] = 0;
+    }
+    for (auto& pe : *r->prof_events) {
+        float t = 0.0f;
+        CPIC_CUDA(cudaEventElapsedTime(&t, pe.second.first, pe.second.second));
+        ms[pe.first] += t;
+        if (count) count[pe.first] += 1;
+        r->prof_pool->push_back(pe.second.first);
+        r->prof_pool->push_back(pe.second.second);
+    }
+    r->prof_events->clear();
     return CPIC_OK;
 }
 

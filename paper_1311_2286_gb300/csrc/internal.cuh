@@ -27,7 +27,13 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
         cudaError_t e_ = (call);                                             \
         if (e_ != cudaSuccess) return cuda_fail(e_, #call, __FILE__, __LINE__); \
     } while (0)
-#define CPIC_CHECK_LAUNCH() CPIC_CUDA(cudaGetLastError())
+// every kernel launch of the library is followed by this check, which also counts it
+void count_launch();
+#define CPIC_CHECK_LAUNCH()           \
+    do {                              \
+        ::cpic::count_launch();       \
+        CPIC_CUDA(cudaGetLastError()); \
+    } while (0)
 
 // ---------------------------------------------------------------- device-side run state
 // Counters written by kernels (one struct in device memory per run).
@@ -142,6 +148,10 @@ struct cpic_run {
     cpic::InjectSpec inj[CPIC_MAX_SPECIES];
     double face_len[6];
     int steps_since_sort;
+    // tracing: event pairs recorded around each phase of cpic_step
+    bool profiling;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>* prof_events;
+    std::vector<cudaEvent_t>* prof_pool;
 };
 
 namespace cpic {

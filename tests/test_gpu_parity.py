@@ -1,0 +1,377 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle, element by element.
+
+Tolerances: integer, index and fixed-point results (cells, absorption faces, deposit
+counts, kinetic-energy fixed-point sums) bit-exact against the FP32 replay of the same
+operation sequence; FP32 state within 1e-5 normwise of the FP64 oracle after one step;
+FP64 geometry bit-exact (same operation order); field solve relative L2 <= 1e-10.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import deposit as odep
+from oracle import geometry, gradient, inject, mover, poisson
+from paper_1311_2286_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+P, Dr, Ne = 0, 1, 2
+PP, PA = 0, 1
+
+
+def _unpack(cell, D=2):
+    c = cell.astype(np.int64)
+    if D == 2:
+        return np.stack([c & 0xFFFF, c >> 16])
+    return np.stack([c & 0x3FF, (c >> 10) & 0x3FF, c >> 20])
+
+
+def _geom(w):
+    per = [w.field_bc[2 * a] == P for a in range(w.dim)]
+    return geometry.build_geometry(w.vertices, per, axisym=w.omega_axisym), per
+
+
+def _cylinder(n1=64, n2=128, npart=200_003, phi_obj=-5.0, seed=5, inject=False):
+    return wl.cylinder(n1=n1, n2=n2, npart_per_species=npart, phi_obj=phi_obj, seed=seed, inject=inject)
+
+
+CASES = {
+    "map2_periodic": lambda: wl.langmuir_map2(32, 32, eps=0.05, ppc=100, vth=0.3, amp=0.01, dt=0.1, seed=3),
+    "cylinder": lambda: _cylinder(),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_geometry_bit_exact(cpic, case):
+    """Spec M on the device reproduces the oracle's FP64 k and J_c bit for bit (same
+    vertex map, same operation order), hence the FP32 mover table too."""
+    w = CASES[case]()
+    g, _ = _geom(w)
+    run = cpic.run_from_workload(w)
+    k64, jc = run.geometry()
+    assert np.array_equal(k64, g.k)
+    assert np.array_equal(jc, g.Jc)
+    K32, _ = run.vertex_tables()
+    assert np.array_equal(K32, g.k.astype(np.float32))
+    run.close()
+
+
+def test_analytic_map_matches_vertex_map(cpic):
+    """The device-evaluated annulus map gives the same metric to rounding."""
+    w = _cylinder(32, 64, 1000)
+    g, _ = _geom(w)
+    run = cpic.run_from_workload(w, analytic=(cpic.CPIC_MAP_ANNULUS, [1.0, 40.0]))
+    k64, jc = run.geometry()
+    np.testing.assert_allclose(k64, g.k, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(jc, g.Jc, rtol=1e-12)
+    run.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_vertex_field_bit_exact(cpic, case):
+    """Spec G: G = float32 of the FP64 vertex differences, bit for bit, given the same phi."""
+    w = CASES[case]()
+    run = cpic.run_from_workload(w)
+    rng = np.random.default_rng(1)
+    phi = wl.random_field(rng, tuple(reversed(w.n)), 0.7)
+    run.set_phi(phi)
+    run.vertex_field()
+    _, G = run.vertex_tables()
+    ref = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value).astype(np.float32)
+    assert np.array_equal(G, ref)
+    run.close()
+
+
+def _push_case(cpic, w, phi, sort_first=False):
+    g, per = _geom(w)
+    run = cpic.run_from_workload(w)
+    if sort_first:
+        run.sort()
+    run.set_phi(phi)
+    run.vertex_field()
+    pre = [run.particles(s) for s in range(len(w.species))]
+    run.push()
+    post = [run.particles(s) for s in range(len(w.species))]
+    charge = [run.charge(s) for s in range(len(w.species))]
+    d = run.diag()
+    run.close()
+    G32 = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value).astype(np.float32)
+    k32 = g.k.astype(np.float32)
+    return g, per, pre, post, charge, d, k32, G32
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("sort_first", [False, True])
+def test_push_bit_exact_vs_replay(cpic, case, sort_first):
+    """a2-a6: after one push, every particle's cell, offsets and velocity equal the FP32
+    replay bit for bit; absorbed counts per face match; the fixed-point charge equals the
+    oracle's spec-Q deposit of the replayed particles exactly; the kinetic-energy
+    fixed-point sum matches exactly."""
+    w = CASES[case]()
+    rng = np.random.default_rng(2)
+    phi = wl.random_field(rng, tuple(reversed(w.n)), 0.5)
+    if case == "cylinder":
+        phi = phi + np.linspace(-5, 0, w.n[0])[None, :]
+    g, per, pre, post, charge, d, k32, G32 = _push_case(cpic, w, phi, sort_first)
+    ke_total = 0.0
+    for s, sp in enumerate(w.species):
+        cell0, t0, v0 = pre[s]
+        idx = _unpack(cell0)
+        i32, t32, v32, face, kefp = mover.push32(idx, t0, v0, k32, G32, w.n, w.particle_bc,
+                                                np.float32(w.dt * sp.q / sp.m), np.float32(0.5 * w.dt),
+                                                np.float32(w.dt))
+        alive = face < 0
+        ref_cell = (i32[0] | (i32[1] << 16))[alive].astype(np.int32)
+        cell1, t1, v1 = post[s]
+        assert cell1.shape == ref_cell.shape
+        assert np.array_equal(cell1, ref_cell)
+        assert np.array_equal(t1, t32[:, alive])
+        assert np.array_equal(v1, v32[:, alive])
+        for f in range(4):
+            assert d["absorbed"][s][f] == int(np.sum(face == f)), (s, f)
+        Cref = odep.deposit_fixed(i32[:, alive].astype(np.int64), t32[:, alive], w.n, per)
+        assert np.array_equal(charge[s], Cref)
+        ke_total += 0.5 * sp.m * sp.w * math.ldexp(float(int(kefp.sum())), -24)
+        assert d["n"][s] == int(alive.sum())
+    assert d["W_K"] == pytest.approx(ke_total, rel=1e-15, abs=1e-300)
+    if case == "cylinder":
+        assert sum(d["absorbed"][0]) > 0  # the case exercises absorption
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_push_vs_fp64_single_step(cpic, case):
+    """Single-step particle state error of FP32 vs FP64 <= 1e-5 normwise (global xi and v);
+    cell/absorption decisions differ only for particles within 1e-5 cells of a face."""
+    w = CASES[case]()
+    rng = np.random.default_rng(3)
+    phi = wl.random_field(rng, tuple(reversed(w.n)), 0.5)
+    g, per, pre, post, charge, d, k32, G32 = _push_case(cpic, w, phi)
+    G64 = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value)
+    for s, sp in enumerate(w.species):
+        cell0, t0, v0 = pre[s]
+        idx = _unpack(cell0)
+        i64, t64, v64, face = mover.push64(idx, t0.astype(np.float64), v0.astype(np.float64), g.k, G64, w.dt,
+                                           sp.q / sp.m, w.n, w.particle_bc)
+        alive64 = face < 0
+        cell1, t1, v1 = post[s]
+        n_mismatch = abs(int(alive64.sum()) - cell1.shape[0])
+        assert n_mismatch <= 2
+        if n_mismatch == 0:
+            i1 = _unpack(cell1)
+            u32 = (i1 + t1.astype(np.float64)) / np.array(w.n)[:, None]
+            u64 = (i64[:, alive64] + t64[:, alive64]) / np.array(w.n)[:, None]
+            du = np.abs(u32 - u64)
+            du = np.minimum(du, 1.0 - du) if case == "map2_periodic" else du
+            assert np.max(du) / np.max(np.abs(u64)) <= 1e-5
+            dv = np.abs(v1.astype(np.float64) - v64[:, alive64])
+            assert np.max(dv) / np.max(np.abs(v64)) <= 1e-5
+
+
+def test_kick_bit_exact(cpic):
+    w = CASES["map2_periodic"]()
+    g, _ = _geom(w)
+    run = cpic.run_from_workload(w)
+    rng = np.random.default_rng(4)
+    phi = wl.random_field(rng, (32, 32), 0.5)
+    run.set_phi(phi)
+    run.vertex_field()
+    run.kick(-0.5)
+    _, _, v = run.particles(0)
+    ps = w.particles[0]
+    G32 = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value).astype(np.float32)
+    ref = mover.kick32(_unpack(ps.cell), ps.t, ps.v, g.k.astype(np.float32), G32, w.n,
+                       np.float32(-0.5 * w.dt * w.species[0].q / w.species[0].m))
+    assert np.array_equal(v, ref)
+    run.close()
+
+
+# ------------------------------------------------------------------ field solve
+
+SOLVER_CASES = {
+    "map2_periodic_9pt": (lambda: wl.map2_vertices(64, 64, 0.08), [P] * 4, [0.0] * 4, False),
+    "annulus_128x256": (lambda: wl.annulus_vertices(128, 256, 1.0, 40.0), [Dr, Dr, P, P], [-5.0, 0.0, 0, 0], False),
+    "map2_dirichlet_neumann": (lambda: wl.map2_vertices(64, 32, 0.08), [Dr, Ne, Dr, Dr], [0.3, 0.0, -1.0, 2.0], False),
+    "sphere_axisym_mms": (lambda: wl.sphere_axisym_vertices(64, 64, 1.0, 10.0), [Dr, Dr, Ne, Ne], [0.0] * 4, True),
+}
+
+
+@pytest.mark.parametrize("case", list(SOLVER_CASES))
+def test_field_solve_vs_direct(cpic, case):
+    """a9: the device multigrid solution equals the oracle's direct solve to relative L2
+    1e-10 on the same charge, for periodic (singular, cross terms), Dirichlet annulus,
+    mixed Dirichlet/Neumann non-orthogonal and anisotropic Omega = r problems."""
+    mk, bc, bv, axisym = SOLVER_CASES[case]
+    X = mk()
+    D = 2
+    n = (X.shape[1] - 1, X.shape[0] - 1)
+    per = [bc[0] == P, bc[2] == P]
+    g = geometry.build_geometry(X, per, axisym=axisym)
+    M, bbc = poisson.assemble(g, bc, bv)
+    rng = np.random.default_rng(5)
+    npart = 50_000
+    idx = np.stack([rng.integers(0, n[0], npart), rng.integers(0, n[1], npart)])
+    t = rng.random((2, npart)).astype(np.float32)
+    pbc = [PP if b == P else PA for b in bc]
+    cfg = cpic.make_config(2, n, bc, bv, pbc, 0.1, [(-1.0, 1.0, 1e-3, npart)], background=0.3,
+                           axisymmetric=axisym)
+    run = cpic.Run(cfg)
+    run.set_map_vertices(X)
+    cell = (idx[0] | (idx[1] << 16)).astype(np.int32)
+    run.load_particles(0, cell, t, np.zeros((3, npart), np.float32))
+    run.deposit()
+    cycles, res = run.solve_field(rtol=1e-13, max_cycles=200)
+    phi = run.phi()
+    C = run.charge(0)
+    assert np.array_equal(C, odep.deposit_fixed(idx, t, n, per))
+    Q = poisson.charge_in_cells(g, [C], [-1e-3], 0.3)
+    ref = poisson.solve(g, M, bbc, Q, bc)
+    err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+    assert err <= 1e-10, (err, cycles, res)
+    run.close()
+
+
+# ------------------------------------------------------------------ sort, injection
+
+def test_sort_preserves_particles_and_orders_cells(cpic):
+    w = _cylinder(64, 128, 100_001)
+    run = cpic.run_from_workload(w)
+    rng = np.random.default_rng(6)
+    run.set_phi(wl.random_field(rng, (128, 64), 0.5) + np.linspace(-5, 0, 64)[None, :])
+    run.vertex_field()
+    run.push()  # creates dead slots
+    before = [run.particles(s) for s in range(2)]
+    d0 = run.diag()
+    run.sort()
+    after = [run.particles(s) for s in range(2)]
+    d1 = run.diag()
+    for s in range(2):
+        cb, tb, vb = before[s]
+        ca, ta, va = after[s]
+        key = (ca & 0xFFFF).astype(np.int64) + 64 * (ca >> 16).astype(np.int64)
+        assert np.all(np.diff(key) >= 0)
+        rec_b = np.rec.fromarrays([cb, tb[0], tb[1], vb[0], vb[1], vb[2]])
+        rec_a = np.rec.fromarrays([ca, ta[0], ta[1], va[0], va[1], va[2]])
+        assert np.array_equal(np.sort(rec_b), np.sort(rec_a))
+        assert d1["n"][s] == d0["n"][s] == ca.shape[0]
+    # charge after sort (deposit of the sorted set) is identical
+    c_before = [run.charge(s) for s in range(2)]
+    run.deposit()
+    for s in range(2):
+        assert np.array_equal(run.charge(s), c_before[s])
+    run.close()
+
+
+def test_injection_matches_oracle(cpic):
+    """a8: the injected count follows floor((n+1) r) - floor(n r); Philox draws and the
+    deposited charge agree with the oracle; velocities agree to FP32 rounding."""
+    n1, n2 = 32, 64
+    w = wl.cylinder(n1=n1, n2=n2, npart_per_species=1000, seed=9, inject=True)
+    g, per = _geom(w)
+    run = cpic.run_from_workload(w)
+    run.vertex_field()
+    run.push()
+    before = [run.particles(s) for s in range(2)]
+    run.inject()
+    after = [run.particles(s) for s in range(2)]
+    d = run.diag()
+    for s, (sp, (s_, face, dens, vth, seed)) in enumerate(zip(w.species, w.injection)):
+        area = inject.face_length_2d(w.vertices, 1)
+        rate = inject.rate_per_step(dens, vth, area, w.dt, sp.w)
+        cnt = inject.count_at_step(rate, 0)
+        idx, t32, v32, keep = inject.inject_2d(g.k, (n1, n2), 1, cnt, 0, s, seed, vth, (0, 0, 0), w.dt)
+        nb = before[s][0].shape[0]
+        ca, ta, va = after[s]
+        new_c, new_t, new_v = ca[nb:], ta[:, nb:], va[:, nb:]
+        assert new_c.shape[0] == int(keep.sum())
+        assert d["injected"][s] == int(keep.sum())
+        np.testing.assert_allclose(new_v, v32, rtol=2e-7, atol=1e-7)
+        ref_cell = (idx[0] | (idx[1] << 16)).astype(np.int32)
+        mism = np.sum(new_c != ref_cell)
+        assert mism <= max(1, cnt // 10000)
+        np.testing.assert_allclose(new_t, t32, atol=1e-5)
+    run.close()
+
+
+def test_edge_cases_empty_and_capacity(cpic):
+    """Empty species, a species filled to capacity with injection (drops are counted, no
+    write past capacity), and particles exactly on the logical boundaries."""
+    # 2000 particles: ~4 injected electrons per step into a species already at capacity
+    w = wl.cylinder(n1=16, n2=32, npart_per_species=2000, seed=3, inject=True, capacity_factor=1.0)
+    w.particles[1] = wl.ParticleSet(np.zeros(0, np.int32), np.zeros((2, 0), np.float32), np.zeros((3, 0), np.float32))
+    # particle at xi = 0 exactly (cell 0, t = 0) and at the last offset below 1
+    w.particles[0].cell[:2] = np.array([0 | (5 << 16), 15 | (7 << 16)], np.int32)
+    w.particles[0].t[0, :2] = np.array([0.0, np.nextafter(np.float32(1), np.float32(0))], np.float32)
+    run = cpic.run_from_workload(w)
+    run.initialize()
+    run.step(3)
+    d = run.diag()
+    assert d["n"][0] <= 2000
+    assert d["dropped"][0] > 0  # capacity exhausted by injection
+    assert d["n"][1] >= 0
+    run.close()
+
+
+def test_invalid_load_is_dropped(cpic):
+    """Particles loaded outside the grid are dropped at load (never gathered)."""
+    w = wl.langmuir_map2(8, 8, ppc=4, seed=1)
+    ps = w.particles[0]
+    ps.cell[:3] = np.array([8, 8 << 16, -1], np.int32)  # i = N1, j = N2, dead
+    ps.t[0, 3] = np.float32(1.0)
+    run = cpic.run_from_workload(w)
+    d = run.diag()
+    assert d["dropped"][0] == 4 and d["n"][0] == ps.n - 4
+    run.deposit()
+    assert int(run.charge(0).sum()) == (ps.n - 4) << 24
+    run.close()
+
+
+# ------------------------------------------------------------------ whole loop
+
+def test_langmuir_cold_frequency_on_device(cpic):
+    """P8 on the device: the cold Langmuir oscillation frequency is within 1% of
+    (2/dt) asin(dt/2) on the distorted map2 grid; charge conserved every step."""
+    w = wl.langmuir_map2(32, 32, eps=0.05, ppc=16, vth=0.0, amp=0.05, dt=0.1, seed=0)
+    run = cpic.run_from_workload(w, mg_rtol=1e-12)
+    run.initialize()
+    amps = []
+    for k in range(101):
+        cell, t, _ = run.particles(0)
+        i = _unpack(cell)
+        xi = (i[0] + t[0].astype(np.float64)) / 32
+        eta = (i[1] + t[1].astype(np.float64)) / 32
+        x = xi + 0.05 * np.sin(2 * np.pi * xi) * np.sin(2 * np.pi * eta)
+        amps.append(np.sum(np.cos(2 * np.pi * x)))
+        if k < 100:
+            run.step(1)
+            assert int(run.charge(0).sum()) == w.particles[0].n << 24
+    import sys, os
+
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_pic import _frequency
+
+    amps = np.array(amps)
+    wfreq = _frequency(amps - amps.mean(), 0.1)
+    target = 2 / 0.1 * math.asin(0.05)
+    assert abs(wfreq - target) / target < 0.01
+    run.close()
+
+
+def test_full_size_cylinder_push_parity(cpic):
+    """Full-size 2D cylinder (128 x 256 cells, 2M + 2M particles, the benchmark's launch
+    configuration): one push compared element by element with the FP32 replay, and the
+    deposit with the oracle's fixed-point deposit."""
+    w = wl.cylinder(n1=128, n2=256, npart_per_species=2_000_000, seed=1, inject=False)
+    rng = np.random.default_rng(8)
+    phi = wl.random_field(rng, (256, 128), 0.3) + np.linspace(-5, 0, 128)[None, :]
+    g, per, pre, post, charge, d, k32, G32 = _push_case(cpic, w, phi, sort_first=True)
+    for s, sp in enumerate(w.species):
+        cell0, t0, v0 = pre[s]
+        i32, t32, v32, face, kefp = mover.push32(_unpack(cell0), t0, v0, k32, G32, w.n, w.particle_bc,
+                                                np.float32(w.dt * sp.q / sp.m), np.float32(0.5 * w.dt),
+                                                np.float32(w.dt))
+        alive = face < 0
+        cell1, t1, v1 = post[s]
+        assert np.array_equal(cell1, (i32[0] | (i32[1] << 16))[alive].astype(np.int32))
+        assert np.array_equal(t1, t32[:, alive]) and np.array_equal(v1, v32[:, alive])
+        assert np.array_equal(charge[s], odep.deposit_fixed(i32[:, alive].astype(np.int64), t32[:, alive], w.n, per))
