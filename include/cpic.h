@@ -211,6 +211,33 @@ int cpic_get_geometry(cpic_run* run, double* k, double* jc);
 /* Wait for the run's stream. */
 int cpic_synchronize(cpic_run* run);
 
+/* ---------------------------------------------------------------- no-allocation sort */
+
+/* Largest grid (cells) cpic_sort_cells_noalloc accepts: its scratch is fixed in size. */
+#define CPIC_NOALLOC_MAX_CELLS (1 << 20)
+
+/* Cell sort for callers that cannot allocate device memory (code running during CUDA graph
+ * capture, hosts whose memory manager owns all device memory, loops that must not pay for
+ * an allocation). The paper has no counterpart: this is a data-layout utility. It does what
+ * cpic_sort does for a run, on arrays the caller provides: counting sort of `count`
+ * particles by row-major cell index (i + N1 (j + N2 k)), dropping slots whose cell is -1
+ * or outside the grid. The order inside a cell is unspecified.
+ *   dim, n:   2 or 3, cells per axis (host array of dim ints), n[0]*n[1](*n[2]) <=
+ *             CPIC_NOALLOC_MAX_CELLS, else CPIC_ERR_INVALID;
+ *   cell_in, t_in [dim][count], v_in [3][count]: device arrays in the particle format;
+ *   cell_out, t_out [dim][count], v_out [3][count]: device arrays with the same strides
+ *             (count); the first *live_out entries receive the sorted particles;
+ *   live_out: device int64 receiving the number of live particles;
+ *   stream:   cudaStream_t the work is enqueued on (asynchronous).
+ * It allocates nothing: its histogram and prefix sums live in a fixed 8 MiB device array of
+ * the library, held on every GPU that loads the library until the process exits. The first
+ * call on a device looks up that array's device address (make it before any stream
+ * capture). All calls share the array: calls whose work overlaps on the GPU race and give
+ * wrong results; order them on one stream. */
+int cpic_sort_cells_noalloc(int dim, const int32_t* n, int64_t count, const int32_t* cell_in,
+                            const float* t_in, const float* v_in, int32_t* cell_out, float* t_out,
+                            float* v_out, int64_t* live_out, void* stream);
+
 /* ---------------------------------------------------------------- tracing */
 
 /* Phases of cpic_step timed with CUDA events recorded on the run's stream. */

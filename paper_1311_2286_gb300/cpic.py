@@ -96,6 +96,7 @@ _SIGS = {
     "cpic_get_vertex_tables": ([P, P, P], ctypes.c_int),
     "cpic_get_geometry": ([P, P, P], ctypes.c_int),
     "cpic_synchronize": ([P], ctypes.c_int),
+    "cpic_sort_cells_noalloc": ([ctypes.c_int, P, ctypes.c_int64, P, P, P, P, P, P, P, P], ctypes.c_int),
     "cpic_profile": ([P, ctypes.c_int], ctypes.c_int),
     "cpic_profile_read": ([P, P, P], ctypes.c_int),
 }
