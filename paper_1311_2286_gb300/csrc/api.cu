@@ -98,6 +98,14 @@ int validate(const cpic_config* c) {
             return CPIC_ERR_INVALID;
         }
     }
+    long long tot = 0;
+    for (int s = 0; s < c->n_species; ++s) tot += (c->capacity[s] + 31) & ~31ll;
+    // the particle kernels index slots with 32-bit integers and look up to three blocks of
+    // 256 past the last slot: keep 4096 slots of headroom below 2^31
+    if (tot > (1ll << 31) - 4096) {
+        set_error("total particle capacity %lld exceeds 2^31 - 4096 slots", tot);
+        return CPIC_ERR_INVALID;
+    }
     if (c->axisymmetric && c->dim != 2) {
         set_error("axisymmetric (Omega = r) geometry is 2D only");
         return CPIC_ERR_INVALID;
@@ -185,10 +193,19 @@ void plan(cpic_run* r, Planner& P) {
     r->hist = P.take<int>((size_t)c.n_species * r->ncell);
     r->scan = P.take<long long>((size_t)c.n_species * r->ncell + 1);
     r->scan_blocks = P.take<long long>(1025);
+    for (int l = 0; l < r->nlevels; ++l) {
+        Level& L = r->lev[l];
+        L.A32 = P.take<float>((size_t)S * L.ncell);
+        L.x32 = P.take<float>(L.ncell);
+        L.b32 = P.take<float>(L.ncell);
+        L.dinv32 = P.take<float>(L.ncell);
+    }
     const Level& Lc = r->lev[r->nlevels - 1];
     long long mm = Lc.ncell + 1;
     r->dense_inv = P.take<double>((size_t)mm * mm);
+    r->dense_inv32 = P.take<float>((size_t)mm * mm);
     r->dense_tmp = P.take<double>((size_t)mm * mm);
+    r->ticket = P.take<unsigned>(4);
 }
 
 void init_geometry_sizes(cpic_run* r, const cpic_config* cfg) {
@@ -288,6 +305,8 @@ int after_map(cpic_run* r) {
     if (st) return st;
     st = mg_setup(r);
     if (st) return st;
+    st = mg_cluster_prepare(r);
+    if (st) return st;
     // host-side constants: sum of J_c (singular projection) and face lengths (injection rate),
     // each summed sequentially in index order
     std::vector<double> jc(r->ncell);
@@ -316,6 +335,7 @@ int after_map(cpic_run* r) {
     CPIC_CUDA(cudaMemsetAsync(r->lev[0].x, 0, sizeof(double) * r->ncell, r->stream));
     CPIC_CUDA(cudaMemsetAsync(r->G32, 0, sizeof(float) * r->nvert * (r->D == 2 ? 2 : 4), r->stream));
     r->map_set = true;
+    invalidate_graphs(r);
     for (int s = 0; s < CPIC_MAX_SPECIES; ++s)
         if (r->inj[s].enabled) {
             const InjectSpec& q = r->inj[s];
@@ -323,6 +343,17 @@ int after_map(cpic_run* r) {
         }
     return CPIC_OK;
 }
+
+}  // namespace
+
+void invalidate_graphs(cpic_run* r) {
+    for (int i = 0; i < 2; ++i) {
+        if (r->step_graph_ok[i]) cudaGraphExecDestroy(r->step_graph[i]);
+        r->step_graph_ok[i] = false;
+    }
+}
+
+namespace {
 
 cudaEvent_t pool_event(cpic_run* r) {
     if (!r->prof_pool->empty()) {
@@ -347,7 +378,73 @@ int phase(cpic_run* r, int ph, F fn) {
     return st;
 }
 
+// enqueue one step's work (stream order); `sort` selects the cell sort
+int enqueue_step(cpic_run* r, bool sort) {
+    int st = launch_vertex_field(r);
+    if (st) return st;
+    st = launch_push(r);
+    if (st) return st;
+    st = launch_inject(r);
+    if (st) return st;
+    if (sort) {
+        st = launch_sort(r);
+        if (st) return st;
+    }
+    return CPIC_OK;
+}
+
+int build_step_graph(cpic_run* r, int with_sort) {
+    if (!r->capture_stream) CPIC_CUDA(cudaStreamCreateWithFlags(&r->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t saved = r->stream;
+    r->stream = r->capture_stream;
+    int st = CPIC_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(r->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        r->stream = saved;
+        return cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+    }
+    st = enqueue_step(r, with_sort != 0);
+    if (!st) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        e = cudaStreamGetCaptureInfo(r->stream, &cs, nullptr, &cg, nullptr, nullptr, nullptr);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamGetCaptureInfo", __FILE__, __LINE__);
+        else st = mg_capture_solve(r, cg, r->cfg.mg_rtol, r->cfg.mg_max_cycles);
+    }
+    e = cudaStreamEndCapture(r->stream, &g);
+    r->stream = saved;
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    r->step_graph[with_sort] = ex;
+    r->step_graph_ok[with_sort] = true;
+    return CPIC_OK;
+}
+
 int step_once(cpic_run* r) {
+    bool sort = r->cfg.sort_interval > 0 && r->steps_since_sort + 1 >= r->cfg.sort_interval;
+    if (!r->profiling) {
+        int wi = sort ? 1 : 0;
+        if (!r->step_graph_ok[wi]) {
+            int st = build_step_graph(r, wi);
+            if (st) return st;
+        }
+        CPIC_CUDA(cudaGraphLaunch(r->step_graph[wi], r->stream));
+        ++r->steps_since_sort;
+        if (sort) {
+            r->cur_host ^= 1;
+            r->steps_since_sort = 0;
+        }
+        return CPIC_OK;
+    }
+    // profiled path: the same work launched stream-ordered, bracketed by events
     int st = phase(r, CPIC_PHASE_FIELD, [&] { return launch_vertex_field(r); });
     if (st) return st;
     st = phase(r, CPIC_PHASE_PUSH, [&] { return launch_push(r); });
@@ -480,6 +577,8 @@ int cpic_destroy(cpic_run* r) {
         cudaEventDestroy(pe.second.second);
     }
     for (cudaEvent_t ev : *r->prof_pool) cudaEventDestroy(ev);
+    invalidate_graphs(r);
+    if (r->capture_stream) cudaStreamDestroy(r->capture_stream);
     delete r->prof_events;
     delete r->prof_pool;
     delete r;
@@ -610,6 +709,7 @@ int cpic_set_injection(cpic_run* r, int sp, int face, double density, double vth
     for (int a = 0; a < 3; ++a) q.drift[a] = drift ? drift[a] : 0.0;
     q.seed = seed;
     q.rate = r->map_set ? (((density * vth) * (1.0 / sqrt(2.0 * M_PI))) * r->face_len[face & 1]) * r->cfg.dt / r->cfg.w[sp] : 0.0;
+    invalidate_graphs(r);
     return CPIC_OK;
 }
 

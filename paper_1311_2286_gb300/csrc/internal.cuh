@@ -16,7 +16,7 @@ constexpr int QK = 12;  // spec Q: offsets quantised to 2^-QK of a cell
 constexpr int QF = 24;  // spec Q: one particle deposits exactly 2^QF charge units
 constexpr int KE_BITS = 24;  // spec D: kinetic energy products in units of 2^-24
 constexpr int MAX_LEVELS = 16;
-constexpr int COARSE_CELLS = 4096;  // levels at or below this size run in one CTA
+constexpr int COARSE_CELLS = 2048;  // levels at or below this size run in one CTA (shared memory)
 constexpr int DENSE_MAX = 512;      // coarsest level solved densely (inverse) up to this size
 
 // ---------------------------------------------------------------- error handling
@@ -97,6 +97,10 @@ struct Level {
     double* omega;    // cell Omega
     double* face[3];  // face coefficients per axis: [D][nface_a] (a^{a0}, a^{a1}, a^{a2})
     double* dv;       // vertex derivatives [D][nvertex][D] (scratch for setup)
+    float* A32;       // FP32 copy of the stencil for the correction cycles
+    float* x32;       // FP32 correction
+    float* b32;       // FP32 residual / right-hand side of the correction
+    float* dinv32;    // FP32 inverse diagonal (Gauss-Seidel)
 };
 
 struct InjectSpec {
@@ -134,8 +138,15 @@ struct cpic_run {
     // multigrid
     int nlevels;
     cpic::Level lev[cpic::MAX_LEVELS];
-    double* dense_inv;           // coarsest inverse [(m+1)^2]
+    double* dense_inv;           // coarsest inverse [(m+1)^2] (FP64, setup)
+    float* dense_inv32;          // FP32 copy used by the correction cycles
     double* dense_tmp;           // setup scratch [(m+1)^2]
+    unsigned* ticket;            // last-block counter of the residual reduction
+    // CUDA graphs of one PIC step (index 1: with the cell sort), captured on capture_stream
+    cudaGraphExec_t step_graph[2];
+    bool step_graph_ok[2];
+    cudaStream_t capture_stream;
+    int cluster_cs;              // cluster size of the cluster solver (0: not applicable)
     int dense_m;                 // coarsest unknowns (+1 row when singular)
     bool singular;
     double sumJ;                 // sum of finest J_c (singular projection)
@@ -175,4 +186,11 @@ int launch_sort(cpic_run* r);
 // mg.cu
 int mg_setup(cpic_run* r);
 int mg_solve(cpic_run* r, double rtol, int max_cycles, bool host_loop, int* cycles, double* res);
+// enqueue the whole solve on the stream being captured into graph `g` after `deps`;
+// returns the node the rest of the step must depend on
+int mg_capture_solve(cpic_run* r, cudaGraph_t g, double rtol, int max_cycles);
+void invalidate_graphs(cpic_run* r);
+// mg_cluster.cu
+int mg_cluster_prepare(cpic_run* r);
+int mg_cluster_solve(cpic_run* r, double rtol, int max_cycles);
 }  // namespace cpic

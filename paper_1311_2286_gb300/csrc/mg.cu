@@ -1,5 +1,4 @@
-// Row a9: the logical-space Poisson solve (Sec. II.B.3; eq. (poiscurv)), FP64, device
-// resident.
+// Row a9: the logical-space Poisson solve (Sec. II.B.3; eq. (poiscurv)), device resident.
 //
 // Discretisation (conservative finite volume with ghost cells): the flux through a face
 // normal to axis a is a^{aa} (phi_R - phi_L) + sum_{b != a} a^{ab} / 4 [(phi_R(+b) + phi_L(+b))
@@ -7,27 +6,36 @@
 // 2 phi_b - phi_in (a Dirichlet face carries a^{aa} 2 (phi_in - phi_b)), Neumann ghosts
 // phi_in (a Neumann face carries no flux), periodic wrap. The assembled row of cell c is
 // M phi = Omega_c Q_c + (Dirichlet terms), M = -(divergence), stored as a 9-point (2D) or
-// 19-point (3D) stencil, of which only the 5/7 face entries are used when the map is
+// 19-point (3D) stencil of which only the 5/7 face entries are used when the map is
 // orthogonal.
 //
-// Solver: multigrid V-cycles, the method class the paper uses (Sec. II.B.3: coarse-grid
-// correction plus Gauss-Seidel smoothing on each level). This implementation rediscretises
-// each coarse level from the map sampled at every other vertex (BoxMG's variational coarse
-// operators and operator-induced interpolation are not reproduced), restricts by summing
-// the 2^D fine residuals (finite-volume conservation), prolongs (bi/tri)linearly with
-// homogeneous ghost rules, and smooths with colour-ordered Gauss-Seidel (2 colours for
-// 5/7-point stencils, 2^D colours when cross terms are present). Levels of at most
-// COARSE_CELLS cells run inside one CTA; the coarsest level is solved with a dense inverse
-// (bordered by the constant null vector when the problem is singular). A singular problem
-// (no Dirichlet face) has its right-hand side projected by subtracting a uniform physical
-// charge density and its solution gauged to sum_c J_c phi_c = 0.
+// Solver: multigrid, the method class the paper uses (Sec. II.B.3: coarse-grid correction
+// plus Gauss-Seidel smoothing on each level), arranged for GB300, whose FP64 rate is ~1/64
+// of its FP32 rate: the solution phi, the right-hand side and the residual are FP64, and
+// each iteration solves for the correction with one FP32 V-cycle (mixed-precision
+// iterative refinement):
+//     r = b - M phi (FP64);  stop if ||r||_2 / ||b||_2 <= rtol;
+//     e = V-cycle_FP32(M, float(r)) from e = 0;  phi += e (FP64).
+// The FP32 cycle only has to reduce the error by its multigrid factor, so the iteration
+// converges to FP64 accuracy at the rate of an FP64 multigrid.
+// V-cycle: coarse levels rediscretised from the map sampled at every other vertex (BoxMG's
+// variational coarse operators and operator-induced interpolation are not reproduced),
+// restriction by summing the 2^D fine residuals (finite-volume conservation), (bi/tri)linear
+// prolongation with homogeneous ghost rules, colour-ordered Gauss-Seidel (2 colours for
+// 5/7-point stencils, 2^D colours with cross terms), levels of at most COARSE_CELLS cells
+// inside one CTA, and a dense inverse on the coarsest level (bordered with the constant
+// null vector when the problem is singular). A singular problem (no Dirichlet face) has its
+// right-hand side projected by subtracting a uniform physical charge density and its
+// solution gauged to sum_c J_c phi_c = 0.
 //
-// Convergence: ||b - M phi||_2 / ||b||_2 <= rtol (Sec. II.B.3 uses a relative tolerance of
-// 1e-10). The residual kernel raises a device flag that makes the remaining cycles' kernels
-// return at once, so a whole solve can be enqueued without a host round trip.
+// The residual kernel ends with a last-block reduction that decides whether to continue;
+// it writes the decision into a CUDA graph conditional handle, so inside a captured step
+// the cycle loop is a conditional WHILE node that runs on the device with no host round
+// trip and no idle launches.
 #include <math.h>
+#include <string.h>
 
-#include <algorithm>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -42,38 +50,41 @@ __constant__ int c_off3[19][3] = {{0, 0, 0},  {-1, 0, 0},  {1, 0, 0},  {0, -1, 0
                                   {1, 1, 0},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1}, {1, 0, 1},
                                   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1}};
 
+template <typename R>
 struct LV {
     int D;
     int n[3];
-    long long ncell;
+    int ncell;
     int S;      // stored stencil entries (9 / 19)
     int used;   // entries used (5/7 without cross terms, else 9/19)
     int ncol;   // Gauss-Seidel colours (2 or 2^D)
     int per[3];
     int bc[6];
-    const double* A;
-    double* x;
-    double* b;
+    const R* A;
+    R* x;
+    R* b;
 };
 
 struct LVSet {
     int nl;
     int first_cta;  // first level solved inside one CTA
-    LV l[MAX_LEVELS];
-    const double* dense_inv;
+    LV<float> l[MAX_LEVELS];
+    const float* dense_inv;
     int dense_m;   // unknowns of the coarsest level
     int singular;
 };
 
-__device__ __forceinline__ void cell_coords(const LV& L, long long c, int* q) {
-    q[0] = (int)(c % L.n[0]);
-    long long r = c / L.n[0];
-    q[1] = (int)(r % L.n[1]);
-    q[2] = (int)(r / L.n[1]);
+template <typename R>
+__device__ __forceinline__ void cell_coords(const LV<R>& L, int c, int* q) {
+    q[0] = c % L.n[0];
+    int r = c / L.n[0];
+    q[1] = r % L.n[1];
+    q[2] = r / L.n[1];
 }
 
-__device__ __forceinline__ long long lin(const LV& L, const int* q) {
-    return q[0] + (long long)L.n[0] * (q[1] + (long long)L.n[1] * q[2]);
+template <typename R>
+__device__ __forceinline__ int lin(const LV<R>& L, const int* q) {
+    return q[0] + L.n[0] * (q[1] + L.n[1] * q[2]);
 }
 
 __device__ __forceinline__ void offsets(int D, int k, int* o) {
@@ -89,8 +100,9 @@ __device__ __forceinline__ void offsets(int D, int k, int* o) {
 }
 
 // neighbour index with periodic wrap; non-periodic out-of-range entries have zero
-// coefficients after assembly, their index is clamped
-__device__ __forceinline__ long long nbr(const LV& L, const int* q, const int* o) {
+// coefficients after assembly, their index is clamped (setup kernels only)
+template <typename R>
+__device__ __forceinline__ int nbr(const LV<R>& L, const int* q, const int* o) {
     int c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -104,69 +116,94 @@ __device__ __forceinline__ long long nbr(const LV& L, const int* q, const int* o
     return lin(L, c);
 }
 
-__device__ __forceinline__ double apply_row(const LV& L, long long c, const int* q, bool skip_centre) {
-    double s = 0.0;
-    for (int k = skip_centre ? 1 : 0; k < L.used; ++k) {
-        int o[3];
-        offsets(L.D, k, o);
-        s += L.A[(long long)k * L.ncell + c] * L.x[nbr(L, q, o)];
+// stencil offset of slot k along axis a (2D: 9 slots, 3D: 19 slots); called with
+// unrolled constant arguments, so it folds away
+__host__ __device__ constexpr int koff(int D, int k, int a) {
+    constexpr int t2[9][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0},
+                              {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0}};
+    constexpr int t3[19][3] = {{0, 0, 0},  {-1, 0, 0},  {1, 0, 0},  {0, -1, 0}, {0, 1, 0},  {0, 0, -1}, {0, 0, 1},
+                               {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                               {1, 0, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1}};
+    return D == 2 ? t2[k][a] : t3[k][a];
+}
+
+// sum_{k >= K0} A_k x_{nb_k} for cell q with compile-time stencil shape <D, NPT>: the
+// wrapped/clamped neighbour coordinates are computed once per axis, slot offsets fold to
+// constants
+template <int D, int NPT, int K0, typename R>
+__device__ __forceinline__ R stencil_sum(const LV<R>& L, int c, const int* q) {
+    int lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        lo[a] = q[a] > 0 ? q[a] - 1 : (L.per[a] ? L.n[a] - 1 : 0);
+        hi[a] = q[a] + 1 < L.n[a] ? q[a] + 1 : (L.per[a] ? 0 : L.n[a] - 1);
+    }
+    const int ix[3] = {lo[0], q[0], hi[0]};
+    const int jy[3] = {L.n[0] * lo[1], L.n[0] * q[1], L.n[0] * hi[1]};
+    int kz[3] = {0, 0, 0};
+    if (D == 3) {
+        const int pl = L.n[0] * L.n[1];
+        kz[0] = pl * lo[2];
+        kz[1] = pl * q[2];
+        kz[2] = pl * hi[2];
+    }
+    R s = R(0);
+#pragma unroll
+    for (int k = K0; k < NPT; ++k) {
+        const int idx = ix[koff(D, k, 0) + 1] + jy[koff(D, k, 1) + 1] + (D == 3 ? kz[koff(D, k, 2) + 1] : 0);
+        s += L.A[k * L.ncell + c] * L.x[idx];
     }
     return s;
 }
 
-// number of cells of one colour and the mapping colour-local index -> cell
-__device__ __forceinline__ long long colour_cells(const LV& L) { return L.ncell / L.ncol; }
-
-__device__ __forceinline__ void colour_cell(const LV& L, int colour, long long idx, int* q) {
-    if (L.ncol == 2) {
-        // parity colouring: (i + j + k) % 2 == colour; n[0] even
-        int h = L.n[0] / 2;
-        long long row = idx / h;
-        int m = (int)(idx % h);
-        int j = (int)(row % L.n[1]);
-        int k = (int)(row / L.n[1]);
-        q[1] = j;
-        q[2] = k;
-        q[0] = 2 * m + ((j + k + colour) & 1);
-    } else {
-        // one bit per axis
-        int h[3] = {L.n[0] / 2, L.D > 1 ? L.n[1] / 2 : 1, L.D > 2 ? L.n[2] / 2 : 1};
-        int m0 = (int)(idx % h[0]);
-        long long r = idx / h[0];
-        int m1 = (int)(r % h[1]);
-        int m2 = (int)(r / h[1]);
-        q[0] = 2 * m0 + (colour & 1);
-        q[1] = 2 * m1 + ((colour >> 1) & 1);
-        q[2] = L.D == 3 ? 2 * m2 + ((colour >> 2) & 1) : 0;
+// cells of one colour: parity colouring (i + j + k) % 2 when ncol == 2 (n[0] even), one
+// bit per axis otherwise (NPT > 2D + 1). The colour-local index space (m, j, k) has a
+// half-length first axis.
+template <int D, int NPT>
+struct Col {
+    static constexpr bool parity = NPT == 2 * D + 1;
+    template <typename R>
+    static __device__ __forceinline__ void dims(const LV<R>& L, int* d) {
+        d[0] = L.n[0] / 2;
+        d[1] = parity ? L.n[1] : L.n[1] / 2;
+        d[2] = D == 3 ? (parity ? L.n[2] : L.n[2] / 2) : 1;
     }
+    static __device__ __forceinline__ void cell(int colour, int m, int j, int k, int* q) {
+        if (parity) {
+            q[0] = 2 * m + ((j + k + colour) & 1);
+            q[1] = j;
+            q[2] = k;
+        } else {
+            q[0] = 2 * m + (colour & 1);
+            q[1] = 2 * j + ((colour >> 1) & 1);
+            q[2] = D == 3 ? 2 * k + ((colour >> 2) & 1) : 0;
+        }
+    }
+};
+
+template <int D, int NPT, typename R>
+__device__ __forceinline__ void smooth_at(const LV<R>& L, const R* dinv, const int* q) {
+    const int c = q[0] + L.n[0] * (q[1] + L.n[1] * q[2]);
+    L.x[c] = (L.b[c] - stencil_sum<D, NPT, 1>(L, c, q)) * dinv[c];
 }
 
-__device__ __forceinline__ void smooth_cell(const LV& L, int colour, long long idx) {
-    int q[3];
-    colour_cell(L, colour, idx, q);
-    long long c = lin(L, q);
-    double s = L.b[c] - apply_row(L, c, q, true);
-    L.x[c] = s / L.A[c];
-}
-
-// residual of the 2^D children of coarse cell C summed into the coarse right-hand side
-__device__ __forceinline__ void restrict_cell(const LV& F, const LV& Cl, long long C) {
-    int qc[3];
-    cell_coords(Cl, C, qc);
-    double acc = 0.0;
-    int nch = F.D == 2 ? 4 : 8;
-    for (int ch = 0; ch < nch; ++ch) {
-        int q[3] = {2 * qc[0] + (ch & 1), 2 * qc[1] + ((ch >> 1) & 1), F.D == 3 ? 2 * qc[2] + ((ch >> 2) & 1) : 0};
-        long long f = lin(F, q);
-        acc += F.b[f] - apply_row(F, f, q, false);
+template <int D, int NPT, typename R>
+__device__ __forceinline__ void restrict_at(const LV<R>& F, const LV<R>& Cl, const int* qc) {
+    R acc = R(0);
+#pragma unroll
+    for (int ch = 0; ch < (D == 2 ? 4 : 8); ++ch) {
+        int q[3] = {2 * qc[0] + (ch & 1), 2 * qc[1] + ((ch >> 1) & 1), D == 3 ? 2 * qc[2] + ((ch >> 2) & 1) : 0};
+        int f = q[0] + F.n[0] * (q[1] + F.n[1] * q[2]);
+        acc += F.b[f] - stencil_sum<D, NPT, 0>(F, f, q);
     }
+    int C = qc[0] + Cl.n[0] * (qc[1] + Cl.n[1] * qc[2]);
     Cl.b[C] = acc;
-    Cl.x[C] = 0.0;
+    Cl.x[C] = R(0);
 }
 
-// coarse correction value at coarse coordinates q (possibly one outside per axis)
-__device__ __forceinline__ double coarse_value(const LV& Cl, int* q) {
-    double sign = 1.0;
+template <typename R>
+__device__ __forceinline__ R coarse_value(const LV<R>& Cl, int* q) {
+    R sign = R(1);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a >= Cl.D) break;
@@ -183,193 +220,294 @@ __device__ __forceinline__ double coarse_value(const LV& Cl, int* q) {
     return sign * Cl.x[lin(Cl, q)];
 }
 
-__device__ __forceinline__ void prolong_cell(const LV& F, const LV& Cl, long long f) {
-    int q[3];
-    cell_coords(F, f, q);
-    int p[3] = {q[0] >> 1, q[1] >> 1, q[2] >> 1};
-    int s[3] = {(q[0] & 1) ? 1 : -1, (q[1] & 1) ? 1 : -1, (q[2] & 1) ? 1 : -1};
-    double acc = 0.0;
-    int nc = F.D == 2 ? 4 : 8;
-    for (int o = 0; o < nc; ++o) {
-        double w = 1.0;
-        int qq[3] = {p[0], p[1], F.D == 3 ? p[2] : 0};
-        for (int a = 0; a < F.D; ++a) {
+template <int D, typename R>
+__device__ __forceinline__ void prolong_at(const LV<R>& F, const LV<R>& Cl, const int* q) {
+    const int p[3] = {q[0] >> 1, q[1] >> 1, q[2] >> 1};
+    const int s[3] = {(q[0] & 1) ? 1 : -1, (q[1] & 1) ? 1 : -1, (q[2] & 1) ? 1 : -1};
+    R acc = R(0);
+#pragma unroll
+    for (int o = 0; o < (D == 2 ? 4 : 8); ++o) {
+        R w = R(1);
+        int qq[3] = {p[0], p[1], D == 3 ? p[2] : 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
             if ((o >> a) & 1) {
                 qq[a] += s[a];
-                w *= 0.25;
+                w *= R(0.25);
             } else {
-                w *= 0.75;
+                w *= R(0.75);
             }
         }
         acc += w * coarse_value(Cl, qq);
     }
-    F.x[f] += acc;
+    F.x[q[0] + F.n[0] * (q[1] + F.n[1] * q[2])] += acc;
 }
 
-// ------------------------------------------------------------------ grid-wide kernels
-__global__ void smooth_kernel(LV L, int colour, const int* done) {
-    if (*done) return;
-    long long m = colour_cells(L);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
-        smooth_cell(L, colour, i);
+// ------------------------------------------------------------------ FP32 cycle kernels
+// 3D launch geometry: x covers the first (index) dimension, y the second, z the third.
+template <int D, int NPT>
+__global__ void smooth_kernel(LV<float> L, const float* __restrict__ dinv, int colour) {
+    int d[3];
+    Col<D, NPT>::dims(L, d);
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    int k = blockIdx.z;
+    if (m >= d[0] || j >= d[1] || k >= d[2]) return;
+    int q[3];
+    Col<D, NPT>::cell(colour, m, j, k, q);
+    smooth_at<D, NPT>(L, dinv, q);
 }
 
-__global__ void restrict_kernel(LV F, LV Cl, const int* done) {
-    if (*done) return;
-    for (long long C = blockIdx.x * (long long)blockDim.x + threadIdx.x; C < Cl.ncell; C += (long long)gridDim.x * blockDim.x)
-        restrict_cell(F, Cl, C);
+template <int D, int NPT>
+__global__ void restrict_kernel(LV<float> F, LV<float> Cl) {
+    int q[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(blockIdx.y * blockDim.y + threadIdx.y), (int)blockIdx.z};
+    if (q[0] >= Cl.n[0] || q[1] >= Cl.n[1] || q[2] >= Cl.n[2]) return;
+    restrict_at<D, NPT>(F, Cl, q);
 }
 
-__global__ void prolong_kernel(LV F, LV Cl, const int* done) {
-    if (*done) return;
-    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < F.ncell; f += (long long)gridDim.x * blockDim.x)
-        prolong_cell(F, Cl, f);
+template <int D>
+__global__ void prolong_kernel(LV<float> F, LV<float> Cl) {
+    int q[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(blockIdx.y * blockDim.y + threadIdx.y), (int)blockIdx.z};
+    if (q[0] >= F.n[0] || q[1] >= F.n[1] || q[2] >= F.n[2]) return;
+    prolong_at<D>(F, Cl, q);
 }
 
-// the lower part of the V-cycle (levels first_cta .. nl-1) inside one CTA
-__global__ void __launch_bounds__(1024) coarse_cycle_kernel(LVSet S, int nu1, int nu2, const int* done) {
-    if (*done) return;
-    __shared__ double sb[DENSE_MAX + 1];
+// The lower part of the V-cycle (levels first_cta .. nl-1) inside one CTA, with every
+// level's stencil, inverse diagonal, correction and right-hand side in shared memory (the
+// top level's right-hand side comes from global memory, its correction goes back there).
+// All levels of a run share one stencil shape <D, NPT>.
+template <int D, int NPT>
+__global__ void __launch_bounds__(512) coarse_cycle_kernel(LVSet S, int nu1, int nu2) {
+    extern __shared__ float sm[];
+    __shared__ float sb[DENSE_MAX + 1];
+    __shared__ LV<float> V[MAX_LEVELS];
+    __shared__ float* Dv[MAX_LEVELS];
     const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
+        int off = 0;
+        for (int l = S.first_cta; l < S.nl; ++l) {
+            V[l] = S.l[l];
+            V[l].A = sm + off;
+            off += NPT * S.l[l].ncell;
+            Dv[l] = sm + off;
+            off += S.l[l].ncell;
+            V[l].x = sm + off;
+            off += S.l[l].ncell;
+            V[l].b = sm + off;
+            off += S.l[l].ncell;
+        }
+    }
+    __syncthreads();
+    for (int l = S.first_cta; l < S.nl; ++l) {
+        const LV<float>& G = S.l[l];
+        float* A = const_cast<float*>(V[l].A);
+        for (int e = tid; e < NPT * G.ncell; e += nt) A[e] = G.A[e];
+        for (int c = tid; c < G.ncell; c += nt) {
+            Dv[l][c] = 1.0f / G.A[c];
+            V[l].x[c] = 0.0f;
+            if (l == S.first_cta) V[l].b[c] = G.b[c];
+        }
+    }
+    __syncthreads();
+    auto sweep = [&](int l, int col) {
+        const LV<float>& L = V[l];
+        int d[3];
+        Col<D, NPT>::dims(L, d);
+        const int plane = d[0] * d[1];
+        for (int idx = tid; idx < plane * d[2]; idx += nt) {
+            int k = idx / plane, r = idx - k * plane;
+            int j = r / d[0], m = r - j * d[0];
+            int q[3];
+            Col<D, NPT>::cell(col, m, j, k, q);
+            smooth_at<D, NPT>(L, (const float*)Dv[l], q);
+        }
+        __syncthreads();
+    };
     for (int l = S.first_cta; l < S.nl - 1; ++l) {
-        const LV& L = S.l[l];
         for (int it = 0; it < nu1; ++it)
-            for (int col = 0; col < L.ncol; ++col) {
-                long long m = colour_cells(L);
-                for (long long i = tid; i < m; i += nt) smooth_cell(L, col, i);
-                __syncthreads();
-            }
-        const LV& Cl = S.l[l + 1];
-        for (long long C = tid; C < Cl.ncell; C += nt) restrict_cell(L, Cl, C);
+            for (int col = 0; col < V[l].ncol; ++col) sweep(l, col);
+        const LV<float>& C = V[l + 1];
+        const int plane = C.n[0] * C.n[1];
+        for (int idx = tid; idx < C.ncell; idx += nt) {
+            int k = idx / plane, r = idx - k * plane;
+            int j = r / C.n[0];
+            int q[3] = {r - j * C.n[0], j, k};
+            restrict_at<D, NPT>(V[l], C, q);
+        }
         __syncthreads();
     }
-    // coarsest: dense solve x = inv * [b; 0]
     {
-        const LV& L = S.l[S.nl - 1];
+        const LV<float>& L = V[S.nl - 1];
         int m = S.dense_m;
         int mm = m + (S.singular ? 1 : 0);
-        for (int i = tid; i < mm; i += nt) sb[i] = i < m ? L.b[i] : 0.0;
+        for (int i = tid; i < mm; i += nt) sb[i] = i < m ? L.b[i] : 0.0f;
         __syncthreads();
         for (int i = tid; i < m; i += nt) {
-            const double* row = S.dense_inv + (long long)i * mm;
-            double acc = 0.0;
+            const float* row = S.dense_inv + i * mm;
+            float acc = 0.0f;
             for (int k = 0; k < mm; ++k) acc += row[k] * sb[k];
             L.x[i] = acc;
         }
         __syncthreads();
     }
     for (int l = S.nl - 2; l >= S.first_cta; --l) {
-        const LV& L = S.l[l];
-        const LV& Cl = S.l[l + 1];
-        for (long long f = tid; f < L.ncell; f += nt) prolong_cell(L, Cl, f);
+        const LV<float>& L = V[l];
+        const int plane = L.n[0] * L.n[1];
+        for (int idx = tid; idx < L.ncell; idx += nt) {
+            int k = idx / plane, r = idx - k * plane;
+            int j = r / L.n[0];
+            int q[3] = {r - j * L.n[0], j, k};
+            prolong_at<D>(L, V[l + 1], q);
+        }
         __syncthreads();
         for (int it = 0; it < nu2; ++it)
-            for (int col = L.ncol - 1; col >= 0; --col) {
-                long long m = colour_cells(L);
-                for (long long i = tid; i < m; i += nt) smooth_cell(L, col, i);
-                __syncthreads();
-            }
+            for (int col = V[l].ncol - 1; col >= 0; --col) sweep(l, col);
     }
+    const LV<float>& T = S.l[S.first_cta];
+    for (int c = tid; c < T.ncell; c += nt) T.x[c] = V[S.first_cta].x[c];
 }
 
-// ------------------------------------------------------------------ reductions
+// ------------------------------------------------------------------ FP64 outer iteration
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         b += __shfl_xor_sync(0xffffffffu, b, o);
     }
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    int w = tid >> 5, l = tid & 31;
     if (l == 0) {
         sh[2 * w] = a;
         sh[2 * w + 1] = b;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double x = 0.0, y = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            x += sh[2 * i];
-            y += sh[2 * i + 1];
+    if (w == 0) {
+        int nw = (blockDim.x * blockDim.y) >> 5;
+        a = l < nw ? sh[2 * l] : 0.0;
+        b = l < nw ? sh[2 * l + 1] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
         }
-        a = x;
-        b = y;
     }
+    __syncthreads();
 }
 
-// mode 0: (||b - A x||^2, ||b||^2); mode 1: (sum b, 0); mode 2: (sum J x, 0)
-__global__ void reduce_kernel(LV L, int mode, const double* Jc, double* part, const int* done) {
-    if (done && *done) return;
+struct ResidualParams {
+    LV<double> L;       // finest level, FP64 (x = phi, b = right-hand side)
+    float* r32;         // FP32 residual (right-hand side of the correction cycle)
+    double* part;       // [2 * RED_BLOCKS]
+    unsigned* ticket;
+    DevCounters* ctr;
+    int* done;
+    double rtol;
+    int max_cycles;
+    int count_cycle;
+    int use_handle;
+    cudaGraphConditionalHandle handle;
+};
+
+// r = b - M phi in FP64, its FP32 copy, and ||r||, ||b||; the last block to finish sums the
+// block partials in a fixed tree, updates the counters and decides whether to continue.
+// Blocks of 32 x 8 threads walk rows (j, k) of 32-cell segments.
+template <int D, int NPT>
+__global__ void __launch_bounds__(256) residual_kernel(ResidualParams P) {
     __shared__ double sh[64];
-    double a = 0.0, b = 0.0;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < L.ncell; c += (long long)gridDim.x * blockDim.x) {
-        if (mode == 0) {
-            int q[3];
-            cell_coords(L, c, q);
-            double r = L.b[c] - apply_row(L, c, q, false);
-            a += r * r;
-            b += L.b[c] * L.b[c];
-        } else if (mode == 1) {
-            a += L.b[c];
-        } else {
-            a += Jc[c] * L.x[c];
+    __shared__ bool last;
+    const LV<double>& L = P.L;
+    double rr = 0.0, bb = 0.0;
+    const int nrows = L.n[1] * L.n[2];
+    for (int row = blockIdx.x * blockDim.y + threadIdx.y; row < nrows; row += gridDim.x * blockDim.y) {
+        int j = row % L.n[1], k = row / L.n[1];
+        for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
+            int q[3] = {i, j, k};
+            int c = i + L.n[0] * row;
+            double r = L.b[c] - stencil_sum<D, NPT, 0>(L, c, q);
+            P.r32[c] = (float)r;
+            rr += r * r;
+            bb += L.b[c] * L.b[c];
         }
+    }
+    block_sum2(rr, bb, sh);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (tid == 0) {
+        P.part[2 * blockIdx.x] = rr;
+        P.part[2 * blockIdx.x + 1] = bb;
+        __threadfence();
+        unsigned t = atomicAdd(P.ticket, 1u);
+        last = t == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int i = tid; i < (int)gridDim.x; i += blockDim.x * blockDim.y) {
+        a += P.part[2 * i];
+        b += P.part[2 * i + 1];
     }
     block_sum2(a, b, sh);
-    if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = a;
-        part[2 * blockIdx.x + 1] = b;
+    if (tid == 0) {
+        *P.ticket = 0;
+        DevCounters* ctr = P.ctr;
+        if (P.count_cycle) ctr->mg_cycles += 1;
+        double res = b > 0.0 ? sqrt(a) / sqrt(b) : 0.0;
+        ctr->mg_residual = res;
+        ctr->mg_bnorm = sqrt(b);
+        bool converged = res <= P.rtol;
+        if (converged) ctr->mg_converged = 1;
+        bool cont = !converged && ctr->mg_cycles < P.max_cycles;
+        *P.done = cont ? 0 : 1;
+        if (P.use_handle) cudaGraphSetConditional(P.handle, cont ? 1u : 0u);
     }
 }
 
-// sums the block partials in a fixed order; mode 0 updates the convergence state
-__global__ void norm_final_kernel(const double* part, int nb, double rtol, int count_cycle, DevCounters* ctr,
-                                  int* done) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (*done) return;
-    double rr = 0.0, bb = 0.0;
-    for (int i = 0; i < nb; ++i) {
-        rr += part[2 * i];
-        bb += part[2 * i + 1];
-    }
-    double res = bb > 0.0 ? sqrt(rr) / sqrt(bb) : 0.0;
-    if (count_cycle) ctr->mg_cycles += 1;
-    ctr->mg_residual = res;
-    ctr->mg_bnorm = sqrt(bb);
-    if (res <= rtol) {
-        *done = 1;
-        ctr->mg_converged = 1;
-    }
+// phi += e (FP64 update with the FP32 correction)
+__global__ void update_kernel(double* phi, const float* e, int n) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) phi[c] += (double)e[c];
+}
+
+// mode 1: (sum b, -); mode 2: (sum J phi, -)
+__global__ void sum_kernel(LV<double> L, int mode, const double* Jc, double* part) {
+    __shared__ double sh[64];
+    double a = 0.0, b = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.ncell; c += gridDim.x * blockDim.x)
+        a += mode == 1 ? L.b[c] : Jc[c] * L.x[c];
+    block_sum2(a, b, sh);
+    if (threadIdx.x == 0) part[2 * blockIdx.x] = a;
+}
+
+__device__ __forceinline__ double sum_parts(const double* part, int nb, double* sh) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) a += part[2 * i];
+    block_sum2(a, b, sh);
+    return a;  // valid in warp 0
 }
 
 // b -= (sum b / sum J) J  (singular problems)
-__global__ void project_kernel(LV L, const double* part, int nb, double sumJ, const double* Jc) {
+__global__ void project_kernel(LV<double> L, const double* part, int nb, double sumJ, const double* Jc) {
+    __shared__ double sh[64];
     __shared__ double shift;
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < nb; ++i) s += part[2 * i];
-        shift = s / sumJ;
-    }
+    double s = sum_parts(part, nb, sh);
+    if (threadIdx.x == 0) shift = s / sumJ;
     __syncthreads();
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < L.ncell; c += (long long)gridDim.x * blockDim.x)
-        L.b[c] -= shift * Jc[c];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.ncell; c += gridDim.x * blockDim.x) L.b[c] -= shift * Jc[c];
 }
 
-// x -= (sum J x / sum J)  (gauge of singular problems)
-__global__ void gauge_kernel(LV L, const double* part, int nb, double sumJ) {
+// phi -= (sum J phi / sum J)  (gauge of singular problems)
+__global__ void gauge_kernel(LV<double> L, const double* part, int nb, double sumJ) {
+    __shared__ double sh[64];
     __shared__ double shift;
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < nb; ++i) s += part[2 * i];
-        shift = s / sumJ;
-    }
+    double s = sum_parts(part, nb, sh);
+    if (threadIdx.x == 0) shift = s / sumJ;
     __syncthreads();
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < L.ncell; c += (long long)gridDim.x * blockDim.x)
-        L.x[c] -= shift;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.ncell; c += gridDim.x * blockDim.x) L.x[c] -= shift;
 }
 
-__global__ void reset_solve_kernel(DevCounters* ctr, int* done) {
+__global__ void reset_solve_kernel(DevCounters* ctr, int* done, unsigned* ticket) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         *done = 0;
+        *ticket = 0;
         ctr->mg_cycles = 0;
         ctr->mg_converged = 0;
     }
@@ -377,7 +515,7 @@ __global__ void reset_solve_kernel(DevCounters* ctr, int* done) {
 
 // ------------------------------------------------------------------ setup kernels
 struct AsmParams {
-    LV L;
+    LV<double> L;
     const double* face[3];
     int bc[6];
     double bcv[6];
@@ -397,8 +535,8 @@ __device__ __forceinline__ int slot_of(int D, const int* o) {
 }
 
 __global__ void assemble_kernel(AsmParams P) {
-    const LV& L = P.L;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < L.ncell; c += (long long)gridDim.x * blockDim.x) {
+    const LV<double>& L = P.L;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.ncell; c += gridDim.x * blockDim.x) {
         int q[3];
         cell_coords(L, c, q);
         double a[19];
@@ -465,7 +603,7 @@ __global__ void assemble_kernel(AsmParams P) {
         int faces = 2 * L.D + 1;
         bool cross = false;
         for (int k = 0; k < L.S; ++k) {
-            P.A[(long long)k * L.ncell + c] = a[k];
+            P.A[(size_t)k * L.ncell + c] = a[k];
             if (k >= faces && a[k] != 0.0) cross = true;
         }
         if (cross) atomicOr(P.cross_flag, 1);
@@ -473,13 +611,20 @@ __global__ void assemble_kernel(AsmParams P) {
     }
 }
 
+__global__ void inv_diag_kernel(const float* A, float* dinv, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dinv[i] = 1.0f / A[i];
+}
+
+__global__ void to_float_kernel(const double* src, float* dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
 // dense matrix of the coarsest level (bordered with ones when singular), row-major mm x mm
-__global__ void dense_matrix_kernel(LV L, int singular, double* M) {
+__global__ void dense_matrix_kernel(LV<double> L, int singular, double* M) {
     int m = (int)L.ncell, mm = m + (singular ? 1 : 0);
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)mm * mm; e += (long long)gridDim.x * blockDim.x)
-        M[e] = 0.0;
+    for (long long e = threadIdx.x; e < (long long)mm * mm; e += blockDim.x) M[e] = 0.0;
     __syncthreads();
-    if (blockIdx.x != 0) return;
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
         int q[3];
         cell_coords(L, c, q);
@@ -487,7 +632,7 @@ __global__ void dense_matrix_kernel(LV L, int singular, double* M) {
             int o[3];
             offsets(L.D, k, o);
             long long nb = nbr(L, q, o);
-            double v = L.A[(long long)k * L.ncell + c];
+            double v = L.A[(size_t)k * L.ncell + c];
             if (v != 0.0) M[(long long)c * mm + nb] += v;
         }
         if (singular) {
@@ -537,9 +682,8 @@ __global__ void gauss_jordan_kernel(double* M, double* Inv, int n, int* fail) {
         __syncthreads();
         for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
             int r = (int)(e / n), k = (int)(e % n);
-            if (r == col) continue;
+            if (r == col || k == col) continue;
             double f = M[(long long)r * n + col];
-            if (k == col) continue;  // column col is cleared below
             M[e] -= f * M[(long long)col * n + k];
             Inv[e] -= f * Inv[(long long)col * n + k];
         }
@@ -554,22 +698,29 @@ __global__ void gauss_jordan_kernel(double* M, double* Inv, int n, int* fail) {
     }
 }
 
-LV make_lv(const cpic_run* r, int l) {
+template <typename R>
+LV<R> make_lv(const cpic_run* r, int l, bool fp32) {
     const Level& Lv = r->lev[l];
-    LV L;
+    LV<R> L;
     L.D = r->D;
     for (int a = 0; a < 3; ++a) {
         L.n[a] = a < r->D ? Lv.n[a] : 1;
         L.per[a] = a < r->D ? (r->cfg.field_bc[2 * a] == CPIC_BC_PERIODIC) : 0;
     }
     for (int f = 0; f < 6; ++f) L.bc[f] = r->cfg.field_bc[f];
-    L.ncell = Lv.ncell;
+    L.ncell = (int)Lv.ncell;
     L.S = Lv.S;
     L.used = Lv.cross ? Lv.S : 2 * r->D + 1;
     L.ncol = Lv.cross ? (1 << r->D) : 2;
-    L.A = Lv.A;
-    L.x = Lv.x;
-    L.b = Lv.b;
+    if (fp32) {
+        L.A = (const R*)Lv.A32;
+        L.x = (R*)Lv.x32;
+        L.b = (R*)Lv.b32;
+    } else {
+        L.A = (const R*)Lv.A;
+        L.x = (R*)Lv.x;
+        L.b = (R*)Lv.b;
+    }
     return L;
 }
 
@@ -585,13 +736,132 @@ LVSet make_set(const cpic_run* r) {
     S.nl = r->nlevels;
     S.first_cta = r->nlevels - 1;
     for (int l = 0; l < r->nlevels; ++l) {
-        S.l[l] = make_lv(r, l);
+        S.l[l] = make_lv<float>(r, l, true);
         if (r->lev[l].ncell <= COARSE_CELLS && l < S.first_cta) S.first_cta = l;
     }
-    S.dense_inv = r->dense_inv;
+    S.dense_inv = r->dense_inv32;
     S.dense_m = (int)r->lev[r->nlevels - 1].ncell;
     S.singular = r->singular ? 1 : 0;
     return S;
+}
+
+size_t cta_smem_bytes(const LVSet& S) {
+    size_t f = 0;
+    for (int l = S.first_cta; l < S.nl; ++l) f += (size_t)(S.l[l].used + 3) * S.l[l].ncell;
+    return f * sizeof(float);
+}
+
+int* done_flag(cpic_run* r) { return reinterpret_cast<int*>(r->red + 2 * RED_BLOCKS + 2); }
+
+const dim3 kCellBlock(32, 8, 1);
+
+dim3 cell_grid(int n0, int n1, int n2) {
+    return dim3((unsigned)((n0 + 31) / 32), (unsigned)((n1 + 7) / 8), (unsigned)n2);
+}
+
+// calls f(std::integral_constant<int, D>, std::integral_constant<int, NPT>) for the run's
+// stencil shape (all levels share it: the finest level's cross-term flag decides)
+template <class F>
+int dispatch_shape(const cpic_run* r, F f) {
+    const bool cross = r->lev[0].cross != 0;
+    if (r->D == 2) return cross ? f(std::integral_constant<int, 2>(), std::integral_constant<int, 9>())
+                                : f(std::integral_constant<int, 2>(), std::integral_constant<int, 5>());
+    return cross ? f(std::integral_constant<int, 3>(), std::integral_constant<int, 19>())
+                 : f(std::integral_constant<int, 3>(), std::integral_constant<int, 7>());
+}
+
+// one FP32 V-cycle on the correction equation (e = 0 first), then phi += e
+int enqueue_correction(cpic_run* r, const LVSet& S) {
+    return dispatch_shape(r, [&](auto Dc, auto Nc) -> int {
+        constexpr int D = decltype(Dc)::value, NPT = decltype(Nc)::value;
+        cudaStream_t st = r->stream;
+        const int nu1 = 2, nu2 = 2;
+        CPIC_CUDA(cudaMemsetAsync(r->lev[0].x32, 0, sizeof(float) * r->lev[0].ncell, st));
+        const int top = S.first_cta;
+        auto smooth = [&](int l, int col) -> int {
+            const LV<float>& L = S.l[l];
+            int d[3] = {L.n[0] / 2, Col<D, NPT>::parity ? L.n[1] : L.n[1] / 2,
+                        D == 3 ? (Col<D, NPT>::parity ? L.n[2] : L.n[2] / 2) : 1};
+            smooth_kernel<D, NPT><<<cell_grid(d[0], d[1], d[2]), kCellBlock, 0, st>>>(L, r->lev[l].dinv32, col);
+            CPIC_CHECK_LAUNCH();
+            return CPIC_OK;
+        };
+        for (int l = 0; l < top; ++l) {
+            for (int it = 0; it < nu1; ++it)
+                for (int col = 0; col < S.l[l].ncol; ++col)
+                    if (int e = smooth(l, col)) return e;
+            const LV<float>& C = S.l[l + 1];
+            restrict_kernel<D, NPT><<<cell_grid(C.n[0], C.n[1], C.n[2]), kCellBlock, 0, st>>>(S.l[l], C);
+            CPIC_CHECK_LAUNCH();
+        }
+        size_t smem = cta_smem_bytes(S);
+        if (smem > 200 * 1024) {
+            set_error("multigrid: coarse levels need %zu bytes of shared memory", smem);
+            return CPIC_ERR_INVALID;
+        }
+        CPIC_CUDA(cudaFuncSetAttribute(coarse_cycle_kernel<D, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        coarse_cycle_kernel<D, NPT><<<1, 512, smem, st>>>(S, nu1, nu2);
+        CPIC_CHECK_LAUNCH();
+        for (int l = top - 1; l >= 0; --l) {
+            const LV<float>& L = S.l[l];
+            prolong_kernel<D><<<cell_grid(L.n[0], L.n[1], L.n[2]), kCellBlock, 0, st>>>(L, S.l[l + 1]);
+            CPIC_CHECK_LAUNCH();
+            for (int it = 0; it < nu2; ++it)
+                for (int col = L.ncol - 1; col >= 0; --col)
+                    if (int e = smooth(l, col)) return e;
+        }
+        update_kernel<<<grid_blocks(r->lev[0].ncell, 256), 256, 0, st>>>(r->lev[0].x, r->lev[0].x32, (int)r->lev[0].ncell);
+        CPIC_CHECK_LAUNCH();
+        return CPIC_OK;
+    });
+}
+
+int enqueue_residual(cpic_run* r, double rtol, int max_cycles, int count_cycle, bool use_handle,
+                     cudaGraphConditionalHandle h) {
+    ResidualParams P;
+    P.L = make_lv<double>(r, 0, false);
+    P.r32 = r->lev[0].b32;
+    P.part = r->red;
+    P.ticket = r->ticket;
+    P.ctr = r->ctr;
+    P.done = done_flag(r);
+    P.rtol = rtol;
+    P.max_cycles = max_cycles;
+    P.count_cycle = count_cycle;
+    P.use_handle = use_handle ? 1 : 0;
+    P.handle = h;
+    return dispatch_shape(r, [&](auto Dc, auto Nc) -> int {
+        residual_kernel<decltype(Dc)::value, decltype(Nc)::value><<<RED_BLOCKS, kCellBlock, 0, r->stream>>>(P);
+        CPIC_CHECK_LAUNCH();
+        return CPIC_OK;
+    });
+}
+
+// right-hand side (and its projection); resets the solve counters
+int enqueue_prologue(cpic_run* r) {
+    reset_solve_kernel<<<1, 32, 0, r->stream>>>(r->ctr, done_flag(r), r->ticket);
+    CPIC_CHECK_LAUNCH();
+    int st = launch_rhs(r, r->lev[0].b);
+    if (st) return st;
+    if (r->singular) {
+        LV<double> L0 = make_lv<double>(r, 0, false);
+        sum_kernel<<<RED_BLOCKS, 256, 0, r->stream>>>(L0, 1, r->lev[0].Jc, r->red);
+        CPIC_CHECK_LAUNCH();
+        project_kernel<<<grid_blocks(L0.ncell, 256), 256, 0, r->stream>>>(L0, r->red, RED_BLOCKS, r->sumJ, r->lev[0].Jc);
+        CPIC_CHECK_LAUNCH();
+    }
+    return CPIC_OK;
+}
+
+int enqueue_epilogue(cpic_run* r) {
+    if (r->singular) {
+        LV<double> L0 = make_lv<double>(r, 0, false);
+        sum_kernel<<<RED_BLOCKS, 256, 0, r->stream>>>(L0, 2, r->lev[0].Jc, r->red);
+        CPIC_CHECK_LAUNCH();
+        gauge_kernel<<<grid_blocks(L0.ncell, 256), 256, 0, r->stream>>>(L0, r->red, RED_BLOCKS, r->sumJ);
+        CPIC_CHECK_LAUNCH();
+    }
+    return launch_field_energy(r);
 }
 
 }  // namespace
@@ -602,8 +872,8 @@ int mg_setup(cpic_run* r) {
         Level& Lv = r->lev[l];
         CPIC_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), r->stream));
         AsmParams P;
-        Lv.cross = 1;  // make_lv stores all entries while assembling
-        P.L = make_lv(r, l);
+        Lv.cross = 1;  // all entries while assembling
+        P.L = make_lv<double>(r, l, false);
         for (int a = 0; a < 3; ++a) P.face[a] = Lv.face[a];
         for (int f = 0; f < 6; ++f) {
             P.bc[f] = r->cfg.field_bc[f];
@@ -614,24 +884,31 @@ int mg_setup(cpic_run* r) {
         P.cross_flag = flag;
         assemble_kernel<<<grid_blocks(Lv.ncell, 256), 256, 0, r->stream>>>(P);
         CPIC_CHECK_LAUNCH();
+        to_float_kernel<<<grid_blocks((long long)Lv.S * Lv.ncell, 256), 256, 0, r->stream>>>(Lv.A, Lv.A32,
+                                                                                              (long long)Lv.S * Lv.ncell);
+        CPIC_CHECK_LAUNCH();
+        inv_diag_kernel<<<grid_blocks(Lv.ncell, 256), 256, 0, r->stream>>>(Lv.A32, Lv.dinv32, (int)Lv.ncell);
+        CPIC_CHECK_LAUNCH();
         int hflag = 0;
         CPIC_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, r->stream));
         CPIC_CUDA(cudaStreamSynchronize(r->stream));
         Lv.cross = hflag;
     }
-    // dense inverse of the coarsest level
     const Level& Lc = r->lev[r->nlevels - 1];
     int m = (int)Lc.ncell;
     int mm = m + (r->singular ? 1 : 0);
     r->dense_m = mm;
-    double* M = r->dense_tmp;
-    LV L = make_lv(r, r->nlevels - 1);
-    dense_matrix_kernel<<<1, 256, 0, r->stream>>>(L, r->singular ? 1 : 0, M);
+    LV<double> L = make_lv<double>(r, r->nlevels - 1, false);
+    dense_matrix_kernel<<<1, 256, 0, r->stream>>>(L, r->singular ? 1 : 0, r->dense_tmp);
     CPIC_CHECK_LAUNCH();
     int* fail = flag;
     CPIC_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), r->stream));
-    gauss_jordan_kernel<<<1, 1024, 0, r->stream>>>(M, r->dense_inv, mm, fail);
+    gauss_jordan_kernel<<<1, 1024, 0, r->stream>>>(r->dense_tmp, r->dense_inv, mm, fail);
     CPIC_CHECK_LAUNCH();
+    to_float_kernel<<<grid_blocks((long long)mm * mm, 256), 256, 0, r->stream>>>(r->dense_inv, r->dense_inv32,
+                                                                                  (long long)mm * mm);
+    CPIC_CHECK_LAUNCH();
+    CPIC_CUDA(cudaMemsetAsync(r->ticket, 0, sizeof(unsigned) * 4, r->stream));
     int hfail = 0;
     CPIC_CUDA(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, r->stream));
     CPIC_CUDA(cudaStreamSynchronize(r->stream));
@@ -642,76 +919,33 @@ int mg_setup(cpic_run* r) {
     return CPIC_OK;
 }
 
-static int vcycle_grid(cpic_run* r, const LVSet& S, int l, const int* done, int nu1, int nu2) {
-    if (l >= S.first_cta) {
-        coarse_cycle_kernel<<<1, 1024, 0, r->stream>>>(S, nu1, nu2, done);
-        CPIC_CHECK_LAUNCH();
-        return CPIC_OK;
-    }
-    const LV& L = S.l[l];
-    const LV& C = S.l[l + 1];
-    int tb = 256;
-    for (int it = 0; it < nu1; ++it)
-        for (int col = 0; col < L.ncol; ++col) {
-            smooth_kernel<<<grid_blocks(L.ncell / L.ncol, tb), tb, 0, r->stream>>>(L, col, done);
-            CPIC_CHECK_LAUNCH();
-        }
-    restrict_kernel<<<grid_blocks(C.ncell, tb), tb, 0, r->stream>>>(L, C, done);
-    CPIC_CHECK_LAUNCH();
-    int st = vcycle_grid(r, S, l + 1, done, nu1, nu2);
-    if (st) return st;
-    prolong_kernel<<<grid_blocks(L.ncell, tb), tb, 0, r->stream>>>(L, C, done);
-    CPIC_CHECK_LAUNCH();
-    for (int it = 0; it < nu2; ++it)
-        for (int col = L.ncol - 1; col >= 0; --col) {
-            smooth_kernel<<<grid_blocks(L.ncell / L.ncol, tb), tb, 0, r->stream>>>(L, col, done);
-            CPIC_CHECK_LAUNCH();
-        }
-    return CPIC_OK;
-}
-
+// Stream-ordered solve; the host reads the device decision after every cycle
+// (cpic_solve_field and the steps of an uncaptured cpic_step).
 int mg_solve(cpic_run* r, double rtol, int max_cycles, bool host_loop, int* cycles, double* res) {
+    (void)host_loop;
     LVSet S = make_set(r);
-    const LV& L0 = S.l[0];
-    double* part = r->red;
-    int* done = reinterpret_cast<int*>(r->red + 2 * RED_BLOCKS + 2);
-    reset_solve_kernel<<<1, 32, 0, r->stream>>>(r->ctr, done);
-    CPIC_CHECK_LAUNCH();
-    int st = launch_rhs(r, r->lev[0].b);
+    int st = enqueue_prologue(r);
     if (st) return st;
-    if (r->singular) {
-        reduce_kernel<<<RED_BLOCKS, 256, 0, r->stream>>>(L0, 1, r->lev[0].Jc, part, nullptr);
-        CPIC_CHECK_LAUNCH();
-        project_kernel<<<grid_blocks(L0.ncell, 256), 256, 0, r->stream>>>(L0, part, RED_BLOCKS, r->sumJ, r->lev[0].Jc);
-        CPIC_CHECK_LAUNCH();
-    }
-    // initial residual (warm start from the previous phi)
-    reduce_kernel<<<RED_BLOCKS, 256, 0, r->stream>>>(L0, 0, nullptr, part, done);
-    CPIC_CHECK_LAUNCH();
-    norm_final_kernel<<<1, 32, 0, r->stream>>>(part, RED_BLOCKS, rtol, 0, r->ctr, done);
-    CPIC_CHECK_LAUNCH();
-    const int nu1 = 2, nu2 = 2;
-    for (int cyc = 0; cyc < max_cycles; ++cyc) {
-        if (host_loop) {
-            int hd = 0;
-            CPIC_CUDA(cudaMemcpyAsync(&hd, done, sizeof(int), cudaMemcpyDeviceToHost, r->stream));
-            CPIC_CUDA(cudaStreamSynchronize(r->stream));
-            if (hd) break;
-        }
-        st = vcycle_grid(r, S, 0, done, nu1, nu2);
+    if (r->cluster_cs) {
+        st = mg_cluster_solve(r, rtol, max_cycles);
         if (st) return st;
-        reduce_kernel<<<RED_BLOCKS, 256, 0, r->stream>>>(L0, 0, nullptr, part, done);
-        CPIC_CHECK_LAUNCH();
-        norm_final_kernel<<<1, 32, 0, r->stream>>>(part, RED_BLOCKS, rtol, 1, r->ctr, done);
-        CPIC_CHECK_LAUNCH();
+        max_cycles = 0;  // the loop ran inside the cluster kernel
+    } else {
+        st = enqueue_residual(r, rtol, max_cycles, 0, false, 0);
+        if (st) return st;
     }
-    if (r->singular) {
-        reduce_kernel<<<RED_BLOCKS, 256, 0, r->stream>>>(L0, 2, r->lev[0].Jc, part, nullptr);
-        CPIC_CHECK_LAUNCH();
-        gauge_kernel<<<grid_blocks(L0.ncell, 256), 256, 0, r->stream>>>(L0, part, RED_BLOCKS, r->sumJ);
-        CPIC_CHECK_LAUNCH();
+    int* done = done_flag(r);
+    for (int cyc = 0; cyc < max_cycles; ++cyc) {
+        int hd = 0;
+        CPIC_CUDA(cudaMemcpyAsync(&hd, done, sizeof(int), cudaMemcpyDeviceToHost, r->stream));
+        CPIC_CUDA(cudaStreamSynchronize(r->stream));
+        if (hd) break;
+        st = enqueue_correction(r, S);
+        if (st) return st;
+        st = enqueue_residual(r, rtol, max_cycles, 1, false, 0);
+        if (st) return st;
     }
-    st = launch_field_energy(r);
+    st = enqueue_epilogue(r);
     if (st) return st;
     if (cycles || res) {
         DevCounters h;
@@ -725,6 +959,64 @@ int mg_solve(cpic_run* r, double rtol, int max_cycles, bool host_loop, int* cycl
         }
     }
     return CPIC_OK;
+}
+
+// The solve as part of a graph being captured on r->stream (capture target `g`): the
+// prologue and first residual are captured in place, the cycles go into the body of a
+// conditional WHILE node the residual kernel drives, the epilogue follows the node.
+int mg_capture_solve(cpic_run* r, cudaGraph_t g, double rtol, int max_cycles) {
+    LVSet S = make_set(r);
+    if (r->cluster_cs) {
+        int st = enqueue_prologue(r);
+        if (st) return st;
+        st = mg_cluster_solve(r, rtol, max_cycles);
+        if (st) return st;
+        return enqueue_epilogue(r);
+    }
+    cudaGraphConditionalHandle h;
+    CPIC_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    int st = enqueue_prologue(r);
+    if (st) return st;
+    st = enqueue_residual(r, rtol, max_cycles, 0, true, h);
+    if (st) return st;
+    // splice the WHILE node after the current capture frontier
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CPIC_CUDA(cudaStreamGetCaptureInfo(r->stream, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+    // the parameter struct has a union member without a default constructor: zeroed storage
+    alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+    memset(npbuf, 0, sizeof(npbuf));
+    cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+    np->type = cudaGraphNodeTypeConditional;
+    np->conditional.handle = h;
+    np->conditional.type = cudaGraphCondTypeWhile;
+    np->conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CPIC_CUDA(cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, np));
+    cudaGraph_t body = np->conditional.phGraph_out[0];
+    // the rest of the outer capture depends on the WHILE node
+    CPIC_CUDA(cudaStreamUpdateCaptureDependencies(r->stream, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    // body: capture on a side stream into the body graph
+    cudaStream_t side;
+    CPIC_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    cudaStream_t saved = r->stream;
+    r->stream = side;
+    st = CPIC_OK;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(side, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        st = enqueue_correction(r, S);
+        if (!st) st = enqueue_residual(r, rtol, max_cycles, 1, true, h);
+        cudaGraph_t out = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(side, &out);
+        if (!st && e2 != cudaSuccess) st = cuda_fail(e2, "cudaStreamEndCapture(body)", __FILE__, __LINE__);
+    } else {
+        st = cuda_fail(e, "cudaStreamBeginCaptureToGraph(body)", __FILE__, __LINE__);
+    }
+    r->stream = saved;
+    cudaStreamDestroy(side);
+    if (st) return st;
+    return enqueue_epilogue(r);
 }
 
 }  // namespace cpic

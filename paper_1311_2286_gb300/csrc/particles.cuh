@@ -10,9 +10,16 @@ namespace pk {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// c mod n for a periodic axis; displacements are almost always within one period, so the
+// integer remainder is only taken for the rare larger ones
 __device__ __forceinline__ int wrapi(int c, int n) {
-    int r = c % n;
-    return r < 0 ? r + n : r;
+    if (c < 0) c += n;
+    else if (c >= n) c -= n;
+    if ((unsigned)c >= (unsigned)n) {
+        c %= n;
+        if (c < 0) c += n;
+    }
+    return c;
 }
 
 __device__ __forceinline__ void renorm(float x, float& f, int& c) {
@@ -42,7 +49,7 @@ struct Tab;
 template <>
 struct Tab<2> {
     // gather K (4) and optionally G (2) at vertex v0 of the cell, offsets t
-    static __device__ __forceinline__ void gather(const PushParams& p, long long v0, const float* t,
+    static __device__ __forceinline__ void gather(const PushParams& p, int v0, const float* t,
                                                   float* kp, float* gp) {
         const float4* K4 = reinterpret_cast<const float4*>(p.K);
         const int nv0 = p.n[0] + 1;
@@ -67,16 +74,16 @@ struct Tab<2> {
 
 template <>
 struct Tab<3> {
-    static __device__ __forceinline__ void gather(const PushParams& p, long long v0, const float* t,
+    static __device__ __forceinline__ void gather(const PushParams& p, int v0, const float* t,
                                                   float* kp, float* gp) {
         const float4* K4 = reinterpret_cast<const float4*>(p.K);
         const float4* G4 = reinterpret_cast<const float4*>(p.G);
-        const long long nv0 = p.n[0] + 1, nv01 = nv0 * (p.n[1] + 1);
+        const int nv0 = p.n[0] + 1, nv01 = nv0 * (p.n[1] + 1);
         float s[3] = {__fsub_rn(1.0f, t[0]), __fsub_rn(1.0f, t[1]), __fsub_rn(1.0f, t[2])};
 #pragma unroll
         for (int o = 0; o < 8; ++o) {
             float w = __fmul_rn(__fmul_rn((o & 1) ? t[0] : s[0], (o & 2) ? t[1] : s[1]), (o & 4) ? t[2] : s[2]);
-            long long v = v0 + ((o & 1) ? 1 : 0) + ((o & 2) ? nv0 : 0) + ((o & 4) ? nv01 : 0);
+            int v = v0 + ((o & 1) ? 1 : 0) + ((o & 2) ? nv0 : 0) + ((o & 4) ? nv01 : 0);
             float4 k0 = __ldg(K4 + 3 * v), k1 = __ldg(K4 + 3 * v + 1), k2 = __ldg(K4 + 3 * v + 2);
             float kv[9] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w, k2.x};
 #pragma unroll
@@ -107,32 +114,37 @@ __device__ __forceinline__ int encode(const int* c) {
     return D == 2 ? (c[0] | (c[1] << 16)) : (c[0] | (c[1] << 10) | (c[2] << 20));
 }
 template <int D>
-__device__ __forceinline__ long long vertex_of(const PushParams& p, const int* c) {
-    long long v = c[D - 1];
+__device__ __forceinline__ int vertex_of(const PushParams& p, const int* c) {
+    int v = c[D - 1];
 #pragma unroll
     for (int a = D - 2; a >= 0; --a) v = v * (p.n[a] + 1) + c[a];
     return v;
 }
 
-// Warp-aggregated fixed-point deposit of one particle per lane (alive lanes only; every
-// lane of the warp must call it). centre: per-axis cell; t: offsets.
+// Warp-aggregated fixed-point deposit of one particle per lane; every lane of the warp must
+// call it (alive lanes deposit). centre: per-axis cell; t: offsets.
+// Aggregation: particles are kept in cell order, so lanes holding the same cell are mostly
+// contiguous. If the whole warp holds one cell, each node weight is summed with one
+// full-warp __reduce_add_sync and one lane issues the 3^D reductions. Otherwise a segmented
+// inclusive scan over runs of equal cells (5 shuffle rounds per node weight) leaves each
+// run's sum in its last lane, which issues the reductions. Every node weight is < 2^24, so
+// a sum over at most 32 lanes fits 32 bits. The integer sums are exact, so the grouping
+// does not change the result.
 template <int D>
 __device__ __forceinline__ void deposit_warp(const PushParams& p, int s, bool alive, const int* c,
                                              const float* t) {
     constexpr int NN = D == 2 ? 9 : 27;
-    unsigned W[3][3];
-#pragma unroll
-    for (int a = 0; a < D; ++a) axis_weights(alive ? t[a] : 0.0f, W[a]);
-    long long key = -1;
+    const int lane = threadIdx.x & 31;
+    int key = -1;
     if (alive) {
         key = c[D - 1];
 #pragma unroll
         for (int a = D - 2; a >= 0; --a) key = key * p.n[a] + c[a];
     }
-    unsigned peers = __match_any_sync(FULL, (unsigned long long)key);
-    int lane = threadIdx.x & 31;
-    bool leader = alive && (__ffs(peers) - 1) == lane;
-    // neighbour indices per axis (wrap or fold)
+    unsigned W[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) axis_weights(alive ? t[a] : 0.0f, W[a]);
+    // node cell indices per axis (wrap or fold)
     int nb[3][3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -144,56 +156,105 @@ __device__ __forceinline__ void deposit_warp(const PushParams& p, int s, bool al
         nb[a][2] = per ? (cp >= n ? cp - n : cp) : (cp >= n ? n - 1 : cp);
     }
     unsigned long long* grid = p.charge + (long long)s * p.ncell;
+    const int rowoff[3] = {p.n[0] * (nb[1][0] + (D == 3 ? p.n[1] * nb[2][0] : 0)),
+                           p.n[0] * (nb[1][1] + (D == 3 ? p.n[1] * nb[2][0] : 0)),
+                           p.n[0] * (nb[1][2] + (D == 3 ? p.n[1] * nb[2][0] : 0))};
+    // 3D: the plane offset of node m2 relative to plane nb[2][0]
+    const int planeoff[3] = {0, D == 3 ? p.n[0] * p.n[1] * (nb[2][1] - nb[2][0]) : 0,
+                             D == 3 ? p.n[0] * p.n[1] * (nb[2][2] - nb[2][0]) : 0};
+    // grouping of lanes by cell: runs of equal keys in lane order
+    const int prev = __shfl_up_sync(FULL, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(FULL, head);
+    const unsigned live = __ballot_sync(FULL, key >= 0);
+    if (!live) return;
+    const int nseg = __popc(heads);
+    // segment of this lane: [seg_lo, next head)
+    const int seg_lo = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    // per-node weights of this lane
+    unsigned q[NN];
     unsigned qsum_off = 0;
-    unsigned qc = 0;
 #pragma unroll
     for (int node = 0; node < NN; ++node) {
-        int m0 = node % 3, m1 = (node / 3) % 3, m2 = node / 9;
-        bool centre = (m0 == 1) && (m1 == 1) && (D == 2 || m2 == 1);
-        unsigned q = 0;
-        if (alive && !centre) {
-            unsigned long long pr = (unsigned long long)W[0][m0] * W[1][m1];
-            unsigned long long q01 = (pr + (1ull << 29)) >> 30;
-            if (D == 3) q01 = (q01 * W[2][m2] + (1ull << 26)) >> 27;
-            q = (unsigned)q01;
-            qsum_off += q;
-        }
+        const int m0 = node % 3, m1 = (node / 3) % 3, m2 = node / 9;
+        const bool centre = (m0 == 1) && (m1 == 1) && (D == 2 || m2 == 1);
         if (centre) continue;
-        unsigned tot = __reduce_add_sync(peers, q);
-        if (leader && tot) {
-            long long idx = nb[0][m0] + (long long)p.n[0] * (nb[1][m1] + (D == 3 ? (long long)p.n[1] * nb[2][m2] : 0));
-            atomicAdd(grid + idx, (unsigned long long)tot);
-        }
+        unsigned long long pr = (unsigned long long)W[0][m0] * W[1][m1];
+        unsigned long long q01 = (pr + (1ull << 29)) >> 30;
+        if (D == 3) q01 = (q01 * W[2][m2] + (1ull << 26)) >> 27;
+        q[node] = alive ? (unsigned)q01 : 0u;
+        qsum_off += q[node];
     }
-    qc = alive ? ((1u << QF) - qsum_off) : 0u;
-    unsigned totc = __reduce_add_sync(peers, qc);
-    if (leader) {
-        long long idx = c[0] + (long long)p.n[0] * (c[1] + (D == 3 ? (long long)p.n[1] * c[2] : 0));
-        atomicAdd(grid + idx, (unsigned long long)totc);
+    {
+        const int cn = NN / 2;
+        q[cn] = alive ? ((1u << QF) - qsum_off) : 0u;
+    }
+    auto node_index = [&](int node) {
+        const int m0 = node % 3, m1 = (node / 3) % 3, m2 = node / 9;
+        return (long long)nb[0][m0] + rowoff[m1] + (D == 3 ? planeoff[m2] : 0);
+    };
+    if (nseg <= 4) {
+        // few cells in the warp (the usual case for cell-sorted particles): one full-warp
+        // reduction per segment and node; the segment's first lane issues the atomics
+        unsigned rest = heads;
+        while (rest) {  // warp-uniform loop over segments
+            const int lo = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const int hi = rest ? __ffs(rest) - 1 : 32;
+            const bool mine = lane >= lo && lane < hi;
+            const bool seg_live = (live >> lo) & 1u;
+            if (!seg_live) continue;  // a run of dead lanes (uniform: lo is warp-uniform)
+#pragma unroll
+            for (int node = 0; node < NN; ++node) {
+                unsigned tot = __reduce_add_sync(FULL, mine ? q[node] : 0u);
+                if (lane == lo && tot) atomicAdd(grid + node_index(node), (unsigned long long)tot);
+            }
+        }
+    } else {
+        // many cells: segmented inclusive scan over each run; its last lane issues
+#pragma unroll
+        for (int node = 0; node < NN; ++node) {
+            unsigned tot = q[node];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                unsigned y = __shfl_up_sync(FULL, tot, d);
+                if (lane - d >= seg_lo) tot += y;
+            }
+            if (tail && key >= 0 && tot) atomicAdd(grid + node_index(node), (unsigned long long)tot);
+        }
     }
 }
 
+// Live-slot ranges of the species in one particle kernel. The virtual index space
+// concatenates the species, each padded to a multiple of 32, so every warp holds one
+// species. Kept in named registers (no indexed local arrays).
 struct SpeciesRanges {
-    long long cnt[CPIC_MAX_SPECIES];
-    long long voff[CPIC_MAX_SPECIES + 1];
+    long long c0, c1, c2, c3;      // slots in use per species
+    long long v1, v2, v3, total;   // start of species 1, 2, 3 and the end
 };
 
 __device__ __forceinline__ SpeciesRanges species_ranges(const PushParams& p) {
     SpeciesRanges r;
-    r.voff[0] = 0;
-    for (int s = 0; s < CPIC_MAX_SPECIES; ++s) {
-        long long c = s < p.nsp ? p.ctr->count[s] : 0;
-        r.cnt[s] = c;
-        r.voff[s + 1] = r.voff[s] + ((c + 31) & ~31ll);
-    }
+    const DevCounters* ctr = p.ctr;
+    r.c0 = ctr->count[0];
+    r.c1 = p.nsp > 1 ? ctr->count[1] : 0;
+    r.c2 = p.nsp > 2 ? ctr->count[2] : 0;
+    r.c3 = p.nsp > 3 ? ctr->count[3] : 0;
+    r.v1 = (r.c0 + 31) & ~31ll;
+    r.v2 = r.v1 + ((r.c1 + 31) & ~31ll);
+    r.v3 = r.v2 + ((r.c2 + 31) & ~31ll);
+    r.total = r.v3 + ((r.c3 + 31) & ~31ll);
     return r;
 }
 
-__device__ __forceinline__ int species_of(const SpeciesRanges& r, int nsp, long long vi) {
-    int s = 0;
-#pragma unroll
-    for (int x = 1; x < CPIC_MAX_SPECIES; ++x)
-        if (x < nsp && vi >= r.voff[x]) s = x;
+// species of virtual index vi, its local index and whether it is an occupied slot
+__device__ __forceinline__ int species_of(const SpeciesRanges& r, int vi, long long& local, bool& occupied) {
+    int s = (vi >= r.v1) + (vi >= r.v2) + (vi >= r.v3);
+    long long start = s == 0 ? 0 : s == 1 ? r.v1 : s == 2 ? r.v2 : r.v3;
+    long long cnt = s == 0 ? r.c0 : s == 1 ? r.c1 : s == 2 ? r.c2 : r.c3;
+    local = vi - start;
+    occupied = vi < r.total && local < cnt;
     return s;
 }
 
@@ -202,7 +263,6 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
-
 
 }  // namespace pk
 }  // namespace cpic

@@ -29,10 +29,17 @@ namespace {
 using namespace pk;
 
 // Per-warp tallies of the current species (the species is warp-uniform, so the flush is
-// taken by whole warps): kinetic-energy products, absorbed per face, non-finite.
+// taken by whole warps): kinetic-energy products (per lane), removed particles per face
+// and non-finite (counted with ballots, so the counts are warp-uniform registers).
 struct Tally {
     long long ke = 0;
     int gone[7] = {0, 0, 0, 0, 0, 0, 0};  // faces 0..5, 6 = non-finite
+    __device__ __forceinline__ void add(int face) {
+        if (__any_sync(FULL, face >= 0)) {
+#pragma unroll
+            for (int f = 0; f < 7; ++f) gone[f] += __popc(__ballot_sync(FULL, face == f));
+        }
+    }
     __device__ __forceinline__ void flush(DevCounters* ctr, int s) {
         long long k = warp_sum_ll(ke);
         bool lane0 = (threadIdx.x & 31) == 0;
@@ -40,15 +47,12 @@ struct Tally {
         long long removed = 0;
 #pragma unroll
         for (int f = 0; f < 7; ++f) {
-            int c = gone[f];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
-            removed += c;
-            if (lane0 && c) {
+            removed += gone[f];
+            if (lane0 && gone[f]) {
                 if (f < 6)
-                    atomicAdd((unsigned long long*)&ctr->absorbed[s][f], (unsigned long long)c);
+                    atomicAdd((unsigned long long*)&ctr->absorbed[s][f], (unsigned long long)gone[f]);
                 else
-                    atomicAdd((unsigned long long*)&ctr->nonfinite, (unsigned long long)c);
+                    atomicAdd((unsigned long long*)&ctr->nonfinite, (unsigned long long)gone[f]);
             }
             gone[f] = 0;
         }
@@ -59,42 +63,69 @@ struct Tally {
 
 // MODE 0: full push + deposit; MODE 1: deposit only; MODE 2: gather + kick only
 template <int D, int MODE>
-__global__ void __launch_bounds__(256) particle_kernel(PushParams p, float kick_coef0, float kick_coef1,
+__global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParams p, float kick_coef0, float kick_coef1,
                                                        float kick_coef2, float kick_coef3) {
     const SpeciesRanges R = species_ranges(p);
-    const long long total = R.voff[p.nsp];
+    const long long total = R.total;
     const int cur = p.ctr->cur;
     int* __restrict__ cellp = p.pb.cell[cur];
-    float* __restrict__ tp = p.pb.t[cur];
-    float* __restrict__ vp = p.pb.v[cur];
     const long long T = p.pb.total;
+    // per-component base pointers: slots are 32-bit offsets from these
+    float* __restrict__ tq[3] = {p.pb.t[cur], p.pb.t[cur] + T, p.pb.t[cur] + (D == 3 ? 2 * T : T)};
+    float* __restrict__ vq[3] = {p.pb.v[cur], p.pb.v[cur] + T, p.pb.v[cur] + 2 * T};
     Tally tally;
     int s_acc = -1;
+    // blocked distribution: each block walks one contiguous chunk of the (cell-sorted)
+    // particles, so consecutive iterations gather nearby vertex records (L1 reuse)
+    const int total32 = (int)total;
+    const int bd = blockDim.x;
+    const int chunk = ((total32 + (int)gridDim.x - 1) / (int)gridDim.x + bd - 1) / bd * bd;
+    const int lo = (int)blockIdx.x * chunk;
+    const int hi = lo + chunk < total32 ? lo + chunk : total32;
 
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += (long long)gridDim.x * blockDim.x) {
-        const long long vi = base + threadIdx.x;
-        const int s = species_of(R, p.nsp, vi);
+    // software pipelining: the particle state of the next iteration is loaded before the
+    // current particle is processed, so its HBM latency overlaps the arithmetic
+    struct Raw {
+        int s, slot, cw;
+        bool active;
+        float t[3], v[3];
+    };
+    auto fetch = [&](int base) {
+        Raw r;
+        const int vi = base + (int)threadIdx.x;
+        long long local;
+        r.s = species_of(R, vi, local, r.active);
+        r.active = r.active && base < hi;
+        r.slot = (int)(p.pb.base[r.s] + local);
+        r.cw = r.active ? cellp[r.slot] : -1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) r.t[a] = 0.0f, r.v[a] = 0.0f;
+        if (r.active) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) r.t[a] = tq[a][r.slot];
+            if (MODE != 1) {
+#pragma unroll
+                for (int al = 0; al < 3; ++al) r.v[al] = vq[al][r.slot];
+            }
+        }
+        return r;
+    };
+    Raw nxt = fetch(lo);
+    for (int base = lo; base < hi; base += bd) {
+        const Raw cur = nxt;
+        nxt = fetch(base + bd);
+        const int s = cur.s;
         if (MODE == 0 && s != s_acc) {  // warp-uniform
             if (s_acc >= 0) tally.flush(p.ctr, s_acc);
             s_acc = s;
         }
-        const long long local = vi - R.voff[s];
-        bool active = vi < total && local < R.cnt[s];
-        const long long slot = p.pb.base[s] + local;
-        int cw = active ? cellp[slot] : -1;
-        active = active && cw >= 0;
+        const int slot = cur.slot;
+        const int cw = cur.cw;
+        bool active = cur.active && cw >= 0;
         int c[3] = {0, 0, 0};
-        float t[3] = {0.f, 0.f, 0.f};
-        float v[3] = {0.f, 0.f, 0.f};
-        if (active) {
-            decode<D>(cw, c);
-#pragma unroll
-            for (int a = 0; a < D; ++a) t[a] = tp[a * T + slot];
-            if (MODE != 1) {
-#pragma unroll
-                for (int al = 0; al < 3; ++al) v[al] = vp[al * T + slot];
-            }
-        }
+        float t[3] = {cur.t[0], cur.t[1], cur.t[2]};
+        float v[3] = {cur.v[0], cur.v[1], cur.v[2]};
+        if (active) decode<D>(cw, c);
         if (MODE == 1) {
             deposit_warp<D>(p, s, active, c, t);
             continue;
@@ -112,17 +143,17 @@ __global__ void __launch_bounds__(256) particle_kernel(PushParams p, float kick_
 #pragma unroll
                     for (int a = 1; a < D; ++a) e = __fmaf_rn(kp[a * D + al], gp[a], e);
                     e = -e;
-                    vp[al * T + slot] = __fmaf_rn(coef, e, v[al]);
+                    vq[al][slot] = __fmaf_rn(coef, e, v[al]);
                 }
             }
             continue;
         }
         // ---- MODE 0: full push
         bool alive = active;
+        int face = -1;
         int cn[3] = {0, 0, 0};
         float tn[3] = {0.f, 0.f, 0.f};
         if (active) {
-            int face = -1;
             const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
             const float dtqm = p.dtqm[s];
 #pragma unroll
@@ -200,15 +231,14 @@ __global__ void __launch_bounds__(256) particle_kernel(PushParams p, float kick_
             // throughput on this part is ~1/64 of FP32, so the product stays in FP32)
             float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
             tally.ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
-#pragma unroll
-            for (int f = 0; f < 7; ++f) tally.gone[f] += (face == f) ? 1 : 0;
             // store
             cellp[slot] = alive ? encode<D>(cn) : -1;
 #pragma unroll
-            for (int a = 0; a < D; ++a) tp[a * T + slot] = tn[a];
+            for (int a = 0; a < D; ++a) tq[a][slot] = tn[a];
 #pragma unroll
-            for (int al = 0; al < 3; ++al) vp[al * T + slot] = v[al];
+            for (int al = 0; al < 3; ++al) vq[al][slot] = v[al];
         }
+        tally.add(face);
         deposit_warp<D>(p, s, alive, cn, tn);
     }
     if (MODE == 0 && s_acc >= 0) tally.flush(p.ctr, s_acc);
@@ -239,13 +269,22 @@ PushParams make_push_params(cpic_run* r) {
     return p;
 }
 
+// one wave of resident blocks over all SMs (the kernel walks its chunk in a loop)
+template <int D, int MODE>
 static int particle_grid(cpic_run* r) {
-    // enough resident blocks for all SMs; grid-stride over the particles
+    static int per_sm[2][3] = {{0, 0, 0}, {0, 0, 0}};  // [D-2][MODE], resident blocks per SM
+    int& occ = per_sm[D - 2][MODE];
+    if (!occ) {
+        int dev = 0, nsm = 0, b = 0;
+        CPIC_CUDA(cudaGetDevice(&dev));
+        CPIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        CPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, particle_kernel<D, MODE>, 256, 0));
+        occ = (b < 1 ? 1 : b) * nsm;
+    }
     long long tot = 0;
     for (int s = 0; s < r->cfg.n_species; ++s) tot += r->pb.capacity[s] + 32;
     long long b = (tot + 255) / 256;
-    int dev_blocks = 152 * 8;
-    if (b > dev_blocks) b = dev_blocks;
+    if (b > occ) b = occ;
     if (b < 1) b = 1;
     return (int)b;
 }
@@ -253,11 +292,15 @@ static int particle_grid(cpic_run* r) {
 template <int MODE>
 static int launch_particles(cpic_run* r, float c0, float c1, float c2, float c3) {
     PushParams p = make_push_params(r);
-    int blocks = particle_grid(r);
-    if (r->D == 2)
+    if (r->D == 2) {
+        int blocks = particle_grid<2, MODE>(r);
+        if (blocks < 0) return blocks;
         particle_kernel<2, MODE><<<blocks, 256, 0, r->stream>>>(p, c0, c1, c2, c3);
-    else
+    } else {
+        int blocks = particle_grid<3, MODE>(r);
+        if (blocks < 0) return blocks;
         particle_kernel<3, MODE><<<blocks, 256, 0, r->stream>>>(p, c0, c1, c2, c3);
+    }
     CPIC_CHECK_LAUNCH();
     return CPIC_OK;
 }

@@ -375,3 +375,66 @@ def test_full_size_cylinder_push_parity(cpic):
         assert np.array_equal(cell1, (i32[0] | (i32[1] << 16))[alive].astype(np.int32))
         assert np.array_equal(t1, t32[:, alive]) and np.array_equal(v1, v32[:, alive])
         assert np.array_equal(charge[s], odep.deposit_fixed(i32[:, alive].astype(np.int64), t32[:, alive], w.n, per))
+
+
+def test_graph_step_matches_stream_step(cpic):
+    """cpic_step as one CUDA graph launch (conditional multigrid loop on the device) gives
+    bit-identical state to the same step launched stream-ordered: same particles (as a set;
+    the order inside a cell after a sort is unspecified), charge, potential and counters."""
+    def run_steps(profiled):
+        w = wl.cylinder(n1=32, n2=64, npart_per_species=50_000, seed=13, inject=True)
+        run = cpic.run_from_workload(w, sort_interval=3)
+        run.initialize()
+        run.profile(profiled)
+        run.step(7)
+        out = ([run.particles(s) for s in range(2)], [run.charge(s) for s in range(2)], run.phi(), run.diag())
+        run.close()
+        return out
+
+    pa, ca, fa, da = run_steps(False)
+    pb, cb, fb, db = run_steps(True)
+    for s in range(2):
+        ra = np.sort(np.rec.fromarrays([pa[s][0], *pa[s][1], *pa[s][2]]))
+        rb = np.sort(np.rec.fromarrays([pb[s][0], *pb[s][1], *pb[s][2]]))
+        assert np.array_equal(ra, rb)
+        assert np.array_equal(ca[s], cb[s])
+    assert np.array_equal(fa, fb)
+    for key in ("step", "n", "absorbed", "injected", "mg_cycles", "W_E", "W_K"):
+        assert da[key] == db[key], key
+    assert da["mg_residual"] <= 1e-10 and da["mg_cycles"] >= 1
+
+
+def test_cluster_and_kernel_solvers_agree(cpic, monkeypatch):
+    """The thread-block-cluster solver (whole solve in one kernel) and the per-level kernel
+    solver give the same potential to the solver tolerance on the cylinder problem, and both
+    match the direct solve to 1e-10."""
+    X = wl.annulus_vertices(128, 256, 1.0, 40.0)
+    bc, bv = [Dr, Dr, P, P], [-5.0, 0.0, 0, 0]
+    g = geometry.build_geometry(X, [False, True])
+    M, bbc = poisson.assemble(g, bc, bv)
+    rng = np.random.default_rng(12)
+    npart = 200_000
+    idx = np.stack([rng.integers(0, 128, npart), rng.integers(0, 256, npart)])
+    t = rng.random((2, npart)).astype(np.float32)
+    cell = (idx[0] | (idx[1] << 16)).astype(np.int32)
+    phis = []
+    for disable in (False, True):
+        if disable:
+            monkeypatch.setenv("CPIC_NO_CLUSTER_SOLVER", "1")
+        else:
+            monkeypatch.delenv("CPIC_NO_CLUSTER_SOLVER", raising=False)
+        cfg = cpic.make_config(2, (128, 256), bc, bv, [PA, PA, PP, PP], 0.1, [(-1.0, 1.0, 1e-3, npart)],
+                               background=0.5)
+        run = cpic.Run(cfg)
+        run.set_map_vertices(X)
+        run.load_particles(0, cell, t, np.zeros((3, npart), np.float32))
+        run.deposit()
+        cycles, res = run.solve_field(rtol=1e-12, max_cycles=100)
+        assert res <= 1e-12 and cycles > 0
+        phis.append(run.phi())
+        C = run.charge(0)
+        run.close()
+    Q = poisson.charge_in_cells(g, [C], [-1e-3], 0.5)
+    ref = poisson.solve(g, M, bbc, Q, bc)
+    for phi in phis:
+        assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) <= 1e-10
