@@ -6,18 +6,22 @@ quadratic B-spline 1/2 (3/2 - |xi|)^2 (Birdsall & Langdon, the reference the pap
 for its assignment functions). b2 is assigned to the 3^D cell centres around the particle
 (density lives at cell centres, Sec. II.B).
 
-Fixed-point spec (constants QK = 12, QF = 24):
+Fixed-point spec (constants QK = 12, QF = 24; per-axis precision B = QF / D, i.e. 12
+bits in 2D and 8 bits in 3D):
   per axis: u = floor(t * 2^QK) (exact), s = 2u + 1 - 2^QK (odd, |s| < 2^QK),
   integer weights for nodes m = -1, 0, +1:
     W[-1] = (2^QK - s)^2,  W[0] = 2 (3 * 2^(2 QK) - s^2),  W[+1] = (2^QK + s)^2,
   which are b2 at the sub-cell centre offset d = s / 2^(QK+1) scaled by 2^(2 QK + 3) and
-  sum to exactly 2^(2 QK + 3).
-  2D node weight: q = (W0[m0] W1[m1] + 2^29) >> 30.
-  3D node weight: q01 = (W0[m0] W1[m1] + 2^29) >> 30, q = (q01 W2[m2] + 2^26) >> 27.
-  The centre node takes 2^QF minus the sum of the other nodes, so each particle deposits
-  exactly 2^QF units (charge conservation is exact, P5).
+  sum to exactly 2^(2 QK + 3);
+  per-axis weights at B bits, outer ones rounded to nearest (halves up), the centre one the
+  remainder:  w[+-1] = (W[+-1] + 2^(h-1)) >> h  with h = 2 QK + 3 - B,
+              w[0] = 2^B - w[-1] - w[+1]   (so the three sum to exactly 2^B);
+  node weight q(m) = prod_a w_a[m_a], exact, and the 3^D node weights of a particle sum to
+  exactly 2^(D B) = 2^QF (charge conservation is exact, P5).
   Node cells outside a non-periodic axis fold onto the boundary cell (charge kept);
   periodic axes wrap.
+The tensor-product form is the b2 assignment of eq. (b2) applied per axis, as the paper's
+multidimensional weights are products of one-dimensional ones (eq. (Wpc)).
 """
 from __future__ import annotations
 
@@ -57,24 +61,27 @@ def axis_weights(t32: np.ndarray):
     return [(one - s) ** 2, 2 * (3 * one * one - s * s), (one + s) ** 2]
 
 
+def axis_weights_fixed(t32: np.ndarray, D: int):
+    """Per-axis weights w[m+1] at B = QF / D bits (int64 arrays), summing to 2^B."""
+    B = QF // D
+    h = 2 * QK + 3 - B
+    W = axis_weights(t32)
+    wm = (W[0] + (1 << (h - 1))) >> h
+    wp = (W[2] + (1 << (h - 1))) >> h
+    return [wm, (1 << B) - wm - wp, wp]
+
+
 def node_weights(t32: np.ndarray):
     """Fixed-point node weights for particles with offsets t32 (D, n).
     Returns dict offset tuple (m0, m1[, m2]) -> int64 array (n,)."""
     D = t32.shape[0]
-    W = [axis_weights(t32[a]) for a in range(D)]
+    w = [axis_weights_fixed(t32[a], D) for a in range(D)]
     out = {}
     for m in itertools.product((-1, 0, 1), repeat=D):
-        if all(x == 0 for x in m):
-            continue
-        p = W[0][m[0] + 1] * W[1][m[1] + 1]
-        q = (p + (1 << 29)) >> 30
-        if D == 3:
-            q = (q * W[2][m[2] + 1] + (1 << 26)) >> 27
+        q = np.ones(t32.shape[1], dtype=np.int64)
+        for a in range(D):
+            q = q * w[a][m[a] + 1]
         out[m] = q
-    centre = np.full(t32.shape[1], 1 << QF, dtype=np.int64)
-    for q in out.values():
-        centre -= q
-    out[(0,) * D] = centre
     return out
 
 

@@ -128,8 +128,38 @@ def test_node_weights_sum_exactly_and_approximate_b2(D):
         for a in range(D):
             exact = exact * dep.b2(d[a] - m[a])
         assert np.all(qm >= 0)
-        # quantisation of the offset to 2^-12 moves b2 by at most ~2^-12 per axis
-        assert np.max(np.abs(qm / 2.0 ** dep.QF - exact)) < D * 2.0 ** -11
+        # per axis: offset quantised to 2^-12 (b2 moves by < 2^-12) and the weight rounded
+        # to 2^-B (error <= 2^-(B+1)), B = 12 in 2D and 8 in 3D
+        B = dep.QF // D
+        axis_err = 2.0 ** -12 + 2.0 ** -(B + 1)
+        assert np.max(np.abs(qm / 2.0 ** dep.QF - exact)) < D * axis_err
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_axis_weights_fixed_are_rounded_b2_and_sum_exactly(D):
+    """The B-bit per-axis weights are the nearest multiples of 2^-B of the exact b2 values
+    of the quantised offset (outer nodes), the centre takes the remainder, and each node
+    weight is the exact product (rational arithmetic)."""
+    rng = np.random.default_rng(40 + D)
+    t = np.concatenate([np.array([0.0, 0.5, np.nextafter(np.float32(1), np.float32(0))], dtype=np.float32),
+                        rng.random(200).astype(np.float32)])
+    B = dep.QF // D
+    w = dep.axis_weights_fixed(t, D)
+    K = dep.QK
+    for p in range(t.size):
+        u = math.floor(Fraction(float(t[p])) * 2 ** K)
+        d = Fraction(2 * u + 1 - 2 ** K, 2 ** (K + 1))
+        for m in (-1, 1):
+            exact = (Fraction(1, 2) * (Fraction(3, 2) - abs(d - m)) ** 2) * 2 ** B
+            assert abs(Fraction(int(w[m + 1][p])) - exact) <= Fraction(1, 2)
+        assert int(w[0][p]) + int(w[1][p]) + int(w[2][p]) == 2 ** B
+    tt = np.stack([t] * D)
+    q = dep.node_weights(tt)
+    for m, qm in q.items():
+        prod = np.ones(t.size, dtype=np.int64)
+        for a in range(D):
+            prod = prod * w[m[a] + 1]
+        assert np.array_equal(qm, prod)
 
 
 @pytest.mark.parametrize("D", [2, 3])
