@@ -174,6 +174,7 @@ void plan(cpic_run* r, Planner& P) {
     r->G32 = P.take<float>((size_t)r->nvert * (D == 2 ? 2 : 4));
     r->rhs_bc = P.take<double>(r->ncell);
     r->charge = P.take<unsigned long long>((size_t)c.n_species * r->ncell);
+    r->charge_h = P.take<unsigned long long>((size_t)c.n_species * r->ncell_h);
     long long total = 0;
     for (int s = 0; s < c.n_species; ++s) {
         r->pb.base[s] = total;
@@ -213,11 +214,13 @@ void init_geometry_sizes(cpic_run* r, const cpic_config* cfg) {
     r->D = cfg->dim;
     r->ncell = 1;
     r->nvert = 1;
+    r->ncell_h = 1;
     for (int a = 0; a < 3; ++a) {
         r->n[a] = a < r->D ? cfg->n[a] : 1;
         r->nvert_axis[a] = a < r->D ? cfg->n[a] + 1 : 1;
         r->ncell *= r->n[a];
         r->nvert *= r->nvert_axis[a];
+        if (a < r->D) r->ncell_h *= r->n[a] + 2;
     }
     if (r->cfg.mg_max_cycles <= 0) r->cfg.mg_max_cycles = 30;
     if (!(r->cfg.mg_rtol > 0.0)) r->cfg.mg_rtol = 1e-10;
@@ -386,6 +389,8 @@ int enqueue_step(cpic_run* r, bool sort) {
     if (st) return st;
     st = launch_inject(r);
     if (st) return st;
+    st = launch_fold(r);
+    if (st) return st;
     if (sort) {
         st = launch_sort(r);
         if (st) return st;
@@ -449,7 +454,10 @@ int step_once(cpic_run* r) {
     if (st) return st;
     st = phase(r, CPIC_PHASE_PUSH, [&] { return launch_push(r); });
     if (st) return st;
-    st = phase(r, CPIC_PHASE_INJECT, [&] { return launch_inject(r); });
+    st = phase(r, CPIC_PHASE_INJECT, [&] {
+        int q = launch_inject(r);
+        return q ? q : launch_fold(r);
+    });
     if (st) return st;
     if (r->cfg.sort_interval > 0 && ++r->steps_since_sort >= r->cfg.sort_interval) {
         st = phase(r, CPIC_PHASE_SORT, [&] { return launch_sort(r); });
@@ -554,6 +562,8 @@ int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* s
     plan(r, P);
     cudaError_t e = cudaMemsetAsync(r->ctr, 0, sizeof(DevCounters), r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->charge, 0, sizeof(unsigned long long) * r->ncell * cfg->n_species, r->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(r->charge_h, 0, sizeof(unsigned long long) * r->ncell_h * cfg->n_species, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->pb.cell[0], 0xff, sizeof(int) * r->pb.total, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->pb.cell[1], 0xff, sizeof(int) * r->pb.total, r->stream);
     if (e != cudaSuccess) {
@@ -717,6 +727,7 @@ int cpic_initialize(cpic_run* r) {
     CHECK_RUN(r);
     CHECK_MAP(r);
     int st = launch_deposit(r);
+    if (!st) st = launch_fold(r);
     if (st) return st;
     st = mg_solve(r, r->cfg.mg_rtol, r->cfg.mg_max_cycles, false, nullptr, nullptr);
     if (st) return st;
@@ -747,13 +758,15 @@ int cpic_vertex_field(cpic_run* r) {
 int cpic_push(cpic_run* r) {
     CHECK_RUN(r);
     CHECK_MAP(r);
-    return launch_push(r);
+    int st = launch_push(r);
+    return st ? st : launch_fold(r);
 }
 
 int cpic_deposit(cpic_run* r) {
     CHECK_RUN(r);
     CHECK_MAP(r);
-    return launch_deposit(r);
+    int st = launch_deposit(r);
+    return st ? st : launch_fold(r);
 }
 
 int cpic_kick(cpic_run* r, double fraction) {
@@ -765,7 +778,8 @@ int cpic_kick(cpic_run* r, double fraction) {
 int cpic_inject(cpic_run* r) {
     CHECK_RUN(r);
     CHECK_MAP(r);
-    return launch_inject(r);
+    int st = launch_inject(r);
+    return st ? st : launch_fold(r);
 }
 
 int cpic_sort(cpic_run* r) {

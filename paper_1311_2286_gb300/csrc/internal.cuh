@@ -78,8 +78,10 @@ struct PushParams {
     const float* K;                // vertex k table: 2D float4 [K00 K01 K10 K11]; 3D 3 x float4 (9 used)
     const float* G;                // vertex G table: 2D float2; 3D float4 (3 used)
     ParticleBuffers pb;
-    unsigned long long* charge;    // [nsp][ncell]
-    long long ncell;
+    unsigned long long* charge;    // padded deposit grid [nsp][ncell_h]
+    long long ncell_h;             // cells of the padded grid: prod (n_a + 2)
+    int hs1, hs2;                  // padded strides of axes 1 and 2
+    int origin;                    // padded index of cell (0, 0, 0)
     DevCounters* ctr;
 };
 
@@ -131,7 +133,9 @@ struct cpic_run {
     float* K32;       // vertex k table (padded records)
     float* G32;       // vertex G table (padded records)
     double* rhs_bc;   // Dirichlet part of the right-hand side (finest)
-    unsigned long long* charge;  // [nsp][ncell]
+    unsigned long long* charge;  // [nsp][ncell] folded charge counts (what the field solve reads)
+    unsigned long long* charge_h;  // [nsp][ncell_h] deposit grid with one halo layer per side
+    long long ncell_h;
     cpic::ParticleBuffers pb;
     cpic::DevCounters* ctr;      // device
     int cur_host;                // host mirror of ctr->cur (every sort flips both)
@@ -179,6 +183,9 @@ int launch_push(cpic_run* r);
 int launch_deposit(cpic_run* r);
 int launch_kick(cpic_run* r, double fraction);
 int launch_finalize_step(cpic_run* r);
+int launch_fold(cpic_run* r);
+PushParams make_push_params(cpic_run* r);
+int launch_push2d(cpic_run* r, const PushParams& p);
 // inject.cu
 int launch_inject(cpic_run* r);
 // sort.cu

@@ -34,13 +34,20 @@ __device__ __forceinline__ void renorm(float x, float& f, int& c) {
     c = (int)cf;
 }
 
-// per-axis integer b2 weights (spec Q), W[m+1] for m = -1, 0, +1
-__device__ __forceinline__ void axis_weights(float t, unsigned W[3]) {
-    int u = (int)floorf(__fmul_rn(t, 4096.0f));
-    int s = 2 * u + 1 - 4096;
-    W[0] = (unsigned)((4096 - s) * (4096 - s));
-    W[1] = (unsigned)(2 * (3 * 4096 * 4096 - s * s));
-    W[2] = (unsigned)((4096 + s) * (4096 + s));
+// Per-axis fixed-point b2 weights (spec Q), w[m+1] for m = -1, 0, +1, at B = 24 / D bits:
+// the offset is quantised to u = floor(t 2^12), the exact integer b2 values of the sub-cell
+// centre (scaled by 2^27) are (2^12 -+ s)^2 for the outer nodes, s = 2u + 1 - 2^12; those
+// are rounded to B bits and the centre takes the remainder, so the three sum to 2^B.
+template <int D>
+__device__ __forceinline__ void axis_weights(float t, int w[3]) {
+    constexpr int B = D == 2 ? 12 : 8;
+    constexpr int H = 2 * QK + 3 - B;
+    const int u = (int)floorf(__fmul_rn(t, 4096.0f));
+    const int s = 2 * u + 1 - 4096;
+    const int lo = 4096 - s, hi = 4096 + s;
+    w[0] = (lo * lo + (1 << (H - 1))) >> H;
+    w[2] = (hi * hi + (1 << (H - 1))) >> H;
+    w[1] = (1 << B) - w[0] - w[2];
 }
 
 template <int D>
@@ -121,107 +128,60 @@ __device__ __forceinline__ int vertex_of(const PushParams& p, const int* c) {
     return v;
 }
 
-// Warp-aggregated fixed-point deposit of one particle per lane; every lane of the warp must
-// call it (alive lanes deposit). centre: per-axis cell; t: offsets.
-// Aggregation: particles are kept in cell order, so lanes holding the same cell are mostly
-// contiguous. If the whole warp holds one cell, each node weight is summed with one
-// full-warp __reduce_add_sync and one lane issues the 3^D reductions. Otherwise a segmented
-// inclusive scan over runs of equal cells (5 shuffle rounds per node weight) leaves each
-// run's sum in its last lane, which issues the reductions. Every node weight is < 2^24, so
-// a sum over at most 32 lanes fits 32 bits. The integer sums are exact, so the grouping
-// does not change the result.
+// Warp-aggregated fixed-point deposit of one particle per lane into the padded grid (one
+// halo layer per side, folded into the cell grid afterwards, so node addresses are the
+// cell's address plus fixed offsets and need no wrap or fold). Every lane of the warp must
+// call it (alive lanes deposit). c: per-axis cell; t: offsets.
+// The node weights are exact integer products of the per-axis weights. Particles are kept
+// in cell order, so many lanes of a warp share one cell: the largest group of lanes with a
+// common cell (__match_any_sync) is summed with full-warp __reduce_add_sync (a node weight
+// is at most 2^24, so 32 of them fit 32 bits) and its leader deposits the sums; the other
+// lanes deposit their own weights. Integer sums are exact, so the grouping does not change
+// the result.
 template <int D>
 __device__ __forceinline__ void deposit_warp(const PushParams& p, int s, bool alive, const int* c,
                                              const float* t) {
     constexpr int NN = D == 2 ? 9 : 27;
     const int lane = threadIdx.x & 31;
-    int key = -1;
-    if (alive) {
-        key = c[D - 1];
-#pragma unroll
-        for (int a = D - 2; a >= 0; --a) key = key * p.n[a] + c[a];
-    }
-    unsigned W[3][3];
-#pragma unroll
-    for (int a = 0; a < D; ++a) axis_weights(alive ? t[a] : 0.0f, W[a]);
-    // node cell indices per axis (wrap or fold)
-    int nb[3][3];
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        int n = p.n[a];
-        bool per = p.pbc[2 * a] == CPIC_PBC_PERIODIC;
-        int cm = c[a] - 1, cp = c[a] + 1;
-        nb[a][0] = per ? (cm < 0 ? cm + n : cm) : (cm < 0 ? 0 : cm);
-        nb[a][1] = c[a];
-        nb[a][2] = per ? (cp >= n ? cp - n : cp) : (cp >= n ? n - 1 : cp);
-    }
-    unsigned long long* grid = p.charge + (long long)s * p.ncell;
-    const int rowoff[3] = {p.n[0] * (nb[1][0] + (D == 3 ? p.n[1] * nb[2][0] : 0)),
-                           p.n[0] * (nb[1][1] + (D == 3 ? p.n[1] * nb[2][0] : 0)),
-                           p.n[0] * (nb[1][2] + (D == 3 ? p.n[1] * nb[2][0] : 0))};
-    // 3D: the plane offset of node m2 relative to plane nb[2][0]
-    const int planeoff[3] = {0, D == 3 ? p.n[0] * p.n[1] * (nb[2][1] - nb[2][0]) : 0,
-                             D == 3 ? p.n[0] * p.n[1] * (nb[2][2] - nb[2][0]) : 0};
-    // grouping of lanes by cell: runs of equal keys in lane order
-    const int prev = __shfl_up_sync(FULL, key, 1);
-    const bool head = lane == 0 || prev != key;
-    const unsigned heads = __ballot_sync(FULL, head);
-    const unsigned live = __ballot_sync(FULL, key >= 0);
+    const unsigned live = __ballot_sync(FULL, alive);
     if (!live) return;
-    const int nseg = __popc(heads);
-    // segment of this lane: [seg_lo, next head)
-    const int seg_lo = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-    // per-node weights of this lane
+    int w[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) axis_weights<D>(alive ? t[a] : 0.0f, w[a]);
+    if (!alive) w[0][0] = w[0][1] = w[0][2] = 0;  // dead lanes carry zero weight
     unsigned q[NN];
-    unsigned qsum_off = 0;
 #pragma unroll
     for (int node = 0; node < NN; ++node) {
         const int m0 = node % 3, m1 = (node / 3) % 3, m2 = node / 9;
-        const bool centre = (m0 == 1) && (m1 == 1) && (D == 2 || m2 == 1);
-        if (centre) continue;
-        unsigned long long pr = (unsigned long long)W[0][m0] * W[1][m1];
-        unsigned long long q01 = (pr + (1ull << 29)) >> 30;
-        if (D == 3) q01 = (q01 * W[2][m2] + (1ull << 26)) >> 27;
-        q[node] = alive ? (unsigned)q01 : 0u;
-        qsum_off += q[node];
+        unsigned v = (unsigned)(w[0][m0] * w[1][m1]);
+        if (D == 3) v *= (unsigned)w[2][m2];
+        q[node] = v;
     }
-    {
-        const int cn = NN / 2;
-        q[cn] = alive ? ((1u << QF) - qsum_off) : 0u;
-    }
-    auto node_index = [&](int node) {
-        const int m0 = node % 3, m1 = (node / 3) % 3, m2 = node / 9;
-        return (long long)nb[0][m0] + rowoff[m1] + (D == 3 ? planeoff[m2] : 0);
-    };
-    if (nseg <= 4) {
-        // few cells in the warp (the usual case for cell-sorted particles): one full-warp
-        // reduction per segment and node; the segment's first lane issues the atomics
-        unsigned rest = heads;
-        while (rest) {  // warp-uniform loop over segments
-            const int lo = __ffs(rest) - 1;
-            rest &= rest - 1;
-            const int hi = rest ? __ffs(rest) - 1 : 32;
-            const bool mine = lane >= lo && lane < hi;
-            const bool seg_live = (live >> lo) & 1u;
-            if (!seg_live) continue;  // a run of dead lanes (uniform: lo is warp-uniform)
-#pragma unroll
-            for (int node = 0; node < NN; ++node) {
-                unsigned tot = __reduce_add_sync(FULL, mine ? q[node] : 0u);
-                if (lane == lo && tot) atomicAdd(grid + node_index(node), (unsigned long long)tot);
-            }
-        }
-    } else {
-        // many cells: segmented inclusive scan over each run; its last lane issues
+    // padded offset of this lane's cell; dead lanes take the first live lane's cell
+    int off = c[0] + c[1] * p.hs1 + (D == 3 ? c[2] * p.hs2 : 0);
+    const int off_first = __shfl_sync(FULL, off, __ffs(live) - 1);
+    if (!alive) off = off_first;
+    const unsigned peers = __match_any_sync(FULL, off);
+    const unsigned score = ((unsigned)__popc(peers) << 5) | (31u - (unsigned)(__ffs(peers) - 1));
+    const unsigned best = __reduce_max_sync(FULL, score);
+    bool issue = alive;  // lanes that issue reductions: the group leader and the others
+    if ((best >> 5) > 1) {  // warp-uniform: some cell holds two or more lanes
+        const int leader = 31 - (int)(best & 31u);
+        const bool mine = off == __shfl_sync(FULL, off, leader);
 #pragma unroll
         for (int node = 0; node < NN; ++node) {
-            unsigned tot = q[node];
+            const unsigned tot = __reduce_add_sync(FULL, mine ? q[node] : 0u);
+            q[node] = mine ? tot : q[node];
+        }
+        issue = mine ? lane == leader : alive;
+    }
+    if (issue) {
+        unsigned long long* g = p.charge + (long long)s * p.ncell_h + p.origin + off;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                unsigned y = __shfl_up_sync(FULL, tot, d);
-                if (lane - d >= seg_lo) tot += y;
-            }
-            if (tail && key >= 0 && tot) atomicAdd(grid + node_index(node), (unsigned long long)tot);
+        for (int node = 0; node < NN; ++node) {
+            const int m0 = node % 3, m1 = (node / 3) % 3, m2 = node / 9;
+            const int d = (m0 - 1) + (m1 - 1) * p.hs1 + (D == 3 ? (m2 - 1) * p.hs2 : 0);
+            if (q[node]) atomicAdd(g + d, (unsigned long long)q[node]);
         }
     }
 }

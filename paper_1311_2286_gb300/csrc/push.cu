@@ -244,6 +244,52 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
     if (MODE == 0 && s_acc >= 0) tally.flush(p.ctr, s_acc);
 }
 
+// Folds the padded deposit grid into the cell grid the field solve reads: every cell takes
+// its own padded entry plus, on each axis where it is an edge cell, the halo entry that maps
+// onto it (periodic axes wrap: halo -1 -> n-1, halo n -> 0; other axes fold the halo onto
+// the adjacent boundary cell, so charge deposited outside is kept). Gather form: each cell
+// is written by one thread, no atomics.
+struct FoldParams {
+    int D, n[3], per[3], hs1, hs2, nsp;
+    long long ncell, ncell_h;
+    const unsigned long long* src;
+    unsigned long long* dst;
+};
+
+__global__ void fold_kernel(FoldParams f) {
+    const long long total = f.ncell * f.nsp;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(x / f.ncell);
+        const long long c = x - (long long)s * f.ncell;
+        int ci[3] = {(int)(c % f.n[0]), (int)((c / f.n[0]) % f.n[1]), (int)(c / ((long long)f.n[0] * f.n[1]))};
+        // padded source coordinates per axis: the cell itself and at most one halo
+        int src[3][2], ns[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            src[a][0] = ci[a] + 1;
+            ns[a] = 1;
+            if (a < f.D) {
+                const int n = f.n[a];
+                const int lo = f.per[a] ? n - 1 : 0;   // cell receiving halo -1
+                const int hi = f.per[a] ? 0 : n - 1;   // cell receiving halo n
+                if (ci[a] == lo) src[a][ns[a]++] = 0;
+                if (ci[a] == hi) src[a][ns[a]++] = n + 1;
+            }
+        }
+        const unsigned long long* g = f.src + (long long)s * f.ncell_h;
+        unsigned long long acc = 0;
+        for (int k = 0; k < (f.D == 3 ? ns[2] : 1); ++k)
+            for (int j = 0; j < ns[1]; ++j)
+                for (int i = 0; i < ns[0]; ++i) {
+                    long long idx = src[0][i] + (long long)src[1][j] * f.hs1;
+                    if (f.D == 3) idx += (long long)src[2][k] * f.hs2;
+                    acc += g[idx];
+                }
+        f.dst[x] = acc;
+    }
+}
+
 __global__ void finalize_step_kernel(DevCounters* ctr) {
     if (threadIdx.x == 0 && blockIdx.x == 0) ctr->step += 1;
 }
@@ -263,8 +309,11 @@ PushParams make_push_params(cpic_run* r) {
     p.K = r->K32;
     p.G = r->G32;
     p.pb = r->pb;
-    p.charge = r->charge;
-    p.ncell = r->ncell;
+    p.charge = r->charge_h;
+    p.ncell_h = r->ncell_h;
+    p.hs1 = r->n[0] + 2;
+    p.hs2 = r->D == 3 ? (r->n[0] + 2) * (r->n[1] + 2) : 0;
+    p.origin = 1 + p.hs1 + p.hs2;
     p.ctr = r->ctr;
     return p;
 }
@@ -306,15 +355,15 @@ static int launch_particles(cpic_run* r, float c0, float c1, float c2, float c3)
 }
 
 int launch_push(cpic_run* r) {
-    CPIC_CUDA(cudaMemsetAsync(r->charge, 0, sizeof(unsigned long long) * r->ncell * r->cfg.n_species, r->stream));
+    CPIC_CUDA(cudaMemsetAsync(r->charge_h, 0, sizeof(unsigned long long) * r->ncell_h * r->cfg.n_species, r->stream));
     CPIC_CUDA(cudaMemsetAsync(&r->ctr->ke_fp[0], 0, sizeof(long long) * CPIC_MAX_SPECIES, r->stream));
-    int st = launch_particles<0>(r, 0, 0, 0, 0);
+    int st = r->D == 2 ? launch_push2d(r, make_push_params(r)) : launch_particles<0>(r, 0, 0, 0, 0);
     if (st) return st;
     return launch_finalize_step(r);
 }
 
 int launch_deposit(cpic_run* r) {
-    CPIC_CUDA(cudaMemsetAsync(r->charge, 0, sizeof(unsigned long long) * r->ncell * r->cfg.n_species, r->stream));
+    CPIC_CUDA(cudaMemsetAsync(r->charge_h, 0, sizeof(unsigned long long) * r->ncell_h * r->cfg.n_species, r->stream));
     return launch_particles<1>(r, 0, 0, 0, 0);
 }
 
@@ -322,6 +371,27 @@ int launch_kick(cpic_run* r, double fraction) {
     float c[4] = {0, 0, 0, 0};
     for (int s = 0; s < r->cfg.n_species; ++s) c[s] = (float)(fraction * r->cfg.dt * r->cfg.q[s] / r->cfg.m[s]);
     return launch_particles<2>(r, c[0], c[1], c[2], c[3]);
+}
+
+int launch_fold(cpic_run* r) {
+    FoldParams f;
+    f.D = r->D;
+    for (int a = 0; a < 3; ++a) {
+        f.n[a] = r->n[a];
+        f.per[a] = a < r->D && r->cfg.particle_bc[2 * a] == CPIC_PBC_PERIODIC;
+    }
+    f.hs1 = r->n[0] + 2;
+    f.hs2 = (r->n[0] + 2) * (r->n[1] + 2);
+    f.nsp = r->cfg.n_species;
+    f.ncell = r->ncell;
+    f.ncell_h = r->ncell_h;
+    f.src = r->charge_h;
+    f.dst = r->charge;
+    long long b = (r->ncell * f.nsp + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    fold_kernel<<<(int)b, 256, 0, r->stream>>>(f);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
 }
 
 int launch_finalize_step(cpic_run* r) {

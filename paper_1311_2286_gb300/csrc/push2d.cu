@@ -1,0 +1,403 @@
+// Rows a2-a6 for two-dimensional runs: the fused hybrid-mover kernel (Sec. II.B.4) with its
+// grid coupling, specialised for the hot path.
+//
+// Same arithmetic as the generic particle kernel (push.cu), which stays in use for three
+// dimensions and for the deposit-only and kick-only passes; this one is organised for
+// instruction economy:
+//   - each block walks chunks of one species (a species' particles are split into chunks
+//     of equal size, a multiple of the block), so q/m and the tallies are block-uniform;
+//   - the boundary kind of each axis is a template parameter (periodic wrap, or clamp of
+//     the predictor and absorption at the corrector);
+//   - 32-bit slot indices, branch-free handling of empty lanes (they gather at vertex 0 and
+//     store nothing) and of non-finite positions (the particle keeps its old cell/offset);
+//   - absorbed counts and the kinetic-energy tally stay in registers until the chunk ends;
+//   - the particle state of the next iteration is loaded before the current one is
+//     processed, so its HBM latency overlaps the arithmetic.
+//
+// Per particle: b1 gather of G and k at xi^n (eqs. (vvp), (Wvp), (b1)); E = -k^T G and the
+// leapfrog kick (eq. (step1)); predictor xi' = xi^n + dt/2 k(xi^n) v (eq. (step2)); k
+// re-gathered at xi' (eq. (step3)); corrector xi^{n+1} = xi^n + dt k(xi') v (eq. (step4));
+// boundaries (Sec. II.B.4); b2 deposit in 64-bit fixed point (eqs. (pg), (Wpc), (b2)).
+#include "particles.cuh"
+
+namespace cpic {
+namespace {
+
+using namespace pk;
+
+constexpr int P2_THREADS = 256;
+
+// predictor component on axis a: renormalise; periodic axes wrap, others clamp to the
+// domain (offset 0 below, 1 above)
+template <bool PER>
+__device__ __forceinline__ void predict_axis(float x, int c, int n, int& cp, float& tp) {
+    int dc;
+    renorm(x, tp, dc);
+    int ci = c + dc;
+    if (PER) {
+        ci = wrapi(ci, n);
+    } else {
+        if (ci < 0) {
+            ci = 0;
+            tp = 0.0f;
+        }
+        if (ci >= n) {
+            ci = n - 1;
+            tp = 1.0f;
+        }
+    }
+    cp = ci;
+}
+
+// Shared-memory charge tile of one chunk: rows [r0, r0 + R) of the padded grid's layout
+// (W = n0 + 2 columns, column 0 and W - 1 the halo), 64-bit counts kept as 32-bit low words
+// with carries into high words (shared 32-bit atomics).
+constexpr int TILE_CELLS = 2048;  // 16 KB of shared memory per block
+
+struct Tile {
+    unsigned* lo;
+    unsigned* hi;
+    int r0, R, W;
+    bool on;
+};
+
+__device__ __forceinline__ void tile_add(const Tile& tl, int i, unsigned v) {
+    const unsigned old = atomicAdd(tl.lo + i, v);
+    if (old + v < old) atomicAdd(tl.hi + i, 1u);
+}
+
+// Deposit of one particle per lane into the chunk's tile; lanes whose 3x3 stencil leaves the
+// tile rows deposit straight into the padded global grid. Lanes sharing a cell are combined
+// first (largest group, __reduce_add_sync) so that the tile's atomics rarely collide.
+__device__ __forceinline__ void deposit_tile(const PushParams& p, const Tile& tl, int s, bool alive,
+                                             const int* c, const float* t) {
+    const int lane = threadIdx.x & 31;
+    const int rr = c[1] - tl.r0;  // tile row of the cell
+    const bool in = alive && rr >= 1 && rr + 1 < tl.R;
+    const bool out = alive && !in;
+    const unsigned live = __ballot_sync(FULL, in);
+    if (__any_sync(FULL, out)) deposit_warp<2>(p, s, out, c, t);
+    if (!live) return;
+    int w[2][3];
+    axis_weights<2>(in ? t[0] : 0.0f, w[0]);
+    axis_weights<2>(in ? t[1] : 0.0f, w[1]);
+    if (!in) w[0][0] = w[0][1] = w[0][2] = 0;
+    unsigned q[9];
+#pragma unroll
+    for (int node = 0; node < 9; ++node) q[node] = (unsigned)(w[0][node % 3] * w[1][node / 3]);
+    int off = rr * tl.W + c[0] + 1;
+    const int off_first = __shfl_sync(FULL, off, __ffs(live) - 1);
+    if (!in) off = off_first;
+    const unsigned peers = __match_any_sync(FULL, off);
+    const unsigned score = ((unsigned)__popc(peers) << 5) | (31u - (unsigned)(__ffs(peers) - 1));
+    const unsigned best = __reduce_max_sync(FULL, score);
+    bool issue = in;
+    if ((best >> 5) > 1) {
+        const int leader = 31 - (int)(best & 31u);
+        const bool mine = off == __shfl_sync(FULL, off, leader);
+#pragma unroll
+        for (int node = 0; node < 9; ++node) {
+            const unsigned tot = __reduce_add_sync(FULL, mine ? q[node] : 0u);
+            q[node] = mine ? tot : q[node];
+        }
+        issue = mine ? lane == leader : in;
+    }
+    if (issue) {
+#pragma unroll
+        for (int node = 0; node < 9; ++node) {
+            const int d = (node % 3 - 1) + (node / 3 - 1) * tl.W;
+            if (q[node]) tile_add(tl, off + d, q[node]);
+        }
+    }
+}
+
+template <bool PER0, bool PER1>
+__global__ void __launch_bounds__(P2_THREADS, 4) push2d_kernel(PushParams p) {
+    __shared__ unsigned tile_lo[TILE_CELLS], tile_hi[TILE_CELLS];
+    __shared__ int red_min[P2_THREADS / 32], red_max[P2_THREADS / 32];
+    const DevCounters* ctr = p.ctr;
+    const int cur = ctr->cur;
+    const int nsp = p.nsp;
+    int cnt[CPIC_MAX_SPECIES];
+    int total = 0;
+#pragma unroll
+    for (int s = 0; s < CPIC_MAX_SPECIES; ++s) {
+        cnt[s] = s < nsp ? (int)ctr->count[s] : 0;
+        total += cnt[s];
+    }
+    if (total == 0) return;
+    // chunk size: a multiple of the block, about one chunk per block
+    const int C = ((total + (int)gridDim.x - 1) / (int)gridDim.x + P2_THREADS - 1) / P2_THREADS * P2_THREADS;
+    const int n0 = p.n[0], n1 = p.n[1], nv0 = n0 + 1;
+    const float4* __restrict__ K4 = reinterpret_cast<const float4*>(p.K);
+    const float2* __restrict__ G2 = reinterpret_cast<const float2*>(p.G);
+    const long long T = p.pb.total;
+    const float hdt = p.hdt, dt = p.dt;
+
+    for (int ch = blockIdx.x;; ch += gridDim.x) {
+        // species and range of chunk ch (block-uniform)
+        int s = 0, local = ch;
+        while (s < nsp) {
+            const int nch = (cnt[s] + C - 1) / C;
+            if (local < nch) break;
+            local -= nch;
+            ++s;
+        }
+        if (s >= nsp) break;
+        const int lo = local * C;
+        const int hi = min(lo + C, cnt[s]);
+        const long long b0 = p.pb.base[s];
+        int* __restrict__ cellp = p.pb.cell[cur] + b0;
+        float* __restrict__ t0p = p.pb.t[cur] + b0;
+        float* __restrict__ t1p = t0p + T;
+        float* __restrict__ v0p = p.pb.v[cur] + b0;
+        float* __restrict__ v1p = v0p + T;
+        float* __restrict__ v2p = v1p + T;
+        const float dtqm = p.dtqm[s];
+
+        // tile rows: the rows of the chunk's particles (sampled; the chunk is in cell order
+        // since the last sort) with two rows of margin for motion and the stencil
+        Tile tl;
+        tl.lo = tile_lo;
+        tl.hi = tile_hi;
+        tl.W = n0 + 2;
+        {
+            const int si = lo + (int)(((long long)(hi - lo - 1) * threadIdx.x) / (P2_THREADS - 1));
+            const int sc = cellp[si];
+            int rmin = sc >= 0 ? (sc >> 16) : 0x7fffffff, rmax = sc >= 0 ? (sc >> 16) : -1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                rmin = min(rmin, __shfl_xor_sync(FULL, rmin, o));
+                rmax = max(rmax, __shfl_xor_sync(FULL, rmax, o));
+            }
+            __syncthreads();  // the previous chunk's flush is done with the tile
+            if ((threadIdx.x & 31) == 0) {
+                red_min[threadIdx.x >> 5] = rmin;
+                red_max[threadIdx.x >> 5] = rmax;
+            }
+            __syncthreads();
+            rmin = red_min[0];
+            rmax = red_max[0];
+#pragma unroll
+            for (int k = 1; k < P2_THREADS / 32; ++k) {
+                rmin = min(rmin, red_min[k]);
+                rmax = max(rmax, red_max[k]);
+            }
+            tl.r0 = rmin - 2;
+            tl.R = rmax - rmin + 5;
+            tl.on = rmax >= rmin && tl.R * tl.W <= TILE_CELLS;
+            if (tl.on)
+                for (int k = threadIdx.x; k < tl.R * tl.W; k += P2_THREADS) tile_lo[k] = tile_hi[k] = 0u;
+            __syncthreads();
+        }
+
+        long long ke = 0;
+        int g0 = 0, g1 = 0, g2 = 0, g3 = 0, gbad = 0;
+
+        int i = lo + (int)threadIdx.x;
+        int ncw = -1;
+        float nt0 = 0.f, nt1 = 0.f, nv0_ = 0.f, nv1_ = 0.f, nv2_ = 0.f;
+        if (i < hi) {
+            ncw = cellp[i];
+            nt0 = t0p[i];
+            nt1 = t1p[i];
+            nv0_ = v0p[i];
+            nv1_ = v1p[i];
+            nv2_ = v2p[i];
+        }
+        for (int base = lo; base < hi; base += P2_THREADS) {
+            const int slot = i;
+            const int cw = ncw;
+            float t[2] = {nt0, nt1};
+            float v[3] = {nv0_, nv1_, nv2_};
+            i += P2_THREADS;
+            ncw = -1;
+            if (i < hi) {
+                ncw = cellp[i];
+                nt0 = t0p[i];
+                nt1 = t1p[i];
+                nv0_ = v0p[i];
+                nv1_ = v1p[i];
+                nv2_ = v2p[i];
+            }
+            const bool active = cw >= 0;
+            int c[2] = {active ? (cw & 0xFFFF) : 0, active ? (cw >> 16) : 0};
+            if (!active) t[0] = t[1] = v[0] = v[1] = v[2] = 0.0f;
+
+            // a2: b1 gather of k and G at xi^n
+            float kp[4], gp[2];
+            {
+                const int v00 = c[0] + c[1] * nv0;
+                const float s0 = __fsub_rn(1.0f, t[0]), s1 = __fsub_rn(1.0f, t[1]);
+                const float w0 = __fmul_rn(s0, s1), w1 = __fmul_rn(t[0], s1);
+                const float w2 = __fmul_rn(s0, t[1]), w3 = __fmul_rn(t[0], t[1]);
+                const float4 a = __ldg(K4 + v00), b = __ldg(K4 + v00 + 1);
+                const float4 cc = __ldg(K4 + v00 + nv0), d = __ldg(K4 + v00 + nv0 + 1);
+                const float2 ga = __ldg(G2 + v00), gb = __ldg(G2 + v00 + 1);
+                const float2 gc = __ldg(G2 + v00 + nv0), gd = __ldg(G2 + v00 + nv0 + 1);
+                kp[0] = __fmaf_rn(w3, d.x, __fmaf_rn(w2, cc.x, __fmaf_rn(w1, b.x, __fmul_rn(w0, a.x))));
+                kp[1] = __fmaf_rn(w3, d.y, __fmaf_rn(w2, cc.y, __fmaf_rn(w1, b.y, __fmul_rn(w0, a.y))));
+                kp[2] = __fmaf_rn(w3, d.z, __fmaf_rn(w2, cc.z, __fmaf_rn(w1, b.z, __fmul_rn(w0, a.z))));
+                kp[3] = __fmaf_rn(w3, d.w, __fmaf_rn(w2, cc.w, __fmaf_rn(w1, b.w, __fmul_rn(w0, a.w))));
+                gp[0] = __fmaf_rn(w3, gd.x, __fmaf_rn(w2, gc.x, __fmaf_rn(w1, gb.x, __fmul_rn(w0, ga.x))));
+                gp[1] = __fmaf_rn(w3, gd.y, __fmaf_rn(w2, gc.y, __fmaf_rn(w1, gb.y, __fmul_rn(w0, ga.y))));
+            }
+            // a3: E^al = -sum_a G^a k^{a al}, kick
+            const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
+#pragma unroll
+            for (int al = 0; al < 2; ++al) {
+                float e = __fmul_rn(kp[al], gp[0]);
+                e = __fmaf_rn(kp[2 + al], gp[1], e);
+                v[al] = __fmaf_rn(dtqm, -e, v[al]);
+            }
+            // a4: predictor (a non-finite component keeps the particle where it is)
+            int cpred[2];
+            float tpred[2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                float d = __fmul_rn(kp[2 * a], v[0]);
+                d = __fmaf_rn(kp[2 * a + 1], v[1], d);
+                float x = __fmaf_rn(hdt, d, t[a]);
+                if (!isfinite(x)) x = t[a];
+                if (a == 0)
+                    predict_axis<PER0>(x, c[0], n0, cpred[0], tpred[0]);
+                else
+                    predict_axis<PER1>(x, c[1], n1, cpred[1], tpred[1]);
+            }
+            // k re-gathered at xi'
+            float kq[4];
+            {
+                const int v00 = cpred[0] + cpred[1] * nv0;
+                const float s0 = __fsub_rn(1.0f, tpred[0]), s1 = __fsub_rn(1.0f, tpred[1]);
+                const float w0 = __fmul_rn(s0, s1), w1 = __fmul_rn(tpred[0], s1);
+                const float w2 = __fmul_rn(s0, tpred[1]), w3 = __fmul_rn(tpred[0], tpred[1]);
+                const float4 a = __ldg(K4 + v00), b = __ldg(K4 + v00 + 1);
+                const float4 cc = __ldg(K4 + v00 + nv0), d = __ldg(K4 + v00 + nv0 + 1);
+                kq[0] = __fmaf_rn(w3, d.x, __fmaf_rn(w2, cc.x, __fmaf_rn(w1, b.x, __fmul_rn(w0, a.x))));
+                kq[1] = __fmaf_rn(w3, d.y, __fmaf_rn(w2, cc.y, __fmaf_rn(w1, b.y, __fmul_rn(w0, a.y))));
+                kq[2] = __fmaf_rn(w3, d.z, __fmaf_rn(w2, cc.z, __fmaf_rn(w1, b.z, __fmul_rn(w0, a.z))));
+                kq[3] = __fmaf_rn(w3, d.w, __fmaf_rn(w2, cc.w, __fmaf_rn(w1, b.w, __fmul_rn(w0, a.w))));
+            }
+            // corrector
+            bool bad = false;
+            int cn[2];
+            float tn[2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                float d = __fmul_rn(kq[2 * a], v[0]);
+                d = __fmaf_rn(kq[2 * a + 1], v[1], d);
+                float x = __fmaf_rn(dt, d, t[a]);
+                if (!isfinite(x)) {
+                    bad = true;
+                    x = t[a];
+                }
+                int dc;
+                renorm(x, tn[a], dc);
+                cn[a] = c[a] + dc;
+            }
+            // a5: boundaries
+            int face = -1;
+            if (PER0) {
+                cn[0] = wrapi(cn[0], n0);
+            } else {
+                if (cn[0] < 0) face = 0;
+                else if (cn[0] >= n0) face = 1;
+            }
+            if (PER1) {
+                cn[1] = wrapi(cn[1], n1);
+            } else if (face < 0) {
+                if (cn[1] < 0) face = 2;
+                else if (cn[1] >= n1) face = 3;
+            }
+            if (bad) face = 6;
+            const bool alive = active && face < 0;
+            if (active) {
+                g0 += face == 0;
+                g1 += face == 1;
+                g2 += face == 2;
+                g3 += face == 3;
+                gbad += face == 6;
+            }
+            // spec D: v_old . v_new as an FP32 fma chain, then round(x 2^24) to int64
+            const float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
+            if (active) ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
+            if (active) {
+                cellp[slot] = alive ? (cn[0] | (cn[1] << 16)) : -1;
+                t0p[slot] = tn[0];
+                t1p[slot] = tn[1];
+                v0p[slot] = v[0];
+                v1p[slot] = v[1];
+                v2p[slot] = v[2];
+            }
+            // a6: deposit
+            if (tl.on)
+                deposit_tile(p, tl, s, alive, cn, tn);
+            else
+                deposit_warp<2>(p, s, alive, cn, tn);
+        }
+        // flush the tile into the padded grid (rows -1 .. n1 exist there; the others hold
+        // nothing)
+        if (tl.on) {
+            __syncthreads();
+            unsigned long long* g = p.charge + (long long)s * p.ncell_h;
+            for (int k = threadIdx.x; k < tl.R * tl.W; k += P2_THREADS) {
+                const unsigned long long v = ((unsigned long long)tile_hi[k] << 32) | tile_lo[k];
+                if (!v) continue;
+                const int row = tl.r0 + k / tl.W;
+                if (row < -1 || row > n1) continue;
+                atomicAdd(g + (long long)(row + 1) * tl.W + k % tl.W, v);
+            }
+        }
+        // tallies of this chunk
+        ke = warp_sum_ll(ke);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            g0 += __shfl_xor_sync(FULL, g0, o);
+            g1 += __shfl_xor_sync(FULL, g1, o);
+            g2 += __shfl_xor_sync(FULL, g2, o);
+            g3 += __shfl_xor_sync(FULL, g3, o);
+            gbad += __shfl_xor_sync(FULL, gbad, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            DevCounters* cw = p.ctr;
+            if (ke) atomicAdd((unsigned long long*)&cw->ke_fp[s], (unsigned long long)ke);
+            const int gf[4] = {g0, g1, g2, g3};
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+                if (gf[f]) atomicAdd((unsigned long long*)&cw->absorbed[s][f], (unsigned long long)gf[f]);
+            if (gbad) atomicAdd((unsigned long long*)&cw->nonfinite, (unsigned long long)gbad);
+            const long long removed = (long long)g0 + g1 + g2 + g3 + gbad;
+            if (removed) atomicAdd((unsigned long long*)&cw->alive[s], (unsigned long long)(-removed));
+        }
+    }
+}
+
+template <bool PER0, bool PER1>
+int launch_push2d_t(cpic_run* r, const PushParams& p) {
+    static int occ = 0;  // resident blocks on the device (one wave)
+    if (!occ) {
+        int dev = 0, nsm = 0, b = 0;
+        CPIC_CUDA(cudaGetDevice(&dev));
+        CPIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        CPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, push2d_kernel<PER0, PER1>, P2_THREADS, 0));
+        occ = (b < 1 ? 1 : b) * nsm;
+    }
+    long long tot = 0;
+    for (int s = 0; s < r->cfg.n_species; ++s) tot += r->pb.capacity[s];
+    long long blocks = (tot + P2_THREADS - 1) / P2_THREADS;
+    if (blocks > occ) blocks = occ;
+    if (blocks < 1) blocks = 1;
+    push2d_kernel<PER0, PER1><<<(int)blocks, P2_THREADS, 0, r->stream>>>(p);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
+}  // namespace
+
+int launch_push2d(cpic_run* r, const PushParams& p) {
+    const bool per0 = p.pbc[0] == CPIC_PBC_PERIODIC, per1 = p.pbc[2] == CPIC_PBC_PERIODIC;
+    if (per0) return per1 ? launch_push2d_t<true, true>(r, p) : launch_push2d_t<true, false>(r, p);
+    return per1 ? launch_push2d_t<false, true>(r, p) : launch_push2d_t<false, false>(r, p);
+}
+
+}  // namespace cpic
