@@ -172,6 +172,11 @@ int cpic_initialize(cpic_run* run);
 /* nsteps full PIC steps (Sec. II cycle): vertex field, push (+ deposit), injection, sort
  * every sort_interval steps, charge -> RHS, multigrid solve to mg_rtol, diagnostics. */
 int cpic_step(cpic_run* run, int nsteps);
+/* nsteps particle steps with the field held fixed: vertex field, push (+ deposit),
+ * injection, sort every sort_interval steps; no charge -> RHS and no field solve. This is
+ * the mover with its grid coupling on its own, as timed with fixed fields in Sec. III
+ * (Tables II and III); the deposited charge of the last step is left in the charge grids. */
+int cpic_step_particles(cpic_run* run, int nsteps);
 
 /* Rows of one step, for callers that drive the cycle themselves: */
 /* a1: G = d phi / d u at vertices from the cell potential (Sec. II.B staggering). */
@@ -241,9 +246,9 @@ int cpic_sort_cells_noalloc(int dim, const int32_t* n, int64_t count, const int3
 /* ---------------------------------------------------------------- tracing */
 
 /* Phases of cpic_step timed with CUDA events recorded on the run's stream. */
-#define CPIC_PHASE_FIELD 0   /* a1 vertex field */
-#define CPIC_PHASE_PUSH 1    /* a2-a6 fused push + deposit */
-#define CPIC_PHASE_INJECT 2  /* a8 */
+#define CPIC_PHASE_FIELD 0   /* a1 vertex field, zeroing of the deposit grid */
+#define CPIC_PHASE_PUSH 1    /* a2-a6 the fused push + deposit kernel alone */
+#define CPIC_PHASE_INJECT 2  /* a8 injection, step counter, halo fold of the deposit grid */
 #define CPIC_PHASE_SORT 3    /* a7 */
 #define CPIC_PHASE_SOLVE 4   /* a9 right-hand side + multigrid + field energy */
 #define CPIC_NPHASES 5

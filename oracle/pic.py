@@ -110,7 +110,9 @@ class OraclePIC:
             else:
                 sp.v = mover.kick32(sp.idx, sp.t, sp.v, k, G, self.n, np.float32(-0.5 * self.dt * qm))
 
-    def step(self):
+    def step(self, solve: bool = True):
+        """One PIC cycle. solve=False holds the field fixed (mover, injection and deposit
+        only: the fixed-field mover runs of Sec. III)."""
         we = 0.5 * float(np.sum(self.phi * self.Q))
         k, G = self.field_tables()
         ke = []
@@ -145,7 +147,10 @@ class OraclePIC:
             sp.idx = np.concatenate([sp.idx, idx], axis=1)
             sp.t = np.concatenate([sp.t, t32], axis=1)
             sp.v = np.concatenate([sp.v, v32], axis=1)
-        self.solve()
+        if solve:
+            self.solve()
+        else:
+            self.Q = self.charge()
         self.step_index += 1
         self.history.append({"step": self.step_index, "W_E": we, "W_K": sum(ke),
                              "n": [sp.idx.shape[1] for sp in self.species],

@@ -81,6 +81,7 @@ _SIGS = {
                            ctypes.c_int),
     "cpic_initialize": ([P], ctypes.c_int),
     "cpic_step": ([P, ctypes.c_int], ctypes.c_int),
+    "cpic_step_particles": ([P, ctypes.c_int], ctypes.c_int),
     "cpic_vertex_field": ([P], ctypes.c_int),
     "cpic_push": ([P], ctypes.c_int),
     "cpic_deposit": ([P], ctypes.c_int),
@@ -249,6 +250,10 @@ class Run:
 
     def step(self, nsteps=1):
         check(load().cpic_step(self.h, nsteps))
+
+    def step_particles(self, nsteps=1):
+        """Particle steps with the field held fixed (no field solve)."""
+        check(load().cpic_step_particles(self.h, nsteps))
 
     def vertex_field(self):
         check(load().cpic_vertex_field(self.h))

@@ -350,10 +350,11 @@ int after_map(cpic_run* r) {
 }  // namespace
 
 void invalidate_graphs(cpic_run* r) {
-    for (int i = 0; i < 2; ++i) {
-        if (r->step_graph_ok[i]) cudaGraphExecDestroy(r->step_graph[i]);
-        r->step_graph_ok[i] = false;
-    }
+    for (int j = 0; j < 2; ++j)
+        for (int i = 0; i < 2; ++i) {
+            if (r->step_graph_ok[j][i]) cudaGraphExecDestroy(r->step_graph[j][i]);
+            r->step_graph_ok[j][i] = false;
+        }
 }
 
 namespace {
@@ -398,7 +399,24 @@ int enqueue_step(cpic_run* r, bool sort) {
     return CPIC_OK;
 }
 
-int build_step_graph(cpic_run* r, int with_sort) {
+// kernel nodes of a graph (top level; a conditional node's body runs a device-decided
+// number of times and is not counted)
+int count_kernel_nodes(cudaGraph_t g, int* out) {
+    size_t n = 0;
+    CPIC_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) CPIC_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+    int k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        CPIC_CUDA(cudaGraphNodeGetType(nodes[i], &t));
+        if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    *out = k;
+    return CPIC_OK;
+}
+
+int build_step_graph(cpic_run* r, int with_solve, int with_sort) {
     if (!r->capture_stream) CPIC_CUDA(cudaStreamCreateWithFlags(&r->capture_stream, cudaStreamNonBlocking));
     cudaStream_t saved = r->stream;
     r->stream = r->capture_stream;
@@ -410,7 +428,7 @@ int build_step_graph(cpic_run* r, int with_sort) {
         return cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
     }
     st = enqueue_step(r, with_sort != 0);
-    if (!st) {
+    if (!st && with_solve) {
         cudaStreamCaptureStatus cs;
         cudaGraph_t cg = nullptr;
         e = cudaStreamGetCaptureInfo(r->stream, &cs, nullptr, &cg, nullptr, nullptr, nullptr);
@@ -424,24 +442,32 @@ int build_step_graph(cpic_run* r, int with_sort) {
         return st;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    int nk = 0;
+    st = count_kernel_nodes(g, &nk);
+    if (st) {
+        cudaGraphDestroy(g);
+        return st;
+    }
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
-    r->step_graph[with_sort] = ex;
-    r->step_graph_ok[with_sort] = true;
+    r->step_graph[with_solve][with_sort] = ex;
+    r->step_graph_ok[with_solve][with_sort] = true;
+    r->graph_kernels[with_solve][with_sort] = nk;
     return CPIC_OK;
 }
 
-int step_once(cpic_run* r) {
+int step_once(cpic_run* r, bool solve) {
     bool sort = r->cfg.sort_interval > 0 && r->steps_since_sort + 1 >= r->cfg.sort_interval;
     if (!r->profiling) {
-        int wi = sort ? 1 : 0;
-        if (!r->step_graph_ok[wi]) {
-            int st = build_step_graph(r, wi);
+        const int wi = sort ? 1 : 0, ws = solve ? 1 : 0;
+        if (!r->step_graph_ok[ws][wi]) {
+            int st = build_step_graph(r, ws, wi);
             if (st) return st;
         }
-        CPIC_CUDA(cudaGraphLaunch(r->step_graph[wi], r->stream));
+        CPIC_CUDA(cudaGraphLaunch(r->step_graph[ws][wi], r->stream));
+        g_launches.fetch_add(r->graph_kernels[ws][wi], std::memory_order_relaxed);
         ++r->steps_since_sort;
         if (sort) {
             r->cur_host ^= 1;
@@ -449,13 +475,18 @@ int step_once(cpic_run* r) {
         }
         return CPIC_OK;
     }
-    // profiled path: the same work launched stream-ordered, bracketed by events
-    int st = phase(r, CPIC_PHASE_FIELD, [&] { return launch_vertex_field(r); });
+    // profiled path: the same work launched stream-ordered, bracketed by events; the push
+    // phase holds the fused push kernel alone
+    int st = phase(r, CPIC_PHASE_FIELD, [&] {
+        int q = launch_vertex_field(r);
+        return q ? q : launch_push_prep(r);
+    });
     if (st) return st;
-    st = phase(r, CPIC_PHASE_PUSH, [&] { return launch_push(r); });
+    st = phase(r, CPIC_PHASE_PUSH, [&] { return launch_push_kernel(r); });
     if (st) return st;
     st = phase(r, CPIC_PHASE_INJECT, [&] {
-        int q = launch_inject(r);
+        int q = launch_finalize_step(r);
+        if (!q) q = launch_inject(r);
         return q ? q : launch_fold(r);
     });
     if (st) return st;
@@ -465,6 +496,7 @@ int step_once(cpic_run* r) {
         r->cur_host ^= 1;
         r->steps_since_sort = 0;
     }
+    if (!solve) return CPIC_OK;
     return phase(r, CPIC_PHASE_SOLVE,
                  [&] { return mg_solve(r, r->cfg.mg_rtol, r->cfg.mg_max_cycles, true, nullptr, nullptr); });
 }
@@ -743,7 +775,17 @@ int cpic_step(cpic_run* r, int nsteps) {
     CHECK_RUN(r);
     CHECK_MAP(r);
     for (int i = 0; i < nsteps; ++i) {
-        int st = step_once(r);
+        int st = step_once(r, true);
+        if (st) return st;
+    }
+    return CPIC_OK;
+}
+
+int cpic_step_particles(cpic_run* r, int nsteps) {
+    CHECK_RUN(r);
+    CHECK_MAP(r);
+    for (int i = 0; i < nsteps; ++i) {
+        int st = step_once(r, false);
         if (st) return st;
     }
     return CPIC_OK;

@@ -147,8 +147,9 @@ struct cpic_run {
     double* dense_tmp;           // setup scratch [(m+1)^2]
     unsigned* ticket;            // last-block counter of the residual reduction
     // CUDA graphs of one PIC step (index 1: with the cell sort), captured on capture_stream
-    cudaGraphExec_t step_graph[2];
-    bool step_graph_ok[2];
+    cudaGraphExec_t step_graph[2][2];  // [with field solve][with sort]
+    bool step_graph_ok[2][2];
+    int graph_kernels[2][2];           // kernel nodes launched by one replay
     cudaStream_t capture_stream;
     int cluster_cs;              // cluster size of the cluster solver (0: not applicable)
     int dense_m;                 // coarsest unknowns (+1 row when singular)
@@ -184,6 +185,8 @@ int launch_deposit(cpic_run* r);
 int launch_kick(cpic_run* r, double fraction);
 int launch_finalize_step(cpic_run* r);
 int launch_fold(cpic_run* r);
+int launch_push_prep(cpic_run* r);    // zero the deposit grid and kinetic-energy tallies
+int launch_push_kernel(cpic_run* r);  // the fused push + deposit kernel alone
 PushParams make_push_params(cpic_run* r);
 int launch_push2d(cpic_run* r, const PushParams& p);
 // inject.cu

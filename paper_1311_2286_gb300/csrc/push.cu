@@ -354,10 +354,19 @@ static int launch_particles(cpic_run* r, float c0, float c1, float c2, float c3)
     return CPIC_OK;
 }
 
-int launch_push(cpic_run* r) {
+int launch_push_prep(cpic_run* r) {
     CPIC_CUDA(cudaMemsetAsync(r->charge_h, 0, sizeof(unsigned long long) * r->ncell_h * r->cfg.n_species, r->stream));
     CPIC_CUDA(cudaMemsetAsync(&r->ctr->ke_fp[0], 0, sizeof(long long) * CPIC_MAX_SPECIES, r->stream));
-    int st = r->D == 2 ? launch_push2d(r, make_push_params(r)) : launch_particles<0>(r, 0, 0, 0, 0);
+    return CPIC_OK;
+}
+
+int launch_push_kernel(cpic_run* r) {
+    return r->D == 2 ? launch_push2d(r, make_push_params(r)) : launch_particles<0>(r, 0, 0, 0, 0);
+}
+
+int launch_push(cpic_run* r) {
+    int st = launch_push_prep(r);
+    if (!st) st = launch_push_kernel(r);
     if (st) return st;
     return launch_finalize_step(r);
 }
