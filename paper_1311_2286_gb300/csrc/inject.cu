@@ -13,6 +13,10 @@
 //    then the split (cell, FP32 offset); a particle whose partial push leaves the domain is
 //    written as a dead slot.
 // New particles are appended to their species in draw order and deposited at once.
+// The arithmetic after the draws is FP32 (u rounded to FP32, the face k from the FP32 vertex
+// table, FP32 Box-Muller, the partial push on the split position), so it agrees with the
+// FP64 reading to FP32 rounding; FP64 on this part runs at a small fraction of the FP32 rate
+// and would make the injection a long serial chain.
 #include <math.h>
 
 #include "particles.cuh"
@@ -38,44 +42,65 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
-__device__ __forceinline__ double u01(unsigned u) { return __dmul_rn(__dadd_rn((double)u, 0.5), 2.3283064365386962890625e-10); }
+// u -> (u + 1/2) 2^-32 in (0, 1], in FP32
+__device__ __forceinline__ float u01f(unsigned u) {
+    return __fmaf_rn(__uint2float_rn(u), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+}
+
+struct InjectOne {
+    int s, side;
+    double rate;
+    float vth, drift[3];
+    unsigned long long seed;
+    int blocks;  // blocks covering this species' draws
+};
 
 struct InjectParams {
     PushParams p;
-    int sp;
-    int side;
-    double rate;
-    double vth;
-    double drift[3];
-    unsigned long long seed;
-    double dt;
-    const double* k64;
+    float dt;
+    int nsp;  // injecting species in this launch (blockIdx.y)
+    InjectOne sp[CPIC_MAX_SPECIES];
 };
 
 __device__ __forceinline__ long long inject_count(double rate, long long step) {
     return (long long)(floor((double)(step + 1) * rate) - floor((double)step * rate));
 }
 
+// split renormalisation of a small FP32 displacement from the start of cell c
+__device__ __forceinline__ void split(float x, int c0, int& c, float& t) {
+    float cf = floorf(x);
+    float f = __fsub_rn(x, cf);
+    if (f >= 1.0f) {
+        f = 0.0f;
+        cf = __fadd_rn(cf, 1.0f);
+    }
+    cf = fminf(fmaxf(cf, -16777216.0f), 16777216.0f);
+    c = c0 + (int)cf;
+    t = f;
+}
+
+// One launch injects every species (blockIdx.y); the last block of a species to finish
+// commits its new particle count (so later kernels of the step see the particles).
 __global__ void inject_kernel(InjectParams ip) {
     const PushParams& p = ip.p;
-    const int s = ip.sp;
+    const InjectOne& sp = ip.sp[blockIdx.y];
+    const int s = sp.s;
     const long long step = p.ctr->step - 1;
-    const long long count = inject_count(ip.rate, step);
+    const long long count = inject_count(sp.rate, step);
     const long long start = p.ctr->count[s];
     const long long room = p.pb.capacity[s] - start;
     const long long nslots = count < room ? count : (room > 0 ? room : 0);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        p.ctr->pending_inject[s] = (int)nslots;
-        if (count > nslots) atomicAdd((unsigned long long*)&p.ctr->dropped[s], (unsigned long long)(count - nslots));
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && count > nslots)
+        atomicAdd((unsigned long long*)&p.ctr->dropped[s], (unsigned long long)(count - nslots));
     const int cur = p.ctr->cur;
     const long long T = p.pb.total;
     const int n1 = p.n[0], n2 = p.n[1];
     const int nv0 = n1 + 1;
-    const uint2 key = make_uint2((unsigned)(ip.seed & 0xffffffffull), (unsigned)(ip.seed >> 32));
+    const float4* K4 = reinterpret_cast<const float4*>(p.K);
+    const uint2 key = make_uint2((unsigned)(sp.seed & 0xffffffffull), (unsigned)(sp.seed >> 32));
     int kept_lane = 0;
     // warp-uniform loop bound
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < nslots; base += (long long)gridDim.x * blockDim.x) {
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < nslots; base += (long long)sp.blocks * blockDim.x) {
         long long pi = base + threadIdx.x;
         bool act = pi < nslots;
         int c[3] = {0, 0, 0};
@@ -84,47 +109,37 @@ __global__ void inject_kernel(InjectParams ip) {
         if (act) {
             uint4 r0 = philox4x32_10(make_uint4((unsigned)pi, (unsigned)step, (unsigned)s, 0u), key);
             uint4 r1 = philox4x32_10(make_uint4((unsigned)pi, (unsigned)step, (unsigned)s, 1u), key);
-            double U0 = u01(r0.x), U1 = u01(r0.y), U2 = u01(r0.z), U3 = u01(r0.w), U4 = u01(r1.x);
-            double u1 = __dmul_rn(U0, (double)n2);
-            int j = (int)floor(u1);
+            const float U0 = u01f(r0.x), U1 = u01f(r0.y), U2 = u01f(r0.z), U3 = u01f(r0.w), U4 = u01f(r1.x);
+            const float u1 = __fmul_rn(U0, (float)n2);
+            int j = (int)floorf(u1);
             if (j > n2 - 1) j = n2 - 1;
-            double sfr = __dsub_rn(u1, (double)j);
-            int col = ip.side == 0 ? 0 : n1;
-            const double* ka = ip.k64 + ((long long)col + (long long)nv0 * j) * 4;
-            const double* kb_ = ip.k64 + ((long long)col + (long long)nv0 * (j + 1)) * 4;
-            double oms = __dsub_rn(1.0, sfr);
-            double kb[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) kb[q] = __dadd_rn(__dmul_rn(oms, ka[q]), __dmul_rn(sfr, kb_[q]));
-            double ga0 = kb[0], ga1 = kb[1];
-            double gn = __dsqrt_rn(__dadd_rn(__dmul_rn(ga0, ga0), __dmul_rn(ga1, ga1)));
-            double sgn = ip.side == 1 ? -1.0 : 1.0;
-            double nin0 = __ddiv_rn(__dmul_rn(sgn, ga0), gn), nin1 = __ddiv_rn(__dmul_rn(sgn, ga1), gn);
-            double tau0 = -nin1, tau1 = nin0;
-            double vn = __dmul_rn(ip.vth, __dsqrt_rn(__dmul_rn(-2.0, log(U1))));
-            double rho = __dmul_rn(ip.vth, __dsqrt_rn(__dmul_rn(-2.0, log(U2))));
-            const double two_pi = 6.283185307179586;
-            double vt = __dmul_rn(rho, cos(__dmul_rn(two_pi, U3)));
-            double vz = __dmul_rn(rho, sin(__dmul_rn(two_pi, U3)));
-            float v0 = __double2float_rn(__dadd_rn(__dadd_rn(__dmul_rn(vn, nin0), __dmul_rn(vt, tau0)), ip.drift[0]));
-            float v1 = __double2float_rn(__dadd_rn(__dadd_rn(__dmul_rn(vn, nin1), __dmul_rn(vt, tau1)), ip.drift[1]));
-            float v2 = __double2float_rn(__dadd_rn(vz, ip.drift[2]));
-            double vd0 = v0, vd1 = v1;
-            double fdt = __dmul_rn(U4, ip.dt);
-            double du0 = __dmul_rn(fdt, __dadd_rn(__dmul_rn(kb[0], vd0), __dmul_rn(kb[1], vd1)));
-            double du1 = __dmul_rn(fdt, __dadd_rn(__dmul_rn(kb[2], vd0), __dmul_rn(kb[3], vd1)));
-            double uu[2] = {__dadd_rn(ip.side == 0 ? 0.0 : (double)n1, du0), __dadd_rn(__dadd_rn((double)j, sfr), du1)};
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                double cf = floor(uu[a]);
-                float f = __double2float_rn(__dsub_rn(uu[a], cf));
-                if (f >= 1.0f) {
-                    f = 0.0f;
-                    cf = cf + 1.0;
-                }
-                c[a] = (int)cf;
-                tt[a] = f;
-            }
+            const float sfr = __fsub_rn(u1, (float)j);
+            const int col = sp.side == 0 ? 0 : n1;
+            // k interpolated along the face (FP32 vertex table)
+            const float4 ka = __ldg(K4 + col + nv0 * j), kb_ = __ldg(K4 + col + nv0 * (j + 1));
+            const float oms = __fsub_rn(1.0f, sfr);
+            const float kb[4] = {__fmaf_rn(sfr, kb_.x, __fmul_rn(oms, ka.x)), __fmaf_rn(sfr, kb_.y, __fmul_rn(oms, ka.y)),
+                                 __fmaf_rn(sfr, kb_.z, __fmul_rn(oms, ka.z)), __fmaf_rn(sfr, kb_.w, __fmul_rn(oms, ka.w))};
+            // inward unit normal along grad xi^0 (row 0 of k) and the tangent
+            const float gn = sqrtf(__fmaf_rn(kb[0], kb[0], __fmul_rn(kb[1], kb[1])));
+            const float sgn = sp.side == 1 ? -1.0f : 1.0f;
+            const float nin0 = __fdiv_rn(sgn * kb[0], gn), nin1 = __fdiv_rn(sgn * kb[1], gn);
+            const float tau0 = -nin1, tau1 = nin0;
+            // flux-weighted normal speed, Gaussian tangential and z components (Box-Muller)
+            const float vn = sp.vth * sqrtf(-2.0f * logf(U1));
+            const float rho = sp.vth * sqrtf(-2.0f * logf(U2));
+            float sn, cs;
+            sincospif(2.0f * U3, &sn, &cs);
+            const float vt = rho * cs, vz = rho * sn;
+            const float v0 = __fadd_rn(__fmaf_rn(vn, nin0, __fmul_rn(vt, tau0)), sp.drift[0]);
+            const float v1 = __fadd_rn(__fmaf_rn(vn, nin1, __fmul_rn(vt, tau1)), sp.drift[1]);
+            const float v2 = __fadd_rn(vz, sp.drift[2]);
+            // partial first push over a uniform fraction U4 of the step, on the split position
+            const float fdt = __fmul_rn(U4, ip.dt);
+            const float du0 = __fmul_rn(fdt, __fmaf_rn(kb[0], v0, __fmul_rn(kb[1], v1)));
+            const float du1 = __fmul_rn(fdt, __fmaf_rn(kb[2], v0, __fmul_rn(kb[3], v1)));
+            split(du0, col, c[0], tt[0]);
+            split(__fadd_rn(sfr, du1), j, c[1], tt[1]);
             c[1] = ((c[1] % n2) + n2) % n2;
             alive = c[0] >= 0 && c[0] < n1;
             long long slot = p.pb.base[s] + start + pi;
@@ -145,42 +160,48 @@ __global__ void inject_kernel(InjectParams ip) {
         atomicAdd((unsigned long long*)&p.ctr->injected[s], (unsigned long long)k);
         atomicAdd((unsigned long long*)&p.ctr->alive[s], (unsigned long long)k);
     }
-}
-
-__global__ void inject_commit_kernel(DevCounters* ctr, int sp) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        ctr->count[sp] += ctr->pending_inject[sp];
-        ctr->pending_inject[sp] = 0;
+    // commit: the last block of this species to finish appends the slots to the species
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&p.ctr->inject_ticket[s], 1u);
+        last = t == (unsigned)gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        p.ctr->count[s] = start + nslots;
+        p.ctr->inject_ticket[s] = 0u;
     }
 }
 
 }  // namespace
 
-PushParams make_push_params(cpic_run* r);
-
 int launch_inject(cpic_run* r) {
+    InjectParams ip;
+    ip.p = make_push_params(r);
+    ip.dt = (float)r->cfg.dt;
+    ip.nsp = 0;
+    long long maxb = 1;
     for (int s = 0; s < r->cfg.n_species; ++s) {
         const InjectSpec& sp = r->inj[s];
         if (!sp.enabled) continue;
-        InjectParams ip;
-        ip.p = make_push_params(r);
-        ip.sp = s;
-        ip.side = sp.face & 1;
-        ip.rate = sp.rate;
-        ip.vth = sp.vth;
-        for (int a = 0; a < 3; ++a) ip.drift[a] = sp.drift[a];
-        ip.seed = sp.seed;
-        ip.dt = r->cfg.dt;
-        ip.k64 = r->k64;
+        InjectOne& o = ip.sp[ip.nsp++];
+        o.s = s;
+        o.side = sp.face & 1;
+        o.rate = sp.rate;
+        o.vth = (float)sp.vth;
+        for (int a = 0; a < 3; ++a) o.drift[a] = (float)sp.drift[a];
+        o.seed = sp.seed;
         long long maxc = (long long)ceil(sp.rate) + 1;
-        long long blocks = (maxc + 255) / 256;
-        if (blocks > 152 * 4) blocks = 152 * 4;
-        if (blocks < 1) blocks = 1;
-        inject_kernel<<<(int)blocks, 256, 0, r->stream>>>(ip);
-        CPIC_CHECK_LAUNCH();
-        inject_commit_kernel<<<1, 32, 0, r->stream>>>(r->ctr, s);
-        CPIC_CHECK_LAUNCH();
+        long long b = (maxc + 255) / 256;
+        if (b > 152 * 4) b = 152 * 4;
+        if (b > maxb) maxb = b;
     }
+    if (!ip.nsp) return CPIC_OK;
+    for (int k = 0; k < ip.nsp; ++k) ip.sp[k].blocks = (int)maxb;
+    inject_kernel<<<dim3((unsigned)maxb, (unsigned)ip.nsp), 256, 0, r->stream>>>(ip);
+    CPIC_CHECK_LAUNCH();
     return CPIC_OK;
 }
 

@@ -47,7 +47,7 @@ struct DevCounters {
     long long ke_fp[CPIC_MAX_SPECIES];     // sum of round(v_old . v_new * 2^24) of the last push
     long long step;                        // completed pushes
     int cur;                               // current particle buffer (0/1)
-    int pending_inject[CPIC_MAX_SPECIES];  // particles written by the last injection
+    unsigned inject_ticket[CPIC_MAX_SPECIES];  // blocks of the running injection that are done
     double field_energy;
     double mg_residual;
     double mg_bnorm;

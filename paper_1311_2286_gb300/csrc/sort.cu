@@ -137,38 +137,71 @@ __global__ void scan_final_kernel(const int* hist, long long N, long long chunk,
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) scan[N] = carry;
 }
 
-__global__ void scatter_kernel(SortParams p) {
-    const Ranges R = ranges(p);
-    const long long total = R.voff[p.nsp];
+// Scatter: blocks walk chunks of one species (block-uniform species, 32-bit slot indices);
+// every thread loads its particle's whole state before reserving its destination, so the
+// loads overlap the cursor atomics; lanes with the same cell reserve consecutive slots with
+// one atomic per group.
+template <int D>
+__global__ void __launch_bounds__(256) scatter_kernel(SortParams p) {
+    const int nsp = p.nsp;
+    int cnt[CPIC_MAX_SPECIES];
+    int total = 0;
+#pragma unroll
+    for (int s = 0; s < CPIC_MAX_SPECIES; ++s) {
+        cnt[s] = s < nsp ? (int)p.ctr->count[s] : 0;
+        total += cnt[s];
+    }
+    if (total == 0) return;
+    const int C = ((total + (int)gridDim.x - 1) / (int)gridDim.x + 255) / 256 * 256;
     const int cur = p.ctr->cur, nxt = 1 - cur;
     const long long T = p.pb.total;
-    const int* cellp = p.pb.cell[cur];
-    const float* tp = p.pb.t[cur];
-    const float* vp = p.pb.v[cur];
-    int* cello = p.pb.cell[nxt];
-    float* to = p.pb.t[nxt];
-    float* vo = p.pb.v[nxt];
     const int lane = threadIdx.x & 31;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += (long long)gridDim.x * blockDim.x) {
-        long long vi = base + threadIdx.x;
-        int s = species_at(R, p.nsp, vi);
-        long long local = vi - R.voff[s];
-        bool act = vi < total && local < R.cnt[s];
-        long long src = p.pb.base[s] + local;
-        int cw = act ? cellp[src] : -1;
-        long long key = cell_key(p, cw);
-        unsigned peers = __match_any_sync(FULL, (unsigned long long)key);
-        int leader = __ffs(peers) - 1;
-        long long start = 0;
-        if (key >= 0 && leader == lane) start = atomicAdd(p.hist + (long long)s * p.ncell + key, __popc(peers));
-        start = __shfl_sync(peers, start, leader);
-        if (key >= 0) {
-            int rank = __popc(peers & ((1u << lane) - 1u));
-            long long idx = (long long)s * p.ncell + key;
-            long long dst = p.pb.base[s] + (p.scan[idx] - p.scan[(long long)s * p.ncell]) + start + rank;
-            cello[dst] = cw;
-            for (int a = 0; a < p.D; ++a) to[a * T + dst] = tp[a * T + src];
-            for (int al = 0; al < 3; ++al) vo[al * T + dst] = vp[al * T + src];
+    const int n0 = p.n[0], n1 = p.n[1];
+    for (int ch = blockIdx.x;; ch += gridDim.x) {
+        int s = 0, local = ch;
+        while (s < nsp) {
+            const int nch = (cnt[s] + C - 1) / C;
+            if (local < nch) break;
+            local -= nch;
+            ++s;
+        }
+        if (s >= nsp) break;
+        const int lo = local * C, hi = min(lo + C, cnt[s]);
+        const long long b0 = p.pb.base[s];
+        const int* __restrict__ cin = p.pb.cell[cur] + b0;
+        const float* __restrict__ tin = p.pb.t[cur] + b0;
+        const float* __restrict__ vin = p.pb.v[cur] + b0;
+        int* __restrict__ cout = p.pb.cell[nxt] + b0;
+        float* __restrict__ tout = p.pb.t[nxt] + b0;
+        float* __restrict__ vout = p.pb.v[nxt] + b0;
+        const long long* __restrict__ scan_s = p.scan + (long long)s * p.ncell;
+        int* __restrict__ cursor = p.hist + (long long)s * p.ncell;
+        const long long sbase = scan_s[0];
+        for (int i = lo + (int)threadIdx.x; i - (int)threadIdx.x < hi; i += 256) {
+            const bool act = i < hi;
+            const int cw = act ? cin[i] : -1;
+            float t[3], v[3];
+#pragma unroll
+            for (int a = 0; a < D; ++a) t[a] = act ? tin[a * T + i] : 0.f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) v[a] = act ? vin[a * T + i] : 0.f;
+            int key = -1;
+            if (cw >= 0)
+                key = D == 2 ? (cw & 0xFFFF) + n0 * (cw >> 16)
+                             : (cw & 1023) + n0 * (((cw >> 10) & 1023) + n1 * (cw >> 20));
+            const unsigned peers = __match_any_sync(FULL, key);
+            const int leader = __ffs(peers) - 1;
+            int start = 0;
+            if (key >= 0 && leader == lane) start = atomicAdd(cursor + key, __popc(peers));
+            start = __shfl_sync(FULL, start, leader);
+            if (key >= 0) {
+                const int dst = (int)(scan_s[key] - sbase) + start + __popc(peers & ((1u << lane) - 1u));
+                cout[dst] = cw;
+#pragma unroll
+                for (int a = 0; a < D; ++a) tout[a * T + dst] = t[a];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) vout[a * T + dst] = v[a];
+            }
         }
     }
 }
@@ -215,7 +248,10 @@ int launch_sort(cpic_run* r) {
     scan_final_kernel<<<nb, SCAN_THREADS, 0, r->stream>>>(r->hist, N, chunk, r->scan_blocks, r->scan);
     CPIC_CHECK_LAUNCH();
     CPIC_CUDA(cudaMemsetAsync(r->hist, 0, sizeof(int) * N, r->stream));
-    scatter_kernel<<<(int)pblocks, 256, 0, r->stream>>>(p);
+    if (p.D == 2)
+        scatter_kernel<2><<<(int)pblocks, 256, 0, r->stream>>>(p);
+    else
+        scatter_kernel<3><<<(int)pblocks, 256, 0, r->stream>>>(p);
     CPIC_CHECK_LAUNCH();
     sort_finalize_kernel<<<1, 32, 0, r->stream>>>(p);
     CPIC_CHECK_LAUNCH();

@@ -264,7 +264,8 @@ def test_sort_preserves_particles_and_orders_cells(cpic):
 
 def test_injection_matches_oracle(cpic):
     """a8: the injected count follows floor((n+1) r) - floor(n r); Philox draws and the
-    deposited charge agree with the oracle; velocities agree to FP32 rounding."""
+    deposited charge agree with the oracle; velocities agree to FP32 arithmetic (a few ulp
+    of FP32 log/sqrt/sincos and the normal, far inside the 1e-5 single-step FP32 bound)."""
     n1, n2 = 32, 64
     w = wl.cylinder(n1=n1, n2=n2, npart_per_species=1000, seed=9, inject=True)
     g, per = _geom(w)
@@ -285,7 +286,7 @@ def test_injection_matches_oracle(cpic):
         new_c, new_t, new_v = ca[nb:], ta[:, nb:], va[:, nb:]
         assert new_c.shape[0] == int(keep.sum())
         assert d["injected"][s] == int(keep.sum())
-        np.testing.assert_allclose(new_v, v32, rtol=2e-7, atol=1e-7)
+        np.testing.assert_allclose(new_v, v32, rtol=2e-6, atol=2e-6 * vth)
         ref_cell = (idx[0] | (idx[1] << 16)).astype(np.int32)
         mism = np.sum(new_c != ref_cell)
         assert mism <= max(1, cnt // 10000)
