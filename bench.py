@@ -68,7 +68,7 @@ def measured_peak():
 def profiled_traffic():
     """dram bytes per push launch from the committed ncu summary, if it was taken on the
     current kernel sources (matching source hash), else None."""
-    path = os.path.join(ROOT, "profiles", "push_cylinder_128x256_4M.md")
+    path = os.path.join(ROOT, "profiles", "push2d_cylinder_128x256_4M.md")
     if not os.path.exists(path):
         return None
     kv = {}
