@@ -164,6 +164,15 @@ int cpic_get_particles(cpic_run* run, int sp, int64_t room, int64_t* n, int32_t*
 int cpic_set_injection(cpic_run* run, int sp, int face, double density, double vth,
                        const double* drift, uint64_t seed);
 
+/* Loads n particles of species sp on the device, replacing its particles: a Maxwellian
+ * plasma of uniform physical density (the paper's runs start from one, Sec. III.A-B).
+ * Cells are drawn with probability J_c / sum J_c (J_c the cell Jacobian), offsets uniform
+ * in each cell, velocities vth * N(0, 1) per component plus drift (host, 3 doubles, may be
+ * NULL). Draws: Philox4x32-10, counter (i, 0x10AD, sp, word), key seed. Requires the map
+ * (CPIC_ERR_STATE otherwise); n <= capacity[sp] (CPIC_ERR_INVALID otherwise). Asynchronous
+ * on the run's stream. */
+int cpic_load_maxwellian(cpic_run* run, int sp, int64_t n, double vth, const double* drift, uint64_t seed);
+
 /* ---------------------------------------------------------------- the PIC cycle */
 
 /* Start-up: deposit rho^0 and solve phi^0, then v^{-1/2} = v^0 - dt/2 (q/m) E(xi^0)
@@ -242,6 +251,31 @@ int cpic_synchronize(cpic_run* run);
 int cpic_sort_cells_noalloc(int dim, const int32_t* n, int64_t count, const int32_t* cell_in,
                             const float* t_in, const float* v_in, int32_t* cell_out, float* t_out,
                             float* v_out, int64_t* live_out, void* stream);
+
+/* ---------------------------------------------------------------- batched runs (row a11) */
+
+/* A batch steps many independent runs together: one CUDA graph launch per batch step, whose
+ * branches (one per member run, no dependencies between them) hold each run's whole step,
+ * so the device runs them concurrently. Runs keep their own arenas and streams; a member
+ * must not be stepped alone, nor change its map or injection. Not in the paper (its runs
+ * are single simulations); the physics of each run is unchanged, so each run's result is
+ * the same in a batch as alone. */
+typedef struct cpic_batch cpic_batch;
+
+/* max_runs: 1 .. 4096. stream: cudaStream_t the batch's graphs are launched on (NULL: the
+ * batch creates and owns a non-blocking stream; graphs cannot be captured on the legacy
+ * default stream). */
+int cpic_batch_create(int max_runs, void* stream, cpic_batch** out);
+int cpic_batch_destroy(cpic_batch* batch);
+/* The run must have its map (CPIC_ERR_STATE) and be initialised; CPIC_ERR_CAPACITY when the
+ * batch is full. Synchronises the run's stream. */
+int cpic_batch_add(cpic_batch* batch, cpic_run* run);
+int cpic_batch_remove(cpic_batch* batch, cpic_run* run);
+int cpic_batch_size(const cpic_batch* batch, int* n);
+/* nsteps batch steps; with_solve != 0: full PIC cycles (cpic_step), 0: fixed-field particle
+ * steps (cpic_step_particles). Each run sorts on its own schedule. Asynchronous. */
+int cpic_batch_step(cpic_batch* batch, int nsteps, int with_solve);
+int cpic_batch_synchronize(cpic_batch* batch);
 
 /* ---------------------------------------------------------------- tracing */
 

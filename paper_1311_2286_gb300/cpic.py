@@ -82,6 +82,14 @@ _SIGS = {
     "cpic_initialize": ([P], ctypes.c_int),
     "cpic_step": ([P, ctypes.c_int], ctypes.c_int),
     "cpic_step_particles": ([P, ctypes.c_int], ctypes.c_int),
+    "cpic_load_maxwellian": ([P, ctypes.c_int, ctypes.c_int64, ctypes.c_double, P, ctypes.c_uint64], ctypes.c_int),
+    "cpic_batch_create": ([ctypes.c_int, P, ctypes.POINTER(P)], ctypes.c_int),
+    "cpic_batch_destroy": ([P], ctypes.c_int),
+    "cpic_batch_add": ([P, P], ctypes.c_int),
+    "cpic_batch_remove": ([P, P], ctypes.c_int),
+    "cpic_batch_size": ([P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "cpic_batch_step": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "cpic_batch_synchronize": ([P], ctypes.c_int),
     "cpic_vertex_field": ([P], ctypes.c_int),
     "cpic_push": ([P], ctypes.c_int),
     "cpic_deposit": ([P], ctypes.c_int),
@@ -240,6 +248,11 @@ class Run:
         v = np.ascontiguousarray(v, dtype=np.float32)
         check(load().cpic_load_particles(self.h, sp, cell.shape[0], _ptr(cell), _ptr(t), _ptr(v)))
 
+    def load_maxwellian(self, sp, n, vth, seed, drift=None):
+        """Device-side Maxwellian load of species sp, uniform in physical space."""
+        d = None if drift is None else np.ascontiguousarray(drift, dtype=np.float64)
+        check(load().cpic_load_maxwellian(self.h, sp, n, vth, _ptr(d), seed))
+
     def set_injection(self, sp, face, density, vth, seed, drift=None):
         d = None if drift is None else np.ascontiguousarray(drift, dtype=np.float64)
         check(load().cpic_set_injection(self.h, sp, face, density, vth, _ptr(d), seed))
@@ -364,3 +377,37 @@ def run_from_workload(wl, sort_interval=0, analytic=None, mg_rtol=0.0, mg_max_cy
     for (s, face, dens, vth, seed) in wl.injection:
         run.set_injection(s, face, dens, vth, seed)
     return run
+
+
+class Batch:
+    """Many runs stepped together (one CUDA graph launch per batch step)."""
+
+    def __init__(self, max_runs, stream=None):
+        h = P()
+        check(load().cpic_batch_create(max_runs, stream, ctypes.byref(h)))
+        self.h = h
+        self.runs = []
+
+    def add(self, run):
+        check(load().cpic_batch_add(self.h, run.h))
+        self.runs.append(run)
+
+    def remove(self, run):
+        check(load().cpic_batch_remove(self.h, run.h))
+        self.runs.remove(run)
+
+    def __len__(self):
+        n = ctypes.c_int()
+        check(load().cpic_batch_size(self.h, ctypes.byref(n)))
+        return n.value
+
+    def step(self, nsteps=1, solve=True):
+        check(load().cpic_batch_step(self.h, nsteps, 1 if solve else 0))
+
+    def synchronize(self):
+        check(load().cpic_batch_synchronize(self.h))
+
+    def close(self):
+        if self.h:
+            load().cpic_batch_destroy(self.h)
+            self.h = None

@@ -17,6 +17,7 @@ static thread_local char g_err[512] = "";
 static std::atomic<long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -173,6 +174,7 @@ void plan(cpic_run* r, Planner& P) {
     r->K32 = P.take<float>((size_t)r->nvert * (D == 2 ? 4 : 12));
     r->G32 = P.take<float>((size_t)r->nvert * (D == 2 ? 2 : 4));
     r->rhs_bc = P.take<double>(r->ncell);
+    r->jcdf = P.take<double>(r->ncell);
     r->charge = P.take<unsigned long long>((size_t)c.n_species * r->ncell);
     r->charge_h = P.take<unsigned long long>((size_t)c.n_species * r->ncell_h);
     long long total = 0;
@@ -318,8 +320,13 @@ int after_map(cpic_run* r) {
     CPIC_CUDA(cudaMemcpyAsync(X.data(), r->lev[0].X, sizeof(double) * X.size(), cudaMemcpyDeviceToHost, r->stream));
     CPIC_CUDA(cudaStreamSynchronize(r->stream));
     double sj = 0.0;
-    for (long long c = 0; c < r->ncell; ++c) sj += jc[c];
+    for (long long c = 0; c < r->ncell; ++c) {
+        sj += jc[c];
+        jc[c] = sj;  // inclusive prefix, for loading uniform in physical space
+    }
     r->sumJ = sj;
+    CPIC_CUDA(cudaMemcpyAsync(r->jcdf, jc.data(), sizeof(double) * r->ncell, cudaMemcpyHostToDevice, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));  // jc is a host temporary
     for (int f = 0; f < 6; ++f) r->face_len[f] = 0.0;
     if (r->D == 2) {
         int nv0 = r->n[0] + 1;
@@ -383,6 +390,8 @@ int phase(cpic_run* r, int ph, F fn) {
 }
 
 // enqueue one step's work (stream order); `sort` selects the cell sort
+}  // namespace
+
 int enqueue_step(cpic_run* r, bool sort) {
     int st = launch_vertex_field(r);
     if (st) return st;
@@ -398,6 +407,11 @@ int enqueue_step(cpic_run* r, bool sort) {
     }
     return CPIC_OK;
 }
+
+namespace {
+
+
+}  // namespace
 
 // kernel nodes of a graph (top level; a conditional node's body runs a device-decided
 // number of times and is not counted)
@@ -415,6 +429,8 @@ int count_kernel_nodes(cudaGraph_t g, int* out) {
     *out = k;
     return CPIC_OK;
 }
+
+namespace {
 
 int build_step_graph(cpic_run* r, int with_solve, int with_sort) {
     if (!r->capture_stream) CPIC_CUDA(cudaStreamCreateWithFlags(&r->capture_stream, cudaStreamNonBlocking));
@@ -685,6 +701,16 @@ int cpic_load_particles(cpic_run* r, int sp, int64_t n, const int32_t* cell, con
     // the copies above may read pageable host memory the caller frees after returning
     CPIC_CUDA(cudaStreamSynchronize(r->stream));
     return CPIC_OK;
+}
+
+int cpic_load_maxwellian(cpic_run* r, int sp, int64_t n, double vth, const double* drift, uint64_t seed) {
+    CHECK_RUN(r);
+    CHECK_MAP(r);
+    if (sp < 0 || sp >= r->cfg.n_species || n < 0 || n > r->pb.capacity[sp] || !(vth >= 0.0)) {
+        set_error("load_maxwellian: bad species, count (n = %lld) or vth", (long long)n);
+        return CPIC_ERR_INVALID;
+    }
+    return launch_load_maxwellian(r, sp, n, vth, drift, seed);
 }
 
 int cpic_get_particles(cpic_run* r, int sp, int64_t room, int64_t* n, int32_t* cell, float* t, float* v) {

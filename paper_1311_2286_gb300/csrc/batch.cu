@@ -1,0 +1,239 @@
+// Row a11: many independent runs stepped together.
+//
+// A batch step is one CUDA graph launch. The graph is captured by forking one branch per
+// member run off the batch stream (an event recorded on the batch stream, waited on by the
+// run's branch stream) and joining the branches back; each branch holds that run's whole
+// step (vertex field, push + deposit, injection, halo fold, the cell sort when it is due,
+// and, for full cycles, its field solve: the cluster kernel or the conditional V-cycle
+// loop). Branches have no dependencies on each other, so the device runs them concurrently:
+// runs far smaller than the GPU (a few thousand cells, 10^4..10^6 particles, a 16-SM solve
+// cluster) fill it together instead of one after another, and the host issues one launch
+// per batch step instead of one per kernel.
+//
+// A graph is captured once per (field solve or not, pattern of which runs sort on this
+// step) and replayed; adding or removing a run drops the cached graphs. A run must not
+// change its map or injection while it is a member, and must not be stepped on its own
+// meanwhile.
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+struct cpic_batch {
+    int max_runs = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;  // created here when the caller passed none
+    std::vector<cpic_run*> runs;
+    std::vector<cudaStream_t> branch;  // one capture branch stream per member
+    std::vector<cudaEvent_t> join;     // one join event per member
+    cudaEvent_t fork = nullptr;
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        int kernels = 0;
+    };
+    std::map<std::string, Graph> graphs;
+};
+
+namespace cpic {
+namespace {
+
+void drop_graphs(cpic_batch* b) {
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second.exec);
+    b->graphs.clear();
+}
+
+int capture(cpic_batch* b, bool solve, const std::string& key, cpic_batch::Graph* out) {
+    CPIC_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int st = CPIC_OK;
+    cudaError_t e = cudaEventRecord(b->fork, b->stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaEventRecord(fork)", __FILE__, __LINE__);
+    for (size_t i = 0; !st && i < b->runs.size(); ++i) {
+        cpic_run* r = b->runs[i];
+        e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "cudaStreamWaitEvent(fork)", __FILE__, __LINE__);
+            break;
+        }
+        cudaStream_t saved = r->stream;
+        r->stream = b->branch[i];
+        st = enqueue_step(r, key[i] == '1');
+        if (!st && solve) {
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t cg = nullptr;
+            e = cudaStreamGetCaptureInfo(r->stream, &cs, nullptr, &cg, nullptr, nullptr, nullptr);
+            if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamGetCaptureInfo", __FILE__, __LINE__);
+            else st = mg_capture_solve(r, cg, r->cfg.mg_rtol, r->cfg.mg_max_cycles);
+        }
+        r->stream = saved;
+        if (st) break;
+        e = cudaEventRecord(b->join[i], b->branch[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "join", __FILE__, __LINE__);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(batch)", __FILE__, __LINE__);
+    st = count_kernel_nodes(g, &out->kernels);
+    if (!st) {
+        e = cudaGraphInstantiate(&out->exec, g, 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphInstantiate(batch)", __FILE__, __LINE__);
+    }
+    cudaGraphDestroy(g);
+    return st;
+}
+
+}  // namespace
+}  // namespace cpic
+
+using namespace cpic;
+
+extern "C" {
+
+int cpic_batch_create(int max_runs, void* stream, cpic_batch** out) {
+    if (!out || max_runs < 1 || max_runs > 4096) {
+        set_error("batch_create: need out != NULL and 1 <= max_runs <= 4096");
+        return CPIC_ERR_INVALID;
+    }
+    cpic_batch* b = new cpic_batch;
+    b->max_runs = max_runs;
+    b->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!b->stream) {  // graphs cannot be captured on the legacy default stream
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->own_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "cudaEventCreate(fork)", __FILE__, __LINE__);
+    }
+    *out = b;
+    return CPIC_OK;
+}
+
+int cpic_batch_destroy(cpic_batch* b) {
+    if (!b) return CPIC_OK;
+    drop_graphs(b);
+    for (auto s : b->branch) cudaStreamDestroy(s);
+    for (auto ev : b->join) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return CPIC_OK;
+}
+
+int cpic_batch_add(cpic_batch* b, cpic_run* r) {
+    if (!b || !r) {
+        set_error("batch_add: NULL batch or run");
+        return CPIC_ERR_INVALID;
+    }
+    if (!r->map_set) {
+        set_error("batch_add: the run has no map yet");
+        return CPIC_ERR_STATE;
+    }
+    if ((int)b->runs.size() >= b->max_runs) {
+        set_error("batch_add: batch is full (%d runs)", b->max_runs);
+        return CPIC_ERR_CAPACITY;
+    }
+    for (auto x : b->runs)
+        if (x == r) {
+            set_error("batch_add: run is already a member");
+            return CPIC_ERR_INVALID;
+        }
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    CPIC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return cuda_fail(e, "cudaEventCreate(join)", __FILE__, __LINE__);
+    }
+    // the run's earlier work (load, initialise) is on its own stream: order the batch after it
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    b->runs.push_back(r);
+    b->branch.push_back(s);
+    b->join.push_back(ev);
+    drop_graphs(b);
+    return CPIC_OK;
+}
+
+int cpic_batch_remove(cpic_batch* b, cpic_run* r) {
+    if (!b || !r) {
+        set_error("batch_remove: NULL batch or run");
+        return CPIC_ERR_INVALID;
+    }
+    for (size_t i = 0; i < b->runs.size(); ++i)
+        if (b->runs[i] == r) {
+            CPIC_CUDA(cudaStreamSynchronize(b->stream));
+            cudaStreamDestroy(b->branch[i]);
+            cudaEventDestroy(b->join[i]);
+            b->runs.erase(b->runs.begin() + i);
+            b->branch.erase(b->branch.begin() + i);
+            b->join.erase(b->join.begin() + i);
+            drop_graphs(b);
+            return CPIC_OK;
+        }
+    set_error("batch_remove: run is not a member");
+    return CPIC_ERR_INVALID;
+}
+
+int cpic_batch_size(const cpic_batch* b, int* n) {
+    if (!b || !n) {
+        set_error("batch_size: NULL argument");
+        return CPIC_ERR_INVALID;
+    }
+    *n = (int)b->runs.size();
+    return CPIC_OK;
+}
+
+int cpic_batch_step(cpic_batch* b, int nsteps, int with_solve) {
+    if (!b || nsteps < 0) {
+        set_error("batch_step: NULL batch or negative step count");
+        return CPIC_ERR_INVALID;
+    }
+    if (b->runs.empty()) return CPIC_OK;
+    for (int k = 0; k < nsteps; ++k) {
+        std::string key(b->runs.size(), '0');
+        for (size_t i = 0; i < b->runs.size(); ++i) {
+            const cpic_run* r = b->runs[i];
+            if (r->cfg.sort_interval > 0 && r->steps_since_sort + 1 >= r->cfg.sort_interval) key[i] = '1';
+        }
+        const std::string full = (with_solve ? "S" : "P") + key;
+        auto it = b->graphs.find(full);
+        if (it == b->graphs.end()) {
+            if (b->graphs.size() >= 8) drop_graphs(b);  // bounded cache: patterns rarely vary
+            cpic_batch::Graph g;
+            int st = capture(b, with_solve != 0, key, &g);
+            if (st) return st;
+            it = b->graphs.emplace(full, g).first;
+        }
+        CPIC_CUDA(cudaGraphLaunch(it->second.exec, b->stream));
+        add_launches(it->second.kernels);
+        for (size_t i = 0; i < b->runs.size(); ++i) {
+            cpic_run* r = b->runs[i];
+            if (key[i] == '1') {
+                r->cur_host ^= 1;
+                r->steps_since_sort = 0;
+            } else {
+                ++r->steps_since_sort;
+            }
+        }
+    }
+    return CPIC_OK;
+}
+
+int cpic_batch_synchronize(cpic_batch* b) {
+    if (!b) {
+        set_error("batch_synchronize: NULL batch");
+        return CPIC_ERR_INVALID;
+    }
+    CPIC_CUDA(cudaStreamSynchronize(b->stream));
+    return CPIC_OK;
+}
+
+}  // extern "C"

@@ -26,21 +26,6 @@ namespace {
 
 using namespace pk;
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-    const unsigned M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-    const unsigned W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) {
-            k.x += W0;
-            k.y += W1;
-        }
-        unsigned hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
-        unsigned hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    }
-    return c;
-}
 
 // u -> (u + 1/2) 2^-32 in (0, 1], in FP32
 __device__ __forceinline__ float u01f(unsigned u) {

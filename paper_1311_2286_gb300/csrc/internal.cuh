@@ -29,6 +29,7 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
     } while (0)
 // every kernel launch of the library is followed by this check, which also counts it
 void count_launch();
+void add_launches(long long n);  // kernels launched by a graph replay
 #define CPIC_CHECK_LAUNCH()           \
     do {                              \
         ::cpic::count_launch();       \
@@ -133,6 +134,7 @@ struct cpic_run {
     float* K32;       // vertex k table (padded records)
     float* G32;       // vertex G table (padded records)
     double* rhs_bc;   // Dirichlet part of the right-hand side (finest)
+    double* jcdf;     // inclusive prefix sums of the cell Jacobians (device loading)
     unsigned long long* charge;  // [nsp][ncell] folded charge counts (what the field solve reads)
     unsigned long long* charge_h;  // [nsp][ncell_h] deposit grid with one halo layer per side
     long long ncell_h;
@@ -189,6 +191,10 @@ int launch_push_prep(cpic_run* r);    // zero the deposit grid and kinetic-energ
 int launch_push_kernel(cpic_run* r);  // the fused push + deposit kernel alone
 PushParams make_push_params(cpic_run* r);
 int launch_push2d(cpic_run* r, const PushParams& p);
+// one PIC step without the field solve, enqueued on r->stream (also inside stream capture)
+int enqueue_step(cpic_run* r, bool sort);
+int count_kernel_nodes(cudaGraph_t g, int* out);
+int launch_load_maxwellian(cpic_run* r, int sp, long long n, double vth, const double* drift, unsigned long long seed);
 // inject.cu
 int launch_inject(cpic_run* r);
 // sort.cu

@@ -186,6 +186,24 @@ __device__ __forceinline__ void deposit_warp(const PushParams& p, int s, bool al
     }
 }
 
+// Philox4x32-10 counter-based generator (Salmon et al., SC'11): 10 rounds of the two
+// 32x32 -> 64-bit multiplies with the published multipliers and Weyl key increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    const unsigned M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const unsigned W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += W0;
+            k.y += W1;
+        }
+        unsigned hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        unsigned hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
 // Live-slot ranges of the species in one particle kernel. The virtual index space
 // concatenates the species, each padded to a multiple of 32, so every warp holds one
 // species. Kept in named registers (no indexed local arrays).
