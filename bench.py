@@ -180,6 +180,8 @@ def main():
     ap.add_argument("--sort-interval", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-runs", type=int, default=256, help="runs of the batched configuration (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every step stream-ordered (per-phase events) instead of as one CUDA graph; "
                          "profilers cannot capture kernels inside graphs with conditional nodes")
@@ -297,6 +299,14 @@ def main():
     if not args.no_e2e:
         e2e = end_to_end(run, cpic, min(args.steps, 50), stream)
 
+    # ---- batched runs: the same full cycles, one graph launch per batch step vs the runs
+    # stepped one after another
+    batched = None
+    if args.batch_runs > 0:
+        run.close()
+        del arena
+        batched = batched_measurement(cpic, args.batch_runs, args.batch_steps, stream)
+
     # ---- CPU baseline (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -324,15 +334,72 @@ def main():
             "push_particle_steps_per_s": particles_per_push / (push_avg_ms * 1e-3),
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "batched": batched,
             "gpu_launches": int(launches),
             "gpu_launches_note": "kernels launched in the timed particle steps (kernel nodes of each replayed "
                                  "CUDA graph, counted by the library)",
             "clocks": clk,
         }
         print(json.dumps(out))
-    run.close()
+    if batched is None:
+        run.close()
     if dist:
         dist.destroy_process_group()
+
+
+def batched_measurement(cpic, nruns, steps, stream):
+    """Independent cylinder runs of uneven size (cells 32..256 x 64..512 in steps of 16, 10^4..2 10^6
+    particles per species, object potential in [-10, 2]), loaded on the device; whole PIC
+    cycles (with the field solve), aggregate particle-steps/s of one batch (one graph launch
+    per batch step) against the same runs stepped one after another on one stream."""
+    import torch
+
+    from paper_1311_2286_gb300 import workloads as wl
+
+    specs = wl.batch_specs(nruns, seed=1000)
+    cs = ctypes_stream(stream)
+    t0 = time.perf_counter()
+    runs = [cpic.cylinder_run_device(**sp, sort_interval=4, stream=cs) for sp in specs]
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+
+    def alive():
+        return sum(sum(r.diag()["n"]) for r in runs)
+
+    def timed(fn, k):
+        fn()  # warm-up (captures graphs)
+        torch.cuda.synchronize()
+        n0 = alive()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        return n0 * k / (ms * 1e-3), ms / k
+
+    def sequential():
+        for r in runs:
+            r.step(1)
+
+    seq_v, seq_ms = timed(sequential, steps)
+    batch = cpic.Batch(len(runs), stream=cs)
+    for r in runs:
+        batch.add(r)
+    bat_v, bat_ms = timed(lambda: batch.step(1), steps)
+    batch.close()
+    cells = sum(sp["n1"] * sp["n2"] for sp in specs)
+    parts = sum(2 * sp["npart_per_species"] for sp in specs)
+    for r in runs:
+        r.close()
+    return {"value": bat_v, "unit": UNIT, "ms_per_step": bat_ms, "sequential_value": seq_v,
+            "sequential_ms_per_step": seq_ms, "speedup": bat_v / seq_v, "runs": nruns, "steps": steps,
+            "particles": parts, "cells": cells, "setup_s": setup_s,
+            "workload": "independent 2D cylinder runs, cells U{32..256}xU{64..512} (steps of 16), particles per species "
+                        "U[1e4, 2e6], phi_obj U[-10, 2], seeds 1000+i, loaded on the device; full PIC cycles "
+                        "with the multigrid solve; batch = one CUDA graph launch per step, sequential = the "
+                        "runs' own graphs one after another on one stream"}
 
 
 def ctypes_stream(stream):

@@ -379,6 +379,29 @@ def run_from_workload(wl, sort_interval=0, analytic=None, mg_rtol=0.0, mg_max_cy
     return run
 
 
+def cylinder_run_device(n1, n2, npart_per_species, phi_obj, seed, sort_interval=4, arena=None, stream=None,
+                        inject=True, r0=1.0, R=40.0):
+    """A cylinder-in-plasma run (annulus map, both species) loaded on the device with
+    cpic_load_maxwellian and initialised."""
+    from . import workloads as wl
+
+    w = wl.cylinder(n1=n1, n2=n2, r0=r0, R=R, npart_per_species=npart_per_species, phi_obj=phi_obj, seed=seed,
+                    inject=inject, host_particles=False)
+    cfg = config_from_workload(w, sort_interval=sort_interval)
+    if arena is None:
+        import torch
+
+        arena = torch.empty(Run.footprint(cfg), dtype=torch.uint8, device="cuda")
+    run = Run(cfg, arena=arena, stream=stream)
+    run.set_map_analytic(CPIC_MAP_ANNULUS, [r0, R])
+    for s, sp in enumerate(w.species):
+        run.load_maxwellian(s, npart_per_species, sp.vth, seed=seed * 16 + s)
+    for (s, face, dens, vth, sd) in w.injection:
+        run.set_injection(s, face, dens, vth, sd)
+    run.initialize()
+    return run
+
+
 class Batch:
     """Many runs stepped together (one CUDA graph launch per batch step)."""
 

@@ -799,7 +799,10 @@ int enqueue_correction(cpic_run* r, const LVSet& S) {
             set_error("multigrid: coarse levels need %zu bytes of shared memory", smem);
             return CPIC_ERR_INVALID;
         }
-        CPIC_CUDA(cudaFuncSetAttribute(coarse_cycle_kernel<D, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // per-function attribute shared by every run (and by graphs captured earlier): set it
+        // to the bound checked above, not to this run's need
+        CPIC_CUDA(cudaFuncSetAttribute(coarse_cycle_kernel<D, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
         coarse_cycle_kernel<D, NPT><<<1, 512, smem, st>>>(S, nu1, nu2);
         CPIC_CHECK_LAUNCH();
         for (int l = top - 1; l >= 0; --l) {

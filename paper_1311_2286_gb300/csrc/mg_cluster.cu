@@ -479,7 +479,18 @@ int mg_cluster_prepare(cpic_run* r) {
                 continue;
             }
         }
-        CPIC_CUDA(cudaFuncSetAttribute(mg_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem));
+        // the attribute is per function, shared by every run of the process: raise it to the
+        // device's opt-in maximum once (it bounds launches, it does not change occupancy)
+        {
+            int dev = 0, optin = 0;
+            CPIC_CUDA(cudaGetDevice(&dev));
+            CPIC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            cudaFuncAttributes fa;
+            CPIC_CUDA(cudaFuncGetAttributes(&fa, mg_cluster_kernel));
+            const int dyn_max = optin - (int)fa.sharedSizeBytes;
+            if ((int)plan.smem > dyn_max) continue;
+            CPIC_CUDA(cudaFuncSetAttribute(mg_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+        }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs, 1, 1);
         cfg.blockDim = dim3(CL_THREADS, 1, 1);

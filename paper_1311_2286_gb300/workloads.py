@@ -284,18 +284,23 @@ def langmuir_map2(n1=32, n2=32, eps=0.05, ppc=64, vth=0.05, amp=0.01, dt=0.1, se
 
 
 def cylinder(n1=128, n2=256, r0=1.0, R=40.0, npart_per_species=2_000_000, phi_obj=-5.0,
-             mass_ratio=1836.0, dt=0.1, seed=1, inject=True, capacity_factor=1.5):
+             mass_ratio=1836.0, dt=0.1, seed=1, inject=True, capacity_factor=1.5, host_particles=True):
     """2D cylinder in plasma on the log-polar annulus: object at xi = 0 held at phi_obj and
     absorbing, outer boundary at xi = 1 (phi = 0, absorbing, Maxwellian flux injection),
     eta periodic. Electrons (q = -1, m = 1, vth = 1) and ions (q = +1, m = mass_ratio,
-    T_i = T_e). Loaded uniform in physical space at density 1."""
+    T_i = T_e). Loaded uniform in physical space at density 1. host_particles=False leaves
+    the particle sets empty (the run is loaded on the device with cpic_load_maxwellian)."""
     rng = np.random.default_rng(seed)
     area = math.pi * (R * R - r0 * r0)
     w = area / npart_per_species
     vti = 1.0 / math.sqrt(mass_ratio)
     cap = int(npart_per_species * capacity_factor)
     sp = [Species(-1.0, 1.0, w, 1.0, cap), Species(1.0, mass_ratio, w, vti, cap)]
-    parts = [load_annulus(rng, n1, n2, r0, R, npart_per_species, s.vth) for s in sp]
+    if host_particles:
+        parts = [load_annulus(rng, n1, n2, r0, R, npart_per_species, s.vth) for s in sp]
+    else:
+        parts = [ParticleSet(np.zeros(0, np.int32), np.zeros((2, 0), np.float32), np.zeros((3, 0), np.float32))
+                 for _ in sp]
     inj = []
     if inject:
         inj = [(0, 1, 1.0, 1.0, seed * 1000 + 7), (1, 1, 1.0, vti, seed * 1000 + 8)]
@@ -324,3 +329,20 @@ def random_field(rng, shape, scale=1.0):
             acc += np.roll(base, 1, axis=ax) + np.roll(base, -1, axis=ax)
         base = acc / (1 + 2 * base.ndim)
     return scale * base
+
+
+def batch_specs(nruns, seed=1000):
+    """Independent cylinder runs of uneven size (the batched configuration): cells
+    N1 x N2 uniform in {32..256} x {64..512} in steps of 16 (so that the multigrid
+    hierarchy halves down to its dense coarse solve of at most 512 cells), particles per
+    species uniform in [10^4, 2 10^6], object potential uniform in [-10, +2], run i
+    seeded seed + i."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nruns):
+        n1 = int(rng.integers(2, 17)) * 16
+        n2 = int(rng.integers(4, 33)) * 16
+        npart = int(rng.integers(10_000, 2_000_001))
+        phi = float(rng.uniform(-10.0, 2.0))
+        out.append(dict(n1=n1, n2=n2, npart_per_species=npart, phi_obj=phi, seed=seed + i))
+    return out
