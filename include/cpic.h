@@ -277,6 +277,67 @@ int cpic_batch_size(const cpic_batch* batch, int* n);
 int cpic_batch_step(cpic_batch* batch, int nsteps, int with_solve);
 int cpic_batch_synchronize(cpic_batch* batch);
 
+/* ---------------------------------------------------------------- served runs (row a12) */
+
+/* A server runs parametric requests with continuous batching: requests queue on submit, a
+ * scheduler thread admits them while a slot is free and the server's device pool holds the
+ * run's footprint (first fit, smaller requests may pass one that does not fit yet), keeps
+ * each admitted run's particles and fields on the device, advances all active runs a slice
+ * of steps at a time on their own streams (their work overlaps on the GPU), and files each
+ * result when its run has taken all its steps. A run's arithmetic is cpic_step's, so its
+ * result does not depend on the other requests. Not in the paper (its runs are single
+ * simulations). */
+typedef struct cpic_server cpic_server;
+
+#define CPIC_REQ_CYLINDER 0 /* 2D cylinder in plasma (annulus map, object at xi = 0, injection at xi = 1) */
+#define CPIC_REQ_SPHERE 1   /* 3D sphere in plasma: not built (CPIC_ERR_NOT_BUILT) */
+
+typedef struct cpic_server_opts {
+    size_t hbm_budget;     /* bytes of the device pool (0: half of the free device memory) */
+    int32_t max_active;    /* runs on the device at once (0: 64) */
+    int32_t steps_per_slice; /* steps a run advances per scheduling turn (0: 10) */
+    int32_t sort_interval; /* cell sort interval of the runs (0: 4) */
+} cpic_server_opts;
+
+typedef struct cpic_request {
+    int32_t kind;                  /* CPIC_REQ_* */
+    int32_t n[3];                  /* cells per logical axis (radial, azimuthal[, polar]) */
+    int64_t particles_per_species; /* initial macro-particles of electrons and of ions */
+    double phi_object;             /* object potential (Dirichlet), in kT_e/e */
+    double density;                /* plasma density (1 = the normalisation density) */
+    double temperature;            /* electron temperature (1 = normalisation; vth_e = sqrt(T)) */
+    double mass_ratio;             /* m_i / m_e (T_i = T_e) */
+    double r_object, r_outer;      /* object and outer radius (Debye lengths) */
+    double dt;                     /* time step (1/omega_pe) */
+    int32_t steps;                 /* PIC cycles to run */
+    uint64_t seed;                 /* load and injection streams */
+} cpic_request;
+
+typedef struct cpic_result {
+    int32_t status;                /* CPIC_OK or the run's failure */
+    uint64_t ticket;
+    int32_t steps;                 /* cycles taken */
+    double queue_s;                /* submit -> admission */
+    double latency_s;              /* submit -> result (time-to-result) */
+    int64_t particle_steps;        /* sum over the cycles of the live particles */
+    double field_energy, kinetic_energy;
+    int64_t n_particles[2], absorbed_object[2], absorbed_outer[2], injected[2];
+    double current_object[2];      /* collected current per species, q w absorbed / (steps dt) */
+    int32_t mg_cycles;             /* V-cycles of the last solve */
+} cpic_result;
+
+int cpic_server_start(const cpic_server_opts* opts, cpic_server** out);
+/* Queues a request (host memory, copied); ticket receives its id. CPIC_ERR_CAPACITY when
+ * the run cannot fit the pool at all; CPIC_ERR_NOT_BUILT for sphere requests. */
+int cpic_server_submit(cpic_server* server, const cpic_request* req, uint64_t* ticket);
+/* CPIC_OK and the result once the run is done (the ticket is then retired), CPIC_ERR_BUSY
+ * while it is queued or running, CPIC_ERR_INVALID for an unknown ticket. */
+int cpic_server_poll(cpic_server* server, uint64_t ticket, cpic_result* out);
+/* Requests queued, runs active, free bytes of the pool (any pointer may be NULL). */
+int cpic_server_stats(cpic_server* server, int* queued, int* active, size_t* pool_free);
+/* Stops the scheduler; active runs are finished on the device and discarded. */
+int cpic_server_stop(cpic_server* server);
+
 /* ---------------------------------------------------------------- tracing */
 
 /* Phases of cpic_step timed with CUDA events recorded on the run's stream. */

@@ -62,6 +62,55 @@ class cpic_diag(ctypes.Structure):
     ]
 
 
+CPIC_REQ_CYLINDER = 0
+CPIC_REQ_SPHERE = 1
+
+
+class cpic_server_opts(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget", ctypes.c_size_t),
+        ("max_active", ctypes.c_int32),
+        ("steps_per_slice", ctypes.c_int32),
+        ("sort_interval", ctypes.c_int32),
+    ]
+
+
+class cpic_request(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("n", ctypes.c_int32 * 3),
+        ("particles_per_species", ctypes.c_int64),
+        ("phi_object", ctypes.c_double),
+        ("density", ctypes.c_double),
+        ("temperature", ctypes.c_double),
+        ("mass_ratio", ctypes.c_double),
+        ("r_object", ctypes.c_double),
+        ("r_outer", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("steps", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class cpic_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("ticket", ctypes.c_uint64),
+        ("steps", ctypes.c_int32),
+        ("queue_s", ctypes.c_double),
+        ("latency_s", ctypes.c_double),
+        ("particle_steps", ctypes.c_int64),
+        ("field_energy", ctypes.c_double),
+        ("kinetic_energy", ctypes.c_double),
+        ("n_particles", ctypes.c_int64 * 2),
+        ("absorbed_object", ctypes.c_int64 * 2),
+        ("absorbed_outer", ctypes.c_int64 * 2),
+        ("injected", ctypes.c_int64 * 2),
+        ("current_object", ctypes.c_double * 2),
+        ("mg_cycles", ctypes.c_int32),
+    ]
+
+
 _lib = None
 P = ctypes.c_void_p
 _SIGS = {
@@ -90,6 +139,12 @@ _SIGS = {
     "cpic_batch_size": ([P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "cpic_batch_step": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "cpic_batch_synchronize": ([P], ctypes.c_int),
+    "cpic_server_start": ([P, ctypes.POINTER(P)], ctypes.c_int),
+    "cpic_server_submit": ([P, P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "cpic_server_poll": ([P, ctypes.c_uint64, P], ctypes.c_int),
+    "cpic_server_stats": ([P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "cpic_server_stop": ([P], ctypes.c_int),
     "cpic_vertex_field": ([P], ctypes.c_int),
     "cpic_push": ([P], ctypes.c_int),
     "cpic_deposit": ([P], ctypes.c_int),
@@ -433,4 +488,70 @@ class Batch:
     def close(self):
         if self.h:
             load().cpic_batch_destroy(self.h)
+            self.h = None
+
+
+def make_request(n1=64, n2=128, particles_per_species=100_000, phi_object=-5.0, density=1.0, temperature=1.0,
+                 mass_ratio=1836.0, r_object=1.0, r_outer=40.0, dt=0.1, steps=100, seed=1, kind=CPIC_REQ_CYLINDER):
+    q = cpic_request()
+    q.kind = kind
+    q.n[0], q.n[1], q.n[2] = n1, n2, 1
+    q.particles_per_species = particles_per_species
+    q.phi_object = phi_object
+    q.density = density
+    q.temperature = temperature
+    q.mass_ratio = mass_ratio
+    q.r_object, q.r_outer = r_object, r_outer
+    q.dt = dt
+    q.steps = steps
+    q.seed = seed
+    return q
+
+
+class Server:
+    """Request loop with continuous batching (cpic_server_*)."""
+
+    def __init__(self, hbm_budget=0, max_active=0, steps_per_slice=0, sort_interval=0):
+        o = cpic_server_opts(hbm_budget, max_active, steps_per_slice, sort_interval)
+        h = P()
+        check(load().cpic_server_start(ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, req) -> int:
+        t = ctypes.c_uint64()
+        check(load().cpic_server_submit(self.h, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        """The result as a dict once done, else None."""
+        r = cpic_result()
+        st = load().cpic_server_poll(self.h, ticket, ctypes.byref(r))
+        if st == CPIC_ERR_BUSY:
+            return None
+        check(st)
+        out = {k: getattr(r, k) for k, _ in cpic_result._fields_}
+        for k in ("n_particles", "absorbed_object", "absorbed_outer", "injected", "current_object"):
+            out[k] = list(out[k])
+        return out
+
+    def wait(self, ticket, timeout=600.0, interval=1e-3):
+        import time
+
+        t0 = time.perf_counter()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.perf_counter() - t0 > timeout:
+                raise TimeoutError(f"ticket {ticket} not done after {timeout} s")
+            time.sleep(interval)
+
+    def stats(self):
+        q, a, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        check(load().cpic_server_stats(self.h, ctypes.byref(q), ctypes.byref(a), ctypes.byref(f)))
+        return {"queued": q.value, "active": a.value, "pool_free": f.value}
+
+    def stop(self):
+        if self.h:
+            load().cpic_server_stop(self.h)
             self.h = None
