@@ -182,6 +182,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=256, help="runs of the batched configuration (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--serve-requests", type=int, default=64, help="requests of the serving run (0: skip)")
+    ap.add_argument("--serve-steps", type=int, default=200, help="PIC cycles per request")
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second (Poisson)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every step stream-ordered (per-phase events) instead of as one CUDA graph; "
                          "profilers cannot capture kernels inside graphs with conditional nodes")
@@ -307,6 +310,11 @@ def main():
         del arena
         batched = batched_measurement(cpic, args.batch_runs, args.batch_steps, stream)
 
+    # ---- served runs: open-loop Poisson arrivals, continuous batching
+    served = None
+    if args.serve_requests > 0:
+        served = serving_measurement(cpic, args.serve_requests, args.serve_steps, args.serve_rate)
+
     # ---- CPU baseline (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -335,6 +343,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "batched": batched,
+            "served": served,
             "gpu_launches": int(launches),
             "gpu_launches_note": "kernels launched in the timed particle steps (kernel nodes of each replayed "
                                  "CUDA graph, counted by the library)",
@@ -400,6 +409,63 @@ def batched_measurement(cpic, nruns, steps, stream):
                         "U[1e4, 2e6], phi_obj U[-10, 2], seeds 1000+i, loaded on the device; full PIC cycles "
                         "with the multigrid solve; batch = one CUDA graph launch per step, sequential = the "
                         "runs' own graphs one after another on one stream"}
+
+
+def serving_measurement(cpic, nreq, steps, rate, seed=4):
+    """Cylinder-in-plasma requests arriving open loop (Poisson, `rate` per second): scale
+    s ~ U[0.25, 1] on the particle count (2M s per species) and on the cells (128 x 256
+    times sqrt(s) per axis, rounded to multiples of 16), object potential U[-10, 2],
+    `steps` PIC cycles each. Time-to-result percentiles and aggregate particle-steps/s."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(nreq):
+        sc = float(rng.uniform(0.25, 1.0))
+        f = math.sqrt(sc)
+        n1 = max(32, int(round(128 * f / 16)) * 16)
+        n2 = max(64, int(round(256 * f / 16)) * 16)
+        reqs.append(cpic.make_request(n1=n1, n2=n2, particles_per_species=int(2_000_000 * sc),
+                                      phi_object=float(rng.uniform(-10, 2)), steps=steps, seed=4000 + i))
+    gaps = rng.exponential(1.0 / rate, nreq)
+    sv = cpic.Server(hbm_budget=0, max_active=64, steps_per_slice=10)
+    t0 = time.perf_counter()
+    tickets = []
+    arrive = t0
+    pending = {}
+    results = []
+    for i, q in enumerate(reqs):
+        arrive += gaps[i]
+        while time.perf_counter() < arrive:
+            for tk in list(pending):
+                r = sv.poll(tk)
+                if r is not None:
+                    results.append(r)
+                    del pending[tk]
+            time.sleep(2e-4)
+        tk = sv.submit(q)
+        pending[tk] = True
+        tickets.append(tk)
+    last_arrival = time.perf_counter() - t0
+    while pending:
+        for tk in list(pending):
+            r = sv.poll(tk)
+            if r is not None:
+                results.append(r)
+                del pending[tk]
+        time.sleep(1e-3)
+    wall = time.perf_counter() - t0
+    sv.stop()
+    lat = np.array([r["latency_s"] for r in results])
+    qs = np.array([r["queue_s"] for r in results])
+    ps = float(sum(r["particle_steps"] for r in results))
+    bad = sum(1 for r in results if r["status"] != 0)
+    return {"requests": nreq, "steps_per_request": steps, "arrival_rate_per_s": rate,
+            "offered_s": last_arrival, "wall_s": wall, "served_per_s": nreq / wall,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "queue_p50_s": float(np.percentile(qs, 50)), "queue_p99_s": float(np.percentile(qs, 99)),
+            "value": ps / wall, "unit": UNIT, "failed": bad,
+            "workload": "2D cylinder requests, open-loop Poisson arrivals; scale U[0.25, 1] on particles "
+                        "(2M per species at 1) and cells (128x256 at 1, multiples of 16); phi_obj U[-10, 2]; "
+                        "continuous batching, admission by device footprint (half the free memory)"}
 
 
 def ctypes_stream(stream):
