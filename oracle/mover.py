@@ -15,6 +15,13 @@ physical velocity. One push (eqs. (step1)-(step4), unmagnetised):
      the particle (Sec. II.B.4: leaving the domain means a logical coordinate < 0 or > 1;
      an offset of exactly 0 on cell 0 is inside, a coordinate of exactly 1 is outside).
 A predictor point outside a non-periodic axis is clamped to the boundary (reading).
+Spec B (reflecting axes; the paper reflects at the axis of its spherical runs, Sec. III.B,
+without a formula): a corrector position outside a reflecting axis is mirrored in logical
+space about the face, u -> -u below and u -> 2N - u above (on the split representation:
+cell -1 - c or 2N - 1 - c, offset 1 - t, renormalised), and the velocity is reflected about
+the unit normal of that face, n = row a of k(xi') (the k the corrector used) normalised:
+v <- v - 2 (v.n) n / (n.n). A particle still outside after one mirror is removed at that
+face. The kinetic-energy tally uses the kicked velocity, before any reflection.
 """
 from __future__ import annotations
 
@@ -57,10 +64,11 @@ def _renorm(x):
     return c.astype(np.int64), f
 
 
-def push64(idx, t, v, k, G, dt, qm, n, pbc):
+def push64(idx, t, v, k, G, dt, qm, n, pbc, return_kicked=False):
     """One FP64 push. idx (D, n) int, t (D, n), v (3, n); k: vertex table (..., a, alpha);
     G: vertex table (..., a); qm: q/m per particle (n,) or scalar.
-    Returns (idx, t, v, face) with face = -1 alive or 2a+side for removed particles."""
+    Returns (idx, t, v, face) with face = -1 alive or 2a+side for removed particles, plus
+    the kicked velocity before any reflection when return_kicked."""
     D = idx.shape[0]
     idx = idx.astype(np.int64)
     t = np.asarray(t, dtype=np.float64)
@@ -89,11 +97,36 @@ def push64(idx, t, v, k, G, dt, qm, n, pbc):
     for a in range(D):
         if pbc[2 * a] == PBC_PERIODIC:
             inew[a] = np.mod(inew[a], n[a])
-        else:
+        elif pbc[2 * a] == PBC_ABSORB:
             lo = (inew[a] < 0) & (face < 0)
             hi = (inew[a] >= n[a]) & (face < 0)
             face[lo] = 2 * a
             face[hi] = 2 * a + 1
+    ke_v = v.copy()
+    for a in range(D):
+        if pbc[2 * a] != PBC_REFLECT:
+            continue
+        below = (inew[a] < 0) & (face < 0)
+        above = (inew[a] >= n[a]) & (face < 0)
+        out = below | above
+        if not np.any(out):
+            continue
+        c2 = np.where(below, -inew[a] - 1, 2 * n[a] - 1 - inew[a])
+        c_add, t2 = _renorm(1.0 - tn[a])
+        c2 = c2 + c_add
+        still = out & ((c2 < 0) | (c2 >= n[a]))
+        face[still & below] = 2 * a
+        face[still & above] = 2 * a + 1
+        ok = out & ~still
+        inew[a] = np.where(ok, c2, inew[a])
+        tn[a] = np.where(ok, t2, tn[a])
+        nv = kq[:, a, :]  # (n, alpha): row a of k(xi')
+        nn = np.sum(nv * nv, axis=1)
+        dot = np.sum(v[:D].T * nv, axis=1)
+        sfac = np.where(ok, 2.0 * dot / nn, 0.0)
+        v[:D] = v[:D] - (sfac[:, None] * nv).T
+    if return_kicked:
+        return inew, tn, v, face, ke_v
     return inew, tn, v, face
 
 

@@ -30,6 +30,7 @@
 
 #define PBC_PERIODIC 0
 #define PBC_ABSORB 1
+#define PBC_REFLECT 2
 
 static int wrap(int c, int n) {
     int r = c % n;
@@ -152,6 +153,8 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
             for (int a = 0; a < D; ++a) {
                 if (pbc[2 * a] == PBC_PERIODIC) {
                     cn[a] = wrap(cn[a], n[a]);
+                } else if (pbc[2 * a] == PBC_REFLECT) {
+                    continue; /* mirrored after the kinetic-energy tally */
                 } else if (cn[a] < 0) {
                     if (fc < 0) fc = 2 * a;
                 } else if (cn[a] >= n[a]) {
@@ -161,6 +164,33 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
         }
         float ke = fmaf(vo[2], vv[2], fmaf(vo[1], vv[1], vo[0] * vv[0]));
         ke_fp[p] = llrintf(ldexpf(ke, 24));
+        /* spec B: mirror about a reflecting face, reflect v about row a of k(xi') */
+        if (fc < 0) {
+            for (int a = 0; a < D && fc < 0; ++a) {
+                if (pbc[2 * a] != PBC_REFLECT || (cn[a] >= 0 && cn[a] < n[a])) continue;
+                int below = cn[a] < 0;
+                int c2 = below ? (-cn[a] - 1) : (2 * n[a] - 1 - cn[a]);
+                float t2 = 1.0f - tn[a];
+                if (t2 >= 1.0f) {
+                    t2 = 0.0f;
+                    c2 += 1;
+                }
+                if (c2 < 0 || c2 >= n[a]) {
+                    fc = 2 * a + (below ? 0 : 1);
+                    break;
+                }
+                cn[a] = c2;
+                tn[a] = t2;
+                float nn = kq[a * D + 0] * kq[a * D + 0];
+                float dot = vv[0] * kq[a * D + 0];
+                for (int al = 1; al < D; ++al) {
+                    nn = fmaf(kq[a * D + al], kq[a * D + al], nn);
+                    dot = fmaf(vv[al], kq[a * D + al], dot);
+                }
+                float sf = (2.0f * dot) / nn;
+                for (int al = 0; al < D; ++al) vv[al] = fmaf(-sf, kq[a * D + al], vv[al]);
+            }
+        }
         face[p] = fc;
         for (int a = 0; a < D; ++a) {
             idx[a * np + p] = fc < 0 ? cn[a] : -1;

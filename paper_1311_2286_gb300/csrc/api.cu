@@ -75,10 +75,10 @@ int validate(const cpic_config* c) {
                 set_error("face %d: particle boundary must be periodic exactly when the field is", 2 * a + s);
                 return CPIC_ERR_INVALID;
             }
-            if (pb == CPIC_PBC_REFLECT) {
-                set_error("face %d: specular reflection is not built in this version", 2 * a + s);
-                return CPIC_ERR_NOT_BUILT;
-            }
+        }
+        if (c->particle_bc[2 * a] != c->particle_bc[2 * a + 1]) {
+            set_error("axis %d: different particle boundary kinds on its two faces are not built", a);
+            return CPIC_ERR_NOT_BUILT;
         }
         if (p0 && (c->n[a] & 1)) {
             set_error("axis %d: a periodic axis needs an even cell count", a);

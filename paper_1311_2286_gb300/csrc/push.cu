@@ -219,6 +219,8 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
                 for (int a = 0; a < D; ++a) {
                     if (p.pbc[2 * a] == CPIC_PBC_PERIODIC) {
                         cn[a] = wrapi(cn[a], p.n[a]);
+                    } else if (p.pbc[2 * a] == CPIC_PBC_REFLECT) {
+                        continue;  // mirrored below, after the kinetic-energy tally
                     } else if (cn[a] < 0) {
                         if (face < 0) face = 2 * a;
                     } else if (cn[a] >= p.n[a]) {
@@ -226,11 +228,43 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
                     }
                 }
             }
-            alive = face < 0;
             // spec D: v_old . v_new as an FP32 fma chain, then round(x 2^24) to int64 (FP64
             // throughput on this part is ~1/64 of FP32, so the product stays in FP32)
             float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
             tally.ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
+            // spec B: a reflecting face mirrors the position in logical space (u -> -u below,
+            // u -> 2N - u above) and reflects v about row a of k(xi'); still outside after one
+            // mirror: removed at that face
+            if (face < 0) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    if (face >= 0 || p.pbc[2 * a] != CPIC_PBC_REFLECT || (cn[a] >= 0 && cn[a] < p.n[a])) continue;
+                    const bool below = cn[a] < 0;
+                    int c2 = below ? (-cn[a] - 1) : (2 * p.n[a] - 1 - cn[a]);
+                    float t2 = __fsub_rn(1.0f, tn[a]);
+                    if (t2 >= 1.0f) {
+                        t2 = 0.0f;
+                        c2 += 1;
+                    }
+                    if (c2 < 0 || c2 >= p.n[a]) {
+                        face = 2 * a + (below ? 0 : 1);
+                        continue;
+                    }
+                    cn[a] = c2;
+                    tn[a] = t2;
+                    float nn = __fmul_rn(kq[a * D], kq[a * D]);
+                    float dot = __fmul_rn(v[0], kq[a * D]);
+#pragma unroll
+                    for (int al = 1; al < D; ++al) {
+                        nn = __fmaf_rn(kq[a * D + al], kq[a * D + al], nn);
+                        dot = __fmaf_rn(v[al], kq[a * D + al], dot);
+                    }
+                    const float sf = __fdiv_rn(__fmul_rn(2.0f, dot), nn);
+#pragma unroll
+                    for (int al = 0; al < D; ++al) v[al] = __fmaf_rn(-sf, kq[a * D + al], v[al]);
+                }
+            }
+            alive = face < 0;
             // store
             cellp[slot] = alive ? encode<D>(cn) : -1;
 #pragma unroll
@@ -361,7 +395,12 @@ int launch_push_prep(cpic_run* r) {
 }
 
 int launch_push_kernel(cpic_run* r) {
-    return r->D == 2 ? launch_push2d(r, make_push_params(r)) : launch_particles<0>(r, 0, 0, 0, 0);
+    // the specialised 2D kernel covers periodic and absorbing axes; reflecting ones take the
+    // generic kernel
+    bool reflect = false;
+    for (int f = 0; f < 2 * r->D; ++f) reflect = reflect || r->cfg.particle_bc[f] == CPIC_PBC_REFLECT;
+    if (r->D == 2 && !reflect) return launch_push2d(r, make_push_params(r));
+    return launch_particles<0>(r, 0, 0, 0, 0);
 }
 
 int launch_push(cpic_run* r) {

@@ -396,6 +396,7 @@ int launch_push2d_t(cpic_run* r, const PushParams& p) {
 
 int launch_push2d(cpic_run* r, const PushParams& p) {
     const bool per0 = p.pbc[0] == CPIC_PBC_PERIODIC, per1 = p.pbc[2] == CPIC_PBC_PERIODIC;
+    if (p.pbc[0] == CPIC_PBC_REFLECT || p.pbc[2] == CPIC_PBC_REFLECT) return CPIC_ERR_NOT_BUILT;
     if (per0) return per1 ? launch_push2d_t<true, true>(r, p) : launch_push2d_t<true, false>(r, p);
     return per1 ? launch_push2d_t<false, true>(r, p) : launch_push2d_t<false, false>(r, p);
 }

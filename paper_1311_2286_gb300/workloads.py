@@ -319,6 +319,63 @@ def cylinder(n1=128, n2=256, r0=1.0, R=40.0, npart_per_species=2_000_000, phi_ob
     )
 
 
+def sphere(n1=128, n2=128, n3=128, r0=1.0, R=30.0, theta_c=math.pi / 32, npart_per_species=32_000_000,
+           phi_obj=-5.0, mass_ratio=1836.0, dt=0.1, seed=2, capacity_factor=1.5, host_particles=True):
+    """3D sphere in plasma on the shell map r = r0 (R/r0)^xi, theta = theta_c + (pi -
+    2 theta_c) eta, phi = 2 pi zeta (polar caps cut out): object at xi = 0 held at phi_obj
+    and absorbing, outer boundary at 0 and absorbing, polar caps Neumann for the field and
+    specular for particles, zeta periodic. Electrons and ions (T_i = T_e), uniform in
+    physical space at density 1."""
+    rng = np.random.default_rng(seed)
+    vol = (4.0 / 3.0) * math.pi * (R**3 - r0**3) * math.cos(theta_c)
+    w = vol / npart_per_species
+    vti = 1.0 / math.sqrt(mass_ratio)
+    cap = int(npart_per_species * capacity_factor)
+    sp = [Species(-1.0, 1.0, w, 1.0, cap), Species(1.0, mass_ratio, w, vti, cap)]
+    n = (n1, n2, n3)
+    if host_particles:
+        parts = [load_shell(rng, n, r0, R, theta_c, npart_per_species, s.vth) for s in sp]
+    else:
+        parts = [ParticleSet(np.zeros(0, np.int32), np.zeros((3, 0), np.float32), np.zeros((3, 0), np.float32))
+                 for _ in sp]
+    return Workload(
+        name=f"sphere_{n1}x{n2}x{n3}_{2 * npart_per_species}",
+        dim=3,
+        n=n,
+        vertices=shell_vertices(n1, n2, n3, r0, R, theta_c),
+        field_bc=[BC_DIRICHLET, BC_DIRICHLET, BC_NEUMANN, BC_NEUMANN, BC_PERIODIC, BC_PERIODIC],
+        field_bc_value=[phi_obj, 0.0, 0.0, 0.0, 0.0, 0.0],
+        particle_bc=[PBC_ABSORB, PBC_ABSORB, PBC_REFLECT, PBC_REFLECT, PBC_PERIODIC, PBC_PERIODIC],
+        dt=dt,
+        species=sp,
+        particles=parts,
+    )
+
+
+def box_reflect(n1=32, n2=32, npart=50_000, vth=1.0, dt=0.1, seed=7):
+    """2D unit square (uniform map) with specular walls on axis 0 (Neumann field) and a
+    periodic axis 1; one electron species at a neutralising background."""
+    rng = np.random.default_rng(seed)
+    X = map2_vertices(n1, n2, 0.0)
+    u = np.stack([rng.random(npart) * n1, rng.random(npart) * n2])
+    u[0] = np.minimum(u[0], np.nextafter(n1, 0))
+    ps = _from_logical(u, (n1, n2), maxwellian(rng, npart, vth))
+    w = 1.0 / npart
+    return Workload(
+        name=f"box_reflect_{n1}x{n2}",
+        dim=2,
+        n=(n1, n2),
+        vertices=X,
+        field_bc=[BC_NEUMANN, BC_NEUMANN, BC_PERIODIC, BC_PERIODIC],
+        field_bc_value=[0.0, 0.0, 0.0, 0.0],
+        particle_bc=[PBC_REFLECT, PBC_REFLECT, PBC_PERIODIC, PBC_PERIODIC],
+        dt=dt,
+        species=[Species(-1.0, 1.0, w, vth, int(npart * 1.5))],
+        particles=[ps],
+        background=1.0,
+    )
+
+
 def random_field(rng, shape, scale=1.0):
     """A smooth-ish random cell-centred potential for frozen-field mover tests."""
     base = rng.standard_normal(shape)

@@ -39,7 +39,12 @@ def _cylinder(n1=64, n2=128, npart=200_003, phi_obj=-5.0, seed=5, inject=False):
 CASES = {
     "map2_periodic": lambda: wl.langmuir_map2(32, 32, eps=0.05, ppc=100, vth=0.3, amp=0.01, dt=0.1, seed=3),
     "cylinder": lambda: _cylinder(),
+    # specular walls (spec B) on axis 0, fast particles (up to several cells per step)
+    "box_reflect": lambda: wl.box_reflect(32, 32, 60_000, vth=2.0, seed=7),
+    # 3D sphere in plasma: absorbing radial faces, reflecting polar caps, periodic azimuth
+    "sphere3d": lambda: wl.sphere(16, 16, 16, npart_per_species=20_000, seed=5),
 }
+DIRICHLET_AXIS0 = {"cylinder", "sphere3d"}
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -111,32 +116,43 @@ def test_push_bit_exact_vs_replay(cpic, case, sort_first):
     w = CASES[case]()
     rng = np.random.default_rng(2)
     phi = wl.random_field(rng, tuple(reversed(w.n)), 0.5)
-    if case == "cylinder":
-        phi = phi + np.linspace(-5, 0, w.n[0])[None, :]
+    if case in DIRICHLET_AXIS0:
+        phi = phi + np.linspace(-5, 0, w.n[0])
     g, per, pre, post, charge, d, k32, G32 = _push_case(cpic, w, phi, sort_first)
     ke_total = 0.0
+    D = w.dim
     for s, sp in enumerate(w.species):
         cell0, t0, v0 = pre[s]
-        idx = _unpack(cell0)
+        idx = _unpack(cell0, D)
         i32, t32, v32, face, kefp = mover.push32(idx, t0, v0, k32, G32, w.n, w.particle_bc,
                                                 np.float32(w.dt * sp.q / sp.m), np.float32(0.5 * w.dt),
                                                 np.float32(w.dt))
         alive = face < 0
-        ref_cell = (i32[0] | (i32[1] << 16))[alive].astype(np.int32)
+        ref_cell = wl.pack_cells(i32[:, alive])
         cell1, t1, v1 = post[s]
         assert cell1.shape == ref_cell.shape
         assert np.array_equal(cell1, ref_cell)
         assert np.array_equal(t1, t32[:, alive])
         assert np.array_equal(v1, v32[:, alive])
-        for f in range(4):
+        for f in range(2 * D):
             assert d["absorbed"][s][f] == int(np.sum(face == f)), (s, f)
         Cref = odep.deposit_fixed(i32[:, alive].astype(np.int64), t32[:, alive], w.n, per)
         assert np.array_equal(charge[s], Cref)
         ke_total += 0.5 * sp.m * sp.w * math.ldexp(float(int(kefp.sum())), -24)
         assert d["n"][s] == int(alive.sum())
     assert d["W_K"] == pytest.approx(ke_total, rel=1e-15, abs=1e-300)
-    if case == "cylinder":
+    if case in DIRICHLET_AXIS0:
         assert sum(d["absorbed"][0]) > 0  # the case exercises absorption
+    if case in ("box_reflect", "sphere3d"):
+        # the case exercises reflection: some particle left and re-entered a reflecting axis
+        cell0, t0, v0 = pre[0]
+        idx = _unpack(cell0, D)
+        i64, t64, v64, face, vk = mover.push64(idx, t0.astype(np.float64), v0.astype(np.float64), g.k,
+                                               gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value), w.dt,
+                                               w.species[0].q / w.species[0].m, w.n, w.particle_bc,
+                                               return_kicked=True)
+        reflected = np.any(v64[:D] != vk[:D], axis=0) & (face < 0)
+        assert np.sum(reflected) > 0
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -148,9 +164,10 @@ def test_push_vs_fp64_single_step(cpic, case):
     phi = wl.random_field(rng, tuple(reversed(w.n)), 0.5)
     g, per, pre, post, charge, d, k32, G32 = _push_case(cpic, w, phi)
     G64 = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value)
+    D = w.dim
     for s, sp in enumerate(w.species):
         cell0, t0, v0 = pre[s]
-        idx = _unpack(cell0)
+        idx = _unpack(cell0, D)
         i64, t64, v64, face = mover.push64(idx, t0.astype(np.float64), v0.astype(np.float64), g.k, G64, w.dt,
                                            sp.q / sp.m, w.n, w.particle_bc)
         alive64 = face < 0
@@ -158,11 +175,13 @@ def test_push_vs_fp64_single_step(cpic, case):
         n_mismatch = abs(int(alive64.sum()) - cell1.shape[0])
         assert n_mismatch <= 2
         if n_mismatch == 0:
-            i1 = _unpack(cell1)
+            i1 = _unpack(cell1, D)
             u32 = (i1 + t1.astype(np.float64)) / np.array(w.n)[:, None]
             u64 = (i64[:, alive64] + t64[:, alive64]) / np.array(w.n)[:, None]
             du = np.abs(u32 - u64)
-            du = np.minimum(du, 1.0 - du) if case == "map2_periodic" else du
+            for a in range(D):
+                if w.particle_bc[2 * a] == wl.PBC_PERIODIC:
+                    du[a] = np.minimum(du[a], 1.0 - du[a])
             assert np.max(du) / np.max(np.abs(u64)) <= 1e-5
             dv = np.abs(v1.astype(np.float64) - v64[:, alive64])
             assert np.max(dv) / np.max(np.abs(v64)) <= 1e-5

@@ -171,3 +171,62 @@ def test_replay32_deterministic_and_absorbs():
     for x, y in zip(a, b):
         np.testing.assert_array_equal(x, y)
     assert list(a[3]) == [0, 1] and list(a[0][0]) == [-1, -1]
+
+
+def test_reflection_is_an_elastic_wall_on_the_uniform_map():
+    """Spec B on the uniform map (k = N I, the textbook Cartesian case): a particle that
+    crosses a reflecting wall ends at the mirror image of its unreflected position, with the
+    normal velocity component reversed and the tangential one unchanged; |v| is kept. The
+    FP32 replay takes the same decisions."""
+    n = (8, 8)
+    X = wl.map2_vertices(8, 8, 0.0)
+    g = geometry.build_geometry(X, [False, True])
+    k = g.k
+    G = np.zeros(k.shape[:-1])
+    pbc = [mover.PBC_REFLECT, mover.PBC_REFLECT, mover.PBC_PERIODIC, mover.PBC_PERIODIC]
+    # cell units: x moves by dt * 8 * vx cells per step
+    idx = np.array([[0, 7, 3], [2, 5, 4]])
+    t = np.array([[0.25, 0.75, 0.5], [0.5, 0.5, 0.5]])
+    v = np.array([[-1.0, 1.0, 0.2], [0.3, -0.4, 0.0], [0.1, 0.0, 0.0]])
+    dt = 0.05  # 0.4 cells of motion for |vx| = 1
+    i1, t1, v1, face = mover.push64(idx, t, v, k, G, dt, 0.0, n, pbc)
+    assert np.all(face == -1)
+    u_free = idx[0] + t[0] + dt * 8 * v[0]
+    u_ref = np.where(u_free < 0, -u_free, np.where(u_free >= 8, 16 - u_free, u_free))
+    np.testing.assert_allclose(i1[0] + t1[0], u_ref, atol=1e-12)
+    np.testing.assert_allclose(v1[0], np.where((u_free < 0) | (u_free >= 8), -v[0], v[0]), atol=1e-15)
+    np.testing.assert_allclose(v1[1:], v[1:], atol=1e-15)
+    np.testing.assert_allclose(np.sum(v1 ** 2, axis=0), np.sum(v ** 2, axis=0), rtol=1e-14)
+    # FP32 replay: same cells and removal decisions, values to FP32 rounding
+    i32, t32, v32, f32, _ = mover.push32(idx, t.astype(np.float32), v.astype(np.float32), k.astype(np.float32),
+                                         G.astype(np.float32), n, pbc, np.float32(0.0), np.float32(dt / 2),
+                                         np.float32(dt))
+    assert np.array_equal(f32, face) and np.array_equal(i32, i1)
+    np.testing.assert_allclose(t32, t1, atol=1e-6)
+    np.testing.assert_allclose(v32, v1, atol=1e-6)
+
+
+def test_reflection_on_a_curved_cap_keeps_speed_and_flips_the_normal():
+    """Spec B on the 3D shell's polar cap: the reflected velocity has the same speed and its
+    component along the cap's normal (row 1 of k, i.e. grad eta) is reversed."""
+    w = wl.sphere(6, 8, 8, npart_per_species=10, seed=3)
+    g = geometry.build_geometry(w.vertices, [False, False, True])
+    k = g.k
+    G = np.zeros(k.shape[:-1])
+    # particles next to the theta = theta_c cap moving towards it (decreasing eta)
+    npart = 6
+    idx = np.stack([np.arange(npart) % 6, np.zeros(npart, int), np.arange(npart) % 8])
+    t = np.stack([np.full(npart, 0.5), np.full(npart, 0.05), np.full(npart, 0.5)])
+    # physical velocity along -grad(eta) at the particle
+    kp = mover.gather(k, idx, t)
+    nrm = kp[:, 1, :] / np.linalg.norm(kp[:, 1, :], axis=1)[:, None]
+    v = (-3.0 * nrm).T.copy()
+    i1, t1, v1, face, vk = mover.push64(idx, t, v, k, G, 0.1, 0.0, w.n, w.particle_bc, return_kicked=True)
+    assert np.all(face < 0)
+    assert np.all((i1[1] >= 0) & (i1[1] < w.n[1]))
+    hit = np.any(v1 != vk, axis=0)  # reflected (the inner cells reach the cap in one step)
+    assert 0 < np.sum(hit) < npart
+    np.testing.assert_allclose(np.linalg.norm(v1, axis=0), np.linalg.norm(vk, axis=0), rtol=1e-13)
+    # the component along grad(eta) was negative (towards the cap) and is now positive
+    assert np.all(np.sum(vk.T * kp[:, 1, :], axis=1) < 0)
+    assert np.all(np.sum(v1.T * kp[:, 1, :], axis=1)[hit] > 0)
