@@ -182,6 +182,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=256, help="runs of the batched configuration (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--sphere-particles", type=int, default=32_000_000,
+                    help="particles per species of the 3D sphere run (0: skip)")
     ap.add_argument("--serve-requests", type=int, default=64, help="requests of the serving run (0: skip)")
     ap.add_argument("--serve-steps", type=int, default=200, help="PIC cycles per request")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second (Poisson)")
@@ -310,6 +312,14 @@ def main():
         del arena
         batched = batched_measurement(cpic, args.batch_runs, args.batch_steps, stream)
 
+    # ---- 3D sphere in plasma (128^3 shell, reflecting polar caps)
+    sphere = None
+    if args.sphere_particles > 0:
+        if batched is None:
+            run.close()
+            batched = False  # the 2D run is closed
+        sphere = sphere_measurement(cpic, args.sphere_particles, 20, stream, flush)
+
     # ---- served runs: open-loop Poisson arrivals, continuous batching
     served = None
     if args.serve_requests > 0:
@@ -342,7 +352,8 @@ def main():
             "push_particle_steps_per_s": particles_per_push / (push_avg_ms * 1e-3),
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "batched": batched,
+            "batched": batched or None,
+            "sphere3d": sphere,
             "served": served,
             "gpu_launches": int(launches),
             "gpu_launches_note": "kernels launched in the timed particle steps (kernel nodes of each replayed "
@@ -350,7 +361,7 @@ def main():
             "clocks": clk,
         }
         print(json.dumps(out))
-    if batched is None:
+    if batched is None and sphere is None:
         run.close()
     if dist:
         dist.destroy_process_group()
@@ -409,6 +420,65 @@ def batched_measurement(cpic, nruns, steps, stream):
                         "U[1e4, 2e6], phi_obj U[-10, 2], seeds 1000+i, loaded on the device; full PIC cycles "
                         "with the multigrid solve; batch = one CUDA graph launch per step, sequential = the "
                         "runs' own graphs one after another on one stream"}
+
+
+def sphere_measurement(cpic, npart, steps, stream, flush):
+    """3D sphere in plasma: shell map r = 30^xi, theta in [pi/32, pi - pi/32], phi periodic,
+    128^3 cells, npart + npart particles loaded on the device uniform in physical space
+    (ppc ~ r^3 sin theta), object at -5; fixed-field particle steps (CUDA graphs, per-step
+    events, L2 flushed) and one full cycle with the 3D multigrid solve. Roofline of the 3D
+    push kernel against 56 B per particle."""
+    import torch
+
+    cs = ctypes_stream(stream)
+    t0 = time.perf_counter()
+    run = cpic.sphere_run_device(128, 128, 128, npart, stream=cs)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    run.step_particles(3)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ps = 0
+    for k in range(steps):
+        ps += sum(run.diag()["n"])
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        run.step_particles(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    # one full cycle (3D multigrid solve to rtol 1e-10)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    run.step(1)
+    b.record(stream)
+    torch.cuda.synchronize()
+    full_ms = a.elapsed_time(b)
+    cyc = run.diag()["mg_cycles"]
+    # push kernel alone (stream-ordered pass with phase events)
+    run.profile(True)
+    run.profile_read()
+    pp = 0
+    for k in range(4):
+        pp += sum(run.diag()["n"])
+        flush.fill_(k & 0xFF)
+        run.step_particles(1)
+    ph = run.profile_read()
+    run.profile(False)
+    push_ms = ph["push"][0] / max(ph["push"][1], 1)
+    achieved = 56 * (pp / 4) / (push_ms * 1e-3) / 1e9
+    peak, kind = measured_peak()
+    run.close()
+    return {"value": ps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "particles": 2 * npart, "cells": 128 ** 3, "setup_s": setup_s,
+            "full_cycle_ms": full_ms, "mg_cycles": cyc,
+            "phases_ms_per_step": {p: m / max(n, 1) for p, (m, n) in ph.items()},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "kernel": "particle_kernel<3,0> (fused gather/push/boundary/deposit, 3D)",
+                         "bytes_per_particle": 56, "peak_kind": kind},
+            "workload": "3D sphere in plasma: shell r=(30)^xi, theta_c=pi/32 (reflecting caps), 128^3 cells, "
+                        f"{npart}+{npart} particles loaded on the device, phi_obj=-5, dt=0.1, no injection "
+                        "(3D injection not built), fixed-field particle steps, L2 flushed between steps"}
 
 
 def serving_measurement(cpic, nreq, steps, rate, seed=4):

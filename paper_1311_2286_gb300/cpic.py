@@ -457,6 +457,31 @@ def cylinder_run_device(n1, n2, npart_per_species, phi_obj, seed, sort_interval=
     return run
 
 
+def sphere_run_device(n1, n2, n3, npart_per_species, phi_obj=-5.0, seed=2, sort_interval=4, arena=None,
+                      stream=None, r0=1.0, R=30.0, theta_c=None):
+    """A 3D sphere-in-plasma run (shell map, reflecting polar caps) loaded on the device
+    with cpic_load_maxwellian and initialised."""
+    import math
+
+    from . import workloads as wl
+
+    theta_c = math.pi / 32 if theta_c is None else theta_c
+    w = wl.sphere(n1=n1, n2=n2, n3=n3, r0=r0, R=R, theta_c=theta_c, npart_per_species=npart_per_species,
+                  phi_obj=phi_obj, seed=seed, host_particles=False)
+    cfg = config_from_workload(w, sort_interval=sort_interval)
+    if arena is None:
+        import torch
+
+        arena = torch.empty(Run.footprint(cfg), dtype=torch.uint8, device="cuda")
+    run = Run(cfg, arena=arena, stream=stream)
+    run.set_map_analytic(CPIC_MAP_SHELL, [r0, R, theta_c])
+    for s, sp in enumerate(w.species):
+        run.load_maxwellian(s, npart_per_species, sp.vth, seed=seed * 16 + s)
+    run.initialize()
+    run._keep = arena
+    return run
+
+
 class Batch:
     """Many runs stepped together (one CUDA graph launch per batch step)."""
 
