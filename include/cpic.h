@@ -132,6 +132,11 @@ int cpic_query_footprint(const cpic_config* cfg, size_t* device_bytes);
  * caller. stream: cudaStream_t to enqueue on (NULL = legacy default stream). */
 int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* stream,
                 cpic_run** out);
+/* The run's configuration as in use (the sort interval as last chosen by cpic_autotune). */
+int cpic_get_config(const cpic_run* run, cpic_config* out);
+/* Changes the cell-sort interval of cpic_step / cpic_step_particles (0 = never); the
+ * steps already taken since the last sort count towards the new interval. */
+int cpic_set_sort_interval(cpic_run* run, int interval);
 /* Synchronise the run's stream and release it (frees what it allocated). NULL is a no-op. */
 int cpic_destroy(cpic_run* run);
 /* Enqueue subsequent work on another stream. */
@@ -251,6 +256,32 @@ int cpic_synchronize(cpic_run* run);
 int cpic_sort_cells_noalloc(int dim, const int32_t* n, int64_t count, const int32_t* cell_in,
                             const float* t_in, const float* v_in, int32_t* cell_out, float* t_out,
                             float* v_out, int64_t* live_out, void* stream);
+
+/* ---------------------------------------------------------------- tuning and checkpoints */
+
+#define CPIC_TUNE_CANDIDATES 5
+
+typedef struct cpic_tuning {
+    int32_t sort_interval;                     /* chosen (and set in the run) */
+    int32_t interval[CPIC_TUNE_CANDIDATES];    /* candidates tried: 1, 2, 4, 8, 16 */
+    float ms_per_step[CPIC_TUNE_CANDIDATES];   /* measured fixed-field particle step time */
+} cpic_tuning;
+
+/* Chooses the run's cell-sort interval: for each candidate, times whole sort cycles of at
+ * least trial_steps fixed-field particle steps on the run's own particles (CUDA events on
+ * the run's stream), restoring the run's particles, counters and potential from a device
+ * snapshot after each trial, so the simulation is unchanged; the fastest interval is set
+ * in the run. The snapshot is a temporary device allocation (CPIC_ERR_OOM if it fails).
+ * Synchronous. Not in the paper (the sort is a GPU locality device). */
+int cpic_autotune(cpic_run* run, int trial_steps, cpic_tuning* out);
+
+/* Writes the run's configuration, vertex map, injection sources, counters, potential and
+ * live-slot particles to a file (synchronous). */
+int cpic_checkpoint(cpic_run* run, const char* path);
+/* Creates a run from a checkpoint (arena/stream as in cpic_create); stepping it continues
+ * the saved run exactly (particles, charge, potential and diagnostics bit for bit).
+ * CPIC_ERR_INVALID for a missing, foreign or truncated file. */
+int cpic_restore(const char* path, void* arena, size_t arena_bytes, void* stream, cpic_run** out);
 
 /* ---------------------------------------------------------------- batched runs (row a11) */
 

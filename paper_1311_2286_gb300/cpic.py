@@ -111,6 +111,17 @@ class cpic_result(ctypes.Structure):
     ]
 
 
+TUNE_CANDIDATES = 5
+
+
+class cpic_tuning(ctypes.Structure):
+    _fields_ = [
+        ("sort_interval", ctypes.c_int32),
+        ("interval", ctypes.c_int32 * TUNE_CANDIDATES),
+        ("ms_per_step", ctypes.c_float * TUNE_CANDIDATES),
+    ]
+
+
 _lib = None
 P = ctypes.c_void_p
 _SIGS = {
@@ -139,6 +150,11 @@ _SIGS = {
     "cpic_batch_size": ([P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "cpic_batch_step": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "cpic_batch_synchronize": ([P], ctypes.c_int),
+    "cpic_get_config": ([P, P], ctypes.c_int),
+    "cpic_set_sort_interval": ([P, ctypes.c_int], ctypes.c_int),
+    "cpic_autotune": ([P, ctypes.c_int, P], ctypes.c_int),
+    "cpic_checkpoint": ([P, ctypes.c_char_p], ctypes.c_int),
+    "cpic_restore": ([ctypes.c_char_p, P, ctypes.c_size_t, P, ctypes.POINTER(P)], ctypes.c_int),
     "cpic_server_start": ([P, ctypes.POINTER(P)], ctypes.c_int),
     "cpic_server_submit": ([P, P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "cpic_server_poll": ([P, ctypes.c_uint64, P], ctypes.c_int),
@@ -318,6 +334,35 @@ class Run:
 
     def step(self, nsteps=1):
         check(load().cpic_step(self.h, nsteps))
+
+    def set_sort_interval(self, interval):
+        check(load().cpic_set_sort_interval(self.h, interval))
+
+    def autotune(self, trial_steps=8):
+        """Choose the sort interval by timing fixed-field particle steps (state restored)."""
+        t = cpic_tuning()
+        check(load().cpic_autotune(self.h, trial_steps, ctypes.byref(t)))
+        return {"sort_interval": t.sort_interval, "interval": list(t.interval), "ms_per_step": list(t.ms_per_step)}
+
+    def checkpoint(self, path):
+        check(load().cpic_checkpoint(self.h, os.fsencode(path)))
+
+    @classmethod
+    def restore(cls, path, stream=None):
+        """A run created from a checkpoint file (owns its device memory)."""
+        h = P()
+        check(load().cpic_restore(os.fsencode(path), None, 0, stream, ctypes.byref(h)))
+        cfg = cpic_config()
+        run = cls.__new__(cls)
+        run._arena = None
+        run.h = h
+        check(load().cpic_get_config(h, ctypes.byref(cfg)))
+        run.cfg = cfg
+        run.D = cfg.dim
+        run.n = tuple(cfg.n[a] for a in range(cfg.dim))
+        run.ncell = int(np.prod(run.n))
+        run.nvert = int(np.prod([x + 1 for x in run.n]))
+        return run
 
     def step_particles(self, nsteps=1):
         """Particle steps with the field held fixed (no field solve)."""

@@ -565,6 +565,24 @@ int cpic_query_footprint(const cpic_config* cfg, size_t* bytes) {
     return CPIC_OK;
 }
 
+int cpic_get_config(const cpic_run* r, cpic_config* out) {
+    if (!r || !out) {
+        set_error("get_config: NULL run or out");
+        return CPIC_ERR_INVALID;
+    }
+    *out = r->cfg;
+    return CPIC_OK;
+}
+
+int cpic_set_sort_interval(cpic_run* r, int interval) {
+    if (!r || interval < 0) {
+        set_error("set_sort_interval: NULL run or negative interval");
+        return CPIC_ERR_INVALID;
+    }
+    r->cfg.sort_interval = interval;
+    return CPIC_OK;
+}
+
 int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* stream, cpic_run** out) {
     if (!out) {
         set_error("out is NULL");

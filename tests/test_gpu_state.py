@@ -1,0 +1,83 @@
+"""Checkpoint/restore and the sort-interval autotuner: a restored run continues the saved
+one exactly; autotuning leaves the simulation unchanged (its trial steps are undone) and
+sets one of its candidate intervals."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1311_2286_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _records(cell, t, v):
+    return np.sort(np.rec.fromarrays([cell] + [t[a] for a in range(t.shape[0])] + [v[0], v[1], v[2]]))
+
+
+def _state(run, nsp):
+    d = run.diag()
+    out = [run.phi(), {k: np.asarray(v) for k, v in d.items()}]
+    for s in range(nsp):
+        out.append(_records(*run.particles(s)))
+        out.append(run.charge(s))
+    return out
+
+
+def _same(a, b):
+    assert np.array_equal(a[0], b[0])
+    for k in a[1]:
+        assert np.array_equal(a[1][k], b[1][k]), k
+    for x, y in zip(a[2:], b[2:]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("case", ["cylinder", "sphere3d"])
+def test_checkpoint_restore_continues_exactly(cpic, tmp_path, case):
+    if case == "cylinder":
+        w = wl.cylinder(n1=32, n2=64, npart_per_species=20_000, seed=61, inject=True)
+    else:
+        w = wl.sphere(16, 16, 16, npart_per_species=20_000, seed=62)
+    a = cpic.run_from_workload(w, sort_interval=3)
+    a.initialize()
+    a.step(5)
+    path = os.path.join(tmp_path, "run.ckpt")
+    a.checkpoint(path)
+    a.step(7)
+    want = _state(a, len(w.species))
+    a.close()
+    b = cpic.Run.restore(path)
+    b.step(7)
+    _same(_state(b, len(w.species)), want)
+    b.close()
+
+
+def test_restore_rejects_foreign_file(cpic, tmp_path):
+    path = os.path.join(tmp_path, "junk.ckpt")
+    with open(path, "wb") as f:
+        f.write(b"not a checkpoint" * 10)
+    with pytest.raises(cpic.CpicError) as e:
+        cpic.Run.restore(path)
+    assert e.value.status == cpic.CPIC_ERR_INVALID
+
+
+def test_autotune_leaves_the_run_unchanged(cpic):
+    w = wl.cylinder(n1=32, n2=64, npart_per_species=40_000, seed=63, inject=True)
+    a = cpic.run_from_workload(w, sort_interval=4)
+    a.initialize()
+    a.step(3)
+    t = a.autotune(trial_steps=6)
+    assert t["sort_interval"] in (1, 2, 4, 8, 16)
+    assert all(ms > 0 for ms in t["ms_per_step"])
+    a.step(6)
+    got = _state(a, 2)
+    chosen = t["sort_interval"]
+    a.close()
+    # the same run without autotuning, stepped with the interval it chose
+    c = cpic.run_from_workload(w, sort_interval=4)
+    c.initialize()
+    c.step(3)
+    c.set_sort_interval(chosen)
+    c.step(6)
+    _same(got, _state(c, 2))
+    c.close()
