@@ -46,7 +46,7 @@ UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE = 48  # 2D: (4 cell + 8 offsets + 12 velocity) read + written
 WORKLOAD = ("2D cylinder in plasma: annulus r=(40)^xi, 128x256 cells, 2M electrons + 2M ions "
             "(m_i/m_e=1836, T_i=T_e), phi_obj=-5, Maxwellian flux injection at r=40, dt=0.1, "
-            "sort every {S} steps, multigrid rtol 1e-10")
+            "sort interval {S}, multigrid rtol 1e-10")
 KERNEL_SOURCES = ["paper_1311_2286_gb300/csrc/push2d.cu", "paper_1311_2286_gb300/csrc/particles.cuh"]
 KERNEL = "push2d_kernel<false,true> (fused gather/push/boundary/deposit, 2D)"
 
@@ -177,7 +177,7 @@ def main():
     ap.add_argument("--full-steps", type=int, default=20, help="full PIC cycles (with the field solve) timed")
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--particles", type=int, default=2_000_000, help="per species")
-    ap.add_argument("--sort-interval", type=int, default=4)
+    ap.add_argument("--sort-interval", type=int, default=0, help="0: chosen by cpic_autotune")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=256, help="runs of the batched configuration (0: skip)")
@@ -197,7 +197,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    workload = WORKLOAD.format(S=args.sort_interval)
+    workload = WORKLOAD.format(S=args.sort_interval if args.sort_interval > 0 else "autotuned")
 
     if args.impl == "reference":
         if rank != 0:
@@ -237,6 +237,9 @@ def main():
     for (s, face, dens, vth, seed) in w.injection:
         run.set_injection(s, face, dens, vth, seed)
     run.initialize()
+    tuning = None
+    if args.sort_interval <= 0:  # choose the sort interval on the run's own particles
+        tuning = run.autotune(trial_steps=8)
     if args.no_graph:
         run.profile(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -338,6 +341,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload, "step": "fixed-field particle step (a1-a8, sort amortised)",
+                       "sort_interval": int(run.cfg.sort_interval) if tuning is None else tuning["sort_interval"],
+                       "autotune": tuning,
                        "particles_per_gpu": 2 * args.particles, "cells": 128 * 256,
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world} (independent runs, no collective)"},
@@ -371,33 +376,51 @@ def batched_measurement(cpic, nruns, steps, stream):
     """Independent cylinder runs of uneven size (cells 32..256 x 64..512 in steps of 16, 10^4..2 10^6
     particles per species, object potential in [-10, 2]), loaded on the device; whole PIC
     cycles (with the field solve), aggregate particle-steps/s of one batch (one graph launch
-    per batch step) against the same runs stepped one after another on one stream."""
+    per batch step) against the same runs stepped one after another on the same stream."""
     import torch
 
     from paper_1311_2286_gb300 import workloads as wl
 
     specs = wl.batch_specs(nruns, seed=1000)
+    # a dedicated stream: the runs and the batch enqueue on it and the events are recorded
+    # on it (the batch would otherwise create its own stream, unordered with the events)
+    stream = torch.cuda.Stream()
     cs = ctypes_stream(stream)
     t0 = time.perf_counter()
     runs = [cpic.cylinder_run_device(**sp, sort_interval=4, stream=cs) for sp in specs]
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    chosen = [r.autotune(trial_steps=4)["sort_interval"] for r in runs]
+    tune_s = time.perf_counter() - t0
 
     def alive():
         return sum(sum(r.diag()["n"]) for r in runs)
 
     def timed(fn, k):
-        fn()  # warm-up (captures graphs)
+        """CUDA-event time of k steps on the runs' stream; the wall clock (synchronised on
+        both sides) and the host time of the launches are kept as a cross-check."""
+        for _ in range(16):  # warm-up: one period of the runs' joint sort pattern (captures graphs)
+            fn()
         torch.cuda.synchronize()
         n0 = alive()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
         a.record(stream)
+        host = 0.0
         for _ in range(k):
+            h0 = time.perf_counter()
             fn()
+            host += time.perf_counter() - h0
         b.record(stream)
         torch.cuda.synchronize()
-        ms = a.elapsed_time(b)
-        return n0 * k / (ms * 1e-3), ms / k
+        wall_ms = (time.perf_counter() - w0) * 1e3
+        ev_ms = a.elapsed_time(b)
+        diag.append({"wall_ms_per_step": wall_ms / k, "host_launch_ms_per_step": host * 1e3 / k})
+        return n0 * k / (ev_ms * 1e-3), ev_ms / k
+
+    diag = []
 
     def sequential():
         for r in runs:
@@ -407,15 +430,26 @@ def batched_measurement(cpic, nruns, steps, stream):
     batch = cpic.Batch(len(runs), stream=cs)
     for r in runs:
         batch.add(r)
+    step0 = [r.diag()["step"] for r in runs]
+    n_before = alive()
+    cyc_before = [r.diag()["mg_cycles"] for r in runs]
     bat_v, bat_ms = timed(lambda: batch.step(1), steps)
     batch.close()
+    # every run advanced by every batch step (16 warm-up + timed)
+    adv = [r.diag()["step"] - s0 for r, s0 in zip(runs, step0)]
+    cyc_after = [r.diag()["mg_cycles"] for r in runs]
+    check = {"steps_advanced_min": int(min(adv)), "steps_advanced_max": int(max(adv)),
+             "expected": 16 + steps, "live_before": int(n_before), "live_after": int(alive()),
+             "mg_cycles_mean_before": float(np.mean(cyc_before)), "mg_cycles_mean_after": float(np.mean(cyc_after)),
+             "sequential_timing": diag[0], "batch_timing": diag[1]}
     cells = sum(sp["n1"] * sp["n2"] for sp in specs)
     parts = sum(2 * sp["npart_per_species"] for sp in specs)
     for r in runs:
         r.close()
     return {"value": bat_v, "unit": UNIT, "ms_per_step": bat_ms, "sequential_value": seq_v,
             "sequential_ms_per_step": seq_ms, "speedup": bat_v / seq_v, "runs": nruns, "steps": steps,
-            "particles": parts, "cells": cells, "setup_s": setup_s,
+            "particles": parts, "cells": cells, "setup_s": setup_s, "autotune_s": tune_s, "check": check,
+            "sort_intervals": {str(k): chosen.count(k) for k in sorted(set(chosen))},
             "workload": "independent 2D cylinder runs, cells U{32..256}xU{64..512} (steps of 16), particles per species "
                         "U[1e4, 2e6], phi_obj U[-10, 2], seeds 1000+i, loaded on the device; full PIC cycles "
                         "with the multigrid solve; batch = one CUDA graph launch per step, sequential = the "

@@ -206,7 +206,9 @@ int cpic_batch_step(cpic_batch* b, int nsteps, int with_solve) {
         const std::string full = (with_solve ? "S" : "P") + key;
         auto it = b->graphs.find(full);
         if (it == b->graphs.end()) {
-            if (b->graphs.size() >= 8) drop_graphs(b);  // bounded cache: patterns rarely vary
+            // bounded cache; runs whose sort intervals are powers of two up to 16 repeat
+            // their joint pattern every 16 steps (32 graphs with and without the solve)
+            if (b->graphs.size() >= 64) drop_graphs(b);
             cpic_batch::Graph g;
             int st = capture(b, with_solve != 0, key, &g);
             if (st) return st;
