@@ -18,7 +18,18 @@ Readings (the paper gives no formulas):
     u = u_face + U4 dt (k v) (cell units, FP64, velocity already rounded to FP32); then the
     split (cell, FP32 offset) with the 1.0 -> next-cell rule, periodic wrap along the face;
     a particle whose partial push leaves the domain is dropped (not counted).
-Only 2D faces normal to axis 0 are defined here.
+3D (faces normal to axis 0 of a 3D map, e.g. the outer shell of the sphere runs):
+  * face area: per face cell the quadrilateral area 1/2 |(X11 - X00) x (X01 - X10)| from its
+    four vertices, summed in face-cell order (axis 1 fastest); the rate uses the total;
+  * position uniform in physical area: the face cell is the first whose inclusive prefix
+    of areas exceeds U0 * total (so on the shell the density on the face goes as sin theta),
+    the offsets along axes 1 and 2 are U5 and U6;
+  * velocity: inward unit normal from row 0 of k (bilinear in the face cell), a tangent
+    basis t1 = the coordinate axis least aligned with the normal (lowest index on ties),
+    made orthogonal to it and normalised, t2 = n x t1; v = vth sqrt(-2 ln U1) n +
+    vth sqrt(-2 ln U2) (cos 2 pi U3 t1 + sin 2 pi U3 t2) + drift;
+  * partial first push u = u_face + U4 dt (k v) with k at the face point; a particle that
+    leaves axis 0 or axis 1 in its partial push is dropped; a periodic axis 2 wraps.
 """
 from __future__ import annotations
 
@@ -106,4 +117,77 @@ def inject_2d(k64, n, side, count, step, species, seed, vth, drift, dt):
         out_t[a] = f32
     out_idx[1] = np.mod(out_idx[1], n2)
     keep = (out_idx[0] >= 0) & (out_idx[0] < n1)
+    return out_idx[:, keep], out_t[:, keep], v32[:, keep], keep
+
+
+def face_areas_3d(X, side):
+    """Physical areas of the face cells of the xi = 0 (side 0) / xi = 1 (side 1) face of a
+    3D vertex map X (N3+1, N2+1, N1+1, 3), as a flat array in face-cell order j + N2 k."""
+    F = X[:, :, 0 if side == 0 else -1, :]  # (N3+1, N2+1, 3), [k, j]
+    X00, X10 = F[:-1, :-1], F[:-1, 1:]
+    X01, X11 = F[1:, :-1], F[1:, 1:]
+    a = X11 - X00
+    b = X01 - X10
+    cx = a[..., 1] * b[..., 2] - a[..., 2] * b[..., 1]
+    cy = a[..., 2] * b[..., 0] - a[..., 0] * b[..., 2]
+    cz = a[..., 0] * b[..., 1] - a[..., 1] * b[..., 0]
+    return (0.5 * np.sqrt(cx * cx + cy * cy + cz * cz)).ravel()
+
+
+def face_area_3d(X, side):
+    acc = 0.0
+    for x in face_areas_3d(X, side):
+        acc += float(x)
+    return acc
+
+
+def inject_3d(X, k64, n, side, count, step, species, seed, vth, drift, dt, periodic2=True):
+    """New particles on the 3D face normal to axis 0. k64: FP64 vertex table
+    (N3+1, N2+1, N1+1, a, alpha). Returns (idx (3, m), t32 (3, m), v32 (3, m), keep)."""
+    n1, n2, n3 = n
+    U = draws(count, step, species, seed)
+    areas = face_areas_3d(X, side)
+    cdf = np.empty_like(areas)
+    acc = 0.0
+    for i, x in enumerate(areas):
+        acc += float(x)
+        cdf[i] = acc
+    target = U[:, 0] * acc
+    cellf = np.searchsorted(cdf, target, side="right")
+    cellf = np.minimum(cellf, n2 * n3 - 1)
+    j, kk = cellf % n2, cellf // n2
+    t1, t2 = U[:, 5], U[:, 6]
+    col = 0 if side == 0 else n1
+    kf = ((1 - t1) * (1 - t2))[:, None, None] * k64[kk, j, col] + (t1 * (1 - t2))[:, None, None] * k64[kk, j + 1, col] \
+        + ((1 - t1) * t2)[:, None, None] * k64[kk + 1, j, col] + (t1 * t2)[:, None, None] * k64[kk + 1, j + 1, col]
+    ga = kf[:, 0, :]
+    sgn = -1.0 if side == 1 else 1.0
+    nin = sgn * ga / np.linalg.norm(ga, axis=1)[:, None]
+    e = np.zeros_like(nin)
+    e[np.arange(count), np.argmin(np.abs(nin), axis=1)] = 1.0
+    t1v = e - np.sum(e * nin, axis=1)[:, None] * nin
+    t1v = t1v / np.linalg.norm(t1v, axis=1)[:, None]
+    t2v = np.cross(nin, t1v)
+    vn = vth * np.sqrt(-2.0 * np.log(U[:, 1]))
+    rho = vth * np.sqrt(-2.0 * np.log(U[:, 2]))
+    c3, s3 = np.cos(2.0 * math.pi * U[:, 3]), np.sin(2.0 * math.pi * U[:, 3])
+    v = (vn[:, None] * nin + (rho * c3)[:, None] * t1v + (rho * s3)[:, None] * t2v).T + np.asarray(drift)[:, None]
+    v32 = v.astype(np.float32)
+    vd = v32.astype(np.float64)
+    du = (U[:, 4] * dt)[None, :] * np.einsum("pab,bp->ap", kf, vd)
+    base = [np.full(count, 0.0 if side == 0 else float(n1)), j + t1, kk + t2]
+    out_idx = np.empty((3, count), dtype=np.int64)
+    out_t = np.empty((3, count), dtype=np.float32)
+    for a in range(3):
+        u = base[a] + du[a]
+        c = np.floor(u)
+        f32 = (u - c).astype(np.float32)
+        one = f32 >= np.float32(1.0)
+        f32[one] = np.float32(0.0)
+        c = c + one
+        out_idx[a] = c.astype(np.int64)
+        out_t[a] = f32
+    if periodic2:
+        out_idx[2] = np.mod(out_idx[2], n3)
+    keep = (out_idx[0] >= 0) & (out_idx[0] < n1) & (out_idx[1] >= 0) & (out_idx[1] < n2)
     return out_idx[:, keep], out_t[:, keep], v32[:, keep], keep

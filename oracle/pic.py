@@ -134,13 +134,20 @@ class OraclePIC:
         for (s, face, dens, vth, seed) in self.injection:
             sp = self.species[s]
             side = face % 2
-            area = inject.face_length_2d(self.geom.X, side)
+            if self.D == 2:
+                area = inject.face_length_2d(self.geom.X, side)
+            else:
+                area = inject.face_area_3d(self.geom.X, side)
             rate = inject.rate_per_step(dens, vth, area, self.dt, sp.w)
             cnt = inject.count_at_step(rate, self.step_index)
             if cnt == 0:
                 continue
-            idx, t32, v32, _ = inject.inject_2d(self.geom.k, self.n, side, cnt, self.step_index, s, seed,
-                                                vth, (0.0, 0.0, 0.0), self.dt)
+            if self.D == 2:
+                idx, t32, v32, _ = inject.inject_2d(self.geom.k, self.n, side, cnt, self.step_index, s, seed,
+                                                    vth, (0.0, 0.0, 0.0), self.dt)
+            else:
+                idx, t32, v32, _ = inject.inject_3d(self.geom.X, self.geom.k, self.n, side, cnt, self.step_index, s,
+                                                    seed, vth, (0.0, 0.0, 0.0), self.dt)
             self.injected[s] += idx.shape[1]
             if self.precision == "fp64":
                 t32, v32 = t32.astype(np.float64), v32.astype(np.float64)

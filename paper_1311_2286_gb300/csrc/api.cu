@@ -175,6 +175,7 @@ void plan(cpic_run* r, Planner& P) {
     r->G32 = P.take<float>((size_t)r->nvert * (D == 2 ? 2 : 4));
     r->rhs_bc = P.take<double>(r->ncell);
     r->jcdf = P.take<double>(r->ncell);
+    r->fcdf = r->D == 3 ? P.take<double>((size_t)2 * r->n[1] * r->n[2]) : nullptr;
     r->charge = P.take<unsigned long long>((size_t)c.n_species * r->ncell);
     r->charge_h = P.take<unsigned long long>((size_t)c.n_species * r->ncell_h);
     long long total = 0;
@@ -341,6 +342,29 @@ int after_map(cpic_run* r) {
             }
             r->face_len[side] = acc;
         }
+    } else {
+        // 3D faces normal to axis 0: quadrilateral face-cell areas 1/2 |(X11 - X00) x (X01 - X10)|
+        // in face-cell order j + N2 k, their inclusive prefix (injection positions) and total
+        const int nv0 = r->n[0] + 1, nv1 = r->n[1] + 1;
+        const long long nf = (long long)r->n[1] * r->n[2];
+        std::vector<double> cdf(2 * nf);
+        for (int side = 0; side < 2; ++side) {
+            const int col = side == 0 ? 0 : r->n[0];
+            auto V = [&](int j, int k) { return &X[(((size_t)k * nv1 + j) * nv0 + col) * 3]; };
+            double acc = 0.0;
+            for (int k = 0; k < r->n[2]; ++k)
+                for (int j = 0; j < r->n[1]; ++j) {
+                    const double *x00 = V(j, k), *x10 = V(j + 1, k), *x01 = V(j, k + 1), *x11 = V(j + 1, k + 1);
+                    const double a0 = x11[0] - x00[0], a1 = x11[1] - x00[1], a2 = x11[2] - x00[2];
+                    const double b0 = x01[0] - x10[0], b1 = x01[1] - x10[1], b2 = x01[2] - x10[2];
+                    const double cx = a1 * b2 - a2 * b1, cy = a2 * b0 - a0 * b2, cz = a0 * b1 - a1 * b0;
+                    acc += 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+                    cdf[side * nf + j + (long long)r->n[1] * k] = acc;
+                }
+            r->face_len[side] = acc;
+        }
+        CPIC_CUDA(cudaMemcpyAsync(r->fcdf, cdf.data(), sizeof(double) * cdf.size(), cudaMemcpyHostToDevice, r->stream));
+        CPIC_CUDA(cudaStreamSynchronize(r->stream));
     }
     CPIC_CUDA(cudaMemsetAsync(r->lev[0].x, 0, sizeof(double) * r->ncell, r->stream));
     CPIC_CUDA(cudaMemsetAsync(r->G32, 0, sizeof(float) * r->nvert * (r->D == 2 ? 2 : 4), r->stream));
@@ -782,9 +806,14 @@ int cpic_get_particles(cpic_run* r, int sp, int64_t room, int64_t* n, int32_t* c
 
 int cpic_set_injection(cpic_run* r, int sp, int face, double density, double vth, const double* drift, uint64_t seed) {
     CHECK_RUN(r);
-    if (sp < 0 || sp >= r->cfg.n_species || r->D != 2 || (face != 0 && face != 1) ||
+    if (sp < 0 || sp >= r->cfg.n_species || (face != 0 && face != 1) ||
         r->cfg.particle_bc[face] != CPIC_PBC_ABSORB || !(density >= 0.0) || !(vth > 0.0)) {
-        set_error("set_injection: 2D faces normal to axis 0 with absorbing particle boundaries only");
+        set_error("set_injection: faces normal to axis 0 with absorbing particle boundaries only");
+        return CPIC_ERR_INVALID;
+    }
+    if ((r->D == 2 && r->cfg.particle_bc[2] != CPIC_PBC_PERIODIC) ||
+        (r->D == 3 && r->cfg.particle_bc[4] != CPIC_PBC_PERIODIC)) {
+        set_error("set_injection: the last logical axis must be periodic");
         return CPIC_ERR_INVALID;
     }
     InjectSpec& q = r->inj[sp];

@@ -45,6 +45,8 @@ struct InjectParams {
     float dt;
     int nsp;  // injecting species in this launch (blockIdx.y)
     InjectOne sp[CPIC_MAX_SPECIES];
+    const double* fcdf;  // 3D: face-cell area prefixes of faces 0 and 1
+    double farea[2];     // 3D: face areas (the prefixes' last entries)
 };
 
 __device__ __forceinline__ long long inject_count(double rate, long long step) {
@@ -62,6 +64,31 @@ __device__ __forceinline__ void split(float x, int c0, int& c, float& t) {
     cf = fminf(fmaxf(cf, -16777216.0f), 16777216.0f);
     c = c0 + (int)cf;
     t = f;
+}
+
+// Counts the kept particles and, in the last block of the species to finish, appends the
+// new slots to the species (so later kernels of the step see them).
+__device__ __forceinline__ void commit_injection(const PushParams& p, int s, int kept_lane, long long start,
+                                                 long long nslots) {
+    int k = kept_lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(FULL, k, o);
+    if ((threadIdx.x & 31) == 0 && k) {
+        atomicAdd((unsigned long long*)&p.ctr->injected[s], (unsigned long long)k);
+        atomicAdd((unsigned long long*)&p.ctr->alive[s], (unsigned long long)k);
+    }
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&p.ctr->inject_ticket[s], 1u);
+        last = t == (unsigned)gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        p.ctr->count[s] = start + nslots;
+        p.ctr->inject_ticket[s] = 0u;
+    }
 }
 
 // One launch injects every species (blockIdx.y); the last block of a species to finish
@@ -138,26 +165,119 @@ __global__ void inject_kernel(InjectParams ip) {
         }
         deposit_warp<2>(p, s, alive, c, tt);
     }
-    int k = kept_lane;
+    commit_injection(p, s, kept_lane, start, nslots);
+}
+
+// 3D faces normal to axis 0 (the outer shell of the sphere runs): the face cell is drawn
+// by inverse CDF of the face-cell areas (FP64, as the count of the draw decides a cell),
+// offsets along axes 1 and 2 from U5 and U6, the inward normal from row 0 of k bilinear in
+// the face cell, a tangent basis from the coordinate axis least aligned with the normal,
+// and the partial first push on the split position; a particle that leaves axis 0 or
+// axis 1 in its partial push is a dead slot; axis 2 (periodic) wraps.
+__global__ void inject3d_kernel(InjectParams ip) {
+    const PushParams& p = ip.p;
+    const InjectOne& sp = ip.sp[blockIdx.y];
+    const int s = sp.s;
+    const long long step = p.ctr->step - 1;
+    const long long count = inject_count(sp.rate, step);
+    const long long start = p.ctr->count[s];
+    const long long room = p.pb.capacity[s] - start;
+    const long long nslots = count < room ? count : (room > 0 ? room : 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && count > nslots)
+        atomicAdd((unsigned long long*)&p.ctr->dropped[s], (unsigned long long)(count - nslots));
+    const int cur = p.ctr->cur;
+    const long long T = p.pb.total;
+    const int n1 = p.n[0], n2 = p.n[1], n3 = p.n[2];
+    const int nv0 = n1 + 1, nv1 = n2 + 1;
+    const long long nf = (long long)n2 * n3;
+    const double* cdf = ip.fcdf + (sp.side ? nf : 0);
+    const double total = ip.farea[sp.side];
+    const float4* K4 = reinterpret_cast<const float4*>(p.K);
+    const uint2 key = make_uint2((unsigned)(sp.seed & 0xffffffffull), (unsigned)(sp.seed >> 32));
+    int kept_lane = 0;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < nslots; base += (long long)sp.blocks * blockDim.x) {
+        long long pi = base + threadIdx.x;
+        bool act = pi < nslots;
+        int c[3] = {0, 0, 0};
+        float tt[3] = {0.f, 0.f, 0.f};
+        bool alive = false;
+        if (act) {
+            const uint4 r0 = philox4x32_10(make_uint4((unsigned)pi, (unsigned)step, (unsigned)s, 0u), key);
+            const uint4 r1 = philox4x32_10(make_uint4((unsigned)pi, (unsigned)step, (unsigned)s, 1u), key);
+            const double target = (((double)r0.x + 0.5) * 2.3283064365386962890625e-10) * total;
+            long long lo = 0, hi = nf - 1;
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (cdf[mid] > target) hi = mid;
+                else lo = mid + 1;
+            }
+            const int j = (int)(lo % n2), k = (int)(lo / n2);
+            const float U1 = u01f(r0.y), U2 = u01f(r0.z), U3 = u01f(r0.w), U4 = u01f(r1.x);
+            const float t1 = u01f(r1.y), t2 = u01f(r1.z);
+            const int col = sp.side == 0 ? 0 : n1;
+            // k at the face point: bilinear in (t1, t2) over the face cell's four vertices
+            const float w00 = __fmul_rn(__fsub_rn(1.0f, t1), __fsub_rn(1.0f, t2)), w10 = __fmul_rn(t1, __fsub_rn(1.0f, t2));
+            const float w01 = __fmul_rn(__fsub_rn(1.0f, t1), t2), w11 = __fmul_rn(t1, t2);
+            const int vv[4] = {col + nv0 * (j + nv1 * k), col + nv0 * (j + 1 + nv1 * k), col + nv0 * (j + nv1 * (k + 1)),
+                               col + nv0 * (j + 1 + nv1 * (k + 1))};
+            const float wv[4] = {w00, w10, w01, w11};
+            float kf[9];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(FULL, k, o);
-    if ((threadIdx.x & 31) == 0 && k) {
-        atomicAdd((unsigned long long*)&p.ctr->injected[s], (unsigned long long)k);
-        atomicAdd((unsigned long long*)&p.ctr->alive[s], (unsigned long long)k);
+            for (int q = 0; q < 9; ++q) kf[q] = 0.0f;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const float4 a = __ldg(K4 + 3 * vv[o]), b = __ldg(K4 + 3 * vv[o] + 1), cc = __ldg(K4 + 3 * vv[o] + 2);
+                const float kv[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, cc.x};
+#pragma unroll
+                for (int q = 0; q < 9; ++q) kf[q] = __fmaf_rn(wv[o], kv[q], kf[q]);
+            }
+            // inward unit normal and tangent basis
+            const float gn = sqrtf(__fmaf_rn(kf[2], kf[2], __fmaf_rn(kf[1], kf[1], __fmul_rn(kf[0], kf[0]))));
+            const float sgn = sp.side == 1 ? -1.0f : 1.0f;
+            const float nin[3] = {__fdiv_rn(sgn * kf[0], gn), __fdiv_rn(sgn * kf[1], gn), __fdiv_rn(sgn * kf[2], gn)};
+            int ax = 0;
+            if (fabsf(nin[1]) < fabsf(nin[ax])) ax = 1;
+            if (fabsf(nin[2]) < fabsf(nin[ax])) ax = 2;
+            float ta[3] = {-nin[ax] * nin[0], -nin[ax] * nin[1], -nin[ax] * nin[2]};
+            ta[ax] = __fadd_rn(ta[ax], 1.0f);
+            const float tn = sqrtf(__fmaf_rn(ta[2], ta[2], __fmaf_rn(ta[1], ta[1], __fmul_rn(ta[0], ta[0]))));
+            ta[0] = __fdiv_rn(ta[0], tn);
+            ta[1] = __fdiv_rn(ta[1], tn);
+            ta[2] = __fdiv_rn(ta[2], tn);
+            const float tb[3] = {__fsub_rn(__fmul_rn(nin[1], ta[2]), __fmul_rn(nin[2], ta[1])),
+                                 __fsub_rn(__fmul_rn(nin[2], ta[0]), __fmul_rn(nin[0], ta[2])),
+                                 __fsub_rn(__fmul_rn(nin[0], ta[1]), __fmul_rn(nin[1], ta[0]))};
+            const float vn = sp.vth * sqrtf(-2.0f * logf(U1));
+            const float rho = sp.vth * sqrtf(-2.0f * logf(U2));
+            float sn, cs;
+            sincospif(2.0f * U3, &sn, &cs);
+            const float va = rho * cs, vb = rho * sn;
+            float v[3];
+#pragma unroll
+            for (int al = 0; al < 3; ++al)
+                v[al] = __fadd_rn(__fmaf_rn(vn, nin[al], __fmaf_rn(va, ta[al], __fmul_rn(vb, tb[al]))), sp.drift[al]);
+            // partial first push over a uniform fraction U4 of the step
+            const float fdt = __fmul_rn(U4, ip.dt);
+            float du[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                du[a] = __fmul_rn(fdt, __fmaf_rn(kf[3 * a + 2], v[2], __fmaf_rn(kf[3 * a + 1], v[1], __fmul_rn(kf[3 * a], v[0]))));
+            split(du[0], col, c[0], tt[0]);
+            split(__fadd_rn(t1, du[1]), j, c[1], tt[1]);
+            split(__fadd_rn(t2, du[2]), k, c[2], tt[2]);
+            c[2] = ((c[2] % n3) + n3) % n3;
+            alive = c[0] >= 0 && c[0] < n1 && c[1] >= 0 && c[1] < n2;
+            const long long slot = p.pb.base[s] + start + pi;
+            p.pb.cell[cur][slot] = alive ? encode<3>(c) : -1;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) p.pb.t[cur][a * T + slot] = tt[a];
+#pragma unroll
+            for (int al = 0; al < 3; ++al) p.pb.v[cur][al * T + slot] = v[al];
+            kept_lane += alive ? 1 : 0;
+        }
+        deposit_warp<3>(p, s, alive, c, tt);
     }
-    // commit: the last block of this species to finish appends the slots to the species
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned t = atomicAdd(&p.ctr->inject_ticket[s], 1u);
-        last = t == (unsigned)gridDim.x - 1u;
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        p.ctr->count[s] = start + nslots;
-        p.ctr->inject_ticket[s] = 0u;
-    }
+    commit_injection(p, s, kept_lane, start, nslots);
 }
 
 }  // namespace
@@ -185,7 +305,13 @@ int launch_inject(cpic_run* r) {
     }
     if (!ip.nsp) return CPIC_OK;
     for (int k = 0; k < ip.nsp; ++k) ip.sp[k].blocks = (int)maxb;
-    inject_kernel<<<dim3((unsigned)maxb, (unsigned)ip.nsp), 256, 0, r->stream>>>(ip);
+    ip.fcdf = r->fcdf;
+    ip.farea[0] = r->face_len[0];
+    ip.farea[1] = r->face_len[1];
+    if (r->D == 2)
+        inject_kernel<<<dim3((unsigned)maxb, (unsigned)ip.nsp), 256, 0, r->stream>>>(ip);
+    else
+        inject3d_kernel<<<dim3((unsigned)maxb, (unsigned)ip.nsp), 256, 0, r->stream>>>(ip);
     CPIC_CHECK_LAUNCH();
     return CPIC_OK;
 }

@@ -135,6 +135,7 @@ struct cpic_run {
     float* G32;       // vertex G table (padded records)
     double* rhs_bc;   // Dirichlet part of the right-hand side (finest)
     double* jcdf;     // inclusive prefix sums of the cell Jacobians (device loading)
+    double* fcdf;     // 3D: inclusive prefix sums of the face-cell areas of faces 0 and 1
     unsigned long long* charge;  // [nsp][ncell] folded charge counts (what the field solve reads)
     unsigned long long* charge_h;  // [nsp][ncell_h] deposit grid with one halo layer per side
     long long ncell_h;

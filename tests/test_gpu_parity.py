@@ -313,6 +313,44 @@ def test_injection_matches_oracle(cpic):
     run.close()
 
 
+def test_injection_3d_matches_oracle(cpic):
+    """a8 in 3D (outer shell of the sphere): count from the face area, face cell by inverse
+    CDF of the face-cell areas, offsets, velocities and partial push agree with the oracle
+    (cells exact up to draws within rounding of a face, values to FP32 arithmetic)."""
+    n = (16, 16, 16)
+    w = wl.sphere(*n, npart_per_species=2000, seed=8, capacity_factor=30.0)
+    g, _ = _geom(w)
+    run = cpic.run_from_workload(w)
+    seeds = (1234, 5678)
+    dens = 5000.0  # enough draws per step for both species at this macro-particle weight
+    for s, sp in enumerate(w.species):
+        run.set_injection(s, 1, dens, sp.vth, seeds[s])
+    run.vertex_field()
+    run.push()
+    before = [run.particles(s) for s in range(2)]
+    run.inject()
+    after = [run.particles(s) for s in range(2)]
+    d = run.diag()
+    for s, sp in enumerate(w.species):
+        area = inject.face_area_3d(w.vertices, 1)
+        rate = inject.rate_per_step(dens, sp.vth, area, w.dt, sp.w)
+        cnt = inject.count_at_step(rate, 0)
+        assert cnt > 100
+        idx, t32, v32, keep = inject.inject_3d(w.vertices, g.k, n, 1, cnt, 0, s, seeds[s], sp.vth, (0, 0, 0), w.dt)
+        nb = before[s][0].shape[0]
+        ca, ta, va = after[s]
+        new_c, new_t, new_v = ca[nb:], ta[:, nb:], va[:, nb:]
+        assert abs(new_c.shape[0] - int(keep.sum())) <= max(1, cnt // 10000)
+        assert d["injected"][s] == new_c.shape[0]
+        if new_c.shape[0] == int(keep.sum()):
+            ref_cell = wl.pack_cells(idx)
+            assert np.sum(new_c != ref_cell) <= max(1, cnt // 10000)
+            same = new_c == ref_cell
+            np.testing.assert_allclose(new_t[:, same], t32[:, same], atol=1e-5)
+            np.testing.assert_allclose(new_v[:, same], v32[:, same], rtol=2e-6, atol=2e-6 * sp.vth)
+    run.close()
+
+
 def test_edge_cases_empty_and_capacity(cpic):
     """Empty species, a species filled to capacity with injection (drops are counted, no
     write past capacity), and particles exactly on the logical boundaries."""

@@ -140,3 +140,41 @@ def test_injection_counts_and_flux_statistics():
     assert np.all(idx[0] == n1 - 1)
     hist, _ = np.histogram(idx[1], bins=n2, range=(0, n2))
     assert np.sum((hist - 40000 / n2) ** 2 / (40000 / n2)) < 120
+
+
+def test_inject_3d_flux_statistics():
+    """Spec I in 3D on the shell's outer face: positions uniform in physical area (face-cell
+    counts follow the face-cell areas, which go as sin theta), the normal speed is
+    Rayleigh (flux-weighted Maxwellian), the tangential components are Gaussian, velocities
+    point inward, and the face area tends to the sphere's 4 pi R^2 cos(theta_c)."""
+    import math
+
+    from oracle import geometry, inject
+    from paper_1311_2286_gb300 import workloads as wl
+
+    n = (8, 16, 24)
+    w = wl.sphere(*n, npart_per_species=10, seed=1)
+    g = geometry.build_geometry(w.vertices, [False, False, True])
+    area = inject.face_area_3d(w.vertices, 1)
+    exact = 4 * math.pi * 30.0**2 * math.cos(math.pi / 32)
+    assert abs(area / exact - 1) < 0.01  # chord-polygon faces under-estimate by O(h^2)
+    cnt, vth = 200_000, 1.3
+    idx, t32, v32, keep = inject.inject_3d(w.vertices, g.k, n, 1, cnt, 0, 0, 77, vth, (0, 0, 0), 1e-2)
+    assert keep.mean() > 0.999
+    areas = inject.face_areas_3d(w.vertices, 1)
+    counts = np.bincount(idx[1] + n[1] * idx[2], minlength=n[1] * n[2]).astype(float)
+    expected = keep.sum() * areas / areas.sum()
+    chi2 = np.sum((counts - expected) ** 2 / expected)
+    dof = n[1] * n[2] - 1
+    assert abs(chi2 - dof) < 6 * np.sqrt(2 * dof)
+    # inward normal = -r_hat at the particle's (theta, phi) on the outer face (analytic
+    # shell map); normal speed Rayleigh with scale vth
+    i, j, k = idx
+    th = math.pi / 32 + (math.pi - math.pi / 16) * (j + t32[1]) / n[1]
+    ph = 2 * math.pi * (k + t32[2]) / n[2]
+    rhat = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+    vn = -np.sum(v32.T.astype(float) * rhat, axis=1)
+    assert np.mean(vn > 0) > 0.995
+    assert abs(np.mean(vn) / (vth * math.sqrt(math.pi / 2)) - 1) < 0.02
+    vt = v32.T.astype(float) + vn[:, None] * rhat
+    assert abs(np.mean(np.sum(vt * vt, axis=1)) / (2 * vth**2) - 1) < 0.03
