@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
-SOURCES = ["api.cu", "geometry.cu", "fields.cu", "push.cu", "push2d.cu", "inject.cu", "sort.cu", "mg.cu", "mg_cluster.cu", "sort_noalloc.cu", "load.cu", "batch.cu", "serve.cu", "state.cu"]
+SOURCES = ["api.cu", "geometry.cu", "fields.cu", "push.cu", "push2d.cu", "push3d.cu", "inject.cu", "sort.cu", "mg.cu", "mg_cluster.cu", "sort_noalloc.cu", "load.cu", "batch.cu", "serve.cu", "state.cu"]
 
 
 def _nvcc():

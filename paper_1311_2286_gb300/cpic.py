@@ -496,6 +496,7 @@ def cylinder_run_device(n1, n2, npart_per_species, phi_obj, seed, sort_interval=
     run.set_map_analytic(CPIC_MAP_ANNULUS, [r0, R])
     for s, sp in enumerate(w.species):
         run.load_maxwellian(s, npart_per_species, sp.vth, seed=seed * 16 + s)
+    run.sort()  # the load draws cells in random order: start in cell order
     for (s, face, dens, vth, sd) in w.injection:
         run.set_injection(s, face, dens, vth, sd)
     run.initialize()
@@ -522,6 +523,7 @@ def sphere_run_device(n1, n2, n3, npart_per_species, phi_obj=-5.0, seed=2, sort_
     run.set_map_analytic(CPIC_MAP_SHELL, [r0, R, theta_c])
     for s, sp in enumerate(w.species):
         run.load_maxwellian(s, npart_per_species, sp.vth, seed=seed * 16 + s)
+    run.sort()  # the load draws cells in random order: start in cell order
     run.initialize()
     run._keep = arena
     return run

@@ -225,7 +225,9 @@ void init_geometry_sizes(cpic_run* r, const cpic_config* cfg) {
         r->nvert *= r->nvert_axis[a];
         if (a < r->D) r->ncell_h *= r->n[a] + 2;
     }
-    if (r->cfg.mg_max_cycles <= 0) r->cfg.mg_max_cycles = 30;
+    // default cycle cap: point smoothing needs about 55 V-cycles on the 128^3 shell
+    // (strong azimuthal coupling near the polar caps), 10-15 on the 2D maps
+    if (r->cfg.mg_max_cycles <= 0) r->cfg.mg_max_cycles = 100;
     if (!(r->cfg.mg_rtol > 0.0)) r->cfg.mg_rtol = 1e-10;
     r->singular = true;
     for (int f = 0; f < 2 * r->D; ++f)

@@ -192,6 +192,7 @@ int launch_push_prep(cpic_run* r);    // zero the deposit grid and kinetic-energ
 int launch_push_kernel(cpic_run* r);  // the fused push + deposit kernel alone
 PushParams make_push_params(cpic_run* r);
 int launch_push2d(cpic_run* r, const PushParams& p);
+int launch_push3d(cpic_run* r, const PushParams& p);  // CPIC_ERR_NOT_BUILT: no specialisation
 // one PIC step without the field solve, enqueued on r->stream (also inside stream capture)
 int enqueue_step(cpic_run* r, bool sort);
 int count_kernel_nodes(cudaGraph_t g, int* out);

@@ -400,6 +400,10 @@ int launch_push_kernel(cpic_run* r) {
     bool reflect = false;
     for (int f = 0; f < 2 * r->D; ++f) reflect = reflect || r->cfg.particle_bc[f] == CPIC_PBC_REFLECT;
     if (r->D == 2 && !reflect) return launch_push2d(r, make_push_params(r));
+    if (r->D == 3) {
+        const int st = launch_push3d(r, make_push_params(r));
+        if (st != CPIC_ERR_NOT_BUILT) return st;
+    }
     return launch_particles<0>(r, 0, 0, 0, 0);
 }
 

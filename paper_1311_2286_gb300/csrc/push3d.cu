@@ -1,0 +1,413 @@
+// Rows a2-a6 for three-dimensional runs: the fused hybrid-mover kernel (Sec. II.B.4) with its
+// grid coupling, specialised for the hot path. Same arithmetic as the generic particle kernel
+// (push.cu) — b1 gathers, kick, predictor / k re-gather / corrector, boundaries (periodic,
+// absorbing, spec B reflection), b2 fixed-point deposit — organised like the 2D kernel:
+//   - blocks walk chunks of one species (at most CHUNK particles, so that a chunk of the
+//     cell-sorted particles covers a few rows of one plane);
+//   - the boundary kind of each axis is a template parameter;
+//   - the next particle's state is loaded before the current one is processed;
+//   - the deposit goes into a shared-memory tile of the chunk's sampled planes and rows (with
+//     the stencil's neighbours), in the padded layout,
+//     flushed once per chunk; lanes whose 3x3x3 stencil leaves the tile
+//     deposit straight into the padded global grid. With ~30 particles per cell, most lanes
+//     of a warp hold a few neighbouring cells, and sending each lane's 27 node weights to L2
+//     as 64-bit atomics would bind the kernel on L2 atomic throughput.
+#include "particles.cuh"
+
+namespace cpic {
+namespace {
+
+using namespace pk;
+
+constexpr int P3_THREADS = 256;
+constexpr int P3_CHUNK = 4096;        // particles per chunk (a few rows of one plane)
+constexpr int P3_TILE_CELLS = 8192;   // 64 KB of shared memory (two 32-bit words per cell); the
+                                      // kernel's registers allow two blocks per SM anyway
+
+enum { K_PER = CPIC_PBC_PERIODIC, K_ABS = CPIC_PBC_ABSORB, K_REF = CPIC_PBC_REFLECT };
+
+struct Tile3 {
+    unsigned* lo;
+    unsigned* hi;
+    int k0, P, j0, R, W;  // planes [k0, k0 + P), rows [j0, j0 + R), W = n0 + 2 columns
+    bool on;
+};
+
+__device__ __forceinline__ void tile3_add(const Tile3& tl, int i, unsigned v) {
+    const unsigned old = atomicAdd(tl.lo + i, v);
+    if (old + v < old) atomicAdd(tl.hi + i, 1u);
+}
+
+// Deposit of one particle per lane into the chunk's tile; lanes whose stencil leaves the
+// tile deposit into the padded global grid (deposit_warp). Lanes sharing a cell are summed
+// first (largest group, __reduce_add_sync) so that the tile's atomics rarely collide.
+__device__ __forceinline__ void deposit_tile3(const PushParams& p, const Tile3& tl, int s, bool alive, const int* c,
+                                              const float* t) {
+    const int lane = threadIdx.x & 31;
+    const int pz = c[2] - tl.k0, ry = c[1] - tl.j0;
+    const bool in = alive && pz >= 1 && pz + 1 < tl.P && ry >= 1 && ry + 1 < tl.R;
+    const bool out = alive && !in;
+    if (__any_sync(FULL, out)) deposit_warp<3>(p, s, out, c, t);
+    const unsigned live = __ballot_sync(FULL, in);
+    if (!live) return;
+    int w[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) axis_weights<3>(in ? t[a] : 0.0f, w[a]);
+    if (!in) w[0][0] = w[0][1] = w[0][2] = 0;
+    int off = (pz * tl.R + ry) * tl.W + c[0] + 1;
+    const int off_first = __shfl_sync(FULL, off, __ffs(live) - 1);
+    if (!in) off = off_first;
+    const unsigned peers = __match_any_sync(FULL, off);
+    const unsigned score = ((unsigned)__popc(peers) << 5) | (31u - (unsigned)(__ffs(peers) - 1));
+    const unsigned best = __reduce_max_sync(FULL, score);
+    const bool grouped = (best >> 5) > 1;
+    const int leader = 31 - (int)(best & 31u);
+    const bool mine = grouped && off == __shfl_sync(FULL, off, leader);
+    const bool issue = mine ? lane == leader : in;
+    const int plane = tl.R * tl.W;
+#pragma unroll
+    for (int m2 = 0; m2 < 3; ++m2)
+#pragma unroll
+        for (int m1 = 0; m1 < 3; ++m1) {
+            const unsigned w01 = (unsigned)(w[1][m1] * w[2][m2]);
+#pragma unroll
+            for (int m0 = 0; m0 < 3; ++m0) {
+                unsigned q = (unsigned)w[0][m0] * w01;
+                if (grouped) {
+                    const unsigned tot = __reduce_add_sync(FULL, mine ? q : 0u);
+                    q = mine ? tot : q;
+                }
+                const int d = (m0 - 1) + (m1 - 1) * tl.W + (m2 - 1) * plane;
+                if (issue && q) tile3_add(tl, off + d, q);
+            }
+        }
+}
+
+template <int KIND>
+__device__ __forceinline__ void predict_axis3(float x, int c, int n, int& cp, float& tp) {
+    int dc;
+    renorm(x, tp, dc);
+    int ci = c + dc;
+    if (KIND == K_PER) {
+        ci = wrapi(ci, n);
+    } else {
+        if (ci < 0) {
+            ci = 0;
+            tp = 0.0f;
+        }
+        if (ci >= n) {
+            ci = n - 1;
+            tp = 1.0f;
+        }
+    }
+    cp = ci;
+}
+
+template <int K0, int K1, int K2>
+__global__ void __launch_bounds__(P3_THREADS, 2) push3d_kernel(PushParams p) {
+    extern __shared__ unsigned tile_dyn[];  // [P3_TILE_CELLS] low words, then high words
+    unsigned* tile_lo = tile_dyn;
+    unsigned* tile_hi = tile_dyn + P3_TILE_CELLS;
+    __shared__ int red[4][P3_THREADS / 32];
+    const DevCounters* ctr = p.ctr;
+    const int cur = ctr->cur;
+    const int nsp = p.nsp;
+    int cnt[CPIC_MAX_SPECIES];
+    int total = 0;
+#pragma unroll
+    for (int s = 0; s < CPIC_MAX_SPECIES; ++s) {
+        cnt[s] = s < nsp ? (int)ctr->count[s] : 0;
+        total += cnt[s];
+    }
+    if (total == 0) return;
+    int C = ((total + (int)gridDim.x - 1) / (int)gridDim.x + P3_THREADS - 1) / P3_THREADS * P3_THREADS;
+    if (C > P3_CHUNK) C = P3_CHUNK;
+    const int n0 = p.n[0], n1 = p.n[1], n2 = p.n[2];
+    const long long T = p.pb.total;
+    const float hdt = p.hdt, dt = p.dt;
+    constexpr int KIND[3] = {K0, K1, K2};
+
+    for (int ch = blockIdx.x;; ch += gridDim.x) {
+        int s = 0, local = ch;
+        while (s < nsp) {
+            const int nch = (cnt[s] + C - 1) / C;
+            if (local < nch) break;
+            local -= nch;
+            ++s;
+        }
+        if (s >= nsp) break;
+        const int lo = local * C;
+        const int hi = min(lo + C, cnt[s]);
+        const long long b0 = p.pb.base[s];
+        int* __restrict__ cellp = p.pb.cell[cur] + b0;
+        float* __restrict__ tq0 = p.pb.t[cur] + b0;
+        float* __restrict__ vq0 = p.pb.v[cur] + b0;
+        const float dtqm = p.dtqm[s];
+
+        // tile: planes and rows of the chunk's (sampled) particles, one plane and one row
+        // of margin each side for the stencil
+        Tile3 tl;
+        tl.lo = tile_lo;
+        tl.hi = tile_hi;
+        tl.W = n0 + 2;
+        {
+            const int si = lo + (int)(((long long)(hi - lo - 1) * threadIdx.x) / (P3_THREADS - 1));
+            const int sc = cellp[si];
+            int jmin = 0x7fffffff, jmax = -1, kmin = 0x7fffffff, kmax = -1;
+            if (sc >= 0) {
+                const int jj = (sc >> 10) & 1023, kk = sc >> 20;
+                jmin = jmax = jj;
+                kmin = kmax = kk;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                jmin = min(jmin, __shfl_xor_sync(FULL, jmin, o));
+                jmax = max(jmax, __shfl_xor_sync(FULL, jmax, o));
+                kmin = min(kmin, __shfl_xor_sync(FULL, kmin, o));
+                kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+            }
+            __syncthreads();  // the previous chunk's flush is done with the tile
+            if ((threadIdx.x & 31) == 0) {
+                red[0][threadIdx.x >> 5] = jmin;
+                red[1][threadIdx.x >> 5] = jmax;
+                red[2][threadIdx.x >> 5] = kmin;
+                red[3][threadIdx.x >> 5] = kmax;
+            }
+            __syncthreads();
+            jmin = red[0][0];
+            jmax = red[1][0];
+            kmin = red[2][0];
+            kmax = red[3][0];
+#pragma unroll
+            for (int w = 1; w < P3_THREADS / 32; ++w) {
+                jmin = min(jmin, red[0][w]);
+                jmax = max(jmax, red[1][w]);
+                kmin = min(kmin, red[2][w]);
+                kmax = max(kmax, red[3][w]);
+            }
+            // the sampled rows and planes with the stencil's neighbours. Between sorts some
+            // particles have moved to neighbouring planes (azimuthal cells near the polar caps
+            // are small), so a spread of up to two planes is taken; particles outside the
+            // tile deposit through the global path
+            tl.j0 = jmin - 1;
+            tl.R = jmax - jmin + 3;
+            tl.k0 = kmin - 1;
+            tl.P = kmax - kmin + 3;
+            if (kmax - kmin > 2) tl.P = 0x7fff;  // a chunk across many planes: no tile
+            tl.on = kmax >= kmin && tl.P * tl.R * tl.W <= P3_TILE_CELLS;
+            if (tl.on)
+                for (int k = threadIdx.x; k < tl.P * tl.R * tl.W; k += P3_THREADS) tile_lo[k] = tile_hi[k] = 0u;
+            __syncthreads();
+        }
+
+        long long ke = 0;
+        int gone[7] = {0, 0, 0, 0, 0, 0, 0};
+
+        int i = lo + (int)threadIdx.x;
+        int ncw = -1;
+        float nt[3] = {0.f, 0.f, 0.f}, nv[3] = {0.f, 0.f, 0.f};
+        if (i < hi) {
+            ncw = cellp[i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) nt[a] = tq0[a * T + i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + i];
+        }
+        for (int base = lo; base < hi; base += P3_THREADS) {
+            const int slot = i;
+            const int cw = ncw;
+            float t[3] = {nt[0], nt[1], nt[2]};
+            float v[3] = {nv[0], nv[1], nv[2]};
+            i += P3_THREADS;
+            ncw = -1;
+            if (i < hi) {
+                ncw = cellp[i];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) nt[a] = tq0[a * T + i];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + i];
+            }
+            const bool active = cw >= 0;
+            int c[3] = {active ? (cw & 1023) : 0, active ? ((cw >> 10) & 1023) : 0, active ? (cw >> 20) : 0};
+            if (!active) t[0] = t[1] = t[2] = v[0] = v[1] = v[2] = 0.0f;
+
+            // a2: b1 gather of k and G at xi^n
+            float kp[9], gp[3];
+            Tab<3>::gather(p, vertex_of<3>(p, c), t, kp, gp);
+            // a3: E^al = -sum_a G^a k^{a al}, kick
+            const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
+#pragma unroll
+            for (int al = 0; al < 3; ++al) {
+                float e = __fmul_rn(kp[al], gp[0]);
+                e = __fmaf_rn(kp[3 + al], gp[1], e);
+                e = __fmaf_rn(kp[6 + al], gp[2], e);
+                v[al] = __fmaf_rn(dtqm, -e, v[al]);
+            }
+            // a4: predictor
+            int cpred[3];
+            float tpred[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float d = __fmul_rn(kp[3 * a], v[0]);
+                d = __fmaf_rn(kp[3 * a + 1], v[1], d);
+                d = __fmaf_rn(kp[3 * a + 2], v[2], d);
+                float x = __fmaf_rn(hdt, d, t[a]);
+                if (!isfinite(x)) x = t[a];
+                if (KIND[a] == K_PER)
+                    predict_axis3<K_PER>(x, c[a], p.n[a], cpred[a], tpred[a]);
+                else
+                    predict_axis3<K_ABS>(x, c[a], p.n[a], cpred[a], tpred[a]);
+            }
+            float kq[9];
+            Tab<3>::gather(p, vertex_of<3>(p, cpred), tpred, kq, nullptr);
+            // corrector
+            bool bad = false;
+            int cn[3];
+            float tn[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float d = __fmul_rn(kq[3 * a], v[0]);
+                d = __fmaf_rn(kq[3 * a + 1], v[1], d);
+                d = __fmaf_rn(kq[3 * a + 2], v[2], d);
+                float x = __fmaf_rn(dt, d, t[a]);
+                if (!isfinite(x)) {
+                    bad = true;
+                    x = t[a];
+                }
+                int dc;
+                renorm(x, tn[a], dc);
+                cn[a] = c[a] + dc;
+            }
+            // a5: boundaries (periodic wrap, absorption), then spec B after the tally
+            int face = -1;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (KIND[a] == K_PER) {
+                    cn[a] = wrapi(cn[a], p.n[a]);
+                } else if (KIND[a] == K_ABS && face < 0) {
+                    if (cn[a] < 0) face = 2 * a;
+                    else if (cn[a] >= p.n[a]) face = 2 * a + 1;
+                }
+            }
+            if (bad) face = 6;
+            const float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
+            if (active) ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
+            if (face < 0) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (KIND[a] != K_REF || face >= 0 || (cn[a] >= 0 && cn[a] < p.n[a])) continue;
+                    const bool below = cn[a] < 0;
+                    int c2 = below ? (-cn[a] - 1) : (2 * p.n[a] - 1 - cn[a]);
+                    float t2 = __fsub_rn(1.0f, tn[a]);
+                    if (t2 >= 1.0f) {
+                        t2 = 0.0f;
+                        c2 += 1;
+                    }
+                    if (c2 < 0 || c2 >= p.n[a]) {
+                        face = 2 * a + (below ? 0 : 1);
+                        continue;
+                    }
+                    cn[a] = c2;
+                    tn[a] = t2;
+                    float nn = __fmul_rn(kq[3 * a], kq[3 * a]);
+                    float dot = __fmul_rn(v[0], kq[3 * a]);
+                    nn = __fmaf_rn(kq[3 * a + 1], kq[3 * a + 1], nn);
+                    dot = __fmaf_rn(v[1], kq[3 * a + 1], dot);
+                    nn = __fmaf_rn(kq[3 * a + 2], kq[3 * a + 2], nn);
+                    dot = __fmaf_rn(v[2], kq[3 * a + 2], dot);
+                    const float sf = __fdiv_rn(__fmul_rn(2.0f, dot), nn);
+#pragma unroll
+                    for (int al = 0; al < 3; ++al) v[al] = __fmaf_rn(-sf, kq[3 * a + al], v[al]);
+                }
+            }
+            const bool alive = active && face < 0;
+            if (active && face >= 0) {
+#pragma unroll
+                for (int f = 0; f < 7; ++f) gone[f] += face == f;
+            }
+            if (active) {
+                cellp[slot] = alive ? (cn[0] | (cn[1] << 10) | (cn[2] << 20)) : -1;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) tq0[a * T + slot] = tn[a];
+#pragma unroll
+                for (int al = 0; al < 3; ++al) vq0[al * T + slot] = v[al];
+            }
+            // a6: deposit
+            if (tl.on)
+                deposit_tile3(p, tl, s, alive, cn, tn);
+            else
+                deposit_warp<3>(p, s, alive, cn, tn);
+        }
+        // flush the tile into the padded grid
+        if (tl.on) {
+            __syncthreads();
+            unsigned long long* g = p.charge + (long long)s * p.ncell_h;
+            const int plane = tl.R * tl.W;
+            for (int k = threadIdx.x; k < tl.P * plane; k += P3_THREADS) {
+                const unsigned long long val = ((unsigned long long)tile_hi[k] << 32) | tile_lo[k];
+                if (!val) continue;
+                const int pk_ = k / plane, rem = k - pk_ * plane;
+                const int row = tl.j0 + rem / tl.W, col = rem % tl.W;
+                const int pl = tl.k0 + pk_;
+                if (row < -1 || row > n1 || pl < -1 || pl > n2) continue;
+                atomicAdd(g + ((long long)(pl + 1) * (n1 + 2) + (row + 1)) * tl.W + col, val);
+            }
+        }
+        // tallies of this chunk
+        ke = warp_sum_ll(ke);
+#pragma unroll
+        for (int f = 0; f < 7; ++f)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) gone[f] += __shfl_xor_sync(FULL, gone[f], o);
+        if ((threadIdx.x & 31) == 0) {
+            DevCounters* cw = p.ctr;
+            if (ke) atomicAdd((unsigned long long*)&cw->ke_fp[s], (unsigned long long)ke);
+            long long removed = 0;
+#pragma unroll
+            for (int f = 0; f < 7; ++f) {
+                removed += gone[f];
+                if (!gone[f]) continue;
+                if (f < 6)
+                    atomicAdd((unsigned long long*)&cw->absorbed[s][f], (unsigned long long)gone[f]);
+                else
+                    atomicAdd((unsigned long long*)&cw->nonfinite, (unsigned long long)gone[f]);
+            }
+            if (removed) atomicAdd((unsigned long long*)&cw->alive[s], (unsigned long long)(-removed));
+        }
+    }
+}
+
+template <int K0, int K1, int K2>
+int launch_push3d_t(cpic_run* r, const PushParams& p) {
+    constexpr size_t smem = sizeof(unsigned) * 2 * P3_TILE_CELLS;
+    static int occ = 0;
+    if (!occ) {
+        int dev = 0, nsm = 0, b = 0;
+        CPIC_CUDA(cudaFuncSetAttribute(push3d_kernel<K0, K1, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CPIC_CUDA(cudaGetDevice(&dev));
+        CPIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        CPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, push3d_kernel<K0, K1, K2>, P3_THREADS, smem));
+        occ = (b < 1 ? 1 : b) * nsm;
+    }
+    long long tot = 0;
+    for (int s = 0; s < r->cfg.n_species; ++s) tot += r->pb.capacity[s];
+    long long blocks = (tot + P3_THREADS - 1) / P3_THREADS;
+    if (blocks > occ) blocks = occ;
+    if (blocks < 1) blocks = 1;
+    push3d_kernel<K0, K1, K2><<<(int)blocks, P3_THREADS, smem, r->stream>>>(p);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
+}  // namespace
+
+// the specialised 3D kernel for the axis kinds it is instantiated for; CPIC_ERR_NOT_BUILT
+// for others (the caller then takes the generic kernel)
+int launch_push3d(cpic_run* r, const PushParams& p) {
+    const int k0 = p.pbc[0], k1 = p.pbc[2], k2 = p.pbc[4];
+    if (k0 == K_ABS && k1 == K_REF && k2 == K_PER) return launch_push3d_t<K_ABS, K_REF, K_PER>(r, p);
+    if (k0 == K_PER && k1 == K_PER && k2 == K_PER) return launch_push3d_t<K_PER, K_PER, K_PER>(r, p);
+    return CPIC_ERR_NOT_BUILT;
+}
+
+}  // namespace cpic

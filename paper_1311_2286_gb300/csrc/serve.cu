@@ -151,6 +151,7 @@ int start_job(cpic_server* sv, Job* j) {
         st = cpic_load_maxwellian(j->run, s, q.particles_per_species, vth[s], nullptr, q.seed * 16 + (uint64_t)s);
     for (int s = 0; !st && s < 2; ++s)
         st = cpic_set_injection(j->run, s, 1, q.density, vth[s], nullptr, q.seed * 1000 + 7 + (uint64_t)s);
+    if (!st) st = cpic_sort(j->run);  // the load draws cells in random order
     if (!st) st = cpic_initialize(j->run);
     return st;
 }
