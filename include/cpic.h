@@ -89,7 +89,7 @@ typedef struct cpic_config {
     double w[CPIC_MAX_SPECIES];   /* physical particles per macro-particle */
     int64_t capacity[CPIC_MAX_SPECIES]; /* particle slots per species (load + injection) */
     int32_t sort_interval;        /* cpic_step sorts every this many steps (0 = never) */
-    int32_t mg_max_cycles;        /* V-cycle limit of the solve inside cpic_step (0: 30) */
+    int32_t mg_max_cycles;        /* V-cycle limit of the solve inside cpic_step (0: 100) */
     double mg_rtol;               /* relative residual target of that solve (0: 1e-10, the
                                      paper's tolerance, Sec. II.B.3) */
 } cpic_config;
@@ -189,7 +189,8 @@ int cpic_step(cpic_run* run, int nsteps);
 /* nsteps particle steps with the field held fixed: vertex field, push (+ deposit),
  * injection, sort every sort_interval steps; no charge -> RHS and no field solve. This is
  * the mover with its grid coupling on its own, as timed with fixed fields in Sec. III
- * (Tables II and III); the deposited charge of the last step is left in the charge grids. */
+ * (Tables II and III); the deposited charge of the last step is kept (cpic_get_charge
+ * returns it). */
 int cpic_step_particles(cpic_run* run, int nsteps);
 
 /* Rows of one step, for callers that drive the cycle themselves: */
@@ -321,7 +322,8 @@ int cpic_batch_synchronize(cpic_batch* batch);
 typedef struct cpic_server cpic_server;
 
 #define CPIC_REQ_CYLINDER 0 /* 2D cylinder in plasma (annulus map, object at xi = 0, injection at xi = 1) */
-#define CPIC_REQ_SPHERE 1   /* 3D sphere in plasma: not built (CPIC_ERR_NOT_BUILT) */
+#define CPIC_REQ_SPHERE 1   /* 3D sphere in plasma (shell map r0 (R/r0)^xi, polar caps cut at pi/32 and
+                               specular, azimuth periodic, injection at the outer shell) */
 
 typedef struct cpic_server_opts {
     size_t hbm_budget;     /* bytes of the device pool (0: half of the free device memory) */
@@ -359,7 +361,7 @@ typedef struct cpic_result {
 
 int cpic_server_start(const cpic_server_opts* opts, cpic_server** out);
 /* Queues a request (host memory, copied); ticket receives its id. CPIC_ERR_CAPACITY when
- * the run cannot fit the pool at all; CPIC_ERR_NOT_BUILT for sphere requests. */
+ * the run cannot fit the pool at all; CPIC_ERR_INVALID for a bad request. */
 int cpic_server_submit(cpic_server* server, const cpic_request* req, uint64_t* ticket);
 /* CPIC_OK and the result once the run is done (the ticket is then retired), CPIC_ERR_BUSY
  * while it is queued or running, CPIC_ERR_INVALID for an unknown ticket. */

@@ -418,15 +418,17 @@ int phase(cpic_run* r, int ph, F fn) {
 // enqueue one step's work (stream order); `sort` selects the cell sort
 }  // namespace
 
-int enqueue_step(cpic_run* r, bool sort) {
+int enqueue_step(cpic_run* r, bool sort, bool fold) {
     int st = launch_vertex_field(r);
     if (st) return st;
     st = launch_push(r);
     if (st) return st;
     st = launch_inject(r);
     if (st) return st;
-    st = launch_fold(r);
-    if (st) return st;
+    if (fold) {  // the compact charge grid is read only by the solve and the charge readers
+        st = launch_fold(r);
+        if (st) return st;
+    }
     if (sort) {
         st = launch_sort(r);
         if (st) return st;
@@ -469,7 +471,7 @@ int build_step_graph(cpic_run* r, int with_solve, int with_sort) {
         r->stream = saved;
         return cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
     }
-    st = enqueue_step(r, with_sort != 0);
+    st = enqueue_step(r, with_sort != 0, with_solve != 0);
     if (!st && with_solve) {
         cudaStreamCaptureStatus cs;
         cudaGraph_t cg = nullptr;
@@ -529,7 +531,7 @@ int step_once(cpic_run* r, bool solve) {
     st = phase(r, CPIC_PHASE_INJECT, [&] {
         int q = launch_finalize_step(r);
         if (!q) q = launch_inject(r);
-        return q ? q : launch_fold(r);
+        return q || !solve ? q : launch_fold(r);
     });
     if (st) return st;
     if (r->cfg.sort_interval > 0 && ++r->steps_since_sort >= r->cfg.sort_interval) {
@@ -970,6 +972,8 @@ int cpic_get_charge(cpic_run* r, int sp, int64_t* counts) {
         set_error("bad species");
         return CPIC_ERR_INVALID;
     }
+    int st = launch_fold(r);  // fixed-field particle steps leave the charge in the padded grid
+    if (st) return st;
     CPIC_CUDA(cudaMemcpyAsync(counts, r->charge + (long long)sp * r->ncell, sizeof(int64_t) * r->ncell, cudaMemcpyDefault,
                               r->stream));
     CPIC_CUDA(cudaStreamSynchronize(r->stream));

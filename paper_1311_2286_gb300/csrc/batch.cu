@@ -57,7 +57,7 @@ int capture(cpic_batch* b, bool solve, const std::string& key, cpic_batch::Graph
         }
         cudaStream_t saved = r->stream;
         r->stream = b->branch[i];
-        st = enqueue_step(r, key[i] == '1');
+        st = enqueue_step(r, key[i] == '1', solve);
         if (!st && solve) {
             cudaStreamCaptureStatus cs;
             cudaGraph_t cg = nullptr;

@@ -194,7 +194,7 @@ PushParams make_push_params(cpic_run* r);
 int launch_push2d(cpic_run* r, const PushParams& p);
 int launch_push3d(cpic_run* r, const PushParams& p);  // CPIC_ERR_NOT_BUILT: no specialisation
 // one PIC step without the field solve, enqueued on r->stream (also inside stream capture)
-int enqueue_step(cpic_run* r, bool sort);
+int enqueue_step(cpic_run* r, bool sort, bool fold);
 int count_kernel_nodes(cudaGraph_t g, int* out);
 int launch_load_maxwellian(cpic_run* r, int sp, long long n, double vth, const double* drift, unsigned long long seed);
 // inject.cu

@@ -1,8 +1,8 @@
 // Row a12: a request loop that serves parametric runs with continuous batching.
 //
 // A server owns one device memory pool (its HBM budget) and a scheduler thread. Requests
-// (a cylinder-in-plasma run: cells, particles, object bias, plasma density and temperature,
-// steps) queue on submit. The scheduler
+// (a cylinder- or sphere-in-plasma run: cells, particles, object bias, plasma density and
+// temperature, steps) queue on submit. The scheduler
 //   - admits queued requests while a slot is free and the pool holds the run's footprint
 //     (cpic_query_footprint; first fit with backfill: a request that does not fit yet does
 //     not block smaller ones behind it),
@@ -104,31 +104,42 @@ struct cpic_server {
 namespace cpic {
 namespace {
 
+constexpr double kThetaCap = M_PI / 32;  // sphere requests: polar caps cut out at theta_c
+
 int make_config(const cpic_request& q, int sort_interval, cpic_config* c) {
-    if (q.kind != CPIC_REQ_CYLINDER) {
-        set_error("server: only cylinder requests are built (kind %d)", q.kind);
-        return CPIC_ERR_NOT_BUILT;
+    if (q.kind != CPIC_REQ_CYLINDER && q.kind != CPIC_REQ_SPHERE) {
+        set_error("server: unknown request kind %d", q.kind);
+        return CPIC_ERR_INVALID;
     }
-    if (q.n[0] < 8 || q.n[1] < 8 || q.particles_per_species < 1 || q.steps < 0 || !(q.density > 0.0) ||
-        !(q.temperature > 0.0) || !(q.mass_ratio > 0.0) || !(q.dt > 0.0) || !(q.r_outer > q.r_object) ||
-        !(q.r_object > 0.0)) {
+    const bool sph = q.kind == CPIC_REQ_SPHERE;
+    if (q.n[0] < 8 || q.n[1] < 8 || (sph && (q.n[2] < 8 || q.n[0] > 1023 || q.n[1] > 1023 || q.n[2] > 1023)) ||
+        q.particles_per_species < 1 || q.steps < 0 || !(q.density > 0.0) || !(q.temperature > 0.0) ||
+        !(q.mass_ratio > 0.0) || !(q.dt > 0.0) || !(q.r_outer > q.r_object) || !(q.r_object > 0.0)) {
         set_error("server: bad request (cells, particles, steps, density, temperature, mass ratio, dt or radii)");
         return CPIC_ERR_INVALID;
     }
     memset(c, 0, sizeof(*c));
-    c->dim = 2;
+    c->dim = sph ? 3 : 2;
     c->n[0] = q.n[0];
     c->n[1] = q.n[1];
-    c->n[2] = 1;
+    c->n[2] = sph ? q.n[2] : 1;
     c->field_bc[0] = c->field_bc[1] = CPIC_BC_DIRICHLET;
-    c->field_bc[2] = c->field_bc[3] = CPIC_BC_PERIODIC;
     c->field_bc_value[0] = q.phi_object;
     c->particle_bc[0] = c->particle_bc[1] = CPIC_PBC_ABSORB;
-    c->particle_bc[2] = c->particle_bc[3] = CPIC_PBC_PERIODIC;
+    if (sph) {  // shell: Neumann, specular polar caps; periodic azimuth
+        c->field_bc[2] = c->field_bc[3] = CPIC_BC_NEUMANN;
+        c->particle_bc[2] = c->particle_bc[3] = CPIC_PBC_REFLECT;
+        c->field_bc[4] = c->field_bc[5] = CPIC_BC_PERIODIC;
+        c->particle_bc[4] = c->particle_bc[5] = CPIC_PBC_PERIODIC;
+    } else {
+        c->field_bc[2] = c->field_bc[3] = CPIC_BC_PERIODIC;
+        c->particle_bc[2] = c->particle_bc[3] = CPIC_PBC_PERIODIC;
+    }
     c->dt = q.dt;
     c->n_species = 2;
-    const double area = M_PI * (q.r_outer * q.r_outer - q.r_object * q.r_object);
-    const double w = area * q.density / (double)q.particles_per_species;
+    const double R = q.r_outer, r0 = q.r_object;
+    const double volume = sph ? (4.0 / 3.0) * M_PI * (R * R * R - r0 * r0 * r0) * cos(kThetaCap) : M_PI * (R * R - r0 * r0);
+    const double w = volume * q.density / (double)q.particles_per_species;
     c->q[0] = -1.0;
     c->m[0] = 1.0;
     c->q[1] = 1.0;
@@ -144,8 +155,9 @@ int start_job(cpic_server* sv, Job* j) {
     int st = cpic_create(&j->cfg, sv->pool.base + j->off, j->footprint, j->stream, &j->run);
     if (st) return st;
     const cpic_request& q = j->req;
-    const double mp[2] = {q.r_object, q.r_outer};
-    st = cpic_set_map_analytic(j->run, CPIC_MAP_ANNULUS, mp, 2);
+    const double mp[3] = {q.r_object, q.r_outer, kThetaCap};
+    st = q.kind == CPIC_REQ_SPHERE ? cpic_set_map_analytic(j->run, CPIC_MAP_SHELL, mp, 3)
+                                   : cpic_set_map_analytic(j->run, CPIC_MAP_ANNULUS, mp, 2);
     const double vth[2] = {sqrt(q.temperature), sqrt(q.temperature / q.mass_ratio)};
     for (int s = 0; !st && s < 2; ++s)
         st = cpic_load_maxwellian(j->run, s, q.particles_per_species, vth[s], nullptr, q.seed * 16 + (uint64_t)s);

@@ -77,8 +77,8 @@ def _cfg_of(cpic, req):
 def test_bad_requests(cpic):
     sv = cpic.Server(hbm_budget=256 << 20, max_active=2)
     with pytest.raises(cpic.CpicError) as e:
-        sv.submit(_req(cpic, kind=cpic.CPIC_REQ_SPHERE))
-    assert e.value.status == cpic.CPIC_ERR_NOT_BUILT
+        sv.submit(_req(cpic, kind=7))
+    assert e.value.status == cpic.CPIC_ERR_INVALID
     with pytest.raises(cpic.CpicError) as e:
         sv.submit(_req(cpic, particles_per_species=0))
     assert e.value.status == cpic.CPIC_ERR_INVALID
@@ -87,4 +87,23 @@ def test_bad_requests(cpic):
     assert e.value.status == cpic.CPIC_ERR_CAPACITY
     with pytest.raises(cpic.CpicError):
         sv.poll(987654)
+    sv.stop()
+
+
+def test_sphere_requests_in_a_mix(cpic):
+    """3D sphere requests run next to cylinder requests and give the same result as alone."""
+    sph = dict(kind=cpic.CPIC_REQ_SPHERE, n1=16, n2=16, particles_per_species=40_000, r_outer=30.0, steps=12,
+               seed=31)
+    sv = cpic.Server(hbm_budget=2 << 30, max_active=8, steps_per_slice=4)
+    q = _req(cpic, **sph)
+    q.n[2] = 16
+    alone = sv.wait(sv.submit(q))
+    assert alone["status"] == 0 and alone["steps"] == 12 and alone["injected"][0] > 0
+    others = [sv.submit(_req(cpic, seed=40 + i)) for i in range(3)]
+    q2 = _req(cpic, **sph)
+    q2.n[2] = 16
+    mixed = sv.wait(sv.submit(q2))
+    for tk in others:
+        assert sv.wait(tk)["status"] == 0
+    _same(alone, mixed)
     sv.stop()
