@@ -184,8 +184,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--sphere-particles", type=int, default=32_000_000,
                     help="particles per species of the 3D sphere run (0: skip)")
-    ap.add_argument("--serve-requests", type=int, default=64, help="requests of the serving run (0: skip)")
-    ap.add_argument("--serve-steps", type=int, default=200, help="PIC cycles per request")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving run (0: skip)")
+    ap.add_argument("--serve-steps", type=int, default=40, help="PIC cycles per request")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second (Poisson)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every step stream-ordered (per-phase events) instead of as one CUDA graph; "
@@ -522,15 +522,27 @@ def serving_measurement(cpic, nreq, steps, rate, seed=4):
     `steps` PIC cycles each. Time-to-result percentiles and aggregate particle-steps/s."""
     rng = np.random.default_rng(seed)
     reqs = []
+    kinds = []
     for i in range(nreq):
         sc = float(rng.uniform(0.25, 1.0))
-        f = math.sqrt(sc)
-        n1 = max(32, int(round(128 * f / 16)) * 16)
-        n2 = max(64, int(round(256 * f / 16)) * 16)
-        reqs.append(cpic.make_request(n1=n1, n2=n2, particles_per_species=int(2_000_000 * sc),
-                                      phi_object=float(rng.uniform(-10, 2)), steps=steps, seed=4000 + i))
+        phi = float(rng.uniform(-10, 2))
+        if rng.random() < 0.5:  # cylinder: 128 x 256 cells and 2M + 2M particles at s = 1
+            f = math.sqrt(sc)
+            n1 = max(32, int(round(128 * f / 16)) * 16)
+            n2 = max(64, int(round(256 * f / 16)) * 16)
+            q = cpic.make_request(n1=n1, n2=n2, particles_per_species=int(2_000_000 * sc), phi_object=phi,
+                                  steps=steps, seed=4000 + i)
+            kinds.append("cylinder")
+        else:  # sphere: 128^3 cells and 32M + 32M particles at s = 1
+            f = sc ** (1.0 / 3.0)
+            nn = max(32, int(round(128 * f / 16)) * 16)
+            q = cpic.make_request(n1=nn, n2=nn, particles_per_species=int(32_000_000 * sc), phi_object=phi,
+                                  r_outer=30.0, steps=steps, seed=4000 + i, kind=cpic.CPIC_REQ_SPHERE)
+            q.n[2] = nn
+            kinds.append("sphere")
+        reqs.append(q)
     gaps = rng.exponential(1.0 / rate, nreq)
-    sv = cpic.Server(hbm_budget=0, max_active=64, steps_per_slice=10)
+    sv = cpic.Server(hbm_budget=0, max_active=12, steps_per_slice=10)
     t0 = time.perf_counter()
     tickets = []
     arrive = t0
@@ -559,6 +571,13 @@ def serving_measurement(cpic, nreq, steps, rate, seed=4):
     wall = time.perf_counter() - t0
     sv.stop()
     lat = np.array([r["latency_s"] for r in results])
+    kind_of = dict(zip(tickets, kinds))
+    by_kind = {}
+    for kname in ("cylinder", "sphere"):
+        lk = np.array([r["latency_s"] for r in results if kind_of[r["ticket"]] == kname])
+        if lk.size:
+            by_kind[kname] = {"requests": int(lk.size), "p50_s": float(np.percentile(lk, 50)),
+                              "p99_s": float(np.percentile(lk, 99))}
     qs = np.array([r["queue_s"] for r in results])
     ps = float(sum(r["particle_steps"] for r in results))
     bad = sum(1 for r in results if r["status"] != 0)
@@ -566,10 +585,12 @@ def serving_measurement(cpic, nreq, steps, rate, seed=4):
             "offered_s": last_arrival, "wall_s": wall, "served_per_s": nreq / wall,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "queue_p50_s": float(np.percentile(qs, 50)), "queue_p99_s": float(np.percentile(qs, 99)),
-            "value": ps / wall, "unit": UNIT, "failed": bad,
-            "workload": "2D cylinder requests, open-loop Poisson arrivals; scale U[0.25, 1] on particles "
-                        "(2M per species at 1) and cells (128x256 at 1, multiples of 16); phi_obj U[-10, 2]; "
-                        "continuous batching, admission by device footprint (half the free memory)"}
+            "value": ps / wall, "unit": UNIT, "failed": bad, "by_kind": by_kind,
+            "workload": "open-loop Poisson arrivals of 2D cylinder and 3D sphere requests (50/50); scale "
+                        "U[0.25, 1] on particles (cylinder 2M, sphere 32M per species at 1) and cells "
+                        "(128x256 and 128^3 at 1, multiples of 16); phi_obj U[-10, 2]; full PIC cycles with "
+                        "the multigrid solve; continuous batching (at most 12 runs on the device, a slice "
+                        "of 10 cycles per turn), admission by device footprint (half the free memory)"}
 
 
 def ctypes_stream(stream):
