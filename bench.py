@@ -65,6 +65,29 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
+def profiled_traffic_3d(particles):
+    """DRAM bytes of one 3D push of `particles` particles, scaled from the committed ncu
+    summary's bytes per particle (captured on a smaller 3D run), if it was taken on the
+    current kernel sources, else None."""
+    path = os.path.join(ROOT, "profiles", "push3d_sphere_128cubed_16M.md")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for f in ["paper_1311_2286_gb300/csrc/push3d.cu", "paper_1311_2286_gb300/csrc/particles.cuh"]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    kv = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            kv[k.strip()] = v.strip().split()[0] if v.strip() else ""
+    if kv.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
+        return None
+    try:
+        return int(float(kv["dram_bytes_per_particle"]) * particles)
+    except (KeyError, ValueError):
+        return None
+
+
 def profiled_traffic():
     """dram bytes per push launch from the committed ncu summary, if it was taken on the
     current kernel sources (matching source hash), else None."""
@@ -508,7 +531,8 @@ def sphere_measurement(cpic, npart, steps, stream, flush):
             "full_cycle_ms": full_ms, "mg_cycles": cyc,
             "phases_ms_per_step": {p: m / max(n, 1) for p, (m, n) in ph.items()},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "kernel": "particle_kernel<3,0> (fused gather/push/boundary/deposit, 3D)",
+                         "traffic": profiled_traffic_3d(pp / 4),
+                         "kernel": "push3d_kernel<absorb,reflect,periodic> (fused gather/push/boundary/deposit, 3D)",
                          "bytes_per_particle": 56, "peak_kind": kind},
             "workload": "3D sphere in plasma: shell r=(30)^xi, theta_c=pi/32 (reflecting caps), 128^3 cells, "
                         f"{npart}+{npart} particles loaded on the device, phi_obj=-5, dt=0.1, no injection "
