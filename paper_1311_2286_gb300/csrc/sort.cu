@@ -137,12 +137,24 @@ __global__ void scan_final_kernel(const int* hist, long long N, long long chunk,
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) scan[N] = carry;
 }
 
-// Scatter: blocks walk chunks of one species (block-uniform species, 32-bit slot indices);
-// every thread loads its particle's whole state before reserving its destination, so the
-// loads overlap the cursor atomics; lanes with the same cell reserve consecutive slots with
-// one atomic per group.
+// Scatter. Blocks walk chunks of SC_CHUNK particles of one species (block-uniform species,
+// 32-bit slot indices). Between sorts the particles are nearly in cell order, so a chunk's
+// keys span a narrow range: the chunk counts its keys in a shared histogram over that range
+// (warp-aggregated), reserves each cell's slots with one global cursor atomic per cell and
+// chunk, and ranks its particles with shared atomics, so the long chain global atomic ->
+// store runs once per cell and chunk instead of once per warp and cell. Chunks whose keys
+// span more than SC_RANGE cells (unsorted loads, injected particles) reserve per warp and
+// cell. Lanes with the same cell get consecutive slots either way.
+constexpr int SC_THREADS = 256;
+constexpr int SC_PER_THREAD = 8;
+constexpr int SC_CHUNK = SC_THREADS * SC_PER_THREAD;
+constexpr int SC_RANGE = 4096;
+
 template <int D>
-__global__ void __launch_bounds__(256) scatter_kernel(SortParams p) {
+__global__ void __launch_bounds__(SC_THREADS) scatter_kernel(SortParams p) {
+    __shared__ int hcount[SC_RANGE];  // counts, then reserved global starts
+    __shared__ int hrank[SC_RANGE];   // running ranks
+    __shared__ int red[2][SC_THREADS / 32];
     const int nsp = p.nsp;
     int cnt[CPIC_MAX_SPECIES];
     int total = 0;
@@ -152,7 +164,6 @@ __global__ void __launch_bounds__(256) scatter_kernel(SortParams p) {
         total += cnt[s];
     }
     if (total == 0) return;
-    const int C = ((total + (int)gridDim.x - 1) / (int)gridDim.x + 255) / 256 * 256;
     const int cur = p.ctr->cur, nxt = 1 - cur;
     const long long T = p.pb.total;
     const int lane = threadIdx.x & 31;
@@ -160,13 +171,13 @@ __global__ void __launch_bounds__(256) scatter_kernel(SortParams p) {
     for (int ch = blockIdx.x;; ch += gridDim.x) {
         int s = 0, local = ch;
         while (s < nsp) {
-            const int nch = (cnt[s] + C - 1) / C;
+            const int nch = (cnt[s] + SC_CHUNK - 1) / SC_CHUNK;
             if (local < nch) break;
             local -= nch;
             ++s;
         }
         if (s >= nsp) break;
-        const int lo = local * C, hi = min(lo + C, cnt[s]);
+        const int lo = local * SC_CHUNK, hi = min(lo + SC_CHUNK, cnt[s]);
         const long long b0 = p.pb.base[s];
         const int* __restrict__ cin = p.pb.cell[cur] + b0;
         const float* __restrict__ tin = p.pb.t[cur] + b0;
@@ -177,26 +188,83 @@ __global__ void __launch_bounds__(256) scatter_kernel(SortParams p) {
         const long long* __restrict__ scan_s = p.scan + (long long)s * p.ncell;
         int* __restrict__ cursor = p.hist + (long long)s * p.ncell;
         const long long sbase = scan_s[0];
-        for (int i = lo + (int)threadIdx.x; i - (int)threadIdx.x < hi; i += 256) {
-            const bool act = i < hi;
-            const int cw = act ? cin[i] : -1;
+        // keys of this thread's particles (element e: slot lo + threadIdx.x + e * SC_THREADS)
+        int key[SC_PER_THREAD];
+        int kmin = 0x7fffffff, kmax = -1;
+#pragma unroll
+        for (int e = 0; e < SC_PER_THREAD; ++e) {
+            const int i = lo + (int)threadIdx.x + e * SC_THREADS;
+            const int cw = i < hi ? cin[i] : -1;
+            int k = -1;
+            if (cw >= 0)
+                k = D == 2 ? (cw & 0xFFFF) + n0 * (cw >> 16) : (cw & 1023) + n0 * (((cw >> 10) & 1023) + n1 * (cw >> 20));
+            key[e] = k;
+            if (k >= 0) {
+                kmin = min(kmin, k);
+                kmax = max(kmax, k);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(FULL, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+        }
+        __syncthreads();  // previous chunk done with the shared arrays
+        if (lane == 0) {
+            red[0][threadIdx.x >> 5] = kmin;
+            red[1][threadIdx.x >> 5] = kmax;
+        }
+        __syncthreads();
+        kmin = red[0][0];
+        kmax = red[1][0];
+#pragma unroll
+        for (int w = 1; w < SC_THREADS / 32; ++w) {
+            kmin = min(kmin, red[0][w]);
+            kmax = max(kmax, red[1][w]);
+        }
+        if (kmax < kmin) continue;  // no live particle in the chunk (block-uniform)
+        const bool local_path = kmax - kmin < SC_RANGE;
+        if (local_path) {
+            const int range = kmax - kmin + 1;
+            for (int k = threadIdx.x; k < range; k += SC_THREADS) hcount[k] = hrank[k] = 0;
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < SC_PER_THREAD; ++e) {
+                const int k = key[e];
+                const unsigned peers = __match_any_sync(FULL, k);
+                if (k >= 0 && (__ffs(peers) - 1) == lane) atomicAdd(&hcount[k - kmin], __popc(peers));
+            }
+            __syncthreads();
+            // one global reservation per cell of the chunk: hcount becomes the cell's first slot
+            for (int k = threadIdx.x; k < range; k += SC_THREADS) {
+                const int c = hcount[k];
+                if (c) hcount[k] = (int)(scan_s[kmin + k] - sbase) + atomicAdd(cursor + kmin + k, c);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int e = 0; e < SC_PER_THREAD; ++e) {
+            const int i = lo + (int)threadIdx.x + e * SC_THREADS;
+            const int k = key[e];
+            const bool act = k >= 0;
             float t[3], v[3];
 #pragma unroll
             for (int a = 0; a < D; ++a) t[a] = act ? tin[a * T + i] : 0.f;
 #pragma unroll
             for (int a = 0; a < 3; ++a) v[a] = act ? vin[a * T + i] : 0.f;
-            int key = -1;
-            if (cw >= 0)
-                key = D == 2 ? (cw & 0xFFFF) + n0 * (cw >> 16)
-                             : (cw & 1023) + n0 * (((cw >> 10) & 1023) + n1 * (cw >> 20));
-            const unsigned peers = __match_any_sync(FULL, key);
+            const unsigned peers = __match_any_sync(FULL, k);
             const int leader = __ffs(peers) - 1;
             int start = 0;
-            if (key >= 0 && leader == lane) start = atomicAdd(cursor + key, __popc(peers));
+            if (act && leader == lane) {
+                if (local_path)
+                    start = hcount[k - kmin] + atomicAdd(&hrank[k - kmin], __popc(peers));
+                else
+                    start = (int)(scan_s[k] - sbase) + atomicAdd(cursor + k, __popc(peers));
+            }
             start = __shfl_sync(FULL, start, leader);
-            if (key >= 0) {
-                const int dst = (int)(scan_s[key] - sbase) + start + __popc(peers & ((1u << lane) - 1u));
-                cout[dst] = cw;
+            if (act) {
+                const int dst = start + __popc(peers & ((1u << lane) - 1u));
+                cout[dst] = cin[i];
 #pragma unroll
                 for (int a = 0; a < D; ++a) tout[a * T + dst] = t[a];
 #pragma unroll
