@@ -30,44 +30,89 @@ __device__ __forceinline__ long long cell_key(const SortParams& p, int cw) {
     return (long long)(cw & 1023) + (long long)p.n[0] * (((cw >> 10) & 1023) + (long long)p.n[1] * (cw >> 20));
 }
 
-struct Ranges {
-    long long cnt[CPIC_MAX_SPECIES];
-    long long voff[CPIC_MAX_SPECIES + 1];
-};
-
-__device__ __forceinline__ Ranges ranges(const SortParams& p) {
-    Ranges r;
-    r.voff[0] = 0;
-    for (int s = 0; s < CPIC_MAX_SPECIES; ++s) {
-        long long c = s < p.nsp ? p.ctr->count[s] : 0;
-        r.cnt[s] = c;
-        r.voff[s + 1] = r.voff[s] + ((c + 31) & ~31ll);
-    }
-    return r;
-}
-
-__device__ __forceinline__ int species_at(const Ranges& r, int nsp, long long vi) {
-    int s = 0;
+// Histogram of cells per species: chunks of SC_CHUNK particles of one species count their
+// keys in a shared histogram over the chunk's key range (warp-aggregated shared atomics) and
+// add each non-zero count to the global histogram once; chunks with wide key ranges add
+// per warp and cell.
+__global__ void __launch_bounds__(256) hist_kernel(SortParams p) {
+    constexpr int CHUNK = 256 * 8, RANGE = 4096;
+    __shared__ int h[RANGE];
+    __shared__ int red[2][8];
+    const int nsp = p.nsp;
+    int cnt[CPIC_MAX_SPECIES];
+    int total = 0;
 #pragma unroll
-    for (int x = 1; x < CPIC_MAX_SPECIES; ++x)
-        if (x < nsp && vi >= r.voff[x]) s = x;
-    return s;
-}
-
-__global__ void hist_kernel(SortParams p) {
-    const Ranges R = ranges(p);
-    const long long total = R.voff[p.nsp];
+    for (int s = 0; s < CPIC_MAX_SPECIES; ++s) {
+        cnt[s] = s < nsp ? (int)p.ctr->count[s] : 0;
+        total += cnt[s];
+    }
+    if (total == 0) return;
     const int cur = p.ctr->cur;
-    const int* cellp = p.pb.cell[cur];
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += (long long)gridDim.x * blockDim.x) {
-        long long vi = base + threadIdx.x;
-        int s = species_at(R, p.nsp, vi);
-        long long local = vi - R.voff[s];
-        bool act = vi < total && local < R.cnt[s];
-        long long key = act ? cell_key(p, cellp[p.pb.base[s] + local]) : -1;
-        unsigned peers = __match_any_sync(FULL, (unsigned long long)key);
-        if (key >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
-            atomicAdd(p.hist + (long long)s * p.ncell + key, __popc(peers));
+    const int lane = threadIdx.x & 31;
+    for (int ch = blockIdx.x;; ch += gridDim.x) {
+        int s = 0, local = ch;
+        while (s < nsp) {
+            const int nch = (cnt[s] + CHUNK - 1) / CHUNK;
+            if (local < nch) break;
+            local -= nch;
+            ++s;
+        }
+        if (s >= nsp) break;
+        const int lo = local * CHUNK, hi = min(lo + CHUNK, cnt[s]);
+        const int* __restrict__ cin = p.pb.cell[cur] + p.pb.base[s];
+        int* __restrict__ hist_s = p.hist + (long long)s * p.ncell;
+        int key[8];
+        int kmin = 0x7fffffff, kmax = -1;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int i = lo + (int)threadIdx.x + e * 256;
+            const long long k = i < hi ? cell_key(p, cin[i]) : -1;
+            key[e] = (int)k;
+            if (k >= 0) {
+                kmin = min(kmin, (int)k);
+                kmax = max(kmax, (int)k);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(FULL, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+        }
+        __syncthreads();
+        if (lane == 0) {
+            red[0][threadIdx.x >> 5] = kmin;
+            red[1][threadIdx.x >> 5] = kmax;
+        }
+        __syncthreads();
+        kmin = red[0][0];
+        kmax = red[1][0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) {
+            kmin = min(kmin, red[0][w]);
+            kmax = max(kmax, red[1][w]);
+        }
+        if (kmax < kmin) continue;
+        if (kmax - kmin < RANGE) {
+            const int range = kmax - kmin + 1;
+            for (int k = threadIdx.x; k < range; k += 256) h[k] = 0;
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = key[e];
+                const unsigned peers = __match_any_sync(FULL, k);
+                if (k >= 0 && (__ffs(peers) - 1) == lane) atomicAdd(&h[k - kmin], __popc(peers));
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < range; k += 256)
+                if (h[k]) atomicAdd(hist_s + kmin + k, h[k]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = key[e];
+                const unsigned peers = __match_any_sync(FULL, k);
+                if (k >= 0 && (__ffs(peers) - 1) == lane) atomicAdd(hist_s + k, __popc(peers));
+            }
+        }
     }
 }
 
