@@ -309,15 +309,8 @@ def main():
         run.step(1)
     phases = run.profile_read()
     run.profile(args.no_graph)
-    if dist:
-        t = torch.tensor([total_ms, full_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, full_ms = float(t[0].item()), float(t[1].item())
-        ps_t = torch.tensor([particle_steps, full_ps], dtype=torch.float64, device="cuda")
-        dist.all_reduce(ps_t)
-        particle_steps_all, full_ps_all = float(ps_t[0].item()), float(ps_t[1].item())
-    else:
-        particle_steps_all, full_ps_all = float(particle_steps), float(full_ps)
+    (total_ms, full_ms), (particle_steps_all, full_ps_all) = aggregate_replicas(
+        dist, [total_ms, full_ms], [particle_steps, full_ps], "cuda")
     value = particle_steps_all / (total_ms * 1e-3)
     push_ms, push_n = phases["push"]
     push_avg_ms = push_ms / max(push_n, 1)
@@ -615,6 +608,21 @@ def serving_measurement(cpic, nreq, steps, rate, seed=4):
                         "(128x256 and 128^3 at 1, multiples of 16); phi_obj U[-10, 2]; full PIC cycles with "
                         "the multigrid solve; continuous batching (at most 12 runs on the device, a slice "
                         "of 10 cycles per turn), admission by device footprint (half the free memory)"}
+
+
+def aggregate_replicas(dist, times_ms, counts, device):
+    """Whole-job figures over N independent replicas (one per GPU, no data exchange): the
+    slowest rank's time and the sum of the units all ranks processed. dist is
+    torch.distributed (initialised) or None for one process."""
+    import torch
+
+    if dist is None:
+        return [float(x) for x in times_ms], [float(x) for x in counts]
+    t = torch.tensor(times_ms, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor(counts, dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return [float(x) for x in t.tolist()], [float(x) for x in c.tolist()]
 
 
 def ctypes_stream(stream):

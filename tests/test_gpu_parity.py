@@ -496,3 +496,37 @@ def test_cluster_and_kernel_solvers_agree(cpic, monkeypatch):
     ref = poisson.solve(g, M, bbc, Q, bc)
     for phi in phis:
         assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) <= 1e-10
+
+
+def test_full_size_sphere_push_parity(cpic):
+    """The 3D configuration's grid (128^3 shell, reflecting caps, the push kernel the bench
+    times) with 1M + 1M device-loaded particles after the start-up solve: one push is
+    replayed for every particle — cells, offsets and velocities bit for bit, absorbed
+    counts per face — and the ions' fixed-point charge equals the oracle's deposit."""
+    run = cpic.sphere_run_device(128, 128, 128, 1_000_000, sort_interval=0)
+    w = wl.sphere(128, 128, 128, npart_per_species=1_000_000, host_particles=False)
+    run.vertex_field()
+    k32, G32 = run.vertex_tables()
+    pre = [run.particles(s) for s in range(2)]
+    d0 = run.diag()
+    run.push()
+    post = [run.particles(s) for s in range(2)]
+    d1 = run.diag()
+    per = [False, False, True]
+    for s, sp in enumerate(w.species):
+        cell0, t0, v0 = pre[s]
+        idx = _unpack(cell0, 3)
+        i32, t32, v32, face, kefp = mover.push32(idx, t0, v0, k32, G32, w.n, w.particle_bc,
+                                                np.float32(w.dt * sp.q / sp.m), np.float32(0.5 * w.dt),
+                                                np.float32(w.dt))
+        alive = face < 0
+        cell1, t1, v1 = post[s]
+        assert np.array_equal(cell1, wl.pack_cells(i32[:, alive]))
+        assert np.array_equal(t1, t32[:, alive])
+        assert np.array_equal(v1, v32[:, alive])
+        for f in range(6):
+            assert d1["absorbed"][s][f] - d0["absorbed"][s][f] == int(np.sum(face == f)), (s, f)
+        if s == 1:
+            Cref = odep.deposit_fixed(i32[:, alive].astype(np.int64), t32[:, alive], w.n, per)
+            assert np.array_equal(run.charge(s), Cref)
+    run.close()
