@@ -280,6 +280,7 @@ def main():
             pstep += sum(d["n"])
             cyc.append(d["mg_cycles"])
             flush.fill_(k & 0xFF)
+            host_ahead()
             ev[k][0].record(stream)
             fn()
             ev[k][1].record(stream)
@@ -306,6 +307,7 @@ def main():
     for k in range(prof_steps):
         prof_particles += sum(run.diag()["n"])
         flush.fill_(k & 0xFF)
+        host_ahead()
         run.step(1)
     phases = run.profile_read()
     run.profile(args.no_graph)
@@ -492,6 +494,7 @@ def sphere_measurement(cpic, npart, steps, stream, flush):
     for k in range(steps):
         ps += sum(run.diag()["n"])
         flush.fill_(k & 0xFF)
+        host_ahead()
         ev[k][0].record(stream)
         run.step_particles(1)
         ev[k][1].record(stream)
@@ -512,6 +515,7 @@ def sphere_measurement(cpic, npart, steps, stream, flush):
     for k in range(4):
         pp += sum(run.diag()["n"])
         flush.fill_(k & 0xFF)
+        host_ahead()
         run.step_particles(1)
     ph = run.profile_read()
     run.profile(False)
@@ -623,6 +627,16 @@ def aggregate_replicas(dist, times_ms, counts, device):
     c = torch.tensor(counts, dtype=torch.float64, device=device)
     dist.all_reduce(c)
     return [float(x) for x in t.tolist()], [float(x) for x in c.tolist()]
+
+
+def host_ahead():
+    """Keep the device busy for about half a millisecond (a clock-bounded sleep kernel on the
+    current stream) so that the host has queued the next timed launches, and their CUDA
+    events, before the device reaches them: event intervals then hold device time only, not
+    host launch gaps."""
+    import torch
+
+    torch.cuda._sleep(1_000_000)
 
 
 def ctypes_stream(stream):

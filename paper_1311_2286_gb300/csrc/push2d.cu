@@ -12,12 +12,19 @@
 //     store nothing) and of non-finite positions (the particle keeps its old cell/offset);
 //   - absorbed counts and the kinetic-energy tally stay in registers until the chunk ends;
 //   - the particle state of the next iteration is loaded before the current one is
-//     processed, so its HBM latency overlaps the arithmetic.
+//     processed, so its HBM latency overlaps the arithmetic;
+//   - component pairs of the gathers and the kick use packed FP32x2 arithmetic (each lane
+//     rounds exactly as the scalar operation, so results are unchanged);
+//   - the deposit tile's 32-bit atomics collect their carries in a bit mask (one rare branch
+//     per deposit instead of one per node), and the state stores are predicated;
+//   - the iteration loop is specialised on whether the chunk's tile is in use.
 //
 // Per particle: b1 gather of G and k at xi^n (eqs. (vvp), (Wvp), (b1)); E = -k^T G and the
 // leapfrog kick (eq. (step1)); predictor xi' = xi^n + dt/2 k(xi^n) v (eq. (step2)); k
 // re-gathered at xi' (eq. (step3)); corrector xi^{n+1} = xi^n + dt k(xi') v (eq. (step4));
 // boundaries (Sec. II.B.4); b2 deposit in 64-bit fixed point (eqs. (pg), (Wpc), (b2)).
+#include <type_traits>
+
 #include "particles.cuh"
 
 namespace cpic {
@@ -51,64 +58,86 @@ __device__ __forceinline__ void predict_axis(float x, int c, int n, int& cp, flo
 
 // Shared-memory charge tile of one chunk: rows [r0, r0 + R) of the padded grid's layout
 // (W = n0 + 2 columns, column 0 and W - 1 the halo), 64-bit counts kept as 32-bit low words
-// with carries into high words (shared 32-bit atomics).
+// with carries into high words (shared 32-bit atomics; a node weight is below 2^32, so one
+// add carries at most once).
 constexpr int TILE_CELLS = 2048;  // 16 KB of shared memory per block
 
 struct Tile {
-    unsigned* lo;
-    unsigned* hi;
+    unsigned lo;      // shared-memory address of the low words
+    unsigned* hi_ptr; // the high words
     int r0, R, W;
     bool on;
 };
 
-__device__ __forceinline__ void tile_add(const Tile& tl, int i, unsigned v) {
-    const unsigned old = atomicAdd(tl.lo + i, v);
-    if (old + v < old) atomicAdd(tl.hi + i, 1u);
+#define CPIC_TILE_ADD(OFF, ARG)                         \
+    "atom.shared.add.u32 o, [%1+" OFF "], " ARG ";\n\t" \
+    "add.cc.u32 s, o, " ARG ";\n\t"                      \
+    "addc.u32 %0, %0, %0;\n\t"
+
+// adds q0, q1, q2 to three consecutive low words starting at shared address a (32-bit
+// atomics); m is shifted left by one bit per word and takes the word's carry out in its
+// lowest bit
+__device__ __forceinline__ void tile_add_row(unsigned& m, unsigned a, unsigned q0, unsigned q1, unsigned q2) {
+    asm volatile("{\n\t.reg .u32 o, s;\n\t" CPIC_TILE_ADD("0", "%2") CPIC_TILE_ADD("4", "%3") CPIC_TILE_ADD("8", "%4") "}"
+                 : "+r"(m)
+                 : "r"(a), "r"(q0), "r"(q1), "r"(q2)
+                 : "memory");
 }
 
 // Deposit of one particle per lane into the chunk's tile; lanes whose 3x3 stencil leaves the
-// tile rows deposit straight into the padded global grid. Lanes sharing a cell are combined
-// first (largest group, __reduce_add_sync) so that the tile's atomics rarely collide.
+// tile rows deposit straight into the padded global grid. The largest group of lanes that
+// share a cell is summed first (__reduce_add_sync over the group) and deposited by one lane.
 __device__ __forceinline__ void deposit_tile(const PushParams& p, const Tile& tl, int s, bool alive,
                                              const int* c, const float* t) {
     const int lane = threadIdx.x & 31;
     const int rr = c[1] - tl.r0;  // tile row of the cell
     const bool in = alive && rr >= 1 && rr + 1 < tl.R;
     const bool out = alive && !in;
-    const unsigned live = __ballot_sync(FULL, in);
     if (__any_sync(FULL, out)) deposit_warp<2>(p, s, out, c, t);
-    if (!live) return;
+    if (!__any_sync(FULL, in)) return;
     int w[2][3];
-    axis_weights<2>(in ? t[0] : 0.0f, w[0]);
-    axis_weights<2>(in ? t[1] : 0.0f, w[1]);
-    if (!in) w[0][0] = w[0][1] = w[0][2] = 0;
+    axis_weights<2>(t[0], w[0]);
+    axis_weights<2>(t[1], w[1]);
     unsigned q[9];
 #pragma unroll
     for (int node = 0; node < 9; ++node) q[node] = (unsigned)(w[0][node % 3] * w[1][node / 3]);
-    int off = rr * tl.W + c[0] + 1;
-    const int off_first = __shfl_sync(FULL, off, __ffs(live) - 1);
-    if (!in) off = off_first;
+    // lanes that do not deposit here get keys of their own
+    const int off = in ? rr * tl.W + c[0] + 1 : -1 - lane;
     const unsigned peers = __match_any_sync(FULL, off);
-    const unsigned score = ((unsigned)__popc(peers) << 5) | (31u - (unsigned)(__ffs(peers) - 1));
+    const unsigned score = ((unsigned)__popc(peers) << 5) | (unsigned)(31 - __clz(peers));
     const unsigned best = __reduce_max_sync(FULL, score);
+    const int leader = (int)(best & 31u);
     bool issue = in;
-    if ((best >> 5) > 1) {
-        const int leader = 31 - (int)(best & 31u);
-        const bool mine = off == __shfl_sync(FULL, off, leader);
+    if ((best >> 5) > 1 && ((peers >> leader) & 1u)) {  // the lanes of the largest group
 #pragma unroll
-        for (int node = 0; node < 9; ++node) {
-            const unsigned tot = __reduce_add_sync(FULL, mine ? q[node] : 0u);
-            q[node] = mine ? tot : q[node];
-        }
-        issue = mine ? lane == leader : in;
+        for (int node = 0; node < 9; ++node) q[node] = __reduce_add_sync(peers, q[node]);
+        issue = lane == leader;
     }
     if (issue) {
+        const unsigned mid = tl.lo + 4u * (unsigned)(off - 1), dw = 4u * (unsigned)tl.W;
+        unsigned m = 0;  // carry out of node k's low word in bit 8 - k
+        tile_add_row(m, mid - dw, q[0], q[1], q[2]);
+        tile_add_row(m, mid, q[3], q[4], q[5]);
+        tile_add_row(m, mid + dw, q[6], q[7], q[8]);
+        if (m) {  // rare: carries into the high words
+            unsigned* hi = tl.hi_ptr + (off - 1);
 #pragma unroll
-        for (int node = 0; node < 9; ++node) {
-            const int d = (node % 3 - 1) + (node / 3 - 1) * tl.W;
-            if (q[node]) tile_add(tl, off + d, q[node]);
+            for (int node = 0; node < 9; ++node)
+                if ((m >> (8 - node)) & 1u) atomicAdd(hi + (node % 3) + (node / 3 - 1) * tl.W, 1u);
         }
     }
+}
+
+// the six state words of one particle, stored when p holds (predicated, no branch)
+__device__ __forceinline__ void store_state(bool p, int* c, int cv, float* a, float av, float* b, float bv, float* d,
+                                            float dv, float* e, float ev, float* f, float fv) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+        "@q st.global.b32 [%1], %2;\n\t@q st.global.f32 [%3], %4;\n\t@q st.global.f32 [%5], %6;\n\t"
+        "@q st.global.f32 [%7], %8;\n\t@q st.global.f32 [%9], %10;\n\t@q st.global.f32 [%11], %12;\n\t}" ::"r"(
+            (unsigned)p),
+        "l"(c), "r"(cv), "l"(a), "f"(av), "l"(b), "f"(bv), "l"(d), "f"(dv), "l"(e), "f"(ev), "l"(f), "f"(fv)
+        : "memory");
 }
 
 template <bool PER0, bool PER1>
@@ -158,8 +187,8 @@ __global__ void __launch_bounds__(P2_THREADS, 4) push2d_kernel(PushParams p) {
         // tile rows: the rows of the chunk's particles (sampled; the chunk is in cell order
         // since the last sort) with two rows of margin for motion and the stencil
         Tile tl;
-        tl.lo = tile_lo;
-        tl.hi = tile_hi;
+        tl.lo = (unsigned)__cvta_generic_to_shared(tile_lo);
+        tl.hi_ptr = tile_hi;
         tl.W = n0 + 2;
         {
             const int si = lo + (int)(((long long)(hi - lo - 1) * threadIdx.x) / (P2_THREADS - 1));
@@ -205,136 +234,157 @@ __global__ void __launch_bounds__(P2_THREADS, 4) push2d_kernel(PushParams p) {
             nv1_ = v1p[i];
             nv2_ = v2p[i];
         }
-        for (int base = lo; base < hi; base += P2_THREADS) {
-            const int slot = i;
-            const int cw = ncw;
-            float t[2] = {nt0, nt1};
-            float v[3] = {nv0_, nv1_, nv2_};
-            i += P2_THREADS;
-            ncw = -1;
-            if (i < hi) {
-                ncw = cellp[i];
-                nt0 = t0p[i];
-                nt1 = t1p[i];
-                nv0_ = v0p[i];
-                nv1_ = v1p[i];
-                nv2_ = v2p[i];
-            }
-            const bool active = cw >= 0;
-            int c[2] = {active ? (cw & 0xFFFF) : 0, active ? (cw >> 16) : 0};
-            if (!active) t[0] = t[1] = v[0] = v[1] = v[2] = 0.0f;
-
-            // a2: b1 gather of k and G at xi^n
-            float kp[4], gp[2];
-            {
-                const int v00 = c[0] + c[1] * nv0;
-                const float s0 = __fsub_rn(1.0f, t[0]), s1 = __fsub_rn(1.0f, t[1]);
-                const float w0 = __fmul_rn(s0, s1), w1 = __fmul_rn(t[0], s1);
-                const float w2 = __fmul_rn(s0, t[1]), w3 = __fmul_rn(t[0], t[1]);
-                const float4 a = __ldg(K4 + v00), b = __ldg(K4 + v00 + 1);
-                const float4 cc = __ldg(K4 + v00 + nv0), d = __ldg(K4 + v00 + nv0 + 1);
-                const float2 ga = __ldg(G2 + v00), gb = __ldg(G2 + v00 + 1);
-                const float2 gc = __ldg(G2 + v00 + nv0), gd = __ldg(G2 + v00 + nv0 + 1);
-                kp[0] = __fmaf_rn(w3, d.x, __fmaf_rn(w2, cc.x, __fmaf_rn(w1, b.x, __fmul_rn(w0, a.x))));
-                kp[1] = __fmaf_rn(w3, d.y, __fmaf_rn(w2, cc.y, __fmaf_rn(w1, b.y, __fmul_rn(w0, a.y))));
-                kp[2] = __fmaf_rn(w3, d.z, __fmaf_rn(w2, cc.z, __fmaf_rn(w1, b.z, __fmul_rn(w0, a.z))));
-                kp[3] = __fmaf_rn(w3, d.w, __fmaf_rn(w2, cc.w, __fmaf_rn(w1, b.w, __fmul_rn(w0, a.w))));
-                gp[0] = __fmaf_rn(w3, gd.x, __fmaf_rn(w2, gc.x, __fmaf_rn(w1, gb.x, __fmul_rn(w0, ga.x))));
-                gp[1] = __fmaf_rn(w3, gd.y, __fmaf_rn(w2, gc.y, __fmaf_rn(w1, gb.y, __fmul_rn(w0, ga.y))));
-            }
-            // a3: E^al = -sum_a G^a k^{a al}, kick
-            const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
-#pragma unroll
-            for (int al = 0; al < 2; ++al) {
-                float e = __fmul_rn(kp[al], gp[0]);
-                e = __fmaf_rn(kp[2 + al], gp[1], e);
-                v[al] = __fmaf_rn(dtqm, -e, v[al]);
-            }
-            // a4: predictor (a non-finite component keeps the particle where it is)
-            int cpred[2];
-            float tpred[2];
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                float d = __fmul_rn(kp[2 * a], v[0]);
-                d = __fmaf_rn(kp[2 * a + 1], v[1], d);
-                float x = __fmaf_rn(hdt, d, t[a]);
-                if (!isfinite(x)) x = t[a];
-                if (a == 0)
-                    predict_axis<PER0>(x, c[0], n0, cpred[0], tpred[0]);
-                else
-                    predict_axis<PER1>(x, c[1], n1, cpred[1], tpred[1]);
-            }
-            // k re-gathered at xi'
-            float kq[4];
-            {
-                const int v00 = cpred[0] + cpred[1] * nv0;
-                const float s0 = __fsub_rn(1.0f, tpred[0]), s1 = __fsub_rn(1.0f, tpred[1]);
-                const float w0 = __fmul_rn(s0, s1), w1 = __fmul_rn(tpred[0], s1);
-                const float w2 = __fmul_rn(s0, tpred[1]), w3 = __fmul_rn(tpred[0], tpred[1]);
-                const float4 a = __ldg(K4 + v00), b = __ldg(K4 + v00 + 1);
-                const float4 cc = __ldg(K4 + v00 + nv0), d = __ldg(K4 + v00 + nv0 + 1);
-                kq[0] = __fmaf_rn(w3, d.x, __fmaf_rn(w2, cc.x, __fmaf_rn(w1, b.x, __fmul_rn(w0, a.x))));
-                kq[1] = __fmaf_rn(w3, d.y, __fmaf_rn(w2, cc.y, __fmaf_rn(w1, b.y, __fmul_rn(w0, a.y))));
-                kq[2] = __fmaf_rn(w3, d.z, __fmaf_rn(w2, cc.z, __fmaf_rn(w1, b.z, __fmul_rn(w0, a.z))));
-                kq[3] = __fmaf_rn(w3, d.w, __fmaf_rn(w2, cc.w, __fmaf_rn(w1, b.w, __fmul_rn(w0, a.w))));
-            }
-            // corrector
-            bool bad = false;
-            int cn[2];
-            float tn[2];
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                float d = __fmul_rn(kq[2 * a], v[0]);
-                d = __fmaf_rn(kq[2 * a + 1], v[1], d);
-                float x = __fmaf_rn(dt, d, t[a]);
-                if (!isfinite(x)) {
-                    bad = true;
-                    x = t[a];
+        // the iteration loop, specialised on whether the chunk's tile is in use
+        auto iterate = [&](auto tile_tag) {
+            constexpr bool TILE = decltype(tile_tag)::value;
+            for (int base = lo; base < hi; base += P2_THREADS) {
+                const int slot = i;
+                const int cw = ncw;
+                float t[2] = {nt0, nt1};
+                float v[3] = {nv0_, nv1_, nv2_};
+                i += P2_THREADS;
+                ncw = -1;
+                if (i < hi) {
+                    ncw = cellp[i];
+                    nt0 = t0p[i];
+                    nt1 = t1p[i];
+                    nv0_ = v0p[i];
+                    nv1_ = v1p[i];
+                    nv2_ = v2p[i];
                 }
-                int dc;
-                renorm(x, tn[a], dc);
-                cn[a] = c[a] + dc;
+                const bool active = cw >= 0;
+                int c[2] = {active ? (cw & 0xFFFF) : 0, active ? (cw >> 16) : 0};
+                if (!active) t[0] = t[1] = v[0] = v[1] = v[2] = 0.0f;
+
+                // a2: b1 gather of k and G at xi^n (pairs of components in packed FP32x2
+                // arithmetic: each lane rounds exactly as the scalar form)
+                float2 k01, k23, gp;
+                {
+                    const int v00 = c[0] + c[1] * nv0;
+                    const float s0 = __fsub_rn(1.0f, t[0]), s1 = __fsub_rn(1.0f, t[1]);
+                    const float2 wa = __fmul2_rn(make_float2(s0, t[0]), make_float2(s1, s1));
+                    const float2 wb = __fmul2_rn(make_float2(s0, t[0]), make_float2(t[1], t[1]));
+                    const float2 W0 = make_float2(wa.x, wa.x), W1 = make_float2(wa.y, wa.y);
+                    const float2 W2 = make_float2(wb.x, wb.x), W3 = make_float2(wb.y, wb.y);
+                    const float4 a = __ldg(K4 + v00), b = __ldg(K4 + v00 + 1);
+                    const float4 cc = __ldg(K4 + v00 + nv0), d = __ldg(K4 + v00 + nv0 + 1);
+                    const float2 ga = __ldg(G2 + v00), gb = __ldg(G2 + v00 + 1);
+                    const float2 gc = __ldg(G2 + v00 + nv0), gd = __ldg(G2 + v00 + nv0 + 1);
+                    k01 = __fmul2_rn(W0, make_float2(a.x, a.y));
+                    k23 = __fmul2_rn(W0, make_float2(a.z, a.w));
+                    gp = __fmul2_rn(W0, ga);
+                    k01 = __ffma2_rn(W1, make_float2(b.x, b.y), k01);
+                    k23 = __ffma2_rn(W1, make_float2(b.z, b.w), k23);
+                    gp = __ffma2_rn(W1, gb, gp);
+                    k01 = __ffma2_rn(W2, make_float2(cc.x, cc.y), k01);
+                    k23 = __ffma2_rn(W2, make_float2(cc.z, cc.w), k23);
+                    gp = __ffma2_rn(W2, gc, gp);
+                    k01 = __ffma2_rn(W3, make_float2(d.x, d.y), k01);
+                    k23 = __ffma2_rn(W3, make_float2(d.z, d.w), k23);
+                    gp = __ffma2_rn(W3, gd, gp);
+                }
+                const float kp[4] = {k01.x, k01.y, k23.x, k23.y};
+                // a3: E^al = -sum_a G^a k^{a al}, kick
+                const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
+                {
+                    float2 e = __fmul2_rn(k01, make_float2(gp.x, gp.x));
+                    e = __ffma2_rn(k23, make_float2(gp.y, gp.y), e);
+                    const float2 vv = __ffma2_rn(make_float2(-dtqm, -dtqm), e, make_float2(v[0], v[1]));
+                    v[0] = vv.x;
+                    v[1] = vv.y;
+                }
+                // a4: predictor (a non-finite component keeps the particle where it is)
+                int cpred[2];
+                float tpred[2];
+    #pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    float d = __fmul_rn(kp[2 * a], v[0]);
+                    d = __fmaf_rn(kp[2 * a + 1], v[1], d);
+                    float x = __fmaf_rn(hdt, d, t[a]);
+                    if (!isfinite(x)) x = t[a];
+                    if (a == 0)
+                        predict_axis<PER0>(x, c[0], n0, cpred[0], tpred[0]);
+                    else
+                        predict_axis<PER1>(x, c[1], n1, cpred[1], tpred[1]);
+                }
+                // k re-gathered at xi'
+                float kq[4];
+                {
+                    const int v00 = cpred[0] + cpred[1] * nv0;
+                    const float s0 = __fsub_rn(1.0f, tpred[0]), s1 = __fsub_rn(1.0f, tpred[1]);
+                    const float2 wa = __fmul2_rn(make_float2(s0, tpred[0]), make_float2(s1, s1));
+                    const float2 wb = __fmul2_rn(make_float2(s0, tpred[0]), make_float2(tpred[1], tpred[1]));
+                    const float4 a = __ldg(K4 + v00), b = __ldg(K4 + v00 + 1);
+                    const float4 cc = __ldg(K4 + v00 + nv0), d = __ldg(K4 + v00 + nv0 + 1);
+                    float2 q01 = __fmul2_rn(make_float2(wa.x, wa.x), make_float2(a.x, a.y));
+                    float2 q23 = __fmul2_rn(make_float2(wa.x, wa.x), make_float2(a.z, a.w));
+                    q01 = __ffma2_rn(make_float2(wa.y, wa.y), make_float2(b.x, b.y), q01);
+                    q23 = __ffma2_rn(make_float2(wa.y, wa.y), make_float2(b.z, b.w), q23);
+                    q01 = __ffma2_rn(make_float2(wb.x, wb.x), make_float2(cc.x, cc.y), q01);
+                    q23 = __ffma2_rn(make_float2(wb.x, wb.x), make_float2(cc.z, cc.w), q23);
+                    q01 = __ffma2_rn(make_float2(wb.y, wb.y), make_float2(d.x, d.y), q01);
+                    q23 = __ffma2_rn(make_float2(wb.y, wb.y), make_float2(d.z, d.w), q23);
+                    kq[0] = q01.x;
+                    kq[1] = q01.y;
+                    kq[2] = q23.x;
+                    kq[3] = q23.y;
+                }
+                // corrector
+                bool bad = false;
+                int cn[2];
+                float tn[2];
+    #pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    float d = __fmul_rn(kq[2 * a], v[0]);
+                    d = __fmaf_rn(kq[2 * a + 1], v[1], d);
+                    float x = __fmaf_rn(dt, d, t[a]);
+                    if (!isfinite(x)) {
+                        bad = true;
+                        x = t[a];
+                    }
+                    int dc;
+                    renorm(x, tn[a], dc);
+                    cn[a] = c[a] + dc;
+                }
+                // a5: boundaries
+                int face = -1;
+                if (PER0) {
+                    cn[0] = wrapi(cn[0], n0);
+                } else {
+                    if (cn[0] < 0) face = 0;
+                    else if (cn[0] >= n0) face = 1;
+                }
+                if (PER1) {
+                    cn[1] = wrapi(cn[1], n1);
+                } else if (face < 0) {
+                    if (cn[1] < 0) face = 2;
+                    else if (cn[1] >= n1) face = 3;
+                }
+                if (bad) face = 6;
+                const bool alive = active && face < 0;
+                if (__any_sync(FULL, active && face >= 0)) {
+                    g0 += active && face == 0;
+                    g1 += active && face == 1;
+                    g2 += active && face == 2;
+                    g3 += active && face == 3;
+                    gbad += active && face == 6;
+                }
+                // spec D: v_old . v_new as an FP32 fma chain, then round(x 2^24) to int64
+                const float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
+                if (active) ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
+                store_state(active, cellp + slot, alive ? (cn[0] | (cn[1] << 16)) : -1, t0p + slot, tn[0], t1p + slot,
+                            tn[1], v0p + slot, v[0], v1p + slot, v[1], v2p + slot, v[2]);
+                // a6: deposit
+                if constexpr (TILE)
+                    deposit_tile(p, tl, s, alive, cn, tn);
+                else
+                    deposit_warp<2>(p, s, alive, cn, tn);
             }
-            // a5: boundaries
-            int face = -1;
-            if (PER0) {
-                cn[0] = wrapi(cn[0], n0);
-            } else {
-                if (cn[0] < 0) face = 0;
-                else if (cn[0] >= n0) face = 1;
-            }
-            if (PER1) {
-                cn[1] = wrapi(cn[1], n1);
-            } else if (face < 0) {
-                if (cn[1] < 0) face = 2;
-                else if (cn[1] >= n1) face = 3;
-            }
-            if (bad) face = 6;
-            const bool alive = active && face < 0;
-            if (active) {
-                g0 += face == 0;
-                g1 += face == 1;
-                g2 += face == 2;
-                g3 += face == 3;
-                gbad += face == 6;
-            }
-            // spec D: v_old . v_new as an FP32 fma chain, then round(x 2^24) to int64
-            const float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
-            if (active) ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
-            if (active) {
-                cellp[slot] = alive ? (cn[0] | (cn[1] << 16)) : -1;
-                t0p[slot] = tn[0];
-                t1p[slot] = tn[1];
-                v0p[slot] = v[0];
-                v1p[slot] = v[1];
-                v2p[slot] = v[2];
-            }
-            // a6: deposit
-            if (tl.on)
-                deposit_tile(p, tl, s, alive, cn, tn);
-            else
-                deposit_warp<2>(p, s, alive, cn, tn);
-        }
+        };
+        if (tl.on)
+            iterate(std::true_type{});
+        else
+            iterate(std::false_type{});
         // flush the tile into the padded grid (rows -1 .. n1 exist there; the others hold
         // nothing)
         if (tl.on) {
