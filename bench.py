@@ -484,7 +484,7 @@ def sphere_measurement(cpic, npart, steps, stream, flush):
 
     cs = ctypes_stream(stream)
     t0 = time.perf_counter()
-    run = cpic.sphere_run_device(128, 128, 128, npart, stream=cs)
+    run = cpic.sphere_run_device(128, 128, 128, npart, stream=cs, inject=True)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     run.step_particles(3)
@@ -532,8 +532,8 @@ def sphere_measurement(cpic, npart, steps, stream, flush):
                          "kernel": "push3d_kernel<absorb,reflect,periodic> (fused gather/push/boundary/deposit, 3D)",
                          "bytes_per_particle": 56, "peak_kind": kind},
             "workload": "3D sphere in plasma: shell r=(30)^xi, theta_c=pi/32 (reflecting caps), 128^3 cells, "
-                        f"{npart}+{npart} particles loaded on the device, phi_obj=-5, dt=0.1, no injection "
-                        "(3D injection not built), fixed-field particle steps, L2 flushed between steps"}
+                        f"{npart}+{npart} particles loaded on the device, phi_obj=-5, dt=0.1, Maxwellian flux "
+                        "injection of both species at r=30, fixed-field particle steps, L2 flushed between steps"}
 
 
 def serving_measurement(cpic, nreq, steps, rate, seed=4):

@@ -504,16 +504,17 @@ def cylinder_run_device(n1, n2, npart_per_species, phi_obj, seed, sort_interval=
 
 
 def sphere_run_device(n1, n2, n3, npart_per_species, phi_obj=-5.0, seed=2, sort_interval=4, arena=None,
-                      stream=None, r0=1.0, R=30.0, theta_c=None):
+                      stream=None, r0=1.0, R=30.0, theta_c=None, inject=False):
     """A 3D sphere-in-plasma run (shell map, reflecting polar caps) loaded on the device
-    with cpic_load_maxwellian and initialised."""
+    with cpic_load_maxwellian and initialised; with inject, Maxwellian flux injection of both
+    species through the outer boundary."""
     import math
 
     from . import workloads as wl
 
     theta_c = math.pi / 32 if theta_c is None else theta_c
     w = wl.sphere(n1=n1, n2=n2, n3=n3, r0=r0, R=R, theta_c=theta_c, npart_per_species=npart_per_species,
-                  phi_obj=phi_obj, seed=seed, host_particles=False)
+                  phi_obj=phi_obj, seed=seed, host_particles=False, inject=inject)
     cfg = config_from_workload(w, sort_interval=sort_interval)
     if arena is None:
         import torch
@@ -524,6 +525,8 @@ def sphere_run_device(n1, n2, n3, npart_per_species, phi_obj=-5.0, seed=2, sort_
     for s, sp in enumerate(w.species):
         run.load_maxwellian(s, npart_per_species, sp.vth, seed=seed * 16 + s)
     run.sort()  # the load draws cells in random order: start in cell order
+    for (s, face, dens, vth, sd) in w.injection:
+        run.set_injection(s, face, dens, vth, sd)
     run.initialize()
     run._keep = arena
     return run

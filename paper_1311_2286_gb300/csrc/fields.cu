@@ -46,7 +46,9 @@ __device__ __forceinline__ double phi_ext(const FieldGrid& g, const double* __re
     return val;
 }
 
-__global__ void vertex_field_kernel(FieldGrid g, const double* __restrict__ phi, float* G) {
+// 3D: G is also written into the three padding words of each vertex's k record (K[12 v + 9 ..
+// 11]), so that the mover's first gather reads k and G in three 16-byte loads per corner.
+__global__ void vertex_field_kernel(FieldGrid g, const double* __restrict__ phi, float* G, float* K) {
     long long nv0 = g.n[0] + 1, nv1 = g.n[1] + 1, nv2 = g.D == 3 ? g.n[2] + 1 : 1;
     long long nvt = nv0 * nv1 * nv2;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvt;
@@ -83,6 +85,10 @@ __global__ void vertex_field_kernel(FieldGrid g, const double* __restrict__ phi,
                 out[a] = __double2float_rn(__dmul_rn(acc, 0.25));
             }
             reinterpret_cast<float4*>(G)[v] = make_float4(out[0], out[1], out[2], 0.0f);
+            float* kr = K + 12 * v;
+            kr[9] = out[0];
+            kr[10] = out[1];
+            kr[11] = out[2];
         }
     }
 }
@@ -179,7 +185,7 @@ int launch_vertex_field(cpic_run* r) {
     FieldGrid g = make_field_grid(r);
     long long b = (r->nvert + 255) / 256;
     if (b > 152 * 8) b = 152 * 8;
-    vertex_field_kernel<<<(int)b, 256, 0, r->stream>>>(g, r->lev[0].x, r->G32);
+    vertex_field_kernel<<<(int)b, 256, 0, r->stream>>>(g, r->lev[0].x, r->G32, r->K32);
     CPIC_CHECK_LAUNCH();
     return CPIC_OK;
 }

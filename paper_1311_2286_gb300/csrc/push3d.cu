@@ -11,7 +11,13 @@
 //     flushed once per chunk; lanes whose 3x3x3 stencil leaves the tile
 //     deposit straight into the padded global grid. With ~30 particles per cell, most lanes
 //     of a warp hold a few neighbouring cells, and sending each lane's 27 node weights to L2
-//     as 64-bit atomics would bind the kernel on L2 atomic throughput.
+//     as 64-bit atomics would bind the kernel on L2 atomic throughput;
+//   - instruction economy as in the 2D kernel: component pairs of the gathers in packed
+//     FP32x2 arithmetic (each lane rounds as the scalar form), the tile atomics' carries
+//     collected in a bit mask, predicated state stores, the iteration loop specialised on
+//     whether the chunk's tile is in use.
+#include <type_traits>
+
 #include "particles.cuh"
 
 namespace cpic {
@@ -21,26 +27,37 @@ using namespace pk;
 
 constexpr int P3_THREADS = 256;
 constexpr int P3_CHUNK = 4096;        // particles per chunk (a few rows of one plane)
-constexpr int P3_TILE_CELLS = 8192;   // 64 KB of shared memory (two 32-bit words per cell); the
-                                      // kernel's registers allow two blocks per SM anyway
+constexpr int P3_TILE_CELLS = 8192;   // 64 KB of shared memory (two 32-bit words per cell):
+                                      // three blocks per SM (80 registers a thread)
 
 enum { K_PER = CPIC_PBC_PERIODIC, K_ABS = CPIC_PBC_ABSORB, K_REF = CPIC_PBC_REFLECT };
 
 struct Tile3 {
-    unsigned* lo;
-    unsigned* hi;
+    unsigned lo;        // shared-memory address of the low words
+    unsigned* hi_ptr;   // the high words
     int k0, P, j0, R, W;  // planes [k0, k0 + P), rows [j0, j0 + R), W = n0 + 2 columns
     bool on;
 };
 
-__device__ __forceinline__ void tile3_add(const Tile3& tl, int i, unsigned v) {
-    const unsigned old = atomicAdd(tl.lo + i, v);
-    if (old + v < old) atomicAdd(tl.hi + i, 1u);
+#define CPIC_TILE3_ADD(OFF, ARG)                        \
+    "atom.shared.add.u32 o, [%1+" OFF "], " ARG ";\n\t" \
+    "add.cc.u32 s, o, " ARG ";\n\t"                      \
+    "addc.u32 %0, %0, %0;\n\t"
+
+// adds q0, q1, q2 to three consecutive low words from shared address a (32-bit atomics); m is
+// shifted left by one bit per word and takes the word's carry out in its lowest bit
+__device__ __forceinline__ void tile3_add_row(unsigned& m, unsigned a, unsigned q0, unsigned q1, unsigned q2) {
+    asm volatile("{\n\t.reg .u32 o, s;\n\t" CPIC_TILE3_ADD("0", "%2") CPIC_TILE3_ADD("4", "%3")
+                     CPIC_TILE3_ADD("8", "%4") "}"
+                 : "+r"(m)
+                 : "r"(a), "r"(q0), "r"(q1), "r"(q2)
+                 : "memory");
 }
 
 // Deposit of one particle per lane into the chunk's tile; lanes whose stencil leaves the
-// tile deposit into the padded global grid (deposit_warp). Lanes sharing a cell are summed
-// first (largest group, __reduce_add_sync) so that the tile's atomics rarely collide.
+// tile deposit into the padded global grid (deposit_warp). The largest group of lanes that
+// share a cell is summed first (__reduce_add_sync over the group) and deposited by one lane.
+// Node weights are produced and deposited one row of three at a time (nine rows).
 __device__ __forceinline__ void deposit_tile3(const PushParams& p, const Tile3& tl, int s, bool alive, const int* c,
                                               const float* t) {
     const int lane = threadIdx.x & 31;
@@ -48,39 +65,114 @@ __device__ __forceinline__ void deposit_tile3(const PushParams& p, const Tile3& 
     const bool in = alive && pz >= 1 && pz + 1 < tl.P && ry >= 1 && ry + 1 < tl.R;
     const bool out = alive && !in;
     if (__any_sync(FULL, out)) deposit_warp<3>(p, s, out, c, t);
-    const unsigned live = __ballot_sync(FULL, in);
-    if (!live) return;
+    if (!__any_sync(FULL, in)) return;
     int w[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) axis_weights<3>(in ? t[a] : 0.0f, w[a]);
-    if (!in) w[0][0] = w[0][1] = w[0][2] = 0;
-    int off = (pz * tl.R + ry) * tl.W + c[0] + 1;
-    const int off_first = __shfl_sync(FULL, off, __ffs(live) - 1);
-    if (!in) off = off_first;
+    for (int a = 0; a < 3; ++a) axis_weights<3>(t[a], w[a]);
+    // lanes that do not deposit here get keys of their own
+    const int off = in ? (pz * tl.R + ry) * tl.W + c[0] + 1 : -1 - lane;
     const unsigned peers = __match_any_sync(FULL, off);
-    const unsigned score = ((unsigned)__popc(peers) << 5) | (31u - (unsigned)(__ffs(peers) - 1));
+    const unsigned score = ((unsigned)__popc(peers) << 5) | (unsigned)(31 - __clz(peers));
     const unsigned best = __reduce_max_sync(FULL, score);
-    const bool grouped = (best >> 5) > 1;
-    const int leader = 31 - (int)(best & 31u);
-    const bool mine = grouped && off == __shfl_sync(FULL, off, leader);
-    const bool issue = mine ? lane == leader : in;
+    const int leader = (int)(best & 31u);
+    const bool group = (best >> 5) > 1 && ((peers >> leader) & 1u);  // lanes of the largest group
+    const bool issue = group ? lane == leader : in;
     const int plane = tl.R * tl.W;
+    const unsigned base = tl.lo + 4u * (unsigned)(off - 1 - tl.W - plane);
+    unsigned m = 0;  // carry out of node (m0, m1, m2)'s low word in bit 26 - (m0 + 3 m1 + 9 m2)
 #pragma unroll
     for (int m2 = 0; m2 < 3; ++m2)
 #pragma unroll
         for (int m1 = 0; m1 < 3; ++m1) {
-            const unsigned w01 = (unsigned)(w[1][m1] * w[2][m2]);
+            const unsigned w12 = (unsigned)(w[1][m1] * w[2][m2]);
+            unsigned q0 = (unsigned)w[0][0] * w12, q1 = (unsigned)w[0][1] * w12, q2 = (unsigned)w[0][2] * w12;
+            if (group) {
+                q0 = __reduce_add_sync(peers, q0);
+                q1 = __reduce_add_sync(peers, q1);
+                q2 = __reduce_add_sync(peers, q2);
+            }
+            if (issue) tile3_add_row(m, base + 4u * (unsigned)(m1 * tl.W + m2 * plane), q0, q1, q2);
+        }
+    if (issue && m) {  // rare: carries into the high words
+        unsigned* hi = tl.hi_ptr + (off - 1 - tl.W - plane);
 #pragma unroll
-            for (int m0 = 0; m0 < 3; ++m0) {
-                unsigned q = (unsigned)w[0][m0] * w01;
-                if (grouped) {
-                    const unsigned tot = __reduce_add_sync(FULL, mine ? q : 0u);
-                    q = mine ? tot : q;
-                }
-                const int d = (m0 - 1) + (m1 - 1) * tl.W + (m2 - 1) * plane;
-                if (issue && q) tile3_add(tl, off + d, q);
+        for (int node = 0; node < 27; ++node)
+            if ((m >> (26 - node)) & 1u) atomicAdd(hi + (node % 3) + ((node / 3) % 3) * tl.W + (node / 9) * plane, 1u);
+    }
+}
+
+// the seven state words of one particle, stored when p holds (predicated, no branch)
+__device__ __forceinline__ void store_state3(bool p, int* c, int cv, float* t0, float* t1, float* t2, const float* t,
+                                             float* v0, float* v1, float* v2, const float* v) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+        "@q st.global.b32 [%1], %2;\n\t@q st.global.f32 [%3], %4;\n\t@q st.global.f32 [%5], %6;\n\t"
+        "@q st.global.f32 [%7], %8;\n\t@q st.global.f32 [%9], %10;\n\t@q st.global.f32 [%11], %12;\n\t"
+        "@q st.global.f32 [%13], %14;\n\t}" ::"r"((unsigned)p),
+        "l"(c), "r"(cv), "l"(t0), "f"(t[0]), "l"(t1), "f"(t[1]), "l"(t2), "f"(t[2]), "l"(v0), "f"(v[0]), "l"(v1),
+        "f"(v[1]), "l"(v2), "f"(v[2])
+        : "memory");
+}
+
+// b1 gather of the vertex k table (and G when gp is given) at vertex v0 of the cell, offsets
+// t: the same products and accumulation order as the scalar form, component pairs in packed
+// FP32x2 arithmetic. A vertex record holds k (9 words) and G (3 words, written there by the
+// vertex-field pass), so both come in three 16-byte loads.
+__device__ __forceinline__ void gather3(const PushParams& p, int v0, const float* t, float* kp, float* gp) {
+    const float4* K4 = reinterpret_cast<const float4*>(p.K);
+    const int nv0 = p.n[0] + 1, nv01 = nv0 * (p.n[1] + 1);
+    const float s[3] = {__fsub_rn(1.0f, t[0]), __fsub_rn(1.0f, t[1]), __fsub_rn(1.0f, t[2])};
+    float2 k01, k23, k45, k67, g01;
+    float k8, g2;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const float w = __fmul_rn(__fmul_rn((o & 1) ? t[0] : s[0], (o & 2) ? t[1] : s[1]), (o & 4) ? t[2] : s[2]);
+        const int v = v0 + ((o & 1) ? 1 : 0) + ((o & 2) ? nv0 : 0) + ((o & 4) ? nv01 : 0);
+        const float4 a = __ldg(K4 + 3 * v), b = __ldg(K4 + 3 * v + 1);
+        float4 g;  // (k22, G0, G1, G2)
+        if (gp)
+            g = __ldg(K4 + 3 * v + 2);
+        else
+            g.x = __ldg(reinterpret_cast<const float*>(K4 + 3 * v + 2));
+        const float c = g.x;
+        const float2 ww = make_float2(w, w);
+        if (o == 0) {
+            k01 = __fmul2_rn(ww, make_float2(a.x, a.y));
+            k23 = __fmul2_rn(ww, make_float2(a.z, a.w));
+            k45 = __fmul2_rn(ww, make_float2(b.x, b.y));
+            k67 = __fmul2_rn(ww, make_float2(b.z, b.w));
+            k8 = __fmul_rn(w, c);
+        } else {
+            k01 = __ffma2_rn(ww, make_float2(a.x, a.y), k01);
+            k23 = __ffma2_rn(ww, make_float2(a.z, a.w), k23);
+            k45 = __ffma2_rn(ww, make_float2(b.x, b.y), k45);
+            k67 = __ffma2_rn(ww, make_float2(b.z, b.w), k67);
+            k8 = __fmaf_rn(w, c, k8);
+        }
+        if (gp) {
+            if (o == 0) {
+                g01 = __fmul2_rn(ww, make_float2(g.y, g.z));
+                g2 = __fmul_rn(w, g.w);
+            } else {
+                g01 = __ffma2_rn(ww, make_float2(g.y, g.z), g01);
+                g2 = __fmaf_rn(w, g.w, g2);
             }
         }
+    }
+    kp[0] = k01.x;
+    kp[1] = k01.y;
+    kp[2] = k23.x;
+    kp[3] = k23.y;
+    kp[4] = k45.x;
+    kp[5] = k45.y;
+    kp[6] = k67.x;
+    kp[7] = k67.y;
+    kp[8] = k8;
+    if (gp) {
+        gp[0] = g01.x;
+        gp[1] = g01.y;
+        gp[2] = g2;
+    }
 }
 
 template <int KIND>
@@ -104,7 +196,7 @@ __device__ __forceinline__ void predict_axis3(float x, int c, int n, int& cp, fl
 }
 
 template <int K0, int K1, int K2>
-__global__ void __launch_bounds__(P3_THREADS, 2) push3d_kernel(PushParams p) {
+__global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
     extern __shared__ unsigned tile_dyn[];  // [P3_TILE_CELLS] low words, then high words
     unsigned* tile_lo = tile_dyn;
     unsigned* tile_hi = tile_dyn + P3_TILE_CELLS;
@@ -147,8 +239,8 @@ __global__ void __launch_bounds__(P3_THREADS, 2) push3d_kernel(PushParams p) {
         // tile: planes and rows of the chunk's (sampled) particles, one plane and one row
         // of margin each side for the stencil
         Tile3 tl;
-        tl.lo = tile_lo;
-        tl.hi = tile_hi;
+        tl.lo = (unsigned)__cvta_generic_to_shared(tile_lo);
+        tl.hi_ptr = tile_hi;
         tl.W = n0 + 2;
         {
             const int si = lo + (int)(((long long)(hi - lo - 1) * threadIdx.x) / (P3_THREADS - 1));
@@ -185,14 +277,14 @@ __global__ void __launch_bounds__(P3_THREADS, 2) push3d_kernel(PushParams p) {
                 kmin = min(kmin, red[2][w]);
                 kmax = max(kmax, red[3][w]);
             }
-            // the sampled rows and planes with the stencil's neighbours. Between sorts some
-            // particles have moved to neighbouring planes (azimuthal cells near the polar caps
-            // are small), so a spread of up to two planes is taken; particles outside the
-            // tile deposit through the global path
-            tl.j0 = jmin - 1;
-            tl.R = jmax - jmin + 3;
-            tl.k0 = kmin - 1;
-            tl.P = kmax - kmin + 3;
+            // the sampled rows and planes, one more on each side for particles that moved
+            // there since the last sort (azimuthal cells near the polar caps are small), and
+            // the stencil's neighbours; a spread of up to two sampled planes is taken.
+            // Particles outside the tile deposit through the global path
+            tl.j0 = jmin - 2;
+            tl.R = jmax - jmin + 5;
+            tl.k0 = kmin - 2;
+            tl.P = kmax - kmin + 5;
             if (kmax - kmin > 2) tl.P = 0x7fff;  // a chunk across many planes: no tile
             tl.on = kmax >= kmin && tl.P * tl.R * tl.W <= P3_TILE_CELLS;
             if (tl.on)
@@ -213,131 +305,134 @@ __global__ void __launch_bounds__(P3_THREADS, 2) push3d_kernel(PushParams p) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + i];
         }
-        for (int base = lo; base < hi; base += P3_THREADS) {
-            const int slot = i;
-            const int cw = ncw;
-            float t[3] = {nt[0], nt[1], nt[2]};
-            float v[3] = {nv[0], nv[1], nv[2]};
-            i += P3_THREADS;
-            ncw = -1;
-            if (i < hi) {
-                ncw = cellp[i];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) nt[a] = tq0[a * T + i];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + i];
-            }
-            const bool active = cw >= 0;
-            int c[3] = {active ? (cw & 1023) : 0, active ? ((cw >> 10) & 1023) : 0, active ? (cw >> 20) : 0};
-            if (!active) t[0] = t[1] = t[2] = v[0] = v[1] = v[2] = 0.0f;
+        // the iteration loop, specialised on whether the chunk's tile is in use
+        auto iterate = [&](auto tile_tag) {
+            constexpr bool TILE = decltype(tile_tag)::value;
+            for (int base = lo; base < hi; base += P3_THREADS) {
+                const int slot = i;
+                const int cw = ncw;
+                float t[3] = {nt[0], nt[1], nt[2]};
+                float v[3] = {nv[0], nv[1], nv[2]};
+                i += P3_THREADS;
+                ncw = -1;
+                if (i < hi) {
+                    ncw = cellp[i];
+    #pragma unroll
+                    for (int a = 0; a < 3; ++a) nt[a] = tq0[a * T + i];
+    #pragma unroll
+                    for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + i];
+                }
+                const bool active = cw >= 0;
+                int c[3] = {active ? (cw & 1023) : 0, active ? ((cw >> 10) & 1023) : 0, active ? (cw >> 20) : 0};
+                if (!active) t[0] = t[1] = t[2] = v[0] = v[1] = v[2] = 0.0f;
 
-            // a2: b1 gather of k and G at xi^n
-            float kp[9], gp[3];
-            Tab<3>::gather(p, vertex_of<3>(p, c), t, kp, gp);
-            // a3: E^al = -sum_a G^a k^{a al}, kick
-            const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
-#pragma unroll
-            for (int al = 0; al < 3; ++al) {
-                float e = __fmul_rn(kp[al], gp[0]);
-                e = __fmaf_rn(kp[3 + al], gp[1], e);
-                e = __fmaf_rn(kp[6 + al], gp[2], e);
-                v[al] = __fmaf_rn(dtqm, -e, v[al]);
-            }
-            // a4: predictor
-            int cpred[3];
-            float tpred[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float d = __fmul_rn(kp[3 * a], v[0]);
-                d = __fmaf_rn(kp[3 * a + 1], v[1], d);
-                d = __fmaf_rn(kp[3 * a + 2], v[2], d);
-                float x = __fmaf_rn(hdt, d, t[a]);
-                if (!isfinite(x)) x = t[a];
-                if (KIND[a] == K_PER)
-                    predict_axis3<K_PER>(x, c[a], p.n[a], cpred[a], tpred[a]);
-                else
-                    predict_axis3<K_ABS>(x, c[a], p.n[a], cpred[a], tpred[a]);
-            }
-            float kq[9];
-            Tab<3>::gather(p, vertex_of<3>(p, cpred), tpred, kq, nullptr);
-            // corrector
-            bool bad = false;
-            int cn[3];
-            float tn[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float d = __fmul_rn(kq[3 * a], v[0]);
-                d = __fmaf_rn(kq[3 * a + 1], v[1], d);
-                d = __fmaf_rn(kq[3 * a + 2], v[2], d);
-                float x = __fmaf_rn(dt, d, t[a]);
-                if (!isfinite(x)) {
-                    bad = true;
-                    x = t[a];
+                // a2: b1 gather of k and G at xi^n
+                float kp[9], gp[3];
+                gather3(p, vertex_of<3>(p, c), t, kp, gp);
+                // a3: E^al = -sum_a G^a k^{a al}, kick
+                const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
+    #pragma unroll
+                for (int al = 0; al < 3; ++al) {
+                    float e = __fmul_rn(kp[al], gp[0]);
+                    e = __fmaf_rn(kp[3 + al], gp[1], e);
+                    e = __fmaf_rn(kp[6 + al], gp[2], e);
+                    v[al] = __fmaf_rn(dtqm, -e, v[al]);
                 }
-                int dc;
-                renorm(x, tn[a], dc);
-                cn[a] = c[a] + dc;
-            }
-            // a5: boundaries (periodic wrap, absorption), then spec B after the tally
-            int face = -1;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (KIND[a] == K_PER) {
-                    cn[a] = wrapi(cn[a], p.n[a]);
-                } else if (KIND[a] == K_ABS && face < 0) {
-                    if (cn[a] < 0) face = 2 * a;
-                    else if (cn[a] >= p.n[a]) face = 2 * a + 1;
-                }
-            }
-            if (bad) face = 6;
-            const float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
-            if (active) ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
-            if (face < 0) {
-#pragma unroll
+                // a4: predictor
+                int cpred[3];
+                float tpred[3];
+    #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    if (KIND[a] != K_REF || face >= 0 || (cn[a] >= 0 && cn[a] < p.n[a])) continue;
-                    const bool below = cn[a] < 0;
-                    int c2 = below ? (-cn[a] - 1) : (2 * p.n[a] - 1 - cn[a]);
-                    float t2 = __fsub_rn(1.0f, tn[a]);
-                    if (t2 >= 1.0f) {
-                        t2 = 0.0f;
-                        c2 += 1;
-                    }
-                    if (c2 < 0 || c2 >= p.n[a]) {
-                        face = 2 * a + (below ? 0 : 1);
-                        continue;
-                    }
-                    cn[a] = c2;
-                    tn[a] = t2;
-                    float nn = __fmul_rn(kq[3 * a], kq[3 * a]);
-                    float dot = __fmul_rn(v[0], kq[3 * a]);
-                    nn = __fmaf_rn(kq[3 * a + 1], kq[3 * a + 1], nn);
-                    dot = __fmaf_rn(v[1], kq[3 * a + 1], dot);
-                    nn = __fmaf_rn(kq[3 * a + 2], kq[3 * a + 2], nn);
-                    dot = __fmaf_rn(v[2], kq[3 * a + 2], dot);
-                    const float sf = __fdiv_rn(__fmul_rn(2.0f, dot), nn);
-#pragma unroll
-                    for (int al = 0; al < 3; ++al) v[al] = __fmaf_rn(-sf, kq[3 * a + al], v[al]);
+                    float d = __fmul_rn(kp[3 * a], v[0]);
+                    d = __fmaf_rn(kp[3 * a + 1], v[1], d);
+                    d = __fmaf_rn(kp[3 * a + 2], v[2], d);
+                    float x = __fmaf_rn(hdt, d, t[a]);
+                    if (!isfinite(x)) x = t[a];
+                    if (KIND[a] == K_PER)
+                        predict_axis3<K_PER>(x, c[a], p.n[a], cpred[a], tpred[a]);
+                    else
+                        predict_axis3<K_ABS>(x, c[a], p.n[a], cpred[a], tpred[a]);
                 }
+                float kq[9];
+                gather3(p, vertex_of<3>(p, cpred), tpred, kq, nullptr);
+                // corrector
+                bool bad = false;
+                int cn[3];
+                float tn[3];
+    #pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    float d = __fmul_rn(kq[3 * a], v[0]);
+                    d = __fmaf_rn(kq[3 * a + 1], v[1], d);
+                    d = __fmaf_rn(kq[3 * a + 2], v[2], d);
+                    float x = __fmaf_rn(dt, d, t[a]);
+                    if (!isfinite(x)) {
+                        bad = true;
+                        x = t[a];
+                    }
+                    int dc;
+                    renorm(x, tn[a], dc);
+                    cn[a] = c[a] + dc;
+                }
+                // a5: boundaries (periodic wrap, absorption), then spec B after the tally
+                int face = -1;
+    #pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (KIND[a] == K_PER) {
+                        cn[a] = wrapi(cn[a], p.n[a]);
+                    } else if (KIND[a] == K_ABS && face < 0) {
+                        if (cn[a] < 0) face = 2 * a;
+                        else if (cn[a] >= p.n[a]) face = 2 * a + 1;
+                    }
+                }
+                if (bad) face = 6;
+                const float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
+                if (active) ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
+                if (face < 0) {
+    #pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        if (KIND[a] != K_REF || face >= 0 || (cn[a] >= 0 && cn[a] < p.n[a])) continue;
+                        const bool below = cn[a] < 0;
+                        int c2 = below ? (-cn[a] - 1) : (2 * p.n[a] - 1 - cn[a]);
+                        float t2 = __fsub_rn(1.0f, tn[a]);
+                        if (t2 >= 1.0f) {
+                            t2 = 0.0f;
+                            c2 += 1;
+                        }
+                        if (c2 < 0 || c2 >= p.n[a]) {
+                            face = 2 * a + (below ? 0 : 1);
+                            continue;
+                        }
+                        cn[a] = c2;
+                        tn[a] = t2;
+                        float nn = __fmul_rn(kq[3 * a], kq[3 * a]);
+                        float dot = __fmul_rn(v[0], kq[3 * a]);
+                        nn = __fmaf_rn(kq[3 * a + 1], kq[3 * a + 1], nn);
+                        dot = __fmaf_rn(v[1], kq[3 * a + 1], dot);
+                        nn = __fmaf_rn(kq[3 * a + 2], kq[3 * a + 2], nn);
+                        dot = __fmaf_rn(v[2], kq[3 * a + 2], dot);
+                        const float sf = __fdiv_rn(__fmul_rn(2.0f, dot), nn);
+    #pragma unroll
+                        for (int al = 0; al < 3; ++al) v[al] = __fmaf_rn(-sf, kq[3 * a + al], v[al]);
+                    }
+                }
+                const bool alive = active && face < 0;
+                if (active && face >= 0) {
+    #pragma unroll
+                    for (int f = 0; f < 7; ++f) gone[f] += face == f;
+                }
+                store_state3(active, cellp + slot, alive ? (cn[0] | (cn[1] << 10) | (cn[2] << 20)) : -1, tq0 + slot,
+                             tq0 + T + slot, tq0 + 2 * T + slot, tn, vq0 + slot, vq0 + T + slot, vq0 + 2 * T + slot, v);
+                // a6: deposit
+                if constexpr (TILE)
+                    deposit_tile3(p, tl, s, alive, cn, tn);
+                else
+                    deposit_warp<3>(p, s, alive, cn, tn);
             }
-            const bool alive = active && face < 0;
-            if (active && face >= 0) {
-#pragma unroll
-                for (int f = 0; f < 7; ++f) gone[f] += face == f;
-            }
-            if (active) {
-                cellp[slot] = alive ? (cn[0] | (cn[1] << 10) | (cn[2] << 20)) : -1;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) tq0[a * T + slot] = tn[a];
-#pragma unroll
-                for (int al = 0; al < 3; ++al) vq0[al * T + slot] = v[al];
-            }
-            // a6: deposit
-            if (tl.on)
-                deposit_tile3(p, tl, s, alive, cn, tn);
-            else
-                deposit_warp<3>(p, s, alive, cn, tn);
-        }
+        };
+        if (tl.on)
+            iterate(std::true_type{});
+        else
+            iterate(std::false_type{});
         // flush the tile into the padded grid
         if (tl.on) {
             __syncthreads();

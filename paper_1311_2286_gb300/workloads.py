@@ -320,12 +320,14 @@ def cylinder(n1=128, n2=256, r0=1.0, R=40.0, npart_per_species=2_000_000, phi_ob
 
 
 def sphere(n1=128, n2=128, n3=128, r0=1.0, R=30.0, theta_c=math.pi / 32, npart_per_species=32_000_000,
-           phi_obj=-5.0, mass_ratio=1836.0, dt=0.1, seed=2, capacity_factor=1.5, host_particles=True):
+           phi_obj=-5.0, mass_ratio=1836.0, dt=0.1, seed=2, capacity_factor=1.5, host_particles=True,
+           inject=False):
     """3D sphere in plasma on the shell map r = r0 (R/r0)^xi, theta = theta_c + (pi -
     2 theta_c) eta, phi = 2 pi zeta (polar caps cut out): object at xi = 0 held at phi_obj
     and absorbing, outer boundary at 0 and absorbing, polar caps Neumann for the field and
     specular for particles, zeta periodic. Electrons and ions (T_i = T_e), uniform in
-    physical space at density 1."""
+    physical space at density 1; with inject, both species enter as Maxwellian flux through
+    the outer boundary (face 1) at density 1."""
     rng = np.random.default_rng(seed)
     vol = (4.0 / 3.0) * math.pi * (R**3 - r0**3) * math.cos(theta_c)
     w = vol / npart_per_species
@@ -338,6 +340,9 @@ def sphere(n1=128, n2=128, n3=128, r0=1.0, R=30.0, theta_c=math.pi / 32, npart_p
     else:
         parts = [ParticleSet(np.zeros(0, np.int32), np.zeros((3, 0), np.float32), np.zeros((3, 0), np.float32))
                  for _ in sp]
+    inj = []
+    if inject:
+        inj = [(0, 1, 1.0, 1.0, seed * 1000 + 7), (1, 1, 1.0, vti, seed * 1000 + 8)]
     return Workload(
         name=f"sphere_{n1}x{n2}x{n3}_{2 * npart_per_species}",
         dim=3,
@@ -349,6 +354,7 @@ def sphere(n1=128, n2=128, n3=128, r0=1.0, R=30.0, theta_c=math.pi / 32, npart_p
         dt=dt,
         species=sp,
         particles=parts,
+        injection=inj,
     )
 
 
