@@ -215,6 +215,22 @@ int cpic_sort(cpic_run* run);
  * cycle. cycles, residual: host, may be NULL. CPIC_ERR_NOT_CONVERGED if rtol was not met. */
 int cpic_solve_field(cpic_run* run, double rtol, int max_cycles, int* cycles, double* residual);
 
+/* Outer iteration of the field solve on the kernel-chain path (3D runs, and 2D runs that the
+ * one-cluster solver does not take; the cluster solver always iterates V-cycles):
+ *   CPIC_SOLVER_MG        x += V-cycle(b - M x) until ||r||/||b|| <= rtol (Sec. II.B.3's
+ *                         multigrid iteration);
+ *   CPIC_SOLVER_BICGSTAB  BiCGStab (van der Vorst, SIAM J. Sci. Stat. Comput. 13, 1992) on
+ *                         M x = b, right-preconditioned by the same FP32 V-cycle: two V-cycles,
+ *                         two FP64 products with M and one FP64 residual per iteration, the
+ *                         residual recomputed from x every iteration (the default: about half
+ *                         the V-cycles on the 3D shell, and it converges where point smoothing
+ *                         alone stalls on strongly anisotropic cells). The stopping test and
+ *                         the result's accuracy are the same; mg_cycles counts V-cycles.
+ * Invalidates the run's captured step graphs. CPIC_ERR_INVALID for another value. */
+#define CPIC_SOLVER_MG 0
+#define CPIC_SOLVER_BICGSTAB 1
+int cpic_set_solver(cpic_run* run, int solver);
+
 /* ---------------------------------------------------------------- data out / in */
 
 int cpic_get_diag(cpic_run* run, cpic_diag* out);              /* synchronises */

@@ -23,6 +23,7 @@ CPIC_ERR_CAPACITY, CPIC_ERR_NOT_BUILT = -9, -10
 CPIC_BC_PERIODIC, CPIC_BC_DIRICHLET, CPIC_BC_NEUMANN = 0, 1, 2
 CPIC_PBC_PERIODIC, CPIC_PBC_ABSORB, CPIC_PBC_REFLECT = 0, 1, 2
 CPIC_MAP_SINE, CPIC_MAP_ANNULUS, CPIC_MAP_SPHERE_AXISYM, CPIC_MAP_SHELL = 1, 2, 3, 4
+CPIC_SOLVER_MG, CPIC_SOLVER_BICGSTAB = 0, 1
 MAX_SPECIES = 4
 
 
@@ -152,6 +153,7 @@ _SIGS = {
     "cpic_batch_synchronize": ([P], ctypes.c_int),
     "cpic_get_config": ([P, P], ctypes.c_int),
     "cpic_set_sort_interval": ([P, ctypes.c_int], ctypes.c_int),
+    "cpic_set_solver": ([P, ctypes.c_int], ctypes.c_int),
     "cpic_autotune": ([P, ctypes.c_int, P], ctypes.c_int),
     "cpic_checkpoint": ([P, ctypes.c_char_p], ctypes.c_int),
     "cpic_restore": ([ctypes.c_char_p, P, ctypes.c_size_t, P, ctypes.POINTER(P)], ctypes.c_int),
@@ -337,6 +339,11 @@ class Run:
 
     def set_sort_interval(self, interval):
         check(load().cpic_set_sort_interval(self.h, interval))
+
+    def set_solver(self, solver):
+        """CPIC_SOLVER_MG (V-cycle iteration) or CPIC_SOLVER_BICGSTAB (V-cycle-preconditioned
+        BiCGStab) for the kernel-chain field solve."""
+        check(load().cpic_set_solver(self.h, solver))
 
     def autotune(self, trial_steps=8):
         """Choose the sort interval by timing fixed-field particle steps (state restored)."""

@@ -123,7 +123,10 @@ int plan_levels(const cpic_config* c, int lev_n[MAX_LEVELS][3], int* nl) {
         for (int a = 0; a < 3; ++a) lev_n[l][a] = n[a];
         long long cells = (long long)n[0] * n[1] * n[2];
         bool can = cells > 64 && l + 1 < MAX_LEVELS;
-        for (int a = 0; a < c->dim; ++a) can = can && (n[a] % 2 == 0) && n[a] >= 4;
+        // a periodic axis keeps at least four cells: with two, a cell spans half the period
+        // and a curved map (azimuth) makes it degenerate (vertices on opposite sides)
+        for (int a = 0; a < c->dim; ++a)
+            can = can && (n[a] % 2 == 0) && n[a] >= (c->field_bc[2 * a] == CPIC_BC_PERIODIC ? 8 : 4);
         ++l;
         if (!can) break;
         for (int a = 0; a < c->dim; ++a) n[a] /= 2;
@@ -194,6 +197,9 @@ void plan(cpic_run* r, Planner& P) {
     }
     r->ctr = P.take<DevCounters>(1);
     r->red = P.take<double>(2 * 1024 + 8);
+    r->kry = P.take<KrylovState>(1);
+    r->kv = P.take<double>((size_t)5 * r->ncell);
+    r->ph32 = P.take<float>(r->ncell);
     r->hist = P.take<int>((size_t)c.n_species * r->ncell);
     r->scan = P.take<long long>((size_t)c.n_species * r->ncell + 1);
     r->scan_blocks = P.take<long long>(1025);
@@ -225,8 +231,8 @@ void init_geometry_sizes(cpic_run* r, const cpic_config* cfg) {
         r->nvert *= r->nvert_axis[a];
         if (a < r->D) r->ncell_h *= r->n[a] + 2;
     }
-    // default cycle cap: point smoothing needs about 55 V-cycles on the 128^3 shell
-    // (strong azimuthal coupling near the polar caps), 10-15 on the 2D maps
+    // default cycle cap: the V-cycle iteration needs about 50 V-cycles on the 128^3 shell
+    // (strong azimuthal coupling near the polar caps; BiCGStab about 22), 10-15 on the 2D maps
     if (r->cfg.mg_max_cycles <= 0) r->cfg.mg_max_cycles = 100;
     if (!(r->cfg.mg_rtol > 0.0)) r->cfg.mg_rtol = 1e-10;
     r->singular = true;
@@ -611,6 +617,19 @@ int cpic_set_sort_interval(cpic_run* r, int interval) {
     return CPIC_OK;
 }
 
+int cpic_set_solver(cpic_run* r, int solver) {
+    CHECK_RUN(r);
+    if (solver != CPIC_SOLVER_MG && solver != CPIC_SOLVER_BICGSTAB) {
+        set_error("set_solver: unknown solver %d", solver);
+        return CPIC_ERR_INVALID;
+    }
+    if (r->solver != solver) {
+        r->solver = solver;
+        invalidate_graphs(r);  // captured steps hold the solve
+    }
+    return CPIC_OK;
+}
+
 int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* stream, cpic_run** out) {
     if (!out) {
         set_error("out is NULL");
@@ -621,6 +640,7 @@ int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* s
     if (st) return st;
     cpic_run* r = new cpic_run;
     memset(r, 0, sizeof(*r));
+    r->solver = CPIC_SOLVER_BICGSTAB;
     init_geometry_sizes(r, cfg);
     st = setup_levels(r);
     if (st) {

@@ -56,6 +56,15 @@ struct DevCounters {
     int mg_converged;
 };
 
+// Scalars and reduction partials of the Krylov solve (device).
+constexpr int KRY_BLOCKS = 256;
+struct KrylovState {
+    double rho, alpha, omega, beta;
+    int restart;       // the next direction step starts over: r_hat = r, p = r
+    unsigned ticket;   // last-block counter of the Krylov reductions
+    double part[3 * KRY_BLOCKS];
+};
+
 // Particle storage: two buffers (sort ping-pong), each a structure of arrays over all
 // species; species s owns slots [base[s], base[s] + capacity[s]).
 struct ParticleBuffers {
@@ -159,6 +168,10 @@ struct cpic_run {
     bool singular;
     double sumJ;                 // sum of finest J_c (singular projection)
     double* red;                 // reduction scratch [2 * 1024 + 8]
+    int solver;                  // CPIC_SOLVER_* of the stream solve
+    cpic::KrylovState* kry;      // device scalars of the Krylov solve
+    double* kv;                  // Krylov vectors, FP64 [5][ncell]: r, r_hat, p, v, s
+    float* ph32;                 // preconditioned direction p_hat (FP32)
     // sort scratch
     int* hist;                   // [nsp][ncell] counts -> cursors
     long long* scan;             // [nsp*ncell + 1] exclusive prefix

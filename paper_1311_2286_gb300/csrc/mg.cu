@@ -28,6 +28,15 @@
 // right-hand side projected by subtracting a uniform physical charge density and its
 // solution gauged to sum_c J_c phi_c = 0.
 //
+// Optional outer Krylov iteration (cpic_set_solver): BiCGStab (van der Vorst 1992) on
+// M phi = b, right-preconditioned by the same FP32 V-cycle, on the kernel-chain path. One
+// iteration: p = r + beta (p - omega v); p^ = V(p); v = M p^, alpha = rho / (r^, v);
+// s = r - alpha v; s^ = V(s); t = M s^, omega = (t, s) / (t, t); phi += alpha p^ + omega s^;
+// then r = b - M phi is recomputed in FP64 (not updated), so the stopping test sees the true
+// residual, and rho' = (r^, r), beta = (rho' / rho)(alpha / omega). A vanishing rho, alpha
+// or omega restarts the recurrence with r^ = p = r. The products with M are FP64 on the FP32
+// preconditioned vectors; phi is only ever changed by FP64 additions of those vectors.
+//
 // The residual kernel ends with a last-block reduction that decides whether to continue;
 // it writes the decision into a CUDA graph conditional handle, so inside a captured step
 // the cycle loop is a conditional WHILE node that runs on the device with no host round
@@ -154,6 +163,34 @@ __device__ __forceinline__ R stencil_sum(const LV<R>& L, int c, const int* q) {
         s += L.A[k * L.ncell + c] * L.x[idx];
     }
     return s;
+}
+
+// sum_k A_k y_{nb_k} with the level's coefficients (type R) and values y of type TX,
+// accumulated in R
+template <int D, int NPT, typename R, typename TX>
+__device__ __forceinline__ R stencil_apply(const LV<R>& L, const TX* __restrict__ y, int c, const int* q) {
+    int lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        lo[a] = q[a] > 0 ? q[a] - 1 : (L.per[a] ? L.n[a] - 1 : 0);
+        hi[a] = q[a] + 1 < L.n[a] ? q[a] + 1 : (L.per[a] ? 0 : L.n[a] - 1);
+    }
+    const int ix[3] = {lo[0], q[0], hi[0]};
+    const int jy[3] = {L.n[0] * lo[1], L.n[0] * q[1], L.n[0] * hi[1]};
+    int kz[3] = {0, 0, 0};
+    if (D == 3) {
+        const int pl = L.n[0] * L.n[1];
+        kz[0] = pl * lo[2];
+        kz[1] = pl * q[2];
+        kz[2] = pl * hi[2];
+    }
+    R acc = R(0);
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = ix[koff(D, k, 0) + 1] + jy[koff(D, k, 1) + 1] + (D == 3 ? kz[koff(D, k, 2) + 1] : 0);
+        acc += L.A[k * L.ncell + c] * (R)y[idx];
+    }
+    return acc;
 }
 
 // cells of one colour: parity colouring (i + j + k) % 2 when ncol == 2 (n[0] even), one
@@ -394,16 +431,50 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
     __syncthreads();
 }
 
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    int w = tid >> 5, l = tid & 31;
+    if (l == 0) {
+        sh[3 * w] = a;
+        sh[3 * w + 1] = b;
+        sh[3 * w + 2] = c;
+    }
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x * blockDim.y) >> 5;
+        a = l < nw ? sh[3 * l] : 0.0;
+        b = l < nw ? sh[3 * l + 1] : 0.0;
+        c = l < nw ? sh[3 * l + 2] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+    }
+    __syncthreads();
+}
+
 struct ResidualParams {
     LV<double> L;       // finest level, FP64 (x = phi, b = right-hand side)
-    float* r32;         // FP32 residual (right-hand side of the correction cycle)
-    double* part;       // [2 * RED_BLOCKS]
+    float* r32;         // FP32 residual (right-hand side of the correction cycle), or null
+    double* r64;        // FP64 residual (Krylov iteration), or null
+    const double* rh;   // shadow residual r^: (r^, r) is reduced when ks is set and !init
+    KrylovState* ks;    // Krylov scalars to update, or null
+    int init;           // first residual of a Krylov solve: start the recurrence
+    double* part;       // [3 * RED_BLOCKS]
     unsigned* ticket;
     DevCounters* ctr;
     int* done;
     double rtol;
     int max_cycles;
-    int count_cycle;
+    int count_cycle;    // V-cycles since the previous residual
     int use_handle;
     cudaGraphConditionalHandle handle;
 };
@@ -413,10 +484,11 @@ struct ResidualParams {
 // Blocks of 32 x 8 threads walk rows (j, k) of 32-cell segments.
 template <int D, int NPT>
 __global__ void __launch_bounds__(256) residual_kernel(ResidualParams P) {
-    __shared__ double sh[64];
+    __shared__ double sh[96];
     __shared__ bool last;
     const LV<double>& L = P.L;
-    double rr = 0.0, bb = 0.0;
+    const bool dot_rh = P.ks && !P.init;
+    double rr = 0.0, bb = 0.0, hr = 0.0;
     const int nrows = L.n[1] * L.n[2];
     for (int row = blockIdx.x * blockDim.y + threadIdx.y; row < nrows; row += gridDim.x * blockDim.y) {
         int j = row % L.n[1], k = row / L.n[1];
@@ -424,16 +496,19 @@ __global__ void __launch_bounds__(256) residual_kernel(ResidualParams P) {
             int q[3] = {i, j, k};
             int c = i + L.n[0] * row;
             double r = L.b[c] - stencil_sum<D, NPT, 0>(L, c, q);
-            P.r32[c] = (float)r;
+            if (P.r32) P.r32[c] = (float)r;
+            if (P.r64) P.r64[c] = r;
             rr += r * r;
             bb += L.b[c] * L.b[c];
+            if (dot_rh) hr += P.rh[c] * r;
         }
     }
-    block_sum2(rr, bb, sh);
+    block_sum3(rr, bb, hr, sh);
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     if (tid == 0) {
-        P.part[2 * blockIdx.x] = rr;
-        P.part[2 * blockIdx.x + 1] = bb;
+        P.part[3 * blockIdx.x] = rr;
+        P.part[3 * blockIdx.x + 1] = bb;
+        P.part[3 * blockIdx.x + 2] = hr;
         __threadfence();
         unsigned t = atomicAdd(P.ticket, 1u);
         last = t == gridDim.x - 1;
@@ -441,16 +516,32 @@ __global__ void __launch_bounds__(256) residual_kernel(ResidualParams P) {
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double a = 0.0, b = 0.0;
+    double a = 0.0, b = 0.0, h = 0.0;
     for (int i = tid; i < (int)gridDim.x; i += blockDim.x * blockDim.y) {
-        a += P.part[2 * i];
-        b += P.part[2 * i + 1];
+        a += P.part[3 * i];
+        b += P.part[3 * i + 1];
+        h += P.part[3 * i + 2];
     }
-    block_sum2(a, b, sh);
+    block_sum3(a, b, h, sh);
     if (tid == 0) {
         *P.ticket = 0;
         DevCounters* ctr = P.ctr;
-        if (P.count_cycle) ctr->mg_cycles += 1;
+        ctr->mg_cycles += P.count_cycle;
+        if (KrylovState* ks = P.ks) {
+            // (r^, r) of the new residual; a vanishing rho, alpha or omega restarts the
+            // recurrence from r^ = p = r, whose rho is (r, r)
+            const bool restart = P.init || !(ks->omega != 0.0) || !(ks->rho != 0.0) || !(ks->alpha != 0.0) ||
+                                 !(fabs(h) > 1e-300) || !isfinite(h);
+            if (restart) {
+                ks->restart = 1;
+                ks->rho = a;
+                ks->beta = 0.0;
+            } else {
+                ks->restart = 0;
+                ks->beta = (h / ks->rho) * (ks->alpha / ks->omega);
+                ks->rho = h;
+            }
+        }
         double res = b > 0.0 ? sqrt(a) / sqrt(b) : 0.0;
         ctr->mg_residual = res;
         ctr->mg_bnorm = sqrt(b);
@@ -465,6 +556,102 @@ __global__ void __launch_bounds__(256) residual_kernel(ResidualParams P) {
 // phi += e (FP64 update with the FP32 correction)
 __global__ void update_kernel(double* phi, const float* e, int n) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) phi[c] += (double)e[c];
+}
+
+// ---- BiCGStab steps (the scalars live in KrylovState; see the header comment)
+
+// p = r + beta (p - omega v), or p = r^ = r on a restart; the V-cycle's right-hand side float(p)
+__global__ void bicg_direction_kernel(int n, const double* __restrict__ r, double* rh, double* p, const double* v,
+                                      float* b32, const KrylovState* ks) {
+    const double beta = ks->beta, omega = ks->omega;
+    const bool restart = ks->restart != 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        double pc;
+        if (restart) {
+            rh[c] = r[c];
+            pc = r[c];
+        } else {
+            pc = r[c] + beta * (p[c] - omega * v[c]);
+        }
+        p[c] = pc;
+        b32[c] = (float)pc;
+    }
+}
+
+// y = M x32 (FP64) over the finest level; mode 0: v = y, p^ = x32 kept, reduce (r^, v) ->
+// alpha = rho / (r^, v); mode 1: reduce (y, s), (y, y) -> omega = (t, s) / (t, t)
+template <int D, int NPT>
+__global__ void __launch_bounds__(256) bicg_matvec_kernel(LV<double> L, const float* __restrict__ x32, int mode,
+                                                           double* v, float* ph32, const double* __restrict__ w,
+                                                           KrylovState* ks) {
+    __shared__ double sh[96];
+    __shared__ bool last;
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+    const int nrows = L.n[1] * L.n[2];
+    for (int row = blockIdx.x * blockDim.y + threadIdx.y; row < nrows; row += gridDim.x * blockDim.y) {
+        int j = row % L.n[1], k = row / L.n[1];
+        for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
+            int q[3] = {i, j, k};
+            int c = i + L.n[0] * row;
+            const double y = stencil_apply<D, NPT>(L, x32, c, q);
+            if (mode == 0) {
+                v[c] = y;
+                ph32[c] = x32[c];
+                d0 += w[c] * y;  // w = r^
+            } else {
+                d0 += y * w[c];  // w = s
+                d1 += y * y;
+            }
+        }
+    }
+    block_sum3(d0, d1, d2, sh);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (tid == 0) {
+        ks->part[3 * blockIdx.x] = d0;
+        ks->part[3 * blockIdx.x + 1] = d1;
+        __threadfence();
+        unsigned t = atomicAdd(&ks->ticket, 1u);
+        last = t == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0, z = 0.0;
+    for (int i = tid; i < (int)gridDim.x; i += blockDim.x * blockDim.y) {
+        a += ks->part[3 * i];
+        b += ks->part[3 * i + 1];
+    }
+    block_sum3(a, b, z, sh);
+    if (tid == 0) {
+        ks->ticket = 0;
+        if (mode == 0) {
+            const double al = ks->rho / a;
+            ks->alpha = (a != 0.0 && isfinite(al)) ? al : 0.0;
+            ks->restart = 0;
+        } else {
+            const double om = a / b;
+            ks->omega = (b > 0.0 && isfinite(om)) ? om : 0.0;
+        }
+    }
+}
+
+// s = r - alpha v; the V-cycle's right-hand side float(s)
+__global__ void bicg_s_kernel(int n, const double* __restrict__ r, const double* __restrict__ v, double* s,
+                              float* b32, const KrylovState* ks) {
+    const double alpha = ks->alpha;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const double sc = r[c] - alpha * v[c];
+        s[c] = sc;
+        b32[c] = (float)sc;
+    }
+}
+
+// phi += alpha p^ + omega s^
+__global__ void bicg_update_kernel(int n, double* phi, const float* __restrict__ ph32, const float* __restrict__ sh32,
+                                   const KrylovState* ks) {
+    const double alpha = ks->alpha, omega = ks->omega;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        phi[c] += alpha * (double)ph32[c] + omega * (double)sh32[c];
 }
 
 // mode 1: (sum b, -); mode 2: (sum J phi, -)
@@ -731,13 +918,21 @@ int grid_blocks(long long n, int threads) {
     return (int)b;
 }
 
+constexpr size_t CTA_SMEM_MAX = 200 * 1024;  // shared memory of the one-CTA coarse cycle
+
 LVSet make_set(const cpic_run* r) {
     LVSet S;
     S.nl = r->nlevels;
+    for (int l = 0; l < r->nlevels; ++l) S.l[l] = make_lv<float>(r, l, true);
+    // the one-CTA part starts at the first level of at most COARSE_CELLS cells from which
+    // every coarser level fits the CTA's shared memory (stencil, inverse diagonal, x, b)
     S.first_cta = r->nlevels - 1;
-    for (int l = 0; l < r->nlevels; ++l) {
-        S.l[l] = make_lv<float>(r, l, true);
-        if (r->lev[l].ncell <= COARSE_CELLS && l < S.first_cta) S.first_cta = l;
+    for (int l = r->nlevels - 1; l >= 0; --l) {
+        if (r->lev[l].ncell > COARSE_CELLS) break;
+        size_t f = 0;
+        for (int k = l; k < r->nlevels; ++k) f += (size_t)(S.l[k].used + 3) * S.l[k].ncell;
+        if (f * sizeof(float) > CTA_SMEM_MAX) break;
+        S.first_cta = l;
     }
     S.dense_inv = r->dense_inv32;
     S.dense_m = (int)r->lev[r->nlevels - 1].ncell;
@@ -751,7 +946,7 @@ size_t cta_smem_bytes(const LVSet& S) {
     return f * sizeof(float);
 }
 
-int* done_flag(cpic_run* r) { return reinterpret_cast<int*>(r->red + 2 * RED_BLOCKS + 2); }
+int* done_flag(cpic_run* r) { return reinterpret_cast<int*>(r->red + 3 * RED_BLOCKS + 2); }
 
 const dim3 kCellBlock(32, 8, 1);
 
@@ -770,8 +965,8 @@ int dispatch_shape(const cpic_run* r, F f) {
                  : f(std::integral_constant<int, 3>(), std::integral_constant<int, 7>());
 }
 
-// one FP32 V-cycle on the correction equation (e = 0 first), then phi += e
-int enqueue_correction(cpic_run* r, const LVSet& S) {
+// one FP32 V-cycle on the correction equation (e = 0 first): lev[0].x32 = V(lev[0].b32)
+int enqueue_vcycle(cpic_run* r, const LVSet& S) {
     return dispatch_shape(r, [&](auto Dc, auto Nc) -> int {
         constexpr int D = decltype(Dc)::value, NPT = decltype(Nc)::value;
         cudaStream_t st = r->stream;
@@ -795,14 +990,14 @@ int enqueue_correction(cpic_run* r, const LVSet& S) {
             CPIC_CHECK_LAUNCH();
         }
         size_t smem = cta_smem_bytes(S);
-        if (smem > 200 * 1024) {
+        if (smem > CTA_SMEM_MAX) {
             set_error("multigrid: coarse levels need %zu bytes of shared memory", smem);
             return CPIC_ERR_INVALID;
         }
         // per-function attribute shared by every run (and by graphs captured earlier): set it
         // to the bound checked above, not to this run's need
         CPIC_CUDA(cudaFuncSetAttribute(coarse_cycle_kernel<D, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024));
+                                       (int)CTA_SMEM_MAX));
         coarse_cycle_kernel<D, NPT><<<1, 512, smem, st>>>(S, nu1, nu2);
         CPIC_CHECK_LAUNCH();
         for (int l = top - 1; l >= 0; --l) {
@@ -813,17 +1008,31 @@ int enqueue_correction(cpic_run* r, const LVSet& S) {
                 for (int col = L.ncol - 1; col >= 0; --col)
                     if (int e = smooth(l, col)) return e;
         }
-        update_kernel<<<grid_blocks(r->lev[0].ncell, 256), 256, 0, st>>>(r->lev[0].x, r->lev[0].x32, (int)r->lev[0].ncell);
-        CPIC_CHECK_LAUNCH();
         return CPIC_OK;
     });
 }
 
+// one V-cycle on the residual, then phi += e
+int enqueue_correction(cpic_run* r, const LVSet& S) {
+    int st = enqueue_vcycle(r, S);
+    if (st) return st;
+    update_kernel<<<grid_blocks(r->lev[0].ncell, 256), 256, 0, r->stream>>>(r->lev[0].x, r->lev[0].x32,
+                                                                            (int)r->lev[0].ncell);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
+// krylov: 0 plain iteration (FP32 residual for the next V-cycle); 1 first residual of a
+// BiCGStab solve; 2 residual after a BiCGStab iteration
 int enqueue_residual(cpic_run* r, double rtol, int max_cycles, int count_cycle, bool use_handle,
-                     cudaGraphConditionalHandle h) {
+                     cudaGraphConditionalHandle h, int krylov = 0) {
     ResidualParams P;
     P.L = make_lv<double>(r, 0, false);
-    P.r32 = r->lev[0].b32;
+    P.r32 = krylov ? nullptr : r->lev[0].b32;
+    P.r64 = krylov ? r->kv : nullptr;
+    P.rh = krylov ? r->kv + r->ncell : nullptr;
+    P.ks = krylov ? r->kry : nullptr;
+    P.init = krylov == 1 ? 1 : 0;
     P.part = r->red;
     P.ticket = r->ticket;
     P.ctr = r->ctr;
@@ -839,6 +1048,49 @@ int enqueue_residual(cpic_run* r, double rtol, int max_cycles, int count_cycle, 
         return CPIC_OK;
     });
 }
+
+// one BiCGStab iteration (two V-cycles) ending with the residual that decides whether to go on
+int enqueue_bicg_iteration(cpic_run* r, const LVSet& S, double rtol, int max_cycles, bool use_handle,
+                           cudaGraphConditionalHandle h) {
+    const int n = (int)r->ncell;
+    double* rv = r->kv;
+    double* rh = r->kv + r->ncell;
+    double* p = r->kv + 2 * r->ncell;
+    double* v = r->kv + 3 * r->ncell;
+    double* s = r->kv + 4 * r->ncell;
+    float* b32 = r->lev[0].b32;
+    float* x32 = r->lev[0].x32;
+    cudaStream_t st = r->stream;
+    const int gb = grid_blocks(n, 256);
+    bicg_direction_kernel<<<gb, 256, 0, st>>>(n, rv, rh, p, v, b32, r->kry);
+    CPIC_CHECK_LAUNCH();
+    int e = enqueue_vcycle(r, S);
+    if (e) return e;
+    LV<double> L0 = make_lv<double>(r, 0, false);
+    e = dispatch_shape(r, [&](auto Dc, auto Nc) -> int {
+        bicg_matvec_kernel<decltype(Dc)::value, decltype(Nc)::value>
+            <<<KRY_BLOCKS, kCellBlock, 0, st>>>(L0, x32, 0, v, r->ph32, rh, r->kry);
+        CPIC_CHECK_LAUNCH();
+        return CPIC_OK;
+    });
+    if (e) return e;
+    bicg_s_kernel<<<gb, 256, 0, st>>>(n, rv, v, s, b32, r->kry);
+    CPIC_CHECK_LAUNCH();
+    e = enqueue_vcycle(r, S);
+    if (e) return e;
+    e = dispatch_shape(r, [&](auto Dc, auto Nc) -> int {
+        bicg_matvec_kernel<decltype(Dc)::value, decltype(Nc)::value>
+            <<<KRY_BLOCKS, kCellBlock, 0, st>>>(L0, x32, 1, nullptr, nullptr, s, r->kry);
+        CPIC_CHECK_LAUNCH();
+        return CPIC_OK;
+    });
+    if (e) return e;
+    bicg_update_kernel<<<gb, 256, 0, st>>>(n, r->lev[0].x, r->ph32, x32, r->kry);
+    CPIC_CHECK_LAUNCH();
+    return enqueue_residual(r, rtol, max_cycles, 2, use_handle, h, 2);
+}
+
+bool use_krylov(const cpic_run* r) { return r->solver == CPIC_SOLVER_BICGSTAB && !r->cluster_cs; }
 
 // right-hand side (and its projection); resets the solve counters
 int enqueue_prologue(cpic_run* r) {
@@ -870,7 +1122,7 @@ int enqueue_epilogue(cpic_run* r) {
 }  // namespace
 
 int mg_setup(cpic_run* r) {
-    int* flag = reinterpret_cast<int*>(r->red + 2 * RED_BLOCKS + 4);
+    int* flag = reinterpret_cast<int*>(r->red + 3 * RED_BLOCKS + 4);
     for (int l = 0; l < r->nlevels; ++l) {
         Level& Lv = r->lev[l];
         CPIC_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), r->stream));
@@ -912,6 +1164,7 @@ int mg_setup(cpic_run* r) {
                                                                                   (long long)mm * mm);
     CPIC_CHECK_LAUNCH();
     CPIC_CUDA(cudaMemsetAsync(r->ticket, 0, sizeof(unsigned) * 4, r->stream));
+    CPIC_CUDA(cudaMemsetAsync(r->kry, 0, sizeof(KrylovState), r->stream));
     int hfail = 0;
     CPIC_CUDA(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, r->stream));
     CPIC_CUDA(cudaStreamSynchronize(r->stream));
@@ -934,7 +1187,7 @@ int mg_solve(cpic_run* r, double rtol, int max_cycles, bool host_loop, int* cycl
         if (st) return st;
         max_cycles = 0;  // the loop ran inside the cluster kernel
     } else {
-        st = enqueue_residual(r, rtol, max_cycles, 0, false, 0);
+        st = enqueue_residual(r, rtol, max_cycles, 0, false, 0, use_krylov(r) ? 1 : 0);
         if (st) return st;
     }
     int* done = done_flag(r);
@@ -943,9 +1196,12 @@ int mg_solve(cpic_run* r, double rtol, int max_cycles, bool host_loop, int* cycl
         CPIC_CUDA(cudaMemcpyAsync(&hd, done, sizeof(int), cudaMemcpyDeviceToHost, r->stream));
         CPIC_CUDA(cudaStreamSynchronize(r->stream));
         if (hd) break;
-        st = enqueue_correction(r, S);
-        if (st) return st;
-        st = enqueue_residual(r, rtol, max_cycles, 1, false, 0);
+        if (use_krylov(r)) {
+            st = enqueue_bicg_iteration(r, S, rtol, max_cycles, false, 0);
+        } else {
+            st = enqueue_correction(r, S);
+            if (!st) st = enqueue_residual(r, rtol, max_cycles, 1, false, 0);
+        }
         if (st) return st;
     }
     st = enqueue_epilogue(r);
@@ -980,7 +1236,7 @@ int mg_capture_solve(cpic_run* r, cudaGraph_t g, double rtol, int max_cycles) {
     CPIC_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
     int st = enqueue_prologue(r);
     if (st) return st;
-    st = enqueue_residual(r, rtol, max_cycles, 0, true, h);
+    st = enqueue_residual(r, rtol, max_cycles, 0, true, h, use_krylov(r) ? 1 : 0);
     if (st) return st;
     // splice the WHILE node after the current capture frontier
     cudaStreamCaptureStatus cs;
@@ -1008,8 +1264,12 @@ int mg_capture_solve(cpic_run* r, cudaGraph_t g, double rtol, int max_cycles) {
     st = CPIC_OK;
     cudaError_t e = cudaStreamBeginCaptureToGraph(side, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        st = enqueue_correction(r, S);
-        if (!st) st = enqueue_residual(r, rtol, max_cycles, 1, true, h);
+        if (use_krylov(r)) {
+            st = enqueue_bicg_iteration(r, S, rtol, max_cycles, true, h);
+        } else {
+            st = enqueue_correction(r, S);
+            if (!st) st = enqueue_residual(r, rtol, max_cycles, 1, true, h);
+        }
         cudaGraph_t out = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(side, &out);
         if (!st && e2 != cudaSuccess) st = cuda_fail(e2, "cudaStreamEndCapture(body)", __FILE__, __LINE__);

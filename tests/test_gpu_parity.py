@@ -17,7 +17,7 @@ from paper_1311_2286_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 P, Dr, Ne = 0, 1, 2
-PP, PA = 0, 1
+PP, PA, PR = 0, 1, 2
 
 
 def _unpack(cell, D=2):
@@ -248,6 +248,94 @@ def test_field_solve_vs_direct(cpic, case):
     err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
     assert err <= 1e-10, (err, cycles, res)
     run.close()
+
+
+@pytest.mark.parametrize("case", list(SOLVER_CASES))
+def test_bicgstab_solve_vs_direct(cpic, case, monkeypatch):
+    """a9 with the Krylov outer iteration (V-cycle-preconditioned BiCGStab, kernel-chain
+    path): the same problems as the V-cycle iteration, the same 1e-10 bound against the
+    oracle's direct solve, through the stream-ordered solve and through a captured step's
+    conditional loop (which must agree bit for bit: same kernels, same order)."""
+    monkeypatch.setenv("CPIC_NO_CLUSTER_SOLVER", "1")
+    mk, bc, bv, axisym = SOLVER_CASES[case]
+    X = mk()
+    n = (X.shape[1] - 1, X.shape[0] - 1)
+    per = [bc[0] == P, bc[2] == P]
+    g = geometry.build_geometry(X, per, axisym=axisym)
+    M, bbc = poisson.assemble(g, bc, bv)
+    rng = np.random.default_rng(5)
+    npart = 50_000
+    idx = np.stack([rng.integers(0, n[0], npart), rng.integers(0, n[1], npart)])
+    t = rng.random((2, npart)).astype(np.float32)
+    pbc = [PP if b == P else PA for b in bc]
+    cfg = cpic.make_config(2, n, bc, bv, pbc, 0.1, [(-1.0, 1.0, 1e-3, npart)], background=0.3,
+                           axisymmetric=axisym)
+    run = cpic.Run(cfg)
+    run.set_map_vertices(X)
+    run.set_solver(cpic.CPIC_SOLVER_BICGSTAB)
+    cell = (idx[0] | (idx[1] << 16)).astype(np.int32)
+    run.load_particles(0, cell, t, np.zeros((3, npart), np.float32))
+    run.deposit()
+    cycles, res = run.solve_field(rtol=1e-13, max_cycles=200)
+    phi = run.phi()
+    C = run.charge(0)
+    Q = poisson.charge_in_cells(g, [C], [-1e-3], 0.3)
+    ref = poisson.solve(g, M, bbc, Q, bc)
+    err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+    assert res <= 1e-13 and err <= 1e-10, (err, cycles, res)
+    run.close()
+
+
+@pytest.mark.parametrize("solver", ["mg", "bicgstab"])
+def test_field_solve_3d_shell_vs_direct(cpic, solver):
+    """a9 in 3D: the 7-point shell problem (geometric radial stretching, Neumann polar caps,
+    periodic azimuth, Dirichlet object and outer boundary) on 32 x 16 x 16 cells against the
+    oracle's direct solve, relative L2 1e-10, for both outer iterations."""
+    n = (32, 16, 16)
+    X = wl.shell_vertices(*n, 1.0, 30.0, math.pi / 32)
+    bc, bv = [Dr, Dr, Ne, Ne, P, P], [-5.0, 0.0, 0.0, 0.0, 0.0, 0.0]
+    per = [False, False, True]
+    g = geometry.build_geometry(X, per)
+    M, bbc = poisson.assemble(g, bc, bv)
+    rng = np.random.default_rng(8)
+    npart = 100_000
+    idx = np.stack([rng.integers(0, n[a], npart) for a in range(3)])
+    t = rng.random((3, npart)).astype(np.float32)
+    cfg = cpic.make_config(3, n, bc, bv, [PA, PA, PR, PR, PP, PP], 0.1, [(-1.0, 1.0, 1e-3, npart)], background=0.2)
+    run = cpic.Run(cfg)
+    run.set_map_vertices(X)
+    if solver == "bicgstab":
+        run.set_solver(cpic.CPIC_SOLVER_BICGSTAB)
+    cell = (idx[0] | (idx[1] << 10) | (idx[2] << 20)).astype(np.int32)
+    run.load_particles(0, cell, t, np.zeros((3, npart), np.float32))
+    run.deposit()
+    cycles, res = run.solve_field(rtol=1e-13, max_cycles=300)
+    phi = run.phi()
+    C = run.charge(0)
+    Q = poisson.charge_in_cells(g, [C], [-1e-3], 0.2)
+    ref = poisson.solve(g, M, bbc, Q, bc)
+    err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+    assert res <= 1e-13 and err <= 1e-10, (err, cycles, res)
+    run.close()
+
+
+def test_bicgstab_graph_step_matches_stream_step(cpic):
+    """The Krylov solve inside a captured step (conditional WHILE node driven by the
+    residual kernel) and the stream-ordered step give identical runs."""
+    outs = []
+    for graph in (False, True):
+        run = cpic.sphere_run_device(32, 32, 32, 100_000, sort_interval=4)
+        run.set_solver(cpic.CPIC_SOLVER_BICGSTAB)
+        run.profile(not graph)  # profiling takes the stream-ordered path
+        run.step(3)
+        d = run.diag()
+        outs.append((run.phi(), d))
+        run.close()
+    (pa, da), (pb, db) = outs
+    assert np.array_equal(pa, pb)
+    for key in ("step", "n", "absorbed", "mg_cycles", "W_E", "W_K"):
+        assert da[key] == db[key], key
+    assert da["mg_residual"] <= 1e-10
 
 
 # ------------------------------------------------------------------ sort, injection
