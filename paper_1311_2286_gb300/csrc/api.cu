@@ -680,6 +680,8 @@ int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* s
         e = cudaMemsetAsync(r->charge_h, 0, sizeof(unsigned long long) * r->ncell_h * cfg->n_species, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->pb.cell[0], 0xff, sizeof(int) * r->pb.total, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->pb.cell[1], 0xff, sizeof(int) * r->pb.total, r->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->ticket, 0, sizeof(unsigned) * 4, r->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->kry, 0, sizeof(KrylovState), r->stream);
     if (e != cudaSuccess) {
         st = cuda_fail(e, "initial memset", __FILE__, __LINE__);
         if (r->own_memory) cudaFree(r->arena);

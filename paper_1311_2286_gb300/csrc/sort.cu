@@ -4,8 +4,9 @@
 //
 // Counting sort of every species by its row-major cell index i + N1 (j + N2 k), compacting
 // dead slots away: histogram (warp-aggregated atomics) -> exclusive scan over
-// [species][cell] -> scatter into the other particle buffer (one atomic per cell group per
-// warp reserves consecutive slots; the order inside a cell is unspecified) -> live counts.
+// [species][cell] -> rank (each live particle's slot in the other buffer; one atomic per cell
+// group reserves consecutive slots; the order inside a cell is unspecified) -> gather of the
+// particle data into the other buffer in slot order -> live counts.
 #include "particles.cuh"
 
 namespace cpic {
@@ -22,12 +23,65 @@ struct SortParams {
     DevCounters* ctr;
     int* hist;         // [nsp][ncell]
     long long* scan;   // [nsp * ncell + 1]
+    unsigned* ticket;  // last-block counter of the gather (zero between sorts)
 };
 
 __device__ __forceinline__ long long cell_key(const SortParams& p, int cw) {
     if (cw < 0) return -1;
     if (p.D == 2) return (long long)(cw & 0xFFFF) + (long long)p.n[0] * (cw >> 16);
     return (long long)(cw & 1023) + (long long)p.n[0] * (((cw >> 10) & 1023) + (long long)p.n[1] * (cw >> 20));
+}
+
+// Block-wide key window of a chunk for the shared-memory path: [wlo, whi] with
+// whi - wlo < RANGE. When all live keys fit, it is their [min, max]; otherwise (3D chunks whose
+// particles have moved to other planes since the last sort: a plane is n0 n1 keys away) it is
+// the [min, max] of the keys within RANGE / 2 of the key at the chunk's middle slot, and the
+// keys outside take the global path. wlo > whi: no key in a window (all global or no live key).
+// Every thread of the block must call it; red is [2][8] shared ints.
+template <int PER, int RANGE>
+__device__ __forceinline__ void chunk_window(const int (&key)[PER], int kmid, int (*red)[8], int& wlo, int& whi) {
+    const int lane = threadIdx.x & 31;
+    auto block_minmax = [&](int lo_bound, int hi_bound, int& mn, int& mx) {
+        mn = 0x7fffffff;
+        mx = -1;
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int k = key[e];
+            if (k >= lo_bound && k <= hi_bound) {
+                mn = min(mn, k);
+                mx = max(mx, k);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = min(mn, __shfl_xor_sync(FULL, mn, o));
+            mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+        }
+        __syncthreads();  // the previous use of red (and of the chunk's shared arrays) is done
+        if (lane == 0) {
+            red[0][threadIdx.x >> 5] = mn;
+            red[1][threadIdx.x >> 5] = mx;
+        }
+        __syncthreads();
+        mn = red[0][0];
+        mx = red[1][0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) {
+            mn = min(mn, red[0][w]);
+            mx = max(mx, red[1][w]);
+        }
+    };
+    int mn, mx;
+    block_minmax(0, 0x7fffffff, mn, mx);
+    if (mx < mn || mx - mn < RANGE) {
+        wlo = mn;
+        whi = mx;
+        return;
+    }
+    const int c = kmid >= 0 ? kmid : mn;
+    block_minmax(max(c - RANGE / 2, 0), c + RANGE / 2 - 1, mn, mx);
+    wlo = mn;
+    whi = mx;
 }
 
 // Histogram of cells per species: chunks of SC_CHUNK particles of one species count their
@@ -62,56 +116,34 @@ __global__ void __launch_bounds__(256) hist_kernel(SortParams p) {
         const int* __restrict__ cin = p.pb.cell[cur] + p.pb.base[s];
         int* __restrict__ hist_s = p.hist + (long long)s * p.ncell;
         int key[8];
-        int kmin = 0x7fffffff, kmax = -1;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int i = lo + (int)threadIdx.x + e * 256;
-            const long long k = i < hi ? cell_key(p, cin[i]) : -1;
-            key[e] = (int)k;
-            if (k >= 0) {
-                kmin = min(kmin, (int)k);
-                kmax = max(kmax, (int)k);
-            }
+            key[e] = i < hi ? (int)cell_key(p, cin[i]) : -1;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            kmin = min(kmin, __shfl_xor_sync(FULL, kmin, o));
-            kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
-        }
-        __syncthreads();
-        if (lane == 0) {
-            red[0][threadIdx.x >> 5] = kmin;
-            red[1][threadIdx.x >> 5] = kmax;
-        }
-        __syncthreads();
-        kmin = red[0][0];
-        kmax = red[1][0];
-#pragma unroll
-        for (int w = 1; w < 8; ++w) {
-            kmin = min(kmin, red[0][w]);
-            kmax = max(kmax, red[1][w]);
-        }
-        if (kmax < kmin) continue;
-        if (kmax - kmin < RANGE) {
+        int kmin, kmax;
+        chunk_window<8, RANGE>(key, (int)cell_key(p, cin[lo + (hi - lo) / 2]), red, kmin, kmax);
+        const bool win = kmax >= kmin;  // block-uniform
+        if (win) {
             const int range = kmax - kmin + 1;
             for (int k = threadIdx.x; k < range; k += 256) h[k] = 0;
             __syncthreads();
+        }
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int k = key[e];
-                const unsigned peers = __match_any_sync(FULL, k);
-                if (k >= 0 && (__ffs(peers) - 1) == lane) atomicAdd(&h[k - kmin], __popc(peers));
+        for (int e = 0; e < 8; ++e) {
+            const int k = key[e];
+            const unsigned peers = __match_any_sync(FULL, k);
+            if (k >= 0 && (__ffs(peers) - 1) == lane) {
+                if (win && k >= kmin && k <= kmax)
+                    atomicAdd(&h[k - kmin], __popc(peers));
+                else
+                    atomicAdd(hist_s + k, __popc(peers));
             }
+        }
+        if (win) {
             __syncthreads();
-            for (int k = threadIdx.x; k < range; k += 256)
+            for (int k = threadIdx.x; k < kmax - kmin + 1; k += 256)
                 if (h[k]) atomicAdd(hist_s + kmin + k, h[k]);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int k = key[e];
-                const unsigned peers = __match_any_sync(FULL, k);
-                if (k >= 0 && (__ffs(peers) - 1) == lane) atomicAdd(hist_s + k, __popc(peers));
-            }
         }
     }
 }
@@ -182,21 +214,26 @@ __global__ void scan_final_kernel(const int* hist, long long N, long long chunk,
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) scan[N] = carry;
 }
 
-// Scatter. Blocks walk chunks of SC_CHUNK particles of one species (block-uniform species,
-// 32-bit slot indices). Between sorts the particles are nearly in cell order, so a chunk's
-// keys span a narrow range: the chunk counts its keys in a shared histogram over that range
+// Rank. Blocks walk chunks of SC_CHUNK particles of one species (block-uniform species,
+// 32-bit slot indices) and give every live particle its slot in the sorted order; the slot
+// receives the particle's source index (in the other buffer's cell array, which the gather
+// below then overwrites), so the particle data itself moves once, in the gather, with
+// coalesced writes. Between sorts the particles are nearly in cell order, so a chunk's keys
+// span a narrow range: the chunk counts its keys in a shared histogram over that range
 // (warp-aggregated), reserves each cell's slots with one global cursor atomic per cell and
 // chunk, and ranks its particles with shared atomics, so the long chain global atomic ->
 // store runs once per cell and chunk instead of once per warp and cell. Chunks whose keys
 // span more than SC_RANGE cells (unsorted loads, injected particles) reserve per warp and
-// cell. Lanes with the same cell get consecutive slots either way.
+// cell; in chunks whose particles have partly moved to other planes (3D), the keys near the
+// chunk's middle key take the shared path and the others the per-warp one. Lanes with the
+// same cell get consecutive slots either way.
 constexpr int SC_THREADS = 256;
 constexpr int SC_PER_THREAD = 8;
 constexpr int SC_CHUNK = SC_THREADS * SC_PER_THREAD;
 constexpr int SC_RANGE = 4096;
 
 template <int D>
-__global__ void __launch_bounds__(SC_THREADS) scatter_kernel(SortParams p) {
+__global__ void __launch_bounds__(SC_THREADS) rank_kernel(SortParams p) {
     __shared__ int hcount[SC_RANGE];  // counts, then reserved global starts
     __shared__ int hrank[SC_RANGE];   // running ranks
     __shared__ int red[2][SC_THREADS / 32];
@@ -210,7 +247,6 @@ __global__ void __launch_bounds__(SC_THREADS) scatter_kernel(SortParams p) {
     }
     if (total == 0) return;
     const int cur = p.ctr->cur, nxt = 1 - cur;
-    const long long T = p.pb.total;
     const int lane = threadIdx.x & 31;
     const int n0 = p.n[0], n1 = p.n[1];
     for (int ch = blockIdx.x;; ch += gridDim.x) {
@@ -225,50 +261,24 @@ __global__ void __launch_bounds__(SC_THREADS) scatter_kernel(SortParams p) {
         const int lo = local * SC_CHUNK, hi = min(lo + SC_CHUNK, cnt[s]);
         const long long b0 = p.pb.base[s];
         const int* __restrict__ cin = p.pb.cell[cur] + b0;
-        const float* __restrict__ tin = p.pb.t[cur] + b0;
-        const float* __restrict__ vin = p.pb.v[cur] + b0;
-        int* __restrict__ cout = p.pb.cell[nxt] + b0;
-        float* __restrict__ tout = p.pb.t[nxt] + b0;
-        float* __restrict__ vout = p.pb.v[nxt] + b0;
+        int* __restrict__ cout = p.pb.cell[nxt] + b0;  // receives source indices
         const long long* __restrict__ scan_s = p.scan + (long long)s * p.ncell;
         int* __restrict__ cursor = p.hist + (long long)s * p.ncell;
         const long long sbase = scan_s[0];
         // keys of this thread's particles (element e: slot lo + threadIdx.x + e * SC_THREADS)
+        auto key_of = [&](int cw) {
+            if (cw < 0) return -1;
+            return D == 2 ? (cw & 0xFFFF) + n0 * (cw >> 16) : (cw & 1023) + n0 * (((cw >> 10) & 1023) + n1 * (cw >> 20));
+        };
         int key[SC_PER_THREAD];
-        int kmin = 0x7fffffff, kmax = -1;
 #pragma unroll
         for (int e = 0; e < SC_PER_THREAD; ++e) {
             const int i = lo + (int)threadIdx.x + e * SC_THREADS;
-            const int cw = i < hi ? cin[i] : -1;
-            int k = -1;
-            if (cw >= 0)
-                k = D == 2 ? (cw & 0xFFFF) + n0 * (cw >> 16) : (cw & 1023) + n0 * (((cw >> 10) & 1023) + n1 * (cw >> 20));
-            key[e] = k;
-            if (k >= 0) {
-                kmin = min(kmin, k);
-                kmax = max(kmax, k);
-            }
+            key[e] = key_of(i < hi ? cin[i] : -1);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            kmin = min(kmin, __shfl_xor_sync(FULL, kmin, o));
-            kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
-        }
-        __syncthreads();  // previous chunk done with the shared arrays
-        if (lane == 0) {
-            red[0][threadIdx.x >> 5] = kmin;
-            red[1][threadIdx.x >> 5] = kmax;
-        }
-        __syncthreads();
-        kmin = red[0][0];
-        kmax = red[1][0];
-#pragma unroll
-        for (int w = 1; w < SC_THREADS / 32; ++w) {
-            kmin = min(kmin, red[0][w]);
-            kmax = max(kmax, red[1][w]);
-        }
-        if (kmax < kmin) continue;  // no live particle in the chunk (block-uniform)
-        const bool local_path = kmax - kmin < SC_RANGE;
+        int kmin, kmax;
+        chunk_window<SC_PER_THREAD, SC_RANGE>(key, key_of(cin[lo + (hi - lo) / 2]), red, kmin, kmax);
+        const bool local_path = kmax >= kmin;  // block-uniform: keys in [kmin, kmax] go through shared memory
         if (local_path) {
             const int range = kmax - kmin + 1;
             for (int k = threadIdx.x; k < range; k += SC_THREADS) hcount[k] = hrank[k] = 0;
@@ -277,7 +287,7 @@ __global__ void __launch_bounds__(SC_THREADS) scatter_kernel(SortParams p) {
             for (int e = 0; e < SC_PER_THREAD; ++e) {
                 const int k = key[e];
                 const unsigned peers = __match_any_sync(FULL, k);
-                if (k >= 0 && (__ffs(peers) - 1) == lane) atomicAdd(&hcount[k - kmin], __popc(peers));
+                if (k >= kmin && k <= kmax && (__ffs(peers) - 1) == lane) atomicAdd(&hcount[k - kmin], __popc(peers));
             }
             __syncthreads();
             // one global reservation per cell of the chunk: hcount becomes the cell's first slot
@@ -292,42 +302,67 @@ __global__ void __launch_bounds__(SC_THREADS) scatter_kernel(SortParams p) {
             const int i = lo + (int)threadIdx.x + e * SC_THREADS;
             const int k = key[e];
             const bool act = k >= 0;
-            float t[3], v[3];
-#pragma unroll
-            for (int a = 0; a < D; ++a) t[a] = act ? tin[a * T + i] : 0.f;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) v[a] = act ? vin[a * T + i] : 0.f;
             const unsigned peers = __match_any_sync(FULL, k);
             const int leader = __ffs(peers) - 1;
             int start = 0;
             if (act && leader == lane) {
-                if (local_path)
+                if (local_path && k >= kmin && k <= kmax)
                     start = hcount[k - kmin] + atomicAdd(&hrank[k - kmin], __popc(peers));
                 else
                     start = (int)(scan_s[k] - sbase) + atomicAdd(cursor + k, __popc(peers));
             }
             start = __shfl_sync(FULL, start, leader);
-            if (act) {
-                const int dst = start + __popc(peers & ((1u << lane) - 1u));
-                cout[dst] = cin[i];
-#pragma unroll
-                for (int a = 0; a < D; ++a) tout[a * T + dst] = t[a];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) vout[a * T + dst] = v[a];
-            }
+            if (act) cout[start + __popc(peers & ((1u << lane) - 1u))] = i;
         }
     }
 }
 
-__global__ void sort_finalize_kernel(SortParams p) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        for (int s = 0; s < p.nsp; ++s) {
-            long long n = p.scan[(long long)(s + 1) * p.ncell] - p.scan[(long long)s * p.ncell];
-            p.ctr->count[s] = n;
-            p.ctr->alive[s] = n;
-        }
-        p.ctr->cur = 1 - p.ctr->cur;
+// Gather: slot d of species s in the other buffer takes the particle whose source index the
+// rank pass stored there; reads follow the source order (mostly ascending: the particles
+// were nearly sorted), writes are coalesced. blockIdx.y is the species. The last block to
+// finish sets the live counts from the scan and flips the current buffer.
+template <int D>
+__global__ void __launch_bounds__(256) gather_kernel(SortParams p) {
+    __shared__ bool last;
+    const int s = blockIdx.y;
+    const long long n = p.scan[(long long)(s + 1) * p.ncell] - p.scan[(long long)s * p.ncell];
+    const int cur = p.ctr->cur, nxt = 1 - cur;
+    const long long T = p.pb.total, b0 = p.pb.base[s];
+    const int* __restrict__ cin = p.pb.cell[cur] + b0;
+    const float* __restrict__ tin = p.pb.t[cur] + b0;
+    const float* __restrict__ vin = p.pb.v[cur] + b0;
+    int* __restrict__ cout = p.pb.cell[nxt] + b0;
+    float* __restrict__ tout = p.pb.t[nxt] + b0;
+    float* __restrict__ vout = p.pb.v[nxt] + b0;
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < (int)n; d += gridDim.x * blockDim.x) {
+        const int i = cout[d];
+        const int cw = cin[i];
+        float t[3], v[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) t[a] = tin[a * T + i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[a] = vin[a * T + i];
+        cout[d] = cw;
+#pragma unroll
+        for (int a = 0; a < D; ++a) tout[a * T + d] = t[a];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vout[a * T + d] = v[a];
     }
+    __syncthreads();  // every thread of the block has read ctr->cur
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(p.ticket, 1u) == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    *p.ticket = 0;
+    for (int sp = 0; sp < p.nsp; ++sp) {
+        const long long cnt = p.scan[(long long)(sp + 1) * p.ncell] - p.scan[(long long)sp * p.ncell];
+        p.ctr->count[sp] = cnt;
+        p.ctr->alive[sp] = cnt;
+    }
+    p.ctr->cur = 1 - p.ctr->cur;
 }
 
 }  // namespace
@@ -342,6 +377,7 @@ int launch_sort(cpic_run* r) {
     p.ctr = r->ctr;
     p.hist = r->hist;
     p.scan = r->scan;
+    p.ticket = r->ticket + 2;
     long long N = (long long)p.nsp * r->ncell;
     long long tot = 0;
     for (int s = 0; s < p.nsp; ++s) tot += r->pb.capacity[s] + 32;
@@ -362,11 +398,18 @@ int launch_sort(cpic_run* r) {
     CPIC_CHECK_LAUNCH();
     CPIC_CUDA(cudaMemsetAsync(r->hist, 0, sizeof(int) * N, r->stream));
     if (p.D == 2)
-        scatter_kernel<2><<<(int)pblocks, 256, 0, r->stream>>>(p);
+        rank_kernel<2><<<(int)pblocks, 256, 0, r->stream>>>(p);
     else
-        scatter_kernel<3><<<(int)pblocks, 256, 0, r->stream>>>(p);
+        rank_kernel<3><<<(int)pblocks, 256, 0, r->stream>>>(p);
     CPIC_CHECK_LAUNCH();
-    sort_finalize_kernel<<<1, 32, 0, r->stream>>>(p);
+    int dev = 0, nsm = 0;
+    CPIC_CUDA(cudaGetDevice(&dev));
+    CPIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const dim3 ggrid((unsigned)(nsm * 8 / p.nsp > 0 ? nsm * 8 / p.nsp : 1), (unsigned)p.nsp);
+    if (p.D == 2)
+        gather_kernel<2><<<ggrid, 256, 0, r->stream>>>(p);
+    else
+        gather_kernel<3><<<ggrid, 256, 0, r->stream>>>(p);
     CPIC_CHECK_LAUNCH();
     return CPIC_OK;
 }
