@@ -282,15 +282,30 @@ typedef struct cpic_tuning {
     int32_t sort_interval;                     /* chosen (and set in the run) */
     int32_t interval[CPIC_TUNE_CANDIDATES];    /* candidates tried: 1, 2, 4, 8, 16 */
     float ms_per_step[CPIC_TUNE_CANDIDATES];   /* measured fixed-field particle step time */
+    int32_t chunk;                             /* chosen particles per block chunk (0: one wave) */
+    int32_t chunks[CPIC_TUNE_CANDIDATES];      /* candidates tried: 0, 1024, 2048, 4096, 8192 */
+    float ms_chunk[CPIC_TUNE_CANDIDATES];      /* step time per chunk candidate */
+    int32_t tile;                              /* chosen deposit tiling (1 shared tile, 0 direct) */
+    float ms_tile[2];                          /* step time with [0] direct, [1] tiled deposit */
 } cpic_tuning;
 
-/* Chooses the run's cell-sort interval: for each candidate, times whole sort cycles of at
+/* Chooses, in this order, the run's cell-sort interval, the particles per block chunk of
+ * the push kernel and its deposit tiling: for each candidate, times whole sort cycles of at
  * least trial_steps fixed-field particle steps on the run's own particles (CUDA events on
  * the run's stream), restoring the run's particles, counters and potential from a device
- * snapshot after each trial, so the simulation is unchanged; the fastest interval is set
- * in the run. The snapshot is a temporary device allocation (CPIC_ERR_OOM if it fails).
- * Synchronous. Not in the paper (the sort is a GPU locality device). */
+ * snapshot after each trial, so the simulation is unchanged; the fastest setting of each
+ * knob is kept for the next. The result is set in the run. The snapshot is a temporary
+ * device allocation (CPIC_ERR_OOM if it fails). Synchronous. Not in the paper (the sort and
+ * the chunking are GPU locality devices). */
 int cpic_autotune(cpic_run* run, int trial_steps, cpic_tuning* out);
+
+/* Push kernel knobs (the autotuner's second and third): chunk = particles per block chunk
+ * (0: the particles split evenly over one wave of resident blocks; otherwise a multiple of
+ * 256 in [256, 2^20]); tile = 1 to deposit through the block's shared-memory tile when the
+ * chunk's cells fit it, 0 to deposit straight into the global grid. The result is the same
+ * either way (integer deposit). CPIC_ERR_INVALID for other values. Invalidates the run's
+ * captured step graphs. */
+int cpic_set_push_tuning(cpic_run* run, int chunk, int tile);
 
 /* Writes the run's configuration, vertex map, injection sources, counters, potential and
  * live-slot particles to a file (synchronous). */

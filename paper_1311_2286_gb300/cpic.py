@@ -120,6 +120,11 @@ class cpic_tuning(ctypes.Structure):
         ("sort_interval", ctypes.c_int32),
         ("interval", ctypes.c_int32 * TUNE_CANDIDATES),
         ("ms_per_step", ctypes.c_float * TUNE_CANDIDATES),
+        ("chunk", ctypes.c_int32),
+        ("chunks", ctypes.c_int32 * TUNE_CANDIDATES),
+        ("ms_chunk", ctypes.c_float * TUNE_CANDIDATES),
+        ("tile", ctypes.c_int32),
+        ("ms_tile", ctypes.c_float * 2),
     ]
 
 
@@ -154,6 +159,7 @@ _SIGS = {
     "cpic_get_config": ([P, P], ctypes.c_int),
     "cpic_set_sort_interval": ([P, ctypes.c_int], ctypes.c_int),
     "cpic_set_solver": ([P, ctypes.c_int], ctypes.c_int),
+    "cpic_set_push_tuning": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "cpic_autotune": ([P, ctypes.c_int, P], ctypes.c_int),
     "cpic_checkpoint": ([P, ctypes.c_char_p], ctypes.c_int),
     "cpic_restore": ([ctypes.c_char_p, P, ctypes.c_size_t, P, ctypes.POINTER(P)], ctypes.c_int),
@@ -346,10 +352,18 @@ class Run:
         check(load().cpic_set_solver(self.h, solver))
 
     def autotune(self, trial_steps=8):
-        """Choose the sort interval by timing fixed-field particle steps (state restored)."""
+        """Choose the sort interval, the push chunk size and the deposit tiling by timing
+        fixed-field particle steps (state restored after every trial)."""
         t = cpic_tuning()
         check(load().cpic_autotune(self.h, trial_steps, ctypes.byref(t)))
-        return {"sort_interval": t.sort_interval, "interval": list(t.interval), "ms_per_step": list(t.ms_per_step)}
+        return {"sort_interval": t.sort_interval, "interval": list(t.interval), "ms_per_step": list(t.ms_per_step),
+                "chunk": t.chunk, "chunks": list(t.chunks), "ms_chunk": list(t.ms_chunk),
+                "tile": t.tile, "ms_tile": list(t.ms_tile)}
+
+    def set_push_tuning(self, chunk=0, tile=1):
+        """Push kernel knobs: particles per block chunk (0: one wave of blocks) and deposit
+        tiling (1: shared-memory tile, 0: direct)."""
+        check(load().cpic_set_push_tuning(self.h, chunk, tile))
 
     def checkpoint(self, path):
         check(load().cpic_checkpoint(self.h, os.fsencode(path)))

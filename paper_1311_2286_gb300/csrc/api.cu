@@ -630,6 +630,21 @@ int cpic_set_solver(cpic_run* r, int solver) {
     return CPIC_OK;
 }
 
+int cpic_set_push_tuning(cpic_run* r, int chunk, int tile) {
+    CHECK_RUN(r);
+    if (chunk < 0 || chunk > (1 << 20) || (chunk % 256) != 0 || (tile != 0 && tile != 1)) {
+        set_error("set_push_tuning: chunk must be 0 or a multiple of 256 up to 2^20, tile 0 or 1 (got %d, %d)", chunk,
+                  tile);
+        return CPIC_ERR_INVALID;
+    }
+    if (r->push_chunk != chunk || r->push_tile != tile) {
+        r->push_chunk = chunk;
+        r->push_tile = tile;
+        invalidate_graphs(r);  // captured steps hold the push parameters
+    }
+    return CPIC_OK;
+}
+
 int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* stream, cpic_run** out) {
     if (!out) {
         set_error("out is NULL");
@@ -641,6 +656,7 @@ int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* s
     cpic_run* r = new cpic_run;
     memset(r, 0, sizeof(*r));
     r->solver = CPIC_SOLVER_BICGSTAB;
+    r->push_tile = 1;
     init_geometry_sizes(r, cfg);
     st = setup_levels(r);
     if (st) {

@@ -92,6 +92,8 @@ struct PushParams {
     long long ncell_h;             // cells of the padded grid: prod (n_a + 2)
     int hs1, hs2;                  // padded strides of axes 1 and 2
     int origin;                    // padded index of cell (0, 0, 0)
+    int chunk;                     // particles per block chunk (0: one wave of blocks)
+    int tile;                      // 1: shared-memory deposit tile when the chunk fits
     DevCounters* ctr;
 };
 
@@ -169,6 +171,8 @@ struct cpic_run {
     double sumJ;                 // sum of finest J_c (singular projection)
     double* red;                 // reduction scratch [2 * 1024 + 8]
     int solver;                  // CPIC_SOLVER_* of the stream solve
+    int push_chunk;              // push kernel: particles per block chunk (0: one wave)
+    int push_tile;               // push kernel: shared-memory deposit tile (1) or direct (0)
     cpic::KrylovState* kry;      // device scalars of the Krylov solve
     double* kv;                  // Krylov vectors, FP64 [5][ncell]: r, r_hat, p, v, s
     float* ph32;                 // preconditioned direction p_hat (FP32)

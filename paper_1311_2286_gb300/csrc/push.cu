@@ -349,6 +349,8 @@ PushParams make_push_params(cpic_run* r) {
     p.hs2 = r->D == 3 ? (r->n[0] + 2) * (r->n[1] + 2) : 0;
     p.origin = 1 + p.hs1 + p.hs2;
     p.ctr = r->ctr;
+    p.chunk = r->push_chunk;
+    p.tile = r->push_tile;
     return p;
 }
 

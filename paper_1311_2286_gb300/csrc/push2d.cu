@@ -155,8 +155,9 @@ __global__ void __launch_bounds__(P2_THREADS, 4) push2d_kernel(PushParams p) {
         total += cnt[s];
     }
     if (total == 0) return;
-    // chunk size: a multiple of the block, about one chunk per block
-    const int C = ((total + (int)gridDim.x - 1) / (int)gridDim.x + P2_THREADS - 1) / P2_THREADS * P2_THREADS;
+    // chunk size: a multiple of the block, about one chunk per block unless set
+    const int C = p.chunk > 0 ? p.chunk
+                              : ((total + (int)gridDim.x - 1) / (int)gridDim.x + P2_THREADS - 1) / P2_THREADS * P2_THREADS;
     const int n0 = p.n[0], n1 = p.n[1], nv0 = n0 + 1;
     const float4* __restrict__ K4 = reinterpret_cast<const float4*>(p.K);
     const float2* __restrict__ G2 = reinterpret_cast<const float2*>(p.G);
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(P2_THREADS, 4) push2d_kernel(PushParams p) {
             }
             tl.r0 = rmin - 2;
             tl.R = rmax - rmin + 5;
-            tl.on = rmax >= rmin && tl.R * tl.W <= TILE_CELLS;
+            tl.on = p.tile && rmax >= rmin && tl.R * tl.W <= TILE_CELLS;
             if (tl.on)
                 for (int k = threadIdx.x; k < tl.R * tl.W; k += P2_THREADS) tile_lo[k] = tile_hi[k] = 0u;
             __syncthreads();

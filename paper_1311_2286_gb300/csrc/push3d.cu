@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
     if (total == 0) return;
     int C = ((total + (int)gridDim.x - 1) / (int)gridDim.x + P3_THREADS - 1) / P3_THREADS * P3_THREADS;
     if (C > P3_CHUNK) C = P3_CHUNK;
+    if (p.chunk > 0) C = p.chunk;
     const int n0 = p.n[0], n1 = p.n[1], n2 = p.n[2];
     const long long T = p.pb.total;
     const float hdt = p.hdt, dt = p.dt;
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
             tl.k0 = kmin - 2;
             tl.P = kmax - kmin + 5;
             if (kmax - kmin > 2) tl.P = 0x7fff;  // a chunk across many planes: no tile
-            tl.on = kmax >= kmin && tl.P * tl.R * tl.W <= P3_TILE_CELLS;
+            tl.on = p.tile && kmax >= kmin && tl.P * tl.R * tl.W <= P3_TILE_CELLS;
             if (tl.on)
                 for (int k = threadIdx.x; k < tl.P * tl.R * tl.W; k += P3_THREADS) tile_lo[k] = tile_hi[k] = 0u;
             __syncthreads();

@@ -67,6 +67,31 @@ using namespace cpic;
 
 extern "C" {
 
+namespace {
+
+// One autotuner trial with the run's current settings: a warm-up sort cycle (captures the
+// graphs), then whole sort cycles of at least trial_steps fixed-field particle steps timed
+// with CUDA events; afterwards the run's particles go back to the snapshot.
+int tune_trial(cpic_run* r, char* buf, int saved_cur, int trial_steps, cudaEvent_t a, cudaEvent_t b, float* ms_per_step) {
+    const int S = r->cfg.sort_interval > 0 ? r->cfg.sort_interval : 1;
+    r->steps_since_sort = 0;
+    int nsteps = trial_steps < S ? S : trial_steps;
+    nsteps = (nsteps + S - 1) / S * S;
+    int st = cpic_step_particles(r, S);
+    if (!st && cudaEventRecord(a, r->stream) != cudaSuccess) st = CPIC_ERR_CUDA;
+    if (!st) st = cpic_step_particles(r, nsteps);
+    if (!st && cudaEventRecord(b, r->stream) != cudaSuccess) st = CPIC_ERR_CUDA;
+    if (!st && cudaEventSynchronize(b) != cudaSuccess) st = CPIC_ERR_CUDA;
+    float ms = 0.0f;
+    if (!st) cudaEventElapsedTime(&ms, a, b);
+    *ms_per_step = ms / nsteps;
+    if (!st) st = snapshot_copy(r, buf, false, saved_cur);  // particles back to their buffer
+    r->cur_host = saved_cur;
+    return st;
+}
+
+}  // namespace
+
 int cpic_autotune(cpic_run* r, int trial_steps, cpic_tuning* out) {
     if (!r || !out || trial_steps < 1) {
         set_error("autotune: NULL run/out or trial_steps < 1");
@@ -77,7 +102,8 @@ int cpic_autotune(cpic_run* r, int trial_steps, cpic_tuning* out) {
         return CPIC_ERR_STATE;
     }
     memset(out, 0, sizeof(*out));
-    const int candidates[CPIC_TUNE_CANDIDATES] = {1, 2, 4, 8, 16};
+    const int intervals[CPIC_TUNE_CANDIDATES] = {1, 2, 4, 8, 16};
+    const int chunks[CPIC_TUNE_CANDIDATES] = {0, 1024, 2048, 4096, 8192};
     char* buf = nullptr;
     const size_t bytes = snapshot_bytes(r);
     cudaError_t e = cudaMalloc(&buf, bytes);
@@ -89,36 +115,54 @@ int cpic_autotune(cpic_run* r, int trial_steps, cpic_tuning* out) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     const int saved_interval = r->cfg.sort_interval, saved_since = r->steps_since_sort, saved_cur = r->cur_host;
+    const int saved_chunk = r->push_chunk, saved_tile = r->push_tile;
     int st = snapshot_copy(r, buf, true, saved_cur);
+    // 1. sort interval
     int best = saved_interval > 0 ? saved_interval : 4;
     float best_ms = 0.0f;
     for (int c = 0; !st && c < CPIC_TUNE_CANDIDATES; ++c) {
-        const int S = candidates[c];
-        r->cfg.sort_interval = S;
-        r->steps_since_sort = 0;
-        // one warm-up cycle of the interval (captures the graphs), then the timed trial
-        int nsteps = trial_steps < S ? S : trial_steps;
-        nsteps = (nsteps + S - 1) / S * S;  // whole sort cycles
-        st = cpic_step_particles(r, S);
-        if (!st && cudaEventRecord(a, r->stream) != cudaSuccess) st = CPIC_ERR_CUDA;
-        if (!st) st = cpic_step_particles(r, nsteps);
-        if (!st && cudaEventRecord(b, r->stream) != cudaSuccess) st = CPIC_ERR_CUDA;
-        if (!st && cudaEventSynchronize(b) != cudaSuccess) st = CPIC_ERR_CUDA;
-        float ms = 0.0f;
-        if (!st) cudaEventElapsedTime(&ms, a, b);
-        out->ms_per_step[c] = ms / nsteps;
-        out->interval[c] = S;
+        r->cfg.sort_interval = intervals[c];
+        out->interval[c] = intervals[c];
+        st = tune_trial(r, buf, saved_cur, trial_steps, a, b, &out->ms_per_step[c]);
         if (!st && (best_ms == 0.0f || out->ms_per_step[c] < best_ms)) {
             best_ms = out->ms_per_step[c];
-            best = S;
+            best = intervals[c];
         }
-        // back to the saved state: particles go to the buffer they were in
-        if (!st) st = snapshot_copy(r, buf, false, saved_cur);
-        r->cur_host = saved_cur;
+    }
+    r->cfg.sort_interval = st ? saved_interval : best;
+    // 2. particles per block chunk, at that interval
+    int best_chunk = saved_chunk;
+    best_ms = 0.0f;
+    for (int c = 0; !st && c < CPIC_TUNE_CANDIDATES; ++c) {
+        st = cpic_set_push_tuning(r, chunks[c], saved_tile);
+        out->chunks[c] = chunks[c];
+        if (!st) st = tune_trial(r, buf, saved_cur, trial_steps, a, b, &out->ms_chunk[c]);
+        if (!st && (best_ms == 0.0f || out->ms_chunk[c] < best_ms)) {
+            best_ms = out->ms_chunk[c];
+            best_chunk = chunks[c];
+        }
+    }
+    // 3. deposit tiling, with that chunk
+    int best_tile = saved_tile;
+    best_ms = 0.0f;
+    for (int t = 0; !st && t < 2; ++t) {
+        st = cpic_set_push_tuning(r, best_chunk, t);
+        if (!st) st = tune_trial(r, buf, saved_cur, trial_steps, a, b, &out->ms_tile[t]);
+        if (!st && (best_ms == 0.0f || out->ms_tile[t] < best_ms)) {
+            best_ms = out->ms_tile[t];
+            best_tile = t;
+        }
     }
     r->steps_since_sort = saved_since;
-    r->cfg.sort_interval = st ? saved_interval : best;
+    if (st) {
+        r->cfg.sort_interval = saved_interval;
+        cpic_set_push_tuning(r, saved_chunk, saved_tile);
+    } else {
+        cpic_set_push_tuning(r, best_chunk, best_tile);
+    }
     out->sort_interval = r->cfg.sort_interval;
+    out->chunk = r->push_chunk;
+    out->tile = r->push_tile;
     cudaStreamSynchronize(r->stream);
     cudaFree(buf);
     cudaEventDestroy(a);

@@ -71,6 +71,17 @@ def test_footprint_and_validation_are_host_only(lib_path):
         cpic.Run.footprint(odd)
 
 
+def test_setters_reject_a_missing_run(lib_path):
+    """The solver and push-tuning setters validate on the host: a NULL run is refused with
+    CPIC_ERR_INVALID and a message, before any CUDA call."""
+    from paper_1311_2286_gb300 import cpic
+
+    lib = cpic.load(lib_path)
+    assert lib.cpic_set_solver(None, cpic.CPIC_SOLVER_BICGSTAB) == cpic.CPIC_ERR_INVALID
+    assert b"NULL" in lib.cpic_last_error()
+    assert lib.cpic_set_push_tuning(None, 1024, 1) == cpic.CPIC_ERR_INVALID
+
+
 def test_product_path_refuses_missing_library(tmp_path):
     from paper_1311_2286_gb300 import cpic
 

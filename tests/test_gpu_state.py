@@ -1,6 +1,6 @@
-"""Checkpoint/restore and the sort-interval autotuner: a restored run continues the saved
-one exactly; autotuning leaves the simulation unchanged (its trial steps are undone) and
-sets one of its candidate intervals."""
+"""Checkpoint/restore and the autotuner: a restored run continues the saved one exactly;
+autotuning leaves the simulation unchanged (its trial steps are undone) and sets one of its
+candidate sort intervals, chunk sizes and deposit paths; the push knobs change no result."""
 import os
 
 import numpy as np
@@ -69,11 +69,15 @@ def test_autotune_leaves_the_run_unchanged(cpic):
     t = a.autotune(trial_steps=6)
     assert t["sort_interval"] in (1, 2, 4, 8, 16)
     assert all(ms > 0 for ms in t["ms_per_step"])
+    assert t["chunk"] in t["chunks"] and t["chunks"] == [0, 1024, 2048, 4096, 8192]
+    assert all(ms > 0 for ms in t["ms_chunk"]) and all(ms > 0 for ms in t["ms_tile"])
+    assert t["tile"] in (0, 1)
     a.step(6)
     got = _state(a, 2)
     chosen = t["sort_interval"]
     a.close()
-    # the same run without autotuning, stepped with the interval it chose
+    # the same run without autotuning, stepped with the interval it chose (the push knobs
+    # change no result: the deposit is integer and the per-particle arithmetic is the same)
     c = cpic.run_from_workload(w, sort_interval=4)
     c.initialize()
     c.step(3)
@@ -81,3 +85,36 @@ def test_autotune_leaves_the_run_unchanged(cpic):
     c.step(6)
     _same(got, _state(c, 2))
     c.close()
+
+
+@pytest.mark.parametrize("chunk,tile", [(0, 0), (1024, 1), (256, 1), (8192, 0)])
+def test_push_tuning_changes_no_result(cpic, chunk, tile):
+    """Any chunk size and either deposit path give the same particles, charge and counters
+    as the defaults (one wave of blocks, tiled deposit), in 2D and 3D."""
+    outs = []
+    for knobs in (None, (chunk, tile)):
+        w = wl.cylinder(n1=32, n2=64, npart_per_species=40_000, seed=64, inject=True)
+        r = cpic.run_from_workload(w, sort_interval=2)
+        r.initialize()
+        if knobs:
+            r.set_push_tuning(*knobs)
+        r.step(5)
+        outs.append(_state(r, 2))
+        r.close()
+    _same(outs[0], outs[1])
+    outs = []
+    for knobs in (None, (chunk, tile)):
+        r = cpic.sphere_run_device(16, 16, 16, 20_000, sort_interval=2)
+        if knobs:
+            r.set_push_tuning(*knobs)
+        r.step_particles(4)
+        outs.append(([r.particles(s) for s in range(2)], [r.charge(s) for s in range(2)], r.diag()))
+        r.close()
+    (pa, ca, da), (pb, cb, db) = outs
+    for s in range(2):
+        ra = np.sort(np.rec.fromarrays([pa[s][0], *pa[s][1], *pa[s][2]]))
+        rb = np.sort(np.rec.fromarrays([pb[s][0], *pb[s][1], *pb[s][2]]))
+        assert np.array_equal(ra, rb)
+        assert np.array_equal(ca[s], cb[s])
+    for key in ("n", "absorbed", "W_K"):
+        assert da[key] == db[key], key
