@@ -171,6 +171,7 @@ struct cpic_run {
     double sumJ;                 // sum of finest J_c (singular projection)
     double* red;                 // reduction scratch [2 * 1024 + 8]
     int solver;                  // CPIC_SOLVER_* of the stream solve
+    int pc_face_only;            // the FP32 V-cycle uses the stencil's face entries only
     int push_chunk;              // push kernel: particles per block chunk (0: one wave)
     int push_tile;               // push kernel: shared-memory deposit tile (1) or direct (0)
     cpic::KrylovState* kry;      // device scalars of the Krylov solve

@@ -52,6 +52,11 @@ namespace cpic {
 namespace {
 
 constexpr int RED_BLOCKS = 256;
+// The V-cycle drops the cross entries of the stencil (face entries only: 2D+1 points, two
+// colours) when no finest-level row's cross entries sum to more than this fraction of its
+// diagonal, e.g. the shell map, orthogonal up to O(h^2) terms of a few 1e-3; the residual
+// and the Krylov products keep the full operator, so only the preconditioner changes.
+constexpr float PC_CROSS_DROP = 0.02f;
 
 __constant__ int c_off2[9][2] = {{0, 0}, {-1, 0}, {1, 0}, {0, -1}, {0, 1}, {-1, -1}, {1, -1}, {-1, 1}, {1, 1}};
 __constant__ int c_off3[19][3] = {{0, 0, 0},  {-1, 0, 0},  {1, 0, 0},  {0, -1, 0}, {0, 1, 0},
@@ -709,6 +714,7 @@ struct AsmParams {
     double* A;
     double* bbc;  // may be null (coarse levels: homogeneous)
     int* cross_flag;
+    unsigned* cross_max;  // largest (sum of |cross entries|) / diagonal of a row, as float bits
 };
 
 __device__ __forceinline__ int slot_of(int D, const int* o) {
@@ -793,7 +799,13 @@ __global__ void assemble_kernel(AsmParams P) {
             P.A[(size_t)k * L.ncell + c] = a[k];
             if (k >= faces && a[k] != 0.0) cross = true;
         }
-        if (cross) atomicOr(P.cross_flag, 1);
+        if (cross) {
+            atomicOr(P.cross_flag, 1);
+            double off = 0.0;
+            for (int k = faces; k < L.S; ++k) off += fabs(a[k]);
+            const float ratio = a[0] != 0.0 ? (float)(off / fabs(a[0])) : 3.0e38f;
+            atomicMax(P.cross_max, __float_as_uint(ratio));  // non-negative floats order as their bits
+        }
         if (P.bbc) P.bbc[c] = rb;
     }
 }
@@ -897,8 +909,9 @@ LV<R> make_lv(const cpic_run* r, int l, bool fp32) {
     for (int f = 0; f < 6; ++f) L.bc[f] = r->cfg.field_bc[f];
     L.ncell = (int)Lv.ncell;
     L.S = Lv.S;
-    L.used = Lv.cross ? Lv.S : 2 * r->D + 1;
-    L.ncol = Lv.cross ? (1 << r->D) : 2;
+    const bool cross = Lv.cross && !(fp32 && r->pc_face_only);
+    L.used = cross ? Lv.S : 2 * r->D + 1;
+    L.ncol = cross ? (1 << r->D) : 2;
     if (fp32) {
         L.A = (const R*)Lv.A32;
         L.x = (R*)Lv.x32;
@@ -965,9 +978,20 @@ int dispatch_shape(const cpic_run* r, F f) {
                  : f(std::integral_constant<int, 3>(), std::integral_constant<int, 7>());
 }
 
+// stencil shape of the FP32 V-cycle: the operator's, or its face entries alone when the
+// cross entries are small enough to leave to the outer iteration (pc_face_only)
+template <class F>
+int dispatch_vshape(const cpic_run* r, F f) {
+    const bool cross = r->lev[0].cross != 0 && !r->pc_face_only;
+    if (r->D == 2) return cross ? f(std::integral_constant<int, 2>(), std::integral_constant<int, 9>())
+                                : f(std::integral_constant<int, 2>(), std::integral_constant<int, 5>());
+    return cross ? f(std::integral_constant<int, 3>(), std::integral_constant<int, 19>())
+                 : f(std::integral_constant<int, 3>(), std::integral_constant<int, 7>());
+}
+
 // one FP32 V-cycle on the correction equation (e = 0 first): lev[0].x32 = V(lev[0].b32)
 int enqueue_vcycle(cpic_run* r, const LVSet& S) {
-    return dispatch_shape(r, [&](auto Dc, auto Nc) -> int {
+    return dispatch_vshape(r, [&](auto Dc, auto Nc) -> int {
         constexpr int D = decltype(Dc)::value, NPT = decltype(Nc)::value;
         cudaStream_t st = r->stream;
         const int nu1 = 2, nu2 = 2;
@@ -1123,9 +1147,12 @@ int enqueue_epilogue(cpic_run* r) {
 
 int mg_setup(cpic_run* r) {
     int* flag = reinterpret_cast<int*>(r->red + 3 * RED_BLOCKS + 4);
+    unsigned* cmax = reinterpret_cast<unsigned*>(r->red + 3 * RED_BLOCKS + 6);
+    r->pc_face_only = 0;
     for (int l = 0; l < r->nlevels; ++l) {
         Level& Lv = r->lev[l];
         CPIC_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), r->stream));
+        CPIC_CUDA(cudaMemsetAsync(cmax, 0, sizeof(unsigned), r->stream));
         AsmParams P;
         Lv.cross = 1;  // all entries while assembling
         P.L = make_lv<double>(r, l, false);
@@ -1137,6 +1164,7 @@ int mg_setup(cpic_run* r) {
         P.A = Lv.A;
         P.bbc = l == 0 ? r->rhs_bc : nullptr;
         P.cross_flag = flag;
+        P.cross_max = cmax;
         assemble_kernel<<<grid_blocks(Lv.ncell, 256), 256, 0, r->stream>>>(P);
         CPIC_CHECK_LAUNCH();
         to_float_kernel<<<grid_blocks((long long)Lv.S * Lv.ncell, 256), 256, 0, r->stream>>>(Lv.A, Lv.A32,
@@ -1145,15 +1173,23 @@ int mg_setup(cpic_run* r) {
         inv_diag_kernel<<<grid_blocks(Lv.ncell, 256), 256, 0, r->stream>>>(Lv.A32, Lv.dinv32, (int)Lv.ncell);
         CPIC_CHECK_LAUNCH();
         int hflag = 0;
+        unsigned hmax = 0;
         CPIC_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, r->stream));
+        CPIC_CUDA(cudaMemcpyAsync(&hmax, cmax, sizeof(unsigned), cudaMemcpyDeviceToHost, r->stream));
         CPIC_CUDA(cudaStreamSynchronize(r->stream));
         Lv.cross = hflag;
+        if (l == 0) {
+            float ratio;
+            memcpy(&ratio, &hmax, sizeof(ratio));
+            r->pc_face_only = hflag && ratio <= PC_CROSS_DROP ? 1 : 0;
+        }
     }
     const Level& Lc = r->lev[r->nlevels - 1];
     int m = (int)Lc.ncell;
     int mm = m + (r->singular ? 1 : 0);
     r->dense_m = mm;
     LV<double> L = make_lv<double>(r, r->nlevels - 1, false);
+    if (r->pc_face_only) L.used = 2 * r->D + 1;  // the coarsest solve of the V-cycle's operator
     dense_matrix_kernel<<<1, 256, 0, r->stream>>>(L, r->singular ? 1 : 0, r->dense_tmp);
     CPIC_CHECK_LAUNCH();
     int* fail = flag;
