@@ -234,8 +234,8 @@ constexpr int SC_RANGE = 4096;
 
 template <int D>
 __global__ void __launch_bounds__(SC_THREADS) rank_kernel(SortParams p) {
-    __shared__ int hcount[SC_RANGE];  // counts, then reserved global starts
-    __shared__ int hrank[SC_RANGE];   // running ranks
+    __shared__ int hcount[SC_RANGE];  // the chunk's count per cell
+    __shared__ int hstart[SC_RANGE];  // the chunk's first slot per cell
     __shared__ int red[2][SC_THREADS / 32];
     const int nsp = p.nsp;
     int cnt[CPIC_MAX_SPECIES];
@@ -279,40 +279,43 @@ __global__ void __launch_bounds__(SC_THREADS) rank_kernel(SortParams p) {
         int kmin, kmax;
         chunk_window<SC_PER_THREAD, SC_RANGE>(key, key_of(cin[lo + (hi - lo) / 2]), red, kmin, kmax);
         const bool local_path = kmax >= kmin;  // block-uniform: keys in [kmin, kmax] go through shared memory
+        // one pass groups the lanes of a warp by key; a group's leader adds the group to its
+        // cell's chunk count (shared) and gets the group's offset in the chunk's share of the
+        // cell back, or (keys outside the window) reserves slots in the global cursor
+        int gpos[SC_PER_THREAD];  // offset in the chunk's share of the cell, or global slot
         if (local_path) {
-            const int range = kmax - kmin + 1;
-            for (int k = threadIdx.x; k < range; k += SC_THREADS) hcount[k] = hrank[k] = 0;
+            for (int k = threadIdx.x; k < kmax - kmin + 1; k += SC_THREADS) hcount[k] = 0;
             __syncthreads();
+        }
 #pragma unroll
-            for (int e = 0; e < SC_PER_THREAD; ++e) {
-                const int k = key[e];
-                const unsigned peers = __match_any_sync(FULL, k);
-                if (k >= kmin && k <= kmax && (__ffs(peers) - 1) == lane) atomicAdd(&hcount[k - kmin], __popc(peers));
+        for (int e = 0; e < SC_PER_THREAD; ++e) {
+            const int k = key[e];
+            const unsigned peers = __match_any_sync(FULL, k);
+            const int leader = __ffs(peers) - 1;
+            int base = 0;
+            if (k >= 0 && leader == lane) {
+                if (local_path && k >= kmin && k <= kmax)
+                    base = atomicAdd(&hcount[k - kmin], __popc(peers));
+                else
+                    base = (int)(scan_s[k] - sbase) + atomicAdd(cursor + k, __popc(peers));
             }
+            gpos[e] = __shfl_sync(FULL, base, leader) + __popc(peers & ((1u << lane) - 1u));
+        }
+        if (local_path) {
             __syncthreads();
-            // one global reservation per cell of the chunk: hcount becomes the cell's first slot
-            for (int k = threadIdx.x; k < range; k += SC_THREADS) {
+            // one global reservation per cell of the chunk: hstart is the chunk's first slot
+            for (int k = threadIdx.x; k < kmax - kmin + 1; k += SC_THREADS) {
                 const int c = hcount[k];
-                if (c) hcount[k] = (int)(scan_s[kmin + k] - sbase) + atomicAdd(cursor + kmin + k, c);
+                if (c) hstart[k] = (int)(scan_s[kmin + k] - sbase) + atomicAdd(cursor + kmin + k, c);
             }
             __syncthreads();
         }
 #pragma unroll
         for (int e = 0; e < SC_PER_THREAD; ++e) {
-            const int i = lo + (int)threadIdx.x + e * SC_THREADS;
             const int k = key[e];
-            const bool act = k >= 0;
-            const unsigned peers = __match_any_sync(FULL, k);
-            const int leader = __ffs(peers) - 1;
-            int start = 0;
-            if (act && leader == lane) {
-                if (local_path && k >= kmin && k <= kmax)
-                    start = hcount[k - kmin] + atomicAdd(&hrank[k - kmin], __popc(peers));
-                else
-                    start = (int)(scan_s[k] - sbase) + atomicAdd(cursor + k, __popc(peers));
-            }
-            start = __shfl_sync(FULL, start, leader);
-            if (act) cout[start + __popc(peers & ((1u << lane) - 1u))] = i;
+            if (k < 0) continue;
+            const int dst = (local_path && k >= kmin && k <= kmax) ? hstart[k - kmin] + gpos[e] : gpos[e];
+            cout[dst] = lo + (int)threadIdx.x + e * SC_THREADS;
         }
     }
 }
