@@ -52,6 +52,7 @@ extern "C" {
 #define CPIC_ERR_STATE (-8)          /* call out of order (e.g. step before a map is set) */
 #define CPIC_ERR_CAPACITY (-9)       /* particles dropped: species capacity exhausted */
 #define CPIC_ERR_NOT_BUILT (-10)     /* the library was built without the requested part */
+#define CPIC_ERR_CANCELLED (-11)     /* a served request was cancelled (cpic_server_cancel) */
 
 /* field boundary conditions (Sec. II.B.3: imposed through ghost cells) */
 #define CPIC_BC_PERIODIC 0
@@ -108,6 +109,12 @@ typedef struct cpic_diag {
     int64_t nonfinite;                     /* cumulative */
     int32_t mg_cycles;                     /* V-cycles of the last solve */
     double mg_residual;                    /* relative residual of the last solve */
+    int32_t pc_face_only;                  /* 1: the FP32 V-cycle uses the stencil's face
+                                              entries only (cross entries below 2% of the
+                                              diagonal; the FP64 residual keeps the full
+                                              operator); 0: the full stencil. The environment
+                                              variable CPIC_PC_FULL_STENCIL, set when the map
+                                              is set, forces 0. */
 } cpic_diag;
 
 /* ---------------------------------------------------------------- general */
@@ -388,6 +395,8 @@ typedef struct cpic_result {
     int64_t n_particles[2], absorbed_object[2], absorbed_outer[2], injected[2];
     double current_object[2];      /* collected current per species, q w absorbed / (steps dt) */
     int32_t mg_cycles;             /* V-cycles of the last solve */
+    char message[160];             /* when status != CPIC_OK: why the request failed (the
+                                      scheduler thread's cpic_last_error text) */
 } cpic_result;
 
 int cpic_server_start(const cpic_server_opts* opts, cpic_server** out);
@@ -397,6 +406,11 @@ int cpic_server_submit(cpic_server* server, const cpic_request* req, uint64_t* t
 /* CPIC_OK and the result once the run is done (the ticket is then retired), CPIC_ERR_BUSY
  * while it is queued or running, CPIC_ERR_INVALID for an unknown ticket. */
 int cpic_server_poll(cpic_server* server, uint64_t ticket, cpic_result* out);
+/* Cancels a request: a queued one leaves the queue at once, an active one stops when the
+ * slice of steps it has in flight ends (its device memory then returns to the pool). Its
+ * result (cpic_server_poll) then has status CPIC_ERR_CANCELLED and the steps it took.
+ * CPIC_ERR_STATE when the request is already done, CPIC_ERR_INVALID for an unknown ticket. */
+int cpic_server_cancel(cpic_server* server, uint64_t ticket);
 /* Requests queued, runs active, free bytes of the pool (any pointer may be NULL). */
 int cpic_server_stats(cpic_server* server, int* queued, int* active, size_t* pool_free);
 /* Stops the scheduler; active runs are finished on the device and discarded. */

@@ -6,22 +6,26 @@ quadratic B-spline 1/2 (3/2 - |xi|)^2 (Birdsall & Langdon, the reference the pap
 for its assignment functions). b2 is assigned to the 3^D cell centres around the particle
 (density lives at cell centres, Sec. II.B).
 
-Fixed-point spec (constants QK = 12, QF = 24; per-axis precision B = QF / D, i.e. 12
-bits in 2D and 8 bits in 3D):
-  per axis: u = floor(t * 2^QK) (exact), s = 2u + 1 - 2^QK (odd, |s| < 2^QK),
-  integer weights for nodes m = -1, 0, +1:
+Fixed-point spec (constants QK = 16, QB = 16, QF = 24):
+  per axis: u = floor(t * 2^QK) (exact for an FP32 offset), s = 2u + 1 - 2^QK (odd,
+  |s| < 2^QK), integer weights for nodes m = -1, 0, +1:
     W[-1] = (2^QK - s)^2,  W[0] = 2 (3 * 2^(2 QK) - s^2),  W[+1] = (2^QK + s)^2,
   which are b2 at the sub-cell centre offset d = s / 2^(QK+1) scaled by 2^(2 QK + 3) and
   sum to exactly 2^(2 QK + 3);
-  per-axis weights at B bits, outer ones rounded to nearest (halves up), the centre one the
-  remainder:  w[+-1] = (W[+-1] + 2^(h-1)) >> h  with h = 2 QK + 3 - B,
-              w[0] = 2^B - w[-1] - w[+1]   (so the three sum to exactly 2^B);
-  node weight q(m) = prod_a w_a[m_a], exact, and the 3^D node weights of a particle sum to
-  exactly 2^(D B) = 2^QF (charge conservation is exact, P5).
+  per-axis weights at QB bits, outer ones rounded to nearest (halves up), the centre one
+  the remainder:  w[+-1] = (W[+-1] + 2^(h-1)) >> h  with h = 2 QK + 3 - QB,
+                  w[0] = 2^QB - w[-1] - w[+1]   (so the three sum to exactly 2^QB);
+  node weights: the exact product p(m) = prod_a w_a[m_a] (eq. (Wpc) builds the
+  multidimensional weight as a product of one-dimensional ones), rounded to QF bits for
+  every node but the centre, q(m) = (p(m) + 2^(r-1)) >> r with r = D QB - QF, and the
+  centre node m = 0 takes the remainder q(0) = 2^QF - sum_{m != 0} q(m), so the 3^D node
+  weights of a particle sum to exactly 2^QF (charge conservation is exact, P5) and every
+  node weight is below 2^QF.
   Node cells outside a non-periodic axis fold onto the boundary cell (charge kept);
   periodic axes wrap.
-The tensor-product form is the b2 assignment of eq. (b2) applied per axis, as the paper's
-multidimensional weights are products of one-dimensional ones (eq. (Wpc)).
+Resolution: offsets to 2^-16 of a cell, per-axis weights to 2^-17, node weights to 2^-25 of
+one particle; the resulting potential differs from the one of the unquantised FP64 deposit
+by a few 1e-7 (2D) to a few 1e-6 (3D) relative L2, pinned by the tests.
 """
 from __future__ import annotations
 
@@ -29,7 +33,8 @@ import itertools
 
 import numpy as np
 
-QK = 12
+QK = 16
+QB = 16
 QF = 24
 
 
@@ -55,27 +60,26 @@ def b2_as_printed(x):
 def axis_weights(t32: np.ndarray):
     """Integer per-axis weights W[m+1] (int64 arrays) from float32 offsets t in [0, 1)."""
     t32 = np.asarray(t32, dtype=np.float32)
-    u = np.floor(t32 * np.float32(1 << QK)).astype(np.int64)
+    u = np.floor(t32.astype(np.float64) * float(1 << QK)).astype(np.int64)
     s = 2 * u + 1 - (1 << QK)
     one = np.int64(1 << QK)
     return [(one - s) ** 2, 2 * (3 * one * one - s * s), (one + s) ** 2]
 
 
-def axis_weights_fixed(t32: np.ndarray, D: int):
-    """Per-axis weights w[m+1] at B = QF / D bits (int64 arrays), summing to 2^B."""
-    B = QF // D
-    h = 2 * QK + 3 - B
+def axis_weights_fixed(t32: np.ndarray):
+    """Per-axis weights w[m+1] at QB bits (int64 arrays), summing to 2^QB."""
+    h = 2 * QK + 3 - QB
     W = axis_weights(t32)
     wm = (W[0] + (1 << (h - 1))) >> h
     wp = (W[2] + (1 << (h - 1))) >> h
-    return [wm, (1 << B) - wm - wp, wp]
+    return [wm, (1 << QB) - wm - wp, wp]
 
 
-def node_weights(t32: np.ndarray):
-    """Fixed-point node weights for particles with offsets t32 (D, n).
-    Returns dict offset tuple (m0, m1[, m2]) -> int64 array (n,)."""
+def node_products(t32: np.ndarray):
+    """Exact products p(m) = prod_a w_a[m_a] of the per-axis weights (int64; at most 48
+    bits). Returns dict offset tuple -> int64 array (n,)."""
     D = t32.shape[0]
-    w = [axis_weights_fixed(t32[a], D) for a in range(D)]
+    w = [axis_weights_fixed(t32[a]) for a in range(D)]
     out = {}
     for m in itertools.product((-1, 0, 1), repeat=D):
         q = np.ones(t32.shape[1], dtype=np.int64)
@@ -83,6 +87,26 @@ def node_weights(t32: np.ndarray):
             q = q * w[a][m[a] + 1]
         out[m] = q
     return out
+
+
+def node_weights(t32: np.ndarray):
+    """Fixed-point node weights for particles with offsets t32 (D, n): the products rounded
+    to QF bits, the centre node the remainder. Returns dict offset tuple (m0, m1[, m2]) ->
+    int64 array (n,)."""
+    D = t32.shape[0]
+    r = D * QB - QF
+    p = node_products(t32)
+    centre = (0,) * D
+    out = {}
+    rest = np.zeros(t32.shape[1], dtype=np.int64)
+    for m, pm in p.items():
+        if m == centre:
+            continue
+        q = (pm + (1 << (r - 1))) >> r
+        out[m] = q
+        rest = rest + q
+    out[centre] = (1 << QF) - rest
+    return dict(sorted(out.items()))
 
 
 def deposit_fixed(idx: np.ndarray, t32: np.ndarray, n, periodic) -> np.ndarray:

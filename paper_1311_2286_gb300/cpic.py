@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libcpic.so")
 CPIC_OK = 0
 CPIC_ERR_INVALID, CPIC_ERR_OOM, CPIC_ERR_CUDA, CPIC_ERR_NOT_CONVERGED = -1, -2, -3, -4
 CPIC_ERR_TIMEOUT, CPIC_ERR_NONFINITE, CPIC_ERR_BUSY, CPIC_ERR_STATE = -5, -6, -7, -8
-CPIC_ERR_CAPACITY, CPIC_ERR_NOT_BUILT = -9, -10
+CPIC_ERR_CAPACITY, CPIC_ERR_NOT_BUILT, CPIC_ERR_CANCELLED = -9, -10, -11
 CPIC_BC_PERIODIC, CPIC_BC_DIRICHLET, CPIC_BC_NEUMANN = 0, 1, 2
 CPIC_PBC_PERIODIC, CPIC_PBC_ABSORB, CPIC_PBC_REFLECT = 0, 1, 2
 CPIC_MAP_SINE, CPIC_MAP_ANNULUS, CPIC_MAP_SPHERE_AXISYM, CPIC_MAP_SHELL = 1, 2, 3, 4
@@ -60,6 +60,7 @@ class cpic_diag(ctypes.Structure):
         ("nonfinite", ctypes.c_int64),
         ("mg_cycles", ctypes.c_int32),
         ("mg_residual", ctypes.c_double),
+        ("pc_face_only", ctypes.c_int32),
     ]
 
 
@@ -109,6 +110,7 @@ class cpic_result(ctypes.Structure):
         ("injected", ctypes.c_int64 * 2),
         ("current_object", ctypes.c_double * 2),
         ("mg_cycles", ctypes.c_int32),
+        ("message", ctypes.c_char * 160),
     ]
 
 
@@ -166,6 +168,7 @@ _SIGS = {
     "cpic_server_start": ([P, ctypes.POINTER(P)], ctypes.c_int),
     "cpic_server_submit": ([P, P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "cpic_server_poll": ([P, ctypes.c_uint64, P], ctypes.c_int),
+    "cpic_server_cancel": ([P, ctypes.c_uint64], ctypes.c_int),
     "cpic_server_stats": ([P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "cpic_server_stop": ([P], ctypes.c_int),
@@ -439,6 +442,7 @@ class Run:
             "absorbed": [[d.absorbed[s][f] for f in range(2 * self.D)] for s in range(ns)],
             "injected": [d.injected[s] for s in range(ns)], "dropped": [d.dropped[s] for s in range(ns)],
             "nonfinite": d.nonfinite, "mg_cycles": d.mg_cycles, "mg_residual": d.mg_residual,
+            "pc_face_only": d.pc_face_only,
         }
 
     def phi(self):
@@ -525,10 +529,12 @@ def cylinder_run_device(n1, n2, npart_per_species, phi_obj, seed, sort_interval=
 
 
 def sphere_run_device(n1, n2, n3, npart_per_species, phi_obj=-5.0, seed=2, sort_interval=4, arena=None,
-                      stream=None, r0=1.0, R=30.0, theta_c=None, inject=False):
+                      stream=None, r0=1.0, R=30.0, theta_c=None, inject=False, host_map=False):
     """A 3D sphere-in-plasma run (shell map, reflecting polar caps) loaded on the device
     with cpic_load_maxwellian and initialised; with inject, Maxwellian flux injection of both
-    species through the outer boundary."""
+    species through the outer boundary. host_map: the map is given as the host vertex array
+    of workloads.shell_vertices (cpic_set_map_vertices) instead of being evaluated on the
+    device (cpic_set_map_analytic)."""
     import math
 
     from . import workloads as wl
@@ -542,7 +548,10 @@ def sphere_run_device(n1, n2, n3, npart_per_species, phi_obj=-5.0, seed=2, sort_
 
         arena = torch.empty(Run.footprint(cfg), dtype=torch.uint8, device="cuda")
     run = Run(cfg, arena=arena, stream=stream)
-    run.set_map_analytic(CPIC_MAP_SHELL, [r0, R, theta_c])
+    if host_map:
+        run.set_map_vertices(w.vertices)
+    else:
+        run.set_map_analytic(CPIC_MAP_SHELL, [r0, R, theta_c])
     for s, sp in enumerate(w.species):
         run.load_maxwellian(s, npart_per_species, sp.vth, seed=seed * 16 + s)
     run.sort()  # the load draws cells in random order: start in cell order
@@ -628,7 +637,12 @@ class Server:
         out = {k: getattr(r, k) for k, _ in cpic_result._fields_}
         for k in ("n_particles", "absorbed_object", "absorbed_outer", "injected", "current_object"):
             out[k] = list(out[k])
+        out["message"] = r.message.decode(errors="replace")
         return out
+
+    def cancel(self, ticket) -> int:
+        """cpic_server_cancel: the status (CPIC_OK, CPIC_ERR_STATE when already done)."""
+        return load().cpic_server_cancel(self.h, ticket)
 
     def wait(self, ticket, timeout=600.0, interval=1e-3):
         import time

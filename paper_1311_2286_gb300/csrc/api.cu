@@ -26,6 +26,20 @@ void set_error(const char* fmt, ...) {
     va_end(ap);
 }
 
+int device_sm_count() {
+    constexpr int MAXDEV = 64;
+    static std::atomic<int> cache[MAXDEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    if (dev >= MAXDEV) dev = MAXDEV - 1;
+    int v = cache[dev].load(std::memory_order_acquire);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        cache[dev].store(v, std::memory_order_release);
+    }
+    return v;
+}
+
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
     return e == cudaErrorMemoryAllocation ? CPIC_ERR_OOM : CPIC_ERR_CUDA;
@@ -571,6 +585,7 @@ const char* cpic_status_string(int s) {
         case CPIC_ERR_STATE: return "call out of order";
         case CPIC_ERR_CAPACITY: return "particle capacity exhausted";
         case CPIC_ERR_NOT_BUILT: return "not built in this version";
+        case CPIC_ERR_CANCELLED: return "cancelled";
         default: return "unknown status";
     }
 }
@@ -777,7 +792,7 @@ int cpic_load_particles(cpic_run* r, int sp, int64_t n, const int32_t* cell, con
     CPIC_CHECK_LAUNCH();
     if (n > 0) {
         long long blocks = (n + 255) / 256;
-        if (blocks > 152 * 4) blocks = 152 * 4;
+        if (blocks > 4LL * device_sm_count()) blocks = 4LL * device_sm_count();
         validate_load_kernel<<<(int)blocks, 256, 0, r->stream>>>(r->D, r->n[0], r->n[1], r->n[2], r->pb.cell[b] + base,
                                                                  r->pb.t[b] + base, r->pb.v[b] + base, T, n, r->ctr, sp);
         CPIC_CHECK_LAUNCH();
@@ -987,6 +1002,7 @@ int cpic_get_diag(cpic_run* r, cpic_diag* out) {
     out->nonfinite = h.nonfinite;
     out->mg_cycles = h.mg_cycles;
     out->mg_residual = h.mg_residual;
+    out->pc_face_only = r->pc_face_only;
     return CPIC_OK;
 }
 

@@ -184,7 +184,7 @@ RhsParams make_rhs_params(const cpic_run* r) {
 int launch_vertex_field(cpic_run* r) {
     FieldGrid g = make_field_grid(r);
     long long b = (r->nvert + 255) / 256;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > 8LL * device_sm_count()) b = 8LL * device_sm_count();
     vertex_field_kernel<<<(int)b, 256, 0, r->stream>>>(g, r->lev[0].x, r->G32, r->K32);
     CPIC_CHECK_LAUNCH();
     return CPIC_OK;
@@ -193,7 +193,7 @@ int launch_vertex_field(cpic_run* r) {
 int launch_rhs(cpic_run* r, double* b) {
     RhsParams p = make_rhs_params(r);
     long long nb = (r->ncell + 255) / 256;
-    if (nb > 152 * 8) nb = 152 * 8;
+    if (nb > 8LL * device_sm_count()) nb = 8LL * device_sm_count();
     rhs_kernel<<<(int)nb, 256, 0, r->stream>>>(p, b);
     CPIC_CHECK_LAUNCH();
     return CPIC_OK;

@@ -379,7 +379,7 @@ Grid make_grid(const cpic_run* r, const int* n) {
 
 int blocks_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > 16LL * device_sm_count()) b = 16LL * device_sm_count();
     if (b < 1) b = 1;
     return (int)b;
 }

@@ -300,7 +300,7 @@ int launch_inject(cpic_run* r) {
         o.seed = sp.seed;
         long long maxc = (long long)ceil(sp.rate) + 1;
         long long b = (maxc + 255) / 256;
-        if (b > 152 * 4) b = 152 * 4;
+        if (b > 4LL * device_sm_count()) b = 4LL * device_sm_count();
         if (b > maxb) maxb = b;
     }
     if (!ip.nsp) return CPIC_OK;

@@ -12,7 +12,8 @@
 namespace cpic {
 
 // ---------------------------------------------------------------- constants
-constexpr int QK = 12;  // spec Q: offsets quantised to 2^-QK of a cell
+constexpr int QK = 16;  // spec Q: offsets quantised to 2^-QK of a cell
+constexpr int QB = 16;  // spec Q: per-axis weights to 2^-QB
 constexpr int QF = 24;  // spec Q: one particle deposits exactly 2^QF charge units
 constexpr int KE_BITS = 24;  // spec D: kinetic energy products in units of 2^-24
 constexpr int MAX_LEVELS = 16;
@@ -27,6 +28,8 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
         cudaError_t e_ = (call);                                             \
         if (e_ != cudaSuccess) return cuda_fail(e_, #call, __FILE__, __LINE__); \
     } while (0)
+// streaming multiprocessors of the current device (queried once per device, cached)
+int device_sm_count();
 // every kernel launch of the library is followed by this check, which also counts it
 void count_launch();
 void add_launches(long long n);  // kernels launched by a graph replay

@@ -106,7 +106,7 @@ int launch_load_maxwellian(cpic_run* r, int sp, long long n, double vth, const d
     lp.seed = seed;
     if (n > 0) {
         long long blocks = (n + 255) / 256;
-        if (blocks > 152 * 16) blocks = 152 * 16;
+        if (blocks > 16LL * device_sm_count()) blocks = 16LL * device_sm_count();
         maxwellian_kernel<<<(int)blocks, 256, 0, r->stream>>>(lp);
         CPIC_CHECK_LAUNCH();
     }

@@ -41,6 +41,7 @@
 // it writes the decision into a CUDA graph conditional handle, so inside a captured step
 // the cycle loop is a conditional WHILE node that runs on the device with no host round
 // trip and no idle launches.
+#include <stdlib.h>
 #include <math.h>
 #include <string.h>
 
@@ -926,7 +927,7 @@ LV<R> make_lv(const cpic_run* r, int l, bool fp32) {
 
 int grid_blocks(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > 8LL * device_sm_count()) b = 8LL * device_sm_count();
     if (b < 1) b = 1;
     return (int)b;
 }
@@ -1181,7 +1182,9 @@ int mg_setup(cpic_run* r) {
         if (l == 0) {
             float ratio;
             memcpy(&ratio, &hmax, sizeof(ratio));
-            r->pc_face_only = hflag && ratio <= PC_CROSS_DROP ? 1 : 0;
+            // CPIC_PC_FULL_STENCIL in the environment keeps the full stencil in the V-cycle
+            // (the face-only form is a cost choice; both meet the same stopping test)
+            r->pc_face_only = hflag && ratio <= PC_CROSS_DROP && !getenv("CPIC_PC_FULL_STENCIL") ? 1 : 0;
         }
     }
     const Level& Lc = r->lev[r->nlevels - 1];

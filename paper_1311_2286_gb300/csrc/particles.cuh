@@ -34,20 +34,49 @@ __device__ __forceinline__ void renorm(float x, float& f, int& c) {
     c = (int)cf;
 }
 
-// Per-axis fixed-point b2 weights (spec Q), w[m+1] for m = -1, 0, +1, at B = 24 / D bits:
-// the offset is quantised to u = floor(t 2^12), the exact integer b2 values of the sub-cell
-// centre (scaled by 2^27) are (2^12 -+ s)^2 for the outer nodes, s = 2u + 1 - 2^12; those
-// are rounded to B bits and the centre takes the remainder, so the three sum to 2^B.
+// Per-axis fixed-point b2 weights (spec Q), w[m+1] for m = -1, 0, +1, at QB = 16 bits: the
+// offset is quantised to u = floor(t 2^16) (exact for an FP32 offset in [0, 1)); the exact
+// integer b2 values of the sub-cell centre, scaled by 2^35, are (2^16 -+ s)^2 for the outer
+// nodes, s = 2u + 1 - 2^16 (up to 2^34, so 64-bit); those are rounded to 16 bits (halves up)
+// and the centre takes the remainder, so the three sum to 2^16. Every weight is below 2^16.
+__device__ __forceinline__ void axis_weights(float t, unsigned w[3]) {
+    constexpr int H = 2 * QK + 3 - QB;
+    const int u = (int)floorf(__fmul_rn(t, 65536.0f));
+    const int s = 2 * u + 1 - 65536;
+    const unsigned lo = (unsigned)(65536 - s), hi = (unsigned)(65536 + s);
+    w[0] = (unsigned)(((unsigned long long)lo * lo + (1ull << (H - 1))) >> H);
+    w[2] = (unsigned)(((unsigned long long)hi * hi + (1ull << (H - 1))) >> H);
+    w[1] = (1u << QB) - w[0] - w[2];
+}
+
+// Node weights (spec Q) of every node but the centre: the exact product of the per-axis
+// weights rounded to QF = 24 bits (halves up). 2D: a b < 2^32; 3D: a (b c) < 2^48. The
+// centre node takes 2^24 minus the others, so a particle deposits exactly 2^24 units and
+// every node weight is below 2^24.
+__device__ __forceinline__ unsigned node_weight2(unsigned a, unsigned b) {
+    return (a * b + (1u << (2 * QB - QF - 1))) >> (2 * QB - QF);
+}
+__device__ __forceinline__ unsigned node_weight3(unsigned a, unsigned bc) {
+    return (unsigned)(((unsigned long long)a * bc + (1ull << (3 * QB - QF - 1))) >> (3 * QB - QF));
+}
+
+// all 3^D node weights of one particle in node order (m0 fastest), centre included
 template <int D>
-__device__ __forceinline__ void axis_weights(float t, int w[3]) {
-    constexpr int B = D == 2 ? 12 : 8;
-    constexpr int H = 2 * QK + 3 - B;
-    const int u = (int)floorf(__fmul_rn(t, 4096.0f));
-    const int s = 2 * u + 1 - 4096;
-    const int lo = 4096 - s, hi = 4096 + s;
-    w[0] = (lo * lo + (1 << (H - 1))) >> H;
-    w[2] = (hi * hi + (1 << (H - 1))) >> H;
-    w[1] = (1 << B) - w[0] - w[2];
+__device__ __forceinline__ void node_weights(const float* t, unsigned* q) {
+    constexpr int NN = D == 2 ? 9 : 27;
+    constexpr int CENTRE = NN / 2;
+    unsigned w[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) axis_weights(t[a], w[a]);
+    unsigned rest = 0;
+#pragma unroll
+    for (int node = 0; node < NN; ++node) {
+        if (node == CENTRE) continue;
+        const int m0 = node % 3, m1 = (node / 3) % 3, m2 = node / 9;
+        q[node] = D == 2 ? node_weight2(w[0][m0], w[1][m1]) : node_weight3(w[0][m0], w[1][m1] * w[2][m2]);
+        rest += q[node];
+    }
+    q[CENTRE] = (1u << QF) - rest;
 }
 
 template <int D>
@@ -135,7 +164,7 @@ __device__ __forceinline__ int vertex_of(const PushParams& p, const int* c) {
 // The node weights are exact integer products of the per-axis weights. Particles are kept
 // in cell order, so many lanes of a warp share one cell: the largest group of lanes with a
 // common cell (__match_any_sync) is summed with full-warp __reduce_add_sync (a node weight
-// is at most 2^24, so 32 of them fit 32 bits) and its leader deposits the sums; the other
+// is below 2^24, so 32 of them fit 32 bits) and its leader deposits the sums; the other
 // lanes deposit their own weights. Integer sums are exact, so the grouping does not change
 // the result.
 template <int D>
@@ -145,17 +174,16 @@ __device__ __forceinline__ void deposit_warp(const PushParams& p, int s, bool al
     const int lane = threadIdx.x & 31;
     const unsigned live = __ballot_sync(FULL, alive);
     if (!live) return;
-    int w[3][3];
-#pragma unroll
-    for (int a = 0; a < D; ++a) axis_weights<D>(alive ? t[a] : 0.0f, w[a]);
-    if (!alive) w[0][0] = w[0][1] = w[0][2] = 0;  // dead lanes carry zero weight
     unsigned q[NN];
+    {
+        float tz[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int node = 0; node < NN; ++node) {
-        const int m0 = node % 3, m1 = (node / 3) % 3, m2 = node / 9;
-        unsigned v = (unsigned)(w[0][m0] * w[1][m1]);
-        if (D == 3) v *= (unsigned)w[2][m2];
-        q[node] = v;
+        for (int a = 0; a < D; ++a) tz[a] = alive ? t[a] : 0.0f;
+        node_weights<D>(tz, q);
+    }
+    if (!alive) {  // dead lanes carry zero weight
+#pragma unroll
+        for (int node = 0; node < NN; ++node) q[node] = 0u;
     }
     // padded offset of this lane's cell; dead lanes take the first live lane's cell
     int off = c[0] + c[1] * p.hs1 + (D == 3 ? c[2] * p.hs2 : 0);

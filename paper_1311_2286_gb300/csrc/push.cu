@@ -21,6 +21,7 @@
 // from axis 0 upwards; gathers as a fused multiply-add chain over corners in the order
 // 0 .. 2^D - 1 (bit a = +1 along axis a); renormalisation c = floor(x), f = x - c, f == 1
 // -> (0, c + 1); the predictor point is clamped on non-periodic axes.
+#include <atomic>
 #include "particles.cuh"
 
 namespace cpic {
@@ -357,15 +358,17 @@ PushParams make_push_params(cpic_run* r) {
 // one wave of resident blocks over all SMs (the kernel walks its chunk in a loop)
 template <int D, int MODE>
 static int particle_grid(cpic_run* r) {
-    static int per_sm[2][3] = {{0, 0, 0}, {0, 0, 0}};  // [D-2][MODE], resident blocks per SM
-    int& occ = per_sm[D - 2][MODE];
-    if (!occ) {
-        int dev = 0, nsm = 0, b = 0;
-        CPIC_CUDA(cudaGetDevice(&dev));
-        CPIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        CPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, particle_kernel<D, MODE>, 256, 0));
-        occ = (b < 1 ? 1 : b) * nsm;
+    static std::atomic<int> per_sm[64];  // resident blocks per SM, per device
+    int dev = 0;
+    CPIC_CUDA(cudaGetDevice(&dev));
+    std::atomic<int>& cache = per_sm[dev & 63];
+    int bs = cache.load(std::memory_order_acquire);
+    if (bs <= 0) {
+        CPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, particle_kernel<D, MODE>, 256, 0));
+        if (bs < 1) bs = 1;
+        cache.store(bs, std::memory_order_release);
     }
+    const long long occ = (long long)bs * device_sm_count();
     long long tot = 0;
     for (int s = 0; s < r->cfg.n_species; ++s) tot += r->pb.capacity[s] + 32;
     long long b = (tot + 255) / 256;
@@ -442,7 +445,7 @@ int launch_fold(cpic_run* r) {
     f.src = r->charge_h;
     f.dst = r->charge;
     long long b = (r->ncell * f.nsp + 255) / 256;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > 8LL * device_sm_count()) b = 8LL * device_sm_count();
     fold_kernel<<<(int)b, 256, 0, r->stream>>>(f);
     CPIC_CHECK_LAUNCH();
     return CPIC_OK;

@@ -23,6 +23,7 @@
 // leapfrog kick (eq. (step1)); predictor xi' = xi^n + dt/2 k(xi^n) v (eq. (step2)); k
 // re-gathered at xi' (eq. (step3)); corrector xi^{n+1} = xi^n + dt k(xi') v (eq. (step4));
 // boundaries (Sec. II.B.4); b2 deposit in 64-bit fixed point (eqs. (pg), (Wpc), (b2)).
+#include <atomic>
 #include <type_traits>
 
 #include "particles.cuh"
@@ -58,8 +59,8 @@ __device__ __forceinline__ void predict_axis(float x, int c, int n, int& cp, flo
 
 // Shared-memory charge tile of one chunk: rows [r0, r0 + R) of the padded grid's layout
 // (W = n0 + 2 columns, column 0 and W - 1 the halo), 64-bit counts kept as 32-bit low words
-// with carries into high words (shared 32-bit atomics; a node weight is below 2^32, so one
-// add carries at most once).
+// with carries into high words (shared 32-bit atomics; a group's node weight is below 2^32,
+// so one add carries at most once).
 constexpr int TILE_CELLS = 2048;  // 16 KB of shared memory per block
 
 struct Tile {
@@ -95,12 +96,8 @@ __device__ __forceinline__ void deposit_tile(const PushParams& p, const Tile& tl
     const bool out = alive && !in;
     if (__any_sync(FULL, out)) deposit_warp<2>(p, s, out, c, t);
     if (!__any_sync(FULL, in)) return;
-    int w[2][3];
-    axis_weights<2>(t[0], w[0]);
-    axis_weights<2>(t[1], w[1]);
     unsigned q[9];
-#pragma unroll
-    for (int node = 0; node < 9; ++node) q[node] = (unsigned)(w[0][node % 3] * w[1][node / 3]);
+    node_weights<2>(t, q);
     // lanes that do not deposit here get keys of their own
     const int off = in ? rr * tl.W + c[0] + 1 : -1 - lane;
     const unsigned peers = __match_any_sync(FULL, off);
@@ -425,14 +422,17 @@ __global__ void __launch_bounds__(P2_THREADS, 4) push2d_kernel(PushParams p) {
 
 template <bool PER0, bool PER1>
 int launch_push2d_t(cpic_run* r, const PushParams& p) {
-    static int occ = 0;  // resident blocks on the device (one wave)
-    if (!occ) {
-        int dev = 0, nsm = 0, b = 0;
-        CPIC_CUDA(cudaGetDevice(&dev));
-        CPIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    static std::atomic<int> per_sm[64];  // resident blocks per SM, per device
+    int dev = 0;
+    CPIC_CUDA(cudaGetDevice(&dev));
+    std::atomic<int>& cache = per_sm[dev & 63];
+    int b = cache.load(std::memory_order_acquire);
+    if (b <= 0) {
         CPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, push2d_kernel<PER0, PER1>, P2_THREADS, 0));
-        occ = (b < 1 ? 1 : b) * nsm;
+        if (b < 1) b = 1;
+        cache.store(b, std::memory_order_release);
     }
+    const long long occ = (long long)b * device_sm_count();  // one wave
     long long tot = 0;
     for (int s = 0; s < r->cfg.n_species; ++s) tot += r->pb.capacity[s];
     long long blocks = (tot + P2_THREADS - 1) / P2_THREADS;

@@ -16,6 +16,7 @@
 //     FP32x2 arithmetic (each lane rounds as the scalar form), the tile atomics' carries
 //     collected in a bit mask, predicated state stores, the iteration loop specialised on
 //     whether the chunk's tile is in use.
+#include <atomic>
 #include <type_traits>
 
 #include "particles.cuh"
@@ -66,9 +67,9 @@ __device__ __forceinline__ void deposit_tile3(const PushParams& p, const Tile3& 
     const bool out = alive && !in;
     if (__any_sync(FULL, out)) deposit_warp<3>(p, s, out, c, t);
     if (!__any_sync(FULL, in)) return;
-    int w[3][3];
+    unsigned w[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) axis_weights<3>(t[a], w[a]);
+    for (int a = 0; a < 3; ++a) axis_weights(t[a], w[a]);
     // lanes that do not deposit here get keys of their own
     const int off = in ? (pz * tl.R + ry) * tl.W + c[0] + 1 : -1 - lane;
     const unsigned peers = __match_any_sync(FULL, off);
@@ -79,25 +80,36 @@ __device__ __forceinline__ void deposit_tile3(const PushParams& p, const Tile3& 
     const bool issue = group ? lane == leader : in;
     const int plane = tl.R * tl.W;
     const unsigned base = tl.lo + 4u * (unsigned)(off - 1 - tl.W - plane);
-    unsigned m = 0;  // carry out of node (m0, m1, m2)'s low word in bit 26 - (m0 + 3 m1 + 9 m2)
+    // rows of three nodes (m1, m2) in the order below, the centre row (1, 1) last, so that the
+    // centre node can take 2^24 minus the other 26 node weights of the lane
+    constexpr int ROW[9] = {0, 1, 2, 3, 5, 6, 7, 8, 4};
+    unsigned rest = 0;
+    unsigned m = 0;  // carry out of the k-th node added (k = 3 i + m0 for the i-th row) in bit 26 - k
 #pragma unroll
-    for (int m2 = 0; m2 < 3; ++m2)
-#pragma unroll
-        for (int m1 = 0; m1 < 3; ++m1) {
-            const unsigned w12 = (unsigned)(w[1][m1] * w[2][m2]);
-            unsigned q0 = (unsigned)w[0][0] * w12, q1 = (unsigned)w[0][1] * w12, q2 = (unsigned)w[0][2] * w12;
-            if (group) {
-                q0 = __reduce_add_sync(peers, q0);
-                q1 = __reduce_add_sync(peers, q1);
-                q2 = __reduce_add_sync(peers, q2);
-            }
-            if (issue) tile3_add_row(m, base + 4u * (unsigned)(m1 * tl.W + m2 * plane), q0, q1, q2);
+    for (int i = 0; i < 9; ++i) {
+        const int m1 = ROW[i] % 3, m2 = ROW[i] / 3;
+        const unsigned w12 = w[1][m1] * w[2][m2];
+        unsigned q0 = node_weight3(w[0][0], w12), q2 = node_weight3(w[0][2], w12), q1;
+        if (ROW[i] == 4) {
+            q1 = (1u << QF) - rest - q0 - q2;
+        } else {
+            q1 = node_weight3(w[0][1], w12);
+            rest += q0 + q1 + q2;
         }
+        if (group) {
+            q0 = __reduce_add_sync(peers, q0);
+            q1 = __reduce_add_sync(peers, q1);
+            q2 = __reduce_add_sync(peers, q2);
+        }
+        if (issue) tile3_add_row(m, base + 4u * (unsigned)(m1 * tl.W + m2 * plane), q0, q1, q2);
+    }
     if (issue && m) {  // rare: carries into the high words
         unsigned* hi = tl.hi_ptr + (off - 1 - tl.W - plane);
 #pragma unroll
-        for (int node = 0; node < 27; ++node)
-            if ((m >> (26 - node)) & 1u) atomicAdd(hi + (node % 3) + ((node / 3) % 3) * tl.W + (node / 9) * plane, 1u);
+        for (int k = 0; k < 27; ++k) {
+            const int r = ROW[k / 3];
+            if ((m >> (26 - k)) & 1u) atomicAdd(hi + (k % 3) + (r % 3) * tl.W + (r / 3) * plane, 1u);
+        }
     }
 }
 
@@ -476,15 +488,19 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
 template <int K0, int K1, int K2>
 int launch_push3d_t(cpic_run* r, const PushParams& p) {
     constexpr size_t smem = sizeof(unsigned) * 2 * P3_TILE_CELLS;
-    static int occ = 0;
-    if (!occ) {
-        int dev = 0, nsm = 0, b = 0;
+    static std::atomic<int> per_sm[64];  // resident blocks per SM, per device (after the
+                                         // shared-memory attribute is set on that device)
+    int dev = 0;
+    CPIC_CUDA(cudaGetDevice(&dev));
+    std::atomic<int>& cache = per_sm[dev & 63];
+    int b = cache.load(std::memory_order_acquire);
+    if (b <= 0) {
         CPIC_CUDA(cudaFuncSetAttribute(push3d_kernel<K0, K1, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        CPIC_CUDA(cudaGetDevice(&dev));
-        CPIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         CPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, push3d_kernel<K0, K1, K2>, P3_THREADS, smem));
-        occ = (b < 1 ? 1 : b) * nsm;
+        if (b < 1) b = 1;
+        cache.store(b, std::memory_order_release);
     }
+    const long long occ = (long long)b * device_sm_count();  // one wave
     long long tot = 0;
     for (int s = 0; s < r->cfg.n_species; ++s) tot += r->pb.capacity[s];
     long long blocks = (tot + P3_THREADS - 1) / P3_THREADS;

@@ -23,6 +23,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <stdio.h>
 #include <thread>
 #include <vector>
 
@@ -81,6 +82,7 @@ struct Job {
     int slice = 0;            // steps of the slice in flight
     long long slice_live = 0; // live particles when it was launched
     Clock::time_point t_submit, t_start;
+    std::atomic<bool> cancel{false};  // set by cpic_server_cancel while the run is active
     cpic_result res{};
 };
 
@@ -96,6 +98,7 @@ struct cpic_server {
     std::vector<Job*> active;
     std::map<uint64_t, Job*> done;
     std::map<uint64_t, int> state;  // ticket -> 0 queued, 1 active, 2 done
+    std::map<uint64_t, Job*> jobs;  // every ticket not yet polled
     uint64_t next_ticket = 1;
     std::atomic<bool> stop{false};
     std::thread worker;
@@ -171,6 +174,12 @@ int start_job(cpic_server* sv, Job* j) {
 void finish_job(cpic_server* sv, Job* j, int status) {
     cpic_result& r = j->res;
     r.status = status;
+    // the failure's message was written on this (the scheduler's) thread: keep it with the
+    // result, where the client that polls for it can read it
+    if (status == CPIC_ERR_CANCELLED)
+        snprintf(r.message, sizeof(r.message), "cancelled after %d of %d steps", j->steps_done, j->req.steps);
+    else if (status)
+        snprintf(r.message, sizeof(r.message), "%s", cpic_last_error());
     r.ticket = j->ticket;
     r.steps = j->steps_done;
     if (j->run && !status) {
@@ -264,6 +273,7 @@ void worker_loop(cpic_server* sv) {
             }
             if (!st) j->res.particle_steps += (long long)j->slice * j->slice_live;
             j->slice = 0;
+            if (!st && j->cancel.load()) st = CPIC_ERR_CANCELLED;
             if (!st && j->steps_done < j->req.steps) {
                 const int k = std::min(sv->opts.steps_per_slice, j->req.steps - j->steps_done);
                 st = cpic_step(j->run, k);
@@ -361,6 +371,7 @@ int cpic_server_submit(cpic_server* sv, const cpic_request* req, uint64_t* ticke
         std::lock_guard<std::mutex> lk(sv->mu);
         j->ticket = sv->next_ticket++;
         sv->state[j->ticket] = 0;
+        sv->jobs[j->ticket] = j;
         sv->queue.push_back(j);
     }
     sv->cv.notify_one();
@@ -383,8 +394,45 @@ int cpic_server_poll(cpic_server* sv, uint64_t ticket, cpic_result* out) {
     Job* j = sv->done[ticket];
     *out = j->res;
     sv->done.erase(ticket);
+    sv->jobs.erase(ticket);
     sv->state.erase(it);
     delete j;
+    return CPIC_OK;
+}
+
+int cpic_server_cancel(cpic_server* sv, uint64_t ticket) {
+    if (!sv) {
+        set_error("server_cancel: NULL server");
+        return CPIC_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->state.find(ticket);
+    if (it == sv->state.end()) {
+        set_error("server_cancel: unknown ticket %llu", (unsigned long long)ticket);
+        return CPIC_ERR_INVALID;
+    }
+    if (it->second == 2) {
+        set_error("server_cancel: ticket %llu is already done", (unsigned long long)ticket);
+        return CPIC_ERR_STATE;
+    }
+    if (it->second == 1) {  // active: the scheduler stops it when its slice in flight ends
+        sv->jobs[ticket]->cancel.store(true);
+        return CPIC_OK;
+    }
+    for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q) {
+        if ((*q)->ticket != ticket) continue;
+        Job* j = *q;
+        sv->queue.erase(q);
+        cpic_result& r = j->res;
+        r.status = CPIC_ERR_CANCELLED;
+        r.ticket = j->ticket;
+        snprintf(r.message, sizeof(r.message), "cancelled before admission");
+        r.latency_s = std::chrono::duration<double>(Clock::now() - j->t_submit).count();
+        r.queue_s = r.latency_s;
+        it->second = 2;
+        sv->done[ticket] = j;
+        return CPIC_OK;
+    }
     return CPIC_OK;
 }
 

@@ -385,7 +385,7 @@ int launch_sort(cpic_run* r) {
     long long tot = 0;
     for (int s = 0; s < p.nsp; ++s) tot += r->pb.capacity[s] + 32;
     long long pblocks = (tot + 255) / 256;
-    if (pblocks > 152 * 8) pblocks = 152 * 8;
+    if (pblocks > 8LL * device_sm_count()) pblocks = 8LL * device_sm_count();
     if (pblocks < 1) pblocks = 1;
     CPIC_CUDA(cudaMemsetAsync(r->hist, 0, sizeof(int) * N, r->stream));
     hist_kernel<<<(int)pblocks, 256, 0, r->stream>>>(p);

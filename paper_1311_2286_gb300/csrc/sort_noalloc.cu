@@ -10,9 +10,9 @@
 //
 // The scratch (CPIC_NOALLOC_MAX_CELLS cells of histogram plus prefix sums, 8 MiB) exists
 // on every GPU that loads the library, until the process exits. Host code may not use the
-// array's name as a device pointer; its device address is looked up once per device with
-// cudaGetSymbolAddress, on the first call made with that device current. That first call
-// should therefore happen before any stream capture. Every call uses the same scratch and
+// array's name as a device pointer; its device address is looked up with
+// cudaGetSymbolAddress on every call made on a stream that is not capturing (the first call
+// on a device is always one: make it before any stream capture), and cached per device. Every call uses the same scratch and
 // leaves its contents behind, so the histogram is cleared at the start of each call, and
 // two calls whose work overlaps on the GPU (different streams, or graph branches without
 // an ordering between them) race on it.
@@ -161,16 +161,24 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 int* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-// device address of the scratch array on the current device (looked up once per device)
-int scratch_for_current_device(int** out) {
+// Device address of the scratch array on the current device. A call on a stream that is not
+// capturing looks the address up again (after a device reset the library's module is loaded
+// anew, possibly elsewhere); a call on a capturing stream uses the address cached by the
+// device's last call outside capture.
+int scratch_for_current_device(cudaStream_t stream, int** out) {
     int dev = -1;
     CPIC_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) {
         set_error("sort_cells_noalloc: device ordinal %d outside [0, %d)", dev, kMaxDevices);
         return CPIC_ERR_INVALID;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;  // not decidable here: take the cached address
+    }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
@@ -213,10 +221,10 @@ extern "C" int cpic_sort_cells_noalloc(int dim, const int32_t* n, int64_t count,
         set_error("sort_cells_noalloc: NULL array");
         return CPIC_ERR_INVALID;
     }
-    int* scratch = nullptr;
-    int st = scratch_for_current_device(&scratch);
-    if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    int* scratch = nullptr;
+    int st = scratch_for_current_device(s, &scratch);
+    if (st) return st;
     NSort p;
     p.D = dim;
     for (int a = 0; a < 3; ++a) p.n[a] = a < dim ? n[a] : 1;
@@ -235,7 +243,7 @@ extern "C" int cpic_sort_cells_noalloc(int dim, const int32_t* n, int64_t count,
     // the scratch keeps the previous call's contents: clear the histogram first
     CPIC_CUDA(cudaMemsetAsync(p.hist, 0, sizeof(int) * ncell, s));
     long long pblocks = (count + 255) / 256;
-    if (pblocks > 152 * 8) pblocks = 152 * 8;
+    if (pblocks > 8LL * device_sm_count()) pblocks = 8LL * device_sm_count();
     if (pblocks < 1) pblocks = 1;
     ns_hist<<<(int)pblocks, 256, 0, s>>>(p);
     CPIC_CHECK_LAUNCH();

@@ -107,3 +107,61 @@ def test_sphere_requests_in_a_mix(cpic):
         assert sv.wait(tk)["status"] == 0
     _same(alone, mixed)
     sv.stop()
+
+
+def test_cancel_queued_and_active_requests(cpic):
+    """Host-side failure paths of the server: a queued request cancelled before admission
+    and an active one cancelled mid-run both come back with CPIC_ERR_CANCELLED and a message
+    saying so (the active one after fewer than its steps), their pool memory returns, a
+    cancel of a finished request is refused with CPIC_ERR_STATE, and the requests around
+    them still complete with their stand-alone results."""
+    long = dict(n1=32, n2=64, particles_per_species=40_000, steps=4000, seed=51)
+    fp = cpic.Run.footprint(_cfg_of(cpic, _req(cpic, **long)))
+    sv = cpic.Server(hbm_budget=int(1.5 * fp), max_active=4, steps_per_slice=5)  # one run at a time
+    t_active = sv.submit(_req(cpic, **long))
+    t_queued = sv.submit(_req(cpic, **long))
+    t_after = sv.submit(_req(cpic, seed=52))
+    t0 = time.time()
+    while sv.stats()["active"] < 1 and time.time() - t0 < 60:
+        time.sleep(1e-3)
+    time.sleep(0.05)
+    assert sv.cancel(t_queued) == cpic.CPIC_OK
+    assert sv.cancel(t_active) == cpic.CPIC_OK
+    rq = sv.wait(t_queued)
+    assert rq["status"] == cpic.CPIC_ERR_CANCELLED and rq["steps"] == 0 and "before admission" in rq["message"]
+    ra = sv.wait(t_active)
+    assert ra["status"] == cpic.CPIC_ERR_CANCELLED and 0 < ra["steps"] < 4000 and "cancelled after" in ra["message"]
+    rafter = sv.wait(t_after)
+    assert rafter["status"] == 0 and rafter["message"] == ""
+    assert sv.cancel(t_after) == cpic.CPIC_ERR_INVALID  # polled: the ticket is retired
+    t_done = sv.submit(_req(cpic, seed=53))
+    while sv.stats()["active"] + sv.stats()["queued"] > 0:
+        time.sleep(1e-3)
+    assert sv.cancel(t_done) == cpic.CPIC_ERR_STATE
+    assert sv.wait(t_done)["status"] == 0
+    assert sv.stats()["pool_free"] == int(1.5 * fp) // 256 * 256
+    ref = cpic.Server(hbm_budget=2 << 30, max_active=2)
+    _same(rafter, ref.wait(ref.submit(_req(cpic, seed=52))))
+    ref.stop()
+    sv.stop()
+
+
+def test_caller_arena_too_small_is_out_of_memory(cpic):
+    """Allocation failure without a GPU fault: a caller arena one byte short of the
+    footprint (or misaligned) is refused with CPIC_ERR_OOM before anything is launched."""
+    import ctypes
+
+    import torch
+
+    cfg = _cfg_of(cpic, _req(cpic))
+    need = cpic.Run.footprint(cfg)
+    buf = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    h = ctypes.c_void_p()
+    lib = cpic.load()
+    st = lib.cpic_create(ctypes.byref(cfg), ctypes.c_void_p(buf.data_ptr()), need - 1, None, ctypes.byref(h))
+    assert st == cpic.CPIC_ERR_OOM and b"arena" in lib.cpic_last_error()
+    st = lib.cpic_create(ctypes.byref(cfg), ctypes.c_void_p(buf.data_ptr() + 16), need, None, ctypes.byref(h))
+    assert st == cpic.CPIC_ERR_OOM
+    st = lib.cpic_create(ctypes.byref(cfg), ctypes.c_void_p(buf.data_ptr()), need, None, ctypes.byref(h))
+    assert st == cpic.CPIC_OK
+    assert lib.cpic_destroy(h) == cpic.CPIC_OK

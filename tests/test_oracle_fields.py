@@ -127,24 +127,26 @@ def test_node_weights_sum_exactly_and_approximate_b2(D):
         exact = np.ones(t.shape[1])
         for a in range(D):
             exact = exact * dep.b2(d[a] - m[a])
-        assert np.all(qm >= 0)
-        # per axis: offset quantised to 2^-12 (b2 moves by < 2^-12) and the weight rounded
-        # to 2^-B (error <= 2^-(B+1)), B = 12 in 2D and 8 in 3D
-        B = dep.QF // D
-        axis_err = 2.0 ** -12 + 2.0 ** -(B + 1)
-        assert np.max(np.abs(qm / 2.0 ** dep.QF - exact)) < D * axis_err
+        assert np.all(qm >= 0) and np.all(qm < 1 << dep.QF)
+        # per axis: the offset is quantised to the centre of its 2^-16 sub-interval (b2 has
+        # slope <= 1, so it moves by <= 2^-17) and the weight rounded to 2^-16 (error
+        # <= 2^-17, twice that for the centre); each product rounded to 2^-24 (the centre
+        # takes the other 3^D - 1 roundings)
+        axis_err = 2.0 ** -17 + 2.0 ** -16
+        assert np.max(np.abs(qm / 2.0 ** dep.QF - exact)) < D * axis_err + 3 ** D * 2.0 ** -25
 
 
 @pytest.mark.parametrize("D", [2, 3])
 def test_axis_weights_fixed_are_rounded_b2_and_sum_exactly(D):
-    """The B-bit per-axis weights are the nearest multiples of 2^-B of the exact b2 values
-    of the quantised offset (outer nodes), the centre takes the remainder, and each node
-    weight is the exact product (rational arithmetic)."""
+    """The 16-bit per-axis weights are the nearest multiples of 2^-16 of the exact b2
+    values of the quantised offset (outer nodes), the centre takes the remainder; every
+    node weight but the centre is the exact product rounded to 2^-24 (halves up), the
+    centre the remainder (rational arithmetic)."""
     rng = np.random.default_rng(40 + D)
     t = np.concatenate([np.array([0.0, 0.5, np.nextafter(np.float32(1), np.float32(0))], dtype=np.float32),
                         rng.random(200).astype(np.float32)])
-    B = dep.QF // D
-    w = dep.axis_weights_fixed(t, D)
+    B = dep.QB
+    w = dep.axis_weights_fixed(t)
     K = dep.QK
     for p in range(t.size):
         u = math.floor(Fraction(float(t[p])) * 2 ** K)
@@ -155,11 +157,21 @@ def test_axis_weights_fixed_are_rounded_b2_and_sum_exactly(D):
         assert int(w[0][p]) + int(w[1][p]) + int(w[2][p]) == 2 ** B
     tt = np.stack([t] * D)
     q = dep.node_weights(tt)
+    r = D * B - dep.QF
+    centre = (0,) * D
+    rest = np.zeros(t.size, dtype=object)
     for m, qm in q.items():
-        prod = np.ones(t.size, dtype=np.int64)
-        for a in range(D):
-            prod = prod * w[m[a] + 1]
-        assert np.array_equal(qm, prod)
+        if m == centre:
+            continue
+        for p in range(0, t.size, 17):
+            prod = Fraction(1)
+            for a in range(D):
+                prod *= int(w[m[a] + 1][p])
+            x = prod / 2 ** r
+            # round half up: the nearest integer, ties upwards
+            assert Fraction(int(qm[p])) - Fraction(1, 2) < x <= Fraction(int(qm[p])) + Fraction(1, 2)
+        rest = rest + qm.astype(object)
+    assert np.array_equal(q[centre].astype(object), (1 << dep.QF) - rest)
 
 
 @pytest.mark.parametrize("D", [2, 3])
@@ -176,7 +188,7 @@ def test_deposit_conserves_charge_exactly(D):
     assert C.dtype == np.int64 and int(C.sum()) == npart << dep.QF
     E = dep.deposit_exact(idx, t, n, periodic)
     assert abs(E.sum() - npart) < 1e-9
-    assert np.max(np.abs(C / 2.0 ** dep.QF - E)) < npart * 2.0 ** -10
+    assert np.max(np.abs(C / 2.0 ** dep.QF - E)) < npart * 2.0 ** -14
 
 
 def test_deposit_uniform_grid_textbook_tsc():
@@ -191,3 +203,39 @@ def test_deposit_uniform_grid_textbook_tsc():
     for a, b in itertools.product(range(3), range(3)):
         ref[2 + b - 1, 3 + a - 1] = w[0][a] * w[1][b]
     np.testing.assert_allclose(E, ref, atol=1e-15)
+
+
+def _potential_error_of_quantisation(w):
+    """Relative L2 difference of the potentials solved from the spec-Q deposit and from the
+    unquantised FP64 deposit of the same particles (the solve is linear, so the difference
+    is the solve of the charge difference with homogeneous boundary values)."""
+    per = [w.field_bc[2 * a] == P for a in range(w.dim)]
+    g = geometry.build_geometry(w.vertices, per)
+    M, bbc = poisson.assemble(g, w.field_bc, w.field_bc_value)
+    M0, b0 = poisson.assemble(g, w.field_bc, [0.0] * len(w.field_bc_value))
+    dQ = np.zeros(g.Jc.shape)
+    Qe = w.background * g.Jc
+    for sp, ps in zip(w.species, w.particles):
+        idx = wl.unpack_cells(ps.cell, w.dim)
+        Cf = dep.deposit_fixed(idx, ps.t, w.n, per)
+        Ce = dep.deposit_exact(idx, ps.t.astype(np.float64), w.n, per)
+        dQ += sp.q * sp.w * (np.ldexp(Cf.astype(np.float64), -dep.QF) - Ce)
+        Qe += sp.q * sp.w * Ce
+    phi = poisson.solve(g, M, bbc, Qe, w.field_bc)
+    dphi = poisson.solve(g, M0, b0, dQ, w.field_bc)
+    return np.linalg.norm(dphi) / np.linalg.norm(phi)
+
+
+@pytest.mark.parametrize("case", ["cylinder_128x256_4M", "shell_24x24x24_414k"])
+def test_quantised_deposit_potential_within_fp32_state_tolerance(case):
+    """Spec Q's effect on the field: at the cylinder configuration's full size (128 x 256,
+    2M + 2M particles) and on a 3D shell with the sphere configuration's particles per cell
+    (about 30), the potential solved from the fixed-point deposit is within 1e-5 relative
+    L2 (the single-step FP32 state tolerance) of the one solved from the exact FP64 b2
+    deposit of the same particles."""
+    if case.startswith("cylinder"):
+        w = wl.cylinder(n1=128, n2=256, npart_per_species=2_000_000, seed=1, inject=False)
+    else:
+        w = wl.sphere(24, 24, 24, npart_per_species=207_000, seed=2)
+    err = _potential_error_of_quantisation(w)
+    assert err <= 1e-5, err

@@ -90,6 +90,41 @@ def test_charge_conservation_every_step_fp32_path():
 
 # ------------------------------------------------------------------ Philox and injection
 
+def test_philox_known_answer_vectors():
+    """Philox4x32-10 reproduces the generator's published known-answer vectors (golden file,
+    cited there): a swapped word, a wrong multiplier or key schedule fails this."""
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = philox.philox4x32_10(np.array([v[0:4]], np.uint32), np.array([v[4:6]], np.uint32))
+        assert [int(x) for x in out[0]] == v[6:10]
+
+
+def test_thermal_flux_rate_by_brute_force_crossing_count():
+    """Spec I's injection rate n vth / sqrt(2 pi) A dt / w is the one-sided Maxwellian flux:
+    brute force on a box of uniform Maxwellian plasma (density n, thermal speed vth) next
+    to a plane: the macro-particles that cross the plane within dt (x + vx dt > 0 from
+    x < 0) number rate_per_step within 4 sigma of Poisson counting; a wrong constant (1/2,
+    1/sqrt(pi), 1/4 of the mean speed's flux ...) differs by more than 10%."""
+    rng = np.random.default_rng(21)
+    vth, dt, dens, A = 1.7, 0.05, 3.0, 2.5
+    L = 8.0 * vth * dt  # deeper than any particle can travel in dt (8 sigma)
+    npart = 4_000_000
+    w = dens * L * A / npart  # physical particles per macro-particle
+    crossed = 0
+    for _ in range(4):
+        x = -L * rng.random(npart)
+        vx = vth * rng.standard_normal(npart)
+        crossed += int(np.sum(x + vx * dt > 0.0))
+    expected = 4 * inject.rate_per_step(dens, vth, A, dt, w)
+    assert abs(crossed - expected) < 4.0 * math.sqrt(expected), (crossed, expected)
+    assert expected > 1e5
+
+
 def test_philox_uniformity_and_stream_independence():
     """Statistical pins of the counter-based generator: uniform (chi^2 over 64 bins),
     distinct keys and counters give uncorrelated streams."""

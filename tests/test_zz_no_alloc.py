@@ -20,11 +20,24 @@ pytestmark = pytest.mark.gpu
 
 
 def _records(cell, t, v):
-    return np.sort(np.rec.fromarrays([cell, t[0], t[1], v[0], v[1], v[2]]))
+    return np.sort(np.rec.fromarrays([cell, *t, v[0], v[1], v[2]]))
 
 
-def _key(cell, n1):
-    return (cell & 0xFFFF).astype(np.int64) + n1 * (cell >> 16).astype(np.int64)
+def _key(cell, n):
+    idx = wl.unpack_cells(cell, len(n))
+    key = np.zeros(cell.shape, np.int64)
+    for a in reversed(range(len(n))):
+        key = key * n[a] + idx[a]
+    return key
+
+
+def _valid(cell, n):
+    """Slots in the grid: live (cell >= 0) with every axis index below its cell count."""
+    idx = wl.unpack_cells(cell, len(n))
+    ok = cell >= 0
+    for a in range(len(n)):
+        ok &= idx[a] < n[a]
+    return ok
 
 
 def _run_sort(cpic, w, s):
@@ -38,7 +51,7 @@ def _run_sort(cpic, w, s):
 def _noalloc_sort(cpic, ps, n):
     import torch
 
-    D, cnt = 2, ps.n
+    D, cnt = len(n), ps.n
     dev = torch.device("cuda")
     cin = torch.from_numpy(ps.cell).to(dev)
     tin = torch.from_numpy(np.ascontiguousarray(ps.t).reshape(-1)).to(dev)
@@ -47,7 +60,7 @@ def _noalloc_sort(cpic, ps, n):
     tout = torch.empty_like(tin)
     vout = torch.empty_like(vin)
     live = torch.zeros(1, dtype=torch.int64, device=dev)
-    nn = (ctypes.c_int32 * 3)(n[0], n[1], 1)
+    nn = (ctypes.c_int32 * 3)(n[0], n[1], n[2] if D == 3 else 1)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     cpic.check(cpic.load().cpic_sort_cells_noalloc(D, ctypes.cast(nn, ctypes.c_void_p), cnt, cpic._ptr(cin),
                                                    cpic._ptr(tin), cpic._ptr(vin), cpic._ptr(cout), cpic._ptr(tout),
@@ -61,21 +74,26 @@ def _noalloc_sort(cpic, ps, n):
 
 
 def test_noalloc_sort_matches_run_sort_on_two_calls(cpic):
-    """Two calls in a row (different particle sets, the second on a smaller grid), each
-    compared with the run-based sort of the same input: equal live counts, non-decreasing
-    cell keys, identical particle sets (bit for bit)."""
+    """Three calls in a row (different particle sets: a 2D grid, a smaller 2D grid, a 3D
+    grid), each compared with the run-based sort of the same input: equal live counts,
+    non-decreasing cell keys, identical particle sets (bit for bit). Dead slots and, in 3D,
+    packed cells beyond the grid's last plane are dropped by both (the run drops the latter
+    when it loads them)."""
     cases = [
         wl.cylinder(n1=64, n2=128, npart_per_species=150_001, seed=21, inject=False),
         wl.cylinder(n1=32, n2=64, npart_per_species=70_007, seed=22, inject=False),
+        wl.sphere(24, 20, 16, npart_per_species=60_013, seed=23),
     ]
     for w in cases:
         ps = w.particles[0]
         # dead slots in the input are dropped by both sorts
         ps.cell[::97] = -1
+        if w.dim == 3:  # plane index n3 (inside the 10-bit field, outside the grid)
+            ps.cell[5::101] = (ps.cell[5::101] & 0xFFFFF) | (w.n[2] << 20)
         ref = _run_sort(cpic, w, 0)
         got = _noalloc_sort(cpic, ps, w.n)
-        assert got[0].shape == ref[0].shape == (int(np.sum(ps.cell >= 0)),)
-        assert np.all(np.diff(_key(got[0], w.n[0])) >= 0)
+        assert got[0].shape == ref[0].shape == (int(np.sum(_valid(ps.cell, w.n))),)
+        assert np.all(np.diff(_key(got[0], w.n)) >= 0)
         assert np.array_equal(_records(*got), _records(*ref))
 
 
