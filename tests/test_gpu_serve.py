@@ -135,7 +135,10 @@ def test_cancel_queued_and_active_requests(cpic):
     assert rafter["status"] == 0 and rafter["message"] == ""
     assert sv.cancel(t_after) == cpic.CPIC_ERR_INVALID  # polled: the ticket is retired
     t_done = sv.submit(_req(cpic, seed=53))
-    while sv.stats()["active"] + sv.stats()["queued"] > 0:
+    while True:  # one snapshot per test (two calls could straddle the admission)
+        st = sv.stats()
+        if st["active"] + st["queued"] == 0:
+            break
         time.sleep(1e-3)
     assert sv.cancel(t_done) == cpic.CPIC_ERR_STATE
     assert sv.wait(t_done)["status"] == 0
