@@ -144,3 +144,20 @@ def deposit_exact(idx: np.ndarray, t: np.ndarray, n, periodic) -> np.ndarray:
             lin = lin * n[a] + c
         np.add.at(C, lin, w)
     return C.reshape(tuple(reversed(n)))
+
+
+def deposit_exact_c(idx: np.ndarray, t: np.ndarray, n, periodic, threads: int = 1) -> np.ndarray:
+    """deposit_exact as C loops (oracle/pic64.c); with threads > 1 each thread deposits a
+    contiguous block of particles into its own grid, added in thread order."""
+    from .mover import _lib64, _ptr
+
+    D = len(n)
+    C = np.zeros(int(np.prod(n)), dtype=np.float64)
+    idx_c = np.ascontiguousarray(idx, dtype=np.int64)
+    t_c = np.ascontiguousarray(t, dtype=np.float64)
+    nn = np.asarray(list(n) + [1] * (3 - D), dtype=np.int32)
+    per = np.asarray(list(periodic) + [0] * (3 - D), dtype=np.int32)
+    if _lib64().oracle_deposit64(D, _ptr(nn), _ptr(per), idx_c.shape[1], _ptr(idx_c), _ptr(t_c), _ptr(C),
+                                 int(threads)) != 0:
+        raise MemoryError("oracle_deposit64: per-thread grids")
+    return C.reshape(tuple(reversed(n)))

@@ -202,3 +202,58 @@ def kick32(idx, t32, v32, k32, G32, n, coef):
     _lib().replay_kick(D, _ptr(nn), idx.shape[1], _ptr(idx_c), _ptr(t_c), _ptr(v_c), _ptr(K), _ptr(G),
                        np.float32(coef))
     return v_c
+
+
+# ---------------------------------------------------------------------------------------
+# FP64 mover as C loops (oracle/pic64.c): the same definition as push64
+# ---------------------------------------------------------------------------------------
+
+_LIB64 = None
+
+
+def _lib64():
+    global _LIB64
+    if _LIB64 is None:
+        from .build import build_pic64
+
+        lib = ctypes.CDLL(build_pic64())
+        P = ctypes.c_void_p
+        lib.oracle_push64.argtypes = [ctypes.c_int, P, P, ctypes.c_long, P, P, P, P, P, ctypes.c_double,
+                                      ctypes.c_double, P, P, ctypes.c_int]
+        lib.oracle_push64.restype = None
+        lib.oracle_deposit64.argtypes = [ctypes.c_int, P, P, ctypes.c_long, P, P, P, ctypes.c_int]
+        lib.oracle_deposit64.restype = ctypes.c_int
+        lib.oracle_openmp_threads.argtypes = []
+        lib.oracle_openmp_threads.restype = ctypes.c_int
+        _LIB64 = lib
+    return _LIB64
+
+
+def openmp_threads():
+    """Threads the C loops can use (1 when built without OpenMP)."""
+    return int(_lib64().oracle_openmp_threads())
+
+
+def push64_c(idx, t, v, k, G, dt, qm, n, pbc, threads=1, inplace=False):
+    """push64 as C loops. qm is a scalar. Returns (idx, t, v, face, vdot) with vdot the
+    per-particle v^{n-1/2} . v^{n+1/2} (kicked velocity, before any reflection). With
+    inplace, idx (int64), t and v (float64), C-contiguous, are updated and returned."""
+    D = idx.shape[0]
+    np_ = idx.shape[1]
+    if inplace:
+        idx_c, t_c, v_c = idx, t, v
+        assert idx_c.dtype == np.int64 and t_c.dtype == np.float64 and v_c.dtype == np.float64
+        assert idx_c.flags.c_contiguous and t_c.flags.c_contiguous and v_c.flags.c_contiguous
+    else:
+        idx_c = np.array(idx, dtype=np.int64, order="C")
+        t_c = np.array(t, dtype=np.float64, order="C")
+        v_c = np.array(v, dtype=np.float64, order="C")
+    K = np.ascontiguousarray(k, dtype=np.float64).reshape(-1)
+    Gc = np.ascontiguousarray(G, dtype=np.float64).reshape(-1)
+    nn = np.asarray(list(n) + [1] * (3 - D), dtype=np.int32)
+    pb = np.asarray(list(pbc) + [0] * (6 - len(pbc)), dtype=np.int32)
+    face = np.empty(np_, dtype=np.int32)
+    vdot = np.empty(np_, dtype=np.float64)
+    _lib64().oracle_push64(D, _ptr(nn), _ptr(pb), np_, _ptr(idx_c), _ptr(t_c), _ptr(v_c), _ptr(K), _ptr(Gc),
+                           float(dt), float(qm), _ptr(face), _ptr(vdot), int(threads))
+    return idx_c, t_c, v_c, face.astype(np.int64), vdot

@@ -13,7 +13,11 @@ Start-up: deposit and solve at xi^0, then v^{-1/2} = v^0 - dt/2 (q/m) E(xi^0).
 Two precisions: "fp64" uses the FP64 mover and the exact FP64 b2 deposit; "fp32" replays
 the FP32 operation sequence of spec R with FP32 tables and the fixed-point deposit of
 spec Q (the results a GPU implementation of the same specs must reproduce bit for bit
-given the same potential).
+given the same potential). The FP64 mover and deposit run either as numpy array
+operations (engine "numpy") or as the same definitions in C loops (engine "c",
+oracle/pic64.c, optionally on several OpenMP threads), for long runs. The direct solve's
+factorisation is kept for the run.
+W_K uses the kicked velocity v^{n+1/2} (before any specular reflection), as spec D reads.
 """
 from __future__ import annotations
 
@@ -49,8 +53,10 @@ class SpeciesState:
 
 
 class OraclePIC:
-    def __init__(self, wl, precision: str = "fp64"):
+    def __init__(self, wl, precision: str = "fp64", engine: str = "numpy", threads: int = 1):
         self.wl = wl
+        self.engine = engine
+        self.threads = threads
         self.D = wl.dim
         self.n = tuple(wl.n)
         self.precision = precision
@@ -61,6 +67,7 @@ class OraclePIC:
         self.periodic = periodic
         self.geom = build_geometry(wl.vertices, periodic, axisym=wl.omega_axisym)
         self.M, self.bbc = poisson.assemble(self.geom, self.bc, self.bcval)
+        self.solver = poisson.DirectSolver(self.geom, self.M, self.bbc, self.bc)
         self.dt = wl.dt
         self.step_index = 0
         self.species = []
@@ -75,6 +82,7 @@ class OraclePIC:
         self.phi = np.zeros(self.geom.Jc.shape)
         self.history = []
         self.injected = [0] * len(self.species)
+        self._face_area = {}
 
     # ---- steps ---------------------------------------------------------------------
     def charge(self):
@@ -82,7 +90,10 @@ class OraclePIC:
         Q = self.wl.background * self.geom.Jc
         for sp in self.species:
             if self.precision == "fp64":
-                C = dep.deposit_exact(sp.idx, sp.t, self.n, self.periodic)
+                if self.engine == "c":
+                    C = dep.deposit_exact_c(sp.idx, sp.t, self.n, self.periodic, self.threads)
+                else:
+                    C = dep.deposit_exact(sp.idx, sp.t, self.n, self.periodic)
                 Q = Q + (sp.q * sp.w) * C
             else:
                 C = dep.deposit_fixed(sp.idx, sp.t, self.n, self.periodic)
@@ -91,7 +102,7 @@ class OraclePIC:
 
     def solve(self):
         self.Q = self.charge()
-        self.phi = poisson.solve(self.geom, self.M, self.bbc, self.Q, self.bc)
+        self.phi = self.solver(self.Q)
         return self.phi
 
     def field_tables(self):
@@ -118,26 +129,37 @@ class OraclePIC:
         ke = []
         for s, sp in enumerate(self.species):
             qm = sp.q / sp.m
-            if self.precision == "fp64":
+            if self.precision == "fp64" and self.engine == "c":
+                sp.idx = np.ascontiguousarray(sp.idx, dtype=np.int64)
+                sp.t = np.ascontiguousarray(sp.t, dtype=np.float64)
+                sp.v = np.ascontiguousarray(sp.v, dtype=np.float64)
+                idx, t, v, face, vdot = mover.push64_c(sp.idx, sp.t, sp.v, k, G, self.dt, qm, self.n, self.pbc,
+                                                       self.threads, inplace=True)
+                ke.append(0.5 * sp.m * sp.w * float(np.sum(vdot)))
+            elif self.precision == "fp64":
                 vold = sp.v
-                idx, t, v, face = mover.push64(sp.idx, sp.t, sp.v, k, G, self.dt, qm, self.n, self.pbc)
-                ke.append(0.5 * sp.m * sp.w * float(np.sum(vold * v)))
+                idx, t, v, face, vk = mover.push64(sp.idx, sp.t, sp.v, k, G, self.dt, qm, self.n, self.pbc,
+                                                   return_kicked=True)
+                ke.append(0.5 * sp.m * sp.w * float(np.sum(vold * vk)))
             else:
                 idx, t, v, face, kefp = mover.push32(
                     sp.idx, sp.t, sp.v, k, G, self.n, self.pbc,
                     np.float32(self.dt * qm), np.float32(0.5 * self.dt), np.float32(self.dt))
                 ke.append(0.5 * sp.m * sp.w * float(np.ldexp(float(kefp.sum()), -24)))
             alive = face < 0
-            for f in range(2 * self.D):
-                sp.absorbed[f] += int(np.sum(face == f))
-            sp.idx, sp.t, sp.v = idx[:, alive].astype(np.int64), t[:, alive], v[:, alive]
+            if np.all(alive):
+                sp.idx, sp.t, sp.v = idx.astype(np.int64, copy=False), t, v
+                continue
+            sp.absorbed += np.bincount(face[~alive], minlength=2 * self.D)[: 2 * self.D]
+            sp.idx = np.compress(alive, idx, axis=1).astype(np.int64, copy=False)
+            sp.t, sp.v = np.compress(alive, t, axis=1), np.compress(alive, v, axis=1)
         for (s, face, dens, vth, seed) in self.injection:
             sp = self.species[s]
             side = face % 2
-            if self.D == 2:
-                area = inject.face_length_2d(self.geom.X, side)
-            else:
-                area = inject.face_area_3d(self.geom.X, side)
+            if side not in self._face_area:
+                self._face_area[side] = (inject.face_length_2d(self.geom.X, side) if self.D == 2
+                                         else inject.face_area_3d(self.geom.X, side))
+            area = self._face_area[side]
             rate = inject.rate_per_step(dens, vth, area, self.dt, sp.w)
             cnt = inject.count_at_step(rate, self.step_index)
             if cnt == 0:

@@ -175,6 +175,31 @@ def solve(geom, M, bbc, Q, bc):
     return phi.reshape(geom.Jc.shape)
 
 
+class DirectSolver:
+    """solve() with the sparse LU factorisation (scipy SuperLU, a library primitive) kept
+    between calls: the operator of a run does not change, only the charge does."""
+
+    def __init__(self, geom, M, bbc, bc):
+        self.geom, self.bbc, self.bc = geom, bbc, bc
+        self.singular = is_singular(bc, geom.dim)
+        self.J = geom.Jc.ravel(order="C")
+        if self.singular:
+            N = self.J.size
+            Jcol = sp.csr_matrix(self.J.reshape(N, 1))
+            self.lu = spla.splu(sp.bmat([[M, Jcol], [Jcol.T, None]], format="csc"))
+        else:
+            self.lu = spla.splu(M.tocsc())
+
+    def __call__(self, Q):
+        rhs = (self.geom.omega_c * Q).ravel(order="C") + self.bbc
+        if self.singular:
+            rhs = rhs - (rhs.sum() / self.J.sum()) * self.J
+            phi = self.lu.solve(np.concatenate([rhs, [0.0]]))[: rhs.size]
+        else:
+            phi = self.lu.solve(rhs)
+        return phi.reshape(self.geom.Jc.shape)
+
+
 def residual_norm(M, bbc, geom, Q, phi, bc):
     """Relative residual ||rhs - M phi|| / ||rhs|| (with the singular-case projection)."""
     rhs = (geom.omega_c * Q).ravel() + bbc

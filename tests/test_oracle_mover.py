@@ -230,3 +230,45 @@ def test_reflection_on_a_curved_cap_keeps_speed_and_flips_the_normal():
     # the component along grad(eta) was negative (towards the cap) and is now positive
     assert np.all(np.sum(vk.T * kp[:, 1, :], axis=1) < 0)
     assert np.all(np.sum(v1.T * kp[:, 1, :], axis=1)[hit] > 0)
+
+
+@pytest.mark.parametrize("case", ["map2", "cylinder", "box_reflect", "sphere3d"])
+def test_c_loop_mover_and_deposit_equal_the_numpy_forms(case):
+    """oracle/pic64.c restates push64 and deposit_exact as loops (for long runs): the push
+    is bit-identical to the numpy form (same operation order: positions, faces, velocities
+    and the v.v products), also on several threads, including absorption, reflection and
+    3D; the deposit agrees to FP64 rounding of the summation order. The pins of the numpy
+    forms (uniform-map limit, reversibility, second order, elastic walls) therefore hold for
+    the C loops too."""
+    from oracle import deposit as dep
+    from oracle import geometry, gradient
+    from paper_1311_2286_gb300 import workloads as wl
+
+    w = {"map2": lambda: wl.langmuir_map2(32, 32, eps=0.1, ppc=20, vth=0.3, seed=1),
+         "cylinder": lambda: wl.cylinder(32, 64, npart_per_species=50_000, seed=2, inject=False),
+         "box_reflect": lambda: wl.box_reflect(16, 16, 20_000, vth=2.0),
+         "sphere3d": lambda: wl.sphere(12, 10, 8, npart_per_species=20_000, seed=3)}[case]()
+    per = [w.field_bc[2 * a] == 0 for a in range(w.dim)]
+    g = geometry.build_geometry(w.vertices, per)
+    phi = wl.random_field(np.random.default_rng(0), tuple(reversed(w.n)), 0.5)
+    if case in ("cylinder", "sphere3d"):
+        phi = phi + np.linspace(-5, 0, w.n[0])
+    G = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value)
+    ps = w.particles[0]
+    idx = wl.unpack_cells(ps.cell, w.dim)
+    t, v = ps.t.astype(np.float64), ps.v.astype(np.float64)
+    a = mover.push64(idx, t, v, g.k, G, w.dt, -1.0, w.n, w.particle_bc, return_kicked=True)
+    for threads in (1, 3):
+        b = mover.push64_c(idx, t, v, g.k, G, w.dt, -1.0, w.n, w.particle_bc, threads=threads)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[3], b[3])
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+        assert np.array_equal(np.sum(a[4] * v, axis=0), b[4])
+    if case in ("cylinder", "sphere3d"):
+        assert np.any(a[3] >= 0)  # the case removes particles
+    if case in ("box_reflect", "sphere3d"):
+        assert np.any(np.any(a[2] != a[4], axis=0) & (a[3] < 0))  # and reflects some
+    alive = a[3] < 0
+    e1 = dep.deposit_exact(a[0][:, alive], a[1][:, alive], w.n, per)
+    for threads in (1, 4):
+        e2 = dep.deposit_exact_c(a[0][:, alive], a[1][:, alive], w.n, per, threads=threads)
+        assert np.max(np.abs(e1 - e2)) <= 1e-12 * np.max(np.abs(e1))

@@ -292,3 +292,20 @@ def test_map2_manufactured_second_order():
         ex = ex - np.sum(ex * g.Jc) / np.sum(g.Jc)
         errs.append(np.max(np.abs(phi - ex)))
     assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.6
+
+
+@pytest.mark.parametrize("case", ["periodic", "dirichlet"])
+def test_factorised_solver_equals_direct_solve(case):
+    """poisson.DirectSolver (the sparse LU kept for a run) gives solve()'s potential."""
+    rng = np.random.default_rng(17)
+    if case == "periodic":
+        X, bc, bv, per = wl.map2_vertices(24, 16, 0.08), [P] * 4, [0.0] * 4, [True, True]
+    else:
+        X, bc, bv, per = wl.annulus_vertices(16, 32, 1.0, 10.0), [Dr, Dr, P, P], [-2.0, 0.5, 0, 0], [False, True]
+    g = geometry.build_geometry(X, per)
+    M, bbc = poisson.assemble(g, bc, bv)
+    S = poisson.DirectSolver(g, M, bbc, bc)
+    for _ in range(2):
+        Q = rng.standard_normal(g.Jc.shape)
+        ref = poisson.solve(g, M, bbc, Q, bc)
+        assert np.max(np.abs(S(Q) - ref)) <= 1e-12 * np.max(np.abs(ref))
