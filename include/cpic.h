@@ -162,12 +162,18 @@ int cpic_set_map_analytic(cpic_run* run, int map_id, const double* params, int n
 /* ---------------------------------------------------------------- particles */
 
 /* Replace species sp's particles (Sec. III.B: initial load). cell, t, v: host or device,
- * particle format above, n <= capacity. */
+ * particle format above, n <= capacity. Asynchronous on the run's stream when all three
+ * arrays are device, managed or page-locked host memory (the caller keeps them unchanged
+ * until the stream has passed the call); synchronises for pageable host memory. Slots
+ * outside the grid are dropped (counted in dropped[sp]). */
 int cpic_load_particles(cpic_run* run, int sp, int64_t n, const int32_t* cell, const float* t,
                         const float* v);
 /* Copy species sp's live particles out (synchronises). cell, t, v: host or device with room
  * for `room` particles; *n receives the count (CPIC_ERR_INVALID if room is too small). The
- * order is the storage order (cell-sorted after cpic_sort, unspecified within a cell). */
+ * order is the storage order (cell-sorted after cpic_sort, unspecified within a cell).
+ * Dead slots left by absorption since the last sort are compacted on the device (into the
+ * run's second particle buffer, which is free between sorts); then one copy per array goes
+ * straight into the caller's buffers. */
 int cpic_get_particles(cpic_run* run, int sp, int64_t room, int64_t* n, int32_t* cell, float* t,
                        float* v);
 /* Maxwellian flux injection through face `face` for species sp (Sec. III.A-B): density,

@@ -328,6 +328,79 @@ __global__ void validate_load_kernel(int D, int n0, int n1, int n2, int* cell, c
         }                                                       \
     } while (0)
 
+// Stable compaction of one species' live slots (cell >= 0) into the other particle buffer
+// (free between sorts), for cpic_get_particles: the slots are split into nb contiguous
+// ranges; pass 1 counts the live slots of each range, pass 2 turns the counts into
+// exclusive offsets, pass 3 writes each range's live particles in slot order.
+constexpr int COMPACT_BLOCKS = 1024;
+
+__global__ void compact_count_kernel(const int* cell, long long n, long long chunk, long long* counts) {
+    const long long lo = (long long)blockIdx.x * chunk, hi = min(lo + chunk, n);
+    int c = 0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) c += cell[i] >= 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    __shared__ int part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+__global__ void compact_offsets_kernel(long long* counts, int nb) {
+    if (threadIdx.x == 0) {  // nb <= 1024 partial counts: one sequential pass
+        long long acc = 0;
+        for (int b = 0; b < nb; ++b) {
+            const long long c = counts[b];
+            counts[b] = acc;
+            acc += c;
+        }
+        counts[nb] = acc;
+    }
+}
+
+__global__ void compact_scatter_kernel(int D, const int* cell, const float* t, const float* v, long long stride,
+                                       long long n, long long chunk, const long long* offsets, int* ocell, float* ot,
+                                       float* ov, long long ostride) {
+    const long long lo = (long long)blockIdx.x * chunk, hi = min(lo + chunk, n);
+    __shared__ int warp_tot[32];
+    long long dst0 = offsets[blockIdx.x];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (long long base = lo; base < hi; base += blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const bool live = i < hi && cell[i] >= 0;
+        const unsigned m = __ballot_sync(0xffffffffu, live);
+        if (lane == 0) warp_tot[wid] = __popc(m);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < nw; ++w) {
+            before += w < wid ? warp_tot[w] : 0;
+            total += warp_tot[w];
+        }
+        if (live) {
+            const long long d = dst0 + before + __popc(m & ((1u << lane) - 1u));
+            ocell[d] = cell[i];
+            for (int a = 0; a < D; ++a) ot[a * ostride + d] = t[a * stride + i];
+            for (int a = 0; a < 3; ++a) ov[a * ostride + d] = v[a * stride + i];
+        }
+        dst0 += total;
+        __syncthreads();
+    }
+}
+
+// true for device, managed and page-locked host memory (a copy from it may stay in flight
+// after the call returns); false for pageable host memory
+bool stream_ordered_source(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged || at.type == cudaMemoryTypeHost;
+}
+
 int after_map(cpic_run* r) {
     int st = launch_geometry(r);
     if (st) return st;
@@ -797,8 +870,10 @@ int cpic_load_particles(cpic_run* r, int sp, int64_t n, const int32_t* cell, con
                                                                  r->pb.t[b] + base, r->pb.v[b] + base, T, n, r->ctr, sp);
         CPIC_CHECK_LAUNCH();
     }
-    // the copies above may read pageable host memory the caller frees after returning
-    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    // copies from pageable host memory must be complete before the caller may free or reuse
+    // it; device and page-locked inputs stay stream-ordered (asynchronous)
+    if (n > 0 && !(stream_ordered_source(cell) && stream_ordered_source(t) && stream_ordered_source(v)))
+        CPIC_CUDA(cudaStreamSynchronize(r->stream));
     return CPIC_OK;
 }
 
@@ -821,20 +896,9 @@ int cpic_get_particles(cpic_run* r, int sp, int64_t room, int64_t* n, int32_t* c
     DevCounters h;
     CPIC_CUDA(cudaMemcpyAsync(&h, r->ctr, sizeof(h), cudaMemcpyDeviceToHost, r->stream));
     CPIC_CUDA(cudaStreamSynchronize(r->stream));
-    long long cnt = h.count[sp];
-    int b = h.cur;
-    long long base = r->pb.base[sp], T = r->pb.total;
-    std::vector<int> hc(cnt);
-    std::vector<float> ht((size_t)r->D * cnt), hv((size_t)3 * cnt);
-    if (cnt > 0) {
-        CPIC_CUDA(cudaMemcpy(hc.data(), r->pb.cell[b] + base, sizeof(int) * cnt, cudaMemcpyDeviceToHost));
-        for (int a = 0; a < r->D; ++a)
-            CPIC_CUDA(cudaMemcpy(ht.data() + a * cnt, r->pb.t[b] + a * T + base, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
-        for (int a = 0; a < 3; ++a)
-            CPIC_CUDA(cudaMemcpy(hv.data() + a * cnt, r->pb.v[b] + a * T + base, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
-    }
-    long long live = 0;
-    for (long long i = 0; i < cnt; ++i) live += hc[i] >= 0;
+    const long long cnt = h.count[sp], live = h.alive[sp];
+    const int b = h.cur;
+    const long long base = r->pb.base[sp], T = r->pb.total;
     *n = live;
     if (live > room) {
         set_error("get_particles: room %lld < %lld live particles", (long long)room, live);
@@ -845,19 +909,41 @@ int cpic_get_particles(cpic_run* r, int sp, int64_t room, int64_t* n, int32_t* c
         set_error("get_particles: NULL output array");
         return CPIC_ERR_INVALID;
     }
-    std::vector<int> oc(live);
-    std::vector<float> ot((size_t)r->D * live), ov((size_t)3 * live);
-    long long k = 0;
-    for (long long i = 0; i < cnt; ++i) {
-        if (hc[i] < 0) continue;
-        oc[k] = hc[i];
-        for (int a = 0; a < r->D; ++a) ot[a * live + k] = ht[a * cnt + i];
-        for (int a = 0; a < 3; ++a) ov[a * live + k] = hv[a * cnt + i];
-        ++k;
+    const int* src_c = r->pb.cell[b] + base;
+    const float* src_t = r->pb.t[b] + base;
+    const float* src_v = r->pb.v[b] + base;
+    long long stride = T;
+    if (live < cnt) {  // dead slots since the last sort: compact on the device first
+        const int o = 1 - b;
+        long long chunk = (cnt + COMPACT_BLOCKS - 1) / COMPACT_BLOCKS;
+        if (chunk < 1024) chunk = 1024;
+        const int nb = (int)((cnt + chunk - 1) / chunk);
+        compact_count_kernel<<<nb, 256, 0, r->stream>>>(src_c, cnt, chunk, r->scan_blocks);
+        CPIC_CHECK_LAUNCH();
+        compact_offsets_kernel<<<1, 32, 0, r->stream>>>(r->scan_blocks, nb);
+        CPIC_CHECK_LAUNCH();
+        compact_scatter_kernel<<<nb, 256, 0, r->stream>>>(r->D, src_c, src_t, src_v, T, cnt, chunk, r->scan_blocks,
+                                                         r->pb.cell[o] + base, r->pb.t[o] + base, r->pb.v[o] + base,
+                                                         T);
+        CPIC_CHECK_LAUNCH();
+        src_c = r->pb.cell[o] + base;
+        src_t = r->pb.t[o] + base;
+        src_v = r->pb.v[o] + base;
+        long long got = 0;  // the compaction's own count must be the live counter
+        CPIC_CUDA(cudaMemcpyAsync(&got, r->scan_blocks + nb, sizeof(got), cudaMemcpyDeviceToHost, r->stream));
+        CPIC_CUDA(cudaStreamSynchronize(r->stream));
+        if (got != live) {
+            set_error("get_particles: %lld live slots but the live counter is %lld", got, live);
+            return CPIC_ERR_STATE;
+        }
     }
-    CPIC_CUDA(cudaMemcpy(cell, oc.data(), sizeof(int) * live, cudaMemcpyDefault));
-    CPIC_CUDA(cudaMemcpy(t, ot.data(), sizeof(float) * ot.size(), cudaMemcpyDefault));
-    CPIC_CUDA(cudaMemcpy(v, ov.data(), sizeof(float) * ov.size(), cudaMemcpyDefault));
+    // one copy per array into the caller's buffers (host or device)
+    CPIC_CUDA(cudaMemcpyAsync(cell, src_c, sizeof(int) * live, cudaMemcpyDefault, r->stream));
+    for (int a = 0; a < r->D; ++a)
+        CPIC_CUDA(cudaMemcpyAsync(t + a * live, src_t + a * stride, sizeof(float) * live, cudaMemcpyDefault, r->stream));
+    for (int a = 0; a < 3; ++a)
+        CPIC_CUDA(cudaMemcpyAsync(v + a * live, src_v + a * stride, sizeof(float) * live, cudaMemcpyDefault, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
     return CPIC_OK;
 }
 

@@ -120,6 +120,8 @@ def test_langmuir_cycle_matches_oracle(cpic):
     assert err1[0] <= 1e-5 and err1[1] <= 1e-5, err1
     np.testing.assert_allclose(we, we_chk, rtol=1e-12)
     assert abs(we.mean() / we_ora.mean() - 1.0) <= 0.01, (we.mean(), we_ora.mean())
+    print("langmuir cycle: errors start-up %s step 1 %s; W_E mean device %.6e oracle %.6e"
+          % (err0, err1, we.mean(), we_ora.mean()))
     wk_dev = np.array([run.diag()["W_K"]])
     assert abs(wk_dev[0] / pic.history[-1]["W_K"] - 1.0) <= 0.01
     run.close()
@@ -143,6 +145,9 @@ def test_cylinder_cycle_matches_oracle(cpic, record_property):
     report = []
     _current_check(dev_abs, ora_abs, w, 1, CYL_STEPS, report)
     record_property("currents", report)
+    print("cylinder cycle: W_E mean device %.6e oracle %.6e" % (we.mean(), we_ora.mean()))
+    for r in report:
+        print("cylinder cycle current:", r)
     assert any(r["species"] == 1 and r["face"] == 0 and r["device"] > 0 for r in report)  # ions collected
     run.close()
 
@@ -243,4 +248,7 @@ def test_served_request_matches_oracle(cpic):
     assert abs(we.mean() / we_ora.mean() - 1.0) <= 0.01, (we.mean(), we_ora.mean())
     report = []
     _current_check(dev_abs, ora_abs, w, 1, steps, report)
+    print("served cycle: W_E mean device %.6e oracle %.6e" % (we.mean(), we_ora.mean()))
+    for r in report:
+        print("served cycle current:", r)
     run.close()

@@ -143,7 +143,7 @@ def test_cancel_queued_and_active_requests(cpic):
     assert sv.cancel(t_done) == cpic.CPIC_ERR_STATE
     assert sv.wait(t_done)["status"] == 0
     assert sv.stats()["pool_free"] == int(1.5 * fp) // 256 * 256
-    ref = cpic.Server(hbm_budget=2 << 30, max_active=2)
+    ref = cpic.Server(hbm_budget=2 << 30, max_active=2, steps_per_slice=5)
     _same(rafter, ref.wait(ref.submit(_req(cpic, seed=52))))
     ref.stop()
     sv.stop()

@@ -213,3 +213,57 @@ def test_inject_3d_flux_statistics():
     assert abs(np.mean(vn) / (vth * math.sqrt(math.pi / 2)) - 1) < 0.02
     vt = v32.T.astype(float) + vn[:, None] * rhat
     assert abs(np.mean(np.sum(vt * vt, axis=1)) / (2 * vth**2) - 1) < 0.03
+
+
+# ------------------------------------------------------------------ P7: OML currents
+
+def _oml_run(phi_obj, mass_ratio, steps, window, npart=100_000, seed=31):
+    """Oracle run of the biased cylinder (annulus r = 10^xi around a cylinder of radius 1
+    Debye length, 32 x 64 cells, object held at phi_obj and absorbing, Maxwellian flux
+    injection of both species at r = 10, T_i = T_e); time-averaged collected current per
+    unit length of each species over the last `window` steps, in units of the OML value."""
+    from scipy.special import erfc
+
+    w = wl.cylinder(n1=32, n2=64, r0=1.0, R=10.0, npart_per_species=npart, phi_obj=phi_obj, seed=seed,
+                    inject=True, mass_ratio=mass_ratio)
+    import os
+
+    pic = OraclePIC(w, "fp64", engine="c", threads=max(1, len(os.sched_getaffinity(0))))
+    pic.initialize()
+    for _ in range(steps):
+        pic.step()
+    h = pic.history
+    out = {}
+    for s, sp in enumerate(w.species):
+        vth = 1.0 / math.sqrt(sp.m)
+        I0 = vth / math.sqrt(2.0 * math.pi) * 2.0 * math.pi * 1.0  # random current, n = |q| = r0 = 1
+        chi = -sp.q * phi_obj  # > 0: attracted
+        oml = I0 * (2.0 * math.sqrt(chi / math.pi) + math.exp(chi) * erfc(math.sqrt(chi))) if chi > 0 \
+            else I0 * math.exp(chi)
+        cnt = int(h[-1]["absorbed"][s][0]) - int(h[-1 - window]["absorbed"][s][0])
+        out[s] = (cnt * sp.w / (window * w.dt) / oml, cnt)
+    return out
+
+
+@pytest.mark.slow
+def test_oml_currents_to_a_biased_cylinder():
+    """P7 (Sec. III.B compares with orbit-motion-limited theory): the oracle's collected
+    currents to a cylinder of radius lambda_D biased to -5 kT/e are the OML values within
+    +-15% for the attracted ions, I0 [2 sqrt(chi/pi) + e^chi erfc(sqrt(chi))], and +-20% for
+    the repelled electrons, I0 e^-chi, with I0 = q n vth / sqrt(2 pi) 2 pi r0 the random
+    current. A wrong injection flux constant, a wrong absorption tally or a wrong charge
+    normalisation moves these by far more. The ions have m_i/m_e = 25 here (reading): OML
+    depends on the mass only through vth, and the lighter ions reach their steady sheath
+    within the run (with 1836 the ion current still falls through the run's length)."""
+    r = _oml_run(-5.0, 25.0, 1200, 600)
+    assert r[1][1] > 20_000 and abs(r[1][0] - 1.0) <= 0.15, r
+    assert r[0][1] > 200 and abs(r[0][0] - 1.0) <= 0.20, r
+
+
+@pytest.mark.slow
+def test_oml_current_of_attracted_electrons():
+    """P7 with the bias reversed (+2 kT/e): the attracted electrons' collected current is the
+    OML value I0 [2 sqrt(chi/pi) + e^chi erfc(sqrt(chi))] within +-15% (electrons reach
+    steady state within a few tens of plasma periods)."""
+    r = _oml_run(2.0, 1836.0, 600, 300)
+    assert r[0][1] > 20_000 and abs(r[0][0] - 1.0) <= 0.15, r
