@@ -1,27 +1,32 @@
 """Benchmark of the curvilinear PIC hot path on GB300 (one JSON line on rank 0).
 
-Workload (the 2D cylinder-in-plasma configuration): log-polar annulus r = (40)^xi around a
-cylinder of radius 1, 128 x 256 cells, 2M electrons + 2M ions (m_i/m_e = 1836,
-T_i = T_e) loaded uniform in physical space, object at -5 (Dirichlet, absorbing), outer
-boundary at 0 with Maxwellian flux injection, theta periodic, dt = 0.1, synthetic seeded
-inputs.
+Headline workload (value, roofline, e2e, cpu_baseline): the 3D sphere in plasma, the largest
+single-GPU configuration: shell map r = 30^xi around a sphere of radius 1, polar angle in
+[pi/32, pi - pi/32] (specular caps), periodic azimuth, 128^3 cells, 32M electrons + 32M
+ions (m_i/m_e = 1836, T_i = T_e) loaded on the device uniform in physical space (particles
+per cell ~ r^3 sin theta), object at -5 (Dirichlet, absorbing), outer boundary at 0 with
+Maxwellian flux injection of both species, dt = 0.1, synthetic seeded inputs.
 
 value: particle-steps/s of the mover with its grid coupling, the metric's "gather + push +
-deposit" (rows a2-a6, with a1 vertex field, a8 injection and the a7 cell sort every few
+deposit" (rows a2-a6, with the a1 vertex field, a8 injection and the a7 cell sort every few
 steps included): K particle steps with the field held fixed (cpic_step_particles, one CUDA
-graph replay per step), inputs resident in HBM, per-step CUDA events on the run's stream,
-L2 flushed (256 MB write) between timed steps (state is 96 MB < L2).
-full_cycle: the same workload stepped with the multigrid field solve (cpic_step, rtol
-1e-10), reported beside it.
-e2e: the value's metric through the public API with host buffers: each step loads the
-particle state from pinned host memory (cpic_load_particles), steps (cpic_step_particles),
-and reads the state and diagnostics back (cpic_get_particles, cpic_get_diag), copies
-inside the timed region.
-roofline: the fused push kernel alone (events around that kernel in a stream-ordered pass)
-against the measured HBM copy bandwidth, algorithmic bytes = 48 B per particle (state read
-once, written once).
---impl reference / cpu_baseline: the oracle (oracle/, plain FP64 CPU) timed on a bounded
-sample of the same workload with the same fixed-field particle steps.
+graph replay per step), inputs resident in HBM (1.8 GB of particle state, larger than the
+129 MB L2, which is flushed between steps all the same), per-step CUDA events on the run's
+stream. The full PIC cycle (with the FP64 multigrid solve) is reported beside it.
+roofline: the fused 3D push kernel alone (events around that kernel in a stream-ordered
+pass) against the measured HBM copy bandwidth, algorithmic bytes = 56 B per particle
+(state read once, written once).
+e2e: the same metric through the public API with host buffers: each step loads the particle
+state from pinned host memory (cpic_load_particles), steps (cpic_step_particles), and reads
+the state and the diagnostics back (cpic_get_particles, cpic_get_diag), copies inside the
+timed region.
+Beside the headline: the 2D cylinder in plasma at 128 x 256 cells and 2M + 2M particles
+(state 96 MB, inside L2) and the same map at 512 x 1024 cells with 32M + 32M particles
+(1.5 GB, the 2D HBM roofline run); the batched configuration (256 uneven cylinder runs);
+the served configuration (Poisson arrivals of cylinder and sphere requests, open loop and at
+about 70% of the measured capacity, with a sequential baseline).
+--impl reference / cpu_baseline: the oracle (oracle/, plain FP64 CPU, its mover and deposit
+as C loops on all allowed cores) timed on a bounded sample of the headline workload.
 """
 from __future__ import annotations
 
@@ -43,17 +48,21 @@ if ROOT not in sys.path:
 
 METRIC = "particle-steps/s (gather+push+deposit) & % HBM roofline; served p50/p99 latency"
 UNIT = "particle-steps/s"
-BYTES_PER_PARTICLE = 48  # 2D: (4 cell + 8 offsets + 12 velocity) read + written
-WORKLOAD = ("2D cylinder in plasma: annulus r=(40)^xi, 128x256 cells, 2M electrons + 2M ions "
-            "(m_i/m_e=1836, T_i=T_e), phi_obj=-5, Maxwellian flux injection at r=40, dt=0.1, "
-            "sort interval {S}, multigrid rtol 1e-10")
-KERNEL_SOURCES = ["paper_1311_2286_gb300/csrc/push2d.cu", "paper_1311_2286_gb300/csrc/particles.cuh"]
-KERNEL = "push2d_kernel<false,true> (fused gather/push/boundary/deposit, 2D)"
+B3, B2 = 56, 48  # algorithmic bytes per particle-step (state read once, written once)
+WORKLOAD = ("3D sphere in plasma: shell r=30^xi, theta in [pi/32, pi-pi/32] (specular caps), phi periodic, "
+            "128^3 cells, 32M electrons + 32M ions (m_i/m_e=1836, T_i=T_e) loaded on the device, phi_obj=-5, "
+            "Maxwellian flux injection of both species at r=30, dt=0.1, sort interval {S}, fixed-field particle "
+            "steps")
+SRC3 = ["paper_1311_2286_gb300/csrc/push3d.cu", "paper_1311_2286_gb300/csrc/particles.cuh"]
+SRC2 = ["paper_1311_2286_gb300/csrc/push2d.cu", "paper_1311_2286_gb300/csrc/particles.cuh"]
+PROFILE3 = "profiles/push3d_sphere_128cubed.md"
+PROFILE2 = "profiles/push2d_cylinder_512x1024_64M.md"
+PROFILE2_SMALL = "profiles/push2d_cylinder_128x256_4M.md"
 
 
-def kernel_hash():
+def sources_hash(files):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files:
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -65,44 +74,23 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
-def profiled_traffic_3d(particles):
-    """DRAM bytes of one 3D push of `particles` particles, scaled from the committed ncu
-    summary's bytes per particle (captured on a smaller 3D run), if it was taken on the
-    current kernel sources, else None."""
-    path = os.path.join(ROOT, "profiles", "push3d_sphere_128cubed_16M.md")
+def profiled_traffic(path, sources, particles):
+    """DRAM bytes (read + write) of one push launch over `particles` particles, from the
+    committed ncu summary's bytes per particle (captured on a smaller case of the same
+    kernel, traffic growing with the particle count), if the summary was taken on the
+    current kernel sources (matching hash), else None."""
+    path = os.path.join(ROOT, path)
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256()
-    for f in ["paper_1311_2286_gb300/csrc/push3d.cu", "paper_1311_2286_gb300/csrc/particles.cuh"]:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
     kv = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
             k, v = line[2:].split(":", 1)
             kv[k.strip()] = v.strip().split()[0] if v.strip() else ""
-    if kv.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
+    if kv.get("kernel_sources_sha256_16") != sources_hash(sources):
         return None
     try:
         return int(float(kv["dram_bytes_per_particle"]) * particles)
-    except (KeyError, ValueError):
-        return None
-
-
-def profiled_traffic():
-    """dram bytes per push launch from the committed ncu summary, if it was taken on the
-    current kernel sources (matching source hash), else None."""
-    path = os.path.join(ROOT, "profiles", "push2d_cylinder_128x256_4M.md")
-    if not os.path.exists(path):
-        return None
-    kv = {}
-    for line in open(path):
-        if ":" in line and line.startswith("- "):
-            k, v = line[2:].split(":", 1)
-            kv[k.strip()] = v.strip()
-    if kv.get("kernel_sources_sha256_16") != kernel_hash():
-        return None
-    try:
-        return int(float(kv["dram_bytes_per_launch"]))
     except (KeyError, ValueError):
         return None
 
@@ -161,242 +149,338 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def make_workload(seed, npart):
-    from paper_1311_2286_gb300 import workloads as wl
-
-    return wl.cylinder(n1=128, n2=256, npart_per_species=npart, seed=seed, inject=True)
-
-
 # ------------------------------------------------------------------------------- oracle
 
-def oracle_sample(steps, warmup, seed=1, npart=100_000):
-    """The FP64 oracle (as it stands) on a bounded sample of the workload: the same grid,
-    map, boundaries and injection, npart particles per species, fixed-field particle steps
-    (mover, injection, deposit). Returns particle-steps/s, seconds, description."""
+def oracle_sample(steps, threads, npart=1_000_000, single_thread_steps=0):
+    """The FP64 oracle (as it stands: oracle/pic.py with its mover and deposit as C loops)
+    on a bounded sample of the headline workload: the same 128^3 shell map, boundaries and
+    injection, npart + npart particles loaded uniform in physical space, fixed-field
+    particle steps (mover, injection, exact b2 deposit) in a fixed radial potential.
+    Returns particle-steps/s on `threads` threads, seconds, description, and (with
+    single_thread_steps) particle-steps/s on one thread."""
     from oracle.pic import OraclePIC
+    from paper_1311_2286_gb300 import workloads as wl
 
-    w = make_workload(seed, npart)
-    pic = OraclePIC(w, "fp64")
-    pic.initialize()
-    for _ in range(warmup):
-        pic.step(solve=False)
-    t0 = time.perf_counter()
+    w = wl.sphere(128, 128, 128, npart_per_species=npart, seed=2, inject=True)
+    pic = OraclePIC(w, "fp64", engine="c", threads=threads)
+    r = np.exp(np.log(30.0) * (np.arange(128) + 0.5) / 128)
+    pic.phi = np.broadcast_to(-5.0 / r, (128, 128, 128)).copy()
+    pic.Q = pic.charge()
+    pic.step(solve=False)  # warm-up
+
+    def timed(k):
+        t0 = time.perf_counter()
+        ps = 0
+        for _ in range(k):
+            ps += sum(sp.idx.shape[1] for sp in pic.species)
+            pic.step(solve=False)
+        dt = time.perf_counter() - t0
+        return ps / dt, dt
+
+    v, dt = timed(steps)
+    v1 = None
+    if single_thread_steps > 0:
+        pic.threads = 1
+        v1, _ = timed(single_thread_steps)
+    return v, dt, (f"{steps} fixed-field oracle steps (FP64 mover, injection, exact b2 deposit; C loops on "
+                   f"{threads} thread(s)) on the 128^3 shell with {npart}+{npart} particles"), v1
+
+
+# ------------------------------------------------------------------------------- device
+
+def timed_steps(run, nsteps, fn, flush, stream):
+    """CUDA-event time of nsteps calls of fn on the run's stream (L2 flushed and the host a
+    step ahead before each), and the particle-steps they did."""
+    import torch
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
     ps = 0
-    for _ in range(steps):
-        ps += sum(sp.idx.shape[1] for sp in pic.species)
-        pic.step(solve=False)
-    dt = time.perf_counter() - t0
-    return ps / dt, dt, (f"{steps} fixed-field oracle steps (FP64 mover, injection, exact b2 deposit) on 128x256 "
-                         f"cells with {npart}+{npart} particles, one thread")
+    cyc = []
+    for k in range(nsteps):
+        d = run.diag()  # synchronises (outside the timed events)
+        ps += sum(d["n"])
+        cyc.append(d["mg_cycles"])
+        flush_l2(flush, k)
+        host_ahead()
+        ev[k][0].record(stream)
+        fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return float(sum(a.elapsed_time(b) for a, b in ev)), ps, cyc
 
 
-# ------------------------------------------------------------------------------- main
+def profiled_phases(run, nsteps, fn, flush):
+    """The same steps launched stream-ordered with CUDA events around each phase."""
+    run.profile(True)
+    run.profile_read()
+    n = 0
+    for k in range(nsteps):
+        n += sum(run.diag()["n"])
+        flush_l2(flush, k)
+        host_ahead()
+        fn()
+    ph = run.profile_read()
+    run.profile(False)
+    return ph, n / nsteps
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--full-steps", type=int, default=20, help="full PIC cycles (with the field solve) timed")
-    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
-    ap.add_argument("--particles", type=int, default=2_000_000, help="per species")
-    ap.add_argument("--sort-interval", type=int, default=0, help="0: chosen by cpic_autotune")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch-runs", type=int, default=256, help="runs of the batched configuration (0: skip)")
-    ap.add_argument("--batch-steps", type=int, default=5)
-    ap.add_argument("--sphere-particles", type=int, default=32_000_000,
-                    help="particles per species of the 3D sphere run (0: skip)")
-    ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving run (0: skip)")
-    ap.add_argument("--serve-steps", type=int, default=40, help="PIC cycles per request")
-    ap.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second (Poisson)")
-    ap.add_argument("--no-graph", action="store_true",
-                    help="launch every step stream-ordered (per-phase events) instead of as one CUDA graph; "
-                         "profilers cannot capture kernels inside graphs with conditional nodes")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    workload = WORKLOAD.format(S=args.sort_interval if args.sort_interval > 0 else "autotuned")
+def roofline(push_ms, particles, bpp, peak, kind, traffic, kernel):
+    achieved = bpp * particles / (push_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": kernel, "peak_kind": kind, "bytes_per_particle": bpp,
+            "particles_per_launch": particles, "push_ms": push_ms}
 
-    if args.impl == "reference":
-        if rank != 0:
-            return
-        steps = max(1, args.steps // 10)
-        v, secs, sample = oracle_sample(steps, 1, npart=250_000)
-        cores = 1
-        print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": steps, "warmup": 1, "ms_per_step": 1000 * secs / steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload, "sample": sample},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        }))
-        return
+
+def sphere_measurement(cpic, npart, steps, warmup, full_steps, stream, flush, e2e_steps):
+    """The headline: fixed-field particle steps of the 3D sphere (autotuned sort interval,
+    push chunking and deposit tiling), the push kernel's roofline, full cycles with the 3D
+    multigrid solve, and the end-to-end figure through the public API."""
+    import torch
+
+    cs = ctypes_stream(stream)
+    t0 = time.perf_counter()
+    run = cpic.sphere_run_device(128, 128, 128, npart, stream=cs, inject=True)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    tuning = run.autotune(trial_steps=4)
+    run.step_particles(warmup)
+    torch.cuda.synchronize()
+    launches0 = cpic.load().cpic_kernel_launches()
+    ms, ps, _ = timed_steps(run, steps, lambda: run.step_particles(1), flush, stream)
+    launches = cpic.load().cpic_kernel_launches() - launches0
+    ph, pp = profiled_phases(run, 4, lambda: run.step_particles(1), flush)
+    push_ms = ph["push"][0] / max(ph["push"][1], 1)
+    peak, kind = measured_peak()
+    roof = roofline(push_ms, pp, B3, peak, kind, profiled_traffic(PROFILE3, SRC3, pp),
+                    "push3d_kernel<absorb,reflect,periodic> (fused gather/push/boundary/deposit, 3D)")
+    run.step(1)
+    full_ms, full_ps, cyc = timed_steps(run, full_steps, lambda: run.step(1), flush, stream)
+    e2e = end_to_end(run, cpic, e2e_steps) if e2e_steps > 0 else None
+    out = {"value": ps / (ms * 1e-3), "total_ms": ms, "particle_steps": ps, "ms_per_step": ms / steps,
+           "particles": int(pp), "setup_s": setup_s, "tuning": tuning, "gpu_launches": int(launches),
+           "phases_ms_per_step": {p: m / max(n, 1) for p, (m, n) in ph.items()}, "roofline": roof,
+           "full_cycle": {"value": full_ps / (full_ms * 1e-3), "unit": UNIT, "ms_per_step": full_ms / full_steps,
+                          "steps": full_steps, "mg_cycles_mean": float(np.mean(cyc)),
+                          "note": "whole PIC step incl. charge -> RHS and the 3D multigrid solve to rtol 1e-10"},
+           "e2e": e2e}
+    run.close()
+    return out
+
+
+def cylinder_measurement(cpic, n1, n2, npart, steps, warmup, full_steps, stream, flush, device_load, profile):
+    """The 2D cylinder in plasma (annulus r = 40^xi): fixed-field particle steps, the 2D push
+    kernel's roofline, and full cycles with the multigrid solve."""
+    import torch
+
+    from paper_1311_2286_gb300 import workloads as wl
+
+    cs = ctypes_stream(stream)
+    t0 = time.perf_counter()
+    if device_load:
+        run = cpic.cylinder_run_device(n1, n2, npart, -5.0, 1, sort_interval=4, stream=cs)
+    else:
+        w = wl.cylinder(n1=n1, n2=n2, npart_per_species=npart, seed=1, inject=True)
+        cfg = cpic.config_from_workload(w, sort_interval=4, mg_rtol=1e-10, mg_max_cycles=30)
+        run = cpic.Run(cfg, stream=cs)
+        run.set_map_analytic(cpic.CPIC_MAP_ANNULUS, [1.0, 40.0])
+        for s, p in enumerate(w.particles):
+            run.load_particles(s, p.cell, p.t, p.v)
+        for (s, face, dens, vth, seed) in w.injection:
+            run.set_injection(s, face, dens, vth, seed)
+        run.initialize()
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    tuning = run.autotune(trial_steps=8)
+    run.step_particles(warmup)
+    ms, ps, _ = timed_steps(run, steps, lambda: run.step_particles(1), flush, stream)
+    ph, pp = profiled_phases(run, min(steps, 20), lambda: run.step_particles(1), flush)
+    push_ms = ph["push"][0] / max(ph["push"][1], 1)
+    peak, kind = measured_peak()
+    roof = roofline(push_ms, pp, B2, peak, kind, profiled_traffic(profile, SRC2, pp),
+                    "push2d_kernel<false,true> (fused gather/push/boundary/deposit, 2D)")
+    out = {"value": ps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps, "particles": int(pp),
+           "cells": n1 * n2, "setup_s": setup_s, "tuning": tuning, "roofline": roof,
+           "phases_ms_per_step": {p: m / max(n, 1) for p, (m, n) in ph.items()}}
+    if full_steps > 0:
+        run.step(warmup)
+        full_ms, full_ps, cyc = timed_steps(run, full_steps, lambda: run.step(1), flush, stream)
+        phf, _ = profiled_phases(run, min(full_steps, 10), lambda: run.step(1), flush)
+        out["full_cycle"] = {"value": full_ps / (full_ms * 1e-3), "unit": UNIT, "ms_per_step": full_ms / full_steps,
+                             "steps": full_steps, "mg_cycles_mean": float(np.mean(cyc)),
+                             "solve_ms_per_step": phf["solve"][0] / max(phf["solve"][1], 1),
+                             "note": "whole PIC step incl. charge -> RHS and multigrid solve to rtol 1e-10"}
+    run.close()
+    return out
+
+
+def end_to_end(run, cpic, steps):
+    """The value's metric through the public API with host buffers (pinned), copies
+    included: per step, cpic_load_particles from host, cpic_step_particles,
+    cpic_get_particles into host, cpic_get_diag."""
+    import ctypes
 
     import torch
 
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    from paper_1311_2286_gb300 import cpic
-
-    cpic.load()
-    stream = torch.cuda.current_stream()
-    w = make_workload(1 + rank, args.particles)
-    cfg = cpic.config_from_workload(w, sort_interval=args.sort_interval, mg_rtol=1e-10, mg_max_cycles=30)
-    arena = torch.empty(cpic.Run.footprint(cfg), dtype=torch.uint8, device="cuda")
-    run = cpic.Run(cfg, arena=arena, stream=ctypes_stream(stream))
-    run.set_map_analytic(cpic.CPIC_MAP_ANNULUS, [1.0, 40.0])
-    for s, ps in enumerate(w.particles):
-        run.load_particles(s, ps.cell, ps.t, ps.v)
-    for (s, face, dens, vth, seed) in w.injection:
-        run.set_injection(s, face, dens, vth, seed)
-    run.initialize()
-    tuning = None
-    if args.sort_interval <= 0:  # choose the sort interval on the run's own particles
-        tuning = run.autotune(trial_steps=8)
-    if args.no_graph:
-        run.profile(True)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    clocks = Clocks(local)
-    clocks.start()
-    run.step_particles(args.warmup)
-    run.synchronize()
-
-    def timed(nsteps, fn):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
-        pstep = 0
-        cyc = []
-        for k in range(nsteps):
-            d = run.diag()  # synchronises (outside the timed events)
-            pstep += sum(d["n"])
-            cyc.append(d["mg_cycles"])
-            flush_l2(flush, k)
-            host_ahead()
-            ev[k][0].record(stream)
-            fn()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        return float(sum(a.elapsed_time(b) for a, b in ev)), pstep, cyc
-
-    if dist:
-        dist.barrier()
+    ns = run.cfg.n_species
+    D = run.D
+    bufs = []
+    for s in range(ns):
+        cap = int(run.cfg.capacity[s])
+        bufs.append((torch.empty(cap, dtype=torch.int32).pin_memory(),
+                     torch.empty(D * cap, dtype=torch.float32).pin_memory(),
+                     torch.empty(3 * cap, dtype=torch.float32).pin_memory()))
+    counts = []
+    for s in range(ns):
+        n = ctypes.c_int64()
+        c, t, v = bufs[s]
+        cpic.check(cpic.load().cpic_get_particles(run.h, s, c.numel(), ctypes.byref(n), cpic._ptr(c), cpic._ptr(t),
+                                                  cpic._ptr(v)))
+        counts.append(n.value)
     torch.cuda.synchronize()
-    launches0 = cpic.load().cpic_kernel_launches()
-    total_ms, particle_steps, _ = timed(args.steps, lambda: run.step_particles(1))
-    launches = cpic.load().cpic_kernel_launches() - launches0
-    if dist:
-        dist.barrier()
+    t0 = time.perf_counter()
+    ps = 0
+    h2d = d2h = 0
+    for _ in range(steps):
+        for s in range(ns):
+            c, t, v = bufs[s]
+            n = counts[s]
+            cpic.check(cpic.load().cpic_load_particles(run.h, s, n, cpic._ptr(c), cpic._ptr(t), cpic._ptr(v)))
+            h2d += n * (4 + 4 * D + 12)
+            ps += n
+        run.step_particles(1)
+        for s in range(ns):
+            c, t, v = bufs[s]
+            n = ctypes.c_int64()
+            cpic.check(cpic.load().cpic_get_particles(run.h, s, c.numel(), ctypes.byref(n), cpic._ptr(c),
+                                                      cpic._ptr(t), cpic._ptr(v)))
+            counts[s] = n.value
+            d2h += n.value * (4 + 4 * D + 12)
+        run.diag()
+        d2h += ctypes.sizeof(cpic.cpic_diag)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    return {"value": ps / secs, "unit": UNIT, "h2d_bytes_per_step": int(h2d / steps),
+            "d2h_bytes_per_step": int(d2h / steps), "steps": steps,
+            "copy_gbs": (h2d + d2h) / secs / 1e9}
 
-    def profiled(nsteps, fn):
-        # the same steps launched stream-ordered with CUDA events around each phase
-        run.profile(True)
-        run.profile_read()
-        n = 0
-        for k in range(nsteps):
-            n += sum(run.diag()["n"])
-            flush_l2(flush, k)
-            host_ahead()
-            fn()
-        ph = run.profile_read()
-        run.profile(args.no_graph)
-        return ph, n
 
-    # per-phase breakdown of the fixed-field particle steps, right after the timed region
-    # (the run's state keeps evolving, so the breakdown is taken next to the steps it explains)
-    prof_steps = min(args.steps, 20)
-    phases, prof_particles = profiled(prof_steps, lambda: run.step_particles(1))
-    # the full PIC cycle (with the field solve) on the same run, and its solve phase
-    run.step(args.warmup)
-    full_ms, full_ps, full_cyc = timed(args.full_steps, lambda: run.step(1))
-    clk = clocks.stop()
-    phases_full, _ = profiled(min(args.full_steps, 10), lambda: run.step(1))
-    phases["solve"] = phases_full["solve"]
-    (total_ms, full_ms), (particle_steps_all, full_ps_all) = aggregate_replicas(
-        dist, [total_ms, full_ms], [particle_steps, full_ps], "cuda")
-    value = particle_steps_all / (total_ms * 1e-3)
-    push_ms, push_n = phases["push"]
-    push_avg_ms = push_ms / max(push_n, 1)
-    particles_per_push = prof_particles / prof_steps
-    achieved = BYTES_PER_PARTICLE * particles_per_push / (push_avg_ms * 1e-3) / 1e9
-    peak, peak_kind = measured_peak()
+def serve_requests(cpic, nreq, steps, seed=4):
+    """The served configuration's request mix: half 2D cylinders, half 3D spheres, scale
+    s ~ U[0.25, 1] on the particle count (cylinder 2M, sphere 32M per species at 1) and on
+    the cells (128 x 256 and 128^3 at 1, per axis s^(1/d), multiples of 16), object
+    potential U[-10, 2], `steps` PIC cycles each."""
+    rng = np.random.default_rng(seed)
+    reqs, kinds = [], []
+    for i in range(nreq):
+        sc = float(rng.uniform(0.25, 1.0))
+        phi = float(rng.uniform(-10, 2))
+        if rng.random() < 0.5:
+            f = math.sqrt(sc)
+            n1 = max(32, int(round(128 * f / 16)) * 16)
+            n2 = max(64, int(round(256 * f / 16)) * 16)
+            q = cpic.make_request(n1=n1, n2=n2, particles_per_species=int(2_000_000 * sc), phi_object=phi,
+                                  steps=steps, seed=4000 + i)
+            kinds.append("cylinder")
+        else:
+            f = sc ** (1.0 / 3.0)
+            nn = max(32, int(round(128 * f / 16)) * 16)
+            q = cpic.make_request(n1=nn, n2=nn, particles_per_species=int(32_000_000 * sc), phi_object=phi,
+                                  r_outer=30.0, steps=steps, seed=4000 + i, kind=cpic.CPIC_REQ_SPHERE)
+            q.n[2] = nn
+            kinds.append("sphere")
+        reqs.append(q)
+    return reqs, kinds
 
-    # ---- end to end through the public API with host buffers
-    e2e = None
-    if not args.no_e2e:
-        e2e = end_to_end(run, cpic, min(args.steps, 50), stream)
 
-    # ---- batched runs: the same full cycles, one graph launch per batch step vs the runs
-    # stepped one after another
-    batched = None
-    if args.batch_runs > 0:
+def serve_run(cpic, reqs, kinds, rate, seed, max_active=12):
+    """Open-loop Poisson arrivals at `rate` per second into a server (continuous batching,
+    admission by device footprint); time-to-result percentiles and aggregate throughput."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, len(reqs))
+    sv = cpic.Server(hbm_budget=0, max_active=max_active, steps_per_slice=10)
+    t0 = time.perf_counter()
+    tickets, pending, results = [], {}, []
+    arrive = t0
+
+    def drain():
+        for tk in list(pending):
+            r = sv.poll(tk)
+            if r is not None:
+                results.append(r)
+                del pending[tk]
+
+    for i, q in enumerate(reqs):
+        arrive += gaps[i]
+        while time.perf_counter() < arrive:
+            drain()
+            time.sleep(2e-4)
+        tk = sv.submit(q)
+        pending[tk] = True
+        tickets.append(tk)
+    last_arrival = time.perf_counter() - t0
+    while pending:
+        drain()
+        time.sleep(1e-3)
+    wall = time.perf_counter() - t0
+    sv.stop()
+    lat = np.array([r["latency_s"] for r in results])
+    qs = np.array([r["queue_s"] for r in results])
+    kind_of = dict(zip(tickets, kinds))
+    by_kind = {}
+    for kname in ("cylinder", "sphere"):
+        lk = np.array([r["latency_s"] for r in results if kind_of[r["ticket"]] == kname])
+        if lk.size:
+            by_kind[kname] = {"requests": int(lk.size), "p50_s": float(np.percentile(lk, 50)),
+                              "p99_s": float(np.percentile(lk, 99))}
+    ps = float(sum(r["particle_steps"] for r in results))
+    return {"requests": len(reqs), "arrival_rate_per_s": rate, "offered_s": last_arrival, "wall_s": wall,
+            "served_per_s": len(reqs) / wall, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "queue_p50_s": float(np.percentile(qs, 50)),
+            "queue_p99_s": float(np.percentile(qs, 99)), "value": ps / wall, "unit": UNIT,
+            "failed": sum(1 for r in results if r["status"] != 0), "by_kind": by_kind}
+
+
+def sequential_baseline(cpic, reqs, nseq):
+    """The same requests as plain runs, one after another (each set up exactly as the
+    server sets it up, stepped with cpic_step): aggregate particle-steps/s over the first
+    nseq requests of the mix (wall clock, synchronised)."""
+    import torch
+
+    ps, wall = 0.0, 0.0
+    for q in reqs[:nseq]:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run = cpic.run_for_request(q)
+        done = 0
+        while done < q.steps:
+            k = min(10, q.steps - done)
+            live = sum(run.diag()["n"])
+            run.step(k)
+            ps += k * live
+            done += k
+        run.synchronize()
+        wall += time.perf_counter() - t0
         run.close()
-        del arena
-        batched = batched_measurement(cpic, args.batch_runs, args.batch_steps, stream)
+    return {"requests": nseq, "value": ps / wall, "unit": UNIT, "wall_s": wall,
+            "note": "each request as a stand-alone run (same set-up as the server: device load, injection, "
+                    "start-up solve), stepped in slices of 10 cycles with cpic_step, one after another"}
 
-    # ---- 3D sphere in plasma (128^3 shell, reflecting polar caps)
-    sphere = None
-    if args.sphere_particles > 0:
-        if batched is None:
-            run.close()
-            batched = False  # the 2D run is closed
-        sphere = sphere_measurement(cpic, args.sphere_particles, 20, stream, flush)
 
-    # ---- served runs: open-loop Poisson arrivals, continuous batching
-    served = None
-    if args.serve_requests > 0:
-        served = serving_measurement(cpic, args.serve_requests, args.serve_steps, args.serve_rate)
-
-    # ---- CPU baseline (rank 0, N = 1)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, secs, sample = oracle_sample(20, 1, npart=250_000)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample + f" ({secs:.1f} s)"}
-    if dist:
-        dist.barrier()
-    if rank == 0:
-        out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload, "step": "fixed-field particle step (a1-a8, sort amortised)",
-                       "sort_interval": int(run.cfg.sort_interval) if tuning is None else tuning["sort_interval"],
-                       "autotune": tuning,
-                       "particles_per_gpu": 2 * args.particles, "cells": 128 * 256,
-                       "l2": "flushed between timed steps (256 MB write, then a 256 MB read that drains the dirty lines)",
-                       "parallelism": f"replicas x{world} (independent runs, no collective)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(), "kernel": KERNEL,
-                         "peak_kind": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE},
-            "full_cycle": {"value": full_ps_all / (full_ms * 1e-3), "unit": UNIT,
-                           "ms_per_step": full_ms / args.full_steps, "steps": args.full_steps,
-                           "mg_cycles_mean": float(np.mean(full_cyc)),
-                           "note": "whole PIC step incl. charge -> RHS and multigrid solve to rtol 1e-10"},
-            "phases_ms_per_step": {p: ms / max(n, 1) for p, (ms, n) in phases.items()},
-            "push_particle_steps_per_s": particles_per_push / (push_avg_ms * 1e-3),
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "batched": batched or None,
-            "sphere3d": sphere,
-            "served": served,
-            "gpu_launches": int(launches),
-            "gpu_launches_note": "kernels launched in the timed particle steps (kernel nodes of each replayed "
-                                 "CUDA graph, counted by the library)",
-            "clocks": clk,
-        }
-        print(json.dumps(out))
-    if batched is None and sphere is None:
-        run.close()
-    if dist:
-        dist.destroy_process_group()
+def serving_measurement(cpic, nreq, steps, rate, nseq):
+    reqs, kinds = serve_requests(cpic, nreq, steps)
+    over = serve_run(cpic, reqs, kinds, rate, seed=4)
+    capacity = over["served_per_s"]
+    at70 = serve_run(cpic, reqs, kinds, 0.7 * capacity, seed=5)
+    seq = sequential_baseline(cpic, reqs, nseq) if nseq > 0 else None
+    return {"open_loop": over, "at_70pct_capacity": at70, "capacity_requests_per_s": capacity,
+            "sequential": seq, "speedup_vs_sequential": (over["value"] / seq["value"]) if seq else None,
+            "steps_per_request": steps,
+            "workload": "Poisson arrivals of 2D cylinder and 3D sphere requests (50/50); scale U[0.25, 1] on particles "
+                        "(cylinder 2M, sphere 32M per species at 1) and cells (128x256 and 128^3 at 1, multiples of "
+                        "16); phi_obj U[-10, 2]; full PIC cycles with the multigrid solve; continuous batching (at "
+                        "most 12 runs on the device, slices of 10 cycles), admission by device footprint (half the "
+                        "free memory); open loop at the configured rate, then at 70% of the capacity that run "
+                        "measured"}
 
 
 def batched_measurement(cpic, nruns, steps, stream):
@@ -483,146 +567,6 @@ def batched_measurement(cpic, nruns, steps, stream):
                         "runs' own graphs one after another on one stream"}
 
 
-def sphere_measurement(cpic, npart, steps, stream, flush):
-    """3D sphere in plasma: shell map r = 30^xi, theta in [pi/32, pi - pi/32], phi periodic,
-    128^3 cells, npart + npart particles loaded on the device uniform in physical space
-    (ppc ~ r^3 sin theta), object at -5; fixed-field particle steps (CUDA graphs, per-step
-    events, L2 flushed) and one full cycle with the 3D multigrid solve. Roofline of the 3D
-    push kernel against 56 B per particle."""
-    import torch
-
-    cs = ctypes_stream(stream)
-    t0 = time.perf_counter()
-    run = cpic.sphere_run_device(128, 128, 128, npart, stream=cs, inject=True)
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t0
-    run.step_particles(3)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    ps = 0
-    for k in range(steps):
-        ps += sum(run.diag()["n"])
-        flush_l2(flush, k)
-        host_ahead()
-        ev[k][0].record(stream)
-        run.step_particles(1)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    ms = float(sum(a.elapsed_time(b) for a, b in ev))
-    # one full cycle (3D multigrid solve to rtol 1e-10)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    run.step(1)
-    b.record(stream)
-    torch.cuda.synchronize()
-    full_ms = a.elapsed_time(b)
-    cyc = run.diag()["mg_cycles"]
-    # push kernel alone (stream-ordered pass with phase events)
-    run.profile(True)
-    run.profile_read()
-    pp = 0
-    for k in range(4):
-        pp += sum(run.diag()["n"])
-        flush_l2(flush, k)
-        host_ahead()
-        run.step_particles(1)
-    ph = run.profile_read()
-    run.profile(False)
-    push_ms = ph["push"][0] / max(ph["push"][1], 1)
-    achieved = 56 * (pp / 4) / (push_ms * 1e-3) / 1e9
-    peak, kind = measured_peak()
-    run.close()
-    return {"value": ps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
-            "particles": 2 * npart, "cells": 128 ** 3, "setup_s": setup_s,
-            "full_cycle_ms": full_ms, "mg_cycles": cyc,
-            "phases_ms_per_step": {p: m / max(n, 1) for p, (m, n) in ph.items()},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": profiled_traffic_3d(pp / 4),
-                         "kernel": "push3d_kernel<absorb,reflect,periodic> (fused gather/push/boundary/deposit, 3D)",
-                         "bytes_per_particle": 56, "peak_kind": kind},
-            "workload": "3D sphere in plasma: shell r=(30)^xi, theta_c=pi/32 (reflecting caps), 128^3 cells, "
-                        f"{npart}+{npart} particles loaded on the device, phi_obj=-5, dt=0.1, Maxwellian flux "
-                        "injection of both species at r=30, fixed-field particle steps, L2 flushed between steps"}
-
-
-def serving_measurement(cpic, nreq, steps, rate, seed=4):
-    """Cylinder-in-plasma requests arriving open loop (Poisson, `rate` per second): scale
-    s ~ U[0.25, 1] on the particle count (2M s per species) and on the cells (128 x 256
-    times sqrt(s) per axis, rounded to multiples of 16), object potential U[-10, 2],
-    `steps` PIC cycles each. Time-to-result percentiles and aggregate particle-steps/s."""
-    rng = np.random.default_rng(seed)
-    reqs = []
-    kinds = []
-    for i in range(nreq):
-        sc = float(rng.uniform(0.25, 1.0))
-        phi = float(rng.uniform(-10, 2))
-        if rng.random() < 0.5:  # cylinder: 128 x 256 cells and 2M + 2M particles at s = 1
-            f = math.sqrt(sc)
-            n1 = max(32, int(round(128 * f / 16)) * 16)
-            n2 = max(64, int(round(256 * f / 16)) * 16)
-            q = cpic.make_request(n1=n1, n2=n2, particles_per_species=int(2_000_000 * sc), phi_object=phi,
-                                  steps=steps, seed=4000 + i)
-            kinds.append("cylinder")
-        else:  # sphere: 128^3 cells and 32M + 32M particles at s = 1
-            f = sc ** (1.0 / 3.0)
-            nn = max(32, int(round(128 * f / 16)) * 16)
-            q = cpic.make_request(n1=nn, n2=nn, particles_per_species=int(32_000_000 * sc), phi_object=phi,
-                                  r_outer=30.0, steps=steps, seed=4000 + i, kind=cpic.CPIC_REQ_SPHERE)
-            q.n[2] = nn
-            kinds.append("sphere")
-        reqs.append(q)
-    gaps = rng.exponential(1.0 / rate, nreq)
-    sv = cpic.Server(hbm_budget=0, max_active=12, steps_per_slice=10)
-    t0 = time.perf_counter()
-    tickets = []
-    arrive = t0
-    pending = {}
-    results = []
-    for i, q in enumerate(reqs):
-        arrive += gaps[i]
-        while time.perf_counter() < arrive:
-            for tk in list(pending):
-                r = sv.poll(tk)
-                if r is not None:
-                    results.append(r)
-                    del pending[tk]
-            time.sleep(2e-4)
-        tk = sv.submit(q)
-        pending[tk] = True
-        tickets.append(tk)
-    last_arrival = time.perf_counter() - t0
-    while pending:
-        for tk in list(pending):
-            r = sv.poll(tk)
-            if r is not None:
-                results.append(r)
-                del pending[tk]
-        time.sleep(1e-3)
-    wall = time.perf_counter() - t0
-    sv.stop()
-    lat = np.array([r["latency_s"] for r in results])
-    kind_of = dict(zip(tickets, kinds))
-    by_kind = {}
-    for kname in ("cylinder", "sphere"):
-        lk = np.array([r["latency_s"] for r in results if kind_of[r["ticket"]] == kname])
-        if lk.size:
-            by_kind[kname] = {"requests": int(lk.size), "p50_s": float(np.percentile(lk, 50)),
-                              "p99_s": float(np.percentile(lk, 99))}
-    qs = np.array([r["queue_s"] for r in results])
-    ps = float(sum(r["particle_steps"] for r in results))
-    bad = sum(1 for r in results if r["status"] != 0)
-    return {"requests": nreq, "steps_per_request": steps, "arrival_rate_per_s": rate,
-            "offered_s": last_arrival, "wall_s": wall, "served_per_s": nreq / wall,
-            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "queue_p50_s": float(np.percentile(qs, 50)), "queue_p99_s": float(np.percentile(qs, 99)),
-            "value": ps / wall, "unit": UNIT, "failed": bad, "by_kind": by_kind,
-            "workload": "open-loop Poisson arrivals of 2D cylinder and 3D sphere requests (50/50); scale "
-                        "U[0.25, 1] on particles (cylinder 2M, sphere 32M per species at 1) and cells "
-                        "(128x256 and 128^3 at 1, multiples of 16); phi_obj U[-10, 2]; full PIC cycles with "
-                        "the multigrid solve; continuous batching (at most 12 runs on the device, a slice "
-                        "of 10 cycles per turn), admission by device footprint (half the free memory)"}
-
-
 def aggregate_replicas(dist, times_ms, counts, device):
     """Whole-job figures over N independent replicas (one per GPU, no data exchange): the
     slowest rank's time and the sum of the units all ranks processed. dist is
@@ -664,52 +608,127 @@ def ctypes_stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def end_to_end(run, cpic, steps, stream):
-    """Same metric through the public API with host buffers (pinned), copies included."""
+# ------------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--full-steps", type=int, default=5, help="full PIC cycles (with the field solve) timed")
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--sphere-particles", type=int, default=32_000_000, help="per species (headline)")
+    ap.add_argument("--cyl-particles", type=int, default=2_000_000, help="per species, 128x256 cylinder (0: skip)")
+    ap.add_argument("--cyl64-particles", type=int, default=32_000_000,
+                    help="per species, 512x1024 cylinder, the 2D HBM roofline run (0: skip)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-particles", type=int, default=1_000_000, help="per species, oracle sample")
+    ap.add_argument("--batch-runs", type=int, default=256, help="runs of the batched configuration (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests of the serving runs (0: skip)")
+    ap.add_argument("--serve-steps", type=int, default=20, help="PIC cycles per request")
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second (Poisson)")
+    ap.add_argument("--serve-seq", type=int, default=30, help="requests of the sequential baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cores = len(os.sched_getaffinity(0))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = max(1, min(args.steps, 5))
+        v, secs, sample, _ = oracle_sample(steps, cores, npart=args.oracle_particles)
+        wk = WORKLOAD.format(S="autotuned")
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": 1, "ms_per_step": 1000 * secs / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wk, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
     import torch
 
-    ns = run.cfg.n_species
-    D = run.D
-    bufs = []
-    for s in range(ns):
-        cap = int(run.cfg.capacity[s])
-        bufs.append((torch.empty(cap, dtype=torch.int32).pin_memory(),
-                     torch.empty(D * cap, dtype=torch.float32).pin_memory(),
-                     torch.empty(3 * cap, dtype=torch.float32).pin_memory()))
-    import ctypes
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
 
-    counts = []
-    for s in range(ns):
-        n = ctypes.c_int64()
-        c, t, v = bufs[s]
-        cpic.check(cpic.load().cpic_get_particles(run.h, s, c.numel(), ctypes.byref(n), cpic._ptr(c), cpic._ptr(t),
-                                                  cpic._ptr(v)))
-        counts.append(n.value)
+        dist.init_process_group("nccl")
+    from paper_1311_2286_gb300 import cpic
+
+    cpic.load()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = Clocks(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ps = 0
-    h2d = d2h = 0
-    for _ in range(steps):
-        for s in range(ns):
-            c, t, v = bufs[s]
-            n = counts[s]
-            cpic.check(cpic.load().cpic_load_particles(run.h, s, n, cpic._ptr(c), cpic._ptr(t), cpic._ptr(v)))
-            h2d += n * (4 + 4 * D + 12)
-            ps += n
-        run.step_particles(1)
-        for s in range(ns):
-            c, t, v = bufs[s]
-            n = ctypes.c_int64()
-            cpic.check(cpic.load().cpic_get_particles(run.h, s, c.numel(), ctypes.byref(n), cpic._ptr(c),
-                                                      cpic._ptr(t), cpic._ptr(v)))
-            counts[s] = n.value
-            d2h += n.value * (4 + 4 * D + 12)
-        run.diag()
-        d2h += ctypes.sizeof(cpic.cpic_diag)
-    torch.cuda.synchronize()
-    secs = time.perf_counter() - t0
-    return {"value": ps / secs, "unit": UNIT, "h2d_bytes_per_step": int(h2d / steps),
-            "d2h_bytes_per_step": int(d2h / steps)}
+    head = sphere_measurement(cpic, args.sphere_particles, args.steps, args.warmup, args.full_steps, stream, flush,
+                              0 if args.no_e2e else args.e2e_steps)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    (total_ms,), (particle_steps,) = aggregate_replicas(dist, [head["total_ms"]], [head["particle_steps"]], "cuda")
+    value = particle_steps / (total_ms * 1e-3)
+
+    cyl = cyl64 = batched = served = None
+    if args.cyl_particles > 0:
+        cyl = cylinder_measurement(cpic, 128, 256, args.cyl_particles, max(args.steps, 100), args.warmup,
+                                   args.full_steps * 4, stream, flush, device_load=False, profile=PROFILE2_SMALL)
+    if args.cyl64_particles > 0:
+        cyl64 = cylinder_measurement(cpic, 512, 1024, args.cyl64_particles, args.steps, args.warmup, args.full_steps,
+                                     stream, flush, device_load=True, profile=PROFILE2)
+    if args.batch_runs > 0:
+        batched = batched_measurement(cpic, args.batch_runs, args.batch_steps, stream)
+    if args.serve_requests > 0:
+        served = serving_measurement(cpic, args.serve_requests, args.serve_steps, args.serve_rate, args.serve_seq)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, secs, sample, v1 = oracle_sample(3, cores, npart=args.oracle_particles, single_thread_steps=1)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample + f" ({secs:.1f} s)",
+               "single_thread_value": v1}
+    if dist:
+        dist.barrier()
+    if rank == 0:
+        tuning = head["tuning"]
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD.format(S=tuning["sort_interval"]),
+                       "step": "fixed-field particle step (a1-a8, sort amortised)", "autotune": tuning,
+                       "particles_per_gpu": 2 * args.sphere_particles, "cells": 128 ** 3,
+                       "l2": "inputs (1.8 GB of particle state) larger than L2; L2 also flushed between timed steps "
+                             "(256 MB write, then a 256 MB read that drains the dirty lines)",
+                       "parallelism": f"replicas x{world} (independent runs, no collective)"},
+            "roofline": head["roofline"],
+            "full_cycle": head["full_cycle"],
+            "phases_ms_per_step": head["phases_ms_per_step"],
+            "cpu_baseline": cpu,
+            "e2e": head["e2e"],
+            "cylinder_2d_128x256": cyl,
+            "cylinder_2d_512x1024": cyl64,
+            "batched": batched,
+            "served": served,
+            "gpu_launches": head["gpu_launches"],
+            "gpu_launches_note": "kernels launched in the timed particle steps (kernel nodes of each replayed "
+                                 "CUDA graph, counted by the library)",
+            "clocks": clk,
+        }
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -66,8 +66,7 @@ class OraclePIC:
         periodic = [self.bc[2 * a] == BC_PERIODIC for a in range(self.D)]
         self.periodic = periodic
         self.geom = build_geometry(wl.vertices, periodic, axisym=wl.omega_axisym)
-        self.M, self.bbc = poisson.assemble(self.geom, self.bc, self.bcval)
-        self.solver = poisson.DirectSolver(self.geom, self.M, self.bbc, self.bc)
+        self._solver = None  # assembled and factorised on the first solve
         self.dt = wl.dt
         self.step_index = 0
         self.species = []
@@ -102,7 +101,10 @@ class OraclePIC:
 
     def solve(self):
         self.Q = self.charge()
-        self.phi = self.solver(self.Q)
+        if self._solver is None:
+            self.M, self.bbc = poisson.assemble(self.geom, self.bc, self.bcval)
+            self._solver = poisson.DirectSolver(self.geom, self.M, self.bbc, self.bc)
+        self.phi = self._solver(self.Q)
         return self.phi
 
     def field_tables(self):

@@ -613,6 +613,45 @@ def make_request(n1=64, n2=128, particles_per_species=100_000, phi_object=-5.0, 
     return q
 
 
+def run_for_request(req, sort_interval=4, stream=None, start=True):
+    """A stand-alone run set up exactly as the server sets up request `req` (cpic_request):
+    the device-evaluated map, cpic_load_maxwellian of both species with the request's
+    seeds, flux injection at the outer boundary, a cell sort and (with start) the start-up
+    solve. Stepping it with cpic_step gives the served result."""
+    import math
+
+    from . import workloads as wl
+
+    sph = req.kind == CPIC_REQ_SPHERE
+    pps = req.particles_per_species
+    if sph:
+        w = wl.sphere(n1=req.n[0], n2=req.n[1], n3=req.n[2], r0=req.r_object, R=req.r_outer,
+                      npart_per_species=pps, phi_obj=req.phi_object, mass_ratio=req.mass_ratio, dt=req.dt,
+                      host_particles=False)
+    else:
+        w = wl.cylinder(n1=req.n[0], n2=req.n[1], r0=req.r_object, R=req.r_outer, npart_per_species=pps,
+                        phi_obj=req.phi_object, mass_ratio=req.mass_ratio, dt=req.dt, host_particles=False)
+    for sp in w.species:
+        sp.w = sp.w * req.density
+    cfg = config_from_workload(w, sort_interval=sort_interval)
+    for s in range(2):
+        cfg.capacity[s] = pps + pps // 2 + 1024
+    run = Run(cfg, stream=stream)
+    if sph:
+        run.set_map_analytic(CPIC_MAP_SHELL, [req.r_object, req.r_outer, math.pi / 32])
+    else:
+        run.set_map_analytic(CPIC_MAP_ANNULUS, [req.r_object, req.r_outer])
+    vth = [math.sqrt(req.temperature), math.sqrt(req.temperature / req.mass_ratio)]
+    for s in range(2):
+        run.load_maxwellian(s, pps, vth[s], seed=req.seed * 16 + s)
+    for s in range(2):
+        run.set_injection(s, 1, req.density, vth[s], req.seed * 1000 + 7 + s)
+    run.sort()
+    if start:
+        run.initialize()
+    return run
+
+
 class Server:
     """Request loop with continuous batching (cpic_server_*)."""
 

@@ -194,29 +194,16 @@ def test_cylinder_cycle_same_in_batch_and_alone(cpic):
 
 
 def _request_run(cpic, req, sort_interval=4):
-    """A stand-alone run set up exactly as the server sets up a cylinder request (device map,
-    device Maxwellian load with the request's seeds, injection, sort, start-up), with its
-    loaded particles read back before the start-up (for the oracle)."""
+    """A stand-alone run set up exactly as the server sets up a cylinder request
+    (cpic.run_for_request, before its start-up), and the workload the oracle runs from it:
+    the particles the device loaded (read back), the same map, boundaries and injection."""
+    run = cpic.run_for_request(req, sort_interval=sort_interval, start=False)
     w = wl.cylinder(n1=req.n[0], n2=req.n[1], r0=req.r_object, R=req.r_outer,
                     npart_per_species=req.particles_per_species, phi_obj=req.phi_object, seed=0,
                     mass_ratio=req.mass_ratio, dt=req.dt, inject=True, host_particles=False)
-    cfg = cpic.config_from_workload(w, sort_interval=sort_interval)
-    pps = req.particles_per_species
-    for s in range(2):
-        cfg.capacity[s] = pps + pps // 2 + 1024
-    run = cpic.Run(cfg)
-    run.set_map_analytic(cpic.CPIC_MAP_ANNULUS, [req.r_object, req.r_outer])
     vth = [math.sqrt(req.temperature), math.sqrt(req.temperature / req.mass_ratio)]
-    for s in range(2):
-        run.load_maxwellian(s, pps, vth[s], seed=req.seed * 16 + s)
-    inj = []
-    for s in range(2):
-        run.set_injection(s, 1, req.density, vth[s], req.seed * 1000 + 7 + s)
-        inj.append((s, 1, req.density, vth[s], req.seed * 1000 + 7 + s))
-    run.sort()
-    loaded = [run.particles(s) for s in range(2)]
-    w.particles = [wl.ParticleSet(c, t, v) for c, t, v in loaded]
-    w.injection = inj
+    w.particles = [wl.ParticleSet(*run.particles(s)) for s in range(2)]
+    w.injection = [(s, 1, req.density, vth[s], req.seed * 1000 + 7 + s) for s in range(2)]
     return run, w
 
 
