@@ -34,11 +34,24 @@ constexpr int P3_TILE_CELLS = 8192;   // 64 KB of shared memory (two 32-bit word
 enum { K_PER = CPIC_PBC_PERIODIC, K_ABS = CPIC_PBC_ABSORB, K_REF = CPIC_PBC_REFLECT };
 
 struct Tile3 {
-    unsigned lo;        // shared-memory address of the low words
-    unsigned* hi_ptr;   // the high words
-    int k0, P, j0, R, W;  // planes [k0, k0 + P), rows [j0, j0 + R), W = n0 + 2 columns
+    unsigned lo;          // shared-memory address of the low words
+    unsigned* hi_ptr;     // the high words
+    int i0, j0, k0;       // cell of the tile's corner (tile coordinates are taken modulo the
+                          // axis length on periodic axes)
+    int W, R, P;          // columns, rows, planes
     bool on;
 };
+
+// tile coordinate of cell index c on an axis: c - origin, wrapped into [0, n) when periodic
+template <int KIND>
+__device__ __forceinline__ int tile_coord(int c, int origin, int n) {
+    int d = c - origin;
+    if (KIND == CPIC_PBC_PERIODIC) {
+        if (d < 0) d += n;
+        if (d >= n) d -= n;
+    }
+    return d;
+}
 
 #define CPIC_TILE3_ADD(OFF, ARG)                        \
     "atom.shared.add.u32 o, [%1+" OFF "], " ARG ";\n\t" \
@@ -59,11 +72,14 @@ __device__ __forceinline__ void tile3_add_row(unsigned& m, unsigned a, unsigned 
 // tile deposit into the padded global grid (deposit_warp). The largest group of lanes that
 // share a cell is summed first (__reduce_add_sync over the group) and deposited by one lane.
 // Node weights are produced and deposited one row of three at a time (nine rows).
+template <int K0, int K1, int K2>
 __device__ __forceinline__ void deposit_tile3(const PushParams& p, const Tile3& tl, int s, bool alive, const int* c,
                                               const float* t) {
     const int lane = threadIdx.x & 31;
-    const int pz = c[2] - tl.k0, ry = c[1] - tl.j0;
-    const bool in = alive && pz >= 1 && pz + 1 < tl.P && ry >= 1 && ry + 1 < tl.R;
+    const int px = tile_coord<K0>(c[0], tl.i0, p.n[0]);
+    const int ry = tile_coord<K1>(c[1], tl.j0, p.n[1]);
+    const int pz = tile_coord<K2>(c[2], tl.k0, p.n[2]);
+    const bool in = alive && px >= 1 && px + 1 < tl.W && pz >= 1 && pz + 1 < tl.P && ry >= 1 && ry + 1 < tl.R;
     const bool out = alive && !in;
     if (__any_sync(FULL, out)) deposit_warp<3>(p, s, out, c, t);
     if (!__any_sync(FULL, in)) return;
@@ -71,7 +87,7 @@ __device__ __forceinline__ void deposit_tile3(const PushParams& p, const Tile3& 
 #pragma unroll
     for (int a = 0; a < 3; ++a) axis_weights(t[a], w[a]);
     // lanes that do not deposit here get keys of their own
-    const int off = in ? (pz * tl.R + ry) * tl.W + c[0] + 1 : -1 - lane;
+    const int off = in ? (pz * tl.R + ry) * tl.W + px : -1 - lane;
     const unsigned peers = __match_any_sync(FULL, off);
     const unsigned score = ((unsigned)__popc(peers) << 5) | (unsigned)(31 - __clz(peers));
     const unsigned best = __reduce_max_sync(FULL, score);
@@ -212,7 +228,8 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
     extern __shared__ unsigned tile_dyn[];  // [P3_TILE_CELLS] low words, then high words
     unsigned* tile_lo = tile_dyn;
     unsigned* tile_hi = tile_dyn + P3_TILE_CELLS;
-    __shared__ int red[4][P3_THREADS / 32];
+    __shared__ int red[6][P3_THREADS / 32];
+    __shared__ int sh_gone[8];  // removed particles of the chunk per face (6: non-finite)
     const DevCounters* ctr = p.ctr;
     const int cur = ctr->cur;
     const int nsp = p.nsp;
@@ -254,59 +271,91 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
         Tile3 tl;
         tl.lo = (unsigned)__cvta_generic_to_shared(tile_lo);
         tl.hi_ptr = tile_hi;
-        tl.W = n0 + 2;
         {
+            // The tile: the cells around the chunk's middle particle that its sampled
+            // particles occupy, plus two cells on every side (the stencil's neighbour and one
+            // cell of motion since the last sort). Samples more than two planes or eight rows
+            // from the middle one (particles near the polar caps cross the small azimuthal
+            // cells quickly, a chunk may end in the next plane) are left out of the bounds:
+            // the few particles outside the tile deposit through the global path.
             const int si = lo + (int)(((long long)(hi - lo - 1) * threadIdx.x) / (P3_THREADS - 1));
             const int sc = cellp[si];
-            int jmin = 0x7fffffff, jmax = -1, kmin = 0x7fffffff, kmax = -1;
-            if (sc >= 0) {
-                const int jj = (sc >> 10) & 1023, kk = sc >> 20;
-                jmin = jmax = jj;
-                kmin = kmax = kk;
+            __syncthreads();  // the previous chunk's flush is done with the tile and red[]
+            if (threadIdx.x == 0) red[0][0] = 0x7fffffff;
+            __syncthreads();
+            const int dist = threadIdx.x > P3_THREADS / 2 ? threadIdx.x - P3_THREADS / 2 : P3_THREADS / 2 - threadIdx.x;
+            if (sc >= 0) atomicMin(&red[0][0], dist * 1024 + (int)threadIdx.x);
+            __syncthreads();
+            const int pick = red[0][0];
+            int cc[3] = {0, 0, 0};
+            bool have = pick != 0x7fffffff;
+            if (have) {
+                const int cw = cellp[lo + (int)(((long long)(hi - lo - 1) * (pick & 1023)) / (P3_THREADS - 1))];
+                cc[0] = cw & 1023;
+                cc[1] = (cw >> 10) & 1023;
+                cc[2] = cw >> 20;
+            }
+            int dmin[3] = {0, 0, 0}, dmax[3] = {0, 0, 0};
+            if (have && sc >= 0) {
+                const int sx[3] = {sc & 1023, (sc >> 10) & 1023, sc >> 20};
+                int d[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    d[a] = sx[a] - cc[a];
+                    if (KIND[a] == K_PER) {  // nearest image
+                        if (2 * d[a] > p.n[a]) d[a] -= p.n[a];
+                        if (2 * d[a] < -p.n[a]) d[a] += p.n[a];
+                    }
+                }
+                if (d[2] >= -2 && d[2] <= 2 && d[1] >= -8 && d[1] <= 8) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) dmin[a] = dmax[a] = d[a];
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                jmin = min(jmin, __shfl_xor_sync(FULL, jmin, o));
-                jmax = max(jmax, __shfl_xor_sync(FULL, jmax, o));
-                kmin = min(kmin, __shfl_xor_sync(FULL, kmin, o));
-                kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    dmin[a] = min(dmin[a], __shfl_xor_sync(FULL, dmin[a], o));
+                    dmax[a] = max(dmax[a], __shfl_xor_sync(FULL, dmax[a], o));
+                }
             }
-            __syncthreads();  // the previous chunk's flush is done with the tile
+            __syncthreads();  // everyone has read red[0][0]
             if ((threadIdx.x & 31) == 0) {
-                red[0][threadIdx.x >> 5] = jmin;
-                red[1][threadIdx.x >> 5] = jmax;
-                red[2][threadIdx.x >> 5] = kmin;
-                red[3][threadIdx.x >> 5] = kmax;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    red[a][threadIdx.x >> 5] = dmin[a];
+                    red[3 + a][threadIdx.x >> 5] = dmax[a];
+                }
             }
+            if (threadIdx.x < 8) sh_gone[threadIdx.x] = 0;
             __syncthreads();
-            jmin = red[0][0];
-            jmax = red[1][0];
-            kmin = red[2][0];
-            kmax = red[3][0];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                dmin[a] = red[a][0];
+                dmax[a] = red[3 + a][0];
+            }
 #pragma unroll
             for (int w = 1; w < P3_THREADS / 32; ++w) {
-                jmin = min(jmin, red[0][w]);
-                jmax = max(jmax, red[1][w]);
-                kmin = min(kmin, red[2][w]);
-                kmax = max(kmax, red[3][w]);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    dmin[a] = min(dmin[a], red[a][w]);
+                    dmax[a] = max(dmax[a], red[3 + a][w]);
+                }
             }
-            // the sampled rows and planes, one more on each side for particles that moved
-            // there since the last sort (azimuthal cells near the polar caps are small), and
-            // the stencil's neighbours; a spread of up to two sampled planes is taken.
-            // Particles outside the tile deposit through the global path
-            tl.j0 = jmin - 2;
-            tl.R = jmax - jmin + 5;
-            tl.k0 = kmin - 2;
-            tl.P = kmax - kmin + 5;
-            if (kmax - kmin > 2) tl.P = 0x7fff;  // a chunk across many planes: no tile
-            tl.on = p.tile && kmax >= kmin && tl.P * tl.R * tl.W <= P3_TILE_CELLS;
+            tl.i0 = cc[0] + dmin[0] - 2;
+            tl.j0 = cc[1] + dmin[1] - 2;
+            tl.k0 = cc[2] + dmin[2] - 2;
+            tl.W = dmax[0] - dmin[0] + 5;
+            tl.R = dmax[1] - dmin[1] + 5;
+            tl.P = dmax[2] - dmin[2] + 5;
+            tl.on = p.tile && have && tl.P * tl.R * tl.W <= P3_TILE_CELLS;
             if (tl.on)
                 for (int k = threadIdx.x; k < tl.P * tl.R * tl.W; k += P3_THREADS) tile_lo[k] = tile_hi[k] = 0u;
             __syncthreads();
         }
 
         long long ke = 0;
-        int gone[7] = {0, 0, 0, 0, 0, 0, 0};
 
         int i = lo + (int)threadIdx.x;
         int ncw = -1;
@@ -429,15 +478,12 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
                     }
                 }
                 const bool alive = active && face < 0;
-                if (active && face >= 0) {
-    #pragma unroll
-                    for (int f = 0; f < 7; ++f) gone[f] += face == f;
-                }
+                if (active && face >= 0) atomicAdd(&sh_gone[face], 1);  // rare: kept in shared memory
                 store_state3(active, cellp + slot, alive ? (cn[0] | (cn[1] << 10) | (cn[2] << 20)) : -1, tq0 + slot,
                              tq0 + T + slot, tq0 + 2 * T + slot, tn, vq0 + slot, vq0 + T + slot, vq0 + 2 * T + slot, v);
                 // a6: deposit
                 if constexpr (TILE)
-                    deposit_tile3(p, tl, s, alive, cn, tn);
+                    deposit_tile3<K0, K1, K2>(p, tl, s, alive, cn, tn);
                 else
                     deposit_warp<3>(p, s, alive, cn, tn);
             }
@@ -446,7 +492,8 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
             iterate(std::true_type{});
         else
             iterate(std::false_type{});
-        // flush the tile into the padded grid
+        // flush the tile into the padded grid (one halo layer per side; a periodic axis wraps
+        // tile cells beyond its halo, a non-periodic one holds nothing there)
         if (tl.on) {
             __syncthreads();
             unsigned long long* g = p.charge + (long long)s * p.ncell_h;
@@ -455,30 +502,30 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
                 const unsigned long long val = ((unsigned long long)tile_hi[k] << 32) | tile_lo[k];
                 if (!val) continue;
                 const int pk_ = k / plane, rem = k - pk_ * plane;
-                const int row = tl.j0 + rem / tl.W, col = rem % tl.W;
-                const int pl = tl.k0 + pk_;
-                if (row < -1 || row > n1 || pl < -1 || pl > n2) continue;
-                atomicAdd(g + ((long long)(pl + 1) * (n1 + 2) + (row + 1)) * tl.W + col, val);
+                const int rr = rem / tl.W;
+                int gx = tl.i0 + (rem - rr * tl.W), gy = tl.j0 + rr, gz = tl.k0 + pk_;
+                if (K0 == K_PER) gx = gx < -1 ? gx + n0 : (gx > n0 ? gx - n0 : gx);
+                if (K1 == K_PER) gy = gy < -1 ? gy + n1 : (gy > n1 ? gy - n1 : gy);
+                if (K2 == K_PER) gz = gz < -1 ? gz + n2 : (gz > n2 ? gz - n2 : gz);
+                if (gx < -1 || gx > n0 || gy < -1 || gy > n1 || gz < -1 || gz > n2) continue;
+                atomicAdd(g + ((long long)(gz + 1) * (n1 + 2) + (gy + 1)) * (n0 + 2) + (gx + 1), val);
             }
         }
         // tallies of this chunk
         ke = warp_sum_ll(ke);
-#pragma unroll
-        for (int f = 0; f < 7; ++f)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) gone[f] += __shfl_xor_sync(FULL, gone[f], o);
-        if ((threadIdx.x & 31) == 0) {
+        if ((threadIdx.x & 31) == 0 && ke) atomicAdd((unsigned long long*)&p.ctr->ke_fp[s], (unsigned long long)ke);
+        __syncthreads();  // every absorption of the chunk is in sh_gone
+        if (threadIdx.x == 0) {
             DevCounters* cw = p.ctr;
-            if (ke) atomicAdd((unsigned long long*)&cw->ke_fp[s], (unsigned long long)ke);
             long long removed = 0;
-#pragma unroll
             for (int f = 0; f < 7; ++f) {
-                removed += gone[f];
-                if (!gone[f]) continue;
+                const int g = sh_gone[f];
+                removed += g;
+                if (!g) continue;
                 if (f < 6)
-                    atomicAdd((unsigned long long*)&cw->absorbed[s][f], (unsigned long long)gone[f]);
+                    atomicAdd((unsigned long long*)&cw->absorbed[s][f], (unsigned long long)g);
                 else
-                    atomicAdd((unsigned long long*)&cw->nonfinite, (unsigned long long)gone[f]);
+                    atomicAdd((unsigned long long*)&cw->nonfinite, (unsigned long long)g);
             }
             if (removed) atomicAdd((unsigned long long*)&cw->alive[s], (unsigned long long)(-removed));
         }
