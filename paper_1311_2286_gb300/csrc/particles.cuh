@@ -185,23 +185,17 @@ __device__ __forceinline__ void deposit_warp(const PushParams& p, int s, bool al
 #pragma unroll
         for (int node = 0; node < NN; ++node) q[node] = 0u;
     }
-    // padded offset of this lane's cell; dead lanes take the first live lane's cell
-    int off = c[0] + c[1] * p.hs1 + (D == 3 ? c[2] * p.hs2 : 0);
-    const int off_first = __shfl_sync(FULL, off, __ffs(live) - 1);
-    if (!alive) off = off_first;
+    // padded offset of this lane's cell (dead lanes: keys of their own); every group of lanes
+    // that share a cell is summed over its lanes and deposited by its lowest lane
+    const int off = alive ? c[0] + c[1] * p.hs1 + (D == 3 ? c[2] * p.hs2 : 0) : -1 - lane;
     const unsigned peers = __match_any_sync(FULL, off);
-    const unsigned score = ((unsigned)__popc(peers) << 5) | (31u - (unsigned)(__ffs(peers) - 1));
-    const unsigned best = __reduce_max_sync(FULL, score);
-    bool issue = alive;  // lanes that issue reductions: the group leader and the others
-    if ((best >> 5) > 1) {  // warp-uniform: some cell holds two or more lanes
-        const int leader = 31 - (int)(best & 31u);
-        const bool mine = off == __shfl_sync(FULL, off, leader);
+    const int my_leader = __ffs(peers) - 1;
+    const bool issue = alive && lane == my_leader;
+    for (unsigned g = __ballot_sync(FULL, issue && (peers & (peers - 1u)) != 0u); g; g &= g - 1u) {
+        if (my_leader == __ffs(g) - 1) {
 #pragma unroll
-        for (int node = 0; node < NN; ++node) {
-            const unsigned tot = __reduce_add_sync(FULL, mine ? q[node] : 0u);
-            q[node] = mine ? tot : q[node];
+            for (int node = 0; node < NN; ++node) q[node] = __reduce_add_sync(peers, q[node]);
         }
-        issue = mine ? lane == leader : alive;
     }
     if (issue) {
         unsigned long long* g = p.charge + (long long)s * p.ncell_h + p.origin + off;

@@ -86,8 +86,8 @@ __device__ __forceinline__ void tile_add_row(unsigned& m, unsigned a, unsigned q
 }
 
 // Deposit of one particle per lane into the chunk's tile; lanes whose 3x3 stencil leaves the
-// tile rows deposit straight into the padded global grid. The largest group of lanes that
-// share a cell is summed first (__reduce_add_sync over the group) and deposited by one lane.
+// tile rows deposit straight into the padded global grid. Lanes that share a cell are summed
+// first (__reduce_add_sync over each such group) and deposited by one lane of the group.
 __device__ __forceinline__ void deposit_tile(const PushParams& p, const Tile& tl, int s, bool alive,
                                              const int* c, const float* t) {
     const int lane = threadIdx.x & 31;
@@ -98,17 +98,17 @@ __device__ __forceinline__ void deposit_tile(const PushParams& p, const Tile& tl
     if (!__any_sync(FULL, in)) return;
     unsigned q[9];
     node_weights<2>(t, q);
-    // lanes that do not deposit here get keys of their own
+    // lanes that do not deposit here get keys of their own; every group of lanes that share a
+    // cell is summed over its lanes and deposited by its lowest lane
     const int off = in ? rr * tl.W + c[0] + 1 : -1 - lane;
     const unsigned peers = __match_any_sync(FULL, off);
-    const unsigned score = ((unsigned)__popc(peers) << 5) | (unsigned)(31 - __clz(peers));
-    const unsigned best = __reduce_max_sync(FULL, score);
-    const int leader = (int)(best & 31u);
-    bool issue = in;
-    if ((best >> 5) > 1 && ((peers >> leader) & 1u)) {  // the lanes of the largest group
+    const int my_leader = __ffs(peers) - 1;
+    const bool issue = in && lane == my_leader;
+    for (unsigned g = __ballot_sync(FULL, issue && (peers & (peers - 1u)) != 0u); g; g &= g - 1u) {
+        if (my_leader == __ffs(g) - 1) {
 #pragma unroll
-        for (int node = 0; node < 9; ++node) q[node] = __reduce_add_sync(peers, q[node]);
-        issue = lane == leader;
+            for (int node = 0; node < 9; ++node) q[node] = __reduce_add_sync(peers, q[node]);
+        }
     }
     if (issue) {
         const unsigned mid = tl.lo + 4u * (unsigned)(off - 1), dw = 4u * (unsigned)tl.W;

@@ -69,8 +69,8 @@ __device__ __forceinline__ void tile3_add_row(unsigned& m, unsigned a, unsigned 
 }
 
 // Deposit of one particle per lane into the chunk's tile; lanes whose stencil leaves the
-// tile deposit into the padded global grid (deposit_warp). The largest group of lanes that
-// share a cell is summed first (__reduce_add_sync over the group) and deposited by one lane.
+// tile deposit into the padded global grid (deposit_warp). Lanes that share a cell are summed
+// first (__reduce_add_sync over each such group) and deposited by one lane of the group.
 // Node weights are produced and deposited one row of three at a time (nine rows).
 template <int K0, int K1, int K2>
 __device__ __forceinline__ void deposit_tile3(const PushParams& p, const Tile3& tl, int s, bool alive, const int* c,
@@ -86,14 +86,14 @@ __device__ __forceinline__ void deposit_tile3(const PushParams& p, const Tile3& 
     unsigned w[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) axis_weights(t[a], w[a]);
-    // lanes that do not deposit here get keys of their own
+    // lanes that do not deposit here get keys of their own; every group of lanes that share a
+    // cell is summed over its lanes (__reduce_add_sync) and deposited by its lowest lane, so
+    // no two lanes of one atomic instruction add to the same word
     const int off = in ? (pz * tl.R + ry) * tl.W + px : -1 - lane;
     const unsigned peers = __match_any_sync(FULL, off);
-    const unsigned score = ((unsigned)__popc(peers) << 5) | (unsigned)(31 - __clz(peers));
-    const unsigned best = __reduce_max_sync(FULL, score);
-    const int leader = (int)(best & 31u);
-    const bool group = (best >> 5) > 1 && ((peers >> leader) & 1u);  // lanes of the largest group
-    const bool issue = group ? lane == leader : in;
+    const int my_leader = __ffs(peers) - 1;
+    const bool issue = in && lane == my_leader;
+    const unsigned groups = __ballot_sync(FULL, issue && (peers & (peers - 1u)) != 0u);  // leaders of shared cells
     const int plane = tl.R * tl.W;
     const unsigned base = tl.lo + 4u * (unsigned)(off - 1 - tl.W - plane);
     // rows of three nodes (m1, m2) in the order below, the centre row (1, 1) last, so that the
@@ -112,10 +112,12 @@ __device__ __forceinline__ void deposit_tile3(const PushParams& p, const Tile3& 
             q1 = node_weight3(w[0][1], w12);
             rest += q0 + q1 + q2;
         }
-        if (group) {
-            q0 = __reduce_add_sync(peers, q0);
-            q1 = __reduce_add_sync(peers, q1);
-            q2 = __reduce_add_sync(peers, q2);
+        for (unsigned g = groups; g; g &= g - 1u) {  // warp-uniform: one pass per shared cell
+            if (my_leader == __ffs(g) - 1) {
+                q0 = __reduce_add_sync(peers, q0);
+                q1 = __reduce_add_sync(peers, q1);
+                q2 = __reduce_add_sync(peers, q2);
+            }
         }
         if (issue) tile3_add_row(m, base + 4u * (unsigned)(m1 * tl.W + m2 * plane), q0, q1, q2);
     }
@@ -349,6 +351,20 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
             tl.W = dmax[0] - dmin[0] + 5;
             tl.R = dmax[1] - dmin[1] + 5;
             tl.P = dmax[2] - dmin[2] + 5;
+            // a spread-out chunk (few particles per cell): narrow the columns, then the rows,
+            // to a window around the middle particle that fits the shared memory
+            if (tl.P * tl.R * tl.W > P3_TILE_CELLS) {
+                const int wmax = max(5, P3_TILE_CELLS / (tl.P * tl.R));
+                if (tl.W > wmax) {
+                    tl.W = wmax;
+                    tl.i0 = cc[0] - wmax / 2;
+                }
+                const int rmax = max(5, P3_TILE_CELLS / (tl.P * tl.W));
+                if (tl.R > rmax) {
+                    tl.R = rmax;
+                    tl.j0 = cc[1] - rmax / 2;
+                }
+            }
             tl.on = p.tile && have && tl.P * tl.R * tl.W <= P3_TILE_CELLS;
             if (tl.on)
                 for (int k = threadIdx.x; k < tl.P * tl.R * tl.W; k += P3_THREADS) tile_lo[k] = tile_hi[k] = 0u;
