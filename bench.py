@@ -231,7 +231,7 @@ def roofline(push_ms, particles, bpp, peak, kind, traffic, kernel):
             "particles_per_launch": particles, "push_ms": push_ms}
 
 
-def sphere_measurement(cpic, npart, steps, warmup, full_steps, stream, flush, e2e_steps):
+def sphere_measurement(cpic, npart, steps, warmup, full_steps, stream, flush, e2e_steps, tuning=None):
     """The headline: fixed-field particle steps of the 3D sphere (autotuned sort interval,
     push chunking and deposit tiling), the push kernel's roofline, full cycles with the 3D
     multigrid solve, and the end-to-end figure through the public API."""
@@ -242,7 +242,12 @@ def sphere_measurement(cpic, npart, steps, warmup, full_steps, stream, flush, e2
     run = cpic.sphere_run_device(128, 128, 128, npart, stream=cs, inject=True)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    tuning = run.autotune(trial_steps=4)
+    if tuning is None:
+        tuning = run.autotune(trial_steps=4)
+    else:  # fixed knobs (profiling a known configuration): sort interval, chunk, tile
+        run.set_sort_interval(tuning[0])
+        run.set_push_tuning(tuning[1], tuning[2])
+        tuning = {"sort_interval": tuning[0], "chunk": tuning[1], "tile": tuning[2], "fixed": True}
     run.step_particles(warmup)
     torch.cuda.synchronize()
     launches0 = cpic.load().cpic_kernel_launches()
@@ -631,6 +636,8 @@ def main():
     ap.add_argument("--serve-steps", type=int, default=20, help="PIC cycles per request")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second (Poisson)")
     ap.add_argument("--serve-seq", type=int, default=30, help="requests of the sequential baseline")
+    ap.add_argument("--tuning", default="", help="S,C,T: fixed sort interval, push chunk and deposit tiling of the "
+                                                 "headline run instead of the autotuner (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -674,8 +681,9 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    fixed = tuple(int(x) for x in args.tuning.split(",")) if args.tuning else None
     head = sphere_measurement(cpic, args.sphere_particles, args.steps, args.warmup, args.full_steps, stream, flush,
-                              0 if args.no_e2e else args.e2e_steps)
+                              0 if args.no_e2e else args.e2e_steps, tuning=fixed)
     if dist:
         dist.barrier()
     clk = clocks.stop()

@@ -115,6 +115,9 @@ typedef struct cpic_diag {
                                               operator); 0: the full stencil. The environment
                                               variable CPIC_PC_FULL_STENCIL, set when the map
                                               is set, forces 0. */
+    double object_potential;               /* floating conductor (cpic_set_floating): its
+                                              potential after the last solve (0 without one) */
+    double object_charge;                  /* and its charge (initial + collected) */
 } cpic_diag;
 
 /* ---------------------------------------------------------------- general */
@@ -181,6 +184,20 @@ int cpic_get_particles(cpic_run* run, int sp, int64_t room, int64_t* n, int32_t*
  * 2D faces normal to axis 0 only. */
 int cpic_set_injection(cpic_run* run, int sp, int face, double density, double vth,
                        const double* drift, uint64_t seed);
+
+/* Floating conductor (Sec. III.A-B: the object collects the particles that reach it and
+ * charges up to a floating potential; Figs. of the wall and sphere potential against time).
+ * From now on the Dirichlet face `face` (0 or 1: the ends of axis 0, e.g. the object at
+ * xi = 0) is a conductor whose potential V is set at every field solve by Gauss's law from
+ * its charge Q = charge0 + sum_s q_s w_s (particles of species s absorbed at that face,
+ * counted since the run started): Q equals minus the flux of grad phi out through the face,
+ * 2 a^{00} (phi_c - V) summed over the face's cells in the finite-volume scheme. The solve
+ * computes phi_0 with the conductor at 0 and adds V psi, psi the charge-free potential of
+ * the conductor at 1 (solved here, once, with the other Dirichlet faces at 0). The face's
+ * configured Dirichlet value is no longer used; cpic_get_diag reports V and Q. Requires the
+ * map and a run that is not yet initialised (CPIC_ERR_STATE otherwise), a Dirichlet face
+ * and a non-axisymmetric run (CPIC_ERR_INVALID otherwise). Synchronous. */
+int cpic_set_floating(cpic_run* run, int face, double charge0);
 
 /* Loads n particles of species sp on the device, replacing its particles: a Maxwellian
  * plasma of uniform physical density (the paper's runs start from one, Sec. III.A-B).

@@ -67,6 +67,9 @@ class OraclePIC:
         self.periodic = periodic
         self.geom = build_geometry(wl.vertices, periodic, axisym=wl.omega_axisym)
         self._solver = None  # assembled and factorised on the first solve
+        self.floating = None  # (face, charge0) of a floating conductor
+        self.object_potential = 0.0
+        self.object_charge = 0.0
         self.dt = wl.dt
         self.step_index = 0
         self.species = []
@@ -102,10 +105,53 @@ class OraclePIC:
     def solve(self):
         self.Q = self.charge()
         if self._solver is None:
-            self.M, self.bbc = poisson.assemble(self.geom, self.bc, self.bcval)
+            bv = list(self.bcval)
+            if self.floating is not None:
+                bv[self.floating[0]] = 0.0  # the conductor's potential is added below
+            self.M, self.bbc = poisson.assemble(self.geom, self.bc, bv)
             self._solver = poisson.DirectSolver(self.geom, self.M, self.bbc, self.bc)
         self.phi = self._solver(self.Q)
+        if self.floating is not None:
+            face, q0 = self.floating
+            qobj = q0
+            for sp in self.species:
+                qobj += sp.q * sp.w * float(sp.absorbed[face])
+            V = -(qobj + self._face_flux(self.phi, face, 0.0)) / self._cpsi
+            self.phi = self.phi + V * self._psi
+            self.bcval[face] = V  # the vertex field's Dirichlet value on that face
+            self.object_potential, self.object_charge = V, qobj
         return self.phi
+
+    def _face_flux(self, u, face, ub):
+        """sum over the cells at face `face` (axis 0) of the Dirichlet face flux
+        2 a^{00} (u_c - ub), in cell-index order (axis 1 fastest)."""
+        a00 = self.geom.face[0][0]  # numpy face layout, axis 0 last
+        col_f = 0 if face == 0 else self.n[0]
+        col_c = 0 if face == 0 else self.n[0] - 1
+        af = a00[..., col_f].ravel()
+        uc = u[..., col_c].ravel()
+        acc = 0.0
+        for x, y in zip(af, uc):
+            acc += 2.0 * x * (y - ub)
+        return acc
+
+    def set_floating(self, face, charge0=0.0):
+        """The conductor at Dirichlet face `face` (0 or 1, the ends of axis 0) floats
+        (Sec. III.A-B: the object charges up with the particles it collects). Gauss's law
+        for the conductor: its charge Q = charge0 + sum_s q_s w_s (absorbed at the face) is
+        minus the outward flux of grad phi through its surface, which in the finite-volume
+        scheme (spec P) is the Dirichlet face flux 2 a^{00} (phi_c - V) summed over the
+        face's cells. Every solve takes phi_0 with the conductor at 0 and adds V psi, psi
+        the charge-free potential with the conductor at 1 and every other Dirichlet face at
+        0; V = -(Q + G0) / Cpsi with G0, Cpsi the face flux sums of phi_0 (about 0) and of
+        psi (about 1)."""
+        bv = [0.0] * len(self.bcval)
+        bv[face] = 1.0
+        M1, b1 = poisson.assemble(self.geom, self.bc, bv)
+        self._psi = poisson.DirectSolver(self.geom, M1, b1, self.bc)(np.zeros(self.geom.Jc.shape))
+        self._cpsi = self._face_flux(self._psi, face, 1.0)
+        self.floating = (face, float(charge0))
+        self._solver = None
 
     def field_tables(self):
         G = gradient.vertex_gradient(self.phi, self.bc, self.bcval)
@@ -184,6 +230,7 @@ class OraclePIC:
             self.Q = self.charge()
         self.step_index += 1
         self.history.append({"step": self.step_index, "W_E": we, "W_K": sum(ke),
+                             "object_potential": self.object_potential, "object_charge": self.object_charge,
                              "n": [sp.idx.shape[1] for sp in self.species],
                              "absorbed": [sp.absorbed.copy() for sp in self.species]})
         return self.history[-1]

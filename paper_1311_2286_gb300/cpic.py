@@ -61,6 +61,8 @@ class cpic_diag(ctypes.Structure):
         ("mg_cycles", ctypes.c_int32),
         ("mg_residual", ctypes.c_double),
         ("pc_face_only", ctypes.c_int32),
+        ("object_potential", ctypes.c_double),
+        ("object_charge", ctypes.c_double),
     ]
 
 
@@ -145,6 +147,7 @@ _SIGS = {
     "cpic_set_map_analytic": ([P, ctypes.c_int, P, ctypes.c_int], ctypes.c_int),
     "cpic_load_particles": ([P, ctypes.c_int, ctypes.c_int64, P, P, P], ctypes.c_int),
     "cpic_get_particles": ([P, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), P, P, P], ctypes.c_int),
+    "cpic_set_floating": ([P, ctypes.c_int, ctypes.c_double], ctypes.c_int),
     "cpic_set_injection": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, ctypes.c_uint64],
                            ctypes.c_int),
     "cpic_initialize": ([P], ctypes.c_int),
@@ -388,6 +391,11 @@ class Run:
         run.nvert = int(np.prod([x + 1 for x in run.n]))
         return run
 
+    def set_floating(self, face=0, charge0=0.0):
+        """cpic_set_floating: the face's conductor floats (Gauss's-law potential from its
+        collected charge)."""
+        check(load().cpic_set_floating(self.h, face, charge0))
+
     def step_particles(self, nsteps=1):
         """Particle steps with the field held fixed (no field solve)."""
         check(load().cpic_step_particles(self.h, nsteps))
@@ -442,7 +450,8 @@ class Run:
             "absorbed": [[d.absorbed[s][f] for f in range(2 * self.D)] for s in range(ns)],
             "injected": [d.injected[s] for s in range(ns)], "dropped": [d.dropped[s] for s in range(ns)],
             "nonfinite": d.nonfinite, "mg_cycles": d.mg_cycles, "mg_residual": d.mg_residual,
-            "pc_face_only": d.pc_face_only,
+            "pc_face_only": d.pc_face_only, "object_potential": d.object_potential,
+            "object_charge": d.object_charge,
         }
 
     def phi(self):

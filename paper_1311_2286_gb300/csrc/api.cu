@@ -191,6 +191,7 @@ void plan(cpic_run* r, Planner& P) {
     r->K32 = P.take<float>((size_t)r->nvert * (D == 2 ? 4 : 12));
     r->G32 = P.take<float>((size_t)r->nvert * (D == 2 ? 2 : 4));
     r->rhs_bc = P.take<double>(r->ncell);
+    r->psi = P.take<double>(r->ncell);
     r->jcdf = P.take<double>(r->ncell);
     r->fcdf = r->D == 3 ? P.take<double>((size_t)2 * r->n[1] * r->n[2]) : nullptr;
     r->charge = P.take<unsigned long long>((size_t)c.n_species * r->ncell);
@@ -744,6 +745,7 @@ int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* s
     cpic_run* r = new cpic_run;
     memset(r, 0, sizeof(*r));
     r->solver = CPIC_SOLVER_BICGSTAB;
+    r->floating_face = -1;
     r->push_tile = 1;
     init_geometry_sizes(r, cfg);
     st = setup_levels(r);
@@ -947,6 +949,53 @@ int cpic_get_particles(cpic_run* r, int sp, int64_t room, int64_t* n, int32_t* c
     return CPIC_OK;
 }
 
+int cpic_set_floating(cpic_run* r, int face, double charge0) {
+    CHECK_RUN(r);
+    CHECK_MAP(r);
+    if (r->initialized) {
+        set_error("set_floating: call before cpic_initialize");
+        return CPIC_ERR_STATE;
+    }
+    if ((face != 0 && face != 1) || r->cfg.field_bc[face] != CPIC_BC_DIRICHLET || r->cfg.axisymmetric ||
+        !(charge0 == charge0)) {
+        set_error("set_floating: a Dirichlet face normal to axis 0 of a non-axisymmetric run");
+        return CPIC_ERR_INVALID;
+    }
+    r->floating_face = -1;  // no conductor correction while psi is solved
+    double saved[6];
+    memcpy(saved, r->cfg.field_bc_value, sizeof(saved));
+    const double bg = r->cfg.background;
+    // psi: charge-free space, this face at potential 1, every other Dirichlet face at 0
+    for (int f = 0; f < 6; ++f)
+        if (r->cfg.field_bc[f] == CPIC_BC_DIRICHLET) r->cfg.field_bc_value[f] = f == face ? 1.0 : 0.0;
+    r->cfg.background = 0.0;
+    int st = mg_setup(r);
+    if (!st) {
+        CPIC_CUDA(cudaMemsetAsync(r->charge, 0, sizeof(unsigned long long) * r->cfg.n_species * r->ncell, r->stream));
+        CPIC_CUDA(cudaMemsetAsync(r->lev[0].x, 0, sizeof(double) * r->ncell, r->stream));
+        st = mg_solve(r, 1e-13, 400, true, nullptr, nullptr);
+    }
+    if (!st) {
+        CPIC_CUDA(cudaMemcpyAsync(r->psi, r->lev[0].x, sizeof(double) * r->ncell, cudaMemcpyDeviceToDevice, r->stream));
+        r->floating_face = face;
+        r->float_q0 = charge0;
+        st = launch_floating_capacity(r);
+    }
+    // the run's own solves: the conductor's face at 0 (its potential is added after each solve)
+    memcpy(r->cfg.field_bc_value, saved, sizeof(saved));
+    r->cfg.field_bc_value[face] = 0.0;
+    r->cfg.background = bg;
+    if (!st) st = mg_setup(r);
+    if (st) {
+        r->floating_face = -1;
+        return st;
+    }
+    CPIC_CUDA(cudaMemsetAsync(r->lev[0].x, 0, sizeof(double) * r->ncell, r->stream));
+    invalidate_graphs(r);
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    return CPIC_OK;
+}
+
 int cpic_set_injection(cpic_run* r, int sp, int face, double density, double vth, const double* drift, uint64_t seed) {
     CHECK_RUN(r);
     if (sp < 0 || sp >= r->cfg.n_species || (face != 0 && face != 1) ||
@@ -1089,6 +1138,8 @@ int cpic_get_diag(cpic_run* r, cpic_diag* out) {
     out->mg_cycles = h.mg_cycles;
     out->mg_residual = h.mg_residual;
     out->pc_face_only = r->pc_face_only;
+    out->object_potential = r->floating_face >= 0 ? h.object_potential : 0.0;
+    out->object_charge = r->floating_face >= 0 ? h.object_charge : 0.0;
     return CPIC_OK;
 }
 

@@ -18,6 +18,8 @@ struct FieldGrid {
     int n[3];
     int bc[6];
     double bcv[6];
+    int fface;             // floating conductor's face (-1: none): its Dirichlet value is
+    const double* fphi;    // the conductor potential of the last solve, read on the device
 };
 
 __device__ __forceinline__ double phi_ext(const FieldGrid& g, const double* __restrict__ phi, int i, int j, int k) {
@@ -49,6 +51,7 @@ __device__ __forceinline__ double phi_ext(const FieldGrid& g, const double* __re
 // 3D: G is also written into the three padding words of each vertex's k record (K[12 v + 9 ..
 // 11]), so that the mover's first gather reads k and G in three 16-byte loads per corner.
 __global__ void vertex_field_kernel(FieldGrid g, const double* __restrict__ phi, float* G, float* K) {
+    if (g.fface >= 0) g.bcv[g.fface] = *g.fphi;
     long long nv0 = g.n[0] + 1, nv1 = g.n[1] + 1, nv2 = g.D == 3 ? g.n[2] + 1 : 1;
     long long nvt = nv0 * nv1 * nv2;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvt;
@@ -163,7 +166,85 @@ FieldGrid make_field_grid(const cpic_run* r) {
         g.bc[f] = r->cfg.field_bc[f];
         g.bcv[f] = r->cfg.field_bc_value[f];
     }
+    g.fface = r->floating_face;
+    g.fphi = &r->ctr->object_potential;
     return g;
+}
+
+// Floating conductor on the face normal to axis 0 at side `side` (Sec. III.A-B: an object
+// that collects the particles reaching it and floats to the potential its charge gives).
+// Gauss's law for the conductor: its charge is minus the outward flux of grad phi through
+// its surface, which in the finite-volume scheme is the Dirichlet face flux
+// 2 a^{00}_f (phi_c - phi_b) summed over the face's cells (a^{00} = Omega J g^{00} of the
+// face, cell units). With phi = phi_0 + V psi (phi_0: the solve with the conductor at 0;
+// psi: charge-free, conductor at 1, other Dirichlet values 0), the charge condition
+// Q = -sum 2 a (phi_0 + V psi - V) fixes V = -(Q + G0) / Cpsi, G0 = sum 2 a phi_0,
+// Cpsi = sum 2 a (psi - 1). Sums run in a fixed order (one block).
+struct FloatParams {
+    int n0, n1, n2, side, face, nsp;
+    long long nf;           // faces normal to axis 0
+    const double* a00;      // face coefficient a^{00} of those faces
+    const double* phi;      // cell potential
+    const double* psi;
+    double q0;              // charge before any collection
+    double qw[CPIC_MAX_SPECIES];
+};
+
+__device__ double face_flux_sum(const FloatParams& p, const double* u, double ub) {
+    __shared__ double part[256];
+    const int i = p.side == 0 ? 0 : p.n0 - 1, fi = p.side == 0 ? 0 : p.n0;
+    const long long m = (long long)p.n1 * p.n2;
+    double acc = 0.0;
+    for (long long jk = threadIdx.x; jk < m; jk += blockDim.x) {
+        const long long c = i + (long long)p.n0 * jk;
+        const long long f = fi + (long long)(p.n0 + 1) * jk;
+        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(2.0, p.a00[f]), __dsub_rn(u[c], ub)));
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] = __dadd_rn(part[threadIdx.x], part[threadIdx.x + w]);
+        __syncthreads();
+    }
+    return part[0];
+}
+
+__global__ void floating_kernel(FloatParams p, DevCounters* ctr) {
+    const double g0 = face_flux_sum(p, p.phi, 0.0);
+    if (threadIdx.x == 0) {
+        double q = p.q0;
+        for (int s = 0; s < p.nsp; ++s) q = __dadd_rn(q, __dmul_rn(p.qw[s], (double)ctr->absorbed[s][p.face]));
+        ctr->object_charge = q;
+        ctr->object_potential = -(q + g0) / ctr->float_cpsi;
+    }
+}
+
+__global__ void floating_capacity_kernel(FloatParams p, DevCounters* ctr) {
+    const double c = face_flux_sum(p, p.psi, 1.0);
+    if (threadIdx.x == 0) ctr->float_cpsi = c;
+}
+
+__global__ void floating_axpy_kernel(double* phi, const double* psi, long long n, const DevCounters* ctr) {
+    const double v = ctr->object_potential;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        phi[c] = __fma_rn(v, psi[c], phi[c]);
+}
+
+FloatParams make_float_params(const cpic_run* r) {
+    FloatParams p;
+    p.n0 = r->n[0];
+    p.n1 = r->n[1];
+    p.n2 = r->D == 3 ? r->n[2] : 1;
+    p.face = r->floating_face;
+    p.side = r->floating_face & 1;
+    p.nsp = r->cfg.n_species;
+    p.nf = (long long)(p.n0 + 1) * p.n1 * p.n2;
+    p.a00 = r->lev[0].face[0];
+    p.phi = r->lev[0].x;
+    p.psi = r->psi;
+    p.q0 = r->float_q0;
+    for (int s = 0; s < CPIC_MAX_SPECIES; ++s) p.qw[s] = s < p.nsp ? r->cfg.q[s] * r->cfg.w[s] : 0.0;
+    return p;
 }
 
 }  // namespace
@@ -195,6 +276,25 @@ int launch_rhs(cpic_run* r, double* b) {
     long long nb = (r->ncell + 255) / 256;
     if (nb > 8LL * device_sm_count()) nb = 8LL * device_sm_count();
     rhs_kernel<<<(int)nb, 256, 0, r->stream>>>(p, b);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
+int launch_floating(cpic_run* r) {
+    if (r->floating_face < 0) return CPIC_OK;
+    FloatParams p = make_float_params(r);
+    floating_kernel<<<1, 256, 0, r->stream>>>(p, r->ctr);
+    CPIC_CHECK_LAUNCH();
+    long long nb = (r->ncell + 255) / 256;
+    if (nb > 8LL * device_sm_count()) nb = 8LL * device_sm_count();
+    floating_axpy_kernel<<<(int)nb, 256, 0, r->stream>>>(r->lev[0].x, r->psi, r->ncell, r->ctr);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
+int launch_floating_capacity(cpic_run* r) {
+    FloatParams p = make_float_params(r);
+    floating_capacity_kernel<<<1, 256, 0, r->stream>>>(p, r->ctr);
     CPIC_CHECK_LAUNCH();
     return CPIC_OK;
 }

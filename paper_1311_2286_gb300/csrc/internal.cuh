@@ -57,6 +57,11 @@ struct DevCounters {
     double mg_bnorm;
     int mg_cycles;
     int mg_converged;
+    // floating conductor (cpic_set_floating): its potential and charge after the last solve,
+    // and the flux sum of the unit-potential solution (set once)
+    double object_potential;
+    double object_charge;
+    double float_cpsi;
 };
 
 // Scalars and reduction partials of the Krylov solve (device).
@@ -175,6 +180,9 @@ struct cpic_run {
     double* red;                 // reduction scratch [2 * 1024 + 8]
     int solver;                  // CPIC_SOLVER_* of the stream solve
     int pc_face_only;            // the FP32 V-cycle uses the stencil's face entries only
+    int floating_face;           // face whose conductor floats (cpic_set_floating), -1: none
+    double float_q0;             // its charge before any particle was collected
+    double* psi;                 // potential of the unit-potential conductor in charge-free space
     int push_chunk;              // push kernel: particles per block chunk (0: one wave)
     int push_tile;               // push kernel: shared-memory deposit tile (1) or direct (0)
     cpic::KrylovState* kry;      // device scalars of the Krylov solve
@@ -203,6 +211,10 @@ int launch_geometry(cpic_run* r);
 int launch_vertex_field(cpic_run* r);
 int launch_rhs(cpic_run* r, double* b);
 int launch_field_energy(cpic_run* r);
+// floating conductor: Gauss's-law potential of the face's conductor, then phi += V psi
+int launch_floating(cpic_run* r);
+// flux sum of the face's unit-potential solution (set-up of the floating conductor)
+int launch_floating_capacity(cpic_run* r);
 // push.cu
 int launch_push(cpic_run* r);
 int launch_deposit(cpic_run* r);

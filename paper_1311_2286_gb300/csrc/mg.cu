@@ -1141,6 +1141,8 @@ int enqueue_epilogue(cpic_run* r) {
         gauge_kernel<<<grid_blocks(L0.ncell, 256), 256, 0, r->stream>>>(L0, r->red, RED_BLOCKS, r->sumJ);
         CPIC_CHECK_LAUNCH();
     }
+    int st = launch_floating(r);  // a floating conductor's potential from its charge
+    if (st) return st;
     return launch_field_energy(r);
 }
 

@@ -197,13 +197,14 @@ __device__ __forceinline__ void deposit_warp(const PushParams& p, int s, bool al
             for (int node = 0; node < NN; ++node) q[node] = __reduce_add_sync(peers, q[node]);
         }
     }
-    if (issue) {
+    if (issue) {  // every node, without a per-node test (a zero weight adds nothing)
         unsigned long long* g = p.charge + (long long)s * p.ncell_h + p.origin + off;
 #pragma unroll
-        for (int node = 0; node < NN; ++node) {
-            const int m0 = node % 3, m1 = (node / 3) % 3, m2 = node / 9;
-            const int d = (m0 - 1) + (m1 - 1) * p.hs1 + (D == 3 ? (m2 - 1) * p.hs2 : 0);
-            if (q[node]) atomicAdd(g + d, (unsigned long long)q[node]);
+        for (int m12 = 0; m12 < NN / 3; ++m12) {
+            unsigned long long* row = g + ((m12 % 3) - 1) * p.hs1 + (D == 3 ? (m12 / 3 - 1) * p.hs2 : 0);
+            atomicAdd(row - 1, (unsigned long long)q[3 * m12]);
+            atomicAdd(row, (unsigned long long)q[3 * m12 + 1]);
+            atomicAdd(row + 1, (unsigned long long)q[3 * m12 + 2]);
         }
     }
 }

@@ -63,14 +63,21 @@ def _field_energy_from_device(run, w, geom):
     return 0.5 * float(np.sum(run.phi() * Q))
 
 
-def _run_pair(cpic, w, steps, sort_interval, run=None):
+def _run_pair(cpic, w, steps, sort_interval, run=None, floating=None, trace=None):
     """Device and oracle runs of the same workload; returns per-level field energies and
-    cumulative absorbed counts of both, and the one-step errors."""
+    cumulative absorbed counts of both, and the one-step errors. floating: (face, charge0)
+    of a floating conductor on both sides; trace: a list that receives, per level, the
+    device's and the oracle's conductor potential."""
     if run is None:
         run = cpic.run_from_workload(w, sort_interval=sort_interval, mg_rtol=1e-12, mg_max_cycles=200)
     pic = OraclePIC(w, "fp64", engine="c", threads=THREADS)
+    if floating is not None:
+        run.set_floating(*floating)
+        pic.set_floating(*floating)
     run.initialize()
     pic.initialize()
+    if trace is not None:
+        trace.append((run.diag()["object_potential"], pic.object_potential))
     err0 = _state_error(run, pic, w)
     dev_we, dev_we_check, dev_abs = [run.diag()["W_E"]], [_field_energy_from_device(run, w, pic.geom)], []
     err1 = None
@@ -83,6 +90,8 @@ def _run_pair(cpic, w, steps, sort_interval, run=None):
         dev_we.append(d["W_E"])
         dev_we_check.append(_field_energy_from_device(run, w, pic.geom))
         dev_abs.append(d["absorbed"])
+        if trace is not None:
+            trace.append((d["object_potential"], pic.object_potential))
     ora_we = [h["W_E"] for h in pic.history] + [0.5 * float(np.sum(pic.phi * pic.Q))]
     ora_abs = [h["absorbed"] for h in pic.history]
     return run, pic, err0, err1, np.array(dev_we), np.array(dev_we_check), np.array(ora_we), dev_abs, ora_abs
@@ -149,6 +158,28 @@ def test_cylinder_cycle_matches_oracle(cpic, record_property):
     for r in report:
         print("cylinder cycle current:", r)
     assert any(r["species"] == 1 and r["face"] == 0 and r["device"] > 0 for r in report)  # ions collected
+    run.close()
+
+
+def test_floating_cylinder_matches_oracle(cpic):
+    """Row f1: the reduced cylinder run with the object as a floating conductor (uncharged
+    at start; Gauss's-law potential from the charge it collects, Sec. III.A-B) on the
+    device and in the oracle: the conductor potential agrees at every level (to 1e-3 of its
+    range), its time average within 1%, the object charges negative (electrons are
+    collected faster than ions), and the device's field energy is 1/2 sum phi Q of its own
+    fields."""
+    w = wl.cylinder(**CYL)
+    trace = []
+    run, pic, err0, _, we, we_chk, we_ora, dev_abs, ora_abs = _run_pair(cpic, w, CYL_STEPS, 4, floating=(0, 0.0),
+                                                                         trace=trace)
+    v = np.array(trace)
+    scale = np.max(np.abs(v[:, 1]))
+    assert np.max(np.abs(v[:, 0] - v[:, 1])) <= 1e-3 * scale, np.max(np.abs(v[:, 0] - v[:, 1]))
+    assert abs(v[:, 0].mean() / v[:, 1].mean() - 1.0) <= 0.01
+    assert v[-1, 1] < -0.5 and run.diag()["object_charge"] < 0.0
+    np.testing.assert_allclose(we, we_chk, rtol=1e-12)
+    print("floating cylinder: V(end) device %.6f oracle %.6f, mean %.6f / %.6f, max |dV| %.2e"
+          % (v[-1, 0], v[-1, 1], v[:, 0].mean(), v[:, 1].mean(), np.max(np.abs(v[:, 0] - v[:, 1]))))
     run.close()
 
 
