@@ -320,7 +320,9 @@ typedef struct cpic_tuning {
 } cpic_tuning;
 
 /* Chooses, in this order, the run's cell-sort interval, the particles per block chunk of
- * the push kernel and its deposit tiling: for each candidate, times whole sort cycles of at
+ * the push kernel and its deposit tiling, then (when chunk or tiling changed) the sort
+ * interval again with them (ms_per_step then holds the second pass): for each candidate,
+ * times whole sort cycles of at
  * least trial_steps fixed-field particle steps on the run's own particles (CUDA events on
  * the run's stream), restoring the run's particles, counters and potential from a device
  * snapshot after each trial, so the simulation is unchanged; the fastest setting of each

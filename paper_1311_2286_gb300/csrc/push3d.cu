@@ -225,6 +225,109 @@ __device__ __forceinline__ void predict_axis3(float x, int c, int n, int& cp, fl
     cp = ci;
 }
 
+// Rows a2-a5 for one particle (per lane): b1 gather of k and G at xi^n, kick, predictor, k
+// re-gather, corrector, boundaries (periodic wrap, absorption, spec B reflection). cw: the
+// packed cell (-1: empty slot); t, v: offsets and velocity in, new velocity out; cn, tn: the
+// new cell and offsets; face: -1 (kept) or the face it left by (6: non-finite); ke32: the
+// FP32 product v_old . v_new of the kinetic-energy tally (0 for empty slots).
+template <int K0, int K1, int K2>
+__device__ __forceinline__ void mover3(const PushParams& p, float dtqm, int cw, float* t, float* v, int* cn,
+                                       float* tn, int& face, float& ke32) {
+    constexpr int KIND[3] = {K0, K1, K2};
+    const float hdt = p.hdt, dt = p.dt;
+    const bool active = cw >= 0;
+    int c[3] = {active ? (cw & 1023) : 0, active ? ((cw >> 10) & 1023) : 0, active ? (cw >> 20) : 0};
+    if (!active) t[0] = t[1] = t[2] = v[0] = v[1] = v[2] = 0.0f;
+
+    // a2: b1 gather of k and G at xi^n
+    float kp[9], gp[3];
+    gather3(p, vertex_of<3>(p, c), t, kp, gp);
+    // a3: E^al = -sum_a G^a k^{a al}, kick
+    const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
+#pragma unroll
+    for (int al = 0; al < 3; ++al) {
+        float e = __fmul_rn(kp[al], gp[0]);
+        e = __fmaf_rn(kp[3 + al], gp[1], e);
+        e = __fmaf_rn(kp[6 + al], gp[2], e);
+        v[al] = __fmaf_rn(dtqm, -e, v[al]);
+    }
+    // a4: predictor
+    int cpred[3];
+    float tpred[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float d = __fmul_rn(kp[3 * a], v[0]);
+        d = __fmaf_rn(kp[3 * a + 1], v[1], d);
+        d = __fmaf_rn(kp[3 * a + 2], v[2], d);
+        float x = __fmaf_rn(hdt, d, t[a]);
+        if (!isfinite(x)) x = t[a];
+        if (KIND[a] == K_PER)
+            predict_axis3<K_PER>(x, c[a], p.n[a], cpred[a], tpred[a]);
+        else
+            predict_axis3<K_ABS>(x, c[a], p.n[a], cpred[a], tpred[a]);
+    }
+    float kq[9];
+    gather3(p, vertex_of<3>(p, cpred), tpred, kq, nullptr);
+    // corrector
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float d = __fmul_rn(kq[3 * a], v[0]);
+        d = __fmaf_rn(kq[3 * a + 1], v[1], d);
+        d = __fmaf_rn(kq[3 * a + 2], v[2], d);
+        float x = __fmaf_rn(dt, d, t[a]);
+        if (!isfinite(x)) {
+            bad = true;
+            x = t[a];
+        }
+        int dc;
+        renorm(x, tn[a], dc);
+        cn[a] = c[a] + dc;
+    }
+    // a5: boundaries (periodic wrap, absorption), then spec B after the tally
+    face = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (KIND[a] == K_PER) {
+            cn[a] = wrapi(cn[a], p.n[a]);
+        } else if (KIND[a] == K_ABS && face < 0) {
+            if (cn[a] < 0) face = 2 * a;
+            else if (cn[a] >= p.n[a]) face = 2 * a + 1;
+        }
+    }
+    if (bad) face = 6;
+    ke32 = active ? __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0]))) : 0.0f;
+    if (face < 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (KIND[a] != K_REF || face >= 0 || (cn[a] >= 0 && cn[a] < p.n[a])) continue;
+            const bool below = cn[a] < 0;
+            int c2 = below ? (-cn[a] - 1) : (2 * p.n[a] - 1 - cn[a]);
+            float t2 = __fsub_rn(1.0f, tn[a]);
+            if (t2 >= 1.0f) {
+                t2 = 0.0f;
+                c2 += 1;
+            }
+            if (c2 < 0 || c2 >= p.n[a]) {
+                face = 2 * a + (below ? 0 : 1);
+                continue;
+            }
+            cn[a] = c2;
+            tn[a] = t2;
+            float nn = __fmul_rn(kq[3 * a], kq[3 * a]);
+            float dot = __fmul_rn(v[0], kq[3 * a]);
+            nn = __fmaf_rn(kq[3 * a + 1], kq[3 * a + 1], nn);
+            dot = __fmaf_rn(v[1], kq[3 * a + 1], dot);
+            nn = __fmaf_rn(kq[3 * a + 2], kq[3 * a + 2], nn);
+            dot = __fmaf_rn(v[2], kq[3 * a + 2], dot);
+            const float sf = __fdiv_rn(__fmul_rn(2.0f, dot), nn);
+#pragma unroll
+            for (int al = 0; al < 3; ++al) v[al] = __fmaf_rn(-sf, kq[3 * a + al], v[al]);
+        }
+    }
+    if (!active) face = -2;
+}
+
 template <int K0, int K1, int K2>
 __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
     extern __shared__ unsigned tile_dyn[];  // [P3_TILE_CELLS] low words, then high words
@@ -400,99 +503,11 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
     #pragma unroll
                     for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + i];
                 }
+                int cn[3], face;
+                float tn[3], ke32;
                 const bool active = cw >= 0;
-                int c[3] = {active ? (cw & 1023) : 0, active ? ((cw >> 10) & 1023) : 0, active ? (cw >> 20) : 0};
-                if (!active) t[0] = t[1] = t[2] = v[0] = v[1] = v[2] = 0.0f;
-
-                // a2: b1 gather of k and G at xi^n
-                float kp[9], gp[3];
-                gather3(p, vertex_of<3>(p, c), t, kp, gp);
-                // a3: E^al = -sum_a G^a k^{a al}, kick
-                const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
-    #pragma unroll
-                for (int al = 0; al < 3; ++al) {
-                    float e = __fmul_rn(kp[al], gp[0]);
-                    e = __fmaf_rn(kp[3 + al], gp[1], e);
-                    e = __fmaf_rn(kp[6 + al], gp[2], e);
-                    v[al] = __fmaf_rn(dtqm, -e, v[al]);
-                }
-                // a4: predictor
-                int cpred[3];
-                float tpred[3];
-    #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    float d = __fmul_rn(kp[3 * a], v[0]);
-                    d = __fmaf_rn(kp[3 * a + 1], v[1], d);
-                    d = __fmaf_rn(kp[3 * a + 2], v[2], d);
-                    float x = __fmaf_rn(hdt, d, t[a]);
-                    if (!isfinite(x)) x = t[a];
-                    if (KIND[a] == K_PER)
-                        predict_axis3<K_PER>(x, c[a], p.n[a], cpred[a], tpred[a]);
-                    else
-                        predict_axis3<K_ABS>(x, c[a], p.n[a], cpred[a], tpred[a]);
-                }
-                float kq[9];
-                gather3(p, vertex_of<3>(p, cpred), tpred, kq, nullptr);
-                // corrector
-                bool bad = false;
-                int cn[3];
-                float tn[3];
-    #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    float d = __fmul_rn(kq[3 * a], v[0]);
-                    d = __fmaf_rn(kq[3 * a + 1], v[1], d);
-                    d = __fmaf_rn(kq[3 * a + 2], v[2], d);
-                    float x = __fmaf_rn(dt, d, t[a]);
-                    if (!isfinite(x)) {
-                        bad = true;
-                        x = t[a];
-                    }
-                    int dc;
-                    renorm(x, tn[a], dc);
-                    cn[a] = c[a] + dc;
-                }
-                // a5: boundaries (periodic wrap, absorption), then spec B after the tally
-                int face = -1;
-    #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (KIND[a] == K_PER) {
-                        cn[a] = wrapi(cn[a], p.n[a]);
-                    } else if (KIND[a] == K_ABS && face < 0) {
-                        if (cn[a] < 0) face = 2 * a;
-                        else if (cn[a] >= p.n[a]) face = 2 * a + 1;
-                    }
-                }
-                if (bad) face = 6;
-                const float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
-                if (active) ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
-                if (face < 0) {
-    #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        if (KIND[a] != K_REF || face >= 0 || (cn[a] >= 0 && cn[a] < p.n[a])) continue;
-                        const bool below = cn[a] < 0;
-                        int c2 = below ? (-cn[a] - 1) : (2 * p.n[a] - 1 - cn[a]);
-                        float t2 = __fsub_rn(1.0f, tn[a]);
-                        if (t2 >= 1.0f) {
-                            t2 = 0.0f;
-                            c2 += 1;
-                        }
-                        if (c2 < 0 || c2 >= p.n[a]) {
-                            face = 2 * a + (below ? 0 : 1);
-                            continue;
-                        }
-                        cn[a] = c2;
-                        tn[a] = t2;
-                        float nn = __fmul_rn(kq[3 * a], kq[3 * a]);
-                        float dot = __fmul_rn(v[0], kq[3 * a]);
-                        nn = __fmaf_rn(kq[3 * a + 1], kq[3 * a + 1], nn);
-                        dot = __fmaf_rn(v[1], kq[3 * a + 1], dot);
-                        nn = __fmaf_rn(kq[3 * a + 2], kq[3 * a + 2], nn);
-                        dot = __fmaf_rn(v[2], kq[3 * a + 2], dot);
-                        const float sf = __fdiv_rn(__fmul_rn(2.0f, dot), nn);
-    #pragma unroll
-                        for (int al = 0; al < 3; ++al) v[al] = __fmaf_rn(-sf, kq[3 * a + al], v[al]);
-                    }
-                }
+                mover3<K0, K1, K2>(p, dtqm, cw, t, v, cn, tn, face, ke32);
+                ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
                 const bool alive = active && face < 0;
                 if (active && face >= 0) atomicAdd(&sh_gone[face], 1);  // rare: kept in shared memory
                 store_state3(active, cellp + slot, alive ? (cn[0] | (cn[1] << 10) | (cn[2] << 20)) : -1, tq0 + slot,
@@ -548,6 +563,180 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
     }
 }
 
+// ---------------------------------------------------------------- direct-deposit kernel
+// The same mover, with the b2 deposit going straight into the padded global grid through a
+// per-warp transposition: every lane writes its 27 node weights (spec Q) into its row of the
+// warp's shared buffer; then lane j (j < 27) walks the 32 rows, summing node j over each
+// run of consecutive lanes whose particles share a cell (particles are kept in cell order),
+// and adds the run's sum for node j with one 64-bit atomic when the run ends. A warp whose
+// 32 particles lie in one cell thus issues a single 27-lane atomic instruction; no lane
+// reduction instructions are needed, and the order of integer additions does not change
+// the result. No deposit tile: the kernel needs 28 KB of shared memory per block and runs
+// four blocks per SM.
+constexpr int PD_THREADS = 256;
+constexpr int PD_STRIDE = 28;  // words per lane row: 27 node weights and one zero
+
+__device__ __forceinline__ void deposit_runs3(const PushParams& p, int s, bool alive, const int* c, const float* t,
+                                              unsigned* wq) {
+    const int lane = threadIdx.x & 31;
+    if (!__any_sync(FULL, alive)) return;
+    unsigned w[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) axis_weights(alive ? t[a] : 0.0f, w[a]);
+    // node weights in node order (m0 fastest), four to a 16-byte store; the centre (node 13)
+    // is written last, as 2^24 minus the other 26
+    unsigned* row = wq + lane * PD_STRIDE;
+    unsigned rest = 0, q4[4];
+#pragma unroll
+    for (int node = 0; node < 28; ++node) {
+        unsigned q = 0;
+        if (node < 27 && node != 13) {
+            q = node_weight3(w[0][node % 3], w[1][(node / 3) % 3] * w[2][node / 9]);
+            rest += q;
+        }
+        q4[node & 3] = alive ? q : 0u;
+        if ((node & 3) == 3) reinterpret_cast<uint4*>(row)[node >> 2] = make_uint4(q4[0], q4[1], q4[2], q4[3]);
+    }
+    row[13] = alive ? (1u << QF) - rest : 0u;
+    const int off = alive ? c[0] + c[1] * p.hs1 + c[2] * p.hs2 : -1;
+    const unsigned ends = __ballot_sync(FULL, lane == 31 || __shfl_down_sync(FULL, off, 1) != off);
+    __syncwarp();
+    const int j = lane < 27 ? lane : 27;  // lanes 27-31 read the zero word
+    const int dj = (j % 3 - 1) + ((j / 3) % 3 - 1) * p.hs1 + (j / 9 - 1) * p.hs2;
+    unsigned long long* g = p.charge + (long long)s * p.ncell_h + p.origin + dj;
+    unsigned acc = 0;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        acc += wq[r * PD_STRIDE + j];
+        if ((ends >> r) & 1u) {  // warp-uniform
+            const int o = __shfl_sync(FULL, off, r);
+            if (o >= 0 && lane < 27) atomicAdd(g + o, (unsigned long long)acc);
+            acc = 0;
+        }
+    }
+    __syncwarp();  // the rows are read before the next particle's weights overwrite them
+}
+
+template <int K0, int K1, int K2>
+__global__ void __launch_bounds__(PD_THREADS, 4) push3d_direct_kernel(PushParams p) {
+    __shared__ __align__(16) unsigned qbuf[PD_THREADS / 32][32 * PD_STRIDE];
+    __shared__ int sh_gone[8];  // removed particles of the chunk per face (6: non-finite)
+    const DevCounters* ctr = p.ctr;
+    const int cur = ctr->cur;
+    const int nsp = p.nsp;
+    int cnt[CPIC_MAX_SPECIES];
+    int total = 0;
+#pragma unroll
+    for (int s = 0; s < CPIC_MAX_SPECIES; ++s) {
+        cnt[s] = s < nsp ? (int)ctr->count[s] : 0;
+        total += cnt[s];
+    }
+    if (total == 0) return;
+    int C = ((total + (int)gridDim.x - 1) / (int)gridDim.x + PD_THREADS - 1) / PD_THREADS * PD_THREADS;
+    if (C > P3_CHUNK) C = P3_CHUNK;
+    if (p.chunk > 0) C = p.chunk;
+    const long long T = p.pb.total;
+    unsigned* wq = qbuf[threadIdx.x >> 5];
+
+    for (int ch = blockIdx.x;; ch += gridDim.x) {
+        int s = 0, local = ch;
+        while (s < nsp) {
+            const int nch = (cnt[s] + C - 1) / C;
+            if (local < nch) break;
+            local -= nch;
+            ++s;
+        }
+        if (s >= nsp) break;
+        const int lo = local * C;
+        const int hi = min(lo + C, cnt[s]);
+        const long long b0 = p.pb.base[s];
+        int* __restrict__ cellp = p.pb.cell[cur] + b0;
+        float* __restrict__ tq0 = p.pb.t[cur] + b0;
+        float* __restrict__ vq0 = p.pb.v[cur] + b0;
+        const float dtqm = p.dtqm[s];
+        __syncthreads();  // the previous chunk's tallies are read
+        if (threadIdx.x < 8) sh_gone[threadIdx.x] = 0;
+        __syncthreads();
+
+        long long ke = 0;
+        int i = lo + (int)threadIdx.x;
+        int ncw = -1;
+        float nt[3] = {0.f, 0.f, 0.f}, nv[3] = {0.f, 0.f, 0.f};
+        if (i < hi) {
+            ncw = cellp[i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) nt[a] = tq0[a * T + i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + i];
+        }
+        for (int base = lo; base < hi; base += PD_THREADS) {
+            const int slot = i;
+            const int cw = ncw;
+            float t[3] = {nt[0], nt[1], nt[2]};
+            float v[3] = {nv[0], nv[1], nv[2]};
+            i += PD_THREADS;
+            ncw = -1;
+            if (i < hi) {
+                ncw = cellp[i];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) nt[a] = tq0[a * T + i];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + i];
+            }
+            int cn[3], face;
+            float tn[3], ke32;
+            const bool active = cw >= 0;
+            mover3<K0, K1, K2>(p, dtqm, cw, t, v, cn, tn, face, ke32);
+            ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
+            const bool alive = active && face < 0;
+            if (active && face >= 0) atomicAdd(&sh_gone[face], 1);
+            store_state3(active, cellp + slot, alive ? (cn[0] | (cn[1] << 10) | (cn[2] << 20)) : -1, tq0 + slot,
+                         tq0 + T + slot, tq0 + 2 * T + slot, tn, vq0 + slot, vq0 + T + slot, vq0 + 2 * T + slot, v);
+            deposit_runs3(p, s, alive, cn, tn, wq);  // a6
+        }
+        ke = warp_sum_ll(ke);
+        if ((threadIdx.x & 31) == 0 && ke) atomicAdd((unsigned long long*)&p.ctr->ke_fp[s], (unsigned long long)ke);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            DevCounters* cw = p.ctr;
+            long long removed = 0;
+            for (int f = 0; f < 7; ++f) {
+                const int g = sh_gone[f];
+                removed += g;
+                if (!g) continue;
+                if (f < 6)
+                    atomicAdd((unsigned long long*)&cw->absorbed[s][f], (unsigned long long)g);
+                else
+                    atomicAdd((unsigned long long*)&cw->nonfinite, (unsigned long long)g);
+            }
+            if (removed) atomicAdd((unsigned long long*)&cw->alive[s], (unsigned long long)(-removed));
+        }
+    }
+}
+
+template <int K0, int K1, int K2>
+int launch_push3d_direct_t(cpic_run* r, const PushParams& p) {
+    static std::atomic<int> per_sm[64];
+    int dev = 0;
+    CPIC_CUDA(cudaGetDevice(&dev));
+    std::atomic<int>& cache = per_sm[dev & 63];
+    int b = cache.load(std::memory_order_acquire);
+    if (b <= 0) {
+        CPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, push3d_direct_kernel<K0, K1, K2>, PD_THREADS, 0));
+        if (b < 1) b = 1;
+        cache.store(b, std::memory_order_release);
+    }
+    const long long occ = (long long)b * device_sm_count();
+    long long tot = 0;
+    for (int s = 0; s < r->cfg.n_species; ++s) tot += r->pb.capacity[s];
+    long long blocks = (tot + PD_THREADS - 1) / PD_THREADS;
+    if (blocks > occ) blocks = occ;
+    if (blocks < 1) blocks = 1;
+    push3d_direct_kernel<K0, K1, K2><<<(int)blocks, PD_THREADS, 0, r->stream>>>(p);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
 template <int K0, int K1, int K2>
 int launch_push3d_t(cpic_run* r, const PushParams& p) {
     constexpr size_t smem = sizeof(unsigned) * 2 * P3_TILE_CELLS;
@@ -580,8 +769,10 @@ int launch_push3d_t(cpic_run* r, const PushParams& p) {
 // for others (the caller then takes the generic kernel)
 int launch_push3d(cpic_run* r, const PushParams& p) {
     const int k0 = p.pbc[0], k1 = p.pbc[2], k2 = p.pbc[4];
-    if (k0 == K_ABS && k1 == K_REF && k2 == K_PER) return launch_push3d_t<K_ABS, K_REF, K_PER>(r, p);
-    if (k0 == K_PER && k1 == K_PER && k2 == K_PER) return launch_push3d_t<K_PER, K_PER, K_PER>(r, p);
+    if (k0 == K_ABS && k1 == K_REF && k2 == K_PER)
+        return p.tile ? launch_push3d_t<K_ABS, K_REF, K_PER>(r, p) : launch_push3d_direct_t<K_ABS, K_REF, K_PER>(r, p);
+    if (k0 == K_PER && k1 == K_PER && k2 == K_PER)
+        return p.tile ? launch_push3d_t<K_PER, K_PER, K_PER>(r, p) : launch_push3d_direct_t<K_PER, K_PER, K_PER>(r, p);
     return CPIC_ERR_NOT_BUILT;
 }
 

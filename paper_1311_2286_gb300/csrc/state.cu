@@ -153,12 +153,26 @@ int cpic_autotune(cpic_run* r, int trial_steps, cpic_tuning* out) {
             best_tile = t;
         }
     }
+    // 4. the sort interval once more, with the chunking and tiling chosen (the first pass
+    //    ran with the tiling the run had; the best interval depends on the push's cost)
+    if (!st) st = cpic_set_push_tuning(r, best_chunk, best_tile);
+    if (!st && (best_chunk != saved_chunk || best_tile != saved_tile)) {
+        best = r->cfg.sort_interval;
+        best_ms = 0.0f;
+        for (int c = 0; !st && c < CPIC_TUNE_CANDIDATES; ++c) {
+            r->cfg.sort_interval = intervals[c];
+            st = tune_trial(r, buf, saved_cur, trial_steps, a, b, &out->ms_per_step[c]);
+            if (!st && (best_ms == 0.0f || out->ms_per_step[c] < best_ms)) {
+                best_ms = out->ms_per_step[c];
+                best = intervals[c];
+            }
+        }
+        r->cfg.sort_interval = best;
+    }
     r->steps_since_sort = saved_since;
     if (st) {
         r->cfg.sort_interval = saved_interval;
         cpic_set_push_tuning(r, saved_chunk, saved_tile);
-    } else {
-        cpic_set_push_tuning(r, best_chunk, best_tile);
     }
     out->sort_interval = r->cfg.sort_interval;
     out->chunk = r->push_chunk;

@@ -88,9 +88,10 @@ def test_vertex_field_bit_exact(cpic, case):
     run.close()
 
 
-def _push_case(cpic, w, phi, sort_first=False):
+def _push_case(cpic, w, phi, sort_first=False, tile=1):
     g, per = _geom(w)
     run = cpic.run_from_workload(w)
+    run.set_push_tuning(0, tile)
     if sort_first:
         run.sort()
     run.set_phi(phi)
@@ -108,17 +109,19 @@ def _push_case(cpic, w, phi, sort_first=False):
 
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("sort_first", [False, True])
-def test_push_bit_exact_vs_replay(cpic, case, sort_first):
+@pytest.mark.parametrize("tile", [1, 0])
+def test_push_bit_exact_vs_replay(cpic, case, sort_first, tile):
     """a2-a6: after one push, every particle's cell, offsets and velocity equal the FP32
     replay bit for bit; absorbed counts per face match; the fixed-point charge equals the
     oracle's spec-Q deposit of the replayed particles exactly; the kinetic-energy
-    fixed-point sum matches exactly."""
+    fixed-point sum matches exactly. Both deposit forms of the push kernels (shared-memory
+    tile, and the direct form: in 3D the kernel with the per-warp transposition)."""
     w = CASES[case]()
     rng = np.random.default_rng(2)
     phi = wl.random_field(rng, tuple(reversed(w.n)), 0.5)
     if case in DIRICHLET_AXIS0:
         phi = phi + np.linspace(-5, 0, w.n[0])
-    g, per, pre, post, charge, d, k32, G32 = _push_case(cpic, w, phi, sort_first)
+    g, per, pre, post, charge, d, k32, G32 = _push_case(cpic, w, phi, sort_first, tile)
     ke_total = 0.0
     D = w.dim
     for s, sp in enumerate(w.species):
@@ -612,13 +615,15 @@ def test_cluster_and_kernel_solvers_agree(cpic, monkeypatch):
         assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) <= 1e-10
 
 
-def test_full_size_sphere_push_parity(cpic):
+@pytest.mark.parametrize("tile", [1, 0])
+def test_full_size_sphere_push_parity(cpic, tile):
     """The 3D configuration's grid (128^3 shell, reflecting caps, the push kernel the bench
     times) with 1M + 1M device-loaded particles after the start-up solve: the vertex k
     table and the vertex field equal the oracle's (spec M from the vertex map, spec G from
     the device's potential), and one push is replayed for every particle — cells, offsets and velocities bit for bit, absorbed
     counts per face — and the ions' fixed-point charge equals the oracle's deposit."""
     run = cpic.sphere_run_device(128, 128, 128, 1_000_000, sort_interval=0, host_map=True)
+    run.set_push_tuning(0, tile)
     w = wl.sphere(128, 128, 128, npart_per_species=1_000_000, host_particles=False)
     run.vertex_field()
     k32, G32 = run.vertex_tables()
