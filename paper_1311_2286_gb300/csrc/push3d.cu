@@ -599,7 +599,8 @@ __device__ __forceinline__ void deposit_runs3(const PushParams& p, int s, bool a
     }
     row[13] = alive ? (1u << QF) - rest : 0u;
     const int off = alive ? c[0] + c[1] * p.hs1 + c[2] * p.hs2 : -1;
-    const unsigned ends = __ballot_sync(FULL, lane == 31 || __shfl_down_sync(FULL, off, 1) != off);
+    const int next = __shfl_down_sync(FULL, off, 1);  // every lane takes part (lane 31 gets its own)
+    const unsigned ends = __ballot_sync(FULL, lane == 31 || next != off);
     __syncwarp();
     const int j = lane < 27 ? lane : 27;  // lanes 27-31 read the zero word
     const int dj = (j % 3 - 1) + ((j / 3) % 3 - 1) * p.hs1 + (j / 9 - 1) * p.hs2;
