@@ -185,6 +185,15 @@ int cpic_get_particles(cpic_run* run, int sp, int64_t room, int64_t* n, int32_t*
 int cpic_set_injection(cpic_run* run, int sp, int face, double density, double vth,
                        const double* drift, uint64_t seed);
 
+/* Uniform magnetic field B0 (host, 3 doubles in physical space; NULL or zero: none), for
+ * the magnetised mover of Sec. II.B.4: the kick of eq. (step1) with the v x B term, taken
+ * by the Boris split (half kick, rotation, half kick) with t = (dt/2)(q/m) B0 and
+ * s = 2 t / (1 + |t|^2); the positions advance as before (the hybrid predictor-corrector
+ * with v^{n+1/2}; in 2D the velocity keeps three components). The start-up kick of
+ * cpic_initialize then takes the Boris step over -dt/2. Magnetised runs push with the
+ * generic particle kernel. Invalidates the run's captured step graphs. */
+int cpic_set_magnetic_field(cpic_run* run, const double* B);
+
 /* Floating conductor (Sec. III.A-B: the object collects the particles that reach it and
  * charges up to a floating potential; Figs. of the wall and sphere potential against time).
  * From now on the Dirichlet face `face` (0 or 1: the ends of axis 0, e.g. the object at

@@ -64,9 +64,21 @@ def _renorm(x):
     return c.astype(np.int64), f
 
 
-def push64(idx, t, v, k, G, dt, qm, n, pbc, return_kicked=False):
+def boris64(v, E3, h, B):
+    """Boris step in FP64 (eq. (step1) with a uniform B0, v x B averaged over the step):
+    v- = v + h E; v' = v- + v- x t; v+ = v- + v' x s; v + = v+ + h E, with t = h B0,
+    s = 2 t / (1 + |t|^2) and h = dt q/m / 2. v, E3: (3, n)."""
+    t = h * np.asarray(B, dtype=np.float64)
+    s = 2.0 * t / (1.0 + float(np.dot(t, t)))
+    vm = v + h * E3
+    vp = vm + np.cross(vm.T, t).T
+    return vm + np.cross(vp.T, s).T + h * E3
+
+
+def push64(idx, t, v, k, G, dt, qm, n, pbc, return_kicked=False, B=None):
     """One FP64 push. idx (D, n) int, t (D, n), v (3, n); k: vertex table (..., a, alpha);
-    G: vertex table (..., a); qm: q/m per particle (n,) or scalar.
+    G: vertex table (..., a); qm: q/m per particle (n,) or scalar; B: uniform magnetic
+    field (3,) or None (the kick is then v += dt q/m E; with B, the Boris step).
     Returns (idx, t, v, face) with face = -1 alive or 2a+side for removed particles, plus
     the kicked velocity before any reflection when return_kicked."""
     D = idx.shape[0]
@@ -76,7 +88,12 @@ def push64(idx, t, v, k, G, dt, qm, n, pbc, return_kicked=False):
     kp = gather(k, idx, t)  # (n, a, alpha)
     gp = gather(G, idx, t)  # (n, a)
     E = -np.einsum("pa,pab->pb", gp, kp)  # (n, alpha), alpha < D
-    v[:D] = v[:D] + dt * np.asarray(qm) * E.T
+    if B is not None and np.any(np.asarray(B)):
+        E3 = np.zeros_like(v)
+        E3[:D] = E.T
+        v = boris64(v, E3, 0.5 * dt * np.asarray(qm), B)
+    else:
+        v[:D] = v[:D] + dt * np.asarray(qm) * E.T
     # predictor
     d = np.einsum("pab,bp->ap", kp, v[:D])
     cpred, tpred = _renorm(t + 0.5 * dt * d)
@@ -130,13 +147,18 @@ def push64(idx, t, v, k, G, dt, qm, n, pbc, return_kicked=False):
     return inew, tn, v, face
 
 
-def kick64(idx, t, v, k, G, coef):
-    """Gather and kick only: v += coef * E (used for the leapfrog start-up half step)."""
+def kick64(idx, t, v, k, G, coef, B=None):
+    """Gather and kick only: v += coef * E (used for the leapfrog start-up half step), coef
+    = fraction * dt q/m; with a uniform B, the Boris step over that fraction of dt."""
     D = idx.shape[0]
     v = np.array(v, dtype=np.float64)
     kp = gather(k, idx.astype(np.int64), np.asarray(t, dtype=np.float64))
     gp = gather(G, idx.astype(np.int64), np.asarray(t, dtype=np.float64))
     E = -np.einsum("pa,pab->pb", gp, kp)
+    if B is not None and np.any(np.asarray(B)):
+        E3 = np.zeros_like(v)
+        E3[:D] = E.T
+        return boris64(v, E3, 0.5 * np.asarray(coef), B)
     v[:D] = v[:D] + np.asarray(coef) * E.T
     return v
 
@@ -158,9 +180,9 @@ def _lib():
         lib = ctypes.CDLL(path)
         P = ctypes.c_void_p
         lib.replay_push.argtypes = [ctypes.c_int, P, P, ctypes.c_long, P, P, P, P, P,
-                                    ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P]
+                                    ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P, P]
         lib.replay_push.restype = None
-        lib.replay_kick.argtypes = [ctypes.c_int, P, ctypes.c_long, P, P, P, P, P, ctypes.c_float]
+        lib.replay_kick.argtypes = [ctypes.c_int, P, ctypes.c_long, P, P, P, P, P, ctypes.c_float, P]
         lib.replay_kick.restype = None
         _LIB = lib
     return _LIB
@@ -170,10 +192,23 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def push32(idx, t32, v32, k32, G32, n, pbc, dtqm, hdt, dt):
+def boris_constants32(dt, qm, B, fraction=1.0):
+    """FP32 Boris constants (h, t0, t1, t2, s0, s1, s2) of a kick over fraction * dt:
+    h = dt q/m / 2, t = h B0, s = 2 t / (1 + |t|^2), computed in FP64 and rounded once;
+    None without a field."""
+    if B is None or not np.any(np.asarray(B, dtype=np.float64)):
+        return None
+    h = 0.5 * fraction * dt * qm
+    t = h * np.asarray(B, dtype=np.float64)
+    s = 2.0 * t / (1.0 + float(np.dot(t, t)))
+    return np.asarray([h, *t, *s], dtype=np.float32)
+
+
+def push32(idx, t32, v32, k32, G32, n, pbc, dtqm, hdt, dt, boris=None):
     """FP32 replay of one push. Arguments as push64 but float32 tables (numpy vertex
     layout, k32 (..., a, alpha), G32 (..., a)) and float32 coefficients
-    dtqm = float32(dt q / m), hdt = float32(dt / 2), dt = float32(dt).
+    dtqm = float32(dt q / m), hdt = float32(dt / 2), dt = float32(dt); boris: the
+    boris_constants32 of a magnetised run (None: no field).
     Returns (idx, t, v, face, ke_fp)."""
     D = idx.shape[0]
     np_ = idx.shape[1]
@@ -186,12 +221,14 @@ def push32(idx, t32, v32, k32, G32, n, pbc, dtqm, hdt, dt):
     pb = np.asarray(list(pbc) + [0] * (6 - len(pbc)), dtype=np.int32)
     face = np.empty(np_, dtype=np.int32)
     ke = np.empty(np_, dtype=np.int64)
+    bc = None if boris is None else np.ascontiguousarray(boris, dtype=np.float32)
     _lib().replay_push(D, _ptr(nn), _ptr(pb), np_, _ptr(idx_c), _ptr(t_c), _ptr(v_c), _ptr(K), _ptr(G),
-                       np.float32(dtqm), np.float32(hdt), np.float32(dt), _ptr(face), _ptr(ke))
+                       np.float32(dtqm), np.float32(hdt), np.float32(dt), _ptr(face), _ptr(ke),
+                       None if bc is None else _ptr(bc))
     return idx_c, t_c, v_c, face, ke
 
 
-def kick32(idx, t32, v32, k32, G32, n, coef):
+def kick32(idx, t32, v32, k32, G32, n, coef, boris=None):
     D = idx.shape[0]
     idx_c = np.ascontiguousarray(idx, dtype=np.int32)
     t_c = np.ascontiguousarray(t32, dtype=np.float32)
@@ -199,8 +236,9 @@ def kick32(idx, t32, v32, k32, G32, n, coef):
     K = np.ascontiguousarray(k32, dtype=np.float32).reshape(-1)
     G = np.ascontiguousarray(G32, dtype=np.float32).reshape(-1)
     nn = np.asarray(list(n) + [1] * (3 - D), dtype=np.int32)
+    bc = None if boris is None else np.ascontiguousarray(boris, dtype=np.float32)
     _lib().replay_kick(D, _ptr(nn), idx.shape[1], _ptr(idx_c), _ptr(t_c), _ptr(v_c), _ptr(K), _ptr(G),
-                       np.float32(coef))
+                       np.float32(coef), None if bc is None else _ptr(bc))
     return v_c
 
 
@@ -219,7 +257,7 @@ def _lib64():
         lib = ctypes.CDLL(build_pic64())
         P = ctypes.c_void_p
         lib.oracle_push64.argtypes = [ctypes.c_int, P, P, ctypes.c_long, P, P, P, P, P, ctypes.c_double,
-                                      ctypes.c_double, P, P, ctypes.c_int]
+                                      ctypes.c_double, P, P, ctypes.c_int, P]
         lib.oracle_push64.restype = None
         lib.oracle_deposit64.argtypes = [ctypes.c_int, P, P, ctypes.c_long, P, P, P, ctypes.c_int]
         lib.oracle_deposit64.restype = ctypes.c_int
@@ -234,7 +272,7 @@ def openmp_threads():
     return int(_lib64().oracle_openmp_threads())
 
 
-def push64_c(idx, t, v, k, G, dt, qm, n, pbc, threads=1, inplace=False):
+def push64_c(idx, t, v, k, G, dt, qm, n, pbc, threads=1, inplace=False, B=None):
     """push64 as C loops. qm is a scalar. Returns (idx, t, v, face, vdot) with vdot the
     per-particle v^{n-1/2} . v^{n+1/2} (kicked velocity, before any reflection). With
     inplace, idx (int64), t and v (float64), C-contiguous, are updated and returned."""
@@ -254,6 +292,8 @@ def push64_c(idx, t, v, k, G, dt, qm, n, pbc, threads=1, inplace=False):
     pb = np.asarray(list(pbc) + [0] * (6 - len(pbc)), dtype=np.int32)
     face = np.empty(np_, dtype=np.int32)
     vdot = np.empty(np_, dtype=np.float64)
+    Bv = None if B is None or not np.any(np.asarray(B)) else np.ascontiguousarray(B, dtype=np.float64)
     _lib64().oracle_push64(D, _ptr(nn), _ptr(pb), np_, _ptr(idx_c), _ptr(t_c), _ptr(v_c), _ptr(K), _ptr(Gc),
-                           float(dt), float(qm), _ptr(face), _ptr(vdot), int(threads))
+                           float(dt), float(qm), _ptr(face), _ptr(vdot), int(threads),
+                           None if Bv is None else _ptr(Bv))
     return idx_c, t_c, v_c, face.astype(np.int64), vdot

@@ -85,6 +85,7 @@ class OraclePIC:
         self.history = []
         self.injected = [0] * len(self.species)
         self._face_area = {}
+        self.B0 = getattr(wl, "B0", None)  # uniform magnetic field: Boris kick
 
     # ---- steps ---------------------------------------------------------------------
     def charge(self):
@@ -165,9 +166,10 @@ class OraclePIC:
         for sp in self.species:
             qm = sp.q / sp.m
             if self.precision == "fp64":
-                sp.v = mover.kick64(sp.idx, sp.t, sp.v, k, G, -0.5 * self.dt * qm)
+                sp.v = mover.kick64(sp.idx, sp.t, sp.v, k, G, -0.5 * self.dt * qm, B=self.B0)
             else:
-                sp.v = mover.kick32(sp.idx, sp.t, sp.v, k, G, self.n, np.float32(-0.5 * self.dt * qm))
+                sp.v = mover.kick32(sp.idx, sp.t, sp.v, k, G, self.n, np.float32(-0.5 * self.dt * qm),
+                                    boris=mover.boris_constants32(self.dt, qm, self.B0, -0.5))
 
     def step(self, solve: bool = True):
         """One PIC cycle. solve=False holds the field fixed (mover, injection and deposit
@@ -182,17 +184,18 @@ class OraclePIC:
                 sp.t = np.ascontiguousarray(sp.t, dtype=np.float64)
                 sp.v = np.ascontiguousarray(sp.v, dtype=np.float64)
                 idx, t, v, face, vdot = mover.push64_c(sp.idx, sp.t, sp.v, k, G, self.dt, qm, self.n, self.pbc,
-                                                       self.threads, inplace=True)
+                                                       self.threads, inplace=True, B=self.B0)
                 ke.append(0.5 * sp.m * sp.w * float(np.sum(vdot)))
             elif self.precision == "fp64":
                 vold = sp.v
                 idx, t, v, face, vk = mover.push64(sp.idx, sp.t, sp.v, k, G, self.dt, qm, self.n, self.pbc,
-                                                   return_kicked=True)
+                                                   return_kicked=True, B=self.B0)
                 ke.append(0.5 * sp.m * sp.w * float(np.sum(vold * vk)))
             else:
                 idx, t, v, face, kefp = mover.push32(
                     sp.idx, sp.t, sp.v, k, G, self.n, self.pbc,
-                    np.float32(self.dt * qm), np.float32(0.5 * self.dt), np.float32(self.dt))
+                    np.float32(self.dt * qm), np.float32(0.5 * self.dt), np.float32(self.dt),
+                    boris=mover.boris_constants32(self.dt, qm, self.B0))
                 ke.append(0.5 * sp.m * sp.w * float(np.ldexp(float(kefp.sum()), -24)))
             alive = face < 0
             if np.all(alive):

@@ -5,8 +5,9 @@
  * The definitions are those of mover.py::push64 and deposit.py::deposit_exact, written as a
  * loop over particles so that long oracle runs (the OML current check, whole-run
  * comparisons with the device, the CPU baseline) finish in seconds:
- *   push (Sec. II.B.4, eqs. (step1)-(step4), B0 = 0): b1 gather (eqs. (vvp), (Wvp), (b1))
- *     of k and of the logical field G at xi^n; E = -k^T G; v += dt (q/m) E; predictor
+ *   push (Sec. II.B.4, eqs. (step1)-(step4)): b1 gather (eqs. (vvp), (Wvp), (b1))
+ *     of k and of the logical field G at xi^n; E = -k^T G; v += dt (q/m) E (with a
+ *     uniform B0: the Boris step); predictor
  *     xi' = xi^n + dt/2 k(xi^n) v (clamped into a non-periodic axis); k(xi') by b1
  *     gather; corrector xi^{n+1} = xi^n + dt k(xi') v; periodic wrap, absorption (a cell
  *     index < 0 or >= N on an absorbing axis removes the particle), specular reflection
@@ -82,8 +83,24 @@ static long wrap(long c, long n) {
     return r < 0 ? r + n : r;
 }
 
+/* Boris step (FP64, the numpy form's order): v- = v + h E, v' = v- + v- x t,
+ * v+ = v- + v' x s, v = v+ + h E, t = h B, s = 2 t / (1 + |t|^2), h = dt q/m / 2 */
+static void boris64(double* v, const double* E, double h, const double* B) {
+    double t[3], s[3], m[3], q[3];
+    for (int a = 0; a < 3; ++a) t[a] = h * B[a];
+    const double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    for (int a = 0; a < 3; ++a) s[a] = 2.0 * t[a] / (1.0 + tt);
+    for (int a = 0; a < 3; ++a) m[a] = v[a] + h * E[a];
+    q[0] = m[0] + (m[1] * t[2] - m[2] * t[1]);
+    q[1] = m[1] + (m[2] * t[0] - m[0] * t[2]);
+    q[2] = m[2] + (m[0] * t[1] - m[1] * t[0]);
+    v[0] = m[0] + (q[1] * s[2] - q[2] * s[1]) + h * E[0];
+    v[1] = m[1] + (q[2] * s[0] - q[0] * s[2]) + h * E[1];
+    v[2] = m[2] + (q[0] * s[1] - q[1] * s[0]) + h * E[2];
+}
+
 static void push_one(int D, const int* n, const int* pbc, const double* K, const double* G, double dt, double qm,
-                     long* c, double* t, double* v, int* face_out, double* vdot_out) {
+                     const double* B, long* c, double* t, double* v, int* face_out, double* vdot_out) {
     double kp[9], gp[3], E[3], vold[3];
     gather(D, n, K, D * D, c, t, kp);
     gather(D, n, G, D, c, t, gp);
@@ -93,8 +110,14 @@ static void push_one(int D, const int* n, const int* pbc, const double* K, const
         E[b] = -e;
     }
     for (int q = 0; q < 3; ++q) vold[q] = v[q];
-    const double dtqm = dt * qm;
-    for (int b = 0; b < D; ++b) v[b] = v[b] + dtqm * E[b];
+    if (B) {
+        double E3[3] = {0.0, 0.0, 0.0};
+        for (int b = 0; b < D; ++b) E3[b] = E[b];
+        boris64(v, E3, 0.5 * dt * qm, B);
+    } else {
+        const double dtqm = dt * qm;
+        for (int b = 0; b < D; ++b) v[b] = v[b] + dtqm * E[b];
+    }
     /* predictor: in 2D only the in-plane velocity moves xi */
     long ip[3];
     double tp[3];
@@ -170,7 +193,7 @@ static void push_one(int D, const int* n, const int* pbc, const double* K, const
  * velocity, before any reflection). */
 void oracle_push64(int D, const int* n, const int* pbc, long np, int64_t* idx, double* t, double* v,
                    const double* K, const double* G, double dt, double qm, int32_t* face, double* vdot,
-                   int nthreads) {
+                   int nthreads, const double* B) {
     if (nthreads < 1) nthreads = 1;
 #pragma omp parallel for schedule(static) num_threads(nthreads)
     for (long p = 0; p < np; ++p) {
@@ -182,7 +205,7 @@ void oracle_push64(int D, const int* n, const int* pbc, long np, int64_t* idx, d
         }
         for (int q = 0; q < 3; ++q) vv[q] = v[q * np + p];
         int f;
-        push_one(D, n, pbc, K, G, dt, qm, c, tt, vv, &f, &vdot[p]);
+        push_one(D, n, pbc, K, G, dt, qm, B, c, tt, vv, &f, &vdot[p]);
         for (int a = 0; a < D; ++a) {
             idx[a * np + p] = c[a];
             t[a * np + p] = tt[a];

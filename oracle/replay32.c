@@ -2,7 +2,8 @@
  * the test suite, the smoke check and the benchmark's CPU-baseline leg may load it.
  *
  * Sec. II.B.4, eqs. (hybridx), (step1)-(step4): full-step kick with the field gathered at
- * xi^n (eq. (step1); unmagnetised, so the Boris rotation is the identity), predictor
+ * xi^n (eq. (step1); without a magnetic field a single fmaf per component, with a uniform
+ * B0 the Boris step below), predictor
  * xi' = xi^n + dt/2 k(xi^n) v^{n+1/2} (eq. (step2)), k re-interpolated at xi' with b1
  * weights (eq. (step3)), corrector xi^{n+1} = xi^n + dt k(xi') v^{n+1/2} (eq. (step4)).
  * b1 weights and vertex interpolation: Sec. II.B.2 eqs. (vvp), (Wvp), (b1).
@@ -50,6 +51,25 @@ static void renorm(float x, float* f, int* c) {
     *c = (int)cf;
 }
 
+/* Boris step with a uniform B0 (eq. (step1) with the magnetic term), FP32 in this order:
+ * v- = v + h E; v' = v- + v- x t; v+ = v- + v' x s; v = v+ + h E, each cross-product
+ * component computed as fmaf(a_y, b_z, -(a_z * b_y)) and added to the left vector's
+ * component. bc = {h, t0, t1, t2, s0, s1, s2}; E has three components (E_z = 0 in 2D). */
+static void boris32(float* v, const float* E, const float* bc) {
+    const float h = bc[0];
+    const float* t = bc + 1;
+    const float* s = bc + 4;
+    float m[3], q[3], w[3];
+    for (int al = 0; al < 3; ++al) m[al] = fmaf(h, E[al], v[al]);
+    q[0] = m[0] + fmaf(m[1], t[2], -(m[2] * t[1]));
+    q[1] = m[1] + fmaf(m[2], t[0], -(m[0] * t[2]));
+    q[2] = m[2] + fmaf(m[0], t[1], -(m[1] * t[0]));
+    w[0] = m[0] + fmaf(q[1], s[2], -(q[2] * s[1]));
+    w[1] = m[1] + fmaf(q[2], s[0], -(q[0] * s[2]));
+    w[2] = m[2] + fmaf(q[0], s[1], -(q[1] * s[0]));
+    for (int al = 0; al < 3; ++al) v[al] = fmaf(h, E[al], w[al]);
+}
+
 /* vertex table index of vertex (i, j[, k]) with N_a + 1 vertices per axis */
 static long vtx(int D, const int* n, const int* c) {
     long v = c[D - 1];
@@ -84,7 +104,7 @@ static void gather(int D, const int* n, const float* Q, int nq, const int* c, co
  * ke = fmaf(vo2, v2, fmaf(vo1, v1, vo0 * v0)) (spec D). */
 void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* t, float* v,
                  const float* K, const float* G, float dtqm, float hdt, float dt, int* face,
-                 long long* ke_fp) {
+                 long long* ke_fp, const float* boris) {
     for (long p = 0; p < np; ++p) {
         int c[3];
         float tt[3], vv[3], vo[3];
@@ -97,12 +117,16 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
         float kp[9], gp[3];
         gather(D, n, K, D * D, c, tt, kp);
         gather(D, n, G, D, c, tt, gp);
+        float E[3] = {0.0f, 0.0f, 0.0f};
         for (int al = 0; al < D; ++al) {
             float e = kp[0 * D + al] * gp[0];
             for (int a = 1; a < D; ++a) e = fmaf(kp[a * D + al], gp[a], e);
-            e = -e;
-            vv[al] = fmaf(dtqm, e, vv[al]);
+            E[al] = -e;
         }
+        if (boris)
+            boris32(vv, E, boris);
+        else
+            for (int al = 0; al < D; ++al) vv[al] = fmaf(dtqm, E[al], vv[al]);
         /* predictor */
         int cp[3];
         float tp[3];
@@ -203,7 +227,7 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
 /* Half kick (leapfrog start-up, v^{-1/2} = v^0 - dt/2 q/m E(xi^0)): only the gather and
  * kick of the push, with the given (negative) coefficient. */
 void replay_kick(int D, const int* n, long np, const int* idx, const float* t, float* v,
-                 const float* K, const float* G, float coef) {
+                 const float* K, const float* G, float coef, const float* boris) {
     for (long p = 0; p < np; ++p) {
         int c[3];
         float tt[3];
@@ -214,11 +238,19 @@ void replay_kick(int D, const int* n, long np, const int* idx, const float* t, f
         float kp[9], gp[3];
         gather(D, n, K, D * D, c, tt, kp);
         gather(D, n, G, D, c, tt, gp);
+        float E[3] = {0.0f, 0.0f, 0.0f};
         for (int al = 0; al < D; ++al) {
             float e = kp[0 * D + al] * gp[0];
             for (int a = 1; a < D; ++a) e = fmaf(kp[a * D + al], gp[a], e);
-            e = -e;
-            v[al * np + p] = fmaf(coef, e, v[al * np + p]);
+            E[al] = -e;
+        }
+        if (boris) {
+            float vv[3];
+            for (int al = 0; al < 3; ++al) vv[al] = v[al * np + p];
+            boris32(vv, E, boris);
+            for (int al = 0; al < 3; ++al) v[al * np + p] = vv[al];
+        } else {
+            for (int al = 0; al < D; ++al) v[al * np + p] = fmaf(coef, E[al], v[al * np + p]);
         }
     }
 }

@@ -148,6 +148,7 @@ _SIGS = {
     "cpic_load_particles": ([P, ctypes.c_int, ctypes.c_int64, P, P, P], ctypes.c_int),
     "cpic_get_particles": ([P, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), P, P, P], ctypes.c_int),
     "cpic_set_floating": ([P, ctypes.c_int, ctypes.c_double], ctypes.c_int),
+    "cpic_set_magnetic_field": ([P, P], ctypes.c_int),
     "cpic_set_injection": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, ctypes.c_uint64],
                            ctypes.c_int),
     "cpic_initialize": ([P], ctypes.c_int),
@@ -391,6 +392,11 @@ class Run:
         run.nvert = int(np.prod([x + 1 for x in run.n]))
         return run
 
+    def set_magnetic_field(self, B):
+        """cpic_set_magnetic_field: uniform B0 (3 components, physical space)."""
+        b = np.ascontiguousarray(B, dtype=np.float64)
+        check(load().cpic_set_magnetic_field(self.h, _ptr(b)))
+
     def set_floating(self, face=0, charge0=0.0):
         """cpic_set_floating: the face's conductor floats (Gauss's-law potential from its
         collected charge)."""
@@ -510,6 +516,8 @@ def run_from_workload(wl, sort_interval=0, analytic=None, mg_rtol=0.0, mg_max_cy
         run.load_particles(s, ps.cell, ps.t, ps.v)
     for (s, face, dens, vth, seed) in wl.injection:
         run.set_injection(s, face, dens, vth, seed)
+    if getattr(wl, "B0", None) is not None:
+        run.set_magnetic_field(wl.B0)
     return run
 
 

@@ -746,6 +746,7 @@ int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* s
     memset(r, 0, sizeof(*r));
     r->solver = CPIC_SOLVER_BICGSTAB;
     r->floating_face = -1;
+    r->kick_fraction = 1.0;
     r->push_tile = 1;
     init_geometry_sizes(r, cfg);
     st = setup_levels(r);
@@ -946,6 +947,22 @@ int cpic_get_particles(cpic_run* r, int sp, int64_t room, int64_t* n, int32_t* c
     for (int a = 0; a < 3; ++a)
         CPIC_CUDA(cudaMemcpyAsync(v + a * live, src_v + a * stride, sizeof(float) * live, cudaMemcpyDefault, r->stream));
     CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    return CPIC_OK;
+}
+
+int cpic_set_magnetic_field(cpic_run* r, const double* B) {
+    CHECK_RUN(r);
+    double b[3] = {0.0, 0.0, 0.0};
+    if (B)
+        for (int a = 0; a < 3; ++a) b[a] = B[a];
+    for (int a = 0; a < 3; ++a)
+        if (!(b[a] == b[a]) || b[a] > 1e30 || b[a] < -1e30) {
+            set_error("set_magnetic_field: non-finite component");
+            return CPIC_ERR_INVALID;
+        }
+    for (int a = 0; a < 3; ++a) r->B0[a] = b[a];
+    r->magnetized = b[0] != 0.0 || b[1] != 0.0 || b[2] != 0.0;
+    invalidate_graphs(r);
     return CPIC_OK;
 }
 

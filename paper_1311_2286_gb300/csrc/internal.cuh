@@ -100,6 +100,10 @@ struct PushParams {
     long long ncell_h;             // cells of the padded grid: prod (n_a + 2)
     int hs1, hs2;                  // padded strides of axes 1 and 2
     int origin;                    // padded index of cell (0, 0, 0)
+    int magnetized;                // uniform B0 (cpic_set_magnetic_field): Boris kick
+    float bh[CPIC_MAX_SPECIES];    // Boris constants per species: half kick (float)(dt q/m / 2),
+    float bt[CPIC_MAX_SPECIES][3]; // t = (float)(dt q/m B0 / 2),
+    float bs[CPIC_MAX_SPECIES][3]; // s = (float)(2 t / (1 + |t|^2)) (t, s from FP64 values)
     int chunk;                     // particles per block chunk (0: one wave of blocks)
     int tile;                      // 1: shared-memory deposit tile when the chunk fits
     DevCounters* ctr;
@@ -180,6 +184,9 @@ struct cpic_run {
     double* red;                 // reduction scratch [2 * 1024 + 8]
     int solver;                  // CPIC_SOLVER_* of the stream solve
     int pc_face_only;            // the FP32 V-cycle uses the stencil's face entries only
+    double B0[3];                // uniform magnetic field (cpic_set_magnetic_field)
+    double kick_fraction;        // fraction of dt of the kick being launched (1 otherwise)
+    int magnetized;              // B0 != 0
     int floating_face;           // face whose conductor floats (cpic_set_floating), -1: none
     double float_q0;             // its charge before any particle was collected
     double* psi;                 // potential of the unit-potential conductor in charge-free space
@@ -224,6 +231,7 @@ int launch_fold(cpic_run* r);
 int launch_push_prep(cpic_run* r);    // zero the deposit grid and kinetic-energy tallies
 int launch_push_kernel(cpic_run* r);  // the fused push + deposit kernel alone
 PushParams make_push_params(cpic_run* r);
+void set_boris_constants(const cpic_run* r, PushParams* p, double fraction);
 int launch_push2d(cpic_run* r, const PushParams& p);
 int launch_push3d(cpic_run* r, const PushParams& p);  // CPIC_ERR_NOT_BUILT: no specialisation
 // one PIC step without the field solve, enqueued on r->stream (also inside stream capture)

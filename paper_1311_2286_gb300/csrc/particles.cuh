@@ -79,6 +79,24 @@ __device__ __forceinline__ void node_weights(const float* t, unsigned* q) {
     q[CENTRE] = (1u << QF) - rest;
 }
 
+// Boris step for a uniform B0 (eq. (step1) with the magnetic term; Boris split): with the
+// half kick h, t = h B0 (q/m folded into h) and s = 2 t / (1 + |t|^2),
+//   v- = v + h E;  v' = v- + v- x t;  v+ = v- + v' x s;  v = v+ + h E,
+// FP32 in this order, each cross-product component as fmaf(a_y, b_z, -(a_z b_y)) added to
+// the left vector's component. E has three components (E_z = 0 in 2D).
+__device__ __forceinline__ void boris_kick(float* v, const float* E, float h, const float* t, const float* s) {
+    const float m0 = __fmaf_rn(h, E[0], v[0]), m1 = __fmaf_rn(h, E[1], v[1]), m2 = __fmaf_rn(h, E[2], v[2]);
+    const float p0 = __fadd_rn(m0, __fmaf_rn(m1, t[2], -__fmul_rn(m2, t[1])));
+    const float p1 = __fadd_rn(m1, __fmaf_rn(m2, t[0], -__fmul_rn(m0, t[2])));
+    const float p2 = __fadd_rn(m2, __fmaf_rn(m0, t[1], -__fmul_rn(m1, t[0])));
+    const float q0 = __fadd_rn(m0, __fmaf_rn(p1, s[2], -__fmul_rn(p2, s[1])));
+    const float q1 = __fadd_rn(m1, __fmaf_rn(p2, s[0], -__fmul_rn(p0, s[2])));
+    const float q2 = __fadd_rn(m2, __fmaf_rn(p0, s[1], -__fmul_rn(p1, s[0])));
+    v[0] = __fmaf_rn(h, E[0], q0);
+    v[1] = __fmaf_rn(h, E[1], q1);
+    v[2] = __fmaf_rn(h, E[2], q2);
+}
+
 template <int D>
 struct Tab;
 

@@ -136,7 +136,19 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
             Tab<D>::gather(p, vertex_of<D>(p, c), t, kp, gp);
         }
         if (MODE == 2) {
-            if (active) {
+            if (active && p.magnetized) {  // Boris step over the kick's fraction of dt
+                float E[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int al = 0; al < D; ++al) {
+                    float e = __fmul_rn(kp[0 * D + al], gp[0]);
+#pragma unroll
+                    for (int a = 1; a < D; ++a) e = __fmaf_rn(kp[a * D + al], gp[a], e);
+                    E[al] = -e;
+                }
+                boris_kick(v, E, p.bh[s], p.bt[s], p.bs[s]);
+#pragma unroll
+                for (int al = 0; al < 3; ++al) vq[al][slot] = v[al];
+            } else if (active) {
                 float coef = s == 0 ? kick_coef0 : s == 1 ? kick_coef1 : s == 2 ? kick_coef2 : kick_coef3;
 #pragma unroll
                 for (int al = 0; al < D; ++al) {
@@ -157,13 +169,25 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
         if (active) {
             const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
             const float dtqm = p.dtqm[s];
+            if (p.magnetized) {  // warp-uniform
+                float E[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int al = 0; al < D; ++al) {
-                float e = __fmul_rn(kp[0 * D + al], gp[0]);
+                for (int al = 0; al < D; ++al) {
+                    float e = __fmul_rn(kp[0 * D + al], gp[0]);
 #pragma unroll
-                for (int a = 1; a < D; ++a) e = __fmaf_rn(kp[a * D + al], gp[a], e);
-                e = -e;
-                v[al] = __fmaf_rn(dtqm, e, v[al]);
+                    for (int a = 1; a < D; ++a) e = __fmaf_rn(kp[a * D + al], gp[a], e);
+                    E[al] = -e;
+                }
+                boris_kick(v, E, p.bh[s], p.bt[s], p.bs[s]);
+            } else {
+#pragma unroll
+                for (int al = 0; al < D; ++al) {
+                    float e = __fmul_rn(kp[0 * D + al], gp[0]);
+#pragma unroll
+                    for (int a = 1; a < D; ++a) e = __fmaf_rn(kp[a * D + al], gp[a], e);
+                    e = -e;
+                    v[al] = __fmaf_rn(dtqm, e, v[al]);
+                }
             }
             // predictor
             int cpred[3];
@@ -352,7 +376,27 @@ PushParams make_push_params(cpic_run* r) {
     p.ctr = r->ctr;
     p.chunk = r->push_chunk;
     p.tile = r->push_tile;
+    set_boris_constants(r, &p, 1.0);
     return p;
+}
+
+// Boris constants of the species for a kick over `fraction` of dt (1: the push; -1/2: the
+// start-up half step backwards), computed in FP64 and rounded once
+void set_boris_constants(const cpic_run* r, PushParams* p, double fraction) {
+    p->magnetized = r->magnetized;
+    for (int s = 0; s < CPIC_MAX_SPECIES; ++s) {
+        double h = 0.0, t[3] = {0.0, 0.0, 0.0};
+        if (s < r->cfg.n_species) {
+            h = 0.5 * fraction * r->cfg.dt * r->cfg.q[s] / r->cfg.m[s];
+            for (int a = 0; a < 3; ++a) t[a] = h * r->B0[a];
+        }
+        const double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+        p->bh[s] = (float)h;
+        for (int a = 0; a < 3; ++a) {
+            p->bt[s][a] = (float)t[a];
+            p->bs[s][a] = (float)(2.0 * t[a] / (1.0 + tt));
+        }
+    }
 }
 
 // one wave of resident blocks over all SMs (the kernel walks its chunk in a loop)
@@ -380,6 +424,7 @@ static int particle_grid(cpic_run* r) {
 template <int MODE>
 static int launch_particles(cpic_run* r, float c0, float c1, float c2, float c3) {
     PushParams p = make_push_params(r);
+    if (MODE == 2) set_boris_constants(r, &p, r->kick_fraction);
     if (r->D == 2) {
         int blocks = particle_grid<2, MODE>(r);
         if (blocks < 0) return blocks;
@@ -404,6 +449,7 @@ int launch_push_kernel(cpic_run* r) {
     // generic kernel
     bool reflect = false;
     for (int f = 0; f < 2 * r->D; ++f) reflect = reflect || r->cfg.particle_bc[f] == CPIC_PBC_REFLECT;
+    if (r->magnetized) return launch_particles<0>(r, 0, 0, 0, 0);  // Boris kick: the generic kernel
     if (r->D == 2 && !reflect) return launch_push2d(r, make_push_params(r));
     if (r->D == 3) {
         const int st = launch_push3d(r, make_push_params(r));
@@ -427,7 +473,10 @@ int launch_deposit(cpic_run* r) {
 int launch_kick(cpic_run* r, double fraction) {
     float c[4] = {0, 0, 0, 0};
     for (int s = 0; s < r->cfg.n_species; ++s) c[s] = (float)(fraction * r->cfg.dt * r->cfg.q[s] / r->cfg.m[s]);
-    return launch_particles<2>(r, c[0], c[1], c[2], c[3]);
+    r->kick_fraction = fraction;  // the Boris constants of this kick (magnetised runs)
+    const int st = launch_particles<2>(r, c[0], c[1], c[2], c[3]);
+    r->kick_fraction = 1.0;
+    return st;
 }
 
 int launch_fold(cpic_run* r) {

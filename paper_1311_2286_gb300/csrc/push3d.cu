@@ -769,6 +769,7 @@ int launch_push3d_t(cpic_run* r, const PushParams& p) {
 // the specialised 3D kernel for the axis kinds it is instantiated for; CPIC_ERR_NOT_BUILT
 // for others (the caller then takes the generic kernel)
 int launch_push3d(cpic_run* r, const PushParams& p) {
+    if (p.magnetized) return CPIC_ERR_NOT_BUILT;
     const int k0 = p.pbc[0], k1 = p.pbc[2], k2 = p.pbc[4];
     if (k0 == K_ABS && k1 == K_REF && k2 == K_PER)
         return p.tile ? launch_push3d_t<K_ABS, K_REF, K_PER>(r, p) : launch_push3d_direct_t<K_ABS, K_REF, K_PER>(r, p);

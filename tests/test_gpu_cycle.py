@@ -270,3 +270,21 @@ def test_served_request_matches_oracle(cpic):
     for r in report:
         print("served cycle current:", r)
     run.close()
+
+
+def test_magnetized_langmuir_cycle_matches_oracle(cpic):
+    """Row f2 through whole cycles: the cold plasma wave across a uniform B_z = 1 (the
+    upper-hybrid oscillation the oracle's pin checks) on the device (generic kernel, Boris
+    kick, Boris start-up) against the oracle from the same particles: start-up and one-step
+    state <= 1e-5 against FP64, W_E at every level 1/2 sum phi Q of the device's fields,
+    time-averaged W_E within 1%."""
+    w = wl.langmuir_map2(32, 32, eps=0.05, ppc=16, vth=0.0, amp=0.05, dt=0.1, seed=0)
+    w.B0 = (0.0, 0.0, 1.0)
+    run = cpic.run_from_workload(w, sort_interval=0, mg_rtol=1e-12, mg_max_cycles=200)
+    run, pic, err0, err1, we, we_chk, we_ora, _, _ = _run_pair(cpic, w, 100, 0, run=run)
+    assert err0[0] <= 1e-5 and err0[1] <= 1e-5, err0
+    assert err1[0] <= 1e-5 and err1[1] <= 1e-5, err1
+    np.testing.assert_allclose(we, we_chk, rtol=1e-12)
+    assert abs(we.mean() / we_ora.mean() - 1.0) <= 0.01, (we.mean(), we_ora.mean())
+    print("magnetized langmuir: W_E mean device %.6e oracle %.6e" % (we.mean(), we_ora.mean()))
+    run.close()

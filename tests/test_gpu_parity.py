@@ -658,3 +658,64 @@ def test_full_size_sphere_push_parity(cpic, tile):
             Cref = odep.deposit_fixed(i32[:, alive].astype(np.int64), t32[:, alive], w.n, per)
             assert np.array_equal(run.charge(s), Cref)
     run.close()
+
+
+# ------------------------------------------------------------------ uniform B0 (row f2)
+
+B_TEST = (0.3, -0.2, 1.1)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_magnetized_push_bit_exact_vs_replay(cpic, case):
+    """Row f2: with a uniform B0 the push's kick is the Boris step (eq. (step1) with the
+    magnetic term): cells, offsets and velocities after one push equal the FP32 replay bit
+    for bit, the deposit equals the oracle's spec-Q deposit, and the state is within 1e-5
+    normwise of the FP64 oracle's Boris push."""
+    w = CASES[case]()
+    w.B0 = B_TEST
+    rng = np.random.default_rng(12)
+    phi = wl.random_field(rng, tuple(reversed(w.n)), 0.5)
+    if case in DIRICHLET_AXIS0:
+        phi = phi + np.linspace(-5, 0, w.n[0])
+    g, per, pre, post, charge, d, k32, G32 = _push_case(cpic, w, phi)
+    G64 = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value)
+    D = w.dim
+    for s, sp in enumerate(w.species):
+        cell0, t0, v0 = pre[s]
+        idx = _unpack(cell0, D)
+        qm = sp.q / sp.m
+        i32, t32, v32, face, kefp = mover.push32(idx, t0, v0, k32, G32, w.n, w.particle_bc, np.float32(w.dt * qm),
+                                                np.float32(0.5 * w.dt), np.float32(w.dt),
+                                                boris=mover.boris_constants32(w.dt, qm, B_TEST))
+        alive = face < 0
+        cell1, t1, v1 = post[s]
+        assert np.array_equal(cell1, wl.pack_cells(i32[:, alive]))
+        assert np.array_equal(t1, t32[:, alive]) and np.array_equal(v1, v32[:, alive])
+        assert np.array_equal(charge[s], odep.deposit_fixed(i32[:, alive].astype(np.int64), t32[:, alive], w.n, per))
+        i64, t64, v64, face64 = mover.push64(idx, t0.astype(np.float64), v0.astype(np.float64), g.k, G64, w.dt, qm,
+                                             w.n, w.particle_bc, B=B_TEST)
+        both = (face64 < 0) & alive
+        keep = both[alive]
+        dv = np.abs(v1[:, keep].astype(np.float64) - v64[:, both])
+        assert np.max(dv) / np.max(np.abs(v64)) <= 1e-5
+
+
+def test_magnetized_start_up_kick_bit_exact(cpic):
+    """The start-up kick of a magnetised run is the Boris step over -dt/2 (FP32 replay)."""
+    w = CASES["map2_periodic"]()
+    w.B0 = B_TEST
+    g, _ = _geom(w)
+    run = cpic.run_from_workload(w)
+    rng = np.random.default_rng(14)
+    phi = wl.random_field(rng, (32, 32), 0.5)
+    run.set_phi(phi)
+    run.vertex_field()
+    run.kick(-0.5)
+    _, _, v = run.particles(0)
+    ps = w.particles[0]
+    qm = w.species[0].q / w.species[0].m
+    G32 = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value).astype(np.float32)
+    ref = mover.kick32(_unpack(ps.cell), ps.t, ps.v, g.k.astype(np.float32), G32, w.n, np.float32(-0.5 * w.dt * qm),
+                       boris=mover.boris_constants32(w.dt, qm, B_TEST, -0.5))
+    assert np.array_equal(v, ref)
+    run.close()

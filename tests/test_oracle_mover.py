@@ -272,3 +272,73 @@ def test_c_loop_mover_and_deposit_equal_the_numpy_forms(case):
     for threads in (1, 4):
         e2 = dep.deposit_exact_c(a[0][:, alive], a[1][:, alive], w.n, per, threads=threads)
         assert np.max(np.abs(e1 - e2)) <= 1e-12 * np.max(np.abs(e1))
+
+
+# ------------------------------------------------------------------ uniform B0 (Boris step)
+
+def _uniform_tables(n, G0):
+    """Uniform map (k = N I in cell units) and a uniform logical field G0 at every vertex."""
+    from oracle import geometry
+    from paper_1311_2286_gb300 import workloads as wl
+
+    X = wl.map2_vertices(n, n, 0.0)
+    g = geometry.build_geometry(X, [True, True])
+    G = np.broadcast_to(np.asarray(G0, dtype=np.float64), g.k.shape[:-2] + (2,)).copy()
+    return g.k, G
+
+
+def test_boris_gyration_phase_and_speed():
+    """Eq. (step1) with a uniform B0 and no E (Boris rotation): the speed is kept to rounding
+    and the velocity turns by exactly 2 atan(omega_c dt / 2) per step, clockwise for
+    q B_z > 0 (the force q v x B), in the FP64 mover, the C loops and the FP32 replay."""
+    n = 16
+    k, G = _uniform_tables(n, (0.0, 0.0))
+    qm, Bz, dt, N = 1.7, 0.8, 0.3, 40
+    idx = np.array([[3], [5]])
+    t = np.array([[0.25], [0.5]])
+    v0 = np.array([[0.02], [0.0], [0.013]])
+    v = v0.copy()
+    i, tt = idx, t
+    for _ in range(N):
+        i, tt, v, face = mover.push64(i, tt, v, k, G, dt, qm, (n, n), [0, 0, 0, 0], B=(0.0, 0.0, Bz))
+    theta = 2.0 * math.atan(qm * Bz * dt / 2.0)
+    ang = math.atan2(v[1, 0], v[0, 0])
+    assert abs(((ang + N * theta) + math.pi) % (2 * math.pi) - math.pi) < 1e-12
+    assert abs(math.hypot(v[0, 0], v[1, 0]) - 0.02) < 1e-15 and v[2, 0] == 0.013
+    b = mover.push64_c(idx, t, v0, k, G, dt, qm, (n, n), [0, 0, 0, 0], B=(0.0, 0.0, Bz))
+    a = mover.push64(idx, t, v0, k, G, dt, qm, (n, n), [0, 0, 0, 0], B=(0.0, 0.0, Bz))
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[1], b[1])
+    bc = mover.boris_constants32(dt, qm, (0.0, 0.0, Bz))
+    r = mover.push32(idx.astype(np.int32), t.astype(np.float32), v0.astype(np.float32), k.astype(np.float32),
+                     G.astype(np.float32), (n, n), [0, 0, 0, 0], np.float32(dt * qm), np.float32(dt / 2),
+                     np.float32(dt), boris=bc)
+    np.testing.assert_allclose(r[2].astype(np.float64), a[2], rtol=0, atol=1e-7)
+
+
+def test_boris_exb_drift():
+    """Uniform E (from a uniform logical field on the uniform map) perpendicular to a uniform
+    B: averaged over whole gyrations the velocity is the E x B drift E x B / B^2 (the Boris
+    step keeps it exactly), and v_z is untouched."""
+    n = 64
+    G0 = np.array([0.01, -0.004])  # cell units: E = -k^T G = -N G0
+    k, G = _uniform_tables(n, G0)
+    qm, Bz, dt = -1.0, 2.0, 0.05
+    E = -n * G0
+    drift = np.array([E[1] * Bz, -E[0] * Bz]) / Bz**2
+    idx = np.array([[10], [20]])
+    t = np.array([[0.5], [0.5]])
+    v = np.array([[0.3], [0.1], [0.05]])
+    omega = abs(qm * Bz)
+    period_steps = 2 * math.pi / (2 * math.atan(omega * dt / 2))
+    N = int(round(25 * period_steps))
+    acc = np.zeros(2)
+    i, tt = idx, t
+    vs = []
+    for _ in range(N):
+        i, tt, v, face = mover.push64(i, tt, v, k, G, dt, qm, (n, n), [0, 0, 0, 0], B=(0.0, 0.0, Bz))
+        vs.append(v[:2, 0].copy())
+    vs = np.array(vs)
+    # average over an integer number of gyrations (the nearest whole number of steps)
+    mean = vs[: int(round(24 * period_steps))].mean(axis=0)
+    assert np.max(np.abs(mean - drift)) < 2e-3 * np.linalg.norm(drift) + 1e-3 * 0.3, (mean, drift)
+    assert v[2, 0] == 0.05

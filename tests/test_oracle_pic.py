@@ -267,3 +267,21 @@ def test_oml_current_of_attracted_electrons():
     steady state within a few tens of plasma periods)."""
     r = _oml_run(2.0, 1836.0, 600, 300)
     assert r[0][1] > 20_000 and abs(r[0][0] - 1.0) <= 0.15, r
+
+
+def test_upper_hybrid_frequency_with_uniform_b():
+    """Row f2 in the whole loop: a cold electron plasma wave across a uniform B0 = B_z
+    (Boris kick) oscillates at the upper-hybrid frequency sqrt(omega_pe^2 + omega_ce^2)
+    (sqrt 2 for B_z = 1 in units of omega_pe), within 2% (leapfrog and Boris phase errors
+    are O(dt^2) = 0.3% here), on the distorted map2 grid."""
+    w = wl.langmuir_map2(32, 32, eps=0.05, ppc=16, vth=0.0, amp=0.05, dt=0.1, seed=0)
+    w.B0 = (0.0, 0.0, 1.0)
+    pic = OraclePIC(w, "fp64")
+    pic.initialize()
+    amps = [_mode_amplitude(pic, 0.05)]
+    for _ in range(100):
+        pic.step()
+        amps.append(_mode_amplitude(pic, 0.05))
+    amps = np.array(amps)
+    wfreq = _frequency(amps - amps.mean(), 0.1)
+    assert abs(wfreq / math.sqrt(2.0) - 1.0) < 0.02, wfreq
