@@ -512,6 +512,28 @@ int phase(cpic_run* r, int ph, F fn) {
 // enqueue one step's work (stream order); `sort` selects the cell sort
 }  // namespace
 
+bool push2d_batchable(const cpic_run* r) {
+    if (r->D != 2 || r->magnetized) return false;
+    for (int f = 0; f < 4; ++f)
+        if (r->cfg.particle_bc[f] == CPIC_PBC_REFLECT) return false;
+    return true;
+}
+
+int enqueue_step_pre(cpic_run* r, bool with_push) {
+    int st = launch_vertex_field(r);
+    if (!st) st = launch_push_prep(r);
+    if (!st && with_push) st = launch_push_kernel(r);
+    return st;
+}
+
+int enqueue_step_post(cpic_run* r, bool sort, bool fold) {
+    int st = launch_finalize_step(r);
+    if (!st) st = launch_inject(r);
+    if (!st && fold) st = launch_fold(r);
+    if (!st && sort) st = launch_sort(r);
+    return st;
+}
+
 int enqueue_step(cpic_run* r, bool sort, bool fold) {
     int st = launch_vertex_field(r);
     if (st) return st;

@@ -1,12 +1,18 @@
 // Row a11: many independent runs stepped together.
 //
-// A batch step is one CUDA graph launch. The graph is captured by forking one branch per
-// member run off the batch stream (an event recorded on the batch stream, waited on by the
-// run's branch stream) and joining the branches back; each branch holds that run's whole
-// step (vertex field, push + deposit, injection, halo fold, the cell sort when it is due,
-// and, for full cycles, its field solve: the cluster kernel or the conditional V-cycle
-// loop). Branches have no dependencies on each other, so the device runs them concurrently:
-// runs far smaller than the GPU (a few thousand cells, 10^4..10^6 particles, a 16-SM solve
+// A batch step is one CUDA graph launch in three phases:
+//   1. one branch per member run, forked off the batch stream: the run's vertex field and
+//      the zeroing of its deposit grid (and the whole push for runs that cannot join the
+//      batched launch: 3D, magnetised or reflecting runs);
+//   2. the particle step (gather, push, boundaries, deposit: rows a2-a6) of every 2D member
+//      in ONE persistent launch per combination of axis kinds: the resident blocks walk the
+//      virtual blocks of all runs (a run's share in proportion to its particle capacity),
+//      each taking its run's parameters from a device table;
+//   3. one branch per run again: step counter, injection, halo fold, the cell sort when it
+//      is due and, for full cycles, the field solve (the cluster kernel or the conditional
+//      V-cycle loop).
+// Branches have no dependencies on each other, so the device runs them concurrently: runs
+// far smaller than the GPU (a few thousand cells, 10^4..10^6 particles, a 16-SM solve
 // cluster) fill it together instead of one after another, and the host issues one launch
 // per batch step instead of one per kernel.
 //
@@ -14,6 +20,7 @@
 // step) and replayed; adding or removing a run drops the cached graphs. A run must not
 // change its map or injection while it is a member, and must not be stepped on its own
 // meanwhile.
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -27,7 +34,11 @@ struct cpic_batch {
     std::vector<cpic_run*> runs;
     std::vector<cudaStream_t> branch;  // one capture branch stream per member
     std::vector<cudaEvent_t> join;     // one join event per member
-    cudaEvent_t fork = nullptr;
+    cudaEvent_t fork = nullptr, fork2 = nullptr;
+    std::vector<cudaEvent_t> join_pre;  // one per member: end of its pre-push branch
+    cpic::PushParams* d_params = nullptr;  // device tables of the batched push (per capture)
+    int* d_vbase = nullptr;
+    size_t table_runs = 0;
     struct Graph {
         cudaGraphExec_t exec = nullptr;
         int kernels = 0;
@@ -43,11 +54,61 @@ void drop_graphs(cpic_batch* b) {
     b->graphs.clear();
 }
 
+// The batched push's device tables: members that can join it, grouped by the kinds of their
+// two axes (periodic or not); per group a run table and virtual-block offsets. Built once
+// per membership (run parameters do not change between steps; counts are read on the
+// device). Per group: its first table entry, runs, axis kinds, total virtual blocks; its
+// n + 1 offsets follow the previous groups' in the offset table.
+struct PushGroup {
+    int first, n, per0, per1, vblocks;
+};
+
+int build_push_tables(cpic_batch* b, std::vector<PushGroup>* groups) {
+    groups->clear();
+    std::vector<PushParams> table;
+    std::vector<int> vbase;
+    for (int kind = 0; kind < 4; ++kind) {
+        const int per0 = kind & 1, per1 = kind >> 1;
+        PushGroup g{(int)table.size(), 0, per0, per1, 0};
+        for (cpic_run* r : b->runs) {
+            if (!push2d_batchable(r)) continue;
+            if ((r->cfg.particle_bc[0] == CPIC_PBC_PERIODIC) != (per0 != 0) ||
+                (r->cfg.particle_bc[2] == CPIC_PBC_PERIODIC) != (per1 != 0))
+                continue;
+            long long cap = 0;
+            for (int s = 0; s < r->cfg.n_species; ++s) cap += r->pb.capacity[s];
+            const int nb = (int)std::max<long long>(1, (cap + 2047) / 2048);  // ~2048 particles a block
+            vbase.push_back(g.vblocks);
+            g.vblocks += nb;
+            table.push_back(make_push_params(r));
+            ++g.n;
+        }
+        if (g.n) {  // the group's n + 1 virtual-block offsets follow the previous group's
+            vbase.push_back(g.vblocks);
+            groups->push_back(g);
+        }
+    }
+    if (b->d_params) cudaFree(b->d_params);
+    if (b->d_vbase) cudaFree(b->d_vbase);
+    b->d_params = nullptr;
+    b->d_vbase = nullptr;
+    b->table_runs = table.size();
+    if (table.empty()) return CPIC_OK;
+    CPIC_CUDA(cudaMalloc(&b->d_params, sizeof(PushParams) * table.size()));
+    CPIC_CUDA(cudaMalloc(&b->d_vbase, sizeof(int) * vbase.size()));
+    CPIC_CUDA(cudaMemcpy(b->d_params, table.data(), sizeof(PushParams) * table.size(), cudaMemcpyHostToDevice));
+    CPIC_CUDA(cudaMemcpy(b->d_vbase, vbase.data(), sizeof(int) * vbase.size(), cudaMemcpyHostToDevice));
+    return CPIC_OK;
+}
+
 int capture(cpic_batch* b, bool solve, const std::string& key, cpic_batch::Graph* out) {
+    std::vector<PushGroup> groups;
+    int st = build_push_tables(b, &groups);  // before the capture: it allocates and copies
+    if (st) return st;
     CPIC_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    int st = CPIC_OK;
     cudaError_t e = cudaEventRecord(b->fork, b->stream);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaEventRecord(fork)", __FILE__, __LINE__);
+    // 1. pre-push branches
     for (size_t i = 0; !st && i < b->runs.size(); ++i) {
         cpic_run* r = b->runs[i];
         e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
@@ -57,7 +118,36 @@ int capture(cpic_batch* b, bool solve, const std::string& key, cpic_batch::Graph
         }
         cudaStream_t saved = r->stream;
         r->stream = b->branch[i];
-        st = enqueue_step(r, key[i] == '1', solve);
+        st = enqueue_step_pre(r, !push2d_batchable(r));
+        r->stream = saved;
+        if (st) break;
+        e = cudaEventRecord(b->join_pre[i], b->branch[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join_pre[i], 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "join (pre-push)", __FILE__, __LINE__);
+    }
+    // 2. the batched particle step, one persistent launch per group
+    int vfirst = 0;
+    for (const PushGroup& g : groups) {
+        if (st) break;
+        const int blocks = std::min(g.vblocks, push2d_batch_blocks());
+        st = launch_push2d_batch(b->d_params + g.first, b->d_vbase + vfirst, g.n, g.per0, g.per1, blocks, b->stream);
+        vfirst += g.n + 1;
+    }
+    if (!st) {
+        e = cudaEventRecord(b->fork2, b->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaEventRecord(fork2)", __FILE__, __LINE__);
+    }
+    // 3. post-push branches (injection, fold, sort, field solve)
+    for (size_t i = 0; !st && i < b->runs.size(); ++i) {
+        cpic_run* r = b->runs[i];
+        e = cudaStreamWaitEvent(b->branch[i], b->fork2, 0);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "cudaStreamWaitEvent(fork2)", __FILE__, __LINE__);
+            break;
+        }
+        cudaStream_t saved = r->stream;
+        r->stream = b->branch[i];
+        st = enqueue_step_post(r, key[i] == '1', solve);
         if (!st && solve) {
             cudaStreamCaptureStatus cs;
             cudaGraph_t cg = nullptr;
@@ -108,6 +198,7 @@ int cpic_batch_create(int max_runs, void* stream, cpic_batch** out) {
         b->own_stream = e == cudaSuccess;
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         delete b;
         return cuda_fail(e, "cudaEventCreate(fork)", __FILE__, __LINE__);
@@ -121,7 +212,11 @@ int cpic_batch_destroy(cpic_batch* b) {
     drop_graphs(b);
     for (auto s : b->branch) cudaStreamDestroy(s);
     for (auto ev : b->join) cudaEventDestroy(ev);
+    for (auto ev : b->join_pre) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->fork2) cudaEventDestroy(b->fork2);
+    if (b->d_params) cudaFree(b->d_params);
+    if (b->d_vbase) cudaFree(b->d_vbase);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return CPIC_OK;
@@ -146,10 +241,12 @@ int cpic_batch_add(cpic_batch* b, cpic_run* r) {
             return CPIC_ERR_INVALID;
         }
     cudaStream_t s = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr, ev_pre = nullptr;
     CPIC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_pre, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        if (ev) cudaEventDestroy(ev);
         cudaStreamDestroy(s);
         return cuda_fail(e, "cudaEventCreate(join)", __FILE__, __LINE__);
     }
@@ -158,6 +255,7 @@ int cpic_batch_add(cpic_batch* b, cpic_run* r) {
     b->runs.push_back(r);
     b->branch.push_back(s);
     b->join.push_back(ev);
+    b->join_pre.push_back(ev_pre);
     drop_graphs(b);
     return CPIC_OK;
 }
@@ -172,9 +270,11 @@ int cpic_batch_remove(cpic_batch* b, cpic_run* r) {
             CPIC_CUDA(cudaStreamSynchronize(b->stream));
             cudaStreamDestroy(b->branch[i]);
             cudaEventDestroy(b->join[i]);
+            cudaEventDestroy(b->join_pre[i]);
             b->runs.erase(b->runs.begin() + i);
             b->branch.erase(b->branch.begin() + i);
             b->join.erase(b->join.begin() + i);
+            b->join_pre.erase(b->join_pre.begin() + i);
             drop_graphs(b);
             return CPIC_OK;
         }

@@ -233,6 +233,17 @@ int launch_push_kernel(cpic_run* r);  // the fused push + deposit kernel alone
 PushParams make_push_params(cpic_run* r);
 void set_boris_constants(const cpic_run* r, PushParams* p, double fraction);
 int launch_push2d(cpic_run* r, const PushParams& p);
+// batched 2D particle step (row a11): one launch over a device table of runs' parameters
+int push2d_batch_blocks();  // resident blocks of the batched kernel (one wave)
+int launch_push2d_batch(const PushParams* runs, const int* vbase, int nruns, int per0, int per1, int blocks,
+                        cudaStream_t stream);
+// true when the run's particle step can join the batched 2D launch
+bool push2d_batchable(const cpic_run* r);
+// one step's work split around the particle push (for the batched launch): vertex field and
+// the zeroing of the deposit grid (and the push itself for runs that cannot join it); then
+// the step counter, injection, halo fold and sort
+int enqueue_step_pre(cpic_run* r, bool with_push);
+int enqueue_step_post(cpic_run* r, bool sort, bool fold);
 int launch_push3d(cpic_run* r, const PushParams& p);  // CPIC_ERR_NOT_BUILT: no specialisation
 // one PIC step without the field solve, enqueued on r->stream (also inside stream capture)
 int enqueue_step(cpic_run* r, bool sort, bool fold);

@@ -137,10 +137,12 @@ __device__ __forceinline__ void store_state(bool p, int* c, int cv, float* a, fl
         : "memory");
 }
 
+// One run's particle step on a virtual grid of nb blocks of which this block is bid: the
+// body of the single-run kernel and of the batched kernel (a run's blocks are a slice of
+// the batched launch).
 template <bool PER0, bool PER1>
-__global__ void __launch_bounds__(P2_THREADS, 4) push2d_kernel(PushParams p) {
-    __shared__ unsigned tile_lo[TILE_CELLS], tile_hi[TILE_CELLS];
-    __shared__ int red_min[P2_THREADS / 32], red_max[P2_THREADS / 32];
+__device__ __forceinline__ void push2d_run(const PushParams& p, int bid, int nb, unsigned* tile_lo, unsigned* tile_hi,
+                                           int* red_min, int* red_max) {
     const DevCounters* ctr = p.ctr;
     const int cur = ctr->cur;
     const int nsp = p.nsp;
@@ -154,14 +156,14 @@ __global__ void __launch_bounds__(P2_THREADS, 4) push2d_kernel(PushParams p) {
     if (total == 0) return;
     // chunk size: a multiple of the block, about one chunk per block unless set
     const int C = p.chunk > 0 ? p.chunk
-                              : ((total + (int)gridDim.x - 1) / (int)gridDim.x + P2_THREADS - 1) / P2_THREADS * P2_THREADS;
+                              : ((total + nb - 1) / nb + P2_THREADS - 1) / P2_THREADS * P2_THREADS;
     const int n0 = p.n[0], n1 = p.n[1], nv0 = n0 + 1;
     const float4* __restrict__ K4 = reinterpret_cast<const float4*>(p.K);
     const float2* __restrict__ G2 = reinterpret_cast<const float2*>(p.G);
     const long long T = p.pb.total;
     const float hdt = p.hdt, dt = p.dt;
 
-    for (int ch = blockIdx.x;; ch += gridDim.x) {
+    for (int ch = bid;; ch += nb) {
         // species and range of chunk ch (block-uniform)
         int s = 0, local = ch;
         while (s < nsp) {
@@ -421,6 +423,35 @@ __global__ void __launch_bounds__(P2_THREADS, 4) push2d_kernel(PushParams p) {
 }
 
 template <bool PER0, bool PER1>
+__global__ void __launch_bounds__(P2_THREADS, 4) push2d_kernel(PushParams p) {
+    __shared__ unsigned tile_lo[TILE_CELLS], tile_hi[TILE_CELLS];
+    __shared__ int red_min[P2_THREADS / 32], red_max[P2_THREADS / 32];
+    push2d_run<PER0, PER1>(p, (int)blockIdx.x, (int)gridDim.x, tile_lo, tile_hi, red_min, red_max);
+}
+
+// Row a11: the particle step of many runs in one persistent launch. Run r owns virtual
+// blocks [vbase[r], vbase[r + 1]) (in proportion to its particle capacity); the resident
+// blocks walk the virtual blocks of all runs, each taking its run's parameters from the
+// device table, so runs of uneven size share one wave of the GPU.
+template <bool PER0, bool PER1>
+__global__ void __launch_bounds__(P2_THREADS, 4) push2d_batch_kernel(const PushParams* __restrict__ runs,
+                                                                      const int* __restrict__ vbase, int nruns) {
+    __shared__ unsigned tile_lo[TILE_CELLS], tile_hi[TILE_CELLS];
+    __shared__ int red_min[P2_THREADS / 32], red_max[P2_THREADS / 32];
+    const int total = vbase[nruns];
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        int a = 0, b = nruns;  // the run of virtual block vb: vbase[a] <= vb < vbase[a + 1]
+        while (b - a > 1) {
+            const int m = (a + b) >> 1;
+            if (vbase[m] <= vb) a = m;
+            else b = m;
+        }
+        push2d_run<PER0, PER1>(runs[a], vb - vbase[a], vbase[a + 1] - vbase[a], tile_lo, tile_hi, red_min, red_max);
+        __syncthreads();  // the next virtual block reuses the tile
+    }
+}
+
+template <bool PER0, bool PER1>
 int launch_push2d_t(cpic_run* r, const PushParams& p) {
     static std::atomic<int> per_sm[64];  // resident blocks per SM, per device
     int dev = 0;
@@ -444,6 +475,32 @@ int launch_push2d_t(cpic_run* r, const PushParams& p) {
 }
 
 }  // namespace
+
+int push2d_batch_blocks() {
+    static std::atomic<int> per_sm[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return device_sm_count();
+    std::atomic<int>& cache = per_sm[dev & 63];
+    int b = cache.load(std::memory_order_acquire);
+    if (b <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, push2d_batch_kernel<false, true>, P2_THREADS, 0) !=
+            cudaSuccess)
+            b = 1;
+        if (b < 1) b = 1;
+        cache.store(b, std::memory_order_release);
+    }
+    return b * device_sm_count();
+}
+
+int launch_push2d_batch(const PushParams* runs, const int* vbase, int nruns, int per0, int per1, int blocks,
+                        cudaStream_t stream) {
+    if (per0 && per1) push2d_batch_kernel<true, true><<<blocks, P2_THREADS, 0, stream>>>(runs, vbase, nruns);
+    else if (per0) push2d_batch_kernel<true, false><<<blocks, P2_THREADS, 0, stream>>>(runs, vbase, nruns);
+    else if (per1) push2d_batch_kernel<false, true><<<blocks, P2_THREADS, 0, stream>>>(runs, vbase, nruns);
+    else push2d_batch_kernel<false, false><<<blocks, P2_THREADS, 0, stream>>>(runs, vbase, nruns);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
 
 int launch_push2d(cpic_run* r, const PushParams& p) {
     const bool per0 = p.pbc[0] == CPIC_PBC_PERIODIC, per1 = p.pbc[2] == CPIC_PBC_PERIODIC;

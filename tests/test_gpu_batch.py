@@ -88,3 +88,50 @@ def test_batch_remove_and_continue(cpic):
     b.close()
     for r in runs:
         r.close()
+
+
+def test_mixed_batch_equals_alone(cpic):
+    """A batch whose 2D cylinder members share the persistent particle launch while a 3D
+    sphere and a magnetised 2D run (which cannot join it) push in their own branches: every
+    member ends bit-identical to the same run stepped alone (full cycles, across sorts)."""
+    def makers():
+        def sphere():
+            w = wl.sphere(16, 12, 8, npart_per_species=4000, seed=44, inject=True)
+            return cpic.run_from_workload(w, sort_interval=2)
+
+        def magnetized():
+            w = wl.cylinder(inject=True, **SPECS[1])
+            w.B0 = (0.0, 0.0, 0.7)
+            return cpic.run_from_workload(w, sort_interval=3)
+
+        return [lambda: _make(cpic, SPECS[0]), sphere, magnetized, lambda: _make(cpic, SPECS[2])]
+
+    def state3(run):
+        d = run.diag()
+        parts = [np.sort(np.rec.fromarrays([c, *t, *v])) for c, t, v in (run.particles(s) for s in range(2))]
+        return run.phi(), d, parts, [run.charge(s) for s in range(2)]
+
+    alone = []
+    for mk in makers():
+        r = mk()
+        r.initialize()
+        r.step(5)
+        alone.append(state3(r))
+        r.close()
+    runs = [mk() for mk in makers()]
+    b = cpic.Batch(8)
+    for r in runs:
+        r.initialize()
+        b.add(r)
+    b.step(5)
+    b.synchronize()
+    for r, ref in zip(runs, alone):
+        got = state3(r)
+        assert np.array_equal(got[0], ref[0])
+        for k in ("step", "n", "absorbed", "injected", "W_E", "W_K", "mg_cycles"):
+            assert got[1][k] == ref[1][k], k
+        for x, y in zip(got[2] + got[3], ref[2] + ref[3]):
+            assert np.array_equal(x, y)
+    b.close()
+    for r in runs:
+        r.close()
