@@ -542,20 +542,28 @@ def batched_measurement(cpic, nruns, steps, stream):
         for r in runs:
             r.step(1)
 
+    def sequential_particles():
+        for r in runs:
+            r.step_particles(1)
+
     seq_v, seq_ms = timed(sequential, steps)
+    seqp_v, seqp_ms = timed(sequential_particles, steps)
     batch = cpic.Batch(len(runs), stream=cs)
     for r in runs:
         batch.add(r)
     step0 = [r.diag()["step"] for r in runs]
     n_before = alive()
     cyc_before = [r.diag()["mg_cycles"] for r in runs]
-    bat_v, bat_ms = timed(lambda: batch.step(1), steps)
+    bat_v, bat_ms = timed(lambda: batch.step(1), steps)  # full cycles: the push in the run branches
+    batp_v, batp_ms = timed(lambda: batch.step(1, solve=False), steps)  # particle steps: one persistent push
+    batch.set_mode(cpic.CPIC_BATCH_PERSISTENT)
+    batpf_v, batpf_ms = timed(lambda: batch.step(1), steps)  # full cycles with the persistent push
     batch.close()
     # every run advanced by every batch step (16 warm-up + timed)
     adv = [r.diag()["step"] - s0 for r, s0 in zip(runs, step0)]
     cyc_after = [r.diag()["mg_cycles"] for r in runs]
     check = {"steps_advanced_min": int(min(adv)), "steps_advanced_max": int(max(adv)),
-             "expected": 16 + steps, "live_before": int(n_before), "live_after": int(alive()),
+             "expected": 3 * (16 + steps), "live_before": int(n_before), "live_after": int(alive()),
              "mg_cycles_mean_before": float(np.mean(cyc_before)), "mg_cycles_mean_after": float(np.mean(cyc_after)),
              "sequential_timing": diag[0], "batch_timing": diag[1]}
     cells = sum(sp["n1"] * sp["n2"] for sp in specs)
@@ -564,12 +572,18 @@ def batched_measurement(cpic, nruns, steps, stream):
         r.close()
     return {"value": bat_v, "unit": UNIT, "ms_per_step": bat_ms, "sequential_value": seq_v,
             "sequential_ms_per_step": seq_ms, "speedup": bat_v / seq_v, "runs": nruns, "steps": steps,
+            "particle_steps": {"batch_value": batp_v, "batch_ms_per_step": batp_ms, "sequential_value": seqp_v,
+                               "sequential_ms_per_step": seqp_ms, "speedup": batp_v / seqp_v,
+                               "note": "fixed-field particle steps: the batch pushes every run in one persistent "
+                                       "launch"},
+            "full_cycle_persistent_push": {"value": batpf_v, "ms_per_step": batpf_ms},
             "particles": parts, "cells": cells, "setup_s": setup_s, "autotune_s": tune_s, "check": check,
             "sort_intervals": {str(k): chosen.count(k) for k in sorted(set(chosen))},
             "workload": "independent 2D cylinder runs, cells U{32..256}xU{64..512} (steps of 16), particles per species "
                         "U[1e4, 2e6], phi_obj U[-10, 2], seeds 1000+i, loaded on the device; full PIC cycles "
                         "with the multigrid solve; batch = one CUDA graph launch per step, sequential = the "
-                        "runs' own graphs one after another on one stream"}
+                        "runs' own graphs one after another on one stream; also fixed-field particle steps "
+                        "(persistent batched push) and full cycles with the persistent push"}
 
 
 def aggregate_replicas(dist, times_ms, counts, device):

@@ -359,8 +359,9 @@ int cpic_restore(const char* path, void* arena, size_t arena_bytes, void* stream
 /* ---------------------------------------------------------------- batched runs (row a11) */
 
 /* A batch steps many independent runs together: one CUDA graph launch per batch step, whose
- * branches (one per member run, no dependencies between them) hold each run's whole step,
- * so the device runs them concurrently. Runs keep their own arenas and streams; a member
+ * branches (one per member run, no dependencies between them) hold each run's step, so the
+ * device runs them concurrently; the 2D members' particle push can be one persistent launch
+ * over all of them (cpic_batch_set_mode). Runs keep their own arenas and streams; a member
  * must not be stepped alone, nor change its map or injection. Not in the paper (its runs
  * are single simulations); the physics of each run is unchanged, so each run's result is
  * the same in a batch as alone. */
@@ -376,6 +377,19 @@ int cpic_batch_destroy(cpic_batch* batch);
 int cpic_batch_add(cpic_batch* batch, cpic_run* run);
 int cpic_batch_remove(cpic_batch* batch, cpic_run* run);
 int cpic_batch_size(const cpic_batch* batch, int* n);
+/* How a batch step runs the particle push of its 2D members (the others always push in
+ * their own branch of the step's graph):
+ *   CPIC_BATCH_BRANCHES    each run's push in its branch, next to its other work;
+ *   CPIC_BATCH_PERSISTENT  one persistent launch for all of them between a pre-push and a
+ *                          post-push phase of per-run branches (the resident blocks walk the
+ *                          runs' chunks from a device table of run parameters);
+ *   CPIC_BATCH_AUTO        (default) persistent for fixed-field particle steps, branches for
+ *                          full cycles (solve-bound: independent branches overlap better).
+ * The results are the same in every mode. CPIC_ERR_INVALID for another value. */
+#define CPIC_BATCH_AUTO 0
+#define CPIC_BATCH_BRANCHES 1
+#define CPIC_BATCH_PERSISTENT 2
+int cpic_batch_set_mode(cpic_batch* batch, int mode);
 /* nsteps batch steps; with_solve != 0: full PIC cycles (cpic_step), 0: fixed-field particle
  * steps (cpic_step_particles). Each run sorts on its own schedule. Asynchronous. */
 int cpic_batch_step(cpic_batch* batch, int nsteps, int with_solve);

@@ -24,6 +24,7 @@ CPIC_BC_PERIODIC, CPIC_BC_DIRICHLET, CPIC_BC_NEUMANN = 0, 1, 2
 CPIC_PBC_PERIODIC, CPIC_PBC_ABSORB, CPIC_PBC_REFLECT = 0, 1, 2
 CPIC_MAP_SINE, CPIC_MAP_ANNULUS, CPIC_MAP_SPHERE_AXISYM, CPIC_MAP_SHELL = 1, 2, 3, 4
 CPIC_SOLVER_MG, CPIC_SOLVER_BICGSTAB = 0, 1
+CPIC_BATCH_AUTO, CPIC_BATCH_BRANCHES, CPIC_BATCH_PERSISTENT = 0, 1, 2
 MAX_SPECIES = 4
 
 
@@ -161,6 +162,7 @@ _SIGS = {
     "cpic_batch_remove": ([P, P], ctypes.c_int),
     "cpic_batch_size": ([P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "cpic_batch_step": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "cpic_batch_set_mode": ([P, ctypes.c_int], ctypes.c_int),
     "cpic_batch_synchronize": ([P], ctypes.c_int),
     "cpic_get_config": ([P, P], ctypes.c_int),
     "cpic_set_sort_interval": ([P, ctypes.c_int], ctypes.c_int),
@@ -603,6 +605,9 @@ class Batch:
 
     def step(self, nsteps=1, solve=True):
         check(load().cpic_batch_step(self.h, nsteps, 1 if solve else 0))
+
+    def set_mode(self, mode):
+        check(load().cpic_batch_set_mode(self.h, mode))
 
     def synchronize(self):
         check(load().cpic_batch_synchronize(self.h))

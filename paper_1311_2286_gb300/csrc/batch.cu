@@ -8,6 +8,9 @@
 //      in ONE persistent launch per combination of axis kinds: the resident blocks walk the
 //      virtual blocks of all runs (a run's share in proportion to its particle capacity),
 //      each taking its run's parameters from a device table;
+//      (cpic_batch_set_mode: the default uses this launch for fixed-field particle steps and
+//      leaves the push in the run branches for full cycles, where the field solves dominate
+//      and branches that do not wait for each other overlap better, as measured);
 //   3. one branch per run again: step counter, injection, halo fold, the cell sort when it
 //      is due and, for full cycles, the field solve (the cluster kernel or the conditional
 //      V-cycle loop).
@@ -44,6 +47,7 @@ struct cpic_batch {
         int kernels = 0;
     };
     std::map<std::string, Graph> graphs;
+    int mode = CPIC_BATCH_AUTO;  // cpic_batch_set_mode
 };
 
 namespace cpic {
@@ -103,7 +107,8 @@ int build_push_tables(cpic_batch* b, std::vector<PushGroup>* groups) {
 
 int capture(cpic_batch* b, bool solve, const std::string& key, cpic_batch::Graph* out) {
     std::vector<PushGroup> groups;
-    int st = build_push_tables(b, &groups);  // before the capture: it allocates and copies
+    const bool persistent = b->mode == CPIC_BATCH_PERSISTENT || (b->mode == CPIC_BATCH_AUTO && !solve);
+    int st = persistent ? build_push_tables(b, &groups) : CPIC_OK;  // before the capture: it allocates
     if (st) return st;
     CPIC_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaEventRecord(b->fork, b->stream);
@@ -118,7 +123,7 @@ int capture(cpic_batch* b, bool solve, const std::string& key, cpic_batch::Graph
         }
         cudaStream_t saved = r->stream;
         r->stream = b->branch[i];
-        st = enqueue_step_pre(r, !push2d_batchable(r));
+        st = enqueue_step_pre(r, !persistent || !push2d_batchable(r));
         r->stream = saved;
         if (st) break;
         e = cudaEventRecord(b->join_pre[i], b->branch[i]);
@@ -288,6 +293,19 @@ int cpic_batch_size(const cpic_batch* b, int* n) {
         return CPIC_ERR_INVALID;
     }
     *n = (int)b->runs.size();
+    return CPIC_OK;
+}
+
+int cpic_batch_set_mode(cpic_batch* b, int mode) {
+    if (!b || mode < CPIC_BATCH_AUTO || mode > CPIC_BATCH_PERSISTENT) {
+        set_error("batch_set_mode: NULL batch or unknown mode %d", mode);
+        return CPIC_ERR_INVALID;
+    }
+    if (mode != b->mode) {
+        CPIC_CUDA(cudaStreamSynchronize(b->stream));
+        drop_graphs(b);
+    }
+    b->mode = mode;
     return CPIC_OK;
 }
 

@@ -42,8 +42,9 @@ def _same(a, b):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("solve", [True, False])
-def test_batch_equals_alone(cpic, solve):
+def test_batch_equals_alone(cpic, solve, mode):
     nsteps = 7  # crosses two sorts (interval 3)
     alone = []
     for spec in SPECS:
@@ -54,6 +55,7 @@ def test_batch_equals_alone(cpic, solve):
         r.close()
     runs = [_make(cpic, spec) for spec in SPECS]
     b = cpic.Batch(8)
+    b.set_mode(mode)
     for r in runs:
         r.initialize()
         b.add(r)
@@ -120,6 +122,7 @@ def test_mixed_batch_equals_alone(cpic):
         r.close()
     runs = [mk() for mk in makers()]
     b = cpic.Batch(8)
+    b.set_mode(cpic.CPIC_BATCH_PERSISTENT)
     for r in runs:
         r.initialize()
         b.add(r)
