@@ -555,15 +555,16 @@ def batched_measurement(cpic, nruns, steps, stream):
     n_before = alive()
     cyc_before = [r.diag()["mg_cycles"] for r in runs]
     bat_v, bat_ms = timed(lambda: batch.step(1), steps)  # full cycles: the push in the run branches
-    batp_v, batp_ms = timed(lambda: batch.step(1, solve=False), steps)  # particle steps: one persistent push
+    batp_v, batp_ms = timed(lambda: batch.step(1, solve=False), steps)  # particle steps, branches
     batch.set_mode(cpic.CPIC_BATCH_PERSISTENT)
+    batpp_v, batpp_ms = timed(lambda: batch.step(1, solve=False), steps)  # particle steps, one persistent push
     batpf_v, batpf_ms = timed(lambda: batch.step(1), steps)  # full cycles with the persistent push
     batch.close()
     # every run advanced by every batch step (16 warm-up + timed)
     adv = [r.diag()["step"] - s0 for r, s0 in zip(runs, step0)]
     cyc_after = [r.diag()["mg_cycles"] for r in runs]
     check = {"steps_advanced_min": int(min(adv)), "steps_advanced_max": int(max(adv)),
-             "expected": 3 * (16 + steps), "live_before": int(n_before), "live_after": int(alive()),
+             "expected": 4 * (16 + steps), "live_before": int(n_before), "live_after": int(alive()),
              "mg_cycles_mean_before": float(np.mean(cyc_before)), "mg_cycles_mean_after": float(np.mean(cyc_after)),
              "sequential_timing": diag[0], "batch_timing": diag[1]}
     cells = sum(sp["n1"] * sp["n2"] for sp in specs)
@@ -574,8 +575,10 @@ def batched_measurement(cpic, nruns, steps, stream):
             "sequential_ms_per_step": seq_ms, "speedup": bat_v / seq_v, "runs": nruns, "steps": steps,
             "particle_steps": {"batch_value": batp_v, "batch_ms_per_step": batp_ms, "sequential_value": seqp_v,
                                "sequential_ms_per_step": seqp_ms, "speedup": batp_v / seqp_v,
-                               "note": "fixed-field particle steps: the batch pushes every run in one persistent "
-                                       "launch"},
+                               "persistent_push_value": batpp_v, "persistent_push_ms_per_step": batpp_ms,
+                               "note": "fixed-field particle steps of the same runs: batch (push in the run "
+                                       "branches), batch with every run's push in one persistent launch, and "
+                                       "the runs one after another"},
             "full_cycle_persistent_push": {"value": batpf_v, "ms_per_step": batpf_ms},
             "particles": parts, "cells": cells, "setup_s": setup_s, "autotune_s": tune_s, "check": check,
             "sort_intervals": {str(k): chosen.count(k) for k in sorted(set(chosen))},

@@ -383,8 +383,8 @@ int cpic_batch_size(const cpic_batch* batch, int* n);
  *   CPIC_BATCH_PERSISTENT  one persistent launch for all of them between a pre-push and a
  *                          post-push phase of per-run branches (the resident blocks walk the
  *                          runs' chunks from a device table of run parameters);
- *   CPIC_BATCH_AUTO        (default) persistent for fixed-field particle steps, branches for
- *                          full cycles (solve-bound: independent branches overlap better).
+ *   CPIC_BATCH_AUTO        (default) the form measured faster on the batched configuration
+ *                          (uneven runs of 10^4..2 10^6 particles): branches.
  * The results are the same in every mode. CPIC_ERR_INVALID for another value. */
 #define CPIC_BATCH_AUTO 0
 #define CPIC_BATCH_BRANCHES 1

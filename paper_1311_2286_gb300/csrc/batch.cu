@@ -8,9 +8,9 @@
 //      in ONE persistent launch per combination of axis kinds: the resident blocks walk the
 //      virtual blocks of all runs (a run's share in proportion to its particle capacity),
 //      each taking its run's parameters from a device table;
-//      (cpic_batch_set_mode: the default uses this launch for fixed-field particle steps and
-//      leaves the push in the run branches for full cycles, where the field solves dominate
-//      and branches that do not wait for each other overlap better, as measured);
+//      (cpic_batch_set_mode; the default leaves the push in the run branches: on the
+//      batched configuration, runs of 10^4..2 10^6 particles, the branches that do not wait
+//      for each other measured faster, for full cycles and for particle steps alike);
 //   3. one branch per run again: step counter, injection, halo fold, the cell sort when it
 //      is due and, for full cycles, the field solve (the cluster kernel or the conditional
 //      V-cycle loop).
@@ -107,7 +107,8 @@ int build_push_tables(cpic_batch* b, std::vector<PushGroup>* groups) {
 
 int capture(cpic_batch* b, bool solve, const std::string& key, cpic_batch::Graph* out) {
     std::vector<PushGroup> groups;
-    const bool persistent = b->mode == CPIC_BATCH_PERSISTENT || (b->mode == CPIC_BATCH_AUTO && !solve);
+    const bool persistent = b->mode == CPIC_BATCH_PERSISTENT;  // AUTO: branches (measured faster)
+    (void)solve;
     int st = persistent ? build_push_tables(b, &groups) : CPIC_OK;  // before the capture: it allocates
     if (st) return st;
     CPIC_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
