@@ -369,6 +369,43 @@ def end_to_end(run, cpic, steps):
             "copy_gbs": (h2d + d2h) / secs / 1e9}
 
 
+def map2_microbench(cpic, stream, steps=200):
+    """The mover-timing experiment's shape (Sec. III, Tables II-III): fixed fields on the
+    map2 square, 64 x 64 cells, 100 particles per cell (409,600 electrons, uniform in
+    physical space, vth = 0.3 so that the largest time step moves a particle about one
+    cell), periodic, for eps = 0 (uniform grid) and eps = 0.1 (Jacobian ratio 4.4) and
+    dt = 0.001 ... 0.05; device time per particle-step, and the same normalised to the
+    uniform grid at dt = 0.001 as the paper's tables are."""
+    import torch
+
+    from paper_1311_2286_gb300 import workloads as wl
+
+    cs = ctypes_stream(stream)
+    rng = np.random.default_rng(17)
+    phi = wl.random_field(rng, (64, 64), 0.05)
+    out = {}
+    for eps in (0.0, 0.1):
+        w = wl.langmuir_map2(64, 64, eps=eps, ppc=100, vth=0.3, amp=0.0, dt=0.001, seed=5)
+        for dt in (0.001, 0.002, 0.004, 0.01, 0.025, 0.05):
+            w.dt = dt
+            run = cpic.run_from_workload(w, sort_interval=4, stream=cs)
+            run.set_phi(phi)
+            run.step_particles(8)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            run.step_particles(steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ns = a.elapsed_time(b) * 1e6 / (steps * w.particles[0].n)
+            out[f"eps{eps}_dt{dt}"] = ns
+            run.close()
+    base = out["eps0.0_dt0.001"]
+    return {"ns_per_particle_step": out, "normalised": {k: v / base for k, v in out.items()},
+            "workload": "map2 64x64, 100 ppc (409,600 particles), vth 0.3, fixed random potential, periodic, "
+                        f"{steps} fixed-field particle steps per point (sort every 4), CUDA events"}
+
+
 def serve_requests(cpic, nreq, steps, seed=4):
     """The served configuration's request mix: half 2D cylinders, half 3D spheres, scale
     s ~ U[0.25, 1] on the particle count (cylinder 2M, sphere 32M per species at 1) and on
@@ -653,6 +690,7 @@ def main():
     ap.add_argument("--serve-steps", type=int, default=20, help="PIC cycles per request")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second (Poisson)")
     ap.add_argument("--serve-seq", type=int, default=30, help="requests of the sequential baseline")
+    ap.add_argument("--no-microbench", action="store_true", help="skip the map2 mover-timing experiment")
     ap.add_argument("--tuning", default="", help="S,C,T: fixed sort interval, push chunk and deposit tiling of the "
                                                  "headline run instead of the autotuner (for profiling)")
     args = ap.parse_args()
@@ -714,6 +752,7 @@ def main():
     if args.cyl64_particles > 0:
         cyl64 = cylinder_measurement(cpic, 512, 1024, args.cyl64_particles, args.steps, args.warmup, args.full_steps,
                                      stream, flush, device_load=True, profile=PROFILE2)
+    micro = None if args.no_microbench else map2_microbench(cpic, stream)
     if args.batch_runs > 0:
         batched = batched_measurement(cpic, args.batch_runs, args.batch_steps, stream)
     if args.serve_requests > 0:
@@ -746,6 +785,7 @@ def main():
             "cylinder_2d_512x1024": cyl64,
             "batched": batched,
             "served": served,
+            "map2_mover_timing": micro,
             "gpu_launches": head["gpu_launches"],
             "gpu_launches_note": "kernels launched in the timed particle steps (kernel nodes of each replayed "
                                  "CUDA graph, counted by the library)",
