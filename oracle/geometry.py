@@ -128,6 +128,7 @@ class Geometry:
     Jc: np.ndarray  # cell Jacobians (cell area / volume)
     omega_c: np.ndarray  # cell geometric factor Omega
     face: list  # per axis a: coefficient arrays coef[b][face index] (Omega J g^{ab})
+    axisym: bool = False  # Omega = r (2D cylindrical geometry with azimuthal symmetry)
 
     def k32(self) -> np.ndarray:
         """FP32 vertex table of k in cell units, [..., a, alpha] (round to nearest)."""
@@ -271,5 +272,5 @@ def build_geometry(X: np.ndarray, periodic, axisym: bool = False) -> Geometry:
         face = face_coefficients_3d(X, dv)
     return Geometry(
         dim=D, n=n, periodic=tuple(bool(p) for p in periodic), X=X, j=j, k=k,
-        Jc=cell_jacobian(X), omega_c=cell_omega(X, axisym), face=face,
+        Jc=cell_jacobian(X), omega_c=cell_omega(X, axisym), face=face, axisym=bool(axisym),
     )

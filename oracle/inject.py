@@ -52,6 +52,25 @@ def face_length_2d(X, side):
     return acc
 
 
+def face_ring_areas_2d(X, side):
+    """Axisymmetric runs (2D (r, z) map, Omega = r): the surface of revolution of each face
+    segment of the xi = 0 / xi = 1 face, 2 pi r_mid |dX| (r_mid the mean radius of the
+    segment's two vertices), in segment order."""
+    col = X[:, 0 if side == 0 else -1, :]
+    out = np.empty(col.shape[0] - 1)
+    for j in range(col.shape[0] - 1):
+        d = col[j + 1] - col[j]
+        out[j] = 2.0 * math.pi * (0.5 * (col[j, 0] + col[j + 1, 0])) * math.sqrt(d[0] * d[0] + d[1] * d[1])
+    return out
+
+
+def face_area_axisym(X, side):
+    acc = 0.0
+    for x in face_ring_areas_2d(X, side):
+        acc += float(x)
+    return acc
+
+
 def rate_per_step(density, vth, area, dt, w):
     return (((density * vth) * INV_SQRT_2PI) * area) * dt / w
 
@@ -74,16 +93,29 @@ def draws(count, step, species, seed):
     return np.concatenate(out, axis=1)  # (count, 8)
 
 
-def inject_2d(k64, n, side, count, step, species, seed, vth, drift, dt):
+def inject_2d(k64, n, side, count, step, species, seed, vth, drift, dt, ring_areas=None):
     """New particles on the face normal to axis 0 (side 0: xi = 0, side 1: xi = 1).
     k64: FP64 vertex table (N2+1, N1+1, a, alpha). Returns (idx (2, m), t32 (2, m),
-    v32 (3, m), keep mask over the count draws)."""
+    v32 (3, m), keep mask over the count draws). ring_areas (axisymmetric runs): the face
+    segments' surfaces of revolution; the segment is then drawn by inverse CDF of those
+    (the first whose inclusive prefix exceeds U0 * total), the offset along it is U5, the
+    out-of-plane component is v_theta, and axis 1 is not periodic (a particle whose partial
+    push leaves it is dropped)."""
     n1, n2 = n
     U = draws(count, step, species, seed)
-    u1 = U[:, 0] * n2
-    j = np.floor(u1).astype(np.int64)
-    j = np.minimum(j, n2 - 1)
-    s = u1 - j
+    if ring_areas is None:
+        u1 = U[:, 0] * n2
+        j = np.floor(u1).astype(np.int64)
+        j = np.minimum(j, n2 - 1)
+        s = u1 - j
+    else:
+        cdf = np.empty_like(ring_areas)
+        acc = 0.0
+        for i, x in enumerate(ring_areas):
+            acc += float(x)
+            cdf[i] = acc
+        j = np.minimum(np.searchsorted(cdf, U[:, 0] * acc, side="right"), n2 - 1).astype(np.int64)
+        s = U[:, 5]
     col = 0 if side == 0 else n1
     kb = (1.0 - s)[:, None, None] * k64[j, col] + s[:, None, None] * k64[j + 1, col]
     ga = kb[:, 0, :]  # d u^0 / d x
@@ -115,8 +147,11 @@ def inject_2d(k64, n, side, count, step, species, seed, vth, drift, dt):
         c = c + one
         out_idx[a] = c.astype(np.int64)
         out_t[a] = f32
-    out_idx[1] = np.mod(out_idx[1], n2)
-    keep = (out_idx[0] >= 0) & (out_idx[0] < n1)
+    if ring_areas is None:
+        out_idx[1] = np.mod(out_idx[1], n2)
+        keep = (out_idx[0] >= 0) & (out_idx[0] < n1)
+    else:
+        keep = (out_idx[0] >= 0) & (out_idx[0] < n1) & (out_idx[1] >= 0) & (out_idx[1] < n2)
     return out_idx[:, keep], out_t[:, keep], v32[:, keep], keep
 
 

@@ -75,10 +75,36 @@ def boris64(v, E3, h, B):
     return vm + np.cross(vp.T, s).T + h * E3
 
 
-def push64(idx, t, v, k, G, dt, qm, n, pbc, return_kicked=False, B=None):
+def axisym_step(rn, v, dt):
+    """The cylindrical part of the axisymmetric mover (2D (r, z) meridional plane, Omega = r,
+    azimuthal symmetry; Sec. II.B: the cylindrical Boris mover in its hybrid form; reading):
+    the particle moves on a straight line in 3D over the step, from (r, 0, z) with velocity
+    (v_r, v_theta, v_z): x = r + dt v_r, y = dt v_theta, r' = sqrt(x^2 + y^2); the meridional
+    displacement is (r' - r, dt v_z) and the velocity turns with the frame by the angle
+    alpha of (x, y): v_r' = cos a v_r + sin a v_theta, v_theta' = cos a v_theta - sin a v_r
+    (the inertial forces; r v_theta is kept). v = (v_r, v_z, v_theta). Returns the
+    displacement (2, n) and the velocity (3, n) in the new frame."""
+    x = rn + dt * v[0]
+    y = dt * v[2]
+    r1 = np.sqrt(x * x + y * y)
+    safe = r1 > 0.0
+    ca = np.where(safe, x / np.where(safe, r1, 1.0), 1.0)
+    sa = np.where(safe, y / np.where(safe, r1, 1.0), 0.0)
+    disp = np.stack([r1 - rn, dt * v[1]])
+    vout = v.copy()
+    vout[0] = ca * v[0] + sa * v[2]
+    vout[2] = ca * v[2] - sa * v[0]
+    return disp, vout
+
+
+def push64(idx, t, v, k, G, dt, qm, n, pbc, return_kicked=False, B=None, R=None):
     """One FP64 push. idx (D, n) int, t (D, n), v (3, n); k: vertex table (..., a, alpha);
     G: vertex table (..., a); qm: q/m per particle (n,) or scalar; B: uniform magnetic
-    field (3,) or None (the kick is then v += dt q/m E; with B, the Boris step).
+    field (3,) or None (the kick is then v += dt q/m E; with B, the Boris step); R: for an
+    axisymmetric run (2D, Omega = r), the vertex table of the cylindrical radius: the
+    position then advances by the meridional displacement of axisym_step instead of dt v,
+    predictor xi' = xi^n + 1/2 k(xi^n) disp, corrector xi^{n+1} = xi^n + k(xi') disp, and
+    the velocity is turned into the new frame.
     Returns (idx, t, v, face) with face = -1 alive or 2a+side for removed particles, plus
     the kicked velocity before any reflection when return_kicked."""
     D = idx.shape[0]
@@ -94,9 +120,15 @@ def push64(idx, t, v, k, G, dt, qm, n, pbc, return_kicked=False, B=None):
         v = boris64(v, E3, 0.5 * dt * np.asarray(qm), B)
     else:
         v[:D] = v[:D] + dt * np.asarray(qm) * E.T
-    # predictor
-    d = np.einsum("pab,bp->ap", kp, v[:D])
-    cpred, tpred = _renorm(t + 0.5 * dt * d)
+    vk = v.copy()
+    if R is not None:
+        disp, vrot = axisym_step(gather(R, idx, t), v, dt)
+        d = np.einsum("pab,bp->ap", kp, disp)
+        cpred, tpred = _renorm(t + 0.5 * d)
+    else:
+        # predictor
+        d = np.einsum("pab,bp->ap", kp, v[:D])
+        cpred, tpred = _renorm(t + 0.5 * dt * d)
     ip = idx + cpred
     for a in range(D):
         if pbc[2 * a] == PBC_PERIODIC:
@@ -107,8 +139,13 @@ def push64(idx, t, v, k, G, dt, qm, n, pbc, return_kicked=False, B=None):
             ip[a] = np.clip(ip[a], 0, n[a] - 1)
             tpred[a] = np.where(low, 0.0, np.where(high, 1.0, tpred[a]))
     kq = gather(k, ip, tpred)
-    d2 = np.einsum("pab,bp->ap", kq, v[:D])
-    cn, tn = _renorm(t + dt * d2)
+    if R is not None:
+        d2 = np.einsum("pab,bp->ap", kq, disp)
+        cn, tn = _renorm(t + d2)
+        v = vrot
+    else:
+        d2 = np.einsum("pab,bp->ap", kq, v[:D])
+        cn, tn = _renorm(t + dt * d2)
     inew = idx + cn
     face = np.full(idx.shape[1], -1, dtype=np.int64)
     for a in range(D):
@@ -119,7 +156,7 @@ def push64(idx, t, v, k, G, dt, qm, n, pbc, return_kicked=False, B=None):
             hi = (inew[a] >= n[a]) & (face < 0)
             face[lo] = 2 * a
             face[hi] = 2 * a + 1
-    ke_v = v.copy()
+    ke_v = vk
     for a in range(D):
         if pbc[2 * a] != PBC_REFLECT:
             continue
@@ -180,7 +217,7 @@ def _lib():
         lib = ctypes.CDLL(path)
         P = ctypes.c_void_p
         lib.replay_push.argtypes = [ctypes.c_int, P, P, ctypes.c_long, P, P, P, P, P,
-                                    ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P, P]
+                                    ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P, P, P]
         lib.replay_push.restype = None
         lib.replay_kick.argtypes = [ctypes.c_int, P, ctypes.c_long, P, P, P, P, P, ctypes.c_float, P]
         lib.replay_kick.restype = None
@@ -204,11 +241,12 @@ def boris_constants32(dt, qm, B, fraction=1.0):
     return np.asarray([h, *t, *s], dtype=np.float32)
 
 
-def push32(idx, t32, v32, k32, G32, n, pbc, dtqm, hdt, dt, boris=None):
+def push32(idx, t32, v32, k32, G32, n, pbc, dtqm, hdt, dt, boris=None, R32=None):
     """FP32 replay of one push. Arguments as push64 but float32 tables (numpy vertex
     layout, k32 (..., a, alpha), G32 (..., a)) and float32 coefficients
     dtqm = float32(dt q / m), hdt = float32(dt / 2), dt = float32(dt); boris: the
-    boris_constants32 of a magnetised run (None: no field).
+    boris_constants32 of a magnetised run (None: no field); R32: the FP32 vertex table of the
+    cylindrical radius of an axisymmetric run (None: Cartesian).
     Returns (idx, t, v, face, ke_fp)."""
     D = idx.shape[0]
     np_ = idx.shape[1]
@@ -222,9 +260,10 @@ def push32(idx, t32, v32, k32, G32, n, pbc, dtqm, hdt, dt, boris=None):
     face = np.empty(np_, dtype=np.int32)
     ke = np.empty(np_, dtype=np.int64)
     bc = None if boris is None else np.ascontiguousarray(boris, dtype=np.float32)
+    Rc = None if R32 is None else np.ascontiguousarray(R32, dtype=np.float32).reshape(-1)
     _lib().replay_push(D, _ptr(nn), _ptr(pb), np_, _ptr(idx_c), _ptr(t_c), _ptr(v_c), _ptr(K), _ptr(G),
                        np.float32(dtqm), np.float32(hdt), np.float32(dt), _ptr(face), _ptr(ke),
-                       None if bc is None else _ptr(bc))
+                       None if bc is None else _ptr(bc), None if Rc is None else _ptr(Rc))
     return idx_c, t_c, v_c, face, ke
 
 
@@ -257,7 +296,7 @@ def _lib64():
         lib = ctypes.CDLL(build_pic64())
         P = ctypes.c_void_p
         lib.oracle_push64.argtypes = [ctypes.c_int, P, P, ctypes.c_long, P, P, P, P, P, ctypes.c_double,
-                                      ctypes.c_double, P, P, ctypes.c_int, P]
+                                      ctypes.c_double, P, P, ctypes.c_int, P, P]
         lib.oracle_push64.restype = None
         lib.oracle_deposit64.argtypes = [ctypes.c_int, P, P, ctypes.c_long, P, P, P, ctypes.c_int]
         lib.oracle_deposit64.restype = ctypes.c_int
@@ -272,7 +311,7 @@ def openmp_threads():
     return int(_lib64().oracle_openmp_threads())
 
 
-def push64_c(idx, t, v, k, G, dt, qm, n, pbc, threads=1, inplace=False, B=None):
+def push64_c(idx, t, v, k, G, dt, qm, n, pbc, threads=1, inplace=False, B=None, R=None):
     """push64 as C loops. qm is a scalar. Returns (idx, t, v, face, vdot) with vdot the
     per-particle v^{n-1/2} . v^{n+1/2} (kicked velocity, before any reflection). With
     inplace, idx (int64), t and v (float64), C-contiguous, are updated and returned."""
@@ -293,7 +332,8 @@ def push64_c(idx, t, v, k, G, dt, qm, n, pbc, threads=1, inplace=False, B=None):
     face = np.empty(np_, dtype=np.int32)
     vdot = np.empty(np_, dtype=np.float64)
     Bv = None if B is None or not np.any(np.asarray(B)) else np.ascontiguousarray(B, dtype=np.float64)
+    Rc = None if R is None else np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
     _lib64().oracle_push64(D, _ptr(nn), _ptr(pb), np_, _ptr(idx_c), _ptr(t_c), _ptr(v_c), _ptr(K), _ptr(Gc),
                            float(dt), float(qm), _ptr(face), _ptr(vdot), int(threads),
-                           None if Bv is None else _ptr(Bv))
+                           None if Bv is None else _ptr(Bv), None if Rc is None else _ptr(Rc))
     return idx_c, t_c, v_c, face.astype(np.int64), vdot

@@ -86,21 +86,26 @@ class OraclePIC:
         self.injected = [0] * len(self.species)
         self._face_area = {}
         self.B0 = getattr(wl, "B0", None)  # uniform magnetic field: Boris kick
+        # axisymmetric runs: the vertex table of the cylindrical radius (component 0 of the map)
+        self.R = np.ascontiguousarray(self.geom.X[..., 0]) if self.geom.axisym else None
 
     # ---- steps ---------------------------------------------------------------------
     def charge(self):
         """Q_c (numpy cell layout)."""
         Q = self.wl.background * self.geom.Jc
+        # axisymmetric runs: a macro-particle is a ring of charge q w (Omega_c Q_c must hold
+        # the ring charge / 2 pi)
+        ring = 1.0 / (2.0 * np.pi * self.geom.omega_c) if self.geom.axisym else 1.0
         for sp in self.species:
             if self.precision == "fp64":
                 if self.engine == "c":
                     C = dep.deposit_exact_c(sp.idx, sp.t, self.n, self.periodic, self.threads)
                 else:
                     C = dep.deposit_exact(sp.idx, sp.t, self.n, self.periodic)
-                Q = Q + (sp.q * sp.w) * C
+                Q = Q + (sp.q * sp.w) * C * ring
             else:
                 C = dep.deposit_fixed(sp.idx, sp.t, self.n, self.periodic)
-                Q = Q + (sp.q * sp.w) * np.ldexp(C.astype(np.float64), -dep.QF)
+                Q = Q + (sp.q * sp.w) * np.ldexp(C.astype(np.float64), -dep.QF) * ring
         return Q
 
     def solve(self):
@@ -117,7 +122,11 @@ class OraclePIC:
             qobj = q0
             for sp in self.species:
                 qobj += sp.q * sp.w * float(sp.absorbed[face])
-            V = -(qobj + self._face_flux(self.phi, face, 0.0)) / self._cpsi
+            if self.geom.axisym:  # Gauss's law on the ring-charge scale of the right-hand side
+                qobj_rhs = qobj / (2.0 * np.pi)
+            else:
+                qobj_rhs = qobj
+            V = -(qobj_rhs + self._face_flux(self.phi, face, 0.0)) / self._cpsi
             self.phi = self.phi + V * self._psi
             self.bcval[face] = V  # the vertex field's Dirichlet value on that face
             self.object_potential, self.object_charge = V, qobj
@@ -184,18 +193,19 @@ class OraclePIC:
                 sp.t = np.ascontiguousarray(sp.t, dtype=np.float64)
                 sp.v = np.ascontiguousarray(sp.v, dtype=np.float64)
                 idx, t, v, face, vdot = mover.push64_c(sp.idx, sp.t, sp.v, k, G, self.dt, qm, self.n, self.pbc,
-                                                       self.threads, inplace=True, B=self.B0)
+                                                       self.threads, inplace=True, B=self.B0, R=self.R)
                 ke.append(0.5 * sp.m * sp.w * float(np.sum(vdot)))
             elif self.precision == "fp64":
                 vold = sp.v
                 idx, t, v, face, vk = mover.push64(sp.idx, sp.t, sp.v, k, G, self.dt, qm, self.n, self.pbc,
-                                                   return_kicked=True, B=self.B0)
+                                                   return_kicked=True, B=self.B0, R=self.R)
                 ke.append(0.5 * sp.m * sp.w * float(np.sum(vold * vk)))
             else:
                 idx, t, v, face, kefp = mover.push32(
                     sp.idx, sp.t, sp.v, k, G, self.n, self.pbc,
                     np.float32(self.dt * qm), np.float32(0.5 * self.dt), np.float32(self.dt),
-                    boris=mover.boris_constants32(self.dt, qm, self.B0))
+                    boris=mover.boris_constants32(self.dt, qm, self.B0),
+                    R32=None if self.R is None else self.R.astype(np.float32))
                 ke.append(0.5 * sp.m * sp.w * float(np.ldexp(float(kefp.sum()), -24)))
             alive = face < 0
             if np.all(alive):
@@ -208,16 +218,20 @@ class OraclePIC:
             sp = self.species[s]
             side = face % 2
             if side not in self._face_area:
-                self._face_area[side] = (inject.face_length_2d(self.geom.X, side) if self.D == 2
-                                         else inject.face_area_3d(self.geom.X, side))
+                if self.geom.axisym:
+                    self._face_area[side] = inject.face_area_axisym(self.geom.X, side)
+                else:
+                    self._face_area[side] = (inject.face_length_2d(self.geom.X, side) if self.D == 2
+                                             else inject.face_area_3d(self.geom.X, side))
             area = self._face_area[side]
             rate = inject.rate_per_step(dens, vth, area, self.dt, sp.w)
             cnt = inject.count_at_step(rate, self.step_index)
             if cnt == 0:
                 continue
             if self.D == 2:
+                rings = inject.face_ring_areas_2d(self.geom.X, side) if self.geom.axisym else None
                 idx, t32, v32, _ = inject.inject_2d(self.geom.k, self.n, side, cnt, self.step_index, s, seed,
-                                                    vth, (0.0, 0.0, 0.0), self.dt)
+                                                    vth, (0.0, 0.0, 0.0), self.dt, ring_areas=rings)
             else:
                 idx, t32, v32, _ = inject.inject_3d(self.geom.X, self.geom.k, self.n, side, cnt, self.step_index, s,
                                                     seed, vth, (0.0, 0.0, 0.0), self.dt)

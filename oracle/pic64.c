@@ -100,7 +100,8 @@ static void boris64(double* v, const double* E, double h, const double* B) {
 }
 
 static void push_one(int D, const int* n, const int* pbc, const double* K, const double* G, double dt, double qm,
-                     const double* B, long* c, double* t, double* v, int* face_out, double* vdot_out) {
+                     const double* B, const double* R, long* c, double* t, double* v, int* face_out,
+                     double* vdot_out) {
     double kp[9], gp[3], E[3], vold[3];
     gather(D, n, K, D * D, c, t, kp);
     gather(D, n, G, D, c, t, gp);
@@ -118,14 +119,34 @@ static void push_one(int D, const int* n, const int* pbc, const double* K, const
         const double dtqm = dt * qm;
         for (int b = 0; b < D; ++b) v[b] = v[b] + dtqm * E[b];
     }
+    double vk[3] = {v[0], v[1], v[2]};
+    /* axisymmetric run: the meridional displacement of straight 3D motion over the step and
+     * the frame's turn (mover.py axisym_step) */
+    double disp[2] = {0.0, 0.0}, vrot[3] = {v[0], v[1], v[2]};
+    if (R) {
+        double rn;
+        gather(D, n, R, 1, c, t, &rn);
+        const double x = rn + dt * v[0], y = dt * v[2];
+        const double r1 = sqrt(x * x + y * y);
+        const double ca = r1 > 0.0 ? x / r1 : 1.0, sa = r1 > 0.0 ? y / r1 : 0.0;
+        disp[0] = r1 - rn;
+        disp[1] = dt * v[1];
+        vrot[0] = ca * v[0] + sa * v[2];
+        vrot[2] = ca * v[2] - sa * v[0];
+    }
     /* predictor: in 2D only the in-plane velocity moves xi */
     long ip[3];
     double tp[3];
     for (int a = 0; a < D; ++a) {
         double d = 0.0;
-        for (int b = 0; b < D; ++b) d = d + kp[a * D + b] * v[b];
         long dc;
-        renorm(t[a] + (0.5 * dt) * d, &dc, &tp[a]);
+        if (R) {
+            for (int b = 0; b < D; ++b) d = d + kp[a * D + b] * disp[b];
+            renorm(t[a] + 0.5 * d, &dc, &tp[a]);
+        } else {
+            for (int b = 0; b < D; ++b) d = d + kp[a * D + b] * v[b];
+            renorm(t[a] + (0.5 * dt) * d, &dc, &tp[a]);
+        }
         ip[a] = c[a] + dc;
         if (pbc[2 * a] == PBC_PERIODIC) {
             ip[a] = wrap(ip[a], n[a]);
@@ -143,11 +164,18 @@ static void push_one(int D, const int* n, const int* pbc, const double* K, const
     double tn[3];
     for (int a = 0; a < D; ++a) {
         double d = 0.0;
-        for (int b = 0; b < D; ++b) d = d + kq[a * D + b] * v[b];
         long dc;
-        renorm(t[a] + dt * d, &dc, &tn[a]);
+        if (R) {
+            for (int b = 0; b < D; ++b) d = d + kq[a * D + b] * disp[b];
+            renorm(t[a] + d, &dc, &tn[a]);
+        } else {
+            for (int b = 0; b < D; ++b) d = d + kq[a * D + b] * v[b];
+            renorm(t[a] + dt * d, &dc, &tn[a]);
+        }
         cn[a] = c[a] + dc;
     }
+    if (R)
+        for (int q = 0; q < 3; ++q) v[q] = vrot[q];
     int face = -1;
     for (int a = 0; a < D; ++a) {
         if (pbc[2 * a] == PBC_PERIODIC) {
@@ -157,7 +185,7 @@ static void push_one(int D, const int* n, const int* pbc, const double* K, const
             else if (cn[a] >= n[a]) face = 2 * a + 1;
         }
     }
-    *vdot_out = vold[0] * v[0] + vold[1] * v[1] + vold[2] * v[2];
+    *vdot_out = vold[0] * vk[0] + vold[1] * vk[1] + vold[2] * vk[2];
     for (int a = 0; a < D; ++a) {
         if (pbc[2 * a] != PBC_REFLECT || face >= 0 || (cn[a] >= 0 && cn[a] < n[a])) continue;
         const int below = cn[a] < 0;
@@ -193,7 +221,7 @@ static void push_one(int D, const int* n, const int* pbc, const double* K, const
  * velocity, before any reflection). */
 void oracle_push64(int D, const int* n, const int* pbc, long np, int64_t* idx, double* t, double* v,
                    const double* K, const double* G, double dt, double qm, int32_t* face, double* vdot,
-                   int nthreads, const double* B) {
+                   int nthreads, const double* B, const double* R) {
     if (nthreads < 1) nthreads = 1;
 #pragma omp parallel for schedule(static) num_threads(nthreads)
     for (long p = 0; p < np; ++p) {
@@ -205,7 +233,7 @@ void oracle_push64(int D, const int* n, const int* pbc, long np, int64_t* idx, d
         }
         for (int q = 0; q < 3; ++q) vv[q] = v[q * np + p];
         int f;
-        push_one(D, n, pbc, K, G, dt, qm, B, c, tt, vv, &f, &vdot[p]);
+        push_one(D, n, pbc, K, G, dt, qm, B, R, c, tt, vv, &f, &vdot[p]);
         for (int a = 0; a < D; ++a) {
             idx[a * np + p] = c[a];
             t[a * np + p] = tt[a];

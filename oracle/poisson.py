@@ -147,10 +147,14 @@ def assemble(geom, bc, bcval):
 def charge_in_cells(geom, charge_counts, qw, background):
     """Q_c: sum_s q_s w_s C_{s,c} 2^-F plus a uniform background density times the cell
     volume J_c (eq. (pg) with the J_c of the density cancelled against the cell volume).
-    charge_counts: list of int64 arrays (numpy cell layout), one per species."""
+    charge_counts: list of int64 arrays (numpy cell layout), one per species.
+    Axisymmetric runs (Omega = r): a macro-particle is a ring of charge q w around the axis,
+    so its charge density is q w / (2 pi r J) and the right-hand side Omega_c Q_c needs
+    Q_c = (sum of ring charges) / (2 pi Omega_c) for the particles."""
     Q = background * geom.Jc
+    scale = 1.0 / (2.0 * np.pi * geom.omega_c) if geom.axisym else 1.0
     for C, f in zip(charge_counts, qw):
-        Q = Q + (f * np.ldexp(C.astype(np.float64), -FIXED_POINT_BITS))
+        Q = Q + (f * np.ldexp(C.astype(np.float64), -FIXED_POINT_BITS)) * scale
     return Q
 
 

@@ -104,7 +104,7 @@ static void gather(int D, const int* n, const float* Q, int nq, const int* c, co
  * ke = fmaf(vo2, v2, fmaf(vo1, v1, vo0 * v0)) (spec D). */
 void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* t, float* v,
                  const float* K, const float* G, float dtqm, float hdt, float dt, int* face,
-                 long long* ke_fp, const float* boris) {
+                 long long* ke_fp, const float* boris, const float* R) {
     for (long p = 0; p < np; ++p) {
         int c[3];
         float tt[3], vv[3], vo[3];
@@ -127,13 +127,43 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
             boris32(vv, E, boris);
         else
             for (int al = 0; al < D; ++al) vv[al] = fmaf(dtqm, E[al], vv[al]);
+        float vk[3] = {vv[0], vv[1], vv[2]}; /* kicked velocity (kinetic-energy tally) */
+        /* axisymmetric run (R: vertex cylindrical radius): straight 3D motion over the step,
+         * x = fmaf(dt, v_r, r), y = dt * v_theta, r' = sqrtf(fmaf(x, x, y * y)); meridional
+         * displacement (r' - r, dt * v_z); the frame turns by (x, y) / r' (cos, sin; (1, 0)
+         * at r' = 0): v_r = fmaf(cos, v_r, sin * v_theta), v_theta = fmaf(cos, v_theta,
+         * -(sin * v_r)); predictor t' = fmaf(0.5f, k . disp, t), corrector t + k' . disp */
+        float disp[2] = {0.0f, 0.0f}, vrot[3] = {vv[0], vv[1], vv[2]};
+        if (R) {
+            float rn;
+            gather(D, n, R, 1, c, tt, &rn);
+            const float x = fmaf(dt, vv[0], rn);
+            const float y = dt * vv[2];
+            const float r1 = sqrtf(fmaf(x, x, y * y));
+            float ca = 1.0f, sa = 0.0f;
+            if (r1 > 0.0f) {
+                ca = x / r1;
+                sa = y / r1;
+            }
+            disp[0] = r1 - rn;
+            disp[1] = dt * vv[1];
+            vrot[0] = fmaf(ca, vv[0], sa * vv[2]);
+            vrot[2] = fmaf(ca, vv[2], -(sa * vv[0]));
+        }
         /* predictor */
         int cp[3];
         float tp[3];
         for (int a = 0; a < D; ++a) {
-            float d = kp[a * D + 0] * vv[0];
-            for (int al = 1; al < D; ++al) d = fmaf(kp[a * D + al], vv[al], d);
-            float x = fmaf(hdt, d, tt[a]);
+            float x;
+            if (R) {
+                float d = kp[a * D + 0] * disp[0];
+                d = fmaf(kp[a * D + 1], disp[1], d);
+                x = fmaf(0.5f, d, tt[a]);
+            } else {
+                float d = kp[a * D + 0] * vv[0];
+                for (int al = 1; al < D; ++al) d = fmaf(kp[a * D + al], vv[al], d);
+                x = fmaf(hdt, d, tt[a]);
+            }
             if (!isfinite(x)) {
                 cp[a] = c[a];
                 tp[a] = tt[a];
@@ -160,9 +190,16 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
         int cn[3];
         float tn[3];
         for (int a = 0; a < D; ++a) {
-            float d = kq[a * D + 0] * vv[0];
-            for (int al = 1; al < D; ++al) d = fmaf(kq[a * D + al], vv[al], d);
-            float x = fmaf(dt, d, tt[a]);
+            float x;
+            if (R) {
+                float d = kq[a * D + 0] * disp[0];
+                d = fmaf(kq[a * D + 1], disp[1], d);
+                x = tt[a] + d;
+            } else {
+                float d = kq[a * D + 0] * vv[0];
+                for (int al = 1; al < D; ++al) d = fmaf(kq[a * D + al], vv[al], d);
+                x = fmaf(dt, d, tt[a]);
+            }
             if (!isfinite(x)) {
                 fc = 2 * D;
                 cn[a] = c[a];
@@ -186,8 +223,10 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
                 }
             }
         }
-        float ke = fmaf(vo[2], vv[2], fmaf(vo[1], vv[1], vo[0] * vv[0]));
+        float ke = fmaf(vo[2], vk[2], fmaf(vo[1], vk[1], vo[0] * vk[0]));
         ke_fp[p] = llrintf(ldexpf(ke, 24));
+        if (R)
+            for (int al = 0; al < 3; ++al) vv[al] = vrot[al];
         /* spec B: mirror about a reflecting face, reflect v about row a of k(xi') */
         if (fc < 0) {
             for (int a = 0; a < D && fc < 0; ++a) {

@@ -359,6 +359,46 @@ def sphere(n1=128, n2=128, n3=128, r0=1.0, R=30.0, theta_c=math.pi / 32, npart_p
     )
 
 
+def sphere_axisym(n1=128, n2=128, r1=1.0, r2=10.0, npart_per_species=1_000_000, phi_obj=-2.5, mass_ratio=1836.0,
+                  dt=0.1, seed=6, inject=True, capacity_factor=1.5):
+    """Sphere in plasma in 2D cylindrical geometry with azimuthal symmetry (Sec. III.B: the
+    spherical-shell map of eqs. (r), (z), Omega = r): sphere of radius r1 at xi = 0 (held at
+    phi_obj and absorbing, or floating), outer sphere r2 at xi = 1 (phi = 0, absorbing,
+    Maxwellian flux injection of both species), the z axis at eta = 0, 1 (Neumann field,
+    specular particles). Macro-particles are rings around the axis, loaded uniform in the
+    3D shell (r_sph^3 uniform, cos of the polar angle uniform) with equal weights;
+    velocities (v_r, v_z, v_theta) Maxwellian; T_i = T_e."""
+    rng = np.random.default_rng(seed)
+    vol = (4.0 / 3.0) * math.pi * (r2**3 - r1**3)
+    w = vol / npart_per_species
+    vti = 1.0 / math.sqrt(mass_ratio)
+    cap = int(npart_per_species * capacity_factor)
+    sp = [Species(-1.0, 1.0, w, 1.0, cap), Species(1.0, mass_ratio, w, vti, cap)]
+    parts = []
+    for s in sp:
+        rs = np.cbrt(r1**3 + rng.random(npart_per_species) * (r2**3 - r1**3))
+        polar = np.arccos(1.0 - 2.0 * rng.random(npart_per_species))
+        u = np.stack([(rs - r1) / (r2 - r1) * n1, (1.0 - polar / math.pi) * n2])
+        u[0] = np.clip(u[0], 0.0, np.nextafter(n1, 0))
+        u[1] = np.clip(u[1], 0.0, np.nextafter(n2, 0))
+        parts.append(_from_logical(u, (n1, n2), maxwellian(rng, npart_per_species, s.vth)))
+    inj = [(0, 1, 1.0, 1.0, seed * 1000 + 7), (1, 1, 1.0, vti, seed * 1000 + 8)] if inject else []
+    return Workload(
+        name=f"sphere_axisym_{n1}x{n2}_{2 * npart_per_species}",
+        dim=2,
+        n=(n1, n2),
+        vertices=sphere_axisym_vertices(n1, n2, r1, r2),
+        field_bc=[BC_DIRICHLET, BC_DIRICHLET, BC_NEUMANN, BC_NEUMANN],
+        field_bc_value=[phi_obj, 0.0, 0.0, 0.0],
+        particle_bc=[PBC_ABSORB, PBC_ABSORB, PBC_REFLECT, PBC_REFLECT],
+        dt=dt,
+        species=sp,
+        particles=parts,
+        omega_axisym=True,
+        injection=inj,
+    )
+
+
 def box_reflect(n1=32, n2=32, npart=50_000, vth=1.0, dt=0.1, seed=7):
     """2D unit square (uniform map) with specular walls on axis 0 (Neumann field) and a
     periodic axis 1; one electron species at a neutralising background."""

@@ -158,6 +158,33 @@ def test_replay32_matches_fp64_single_step():
     assert np.all(np.abs(ke - np.ldexp(ke64, 24)) <= np.abs(np.ldexp(ke64, 24)) * 2e-7 + 1)
 
 
+def test_replay32_axisym_matches_fp64_single_step():
+    """The FP32 replay of the axisymmetric mover (meridional displacement and frame turn)
+    agrees with the FP64 form to the single-step FP32 tolerance on the spherical-shell map
+    with a random radial-plus-noise field, including particles near the axis."""
+    n = (32, 32)
+    w = wl.sphere_axisym(32, 32, npart_per_species=20_000, seed=9, inject=False)
+    g = geometry.build_geometry(w.vertices, [False, False], axisym=True)
+    rng = np.random.default_rng(3)
+    phi = wl.random_field(rng, (32, 32), 0.3) + np.linspace(-3, 0, 32)
+    G = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value)
+    ps = w.particles[0]
+    idx = wl.unpack_cells(ps.cell, 2)
+    R = g.X[..., 0]
+    i64, t64, v64, f64 = mover.push64(idx, ps.t.astype(np.float64), ps.v.astype(np.float64), g.k, G, 0.1, -1.0, n,
+                                      w.particle_bc, R=R)
+    i32, t32, v32, f32, ke = mover.push32(idx, ps.t, ps.v, g.k.astype(np.float32), G.astype(np.float32), n,
+                                          w.particle_bc, np.float32(-0.1), np.float32(0.05), np.float32(0.1),
+                                          R32=R.astype(np.float32))
+    same = (f64 == f32)
+    assert same.mean() > 0.999
+    alive = same & (f64 < 0)
+    u64 = (i64 + t64)[:, alive]
+    u32 = (i32 + t32.astype(np.float64))[:, alive]
+    assert np.max(np.abs(u32 - u64)) < 32 * 2e-5
+    assert np.max(np.abs(v32 - v64)[:, alive]) / np.max(np.abs(v64)) < 2e-5
+
+
 def test_replay32_deterministic_and_absorbs():
     n = (16, 16)
     g = _uniform(*n)
@@ -232,7 +259,7 @@ def test_reflection_on_a_curved_cap_keeps_speed_and_flips_the_normal():
     assert np.all(np.sum(v1.T * kp[:, 1, :], axis=1)[hit] > 0)
 
 
-@pytest.mark.parametrize("case", ["map2", "cylinder", "box_reflect", "sphere3d"])
+@pytest.mark.parametrize("case", ["map2", "cylinder", "box_reflect", "sphere3d", "sphere_axisym"])
 def test_c_loop_mover_and_deposit_equal_the_numpy_forms(case):
     """oracle/pic64.c restates push64 and deposit_exact as loops (for long runs): the push
     is bit-identical to the numpy form (same operation order: positions, faces, velocities
@@ -247,25 +274,27 @@ def test_c_loop_mover_and_deposit_equal_the_numpy_forms(case):
     w = {"map2": lambda: wl.langmuir_map2(32, 32, eps=0.1, ppc=20, vth=0.3, seed=1),
          "cylinder": lambda: wl.cylinder(32, 64, npart_per_species=50_000, seed=2, inject=False),
          "box_reflect": lambda: wl.box_reflect(16, 16, 20_000, vth=2.0),
-         "sphere3d": lambda: wl.sphere(12, 10, 8, npart_per_species=20_000, seed=3)}[case]()
+         "sphere3d": lambda: wl.sphere(12, 10, 8, npart_per_species=20_000, seed=3),
+         "sphere_axisym": lambda: wl.sphere_axisym(24, 24, npart_per_species=30_000, seed=4, inject=False)}[case]()
     per = [w.field_bc[2 * a] == 0 for a in range(w.dim)]
-    g = geometry.build_geometry(w.vertices, per)
+    g = geometry.build_geometry(w.vertices, per, axisym=w.omega_axisym)
+    R = g.X[..., 0] if w.omega_axisym else None
     phi = wl.random_field(np.random.default_rng(0), tuple(reversed(w.n)), 0.5)
-    if case in ("cylinder", "sphere3d"):
+    if case in ("cylinder", "sphere3d", "sphere_axisym"):
         phi = phi + np.linspace(-5, 0, w.n[0])
     G = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value)
     ps = w.particles[0]
     idx = wl.unpack_cells(ps.cell, w.dim)
     t, v = ps.t.astype(np.float64), ps.v.astype(np.float64)
-    a = mover.push64(idx, t, v, g.k, G, w.dt, -1.0, w.n, w.particle_bc, return_kicked=True)
+    a = mover.push64(idx, t, v, g.k, G, w.dt, -1.0, w.n, w.particle_bc, return_kicked=True, R=R)
     for threads in (1, 3):
-        b = mover.push64_c(idx, t, v, g.k, G, w.dt, -1.0, w.n, w.particle_bc, threads=threads)
+        b = mover.push64_c(idx, t, v, g.k, G, w.dt, -1.0, w.n, w.particle_bc, threads=threads, R=R)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[3], b[3])
         assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
         assert np.array_equal(np.sum(a[4] * v, axis=0), b[4])
-    if case in ("cylinder", "sphere3d"):
+    if case in ("cylinder", "sphere3d", "sphere_axisym"):
         assert np.any(a[3] >= 0)  # the case removes particles
-    if case in ("box_reflect", "sphere3d"):
+    if case in ("box_reflect", "sphere3d", "sphere_axisym"):
         assert np.any(np.any(a[2] != a[4], axis=0) & (a[3] < 0))  # and reflects some
     alive = a[3] < 0
     e1 = dep.deposit_exact(a[0][:, alive], a[1][:, alive], w.n, per)
