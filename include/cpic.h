@@ -83,7 +83,14 @@ typedef struct cpic_config {
     int32_t particle_bc[6];       /* CPIC_PBC_* per face; periodic iff the field axis is */
     double dt;                    /* time step (normalised to 1/omega_pe) */
     double background;            /* uniform immobile charge density (e.g. +1: neutralising ions) */
-    int32_t axisymmetric;         /* 1: geometric factor Omega = x^1 in the solver (eq. (poiscurv)) */
+    int32_t axisymmetric;         /* 1 (2D only): azimuthal symmetry about the axis x^1 = 0
+                                     (Sec. II.B): geometric factor Omega = x^1 in the solver
+                                     (eq. (poiscurv)); a macro-particle is a ring of charge
+                                     q w (its deposit is divided by 2 pi Omega_c); the mover
+                                     moves it on a straight line in 3D and turns (v_r, v_theta)
+                                     with the frame, v = (v_r, v_z, v_theta); loading is
+                                     uniform in the 3D volume and injection faces are surfaces
+                                     of revolution */
     int32_t n_species;            /* 1 .. CPIC_MAX_SPECIES */
     double q[CPIC_MAX_SPECIES];   /* charge of a physical particle */
     double m[CPIC_MAX_SPECIES];   /* mass of a physical particle */
@@ -181,7 +188,10 @@ int cpic_get_particles(cpic_run* run, int sp, int64_t room, int64_t* n, int32_t*
                        float* v);
 /* Maxwellian flux injection through face `face` for species sp (Sec. III.A-B): density,
  * thermal speed vth, drift (host, 3 doubles, may be NULL), Philox4x32-10 key `seed`.
- * 2D faces normal to axis 0 only. */
+ * Faces normal to axis 0 (face 0 or 1) with absorbing particle boundaries, and the last
+ * logical axis periodic or (2D) the run axisymmetric, whose face is then a surface of
+ * revolution: segments drawn by ring area 2 pi r_mid |dX|, rate from the total. Otherwise
+ * CPIC_ERR_INVALID. */
 int cpic_set_injection(cpic_run* run, int sp, int face, double density, double vth,
                        const double* drift, uint64_t seed);
 
@@ -191,7 +201,9 @@ int cpic_set_injection(cpic_run* run, int sp, int face, double density, double v
  * s = 2 t / (1 + |t|^2); the positions advance as before (the hybrid predictor-corrector
  * with v^{n+1/2}; in 2D the velocity keeps three components). The start-up kick of
  * cpic_initialize then takes the Boris step over -dt/2. Magnetised runs push with the
- * generic particle kernel. Invalidates the run's captured step graphs. */
+ * generic particle kernel. Invalidates the run's captured step graphs. An axisymmetric run
+ * (v = (v_r, v_z, v_theta)) takes only a field along the symmetry axis, B = (0, B_z, 0)
+ * (CPIC_ERR_INVALID otherwise): the only uniform field that keeps the symmetry. */
 int cpic_set_magnetic_field(cpic_run* run, const double* B);
 
 /* Floating conductor (Sec. III.A-B: the object collects the particles that reach it and
@@ -203,14 +215,16 @@ int cpic_set_magnetic_field(cpic_run* run, const double* B);
  * 2 a^{00} (phi_c - V) summed over the face's cells in the finite-volume scheme. The solve
  * computes phi_0 with the conductor at 0 and adds V psi, psi the charge-free potential of
  * the conductor at 1 (solved here, once, with the other Dirichlet faces at 0). The face's
- * configured Dirichlet value is no longer used; cpic_get_diag reports V and Q. Requires the
- * map and a run that is not yet initialised (CPIC_ERR_STATE otherwise), a Dirichlet face
- * and a non-axisymmetric run (CPIC_ERR_INVALID otherwise). Synchronous. */
+ * configured Dirichlet value is no longer used; cpic_get_diag reports V and Q. In an
+ * axisymmetric run the flux sum is that of the Omega-weighted scheme, so Q / (2 pi) takes
+ * the place of Q. Requires the map and a run that is not yet initialised (CPIC_ERR_STATE
+ * otherwise) and a Dirichlet face (CPIC_ERR_INVALID otherwise). Synchronous. */
 int cpic_set_floating(cpic_run* run, int face, double charge0);
 
 /* Loads n particles of species sp on the device, replacing its particles: a Maxwellian
  * plasma of uniform physical density (the paper's runs start from one, Sec. III.A-B).
- * Cells are drawn with probability J_c / sum J_c (J_c the cell Jacobian), offsets uniform
+ * Cells are drawn with probability J_c / sum J_c (J_c the cell Jacobian; Omega_c J_c, the
+ * ring volume / 2 pi, in an axisymmetric run), offsets uniform
  * in each cell, velocities vth * N(0, 1) per component plus drift (host, 3 doubles, may be
  * NULL). Draws: Philox4x32-10, counter (i, 0x10AD, sp, word), key seed. Requires the map
  * (CPIC_ERR_STATE otherwise); n <= capacity[sp] (CPIC_ERR_INVALID otherwise). Asynchronous

@@ -193,7 +193,9 @@ void plan(cpic_run* r, Planner& P) {
     r->rhs_bc = P.take<double>(r->ncell);
     r->psi = P.take<double>(r->ncell);
     r->jcdf = P.take<double>(r->ncell);
-    r->fcdf = r->D == 3 ? P.take<double>((size_t)2 * r->n[1] * r->n[2]) : nullptr;
+    r->fcdf = r->D == 3 ? P.take<double>((size_t)2 * r->n[1] * r->n[2])
+                        : (c.axisymmetric ? P.take<double>((size_t)2 * r->n[1]) : nullptr);
+    r->R32 = c.axisymmetric ? P.take<float>((size_t)r->nvert) : nullptr;
     r->charge = P.take<unsigned long long>((size_t)c.n_species * r->ncell);
     r->charge_h = P.take<unsigned long long>((size_t)c.n_species * r->ncell_h);
     long long total = 0;
@@ -411,21 +413,53 @@ int after_map(cpic_run* r) {
     if (st) return st;
     // host-side constants: sum of J_c (singular projection) and face lengths (injection rate),
     // each summed sequentially in index order
-    std::vector<double> jc(r->ncell);
+    std::vector<double> jc(r->ncell), om(r->ncell);
     CPIC_CUDA(cudaMemcpyAsync(jc.data(), r->lev[0].Jc, sizeof(double) * r->ncell, cudaMemcpyDeviceToHost, r->stream));
+    CPIC_CUDA(cudaMemcpyAsync(om.data(), r->lev[0].omega, sizeof(double) * r->ncell, cudaMemcpyDeviceToHost, r->stream));
     std::vector<double> X((size_t)r->nvert * r->D);
     CPIC_CUDA(cudaMemcpyAsync(X.data(), r->lev[0].X, sizeof(double) * X.size(), cudaMemcpyDeviceToHost, r->stream));
     CPIC_CUDA(cudaStreamSynchronize(r->stream));
-    double sj = 0.0;
+    const bool axisym = r->cfg.axisymmetric != 0;
+    double sj = 0.0, sl = 0.0;
     for (long long c = 0; c < r->ncell; ++c) {
         sj += jc[c];
-        jc[c] = sj;  // inclusive prefix, for loading uniform in physical space
+        // inclusive prefix, for loading uniform in physical space: the cell's volume is J_c,
+        // or the ring volume 2 pi Omega_c J_c of an axisymmetric run (2 pi drops out)
+        sl += axisym ? om[c] * jc[c] : jc[c];
+        jc[c] = sl;
     }
     r->sumJ = sj;
+    r->load_total = sl;
     CPIC_CUDA(cudaMemcpyAsync(r->jcdf, jc.data(), sizeof(double) * r->ncell, cudaMemcpyHostToDevice, r->stream));
     CPIC_CUDA(cudaStreamSynchronize(r->stream));  // jc is a host temporary
+    if (axisym) {  // FP32 vertex radius table of the axisymmetric mover (x^1, rounded once)
+        std::vector<float> rad(r->nvert);
+        for (long long v = 0; v < r->nvert; ++v) rad[v] = (float)X[(size_t)v * 2];
+        CPIC_CUDA(cudaMemcpyAsync(r->R32, rad.data(), sizeof(float) * r->nvert, cudaMemcpyHostToDevice, r->stream));
+        CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    }
     for (int f = 0; f < 6; ++f) r->face_len[f] = 0.0;
-    if (r->D == 2) {
+    if (r->D == 2 && axisym) {
+        // faces normal to axis 0 of an axisymmetric run are surfaces of revolution: segment
+        // j has area 2 pi r_mid |dX| (r_mid the mean radius of its two vertices); inclusive
+        // prefixes (injection positions) and totals (injection rates)
+        const int nv0 = r->n[0] + 1;
+        std::vector<double> cdf((size_t)2 * r->n[1]);
+        for (int side = 0; side < 2; ++side) {
+            const int col = side == 0 ? 0 : r->n[0];
+            double acc = 0.0;
+            for (int j = 0; j < r->n[1]; ++j) {
+                const double* p0 = &X[((size_t)col + (size_t)nv0 * j) * 2];
+                const double* p1 = &X[((size_t)col + (size_t)nv0 * (j + 1)) * 2];
+                const double dx = p1[0] - p0[0], dy = p1[1] - p0[1];
+                acc += 2.0 * M_PI * (0.5 * (p0[0] + p1[0])) * sqrt(dx * dx + dy * dy);
+                cdf[(size_t)side * r->n[1] + j] = acc;
+            }
+            r->face_len[side] = acc;
+        }
+        CPIC_CUDA(cudaMemcpyAsync(r->fcdf, cdf.data(), sizeof(double) * cdf.size(), cudaMemcpyHostToDevice, r->stream));
+        CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    } else if (r->D == 2) {
         int nv0 = r->n[0] + 1;
         for (int side = 0; side < 2; ++side) {
             int col = side == 0 ? 0 : r->n[0];
@@ -513,7 +547,7 @@ int phase(cpic_run* r, int ph, F fn) {
 }  // namespace
 
 bool push2d_batchable(const cpic_run* r) {
-    if (r->D != 2 || r->magnetized) return false;
+    if (r->D != 2 || r->magnetized || r->cfg.axisymmetric) return false;
     for (int f = 0; f < 4; ++f)
         if (r->cfg.particle_bc[f] == CPIC_PBC_REFLECT) return false;
     return true;
@@ -982,6 +1016,10 @@ int cpic_set_magnetic_field(cpic_run* r, const double* B) {
             set_error("set_magnetic_field: non-finite component");
             return CPIC_ERR_INVALID;
         }
+    if (r->cfg.axisymmetric && (b[0] != 0.0 || b[2] != 0.0)) {
+        set_error("set_magnetic_field: an axisymmetric run takes a field along the axis (component 1) only");
+        return CPIC_ERR_INVALID;
+    }
     for (int a = 0; a < 3; ++a) r->B0[a] = b[a];
     r->magnetized = b[0] != 0.0 || b[1] != 0.0 || b[2] != 0.0;
     invalidate_graphs(r);
@@ -995,9 +1033,8 @@ int cpic_set_floating(cpic_run* r, int face, double charge0) {
         set_error("set_floating: call before cpic_initialize");
         return CPIC_ERR_STATE;
     }
-    if ((face != 0 && face != 1) || r->cfg.field_bc[face] != CPIC_BC_DIRICHLET || r->cfg.axisymmetric ||
-        !(charge0 == charge0)) {
-        set_error("set_floating: a Dirichlet face normal to axis 0 of a non-axisymmetric run");
+    if ((face != 0 && face != 1) || r->cfg.field_bc[face] != CPIC_BC_DIRICHLET || !(charge0 == charge0)) {
+        set_error("set_floating: a Dirichlet face normal to axis 0");
         return CPIC_ERR_INVALID;
     }
     r->floating_face = -1;  // no conductor correction while psi is solved
@@ -1042,9 +1079,11 @@ int cpic_set_injection(cpic_run* r, int sp, int face, double density, double vth
         set_error("set_injection: faces normal to axis 0 with absorbing particle boundaries only");
         return CPIC_ERR_INVALID;
     }
-    if ((r->D == 2 && r->cfg.particle_bc[2] != CPIC_PBC_PERIODIC) ||
+    // the injection kernels wrap the last axis; an axisymmetric face ends on the z axis
+    // instead (its draws stay on the face and the partial push drops what leaves it)
+    if ((r->D == 2 && !r->cfg.axisymmetric && r->cfg.particle_bc[2] != CPIC_PBC_PERIODIC) ||
         (r->D == 3 && r->cfg.particle_bc[4] != CPIC_PBC_PERIODIC)) {
-        set_error("set_injection: the last logical axis must be periodic");
+        set_error("set_injection: the last logical axis must be periodic (or the run axisymmetric)");
         return CPIC_ERR_INVALID;
     }
     InjectSpec& q = r->inj[sp];

@@ -105,15 +105,21 @@ struct RhsParams {
     const double* omega;
     const double* bbc;
     const unsigned long long* charge;
+    int axisym;  // Omega = r: macro-particles are rings
 };
 
 // Q_c = background J_c + sum_s q_s w_s C_{s,c} 2^-24 (eq. (pg) with J_c cancelled against
-// the cell volume); b_c = Omega_c Q_c + Dirichlet terms.
+// the cell volume); b_c = Omega_c Q_c + Dirichlet terms. In an axisymmetric run a
+// macro-particle is a ring of charge q w around the axis, spread over the ring volume
+// 2 pi r J_c: its term is divided by 2 pi Omega_c.
 __device__ __forceinline__ double charge_of(const RhsParams& p, long long c) {
     double Q = __dmul_rn(p.background, p.Jc[c]);
+    const double ring = p.axisym ? __ddiv_rn(1.0, __dmul_rn(2.0 * M_PI, p.omega[c])) : 1.0;
     for (int s = 0; s < p.nsp; ++s) {
         double C = (double)(long long)p.charge[(long long)s * p.ncell + c];
-        Q = __dadd_rn(Q, __dmul_rn(p.qw[s], ldexp(C, -QF)));
+        double t = __dmul_rn(p.qw[s], ldexp(C, -QF));
+        if (p.axisym) t = __dmul_rn(t, ring);
+        Q = __dadd_rn(Q, t);
     }
     return Q;
 }
@@ -188,6 +194,7 @@ struct FloatParams {
     const double* psi;
     double q0;              // charge before any collection
     double qw[CPIC_MAX_SPECIES];
+    int axisym;             // Omega = r: Gauss's law on the ring-charge scale (Q / 2 pi)
 };
 
 __device__ double face_flux_sum(const FloatParams& p, const double* u, double ub) {
@@ -215,7 +222,8 @@ __global__ void floating_kernel(FloatParams p, DevCounters* ctr) {
         double q = p.q0;
         for (int s = 0; s < p.nsp; ++s) q = __dadd_rn(q, __dmul_rn(p.qw[s], (double)ctr->absorbed[s][p.face]));
         ctr->object_charge = q;
-        ctr->object_potential = -(q + g0) / ctr->float_cpsi;
+        const double qr = p.axisym ? q / (2.0 * M_PI) : q;
+        ctr->object_potential = -(qr + g0) / ctr->float_cpsi;
     }
 }
 
@@ -244,6 +252,7 @@ FloatParams make_float_params(const cpic_run* r) {
     p.psi = r->psi;
     p.q0 = r->float_q0;
     for (int s = 0; s < CPIC_MAX_SPECIES; ++s) p.qw[s] = s < p.nsp ? r->cfg.q[s] * r->cfg.w[s] : 0.0;
+    p.axisym = r->cfg.axisymmetric;
     return p;
 }
 
@@ -259,6 +268,7 @@ RhsParams make_rhs_params(const cpic_run* r) {
     p.omega = r->lev[0].omega;
     p.bbc = r->rhs_bc;
     p.charge = r->charge;
+    p.axisym = r->cfg.axisymmetric;
     return p;
 }
 

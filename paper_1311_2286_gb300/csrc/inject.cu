@@ -6,7 +6,8 @@
 //    flux through the face's physical length A), step n injects floor((n+1) r) - floor(n r);
 //  * draws: Philox4x32-10 (Salmon et al., SC'11) with key (seed low, seed high) and counter
 //    (p, n, species, word), u -> (u + 1/2) 2^-32;
-//  * position uniform in the face's logical coordinate; inward normal speed
+//  * position uniform in the face's logical coordinate (axisymmetric runs: the segment by
+//    its surface of revolution 2 pi r_mid |dX|, the offset along it uniform); inward normal speed
 //    vth sqrt(-2 ln U1), tangential/z components vth sqrt(-2 ln U2) (cos, sin)(2 pi U3),
 //    plus the drift; the normal is -+ k^{0.}/|k^{0.}| from k interpolated along the face;
 //  * partial first push u = u_face + U4 dt (k v) for a uniform entry time within the step,
@@ -45,8 +46,10 @@ struct InjectParams {
     float dt;
     int nsp;  // injecting species in this launch (blockIdx.y)
     InjectOne sp[CPIC_MAX_SPECIES];
-    const double* fcdf;  // 3D: face-cell area prefixes of faces 0 and 1
-    double farea[2];     // 3D: face areas (the prefixes' last entries)
+    const double* fcdf;  // 3D: face-cell area prefixes of faces 0 and 1; axisymmetric 2D: the
+                         // face segments' surface-of-revolution prefixes
+    double farea[2];     // face areas (the prefixes' last entries)
+    int axisym;          // 2D, Omega = r
 };
 
 __device__ __forceinline__ long long inject_count(double rate, long long step) {
@@ -122,10 +125,27 @@ __global__ void inject_kernel(InjectParams ip) {
             uint4 r0 = philox4x32_10(make_uint4((unsigned)pi, (unsigned)step, (unsigned)s, 0u), key);
             uint4 r1 = philox4x32_10(make_uint4((unsigned)pi, (unsigned)step, (unsigned)s, 1u), key);
             const float U0 = u01f(r0.x), U1 = u01f(r0.y), U2 = u01f(r0.z), U3 = u01f(r0.w), U4 = u01f(r1.x);
-            const float u1 = __fmul_rn(U0, (float)n2);
-            int j = (int)floorf(u1);
-            if (j > n2 - 1) j = n2 - 1;
-            const float sfr = __fsub_rn(u1, (float)j);
+            int j;
+            float sfr;
+            if (ip.axisym) {
+                // axisymmetric: the segment by inverse CDF of the surfaces of revolution (FP64,
+                // as for the 3D face cells), the offset along it from U5
+                const double* cdf = ip.fcdf + (sp.side ? n2 : 0);
+                const double target = (((double)r0.x + 0.5) * 2.3283064365386962890625e-10) * ip.farea[sp.side];
+                int lo = 0, hi = n2 - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cdf[mid] > target) hi = mid;
+                    else lo = mid + 1;
+                }
+                j = lo;
+                sfr = u01f(r1.y);
+            } else {
+                const float u1 = __fmul_rn(U0, (float)n2);
+                j = (int)floorf(u1);
+                if (j > n2 - 1) j = n2 - 1;
+                sfr = __fsub_rn(u1, (float)j);
+            }
             const int col = sp.side == 0 ? 0 : n1;
             // k interpolated along the face (FP32 vertex table)
             const float4 ka = __ldg(K4 + col + nv0 * j), kb_ = __ldg(K4 + col + nv0 * (j + 1));
@@ -152,8 +172,12 @@ __global__ void inject_kernel(InjectParams ip) {
             const float du1 = __fmul_rn(fdt, __fmaf_rn(kb[2], v0, __fmul_rn(kb[3], v1)));
             split(du0, col, c[0], tt[0]);
             split(__fadd_rn(sfr, du1), j, c[1], tt[1]);
-            c[1] = ((c[1] % n2) + n2) % n2;
-            alive = c[0] >= 0 && c[0] < n1;
+            if (ip.axisym) {  // axis 1 ends on the symmetry axis: not periodic
+                alive = c[0] >= 0 && c[0] < n1 && c[1] >= 0 && c[1] < n2;
+            } else {
+                c[1] = ((c[1] % n2) + n2) % n2;
+                alive = c[0] >= 0 && c[0] < n1;
+            }
             long long slot = p.pb.base[s] + start + pi;
             p.pb.cell[cur][slot] = alive ? encode<2>(c) : -1;
             p.pb.t[cur][slot] = tt[0];
@@ -308,6 +332,7 @@ int launch_inject(cpic_run* r) {
     ip.fcdf = r->fcdf;
     ip.farea[0] = r->face_len[0];
     ip.farea[1] = r->face_len[1];
+    ip.axisym = r->D == 2 && r->cfg.axisymmetric;
     if (r->D == 2)
         inject_kernel<<<dim3((unsigned)maxb, (unsigned)ip.nsp), 256, 0, r->stream>>>(ip);
     else

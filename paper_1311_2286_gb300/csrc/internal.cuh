@@ -100,6 +100,8 @@ struct PushParams {
     long long ncell_h;             // cells of the padded grid: prod (n_a + 2)
     int hs1, hs2;                  // padded strides of axes 1 and 2
     int origin;                    // padded index of cell (0, 0, 0)
+    const float* R;                // axisymmetric runs: vertex table of the cylindrical radius
+                                   // (FP32); nullptr otherwise
     int magnetized;                // uniform B0 (cpic_set_magnetic_field): Boris kick
     float bh[CPIC_MAX_SPECIES];    // Boris constants per species: half kick (float)(dt q/m / 2),
     float bt[CPIC_MAX_SPECIES][3]; // t = (float)(dt q/m B0 / 2),
@@ -156,9 +158,11 @@ struct cpic_run {
     double* k64;      // [nvert][D][D]
     float* K32;       // vertex k table (padded records)
     float* G32;       // vertex G table (padded records)
+    float* R32;       // axisymmetric runs: vertex cylindrical radius x^1 (FP32), else nullptr
     double* rhs_bc;   // Dirichlet part of the right-hand side (finest)
     double* jcdf;     // inclusive prefix sums of the cell Jacobians (device loading)
-    double* fcdf;     // 3D: inclusive prefix sums of the face-cell areas of faces 0 and 1
+    double* fcdf;     // inclusive prefix sums of the face-cell areas of faces 0 and 1 (3D), or
+                      // of the face segments' surfaces of revolution (axisymmetric 2D)
     unsigned long long* charge;  // [nsp][ncell] folded charge counts (what the field solve reads)
     unsigned long long* charge_h;  // [nsp][ncell_h] deposit grid with one halo layer per side
     long long ncell_h;
@@ -181,6 +185,7 @@ struct cpic_run {
     int dense_m;                 // coarsest unknowns (+1 row when singular)
     bool singular;
     double sumJ;                 // sum of finest J_c (singular projection)
+    double load_total;           // last entry of jcdf: sum J_c, or sum Omega_c J_c (axisymmetric)
     double* red;                 // reduction scratch [2 * 1024 + 8]
     int solver;                  // CPIC_SOLVER_* of the stream solve
     int pc_face_only;            // the FP32 V-cycle uses the stencil's face entries only

@@ -6,7 +6,8 @@
 //   cell: the first cell whose inclusive prefix of cell Jacobians exceeds U0 * sum J_c, so
 //         a cell is picked with probability J_c / sum J_c (J_c is the cell's physical volume
 //         in logical units, so the density is uniform in physical space, piecewise constant
-//         per cell);
+//         per cell); in an axisymmetric run the weights are Omega_c J_c (the ring volume
+//         over 2 pi), uniform in the 3D volume;
 //   offsets: uniform in [0, 1) per axis (24-bit draws, exact in FP32);
 //   velocity: vth times standard normals from Box-Muller pairs, plus the drift.
 // The species' previous particles are replaced.
@@ -93,7 +94,7 @@ int launch_load_maxwellian(cpic_run* r, int sp, long long n, double vth, const d
     lp.sp = sp;
     lp.count = n;
     lp.ncell = r->ncell;
-    lp.total = r->sumJ;
+    lp.total = r->load_total;
     lp.cdf = r->jcdf;
     const int b = r->cur_host;
     const long long base = r->pb.base[sp];

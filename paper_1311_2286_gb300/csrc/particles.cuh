@@ -126,6 +126,17 @@ struct Tab<2> {
     }
 };
 
+// b1 interpolation of a scalar 2D vertex table (the axisymmetric radius), with the corner
+// weights and summation order of Tab<2>
+__device__ __forceinline__ float gather_scalar2(const PushParams& p, int v0, const float* t) {
+    const int nv0 = p.n[0] + 1;
+    const float s0 = __fsub_rn(1.0f, t[0]), s1 = __fsub_rn(1.0f, t[1]);
+    const float w0 = __fmul_rn(s0, s1), w1 = __fmul_rn(t[0], s1);
+    const float w2 = __fmul_rn(s0, t[1]), w3 = __fmul_rn(t[0], t[1]);
+    const float a = __ldg(p.R + v0), b = __ldg(p.R + v0 + 1), c = __ldg(p.R + v0 + nv0), d = __ldg(p.R + v0 + nv0 + 1);
+    return __fmaf_rn(w3, d, __fmaf_rn(w2, c, __fmaf_rn(w1, b, __fmul_rn(w0, a))));
+}
+
 template <>
 struct Tab<3> {
     static __device__ __forceinline__ void gather(const PushParams& p, int v0, const float* t,

@@ -189,15 +189,43 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
                     v[al] = __fmaf_rn(dtqm, e, v[al]);
                 }
             }
+            // axisymmetric run (2D, Omega = r): the particle moves on a straight line in 3D
+            // over the step, x = r + dt v_r, y = dt v_theta, r' = |(x, y)|; the meridional
+            // displacement is (r' - r, dt v_z) and (v_r, v_theta) turns with the frame by the
+            // azimuth of (x, y), keeping r v_theta (the inertial forces of the cylindrical
+            // frame); the kinetic-energy tally takes the velocity before the turn
+            const bool axi = D == 2 && p.R != nullptr;  // warp-uniform
+            float disp[2] = {0.0f, 0.0f}, vrot[3] = {v[0], v[1], v[2]};
+            if (axi) {
+                const float rn = gather_scalar2(p, vertex_of<D>(p, c), t);
+                const float x = __fmaf_rn(p.dt, v[0], rn);
+                const float y = __fmul_rn(p.dt, v[2]);
+                const float r1 = __fsqrt_rn(__fmaf_rn(x, x, __fmul_rn(y, y)));
+                float ca = 1.0f, sa = 0.0f;
+                if (r1 > 0.0f) {
+                    ca = __fdiv_rn(x, r1);
+                    sa = __fdiv_rn(y, r1);
+                }
+                disp[0] = __fsub_rn(r1, rn);
+                disp[1] = __fmul_rn(p.dt, v[1]);
+                vrot[0] = __fmaf_rn(ca, v[0], __fmul_rn(sa, v[2]));
+                vrot[2] = __fmaf_rn(ca, v[2], -__fmul_rn(sa, v[0]));
+            }
             // predictor
             int cpred[3];
             float tpred[3];
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                float d = __fmul_rn(kp[a * D + 0], v[0]);
+                float x;
+                if (axi) {
+                    const float d = __fmaf_rn(kp[a * D + 1], disp[1], __fmul_rn(kp[a * D + 0], disp[0]));
+                    x = __fmaf_rn(0.5f, d, t[a]);
+                } else {
+                    float d = __fmul_rn(kp[a * D + 0], v[0]);
 #pragma unroll
-                for (int al = 1; al < D; ++al) d = __fmaf_rn(kp[a * D + al], v[al], d);
-                float x = __fmaf_rn(p.hdt, d, t[a]);
+                    for (int al = 1; al < D; ++al) d = __fmaf_rn(kp[a * D + al], v[al], d);
+                    x = __fmaf_rn(p.hdt, d, t[a]);
+                }
                 if (!isfinite(x)) {
                     cpred[a] = c[a];
                     tpred[a] = t[a];
@@ -223,10 +251,16 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
             bool bad = false;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                float d = __fmul_rn(kq[a * D + 0], v[0]);
+                float x;
+                if (axi) {
+                    const float d = __fmaf_rn(kq[a * D + 1], disp[1], __fmul_rn(kq[a * D + 0], disp[0]));
+                    x = __fadd_rn(t[a], d);
+                } else {
+                    float d = __fmul_rn(kq[a * D + 0], v[0]);
 #pragma unroll
-                for (int al = 1; al < D; ++al) d = __fmaf_rn(kq[a * D + al], v[al], d);
-                float x = __fmaf_rn(p.dt, d, t[a]);
+                    for (int al = 1; al < D; ++al) d = __fmaf_rn(kq[a * D + al], v[al], d);
+                    x = __fmaf_rn(p.dt, d, t[a]);
+                }
                 if (!isfinite(x)) {
                     bad = true;
                     cn[a] = c[a];
@@ -257,6 +291,10 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
             // throughput on this part is ~1/64 of FP32, so the product stays in FP32)
             float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
             tally.ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
+            if (axi) {
+                v[0] = vrot[0];
+                v[2] = vrot[2];
+            }
             // spec B: a reflecting face mirrors the position in logical space (u -> -u below,
             // u -> 2N - u above) and reflects v about row a of k(xi'); still outside after one
             // mirror: removed at that face
@@ -367,6 +405,7 @@ PushParams make_push_params(cpic_run* r) {
     p.dt = (float)r->cfg.dt;
     p.K = r->K32;
     p.G = r->G32;
+    p.R = r->D == 2 ? r->R32 : nullptr;
     p.pb = r->pb;
     p.charge = r->charge_h;
     p.ncell_h = r->ncell_h;
@@ -449,7 +488,8 @@ int launch_push_kernel(cpic_run* r) {
     // generic kernel
     bool reflect = false;
     for (int f = 0; f < 2 * r->D; ++f) reflect = reflect || r->cfg.particle_bc[f] == CPIC_PBC_REFLECT;
-    if (r->magnetized) return launch_particles<0>(r, 0, 0, 0, 0);  // Boris kick: the generic kernel
+    // Boris kick and the axisymmetric mover: the generic kernel
+    if (r->magnetized || (r->D == 2 && r->cfg.axisymmetric)) return launch_particles<0>(r, 0, 0, 0, 0);
     if (r->D == 2 && !reflect) return launch_push2d(r, make_push_params(r));
     if (r->D == 3) {
         const int st = launch_push3d(r, make_push_params(r));

@@ -183,6 +183,64 @@ def test_floating_cylinder_matches_oracle(cpic):
     run.close()
 
 
+SPH = dict(n1=48, n2=48, npart_per_species=150_000, seed=43, dt=0.1)
+SPH_STEPS = 300
+
+
+def test_sphere_axisym_cycle_matches_oracle(cpic, record_property):
+    """Row f3: a reduced Test B run (the sphere r1 = 1 in r2 = 10 on the 2D axisymmetric
+    (r, z) map, Omega = r, 48 x 48 cells, 150k + 150k rings, the sphere floating from zero
+    charge, Maxwellian flux injection at r2, specular z axis, dt 0.1, sort every 4 steps,
+    300 steps) on the device and in the oracle: start-up and first-step state <= 1e-5
+    against FP64; W_E at every level equal to 1/2 sum phi Q of the device's fields; the
+    sphere potential at every level within 1e-3 of its range, its time average within 1%;
+    time-averaged W_E within 1%; collected currents within 1% where the counts resolve it."""
+    w = wl.sphere_axisym(**SPH)
+    trace = []
+    run, pic, err0, _, we, we_chk, we_ora, dev_abs, ora_abs = _run_pair(cpic, w, SPH_STEPS, 4, floating=(0, 0.0),
+                                                                         trace=trace)
+    assert err0[0] <= 1e-5 and err0[1] <= 1e-5, err0
+    np.testing.assert_allclose(we, we_chk, rtol=1e-12)
+    v = np.array(trace)
+    scale = np.max(np.abs(v[:, 1]))
+    assert np.max(np.abs(v[:, 0] - v[:, 1])) <= 1e-3 * scale, np.max(np.abs(v[:, 0] - v[:, 1]))
+    assert abs(v[:, 0].mean() / v[:, 1].mean() - 1.0) <= 0.01
+    assert v[-1, 1] < -0.5
+    assert abs(we.mean() / we_ora.mean() - 1.0) <= 0.01, (we.mean(), we_ora.mean())
+    report = []
+    _current_check(dev_abs, ora_abs, w, 1, SPH_STEPS, report)
+    record_property("currents", report)
+    print("axisymmetric sphere: V(end) device %.6f oracle %.6f, mean %.6f / %.6f, max |dV| %.2e; W_E mean %.6e / %.6e"
+          % (v[-1, 0], v[-1, 1], v[:, 0].mean(), v[:, 1].mean(), np.max(np.abs(v[:, 0] - v[:, 1])), we.mean(),
+             we_ora.mean()))
+    for r in report:
+        print("axisymmetric sphere current:", r)
+    run.close()
+
+
+def test_sphere_floating_potential_test_b(cpic):
+    """Test B at the paper's size (Sec. III.B: 128 x 128, r1 = 1, r2 = 10, dt 0.1, plasma of
+    density 1 and T_i = T_e, m_i/m_e = 1836, the sphere floating from zero charge, flux
+    injection at r2), on the device alone with about 230 rings per cell per species: the
+    sphere potential averaged over the last quarter of 4000 steps lies within 8% of the
+    OML value -2.50 T_e that the paper's -2.54 is compared with (OML is approximate at
+    r1 = lambda_D; the paper's own agreement is 1.6%). Physics, not parity: the parity
+    of this path against the oracle is the test above."""
+    n = 128
+    w = wl.sphere_axisym(n, n, npart_per_species=230 * n * n, seed=8, dt=0.1, capacity_factor=1.6)
+    run = cpic.run_from_workload(w, sort_interval=8)
+    run.set_floating(0, 0.0)
+    run.initialize()
+    steps, vs = 4000, []
+    for _ in range(steps // 50):
+        run.step(50)
+        vs.append(run.diag()["object_potential"])
+    tail = float(np.mean(vs[-len(vs) // 4:]))
+    print("Test B: sphere potential (last quarter of %d steps) %.4f T_e (OML -2.50, paper -2.54)" % (steps, tail))
+    assert abs(tail / -2.50 - 1.0) <= 0.08, tail
+    run.close()
+
+
 def test_cylinder_cycle_same_in_batch_and_alone(cpic):
     """The reduced cylinder run stepped inside a batch, next to two other runs, ends in the
     same state as the stand-alone device run that test_cylinder_cycle_matches_oracle

@@ -64,3 +64,23 @@ def test_maxwellian_load_is_deterministic(cpic):
         assert np.array_equal(x, y)
     assert not np.array_equal(a[2], c[2])
     run.close()
+
+
+def test_maxwellian_load_axisym_is_uniform_in_volume(cpic):
+    """An axisymmetric run loads rings uniform in the 3D volume: cells with probability
+    Omega_c J_c / sum Omega_c J_c (the ring volume 2 pi r J_c, up to the constant)."""
+    n1, n2, N = 16, 32, 300_000
+    w = wl.sphere_axisym(n1, n2, npart_per_species=16, seed=5, inject=False, capacity_factor=N / 16 + 2)
+    run = cpic.run_from_workload(w)
+    run.load_maxwellian(0, N, 1.0, seed=77)
+    cell, t, v = run.particles(0)
+    i, j = cell & 0xFFFF, cell >> 16
+    g = ogeo.build_geometry(w.vertices, [False, False], axisym=True)
+    wgt = (np.asarray(g.omega_c) * np.asarray(g.Jc)).reshape(n2, n1)
+    p = (wgt / wgt.sum()).ravel()
+    counts = np.bincount(i + n1 * j, minlength=n1 * n2).astype(np.float64)
+    expected = N * p
+    chi2 = np.sum((counts - expected) ** 2 / expected)
+    dof = n1 * n2 - 1
+    assert abs(chi2 - dof) < 6 * np.sqrt(2 * dof), (chi2, dof)
+    run.close()

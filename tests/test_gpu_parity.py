@@ -43,8 +43,15 @@ CASES = {
     "box_reflect": lambda: wl.box_reflect(32, 32, 60_000, vth=2.0, seed=7),
     # 3D sphere in plasma: absorbing radial faces, reflecting polar caps, periodic azimuth
     "sphere3d": lambda: wl.sphere(16, 16, 16, npart_per_species=20_000, seed=5),
+    # 2D axisymmetric sphere (Omega = r): ring particles, specular walls on the z axis
+    "sphere_axisym": lambda: wl.sphere_axisym(32, 32, npart_per_species=50_000, seed=5, inject=False),
 }
-DIRICHLET_AXIS0 = {"cylinder", "sphere3d"}
+DIRICHLET_AXIS0 = {"cylinder", "sphere3d", "sphere_axisym"}
+
+
+def _R(g, w, dtype=np.float64):
+    """The vertex radius table of an axisymmetric workload (None otherwise)."""
+    return g.X[..., 0].astype(dtype) if w.omega_axisym else None
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -129,7 +136,7 @@ def test_push_bit_exact_vs_replay(cpic, case, sort_first, tile):
         idx = _unpack(cell0, D)
         i32, t32, v32, face, kefp = mover.push32(idx, t0, v0, k32, G32, w.n, w.particle_bc,
                                                 np.float32(w.dt * sp.q / sp.m), np.float32(0.5 * w.dt),
-                                                np.float32(w.dt))
+                                                np.float32(w.dt), R32=_R(g, w, np.float32))
         alive = face < 0
         ref_cell = wl.pack_cells(i32[:, alive])
         cell1, t1, v1 = post[s]
@@ -148,6 +155,8 @@ def test_push_bit_exact_vs_replay(cpic, case, sort_first, tile):
         assert sum(d["absorbed"][0]) > 0  # the case exercises absorption
     if case in ("box_reflect", "sphere3d"):
         # the case exercises reflection: some particle left and re-entered a reflecting axis
+        # (an axisymmetric ring crosses the z axis by its 3D motion, r' = |(x, y)| >= 0, so
+        # the specular wall there is only a fallback and one step of the case meets none)
         cell0, t0, v0 = pre[0]
         idx = _unpack(cell0, D)
         i64, t64, v64, face, vk = mover.push64(idx, t0.astype(np.float64), v0.astype(np.float64), g.k,
@@ -178,9 +187,10 @@ def test_push_vs_fp64_single_step(cpic, case):
         cell0, t0, v0 = pre[s]
         idx = _unpack(cell0, D)
         i64, t64, v64, face = mover.push64(idx, t0.astype(np.float64), v0.astype(np.float64), g.k, G64, w.dt,
-                                           sp.q / sp.m, w.n, w.particle_bc)
+                                           sp.q / sp.m, w.n, w.particle_bc, R=_R(g, w))
         _, _, _, face32, _ = mover.push32(idx, t0, v0, k32, G32, w.n, w.particle_bc,
-                                          np.float32(w.dt * sp.q / sp.m), np.float32(0.5 * w.dt), np.float32(w.dt))
+                                          np.float32(w.dt * sp.q / sp.m), np.float32(0.5 * w.dt), np.float32(w.dt),
+                                          R32=_R(g, w, np.float32))
         alive64, alive32 = face < 0, face32 < 0
         cell1, t1, v1 = post[s]
         assert cell1.shape[0] == int(alive32.sum())
@@ -468,6 +478,75 @@ def test_injection_3d_matches_oracle(cpic):
     run.close()
 
 
+def test_injection_axisym_matches_oracle(cpic):
+    """a8 on an axisymmetric run (the outer sphere of the 2D (r, z) shell): the count follows
+    the surface of revolution, the segment is drawn by its ring area, the offset along it
+    from U5, and a particle whose partial push leaves the z axis range is dropped; cells,
+    offsets and velocities agree with the oracle (cells exact up to draws within rounding of
+    a face, values to FP32 arithmetic)."""
+    n1, n2 = 32, 32
+    w = wl.sphere_axisym(n1, n2, npart_per_species=1000, seed=9, inject=True, capacity_factor=40.0)
+    # a dense injected plasma, so that both species draw hundreds of particles in one step
+    w.injection = [(s, face, 2000.0, vth, seed) for (s, face, _, vth, seed) in w.injection]
+    g, per = _geom(w)
+    run = cpic.run_from_workload(w)
+    run.vertex_field()
+    run.push()
+    before = [run.particles(s) for s in range(2)]
+    run.inject()
+    after = [run.particles(s) for s in range(2)]
+    d = run.diag()
+    rings = inject.face_ring_areas_2d(w.vertices, 1)
+    for s, (sp, (s_, face, dens, vth, seed)) in enumerate(zip(w.species, w.injection)):
+        rate = inject.rate_per_step(dens, vth, inject.face_area_axisym(w.vertices, 1), w.dt, sp.w)
+        cnt = inject.count_at_step(rate, 0)
+        assert cnt > 100
+        idx, t32, v32, keep = inject.inject_2d(g.k, (n1, n2), 1, cnt, 0, s, seed, vth, (0, 0, 0), w.dt,
+                                               ring_areas=rings)
+        nb = before[s][0].shape[0]
+        ca, ta, va = after[s]
+        new_c, new_t, new_v = ca[nb:], ta[:, nb:], va[:, nb:]
+        assert abs(new_c.shape[0] - int(keep.sum())) <= max(1, cnt // 10000)
+        assert d["injected"][s] == new_c.shape[0]
+        if new_c.shape[0] == int(keep.sum()):
+            ref_cell = wl.pack_cells(idx)
+            assert np.sum(new_c != ref_cell) <= max(1, cnt // 10000)
+            same = new_c == ref_cell
+            np.testing.assert_allclose(new_t[:, same], t32[:, same], atol=1e-5)
+            # FP32 draws: U1 rounded to FP32 near 1 moves ln U1 by up to 3e-8, so a small
+            # normal speed vn carries an error up to ~3e-8 vth^2 / vn; such draws are rare
+            # (a few in 10^5), the rest agree to FP32 arithmetic
+            dv = np.abs(new_v[:, same] - v32[:, same])
+            loose = dv > 2e-6 * np.abs(v32[:, same]) + 2e-6 * vth
+            assert int(np.sum(np.any(loose, axis=0))) <= max(1, cnt // 10000)
+            assert np.max(dv) <= 5e-5 * vth
+    run.close()
+
+
+def test_floating_sphere_axisym_solve(cpic):
+    """Floating conductor on an axisymmetric run: a charged sphere (charge Q, no particles)
+    inside a grounded sphere floats to the oracle's V (which is pinned to Q (1/r1 - 1/r2) /
+    (4 pi)); the device's potential equals the oracle's direct solve to 1e-9."""
+    from oracle.pic import OraclePIC
+
+    Q = 0.61
+    w = wl.sphere_axisym(32, 32, npart_per_species=1, phi_obj=2.0, inject=False)
+    w.particles = [wl.ParticleSet(np.zeros(0, np.int32), np.zeros((2, 0), np.float32),
+                                  np.zeros((3, 0), np.float32)) for _ in w.species]
+    ref = OraclePIC(w, "fp64")
+    ref.set_floating(0, Q)
+    ref.solve()
+    run = cpic.run_from_workload(w, mg_rtol=1e-13, mg_max_cycles=200)
+    run.set_floating(0, Q)
+    run.initialize()
+    d = run.diag()
+    assert d["object_potential"] == pytest.approx(ref.object_potential, rel=1e-9)
+    assert abs(d["object_potential"] - Q * 0.9 / (4.0 * math.pi)) < 0.02 * Q * 0.9 / (4.0 * math.pi)
+    phi = run.phi()
+    assert np.max(np.abs(phi - ref.phi)) <= 1e-9 * np.max(np.abs(ref.phi))
+    run.close()
+
+
 def test_edge_cases_empty_and_capacity(cpic):
     """Empty species, a species filled to capacity with injection (drops are counted, no
     write past capacity), and particles exactly on the logical boundaries."""
@@ -663,6 +742,7 @@ def test_full_size_sphere_push_parity(cpic, tile):
 # ------------------------------------------------------------------ uniform B0 (row f2)
 
 B_TEST = (0.3, -0.2, 1.1)
+B_AXIS = (0.0, 1.1, 0.0)  # axisymmetric runs: a uniform field along the symmetry axis (v = (v_r, v_z, v_theta))
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -672,7 +752,8 @@ def test_magnetized_push_bit_exact_vs_replay(cpic, case):
     for bit, the deposit equals the oracle's spec-Q deposit, and the state is within 1e-5
     normwise of the FP64 oracle's Boris push."""
     w = CASES[case]()
-    w.B0 = B_TEST
+    B = B_AXIS if w.omega_axisym else B_TEST
+    w.B0 = B
     rng = np.random.default_rng(12)
     phi = wl.random_field(rng, tuple(reversed(w.n)), 0.5)
     if case in DIRICHLET_AXIS0:
@@ -686,14 +767,14 @@ def test_magnetized_push_bit_exact_vs_replay(cpic, case):
         qm = sp.q / sp.m
         i32, t32, v32, face, kefp = mover.push32(idx, t0, v0, k32, G32, w.n, w.particle_bc, np.float32(w.dt * qm),
                                                 np.float32(0.5 * w.dt), np.float32(w.dt),
-                                                boris=mover.boris_constants32(w.dt, qm, B_TEST))
+                                                boris=mover.boris_constants32(w.dt, qm, B), R32=_R(g, w, np.float32))
         alive = face < 0
         cell1, t1, v1 = post[s]
         assert np.array_equal(cell1, wl.pack_cells(i32[:, alive]))
         assert np.array_equal(t1, t32[:, alive]) and np.array_equal(v1, v32[:, alive])
         assert np.array_equal(charge[s], odep.deposit_fixed(i32[:, alive].astype(np.int64), t32[:, alive], w.n, per))
         i64, t64, v64, face64 = mover.push64(idx, t0.astype(np.float64), v0.astype(np.float64), g.k, G64, w.dt, qm,
-                                             w.n, w.particle_bc, B=B_TEST)
+                                             w.n, w.particle_bc, B=B, R=_R(g, w))
         both = (face64 < 0) & alive
         keep = both[alive]
         dv = np.abs(v1[:, keep].astype(np.float64) - v64[:, both])
