@@ -206,6 +206,23 @@ int cpic_set_injection(cpic_run* run, int sp, int face, double density, double v
  * (CPIC_ERR_INVALID otherwise): the only uniform field that keeps the symmetry. */
 int cpic_set_magnetic_field(cpic_run* run, const double* B);
 
+/* Integrator of the gyration in the uniform field B0 (Sec. II.B: for a uniform field the
+ * mover can resolve the gyromotion exactly, relaxing the time step constraint when the
+ * cyclotron frequency is large). CPIC_GYRO_BORIS (the default): the Boris step above.
+ * CPIC_GYRO_CYCLOTRONIC: the cyclotronic integrator, read as the splitting of the step
+ * into the electric kick v+ = v + dt (q/m) E(xi^n) and the exact motion in B0 alone over
+ * dt: with b = B0/|B0|, th = (q/m)|B0| dt, u = v+ x b, par = (v+ . b) b, perp = v+ - par,
+ * the new velocity is par + cos th perp + sin th u and the physical displacement
+ * d = dt (par + (sin th / th) perp + ((1 - cos th) / th) u) moves xi through the same
+ * predictor-corrector (xi' = xi^n + k(xi^n) d / 2, xi^{n+1} = xi^n + k(xi') d). Exact for
+ * E = 0 at any th, and exact E x B drift for a uniform E. The start-up kick is then the
+ * plain half kick -dt/2 (q/m) E. Axisymmetric runs start the displacement at the
+ * particle's point in 3D and turn the velocity with the frame. Takes effect only with a
+ * nonzero B0. CPIC_ERR_INVALID for another kind. Invalidates captured step graphs. */
+#define CPIC_GYRO_BORIS 0
+#define CPIC_GYRO_CYCLOTRONIC 1
+int cpic_set_gyro_integrator(cpic_run* run, int kind);
+
 /* Floating conductor (Sec. III.A-B: the object collects the particles that reach it and
  * charges up to a floating potential; Figs. of the wall and sphere potential against time).
  * From now on the Dirichlet face `face` (0 or 1: the ends of axis 0, e.g. the object at

@@ -86,6 +86,8 @@ class OraclePIC:
         self.injected = [0] * len(self.species)
         self._face_area = {}
         self.B0 = getattr(wl, "B0", None)  # uniform magnetic field: Boris kick
+        # the cyclotronic integrator (exact gyration) in place of the Boris step
+        self.gyro = getattr(wl, "gyro", "boris") == "cyclotronic" and self.B0 is not None and bool(np.any(self.B0))
         # axisymmetric runs: the vertex table of the cylindrical radius (component 0 of the map)
         self.R = np.ascontiguousarray(self.geom.X[..., 0]) if self.geom.axisym else None
 
@@ -175,10 +177,12 @@ class OraclePIC:
         for sp in self.species:
             qm = sp.q / sp.m
             if self.precision == "fp64":
-                sp.v = mover.kick64(sp.idx, sp.t, sp.v, k, G, -0.5 * self.dt * qm, B=self.B0)
+                sp.v = mover.kick64(sp.idx, sp.t, sp.v, k, G, -0.5 * self.dt * qm,
+                                    B=None if self.gyro else self.B0, axisym=self.geom.axisym)
             else:
                 sp.v = mover.kick32(sp.idx, sp.t, sp.v, k, G, self.n, np.float32(-0.5 * self.dt * qm),
-                                    boris=mover.boris_constants32(self.dt, qm, self.B0, -0.5))
+                                    boris=None if self.gyro else
+                                    mover.boris_constants32(self.dt, qm, self.B0, -0.5, axisym=self.geom.axisym))
 
     def step(self, solve: bool = True):
         """One PIC cycle. solve=False holds the field fixed (mover, injection and deposit
@@ -193,19 +197,22 @@ class OraclePIC:
                 sp.t = np.ascontiguousarray(sp.t, dtype=np.float64)
                 sp.v = np.ascontiguousarray(sp.v, dtype=np.float64)
                 idx, t, v, face, vdot = mover.push64_c(sp.idx, sp.t, sp.v, k, G, self.dt, qm, self.n, self.pbc,
-                                                       self.threads, inplace=True, B=self.B0, R=self.R)
+                                                       self.threads, inplace=True, B=self.B0, R=self.R,
+                                                       gyro=self.gyro)
                 ke.append(0.5 * sp.m * sp.w * float(np.sum(vdot)))
             elif self.precision == "fp64":
                 vold = sp.v
                 idx, t, v, face, vk = mover.push64(sp.idx, sp.t, sp.v, k, G, self.dt, qm, self.n, self.pbc,
-                                                   return_kicked=True, B=self.B0, R=self.R)
+                                                   return_kicked=True, B=self.B0, R=self.R, gyro=self.gyro)
                 ke.append(0.5 * sp.m * sp.w * float(np.sum(vold * vk)))
             else:
                 idx, t, v, face, kefp = mover.push32(
                     sp.idx, sp.t, sp.v, k, G, self.n, self.pbc,
                     np.float32(self.dt * qm), np.float32(0.5 * self.dt), np.float32(self.dt),
-                    boris=mover.boris_constants32(self.dt, qm, self.B0),
-                    R32=None if self.R is None else self.R.astype(np.float32))
+                    boris=None if self.gyro else mover.boris_constants32(self.dt, qm, self.B0,
+                                                                         axisym=self.geom.axisym),
+                    R32=None if self.R is None else self.R.astype(np.float32),
+                    gyro=mover.gyro_constants32(self.dt, qm, self.B0, self.geom.axisym) if self.gyro else None)
                 ke.append(0.5 * sp.m * sp.w * float(np.ldexp(float(kefp.sum()), -24)))
             alive = face < 0
             if np.all(alive):

@@ -99,9 +99,23 @@ static void boris64(double* v, const double* E, double h, const double* B) {
     v[2] = m[2] + (q[0] * s[1] - q[1] * s[0]) + h * E[2];
 }
 
+/* The exact motion in the uniform field alone over dt (mover.py gyro_flow64, same order):
+ * gy = (b0, b1, b2, cos th, sin th, f1, f2); u = v x b, par = (v . b) b, perp = v - par;
+ * v' = (par + cos th perp) + sin th u, d = dt ((par + f1 perp) + f2 u). */
+static void gyro_flow64(const double* v, double dt, const double* gy, double* d, double* vn) {
+    const double* b = gy;
+    const double vpar = v[0] * b[0] + v[1] * b[1] + v[2] * b[2];
+    const double u[3] = {v[1] * b[2] - v[2] * b[1], v[2] * b[0] - v[0] * b[2], v[0] * b[1] - v[1] * b[0]};
+    for (int a = 0; a < 3; ++a) {
+        const double par = vpar * b[a], perp = v[a] - par;
+        vn[a] = (par + gy[3] * perp) + gy[4] * u[a];
+        d[a] = dt * ((par + gy[5] * perp) + gy[6] * u[a]);
+    }
+}
+
 static void push_one(int D, const int* n, const int* pbc, const double* K, const double* G, double dt, double qm,
-                     const double* B, const double* R, long* c, double* t, double* v, int* face_out,
-                     double* vdot_out) {
+                     const double* B, const double* R, const double* gy, long* c, double* t, double* v,
+                     int* face_out, double* vdot_out) {
     double kp[9], gp[3], E[3], vold[3];
     gather(D, n, K, D * D, c, t, kp);
     gather(D, n, G, D, c, t, gp);
@@ -121,9 +135,28 @@ static void push_one(int D, const int* n, const int* pbc, const double* K, const
     }
     double vk[3] = {v[0], v[1], v[2]};
     /* axisymmetric run: the meridional displacement of straight 3D motion over the step and
-     * the frame's turn (mover.py axisym_step) */
-    double disp[2] = {0.0, 0.0}, vrot[3] = {v[0], v[1], v[2]};
-    if (R) {
+     * the frame's turn (mover.py axisym_step); cyclotronic push: the gyration flow's
+     * displacement and velocity, then (axisymmetric) the frame step (mover.py axisym_frame) */
+    double disp[3] = {0.0, 0.0, 0.0}, vrot[3] = {v[0], v[1], v[2]};
+    const int dform = gy != 0 || R != 0;
+    if (gy) {
+        double d3[3], vn[3];
+        gyro_flow64(v, dt, gy, d3, vn);
+        for (int q = 0; q < 3; ++q) vrot[q] = vn[q];
+        if (R) {
+            double rn;
+            gather(D, n, R, 1, c, t, &rn);
+            const double x = rn + d3[0], y = d3[2];
+            const double r1 = sqrt(x * x + y * y);
+            const double ca = r1 > 0.0 ? x / r1 : 1.0, sa = r1 > 0.0 ? y / r1 : 0.0;
+            disp[0] = r1 - rn;
+            disp[1] = d3[1];
+            vrot[0] = ca * vn[0] + sa * vn[2];
+            vrot[2] = ca * vn[2] - sa * vn[0];
+        } else {
+            for (int q = 0; q < D; ++q) disp[q] = d3[q];
+        }
+    } else if (R) {
         double rn;
         gather(D, n, R, 1, c, t, &rn);
         const double x = rn + dt * v[0], y = dt * v[2];
@@ -140,7 +173,7 @@ static void push_one(int D, const int* n, const int* pbc, const double* K, const
     for (int a = 0; a < D; ++a) {
         double d = 0.0;
         long dc;
-        if (R) {
+        if (dform) {
             for (int b = 0; b < D; ++b) d = d + kp[a * D + b] * disp[b];
             renorm(t[a] + 0.5 * d, &dc, &tp[a]);
         } else {
@@ -165,7 +198,7 @@ static void push_one(int D, const int* n, const int* pbc, const double* K, const
     for (int a = 0; a < D; ++a) {
         double d = 0.0;
         long dc;
-        if (R) {
+        if (dform) {
             for (int b = 0; b < D; ++b) d = d + kq[a * D + b] * disp[b];
             renorm(t[a] + d, &dc, &tn[a]);
         } else {
@@ -174,7 +207,7 @@ static void push_one(int D, const int* n, const int* pbc, const double* K, const
         }
         cn[a] = c[a] + dc;
     }
-    if (R)
+    if (dform)
         for (int q = 0; q < 3; ++q) v[q] = vrot[q];
     int face = -1;
     for (int a = 0; a < D; ++a) {
@@ -218,10 +251,12 @@ static void push_one(int D, const int* n, const int* pbc, const double* K, const
 /* One FP64 push of np particles (arrays in the numpy layout: idx, t [D][np], v [3][np],
  * updated in place); K: vertex k table [vertex][a][alpha], G: [vertex][a]; face[p] = -1
  * (alive) or 2 a + side (removed there); vdot[p] = v^{n-1/2} . v^{n+1/2} (the kicked
- * velocity, before any reflection). */
+ * velocity, before any reflection). B: the uniform field for the Boris step (component
+ * basis) or NULL; gy: the cyclotronic push's gyro constants (mover.py gyro_constants64) or
+ * NULL; R: the vertex radius table of an axisymmetric run or NULL. */
 void oracle_push64(int D, const int* n, const int* pbc, long np, int64_t* idx, double* t, double* v,
                    const double* K, const double* G, double dt, double qm, int32_t* face, double* vdot,
-                   int nthreads, const double* B, const double* R) {
+                   int nthreads, const double* B, const double* R, const double* gy) {
     if (nthreads < 1) nthreads = 1;
 #pragma omp parallel for schedule(static) num_threads(nthreads)
     for (long p = 0; p < np; ++p) {
@@ -233,7 +268,7 @@ void oracle_push64(int D, const int* n, const int* pbc, long np, int64_t* idx, d
         }
         for (int q = 0; q < 3; ++q) vv[q] = v[q * np + p];
         int f;
-        push_one(D, n, pbc, K, G, dt, qm, B, R, c, tt, vv, &f, &vdot[p]);
+        push_one(D, n, pbc, K, G, dt, qm, B, R, gy, c, tt, vv, &f, &vdot[p]);
         for (int a = 0; a < D; ++a) {
             idx[a * np + p] = c[a];
             t[a * np + p] = tt[a];

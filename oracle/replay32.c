@@ -104,7 +104,7 @@ static void gather(int D, const int* n, const float* Q, int nq, const int* c, co
  * ke = fmaf(vo2, v2, fmaf(vo1, v1, vo0 * v0)) (spec D). */
 void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* t, float* v,
                  const float* K, const float* G, float dtqm, float hdt, float dt, int* face,
-                 long long* ke_fp, const float* boris, const float* R) {
+                 long long* ke_fp, const float* boris, const float* R, const float* gyro) {
     for (long p = 0; p < np; ++p) {
         int c[3];
         float tt[3], vv[3], vo[3];
@@ -133,8 +133,46 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
          * displacement (r' - r, dt * v_z); the frame turns by (x, y) / r' (cos, sin; (1, 0)
          * at r' = 0): v_r = fmaf(cos, v_r, sin * v_theta), v_theta = fmaf(cos, v_theta,
          * -(sin * v_r)); predictor t' = fmaf(0.5f, k . disp, t), corrector t + k' . disp */
-        float disp[2] = {0.0f, 0.0f}, vrot[3] = {vv[0], vv[1], vv[2]};
-        if (R) {
+        float disp[3] = {0.0f, 0.0f, 0.0f}, vrot[3] = {vv[0], vv[1], vv[2]};
+        const int dform = gyro != 0 || R != 0;
+        if (gyro) {
+            /* cyclotronic push: exact gyration over dt after the plain kick, gyro = (b0, b1,
+             * b2, cos th, sin th, f1, f2); vpar = fmaf chain of v . b, u = v x b (each
+             * component fmaf(a_y, b_z, -(a_z * b_y))), par = vpar * b, perp = v - par,
+             * v' = fmaf(sin, u, fmaf(cos, perp, par)), d = dt * fmaf(f2, u, fmaf(f1, perp, par));
+             * axisymmetric: x = r + d_r, y = d_theta, disp = (sqrtf(fmaf(x, x, y * y)) - r,
+             * d_z) and the frame turn of v' as above */
+            const float* b = gyro;
+            const float vpar = fmaf(vv[2], b[2], fmaf(vv[1], b[1], vv[0] * b[0]));
+            const float u[3] = {fmaf(vv[1], b[2], -(vv[2] * b[1])), fmaf(vv[2], b[0], -(vv[0] * b[2])),
+                                fmaf(vv[0], b[1], -(vv[1] * b[0]))};
+            float d3[3], vn[3];
+            for (int al = 0; al < 3; ++al) {
+                const float par = vpar * b[al];
+                const float perp = vv[al] - par;
+                vn[al] = fmaf(gyro[4], u[al], fmaf(gyro[3], perp, par));
+                d3[al] = dt * fmaf(gyro[6], u[al], fmaf(gyro[5], perp, par));
+            }
+            for (int al = 0; al < 3; ++al) vrot[al] = vn[al];
+            if (R) {
+                float rn;
+                gather(D, n, R, 1, c, tt, &rn);
+                const float x = rn + d3[0];
+                const float y = d3[2];
+                const float r1 = sqrtf(fmaf(x, x, y * y));
+                float ca = 1.0f, sa = 0.0f;
+                if (r1 > 0.0f) {
+                    ca = x / r1;
+                    sa = y / r1;
+                }
+                disp[0] = r1 - rn;
+                disp[1] = d3[1];
+                vrot[0] = fmaf(ca, vn[0], sa * vn[2]);
+                vrot[2] = fmaf(ca, vn[2], -(sa * vn[0]));
+            } else {
+                for (int a = 0; a < D; ++a) disp[a] = d3[a];
+            }
+        } else if (R) {
             float rn;
             gather(D, n, R, 1, c, tt, &rn);
             const float x = fmaf(dt, vv[0], rn);
@@ -155,9 +193,9 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
         float tp[3];
         for (int a = 0; a < D; ++a) {
             float x;
-            if (R) {
+            if (dform) {
                 float d = kp[a * D + 0] * disp[0];
-                d = fmaf(kp[a * D + 1], disp[1], d);
+                for (int b = 1; b < D; ++b) d = fmaf(kp[a * D + b], disp[b], d);
                 x = fmaf(0.5f, d, tt[a]);
             } else {
                 float d = kp[a * D + 0] * vv[0];
@@ -191,9 +229,9 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
         float tn[3];
         for (int a = 0; a < D; ++a) {
             float x;
-            if (R) {
+            if (dform) {
                 float d = kq[a * D + 0] * disp[0];
-                d = fmaf(kq[a * D + 1], disp[1], d);
+                for (int b = 1; b < D; ++b) d = fmaf(kq[a * D + b], disp[b], d);
                 x = tt[a] + d;
             } else {
                 float d = kq[a * D + 0] * vv[0];
@@ -225,7 +263,7 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
         }
         float ke = fmaf(vo[2], vk[2], fmaf(vo[1], vk[1], vo[0] * vk[0]));
         ke_fp[p] = llrintf(ldexpf(ke, 24));
-        if (R)
+        if (dform)
             for (int al = 0; al < 3; ++al) vv[al] = vrot[al];
         /* spec B: mirror about a reflecting face, reflect v about row a of k(xi') */
         if (fc < 0) {

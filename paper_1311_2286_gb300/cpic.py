@@ -26,6 +26,7 @@ CPIC_MAP_SINE, CPIC_MAP_ANNULUS, CPIC_MAP_SPHERE_AXISYM, CPIC_MAP_SHELL = 1, 2, 
 CPIC_SOLVER_MG, CPIC_SOLVER_BICGSTAB = 0, 1
 CPIC_BATCH_AUTO, CPIC_BATCH_BRANCHES, CPIC_BATCH_PERSISTENT = 0, 1, 2
 MAX_SPECIES = 4
+GYRO_BORIS, GYRO_CYCLOTRONIC = 0, 1  # cpic_set_gyro_integrator kinds
 
 
 class cpic_config(ctypes.Structure):
@@ -150,6 +151,7 @@ _SIGS = {
     "cpic_get_particles": ([P, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), P, P, P], ctypes.c_int),
     "cpic_set_floating": ([P, ctypes.c_int, ctypes.c_double], ctypes.c_int),
     "cpic_set_magnetic_field": ([P, P], ctypes.c_int),
+    "cpic_set_gyro_integrator": ([P, ctypes.c_int], ctypes.c_int),
     "cpic_set_injection": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, ctypes.c_uint64],
                            ctypes.c_int),
     "cpic_initialize": ([P], ctypes.c_int),
@@ -395,9 +397,15 @@ class Run:
         return run
 
     def set_magnetic_field(self, B):
-        """cpic_set_magnetic_field: uniform B0 (3 components, physical space)."""
+        """cpic_set_magnetic_field: uniform B0 (3 components in the velocity components' order;
+        an axisymmetric run's (v_r, v_z, v_theta) takes (0, B_z, 0) only)."""
         b = np.ascontiguousarray(B, dtype=np.float64)
         check(load().cpic_set_magnetic_field(self.h, _ptr(b)))
+
+    def set_gyro_integrator(self, kind):
+        """cpic_set_gyro_integrator: "boris" or "cyclotronic" (exact gyration in B0)."""
+        k = {"boris": GYRO_BORIS, "cyclotronic": GYRO_CYCLOTRONIC}[kind] if isinstance(kind, str) else int(kind)
+        check(load().cpic_set_gyro_integrator(self.h, k))
 
     def set_floating(self, face=0, charge0=0.0):
         """cpic_set_floating: the face's conductor floats (Gauss's-law potential from its
@@ -520,6 +528,7 @@ def run_from_workload(wl, sort_interval=0, analytic=None, mg_rtol=0.0, mg_max_cy
         run.set_injection(s, face, dens, vth, seed)
     if getattr(wl, "B0", None) is not None:
         run.set_magnetic_field(wl.B0)
+        run.set_gyro_integrator(getattr(wl, "gyro", "boris"))
     return run
 
 

@@ -1026,6 +1026,17 @@ int cpic_set_magnetic_field(cpic_run* r, const double* B) {
     return CPIC_OK;
 }
 
+int cpic_set_gyro_integrator(cpic_run* r, int kind) {
+    CHECK_RUN(r);
+    if (kind != CPIC_GYRO_BORIS && kind != CPIC_GYRO_CYCLOTRONIC) {
+        set_error("set_gyro_integrator: CPIC_GYRO_BORIS or CPIC_GYRO_CYCLOTRONIC");
+        return CPIC_ERR_INVALID;
+    }
+    r->gyro_kind = kind;
+    invalidate_graphs(r);
+    return CPIC_OK;
+}
+
 int cpic_set_floating(cpic_run* r, int face, double charge0) {
     CHECK_RUN(r);
     CHECK_MAP(r);

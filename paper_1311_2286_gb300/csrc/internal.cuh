@@ -106,6 +106,9 @@ struct PushParams {
     float bh[CPIC_MAX_SPECIES];    // Boris constants per species: half kick (float)(dt q/m / 2),
     float bt[CPIC_MAX_SPECIES][3]; // t = (float)(dt q/m B0 / 2),
     float bs[CPIC_MAX_SPECIES][3]; // s = (float)(2 t / (1 + |t|^2)) (t, s from FP64 values)
+    int gyro;                      // cyclotronic integrator (exact gyration) instead of Boris
+    float gb[3];                   // its unit field direction b (velocity components' basis)
+    float gy[CPIC_MAX_SPECIES][4]; // per species cos th, sin th, sin th / th, (1 - cos th) / th
     int chunk;                     // particles per block chunk (0: one wave of blocks)
     int tile;                      // 1: shared-memory deposit tile when the chunk fits
     DevCounters* ctr;
@@ -192,6 +195,7 @@ struct cpic_run {
     double B0[3];                // uniform magnetic field (cpic_set_magnetic_field)
     double kick_fraction;        // fraction of dt of the kick being launched (1 otherwise)
     int magnetized;              // B0 != 0
+    int gyro_kind;               // CPIC_GYRO_*: Boris step or cyclotronic integrator
     int floating_face;           // face whose conductor floats (cpic_set_floating), -1: none
     double float_q0;             // its charge before any particle was collected
     double* psi;                 // potential of the unit-potential conductor in charge-free space

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
             Tab<D>::gather(p, vertex_of<D>(p, c), t, kp, gp);
         }
         if (MODE == 2) {
-            if (active && p.magnetized) {  // Boris step over the kick's fraction of dt
+            if (active && p.magnetized && !p.gyro) {  // Boris step over the kick's fraction of dt
                 float E[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
                 for (int al = 0; al < D; ++al) {
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
         if (active) {
             const float vo0 = v[0], vo1 = v[1], vo2 = v[2];
             const float dtqm = p.dtqm[s];
-            if (p.magnetized) {  // warp-uniform
+            if (p.magnetized && !p.gyro) {  // warp-uniform
                 float E[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
                 for (int al = 0; al < D; ++al) {
@@ -195,8 +195,48 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
             // azimuth of (x, y), keeping r v_theta (the inertial forces of the cylindrical
             // frame); the kinetic-energy tally takes the velocity before the turn
             const bool axi = D == 2 && p.R != nullptr;  // warp-uniform
-            float disp[2] = {0.0f, 0.0f}, vrot[3] = {v[0], v[1], v[2]};
-            if (axi) {
+            const bool dform = axi || p.gyro;           // the position moves by disp
+            float disp[3] = {0.0f, 0.0f, 0.0f}, vrot[3] = {v[0], v[1], v[2]};
+            if (p.gyro) {
+                // cyclotronic integrator: after the plain kick, the exact motion in the
+                // uniform field alone over dt, b = B0 / |B0| (velocity components' basis),
+                // th = (q/m) |B0| dt: u = v x b, par = (v . b) b, perp = v - par,
+                // v' = par + cos th perp + sin th u, d = dt (par + f1 perp + f2 u) with
+                // f1 = sin th / th, f2 = (1 - cos th) / th
+                const float* b = p.gb;
+                const float cs = p.gy[s][0], sn = p.gy[s][1], f1 = p.gy[s][2], f2 = p.gy[s][3];
+                const float vpar = __fmaf_rn(v[2], b[2], __fmaf_rn(v[1], b[1], __fmul_rn(v[0], b[0])));
+                const float u[3] = {__fmaf_rn(v[1], b[2], -__fmul_rn(v[2], b[1])),
+                                    __fmaf_rn(v[2], b[0], -__fmul_rn(v[0], b[2])),
+                                    __fmaf_rn(v[0], b[1], -__fmul_rn(v[1], b[0]))};
+                float d3[3];
+#pragma unroll
+                for (int al = 0; al < 3; ++al) {
+                    const float par = __fmul_rn(vpar, b[al]);
+                    const float perp = __fsub_rn(v[al], par);
+                    vrot[al] = __fmaf_rn(sn, u[al], __fmaf_rn(cs, perp, par));
+                    d3[al] = __fmul_rn(p.dt, __fmaf_rn(f2, u[al], __fmaf_rn(f1, perp, par)));
+                }
+                if (axi) {  // the displacement starts at the particle's point in 3D
+                    const float rn = gather_scalar2(p, vertex_of<D>(p, c), t);
+                    const float x = __fadd_rn(rn, d3[0]);
+                    const float y = d3[2];
+                    const float r1 = __fsqrt_rn(__fmaf_rn(x, x, __fmul_rn(y, y)));
+                    float ca = 1.0f, sa = 0.0f;
+                    if (r1 > 0.0f) {
+                        ca = __fdiv_rn(x, r1);
+                        sa = __fdiv_rn(y, r1);
+                    }
+                    disp[0] = __fsub_rn(r1, rn);
+                    disp[1] = d3[1];
+                    const float w0 = vrot[0], w2 = vrot[2];
+                    vrot[0] = __fmaf_rn(ca, w0, __fmul_rn(sa, w2));
+                    vrot[2] = __fmaf_rn(ca, w2, -__fmul_rn(sa, w0));
+                } else {
+#pragma unroll
+                    for (int a = 0; a < D; ++a) disp[a] = d3[a];
+                }
+            } else if (axi) {
                 const float rn = gather_scalar2(p, vertex_of<D>(p, c), t);
                 const float x = __fmaf_rn(p.dt, v[0], rn);
                 const float y = __fmul_rn(p.dt, v[2]);
@@ -217,8 +257,10 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 float x;
-                if (axi) {
-                    const float d = __fmaf_rn(kp[a * D + 1], disp[1], __fmul_rn(kp[a * D + 0], disp[0]));
+                if (dform) {
+                    float d = __fmul_rn(kp[a * D + 0], disp[0]);
+#pragma unroll
+                    for (int b = 1; b < D; ++b) d = __fmaf_rn(kp[a * D + b], disp[b], d);
                     x = __fmaf_rn(0.5f, d, t[a]);
                 } else {
                     float d = __fmul_rn(kp[a * D + 0], v[0]);
@@ -252,8 +294,10 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 float x;
-                if (axi) {
-                    const float d = __fmaf_rn(kq[a * D + 1], disp[1], __fmul_rn(kq[a * D + 0], disp[0]));
+                if (dform) {
+                    float d = __fmul_rn(kq[a * D + 0], disp[0]);
+#pragma unroll
+                    for (int b = 1; b < D; ++b) d = __fmaf_rn(kq[a * D + b], disp[b], d);
                     x = __fadd_rn(t[a], d);
                 } else {
                     float d = __fmul_rn(kq[a * D + 0], v[0]);
@@ -291,9 +335,9 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
             // throughput on this part is ~1/64 of FP32, so the product stays in FP32)
             float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
             tally.ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
-            if (axi) {
-                v[0] = vrot[0];
-                v[2] = vrot[2];
+            if (dform) {
+#pragma unroll
+                for (int al = 0; al < 3; ++al) v[al] = vrot[al];
             }
             // spec B: a reflecting face mirrors the position in logical space (u -> -u below,
             // u -> 2N - u above) and reflects v about row a of k(xi'); still outside after one
@@ -423,11 +467,34 @@ PushParams make_push_params(cpic_run* r) {
 // start-up half step backwards), computed in FP64 and rounded once
 void set_boris_constants(const cpic_run* r, PushParams* p, double fraction) {
     p->magnetized = r->magnetized;
+    // the field in the velocity components' basis: an axisymmetric run's (v_r, v_z,
+    // v_theta) is left-handed, so the component cross product with -B0 is the physical v x B0
+    double Bc[3];
+    for (int a = 0; a < 3; ++a) Bc[a] = r->cfg.axisymmetric ? -r->B0[a] : r->B0[a];
+    // cyclotronic integrator: b = Bc / |Bc| and per species cos th, sin th, sin th / th,
+    // (1 - cos th) / th with th = (q/m) |B0| dt (FP64, rounded once)
+    p->gyro = r->magnetized && r->gyro_kind == CPIC_GYRO_CYCLOTRONIC;
+    const double bm = sqrt(Bc[0] * Bc[0] + Bc[1] * Bc[1] + Bc[2] * Bc[2]);
+    for (int a = 0; a < 3; ++a) p->gb[a] = bm > 0.0 ? (float)(Bc[a] / bm) : 0.0f;
+    for (int s = 0; s < CPIC_MAX_SPECIES; ++s) {
+        double g4[4] = {1.0, 0.0, 1.0, 0.0};
+        if (s < r->cfg.n_species) {
+            const double th = r->cfg.q[s] / r->cfg.m[s] * bm * r->cfg.dt;
+            if (th != 0.0) {
+                const double sh = sin(0.5 * th);
+                g4[0] = cos(th);
+                g4[1] = sin(th);
+                g4[2] = sin(th) / th;
+                g4[3] = 2.0 * sh * sh / th;
+            }
+        }
+        for (int k = 0; k < 4; ++k) p->gy[s][k] = (float)g4[k];
+    }
     for (int s = 0; s < CPIC_MAX_SPECIES; ++s) {
         double h = 0.0, t[3] = {0.0, 0.0, 0.0};
         if (s < r->cfg.n_species) {
             h = 0.5 * fraction * r->cfg.dt * r->cfg.q[s] / r->cfg.m[s];
-            for (int a = 0; a < 3; ++a) t[a] = h * r->B0[a];
+            for (int a = 0; a < 3; ++a) t[a] = h * Bc[a];
         }
         const double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
         p->bh[s] = (float)h;

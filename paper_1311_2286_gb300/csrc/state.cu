@@ -4,7 +4,8 @@
 //
 // Checkpoint file (host byte order, all integers little-endian on the supported hosts):
 //   "CPICCKP1", u32 version, cpic_config, u64 nvert, f64 vertex map [nvert][D],
-//   InjectSpec[CPIC_MAX_SPECIES], DevCounters, i32 steps_since_sort, f64 phi [ncell],
+//   InjectSpec[CPIC_MAX_SPECIES], DevCounters, i32 steps_since_sort, i32 floating face,
+//   f64 its initial charge, f64 B0[3], i32 gyro integrator, f64 phi [ncell],
 //   per species: i64 count, i32 cell [count], f32 t [D][count], f32 v [3][count].
 // A restored run is created from the stored configuration and vertex map (the same metric
 // and multigrid hierarchy bit for bit), then takes the stored particles, counters, potential
@@ -20,7 +21,7 @@ namespace cpic {
 namespace {
 
 constexpr char kMagic[8] = {'C', 'P', 'I', 'C', 'C', 'K', 'P', '1'};
-constexpr unsigned kVersion = 3;  // 2: floating conductor, 3: magnetic field
+constexpr unsigned kVersion = 4;  // 2: floating conductor, 3: magnetic field, 4: gyro integrator
 
 size_t snapshot_bytes(const cpic_run* r) {
     size_t b = sizeof(DevCounters) + sizeof(double) * (size_t)r->ncell;
@@ -210,7 +211,8 @@ int cpic_checkpoint(cpic_run* r, const char* path) {
     const int since = r->steps_since_sort;
     bool ok = wr(f, kMagic, 8) && wr(f, &kVersion, 1) && wr(f, &r->cfg, 1) && wr(f, &nvert, 1) &&
               wr(f, X.data(), X.size()) && wr(f, r->inj, CPIC_MAX_SPECIES) && wr(f, &ctr, 1) && wr(f, &since, 1) &&
-              wr(f, &r->floating_face, 1) && wr(f, &r->float_q0, 1) && wr(f, r->B0, 3) && wr(f, phi.data(), phi.size());
+              wr(f, &r->floating_face, 1) && wr(f, &r->float_q0, 1) && wr(f, r->B0, 3) && wr(f, &r->gyro_kind, 1) &&
+              wr(f, phi.data(), phi.size());
     const int b = ctr.cur;
     const long long T = r->pb.total;
     for (int s = 0; ok && s < r->cfg.n_species; ++s) {
@@ -279,10 +281,12 @@ int cpic_restore(const char* path, void* arena, size_t arena_bytes, void* stream
     if (ok) st = cpic_set_map_vertices(r, X.data());
     int fface = -1;
     double fq0 = 0.0, B0[3] = {0.0, 0.0, 0.0};
+    int gyro = CPIC_GYRO_BORIS;
     ok = ok && !st && rd(f, r->inj, CPIC_MAX_SPECIES) && rd(f, &ctr, 1) && rd(f, &since, 1) && rd(f, &fface, 1) &&
-         rd(f, &fq0, 1) && rd(f, B0, 3);
+         rd(f, &fq0, 1) && rd(f, B0, 3) && rd(f, &gyro, 1);
     if (ok && fface >= 0) st = cpic_set_floating(r, fface, fq0);  // psi and its flux sum, recomputed
     if (ok && !st) st = cpic_set_magnetic_field(r, B0);
+    if (ok && !st) st = cpic_set_gyro_integrator(r, gyro);
     ok = ok && !st && rd(f, phi.data(), phi.size());
     // particles into buffer 0, counters with cur = 0
     const long long T = r->pb.total;

@@ -258,7 +258,8 @@ class Workload:
     omega_axisym: bool = False
     injection: list = field(default_factory=list)  # (species, face, density, vth, seed)
     sort_interval: int = 0
-    B0: tuple = None  # uniform magnetic field (physical space), None: unmagnetised
+    B0: tuple = None  # uniform magnetic field (velocity components), None: unmagnetised
+    gyro: str = "boris"  # magnetised push: "boris" or "cyclotronic" (exact gyration)
 
 
 def langmuir_map2(n1=32, n2=32, eps=0.05, ppc=64, vth=0.05, amp=0.01, dt=0.1, seed=0):

@@ -187,15 +187,21 @@ SPH = dict(n1=48, n2=48, npart_per_species=150_000, seed=43, dt=0.1)
 SPH_STEPS = 300
 
 
-def test_sphere_axisym_cycle_matches_oracle(cpic, record_property):
+@pytest.mark.parametrize("Bz", [0.0, 19.0])
+def test_sphere_axisym_cycle_matches_oracle(cpic, record_property, Bz):
     """Row f3: a reduced Test B run (the sphere r1 = 1 in r2 = 10 on the 2D axisymmetric
     (r, z) map, Omega = r, 48 x 48 cells, 150k + 150k rings, the sphere floating from zero
     charge, Maxwellian flux injection at r2, specular z axis, dt 0.1, sort every 4 steps,
     300 steps) on the device and in the oracle: start-up and first-step state <= 1e-5
     against FP64; W_E at every level equal to 1/2 sum phi Q of the device's fields; the
     sphere potential at every level within 1e-3 of its range, its time average within 1%;
-    time-averaged W_E within 1%; collected currents within 1% where the counts resolve it."""
-    w = wl.sphere_axisym(**SPH)
+    time-averaged W_E within 1%; collected currents within 1% where the counts resolve it.
+    With B_z = 19 along the axis (Test C's moderately magnetised field) both sides push
+    with the cyclotronic integrator at dt 0.05 (w_ce dt = 0.95)."""
+    w = wl.sphere_axisym(**SPH) if Bz == 0.0 else wl.sphere_axisym(**dict(SPH, dt=0.05))
+    if Bz:
+        w.B0 = (0.0, Bz, 0.0)
+        w.gyro = "cyclotronic"
     trace = []
     run, pic, err0, _, we, we_chk, we_ora, dev_abs, ora_abs = _run_pair(cpic, w, SPH_STEPS, 4, floating=(0, 0.0),
                                                                          trace=trace)
@@ -330,19 +336,50 @@ def test_served_request_matches_oracle(cpic):
     run.close()
 
 
-def test_magnetized_langmuir_cycle_matches_oracle(cpic):
+@pytest.mark.parametrize("gyro", ["boris", "cyclotronic"])
+def test_magnetized_langmuir_cycle_matches_oracle(cpic, gyro):
     """Row f2 through whole cycles: the cold plasma wave across a uniform B_z = 1 (the
     upper-hybrid oscillation the oracle's pin checks) on the device (generic kernel, Boris
-    kick, Boris start-up) against the oracle from the same particles: start-up and one-step
-    state <= 1e-5 against FP64, W_E at every level 1/2 sum phi Q of the device's fields,
-    time-averaged W_E within 1%."""
+    kick and start-up, or the cyclotronic push and its plain start-up kick) against the
+    oracle from the same particles: start-up and one-step state <= 1e-5 against FP64, W_E
+    at every level 1/2 sum phi Q of the device's fields, time-averaged W_E within 1%."""
     w = wl.langmuir_map2(32, 32, eps=0.05, ppc=16, vth=0.0, amp=0.05, dt=0.1, seed=0)
     w.B0 = (0.0, 0.0, 1.0)
+    w.gyro = gyro
     run = cpic.run_from_workload(w, sort_interval=0, mg_rtol=1e-12, mg_max_cycles=200)
     run, pic, err0, err1, we, we_chk, we_ora, _, _ = _run_pair(cpic, w, 100, 0, run=run)
     assert err0[0] <= 1e-5 and err0[1] <= 1e-5, err0
     assert err1[0] <= 1e-5 and err1[1] <= 1e-5, err1
     np.testing.assert_allclose(we, we_chk, rtol=1e-12)
     assert abs(we.mean() / we_ora.mean() - 1.0) <= 0.01, (we.mean(), we_ora.mean())
-    print("magnetized langmuir: W_E mean device %.6e oracle %.6e" % (we.mean(), we_ora.mean()))
+    print("magnetized langmuir (%s): W_E mean device %.6e oracle %.6e" % (gyro, we.mean(), we_ora.mean()))
+    run.close()
+
+
+@pytest.mark.parametrize("Bz,expected", [(1.9, -2.51), (19.0, -2.43)])
+def test_sphere_floating_potential_test_c(cpic, Bz, expected):
+    """Test C (Sec. III.C): the sphere of Test B in a uniform field along the axis, B_z0 =
+    1.9 (electron gyroradius 0.53, weakly magnetised) and 19 (0.053, moderately
+    magnetised; w_ce dt = 0.95, which the cyclotronic integrator resolves), 128 x 128,
+    dt 0.05, on the device with the cyclotronic push over 8000 steps (the physical time of
+    Test B's 4000). The paper's own values for these runs are -2.51 T_e and -2.43 T_e
+    (averaged over the last sixth), and it finds them within about 10% of another code's
+    -2.37 and -2.21; the sphere potential averaged over the last sixth here lies within
+    10% of the paper's values (and the potential is less negative in the stronger field).
+    Physics, not parity: the parity of this path is the cyclotronic push and cycle tests."""
+    n = 128
+    w = wl.sphere_axisym(n, n, npart_per_species=230 * n * n, seed=9, dt=0.05, capacity_factor=1.6)
+    w.B0 = (0.0, Bz, 0.0)
+    w.gyro = "cyclotronic"
+    run = cpic.run_from_workload(w, sort_interval=8)
+    run.set_floating(0, 0.0)
+    run.initialize()
+    steps, vs = 8000, []
+    for _ in range(steps // 50):
+        run.step(50)
+        vs.append(run.diag()["object_potential"])
+    tail = float(np.mean(vs[-len(vs) // 6:]))
+    print("Test C (B_z0 %.1f): sphere potential (last sixth of %d steps) %.4f T_e (paper %.2f)"
+          % (Bz, steps, tail, expected))
+    assert abs(tail / expected - 1.0) <= 0.10, tail
     run.close()

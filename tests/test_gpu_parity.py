@@ -739,21 +739,45 @@ def test_full_size_sphere_push_parity(cpic, tile):
     run.close()
 
 
+def test_full_size_sphere_solve_residual(cpic):
+    """a9 at the 3D configuration's full size (128^3 shell, 2.1M unknowns, 1M + 1M device
+    particles): a direct solve is out of reach there, so the device's potential is checked
+    by a property that holds at any size: the relative residual of the oracle's own FP64
+    operator and right-hand side (assembled here from the vertex map, with the charge from
+    the device's fixed-point counts) is <= 1e-10 after the device solve to 1e-12."""
+    run = cpic.sphere_run_device(128, 128, 128, 1_000_000, sort_interval=0, host_map=True)
+    w = wl.sphere(128, 128, 128, npart_per_species=1_000_000, host_particles=False)
+    cycles, res = run.solve_field(rtol=1e-12, max_cycles=200)
+    phi = run.phi()
+    C = [run.charge(s) for s in range(2)]
+    run.close()
+    g = geometry.build_geometry(w.vertices, [False, False, True])
+    M, bbc = poisson.assemble(g, w.field_bc, w.field_bc_value)
+    Q = poisson.charge_in_cells(g, C, [sp.q * sp.w for sp in w.species], w.background)
+    r = poisson.residual_norm(M, bbc, g, Q, phi, w.field_bc)
+    print("128^3 solve: %d cycles, device residual %.2e, oracle-operator residual %.2e" % (cycles, res, r))
+    assert r <= 1e-10, (r, cycles, res)
+
+
 # ------------------------------------------------------------------ uniform B0 (row f2)
 
 B_TEST = (0.3, -0.2, 1.1)
 B_AXIS = (0.0, 1.1, 0.0)  # axisymmetric runs: a uniform field along the symmetry axis (v = (v_r, v_z, v_theta))
 
 
+@pytest.mark.parametrize("gyro", ["boris", "cyclotronic"])
 @pytest.mark.parametrize("case", list(CASES))
-def test_magnetized_push_bit_exact_vs_replay(cpic, case):
+def test_magnetized_push_bit_exact_vs_replay(cpic, case, gyro):
     """Row f2: with a uniform B0 the push's kick is the Boris step (eq. (step1) with the
-    magnetic term): cells, offsets and velocities after one push equal the FP32 replay bit
-    for bit, the deposit equals the oracle's spec-Q deposit, and the state is within 1e-5
-    normwise of the FP64 oracle's Boris push."""
+    magnetic term), or the cyclotronic push (plain kick, then the exact gyration over dt
+    moving xi by its displacement): cells, offsets and velocities after one push equal the
+    FP32 replay bit for bit, the deposit equals the oracle's spec-Q deposit, and the state
+    is within 1e-5 normwise of the FP64 oracle's push."""
     w = CASES[case]()
     B = B_AXIS if w.omega_axisym else B_TEST
     w.B0 = B
+    w.gyro = gyro
+    cyc = gyro == "cyclotronic"
     rng = np.random.default_rng(12)
     phi = wl.random_field(rng, tuple(reversed(w.n)), 0.5)
     if case in DIRICHLET_AXIS0:
@@ -765,26 +789,30 @@ def test_magnetized_push_bit_exact_vs_replay(cpic, case):
         cell0, t0, v0 = pre[s]
         idx = _unpack(cell0, D)
         qm = sp.q / sp.m
-        i32, t32, v32, face, kefp = mover.push32(idx, t0, v0, k32, G32, w.n, w.particle_bc, np.float32(w.dt * qm),
-                                                np.float32(0.5 * w.dt), np.float32(w.dt),
-                                                boris=mover.boris_constants32(w.dt, qm, B), R32=_R(g, w, np.float32))
+        i32, t32, v32, face, kefp = mover.push32(
+            idx, t0, v0, k32, G32, w.n, w.particle_bc, np.float32(w.dt * qm), np.float32(0.5 * w.dt),
+            np.float32(w.dt), boris=None if cyc else mover.boris_constants32(w.dt, qm, B, axisym=w.omega_axisym),
+            R32=_R(g, w, np.float32), gyro=mover.gyro_constants32(w.dt, qm, B, w.omega_axisym) if cyc else None)
         alive = face < 0
         cell1, t1, v1 = post[s]
         assert np.array_equal(cell1, wl.pack_cells(i32[:, alive]))
         assert np.array_equal(t1, t32[:, alive]) and np.array_equal(v1, v32[:, alive])
         assert np.array_equal(charge[s], odep.deposit_fixed(i32[:, alive].astype(np.int64), t32[:, alive], w.n, per))
         i64, t64, v64, face64 = mover.push64(idx, t0.astype(np.float64), v0.astype(np.float64), g.k, G64, w.dt, qm,
-                                             w.n, w.particle_bc, B=B, R=_R(g, w))
+                                             w.n, w.particle_bc, B=B, R=_R(g, w), gyro=cyc)
         both = (face64 < 0) & alive
         keep = both[alive]
         dv = np.abs(v1[:, keep].astype(np.float64) - v64[:, both])
         assert np.max(dv) / np.max(np.abs(v64)) <= 1e-5
 
 
-def test_magnetized_start_up_kick_bit_exact(cpic):
-    """The start-up kick of a magnetised run is the Boris step over -dt/2 (FP32 replay)."""
+@pytest.mark.parametrize("gyro", ["boris", "cyclotronic"])
+def test_magnetized_start_up_kick_bit_exact(cpic, gyro):
+    """The start-up kick of a magnetised run is the Boris step over -dt/2, or with the
+    cyclotronic push the plain half kick (FP32 replay)."""
     w = CASES["map2_periodic"]()
     w.B0 = B_TEST
+    w.gyro = gyro
     g, _ = _geom(w)
     run = cpic.run_from_workload(w)
     rng = np.random.default_rng(14)
@@ -797,6 +825,6 @@ def test_magnetized_start_up_kick_bit_exact(cpic):
     qm = w.species[0].q / w.species[0].m
     G32 = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value).astype(np.float32)
     ref = mover.kick32(_unpack(ps.cell), ps.t, ps.v, g.k.astype(np.float32), G32, w.n, np.float32(-0.5 * w.dt * qm),
-                       boris=mover.boris_constants32(w.dt, qm, B_TEST, -0.5))
+                       boris=None if gyro == "cyclotronic" else mover.boris_constants32(w.dt, qm, B_TEST, -0.5))
     assert np.array_equal(v, ref)
     run.close()

@@ -371,3 +371,124 @@ def test_boris_exb_drift():
     mean = vs[: int(round(24 * period_steps))].mean(axis=0)
     assert np.max(np.abs(mean - drift)) < 2e-3 * np.linalg.norm(drift) + 1e-3 * 0.3, (mean, drift)
     assert v[2, 0] == 0.05
+
+
+# ------------------------------------------------------------------ cyclotronic integrator
+
+def _helix(x0, v0, b, w, t):
+    """Exact motion in a uniform field alone: dv/dt = w (v x b), |b| = 1, from (x0, v0)."""
+    vpar = np.dot(v0, b) * b
+    vperp = v0 - vpar
+    u = np.cross(v0, b)
+    x = x0 + vpar * t + (math.sin(w * t) / w) * vperp + ((1.0 - math.cos(w * t)) / w) * u
+    v = vpar + math.cos(w * t) * vperp + math.sin(w * t) * u
+    return x, v
+
+
+def test_cyclotronic_gyration_is_exact():
+    """The cyclotronic push (plain electric kick, then the exact gyration flow over dt)
+    follows the helix of a uniform field exactly, at any w dt (here 1.3 rad per step, with
+    B oblique to the 2D plane): after 37 steps position and velocity equal the closed form
+    to rounding, while the Boris step at the same dt is off by a phase error of order 0.1
+    per gyration. The C loops and the FP32 replay agree with the FP64 form."""
+    n = 16
+    k, G = _uniform_tables(n, (0.0, 0.0))
+    B = np.array([0.3, -0.4, 1.2])
+    qm, N = -1.0, 37
+    bm = float(np.linalg.norm(B))
+    dt = 1.3 / bm
+    w = qm * bm
+    x0 = np.array([5.25 / n, 7.5 / n, 0.0])
+    v0 = np.array([0.011, -0.006, 0.004])
+    idx = np.array([[5], [7]])
+    t = np.array([[0.25], [0.5]])
+    i, tt, v = idx, t, v0[:, None].copy()
+    ib, tb, vb = idx, t, v0[:, None].copy()
+    for _ in range(N):
+        i, tt, v, face = mover.push64(i, tt, v, k, G, dt, qm, (n, n), [0, 0, 0, 0], B=B, gyro=True)
+        ib, tb, vb, _f = mover.push64(ib, tb, vb, k, G, dt, qm, (n, n), [0, 0, 0, 0], B=B)
+    xe, ve = _helix(x0, v0, B / bm, w, N * dt)
+    pos = (i[:, 0] + tt[:, 0]) / n
+    dpos = (pos - xe[:2] + 0.5) % 1.0 - 0.5
+    assert np.max(np.abs(dpos)) < 1e-13, dpos
+    assert np.max(np.abs(v[:, 0] - ve)) < 1e-14, v[:, 0] - ve
+    assert np.max(np.abs(vb[:, 0] - ve)) > 1e-3  # Boris: the phase error of 2 atan(w dt / 2)
+    a = mover.push64(idx, t, v0[:, None], k, G, dt, qm, (n, n), [0, 0, 0, 0], B=B, gyro=True, return_kicked=True)
+    c = mover.push64_c(idx, t, v0[:, None], k, G, dt, qm, (n, n), [0, 0, 0, 0], B=B, gyro=True)
+    assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1]) and np.array_equal(a[2], c[2])
+    r = mover.push32(idx.astype(np.int32), t.astype(np.float32), v0[:, None].astype(np.float32),
+                     k.astype(np.float32), G.astype(np.float32), (n, n), [0, 0, 0, 0], np.float32(dt * qm),
+                     np.float32(dt / 2), np.float32(dt), gyro=mover.gyro_constants32(dt, qm, B))
+    np.testing.assert_allclose(r[2].astype(np.float64), a[2], rtol=0, atol=1e-8)
+    np.testing.assert_allclose(r[1].astype(np.float64), a[1], rtol=0, atol=1e-6)
+
+
+def test_cyclotronic_exb_drift_is_exact():
+    """Uniform E perpendicular to a uniform B: over a whole number of gyrations the
+    cyclotronic push moves the particle by exactly (E x B / B^2) times the elapsed time,
+    whatever dt (here w dt = pi/4, 8 steps per gyration, 5 gyrations), for any initial
+    velocity: the kick-plus-exact-gyration composition has the E x B drift as its fixed
+    point. The parallel velocity is untouched."""
+    n = 64
+    G0 = np.array([0.0001, -0.00004])  # a drift of (0.02, 0.05) over the run: no wrap
+    k, G = _uniform_tables(n, G0)
+    E = -n * G0
+    qm, Bz = -1.0, 2.0
+    dt = (math.pi / 4) / abs(qm * Bz)
+    drift = np.array([E[1] * Bz, -E[0] * Bz]) / Bz**2
+    idx = np.array([[10], [20]])
+    t = np.array([[0.5], [0.5]])
+    v = np.array([[0.3], [0.1], [0.05]])
+    i, tt = idx, t
+    N = 40
+    for _ in range(N):
+        i, tt, v, face = mover.push64(i, tt, v, k, G, dt, qm, (n, n), [0, 0, 0, 0], B=(0.0, 0.0, Bz), gyro=True)
+    disp = ((i + tt) - (idx + t))[:, 0] / n
+    np.testing.assert_allclose(disp, drift * N * dt, rtol=1e-9, atol=1e-14)
+    assert v[2, 0] == 0.05
+
+
+def test_axisym_gyration_sense_and_circle():
+    """An axisymmetric run with B along the axis: a positive particle moving in +theta
+    (v = (v_r, v_z, v_theta) = (0, v_z, v_theta), B = +B_z) is pushed outward (q v x B
+    along +r): the velocity components' basis (r, z, theta) is left-handed, so the push must
+    take v x B as the component cross product with -B. The cyclotronic push then follows
+    the exact 3D circle (projected on the meridional plane, velocity in the moving frame)
+    to the b1 map's interpolation error, and the Boris push turns the same way."""
+    n = 128
+    X = wl.sphere_axisym_vertices(n, n, 1.0, 10.0)
+    g = geometry.build_geometry(X, [False, False], axisym=True)
+    G = np.zeros(g.X.shape[:2] + (2,))
+    qm, Bz, dt, m = 1.0, 0.5, 0.4, 40
+    r0, z0 = 5.0, 1.0
+    v0 = np.array([0.0, 0.1, 0.4])  # (v_r, v_z, v_theta)
+    R = math.hypot(r0, z0)
+    u = np.array([[(R - 1.0) / 9.0 * n], [(1.0 - math.atan2(r0, z0) / math.pi) * n]])
+    c = np.floor(u).astype(np.int64)
+    B = (0.0, Bz, 0.0)
+    pbc = [1, 1, 2, 2]
+    _, _, vb, _ = mover.push64(c, u - c, v0[:, None], g.k, G, dt, qm, (n, n), pbc, B=B, R=g.X[..., 0])
+    _, _, vc, _ = mover.push64(c, u - c, v0[:, None], g.k, G, dt, qm, (n, n), pbc, B=B, R=g.X[..., 0], gyro=True)
+    assert vb[0, 0] > 0.0 and vc[0, 0] > 0.0  # outward
+    i, tt, v = c, u - c, v0[:, None].copy()
+    for _ in range(m):
+        i, tt, v, face = mover.push64(i, tt, v, g.k, G, dt, qm, (n, n), pbc, B=B, R=g.X[..., 0], gyro=True)
+        assert face[0] == -1
+    # Cartesian: x along r at the start, y along theta, z along the axis
+    xe, ve = _helix(np.array([r0, 0.0, z0]), np.array([v0[0], v0[2], v0[1]]), np.array([0.0, 0.0, 1.0]),
+                    qm * Bz, m * dt)
+    a = math.atan2(xe[1], xe[0])
+    rz = mover.gather(X, i, tt)[0]
+    assert abs(rz[0] - math.hypot(xe[0], xe[1])) < 10.0 / n**2 and abs(rz[1] - xe[2]) < 10.0 / n**2
+    vr = math.cos(a) * ve[0] + math.sin(a) * ve[1]
+    vth = -math.sin(a) * ve[0] + math.cos(a) * ve[1]
+    assert np.max(np.abs(v[:, 0] - np.array([vr, ve[2], vth]))) < 2.0 / n**2
+    # C loops and FP32 replay of one axisymmetric cyclotronic step
+    a64 = mover.push64(c, u - c, v0[:, None], g.k, G, dt, qm, (n, n), pbc, B=B, R=g.X[..., 0], gyro=True)
+    c64 = mover.push64_c(c, u - c, v0[:, None], g.k, G, dt, qm, (n, n), pbc, B=B, R=g.X[..., 0], gyro=True)
+    assert all(np.array_equal(x, y) for x, y in zip(a64[:3], c64[:3]))
+    r32 = mover.push32(c.astype(np.int32), (u - c).astype(np.float32), v0[:, None].astype(np.float32),
+                       g.k.astype(np.float32), G.astype(np.float32), (n, n), pbc, np.float32(dt * qm),
+                       np.float32(dt / 2), np.float32(dt), R32=g.X[..., 0].astype(np.float32),
+                       gyro=mover.gyro_constants32(dt, qm, B, axisym=True))
+    np.testing.assert_allclose(r32[2].astype(np.float64), a64[2], rtol=0, atol=2e-7)
