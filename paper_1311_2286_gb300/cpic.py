@@ -27,6 +27,8 @@ CPIC_SOLVER_MG, CPIC_SOLVER_BICGSTAB = 0, 1
 CPIC_BATCH_AUTO, CPIC_BATCH_BRANCHES, CPIC_BATCH_PERSISTENT = 0, 1, 2
 MAX_SPECIES = 4
 GYRO_BORIS, GYRO_CYCLOTRONIC = 0, 1  # cpic_set_gyro_integrator kinds
+MG_COARSE_REDISCRETIZED, MG_COARSE_GALERKIN = 0, 1  # cpic_set_multigrid
+MG_SMOOTH_POINT, MG_SMOOTH_LINE = 0, 1
 
 
 class cpic_config(ctypes.Structure):
@@ -152,6 +154,7 @@ _SIGS = {
     "cpic_set_floating": ([P, ctypes.c_int, ctypes.c_double], ctypes.c_int),
     "cpic_set_magnetic_field": ([P, P], ctypes.c_int),
     "cpic_set_gyro_integrator": ([P, ctypes.c_int], ctypes.c_int),
+    "cpic_set_multigrid": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "cpic_set_injection": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, ctypes.c_uint64],
                            ctypes.c_int),
     "cpic_initialize": ([P], ctypes.c_int),
@@ -401,6 +404,12 @@ class Run:
         an axisymmetric run's (v_r, v_z, v_theta) takes (0, B_z, 0) only)."""
         b = np.ascontiguousarray(B, dtype=np.float64)
         check(load().cpic_set_magnetic_field(self.h, _ptr(b)))
+
+    def set_multigrid(self, coarse="rediscretized", smoother="point"):
+        """cpic_set_multigrid: coarse "rediscretized" | "galerkin", smoother "point" | "line"."""
+        c = {"rediscretized": MG_COARSE_REDISCRETIZED, "galerkin": MG_COARSE_GALERKIN}[coarse]
+        m = {"point": MG_SMOOTH_POINT, "line": MG_SMOOTH_LINE}[smoother]
+        check(load().cpic_set_multigrid(self.h, c, m))
 
     def set_gyro_integrator(self, kind):
         """cpic_set_gyro_integrator: "boris" or "cyclotronic" (exact gyration in B0)."""

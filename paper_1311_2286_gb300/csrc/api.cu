@@ -226,6 +226,7 @@ void plan(cpic_run* r, Planner& P) {
         L.x32 = P.take<float>(L.ncell);
         L.b32 = P.take<float>(L.ncell);
         L.dinv32 = P.take<float>(L.ncell);
+        L.lw = D == 2 ? P.take<float>((size_t)2 * L.ncell) : nullptr;  // line relaxation work
     }
     const Level& Lc = r->lev[r->nlevels - 1];
     long long mm = Lc.ncell + 1;
@@ -773,6 +774,27 @@ int cpic_set_solver(cpic_run* r, int solver) {
         invalidate_graphs(r);  // captured steps hold the solve
     }
     return CPIC_OK;
+}
+
+int cpic_set_multigrid(cpic_run* r, int coarse, int smoother) {
+    CHECK_RUN(r);
+    if ((coarse != CPIC_MG_COARSE_REDISCRETIZED && coarse != CPIC_MG_COARSE_GALERKIN) ||
+        (smoother != CPIC_MG_SMOOTH_POINT && smoother != CPIC_MG_SMOOTH_LINE)) {
+        set_error("set_multigrid: unknown coarse operator %d or smoother %d", coarse, smoother);
+        return CPIC_ERR_INVALID;
+    }
+    if (r->D != 2 && (coarse != CPIC_MG_COARSE_REDISCRETIZED || smoother != CPIC_MG_SMOOTH_POINT)) {
+        set_error("set_multigrid: Galerkin coarse operators and line relaxation are built for 2D runs only");
+        return CPIC_ERR_NOT_BUILT;
+    }
+    if (r->mg_coarse == coarse && r->mg_smoother == smoother) return CPIC_OK;
+    r->mg_coarse = coarse;
+    r->mg_smoother = smoother;
+    invalidate_graphs(r);
+    if (!r->map_set) return CPIC_OK;  // taken up when the map is set
+    int st = mg_setup(r);
+    if (!st) st = mg_cluster_prepare(r);
+    return st;
 }
 
 int cpic_set_push_tuning(cpic_run* r, int chunk, int tile) {

@@ -132,6 +132,7 @@ struct Level {
     float* x32;       // FP32 correction
     float* b32;       // FP32 residual / right-hand side of the correction
     float* dinv32;    // FP32 inverse diagonal (Gauss-Seidel)
+    float* lw;        // 2D: line-relaxation work [2][ncell] (eliminated upper diagonal, 2nd solve)
 };
 
 struct InjectSpec {
@@ -196,6 +197,8 @@ struct cpic_run {
     double kick_fraction;        // fraction of dt of the kick being launched (1 otherwise)
     int magnetized;              // B0 != 0
     int gyro_kind;               // CPIC_GYRO_*: Boris step or cyclotronic integrator
+    int mg_coarse;               // CPIC_MG_COARSE_*: rediscretised or Galerkin coarse operators
+    int mg_smoother;             // CPIC_MG_SMOOTH_*: point or alternating zebra line Gauss-Seidel
     int floating_face;           // face whose conductor floats (cpic_set_floating), -1: none
     double float_q0;             // its charge before any particle was collected
     double* psi;                 // potential of the unit-potential conductor in charge-free space

@@ -78,11 +78,13 @@ struct LV {
     const R* A;
     R* x;
     R* b;
+    float* lw;  // 2D line relaxation: work [2][ncell] in global memory (FP32 levels)
 };
 
 struct LVSet {
     int nl;
     int first_cta;  // first level solved inside one CTA
+    int line;       // 1: alternating zebra line relaxation (2D) instead of point smoothing
     LV<float> l[MAX_LEVELS];
     const float* dense_inv;
     int dense_m;   // unknowns of the coarsest level
@@ -286,6 +288,170 @@ __device__ __forceinline__ void prolong_at(const LV<R>& F, const LV<R>& Cl, cons
     F.x[q[0] + F.n[0] * (q[1] + F.n[1] * q[2])] += acc;
 }
 
+// ------------------------------------------------------------------ line relaxation (2D)
+// Zebra line Gauss-Seidel (robust for anisotropic cells, Sec. II.B.3): every line of cells
+// along `axis` is solved exactly (a tridiagonal system, cyclic on a periodic axis) with the
+// cells of the neighbouring lines at their current values; lines of one colour (line index
+// parity; a periodic axis with an odd line count gives its last line a third colour) are
+// independent. One sweep relaxes the lines along axis 0, then those along axis 1.
+template <int NPT>
+__device__ void line_solve(const LV<float>& L, int axis, int line) {
+    const int n = L.n[axis];
+    const int stride = axis == 0 ? 1 : L.n[0];
+    const int base = axis == 0 ? line * L.n[0] : line;
+    const int km = axis == 0 ? 1 : 3, kp = axis == 0 ? 2 : 4;  // in-line -1 / +1 slots
+    const bool per = L.per[axis] != 0;
+    float* cp = L.lw;            // eliminated upper diagonal (cells of this line only)
+    float* z = L.lw + L.ncell;   // second solve of the cyclic case
+    const int nc = L.ncell;
+    auto coeff = [&](int k, int c) { return L.A[k * nc + c]; };
+    // right-hand side of cell i: b - (off-line stencil terms), neighbours as in stencil_sum
+    auto rhs = [&](int c) {
+        int q[3];
+        q[0] = c % L.n[0];
+        q[1] = c / L.n[0];
+        const int lo0 = q[0] > 0 ? q[0] - 1 : (L.per[0] ? L.n[0] - 1 : 0);
+        const int hi0 = q[0] + 1 < L.n[0] ? q[0] + 1 : (L.per[0] ? 0 : L.n[0] - 1);
+        const int lo1 = q[1] > 0 ? q[1] - 1 : (L.per[1] ? L.n[1] - 1 : 0);
+        const int hi1 = q[1] + 1 < L.n[1] ? q[1] + 1 : (L.per[1] ? 0 : L.n[1] - 1);
+        const int ix[3] = {lo0, q[0], hi0};
+        const int jy[3] = {L.n[0] * lo1, L.n[0] * q[1], L.n[0] * hi1};
+        float s = L.b[c];
+#pragma unroll
+        for (int k = 1; k < NPT; ++k) {
+            if (k == km || k == kp) continue;
+            s -= coeff(k, c) * L.x[ix[koff(2, k, 0) + 1] + jy[koff(2, k, 1) + 1]];
+        }
+        return s;
+    };
+    if (n == 1) {
+        const int c = base;
+        const float d = coeff(0, c) + (per ? coeff(km, c) + coeff(kp, c) : 0.0f);
+        L.x[c] = rhs(c) / d;
+        return;
+    }
+    if (n == 2 && per) {  // both in-line neighbours are the other cell
+        const int c0 = base, c1 = base + stride;
+        const float a00 = coeff(0, c0), a01 = coeff(km, c0) + coeff(kp, c0);
+        const float a10 = coeff(km, c1) + coeff(kp, c1), a11 = coeff(0, c1);
+        const float r0 = rhs(c0), r1 = rhs(c1);
+        const float det = a00 * a11 - a01 * a10;
+        L.x[c0] = (r0 * a11 - a01 * r1) / det;
+        L.x[c1] = (a00 * r1 - a10 * r0) / det;
+        return;
+    }
+    // cyclic system: corners beta = A[0][n-1] (slot km of cell 0), alpha = A[n-1][0] (slot kp
+    // of the last cell); Sherman-Morrison with gamma = -d_0: T' = A - v w^T, v = (gamma, 0, ..,
+    // 0, alpha), w = (1, 0, .., 0, beta / gamma); x = y - z (w . y) / (1 + w . z) with T' y = r,
+    // T' z = v
+    const int cl = base + (n - 1) * stride;
+    const float beta = per ? coeff(km, base) : 0.0f, alpha = per ? coeff(kp, cl) : 0.0f;
+    const float gamma = -coeff(0, base);
+    float prev_cp = 0.0f, prev_y = 0.0f, prev_z = 0.0f;
+    for (int i = 0; i < n; ++i) {
+        const int c = base + i * stride;
+        float d = coeff(0, c);
+        const float l = i == 0 ? 0.0f : coeff(km, c);
+        const float u = i == n - 1 ? 0.0f : coeff(kp, c);
+        if (per && i == 0) d -= gamma;
+        if (per && i == n - 1) d -= alpha * beta / gamma;
+        const float den = d - l * prev_cp;
+        const float ci = u / den;
+        const float yi = (rhs(c) - l * prev_y) / den;
+        cp[c] = ci;
+        L.x[c] = yi;
+        prev_cp = ci;
+        prev_y = yi;
+        if (per) {
+            const float v = i == 0 ? gamma : (i == n - 1 ? alpha : 0.0f);
+            const float zi = (v - l * prev_z) / den;
+            z[c] = zi;
+            prev_z = zi;
+        }
+    }
+    for (int i = n - 2; i >= 0; --i) {
+        const int c = base + i * stride, cn = c + stride;
+        L.x[c] -= cp[c] * L.x[cn];
+        if (per) z[c] -= cp[c] * z[cn];
+    }
+    if (per) {
+        const float fact = (L.x[base] + beta * L.x[cl] / gamma) / (1.0f + z[base] + beta * z[cl] / gamma);
+        for (int i = 0; i < n; ++i) {
+            const int c = base + i * stride;
+            L.x[c] -= fact * z[c];
+        }
+    }
+}
+
+__host__ __device__ inline int line_colours(int n, int per) { return per && (n & 1) ? 3 : 2; }
+// the idx-th line of colour col (lines of colours 0, 1: parity; colour 2: the last line)
+__host__ __device__ inline int line_count(int n, int per, int col) {
+    if (col == 2) return 1;
+    const int m = line_colours(n, per) == 3 ? n - 1 : n;
+    return col == 0 ? (m + 1) / 2 : m / 2;
+}
+__host__ __device__ inline int line_index(int n, int col, int idx) { return col == 2 ? n - 1 : 2 * idx + col; }
+
+template <int NPT>
+__global__ void line_kernel(LV<float> L, int axis, int col) {
+    const int n = L.n[axis], lines = L.n[1 - axis];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= line_count(lines, L.per[1 - axis], col)) return;
+    (void)n;
+    line_solve<NPT>(L, axis, line_index(lines, col, idx));
+}
+
+// ------------------------------------------------------------------ Galerkin coarse operators
+// A_C = R A P (BoxMG's variational coarse operator, Sec. II.B.3) with the V-cycle's own
+// transfers: R sums the 2^D fine children, P is the bilinear prolongation of prolong_at with
+// its homogeneous ghost rules (an out-of-range coarse source is the boundary cell, negated
+// at a Dirichlet face; periodic axes wrap). Every source of P e_C' reached from a child of C
+// lies within one coarse cell of C, so a 9-point fine operator gives a 9-point coarse one
+// (2D). FP64, one thread per coarse cell, entries in stencil-slot order.
+__global__ void galerkin2_kernel(LV<double> F, LV<double> C, double* Ac) {
+    for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < C.ncell; cc += gridDim.x * blockDim.x) {
+        const int I = cc % C.n[0], J = cc / C.n[0];
+        double acc[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+        for (int ch = 0; ch < 4; ++ch) {
+            const int f0 = 2 * I + (ch & 1), f1 = 2 * J + (ch >> 1);
+            const int f = f0 + F.n[0] * f1;
+            for (int k = 0; k < 9; ++k) {
+                const double a = F.A[k * F.ncell + f];
+                if (a == 0.0) continue;
+                const int g[2] = {f0 + koff(2, k, 0), f1 + koff(2, k, 1)};  // unwrapped
+                int p[2], sdir[2];
+                for (int ax = 0; ax < 2; ++ax) {
+                    p[ax] = g[ax] >> 1;  // floor(g / 2), also for g = -1
+                    sdir[ax] = (g[ax] & 1) ? 1 : -1;
+                }
+                for (int o = 0; o < 4; ++o) {
+                    double w = 1.0;
+                    int off[2];
+                    for (int ax = 0; ax < 2; ++ax) {
+                        const int src = p[ax] + (((o >> ax) & 1) ? sdir[ax] : 0);
+                        w *= ((o >> ax) & 1) ? 0.25 : 0.75;
+                        const int base = ax == 0 ? I : J;
+                        off[ax] = src - base;
+                        if (!C.per[ax] && (src < 0 || src >= C.n[ax])) {
+                            off[ax] = 0;  // the ghost maps onto this boundary cell
+                            const int side = src < 0 ? 0 : 1;
+                            if (C.bc[2 * ax + side] == CPIC_BC_DIRICHLET) w = -w;
+                        }
+                    }
+                    int slot = 0;
+                    for (int k2 = 0; k2 < 9; ++k2)
+                        if (koff(2, k2, 0) == off[0] && koff(2, k2, 1) == off[1]) slot = k2;
+                    acc[slot] += w * a;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ac[k * C.ncell + cc] = acc[k];
+    }
+}
+
 // ------------------------------------------------------------------ FP32 cycle kernels
 // 3D launch geometry: x covers the first (index) dimension, y the second, z the third.
 template <int D, int NPT>
@@ -352,6 +518,24 @@ __global__ void __launch_bounds__(512) coarse_cycle_kernel(LVSet S, int nu1, int
         }
     }
     __syncthreads();
+    // alternating zebra line relaxation (2D): lines along axis 0 then axis 1, each colour
+    // in turn (reverse order after the coarse-grid correction)
+    auto line_sweep = [&](int l, bool reverse) {
+        if constexpr (D == 2) {
+            const LV<float>& L = V[l];
+            for (int st = 0; st < 2; ++st) {
+                const int axis = reverse ? 1 - st : st;
+                const int lines = L.n[1 - axis], per = L.per[1 - axis];
+                const int ncol = line_colours(lines, per);
+                for (int cc = 0; cc < ncol; ++cc) {
+                    const int col = reverse ? ncol - 1 - cc : cc;
+                    const int cnt = line_count(lines, per, col);
+                    for (int idx = tid; idx < cnt; idx += nt) line_solve<NPT>(L, axis, line_index(lines, col, idx));
+                    __syncthreads();
+                }
+            }
+        }
+    };
     auto sweep = [&](int l, int col) {
         const LV<float>& L = V[l];
         int d[3];
@@ -367,8 +551,11 @@ __global__ void __launch_bounds__(512) coarse_cycle_kernel(LVSet S, int nu1, int
         __syncthreads();
     };
     for (int l = S.first_cta; l < S.nl - 1; ++l) {
-        for (int it = 0; it < nu1; ++it)
-            for (int col = 0; col < V[l].ncol; ++col) sweep(l, col);
+        for (int it = 0; it < nu1; ++it) {
+            if (S.line) line_sweep(l, false);
+            else
+                for (int col = 0; col < V[l].ncol; ++col) sweep(l, col);
+        }
         const LV<float>& C = V[l + 1];
         const int plane = C.n[0] * C.n[1];
         for (int idx = tid; idx < C.ncell; idx += nt) {
@@ -403,8 +590,11 @@ __global__ void __launch_bounds__(512) coarse_cycle_kernel(LVSet S, int nu1, int
             prolong_at<D>(L, V[l + 1], q);
         }
         __syncthreads();
-        for (int it = 0; it < nu2; ++it)
-            for (int col = V[l].ncol - 1; col >= 0; --col) sweep(l, col);
+        for (int it = 0; it < nu2; ++it) {
+            if (S.line) line_sweep(l, true);
+            else
+                for (int col = V[l].ncol - 1; col >= 0; --col) sweep(l, col);
+        }
     }
     const LV<float>& T = S.l[S.first_cta];
     for (int c = tid; c < T.ncell; c += nt) T.x[c] = V[S.first_cta].x[c];
@@ -913,6 +1103,7 @@ LV<R> make_lv(const cpic_run* r, int l, bool fp32) {
     const bool cross = Lv.cross && !(fp32 && r->pc_face_only);
     L.used = cross ? Lv.S : 2 * r->D + 1;
     L.ncol = cross ? (1 << r->D) : 2;
+    L.lw = Lv.lw;
     if (fp32) {
         L.A = (const R*)Lv.A32;
         L.x = (R*)Lv.x32;
@@ -937,6 +1128,7 @@ constexpr size_t CTA_SMEM_MAX = 200 * 1024;  // shared memory of the one-CTA coa
 LVSet make_set(const cpic_run* r) {
     LVSet S;
     S.nl = r->nlevels;
+    S.line = r->D == 2 && r->mg_smoother == CPIC_MG_SMOOTH_LINE ? 1 : 0;
     for (int l = 0; l < r->nlevels; ++l) S.l[l] = make_lv<float>(r, l, true);
     // the one-CTA part starts at the first level of at most COARSE_CELLS cells from which
     // every coarser level fits the CTA's shared memory (stencil, inverse diagonal, x, b)
@@ -1006,10 +1198,33 @@ int enqueue_vcycle(cpic_run* r, const LVSet& S) {
             CPIC_CHECK_LAUNCH();
             return CPIC_OK;
         };
+        // alternating zebra line relaxation (2D): one thread per line of a colour
+        auto line_smooth = [&](int l, bool reverse) -> int {
+            if constexpr (D == 2) {
+                const LV<float>& L = S.l[l];
+                for (int stp = 0; stp < 2; ++stp) {
+                    const int axis = reverse ? 1 - stp : stp;
+                    const int lines = L.n[1 - axis], per = L.per[1 - axis];
+                    const int ncol = line_colours(lines, per);
+                    for (int cc = 0; cc < ncol; ++cc) {
+                        const int col = reverse ? ncol - 1 - cc : cc;
+                        const int cnt = line_count(lines, per, col);
+                        line_kernel<NPT><<<(cnt + 63) / 64, 64, 0, st>>>(L, axis, col);
+                        CPIC_CHECK_LAUNCH();
+                    }
+                }
+            }
+            return CPIC_OK;
+        };
         for (int l = 0; l < top; ++l) {
-            for (int it = 0; it < nu1; ++it)
+            for (int it = 0; it < nu1; ++it) {
+                if (S.line) {
+                    if (int e = line_smooth(l, false)) return e;
+                    continue;
+                }
                 for (int col = 0; col < S.l[l].ncol; ++col)
                     if (int e = smooth(l, col)) return e;
+            }
             const LV<float>& C = S.l[l + 1];
             restrict_kernel<D, NPT><<<cell_grid(C.n[0], C.n[1], C.n[2]), kCellBlock, 0, st>>>(S.l[l], C);
             CPIC_CHECK_LAUNCH();
@@ -1029,9 +1244,14 @@ int enqueue_vcycle(cpic_run* r, const LVSet& S) {
             const LV<float>& L = S.l[l];
             prolong_kernel<D><<<cell_grid(L.n[0], L.n[1], L.n[2]), kCellBlock, 0, st>>>(L, S.l[l + 1]);
             CPIC_CHECK_LAUNCH();
-            for (int it = 0; it < nu2; ++it)
+            for (int it = 0; it < nu2; ++it) {
+                if (S.line) {
+                    if (int e = line_smooth(l, true)) return e;
+                    continue;
+                }
                 for (int col = L.ncol - 1; col >= 0; --col)
                     if (int e = smooth(l, col)) return e;
+            }
         }
         return CPIC_OK;
     });
@@ -1168,7 +1388,14 @@ int mg_setup(cpic_run* r) {
         P.bbc = l == 0 ? r->rhs_bc : nullptr;
         P.cross_flag = flag;
         P.cross_max = cmax;
-        assemble_kernel<<<grid_blocks(Lv.ncell, 256), 256, 0, r->stream>>>(P);
+        const bool galerkin = r->D == 2 && r->mg_coarse == CPIC_MG_COARSE_GALERKIN;
+        if (galerkin && l > 0) {
+            // variational coarse operator from the level above (its full 9-point stencil)
+            LV<double> F = make_lv<double>(r, l - 1, false);
+            galerkin2_kernel<<<grid_blocks(Lv.ncell, 256), 256, 0, r->stream>>>(F, P.L, Lv.A);
+        } else {
+            assemble_kernel<<<grid_blocks(Lv.ncell, 256), 256, 0, r->stream>>>(P);
+        }
         CPIC_CHECK_LAUNCH();
         to_float_kernel<<<grid_blocks((long long)Lv.S * Lv.ncell, 256), 256, 0, r->stream>>>(Lv.A, Lv.A32,
                                                                                               (long long)Lv.S * Lv.ncell);
@@ -1181,12 +1408,17 @@ int mg_setup(cpic_run* r) {
         CPIC_CUDA(cudaMemcpyAsync(&hmax, cmax, sizeof(unsigned), cudaMemcpyDeviceToHost, r->stream));
         CPIC_CUDA(cudaStreamSynchronize(r->stream));
         Lv.cross = hflag;
+        // Galerkin coarse operators are 9-point: the V-cycle keeps every entry on every level
+        if (r->D == 2 && r->mg_coarse == CPIC_MG_COARSE_GALERKIN) Lv.cross = 1;
         if (l == 0) {
             float ratio;
             memcpy(&ratio, &hmax, sizeof(ratio));
             // CPIC_PC_FULL_STENCIL in the environment keeps the full stencil in the V-cycle
             // (the face-only form is a cost choice; both meet the same stopping test)
-            r->pc_face_only = hflag && ratio <= PC_CROSS_DROP && !getenv("CPIC_PC_FULL_STENCIL") ? 1 : 0;
+            r->pc_face_only = hflag && ratio <= PC_CROSS_DROP && !getenv("CPIC_PC_FULL_STENCIL") &&
+                                      r->mg_coarse != CPIC_MG_COARSE_GALERKIN
+                                  ? 1
+                                  : 0;
         }
     }
     const Level& Lc = r->lev[r->nlevels - 1];
