@@ -256,8 +256,11 @@ def sphere_measurement(cpic, npart, steps, warmup, full_steps, stream, flush, e2
     ph, pp = profiled_phases(run, 4, lambda: run.step_particles(1), flush)
     push_ms = ph["push"][0] / max(ph["push"][1], 1)
     peak, kind = measured_peak()
-    roof = roofline(push_ms, pp, B3, peak, kind, profiled_traffic(PROFILE3, SRC3, pp),
-                    "push3d_kernel<absorb,reflect,periodic> (fused gather/push/boundary/deposit, 3D)")
+    tiled = bool(tuning.get("tile", 1)) if isinstance(tuning, dict) else True
+    kname = ("push3d_kernel<absorb,reflect,periodic> (fused gather/push/boundary, shared-tile deposit, 3D)" if tiled
+             else "push3d_direct_kernel<absorb,reflect,periodic> (fused gather/push/boundary, per-warp deposit "
+                  "transposition, 3D)")
+    roof = roofline(push_ms, pp, B3, peak, kind, profiled_traffic(PROFILE3, SRC3, pp), kname)
     run.step(1)
     full_ms, full_ps, cyc = timed_steps(run, full_steps, lambda: run.step(1), flush, stream)
     e2e = end_to_end(run, cpic, e2e_steps) if e2e_steps > 0 else None
