@@ -28,6 +28,7 @@ CPIC_BATCH_AUTO, CPIC_BATCH_BRANCHES, CPIC_BATCH_PERSISTENT = 0, 1, 2
 MAX_SPECIES = 4
 GYRO_BORIS, GYRO_CYCLOTRONIC = 0, 1  # cpic_set_gyro_integrator kinds
 MG_COARSE_REDISCRETIZED, MG_COARSE_GALERKIN = 0, 1  # cpic_set_multigrid
+MG_INTERP_BILINEAR, MG_INTERP_OPERATOR = 0, 1
 MG_SMOOTH_POINT, MG_SMOOTH_LINE = 0, 1
 
 
@@ -154,7 +155,7 @@ _SIGS = {
     "cpic_set_floating": ([P, ctypes.c_int, ctypes.c_double], ctypes.c_int),
     "cpic_set_magnetic_field": ([P, P], ctypes.c_int),
     "cpic_set_gyro_integrator": ([P, ctypes.c_int], ctypes.c_int),
-    "cpic_set_multigrid": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "cpic_set_multigrid": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "cpic_set_injection": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, ctypes.c_uint64],
                            ctypes.c_int),
     "cpic_initialize": ([P], ctypes.c_int),
@@ -405,11 +406,13 @@ class Run:
         b = np.ascontiguousarray(B, dtype=np.float64)
         check(load().cpic_set_magnetic_field(self.h, _ptr(b)))
 
-    def set_multigrid(self, coarse="rediscretized", smoother="point"):
-        """cpic_set_multigrid: coarse "rediscretized" | "galerkin", smoother "point" | "line"."""
+    def set_multigrid(self, coarse="rediscretized", smoother="point", interpolation="bilinear"):
+        """cpic_set_multigrid: coarse "rediscretized" | "galerkin", smoother "point" | "line",
+        interpolation "bilinear" | "operator"."""
         c = {"rediscretized": MG_COARSE_REDISCRETIZED, "galerkin": MG_COARSE_GALERKIN}[coarse]
+        i = {"bilinear": MG_INTERP_BILINEAR, "operator": MG_INTERP_OPERATOR}[interpolation]
         m = {"point": MG_SMOOTH_POINT, "line": MG_SMOOTH_LINE}[smoother]
-        check(load().cpic_set_multigrid(self.h, c, m))
+        check(load().cpic_set_multigrid(self.h, c, i, m))
 
     def set_gyro_integrator(self, kind):
         """cpic_set_gyro_integrator: "boris" or "cyclotronic" (exact gyration in B0)."""

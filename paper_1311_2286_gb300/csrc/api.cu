@@ -227,6 +227,8 @@ void plan(cpic_run* r, Planner& P) {
         L.b32 = P.take<float>(L.ncell);
         L.dinv32 = P.take<float>(L.ncell);
         L.lw = D == 2 ? P.take<float>((size_t)2 * L.ncell) : nullptr;  // line relaxation work
+        L.pw = D == 2 ? P.take<double>((size_t)2 * L.ncell) : nullptr;  // operator-induced weights
+        L.pw32 = D == 2 ? P.take<float>((size_t)2 * L.ncell) : nullptr;
     }
     const Level& Lc = r->lev[r->nlevels - 1];
     long long mm = Lc.ncell + 1;
@@ -776,19 +778,23 @@ int cpic_set_solver(cpic_run* r, int solver) {
     return CPIC_OK;
 }
 
-int cpic_set_multigrid(cpic_run* r, int coarse, int smoother) {
+int cpic_set_multigrid(cpic_run* r, int coarse, int interpolation, int smoother) {
     CHECK_RUN(r);
     if ((coarse != CPIC_MG_COARSE_REDISCRETIZED && coarse != CPIC_MG_COARSE_GALERKIN) ||
+        (interpolation != CPIC_MG_INTERP_BILINEAR && interpolation != CPIC_MG_INTERP_OPERATOR) ||
         (smoother != CPIC_MG_SMOOTH_POINT && smoother != CPIC_MG_SMOOTH_LINE)) {
-        set_error("set_multigrid: unknown coarse operator %d or smoother %d", coarse, smoother);
+        set_error("set_multigrid: unknown coarse operator %d, interpolation %d or smoother %d", coarse, interpolation,
+                  smoother);
         return CPIC_ERR_INVALID;
     }
-    if (r->D != 2 && (coarse != CPIC_MG_COARSE_REDISCRETIZED || smoother != CPIC_MG_SMOOTH_POINT)) {
-        set_error("set_multigrid: Galerkin coarse operators and line relaxation are built for 2D runs only");
+    if (r->D != 2 && (coarse != CPIC_MG_COARSE_REDISCRETIZED || interpolation != CPIC_MG_INTERP_BILINEAR ||
+                      smoother != CPIC_MG_SMOOTH_POINT)) {
+        set_error("set_multigrid: the BoxMG components are built for 2D runs only");
         return CPIC_ERR_NOT_BUILT;
     }
-    if (r->mg_coarse == coarse && r->mg_smoother == smoother) return CPIC_OK;
+    if (r->mg_coarse == coarse && r->mg_interp == interpolation && r->mg_smoother == smoother) return CPIC_OK;
     r->mg_coarse = coarse;
+    r->mg_interp = interpolation;
     r->mg_smoother = smoother;
     invalidate_graphs(r);
     if (!r->map_set) return CPIC_OK;  // taken up when the map is set

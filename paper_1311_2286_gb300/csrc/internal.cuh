@@ -133,6 +133,8 @@ struct Level {
     float* b32;       // FP32 residual / right-hand side of the correction
     float* dinv32;    // FP32 inverse diagonal (Gauss-Seidel)
     float* lw;        // 2D: line-relaxation work [2][ncell] (eliminated upper diagonal, 2nd solve)
+    double* pw;       // 2D: operator-induced prolongation weights [2][ncell] of this (fine) level
+    float* pw32;      // their FP32 copy (the V-cycle's prolongation)
 };
 
 struct InjectSpec {
@@ -199,6 +201,7 @@ struct cpic_run {
     int gyro_kind;               // CPIC_GYRO_*: Boris step or cyclotronic integrator
     int mg_coarse;               // CPIC_MG_COARSE_*: rediscretised or Galerkin coarse operators
     int mg_smoother;             // CPIC_MG_SMOOTH_*: point or alternating zebra line Gauss-Seidel
+    int mg_interp;               // CPIC_MG_INTERP_*: bilinear or operator-induced prolongation
     int floating_face;           // face whose conductor floats (cpic_set_floating), -1: none
     double float_q0;             // its charge before any particle was collected
     double* psi;                 // potential of the unit-potential conductor in charge-free space

@@ -79,6 +79,7 @@ struct LV {
     R* x;
     R* b;
     float* lw;  // 2D line relaxation: work [2][ncell] in global memory (FP32 levels)
+    const R* pw;  // 2D operator-induced prolongation: own-parent weight per axis [2][ncell], or null
 };
 
 struct LVSet {
@@ -269,6 +270,11 @@ template <int D, typename R>
 __device__ __forceinline__ void prolong_at(const LV<R>& F, const LV<R>& Cl, const int* q) {
     const int p[3] = {q[0] >> 1, q[1] >> 1, q[2] >> 1};
     const int s[3] = {(q[0] & 1) ? 1 : -1, (q[1] & 1) ? 1 : -1, (q[2] & 1) ? 1 : -1};
+    const int f = q[0] + F.n[0] * (q[1] + F.n[1] * q[2]);
+    R own[3] = {R(0.75), R(0.75), R(0.75)};  // weight of the own parent per axis (bilinear: 3/4)
+    if (F.pw)
+#pragma unroll
+        for (int a = 0; a < D; ++a) own[a] = F.pw[a * F.ncell + f];
     R acc = R(0);
 #pragma unroll
     for (int o = 0; o < (D == 2 ? 4 : 8); ++o) {
@@ -278,9 +284,9 @@ __device__ __forceinline__ void prolong_at(const LV<R>& F, const LV<R>& Cl, cons
         for (int a = 0; a < D; ++a) {
             if ((o >> a) & 1) {
                 qq[a] += s[a];
-                w *= R(0.25);
+                w *= R(1) - own[a];
             } else {
-                w *= R(0.75);
+                w *= own[a];
             }
         }
         acc += w * coarse_value(Cl, qq);
@@ -426,12 +432,18 @@ __global__ void galerkin2_kernel(LV<double> F, LV<double> C, double* Ac) {
                     p[ax] = g[ax] >> 1;  // floor(g / 2), also for g = -1
                     sdir[ax] = (g[ax] & 1) ? 1 : -1;
                 }
+                double own[2] = {0.75, 0.75};  // the prolongation row of fine cell g
+                if (F.pw) {
+                    const int gw0 = (g[0] % F.n[0] + F.n[0]) % F.n[0], gw1 = (g[1] % F.n[1] + F.n[1]) % F.n[1];
+                    own[0] = F.pw[gw0 + F.n[0] * gw1];
+                    own[1] = F.pw[F.ncell + gw0 + F.n[0] * gw1];
+                }
                 for (int o = 0; o < 4; ++o) {
                     double w = 1.0;
                     int off[2];
                     for (int ax = 0; ax < 2; ++ax) {
                         const int src = p[ax] + (((o >> ax) & 1) ? sdir[ax] : 0);
-                        w *= ((o >> ax) & 1) ? 0.25 : 0.75;
+                        w *= ((o >> ax) & 1) ? 1.0 - own[ax] : own[ax];
                         const int base = ax == 0 ? I : J;
                         off[ax] = src - base;
                         if (!C.per[ax] && (src < 0 || src >= C.n[ax])) {
@@ -449,6 +461,56 @@ __global__ void galerkin2_kernel(LV<double> F, LV<double> C, double* Ac) {
         }
 #pragma unroll
         for (int k = 0; k < 9; ++k) Ac[k * C.ncell + cc] = acc[k];
+    }
+}
+
+// ------------------------------------------------------------------ operator-induced prolongation
+// BoxMG takes its interpolation weights from the operator (Sec. II.B.3). Reading for this
+// cell-centred 2:1 hierarchy: along each axis a fine cell is interpolated from its own
+// coarse parent C and the parent's neighbour N on the fine cell's side, with the weights of
+// the flux-continuous 1D solution between the two coarse centres: resistances from the fine
+// operator's couplings across faces, collapsed over the transverse direction (the sum of
+// the three entries linking the two columns of cells, as BoxMG collapses its stencils),
+//   R1 = 1 / (2 g(f_other -> f))   (C's centre is the face between its two children),
+//   R2 = 1 / g(f -> n) + 1 / (2 g(n -> n_other))   (n, n_other: N's children, n next to f),
+// own-parent weight R2 / (R1 + R2); uniform couplings give bilinear's 3/4. The 2D weights
+// are the product of the axes' weights. Cells whose neighbour parent is outside a
+// non-periodic boundary, or whose couplings are not all positive, keep 3/4 (the ghost
+// rule of prolong_at then applies).
+__global__ void interp_weights_kernel(LV<double> F, double* pw, float* pw32) {
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < F.ncell; f += gridDim.x * blockDim.x) {
+        const int q[2] = {f % F.n[0], f / F.n[0]};
+        for (int ax = 0; ax < 2; ++ax) {
+            double w = 0.75;
+            const int s = (q[ax] & 1) ? 1 : -1;                // side of the neighbour parent
+            const int nc = F.n[ax] / 2;
+            const int pn = (q[ax] >> 1) + s;                    // neighbour parent (coarse index)
+            const bool inside = F.per[ax] || (pn >= 0 && pn < nc);
+            if (inside) {
+                // fine cells along the axis: f_other, f, n, n_other at offsets -s, 0, s, 2s
+                auto cell = [&](int d) {
+                    int c[2] = {q[0], q[1]};
+                    c[ax] = ((c[ax] + d) % F.n[ax] + F.n[ax]) % F.n[ax];
+                    return c[0] + F.n[0] * c[1];
+                };
+                // collapsed coupling from cell c towards +dir (dir = +-1) along ax
+                auto coupling = [&](int c, int dir) {
+                    double gsum = 0.0;
+                    for (int k = 1; k < 9; ++k)
+                        if (koff(2, k, ax) == dir) gsum -= F.A[k * F.ncell + c];
+                    return gsum;
+                };
+                const double g1 = coupling(cell(-s), s);   // f_other -> f
+                const double g2 = coupling(f, s);           // f -> n
+                const double g3 = coupling(cell(s), s);     // n -> n_other
+                if (g1 > 0.0 && g2 > 0.0 && g3 > 0.0) {
+                    const double R1 = 0.5 / g1, R2 = 1.0 / g2 + 0.5 / g3;
+                    w = R2 / (R1 + R2);
+                }
+            }
+            pw[ax * F.ncell + f] = w;
+            pw32[ax * F.ncell + f] = (float)w;
+        }
     }
 }
 
@@ -1104,6 +1166,9 @@ LV<R> make_lv(const cpic_run* r, int l, bool fp32) {
     L.used = cross ? Lv.S : 2 * r->D + 1;
     L.ncol = cross ? (1 << r->D) : 2;
     L.lw = Lv.lw;
+    L.pw = nullptr;
+    if (r->D == 2 && r->mg_interp == CPIC_MG_INTERP_OPERATOR && l + 1 < r->nlevels)
+        L.pw = fp32 ? (const R*)(const void*)Lv.pw32 : (const R*)(const void*)Lv.pw;
     if (fp32) {
         L.A = (const R*)Lv.A32;
         L.x = (R*)Lv.x32;
@@ -1389,6 +1454,13 @@ int mg_setup(cpic_run* r) {
         P.cross_flag = flag;
         P.cross_max = cmax;
         const bool galerkin = r->D == 2 && r->mg_coarse == CPIC_MG_COARSE_GALERKIN;
+        if (l > 0 && r->D == 2 && r->mg_interp == CPIC_MG_INTERP_OPERATOR) {
+            // the prolongation weights of the level above, from its (finished) operator
+            LV<double> F = make_lv<double>(r, l - 1, false);
+            interp_weights_kernel<<<grid_blocks(F.ncell, 256), 256, 0, r->stream>>>(F, r->lev[l - 1].pw,
+                                                                                    r->lev[l - 1].pw32);
+            CPIC_CHECK_LAUNCH();
+        }
         if (galerkin && l > 0) {
             // variational coarse operator from the level above (its full 9-point stencil)
             LV<double> F = make_lv<double>(r, l - 1, false);

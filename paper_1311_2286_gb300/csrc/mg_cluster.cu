@@ -413,7 +413,9 @@ struct ClusterPlan {
 
 static bool plan_cluster(const cpic_run* r, int cs, ClusterPlan* out) {
     if (r->D != 2 || r->lev[0].cross || r->nlevels < 2 || r->nlevels > CL_MAX_LEVELS) return false;
-    if (r->mg_coarse != CPIC_MG_COARSE_REDISCRETIZED || r->mg_smoother != CPIC_MG_SMOOTH_POINT) return false;
+    if (r->mg_coarse != CPIC_MG_COARSE_REDISCRETIZED || r->mg_smoother != CPIC_MG_SMOOTH_POINT ||
+        r->mg_interp != CPIC_MG_INTERP_BILINEAR)
+        return false;
     ClParams& P = out->P;
     P.nl = r->nlevels;
     P.cs = cs;

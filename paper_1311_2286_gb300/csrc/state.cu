@@ -6,7 +6,7 @@
 //   "CPICCKP1", u32 version, cpic_config, u64 nvert, f64 vertex map [nvert][D],
 //   InjectSpec[CPIC_MAX_SPECIES], DevCounters, i32 steps_since_sort, i32 floating face,
 //   f64 its initial charge, f64 B0[3], i32 gyro integrator, i32 multigrid coarse operator,
-//   i32 smoother, f64 phi [ncell],
+//   i32 interpolation, i32 smoother, f64 phi [ncell],
 //   per species: i64 count, i32 cell [count], f32 t [D][count], f32 v [3][count].
 // A restored run is created from the stored configuration and vertex map (the same metric
 // and multigrid hierarchy bit for bit), then takes the stored particles, counters, potential
@@ -213,7 +213,7 @@ int cpic_checkpoint(cpic_run* r, const char* path) {
     bool ok = wr(f, kMagic, 8) && wr(f, &kVersion, 1) && wr(f, &r->cfg, 1) && wr(f, &nvert, 1) &&
               wr(f, X.data(), X.size()) && wr(f, r->inj, CPIC_MAX_SPECIES) && wr(f, &ctr, 1) && wr(f, &since, 1) &&
               wr(f, &r->floating_face, 1) && wr(f, &r->float_q0, 1) && wr(f, r->B0, 3) && wr(f, &r->gyro_kind, 1) &&
-              wr(f, &r->mg_coarse, 1) && wr(f, &r->mg_smoother, 1) &&
+              wr(f, &r->mg_coarse, 1) && wr(f, &r->mg_interp, 1) && wr(f, &r->mg_smoother, 1) &&
               wr(f, phi.data(), phi.size());
     const int b = ctr.cur;
     const long long T = r->pb.total;
@@ -283,10 +283,11 @@ int cpic_restore(const char* path, void* arena, size_t arena_bytes, void* stream
     if (ok) st = cpic_set_map_vertices(r, X.data());
     int fface = -1;
     double fq0 = 0.0, B0[3] = {0.0, 0.0, 0.0};
-    int gyro = CPIC_GYRO_BORIS, mgc = CPIC_MG_COARSE_REDISCRETIZED, mgs = CPIC_MG_SMOOTH_POINT;
+    int gyro = CPIC_GYRO_BORIS, mgc = CPIC_MG_COARSE_REDISCRETIZED, mgi = CPIC_MG_INTERP_BILINEAR;
+    int mgs = CPIC_MG_SMOOTH_POINT;
     ok = ok && !st && rd(f, r->inj, CPIC_MAX_SPECIES) && rd(f, &ctr, 1) && rd(f, &since, 1) && rd(f, &fface, 1) &&
-         rd(f, &fq0, 1) && rd(f, B0, 3) && rd(f, &gyro, 1) && rd(f, &mgc, 1) && rd(f, &mgs, 1);
-    if (ok && !st) st = cpic_set_multigrid(r, mgc, mgs);
+         rd(f, &fq0, 1) && rd(f, B0, 3) && rd(f, &gyro, 1) && rd(f, &mgc, 1) && rd(f, &mgi, 1) && rd(f, &mgs, 1);
+    if (ok && !st) st = cpic_set_multigrid(r, mgc, mgi, mgs);
     if (ok && fface >= 0) st = cpic_set_floating(r, fface, fq0);  // psi and its flux sum, recomputed
     if (ok && !st) st = cpic_set_magnetic_field(r, B0);
     if (ok && !st) st = cpic_set_gyro_integrator(r, gyro);

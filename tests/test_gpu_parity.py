@@ -317,14 +317,16 @@ def test_bicgstab_solve_vs_direct(cpic, case, monkeypatch):
     run.close()
 
 
-MG_VARIANTS = [("galerkin", "point"), ("rediscretized", "line"), ("galerkin", "line")]
+MG_VARIANTS = [("galerkin", "point"), ("rediscretized", "line"), ("galerkin", "line"),
+               ("galerkin", "point", "operator"), ("galerkin", "line", "operator")]
 
 
 @pytest.mark.parametrize("variant", MG_VARIANTS)
 @pytest.mark.parametrize("case", list(SOLVER_CASES))
 def test_boxmg_variants_solve_vs_direct(cpic, case, variant):
-    """Row f4: the multigrid with BoxMG's variational (Galerkin) coarse operators and/or
-    alternating zebra line relaxation, as the plain V-cycle iteration: the same four 2D
+    """Row f4: the multigrid with BoxMG's variational (Galerkin) coarse operators, its
+    operator-induced interpolation and/or alternating zebra line relaxation, as the plain
+    V-cycle iteration: the same four 2D
     problems (periodic singular with cross terms, Dirichlet annulus, mixed
     Dirichlet/Neumann non-orthogonal, Omega = r sphere) meet the same 1e-10 bound against
     the oracle's direct solve."""
@@ -354,7 +356,7 @@ def test_boxmg_variants_solve_vs_direct(cpic, case, variant):
     Q = poisson.charge_in_cells(g, [C], [-1e-3], 0.3)
     ref = poisson.solve(g, M, bbc, Q, bc)
     err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
-    print("%s %s/%s: %d V-cycles, residual %.2e, error %.2e" % (case, variant[0], variant[1], cycles, res, err))
+    print("%s %s: %d V-cycles, residual %.2e, error %.2e" % (case, "/".join(variant), cycles, res, err))
     assert res <= 1e-13 and err <= 1e-10, (err, cycles, res)
     run.close()
 
@@ -397,6 +399,51 @@ def test_boxmg_variants_on_anisotropic_cells(cpic, monkeypatch):
     best = cycles[("galerkin", "line")]
     assert best[1] <= 1e-10 and best[0] <= 15, cycles
     assert best[0] < cycles[("rediscretized", "point")][0], cycles
+
+
+def test_boxmg_interpolation_across_a_coefficient_jump(cpic, monkeypatch):
+    """Row f4, BoxMG's reason for operator-induced interpolation (discontinuous
+    coefficients): the cell width along x jumps 400-fold at an interior line (cell 33, which
+    the coarse cells straddle), so the face coefficients jump with it; the cells are
+    anisotropic too, so the smoother is line relaxation. With Galerkin coarse operators,
+    operator-induced interpolation reaches 1e-12 in fewer V-cycles than bilinear
+    interpolation (12 against 14 when measured), and both agree with the direct solve to
+    1e-9."""
+    monkeypatch.setenv("CPIC_NO_CLUSTER_SOLVER", "1")
+    n = (64, 64)
+    jump, ratio = 33, 400.0
+    widths = np.where(np.arange(n[0]) < jump, 1.0, ratio)
+    xv = np.concatenate([[0.0], np.cumsum(widths)])
+    xv /= xv[-1]
+    X = np.empty((n[1] + 1, n[0] + 1, 2))
+    X[..., 0] = xv[None, :]
+    X[..., 1] = (np.arange(n[1] + 1, dtype=np.float64) / n[1] * (20.0 / ratio))[:, None]
+    bc, bv = [Dr, Dr, P, P], [1.0, -1.0, 0.0, 0.0]
+    g = geometry.build_geometry(X, [False, True])
+    M, bbc = poisson.assemble(g, bc, bv)
+    rng = np.random.default_rng(9)
+    npart = 40_000
+    idx = np.stack([rng.integers(0, n[0], npart), rng.integers(0, n[1], npart)])
+    t = rng.random((2, npart)).astype(np.float32)
+    cycles = {}
+    for interp in ("bilinear", "operator"):
+        cfg = cpic.make_config(2, n, bc, bv, [PA, PA, PP, PP], 0.1, [(-1.0, 1.0, 1e-3, npart)], background=0.0)
+        run = cpic.Run(cfg)
+        run.set_map_vertices(X)
+        run.set_multigrid("galerkin", "line", interp)
+        run.set_solver(cpic.CPIC_SOLVER_MG)
+        cell = (idx[0] | (idx[1] << 16)).astype(np.int32)
+        run.load_particles(0, cell, t, np.zeros((3, npart), np.float32))
+        run.deposit()
+        c, res = run.solve_field(rtol=1e-12, max_cycles=200, allow_not_converged=True)
+        cycles[interp] = (c, res)
+        assert res <= 1e-12, (interp, c, res)
+        Q = poisson.charge_in_cells(g, [run.charge(0)], [-1e-3], 0.0)
+        ref = poisson.solve(g, M, bbc, Q, bc)
+        assert np.linalg.norm(run.phi() - ref) / np.linalg.norm(ref) <= 1e-9
+        run.close()
+    print("coefficient jump, V-cycles to 1e-12:", cycles)
+    assert cycles["operator"][0] < cycles["bilinear"][0], cycles
 
 
 @pytest.mark.parametrize("stencil", ["face_only", "full"])
