@@ -306,16 +306,15 @@ int cpic_set_solver(cpic_run* run, int solver);
  * coarse: CPIC_MG_COARSE_REDISCRETIZED (default: each coarse level assembled from the map
  * sampled at every other vertex) or CPIC_MG_COARSE_GALERKIN (A_coarse = R A_fine P with the
  * V-cycle's own restriction, the sum over the 2^D children, and prolongation; 9-point
- * coarse stencils). interpolation: CPIC_MG_INTERP_BILINEAR (default: weights 3/4, 1/4 per
+ * coarse stencils in 2D, 27-point in 3D). interpolation: CPIC_MG_INTERP_BILINEAR (default: weights 3/4, 1/4 per
  * axis, homogeneous ghost rules) or CPIC_MG_INTERP_OPERATOR (per axis, the weights of the
  * flux-continuous 1D solution between the fine cell's parent and the parent's neighbour,
  * from the fine operator's couplings across faces collapsed over the transverse direction;
  * uniform couplings give the bilinear weights). smoother: CPIC_MG_SMOOTH_POINT (default:
  * colour-ordered point Gauss-Seidel) or CPIC_MG_SMOOTH_LINE (alternating zebra line
- * Gauss-Seidel: every line of cells along axis 0, then along axis 1, solved exactly, cyclic
- * on a periodic axis). Any non-default choice runs the solve on the kernel chain (not the
- * one-cluster solver). 2D runs only (CPIC_ERR_NOT_BUILT in 3D); CPIC_ERR_INVALID for an
- * unknown value. Synchronous when the map is already set (the hierarchy is rebuilt);
+ * Gauss-Seidel: every line of cells along axis 0, then along axis 1 (then axis 2), solved
+ * exactly, cyclic on a periodic axis). Any non-default choice runs the solve on the kernel
+ * chain (not the one-cluster solver). CPIC_ERR_INVALID for an unknown value. Synchronous when the map is already set (the hierarchy is rebuilt);
  * invalidates captured step graphs. */
 #define CPIC_MG_COARSE_REDISCRETIZED 0
 #define CPIC_MG_COARSE_GALERKIN 1

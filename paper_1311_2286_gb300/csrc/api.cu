@@ -165,7 +165,7 @@ int plan_levels(const cpic_config* c, int lev_n[MAX_LEVELS][3], int* nl) {
 void plan(cpic_run* r, Planner& P) {
     const cpic_config& c = r->cfg;
     int D = r->D;
-    int S = D == 2 ? 9 : 19;
+    int S = D == 2 ? 9 : 27;  // 3D: the 19-point operator and the corners of Galerkin levels
     for (int l = 0; l < r->nlevels; ++l) {
         Level& L = r->lev[l];
         long long nv = (long long)(L.n[0] + 1) * (L.n[1] + 1) * (D == 3 ? L.n[2] + 1 : 1);
@@ -226,9 +226,9 @@ void plan(cpic_run* r, Planner& P) {
         L.x32 = P.take<float>(L.ncell);
         L.b32 = P.take<float>(L.ncell);
         L.dinv32 = P.take<float>(L.ncell);
-        L.lw = D == 2 ? P.take<float>((size_t)2 * L.ncell) : nullptr;  // line relaxation work
-        L.pw = D == 2 ? P.take<double>((size_t)2 * L.ncell) : nullptr;  // operator-induced weights
-        L.pw32 = D == 2 ? P.take<float>((size_t)2 * L.ncell) : nullptr;
+        L.lw = P.take<float>((size_t)2 * L.ncell);     // line relaxation work
+        L.pw = P.take<double>((size_t)D * L.ncell);    // operator-induced prolongation weights
+        L.pw32 = P.take<float>((size_t)D * L.ncell);
     }
     const Level& Lc = r->lev[r->nlevels - 1];
     long long mm = Lc.ncell + 1;
@@ -786,11 +786,6 @@ int cpic_set_multigrid(cpic_run* r, int coarse, int interpolation, int smoother)
         set_error("set_multigrid: unknown coarse operator %d, interpolation %d or smoother %d", coarse, interpolation,
                   smoother);
         return CPIC_ERR_INVALID;
-    }
-    if (r->D != 2 && (coarse != CPIC_MG_COARSE_REDISCRETIZED || interpolation != CPIC_MG_INTERP_BILINEAR ||
-                      smoother != CPIC_MG_SMOOTH_POINT)) {
-        set_error("set_multigrid: the BoxMG components are built for 2D runs only");
-        return CPIC_ERR_NOT_BUILT;
     }
     if (r->mg_coarse == coarse && r->mg_interp == interpolation && r->mg_smoother == smoother) return CPIC_OK;
     r->mg_coarse = coarse;

@@ -118,7 +118,7 @@ struct PushParams {
 struct Level {
     int n[3];
     long long ncell;
-    int S;            // stencil entries stored: 9 (2D) / 19 (3D)
+    int S;            // stencil entries stored: 9 (2D) / 27 (3D: 19-point operator + Galerkin corners)
     int cross;        // 1 if any cross coefficient is non-zero (9/19-point), else 5/7-point
     double* A;        // [S][ncell]
     double* x;        // solution (finest: phi) / correction
@@ -132,8 +132,8 @@ struct Level {
     float* x32;       // FP32 correction
     float* b32;       // FP32 residual / right-hand side of the correction
     float* dinv32;    // FP32 inverse diagonal (Gauss-Seidel)
-    float* lw;        // 2D: line-relaxation work [2][ncell] (eliminated upper diagonal, 2nd solve)
-    double* pw;       // 2D: operator-induced prolongation weights [2][ncell] of this (fine) level
+    float* lw;        // line-relaxation work [2][ncell] (eliminated upper diagonal, 2nd solve)
+    double* pw;       // operator-induced prolongation weights [D][ncell] of this (fine) level
     float* pw32;      // their FP32 copy (the V-cycle's prolongation)
 };
 

@@ -60,18 +60,21 @@ constexpr int RED_BLOCKS = 256;
 constexpr float PC_CROSS_DROP = 0.02f;
 
 __constant__ int c_off2[9][2] = {{0, 0}, {-1, 0}, {1, 0}, {0, -1}, {0, 1}, {-1, -1}, {1, -1}, {-1, 1}, {1, 1}};
-__constant__ int c_off3[19][3] = {{0, 0, 0},  {-1, 0, 0},  {1, 0, 0},  {0, -1, 0}, {0, 1, 0},
+// 3D slots: 19-point stencil, then the 8 corners that Galerkin coarse operators add
+__constant__ int c_off3[27][3] = {{0, 0, 0},  {-1, 0, 0},  {1, 0, 0},  {0, -1, 0}, {0, 1, 0},
                                   {0, 0, -1}, {0, 0, 1},   {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
                                   {1, 1, 0},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1}, {1, 0, 1},
-                                  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1}};
+                                  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1},
+                                  {-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {1, 1, -1},
+                                  {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}, {1, 1, 1}};
 
 template <typename R>
 struct LV {
     int D;
     int n[3];
     int ncell;
-    int S;      // stored stencil entries (9 / 19)
-    int used;   // entries used (5/7 without cross terms, else 9/19)
+    int S;      // stored stencil entries (9 / 27)
+    int used;   // entries used (5/7 without cross terms, else 9 / 19, or 27 with Galerkin levels)
     int ncol;   // Gauss-Seidel colours (2 or 2^D)
     int per[3];
     int bc[6];
@@ -134,14 +137,16 @@ __device__ __forceinline__ int nbr(const LV<R>& L, const int* q, const int* o) {
     return lin(L, c);
 }
 
-// stencil offset of slot k along axis a (2D: 9 slots, 3D: 19 slots); called with
+// stencil offset of slot k along axis a (2D: 9 slots, 3D: 27 slots); called with
 // unrolled constant arguments, so it folds away
 __host__ __device__ constexpr int koff(int D, int k, int a) {
     constexpr int t2[9][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0},
                               {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0}};
-    constexpr int t3[19][3] = {{0, 0, 0},  {-1, 0, 0},  {1, 0, 0},  {0, -1, 0}, {0, 1, 0},  {0, 0, -1}, {0, 0, 1},
+    constexpr int t3[27][3] = {{0, 0, 0},  {-1, 0, 0},  {1, 0, 0},  {0, -1, 0}, {0, 1, 0},  {0, 0, -1}, {0, 0, 1},
                                {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
-                               {1, 0, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1}};
+                               {1, 0, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1},
+                               {-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {1, 1, -1},
+                               {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}, {1, 1, 1}};
     return D == 2 ? t2[k][a] : t3[k][a];
 }
 
@@ -294,41 +299,49 @@ __device__ __forceinline__ void prolong_at(const LV<R>& F, const LV<R>& Cl, cons
     F.x[q[0] + F.n[0] * (q[1] + F.n[1] * q[2])] += acc;
 }
 
-// ------------------------------------------------------------------ line relaxation (2D)
+// ------------------------------------------------------------------ line relaxation
 // Zebra line Gauss-Seidel (robust for anisotropic cells, Sec. II.B.3): every line of cells
 // along `axis` is solved exactly (a tridiagonal system, cyclic on a periodic axis) with the
-// cells of the neighbouring lines at their current values; lines of one colour (line index
-// parity; a periodic axis with an odd line count gives its last line a third colour) are
-// independent. One sweep relaxes the lines along axis 0, then those along axis 1.
-template <int NPT>
-__device__ void line_solve(const LV<float>& L, int axis, int line) {
+// cells of the neighbouring lines at their current values. Lines are coloured by the parity
+// of their transverse coordinates (a periodic transverse axis with an odd count gives its
+// last index a third colour), so lines of one colour share no stencil entry and are
+// independent. One sweep relaxes the lines along axis 0, then axis 1 (then axis 2).
+template <int D, int NPT>
+__device__ void line_solve(const LV<float>& L, int axis, int base) {
     const int n = L.n[axis];
-    const int stride = axis == 0 ? 1 : L.n[0];
-    const int base = axis == 0 ? line * L.n[0] : line;
-    const int km = axis == 0 ? 1 : 3, kp = axis == 0 ? 2 : 4;  // in-line -1 / +1 slots
+    const int stride = axis == 0 ? 1 : (axis == 1 ? L.n[0] : L.n[0] * L.n[1]);
+    const int km = 1 + 2 * axis, kp = 2 + 2 * axis;  // in-line -1 / +1 slots
     const bool per = L.per[axis] != 0;
     float* cp = L.lw;            // eliminated upper diagonal (cells of this line only)
     float* z = L.lw + L.ncell;   // second solve of the cyclic case
     const int nc = L.ncell;
     auto coeff = [&](int k, int c) { return L.A[k * nc + c]; };
-    // right-hand side of cell i: b - (off-line stencil terms), neighbours as in stencil_sum
+    // right-hand side of cell c: b - (off-line stencil terms), neighbours as in stencil_sum
     auto rhs = [&](int c) {
         int q[3];
-        q[0] = c % L.n[0];
-        q[1] = c / L.n[0];
-        const int lo0 = q[0] > 0 ? q[0] - 1 : (L.per[0] ? L.n[0] - 1 : 0);
-        const int hi0 = q[0] + 1 < L.n[0] ? q[0] + 1 : (L.per[0] ? 0 : L.n[0] - 1);
-        const int lo1 = q[1] > 0 ? q[1] - 1 : (L.per[1] ? L.n[1] - 1 : 0);
-        const int hi1 = q[1] + 1 < L.n[1] ? q[1] + 1 : (L.per[1] ? 0 : L.n[1] - 1);
-        const int ix[3] = {lo0, q[0], hi0};
-        const int jy[3] = {L.n[0] * lo1, L.n[0] * q[1], L.n[0] * hi1};
-        float s = L.b[c];
+        cell_coords(L, c, q);
+        int lo[3], hi[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            lo[a] = q[a] > 0 ? q[a] - 1 : (L.per[a] ? L.n[a] - 1 : 0);
+            hi[a] = q[a] + 1 < L.n[a] ? q[a] + 1 : (L.per[a] ? 0 : L.n[a] - 1);
+        }
+        const int ix[3] = {lo[0], q[0], hi[0]};
+        const int jy[3] = {L.n[0] * lo[1], L.n[0] * q[1], L.n[0] * hi[1]};
+        int kz[3] = {0, 0, 0};
+        if (D == 3) {
+            const int pl = L.n[0] * L.n[1];
+            kz[0] = pl * lo[2];
+            kz[1] = pl * q[2];
+            kz[2] = pl * hi[2];
+        }
+        float sacc = L.b[c];
 #pragma unroll
         for (int k = 1; k < NPT; ++k) {
             if (k == km || k == kp) continue;
-            s -= coeff(k, c) * L.x[ix[koff(2, k, 0) + 1] + jy[koff(2, k, 1) + 1]];
+            sacc -= coeff(k, c) * L.x[ix[koff(D, k, 0) + 1] + jy[koff(D, k, 1) + 1] + (D == 3 ? kz[koff(D, k, 2) + 1] : 0)];
         }
-        return s;
+        return sacc;
     };
     if (n == 1) {
         const int c = base;
@@ -389,63 +402,84 @@ __device__ void line_solve(const LV<float>& L, int axis, int line) {
     }
 }
 
-__host__ __device__ inline int line_colours(int n, int per) { return per && (n & 1) ? 3 : 2; }
-// the idx-th line of colour col (lines of colours 0, 1: parity; colour 2: the last line)
-__host__ __device__ inline int line_count(int n, int per, int col) {
-    if (col == 2) return 1;
-    const int m = line_colours(n, per) == 3 ? n - 1 : n;
-    return col == 0 ? (m + 1) / 2 : m / 2;
-}
-__host__ __device__ inline int line_index(int n, int col, int idx) { return col == 2 ? n - 1 : 2 * idx + col; }
+// colours per transverse axis (2, or 3 for a periodic axis of odd size) and of an index
+__host__ __device__ inline int tcolours(int n, int per) { return per && (n & 1) ? 3 : 2; }
+__host__ __device__ inline int tcolour(int x, int n, int per) { return tcolours(n, per) == 3 && x == n - 1 ? 2 : (x & 1); }
 
-template <int NPT>
-__global__ void line_kernel(LV<float> L, int axis, int col) {
-    const int n = L.n[axis], lines = L.n[1 - axis];
+// the transverse axes of lines along `axis`, and the number of line colours
+template <typename R>
+__host__ __device__ inline void line_axes(const LV<R>& L, int D, int axis, int& b, int& c, int& ncol) {
+    b = axis == 0 ? 1 : 0;
+    c = D == 3 ? (axis == 2 ? 1 : 2) : -1;
+    ncol = tcolours(L.n[b], L.per[b]) * (c >= 0 ? tcolours(L.n[c], L.per[c]) : 1);
+}
+
+// does line `idx` (transverse index, b fastest) have colour `col`? returns its first cell
+template <typename R>
+__host__ __device__ inline int line_start(const LV<R>& L, int D, int axis, int idx, int col) {
+    int b, c, ncol;
+    line_axes(L, D, axis, b, c, ncol);
+    const int xb = idx % L.n[b], xc = c >= 0 ? idx / L.n[b] : 0;
+    const int cb = tcolour(xb, L.n[b], L.per[b]);
+    const int cc = c >= 0 ? tcolour(xc, L.n[c], L.per[c]) : 0;
+    if (cb + tcolours(L.n[b], L.per[b]) * cc != col) return -1;
+    int q[3] = {0, 0, 0};
+    q[b] = xb;
+    if (c >= 0) q[c] = xc;
+    return q[0] + L.n[0] * (q[1] + L.n[1] * q[2]);
+}
+
+template <int D, int NPT>
+__global__ void line_kernel(LV<float> L, int axis, int col, int lines) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= line_count(lines, L.per[1 - axis], col)) return;
-    (void)n;
-    line_solve<NPT>(L, axis, line_index(lines, col, idx));
+    if (idx >= lines) return;
+    const int start = line_start(L, D, axis, idx, col);
+    if (start >= 0) line_solve<D, NPT>(L, axis, start);
 }
 
 // ------------------------------------------------------------------ Galerkin coarse operators
 // A_C = R A P (BoxMG's variational coarse operator, Sec. II.B.3) with the V-cycle's own
-// transfers: R sums the 2^D fine children, P is the bilinear prolongation of prolong_at with
-// its homogeneous ghost rules (an out-of-range coarse source is the boundary cell, negated
-// at a Dirichlet face; periodic axes wrap). Every source of P e_C' reached from a child of C
-// lies within one coarse cell of C, so a 9-point fine operator gives a 9-point coarse one
-// (2D). FP64, one thread per coarse cell, entries in stencil-slot order.
-__global__ void galerkin2_kernel(LV<double> F, LV<double> C, double* Ac) {
+// transfers: R sums the 2^D fine children, P is the prolongation of prolong_at (bilinear or
+// operator-induced weights) with its homogeneous ghost rules (an out-of-range coarse source
+// is the boundary cell, negated at a Dirichlet face; periodic axes wrap). Every source of
+// P e_C' reached from a child of C lies within one coarse cell of C, so the coarse operator
+// has the 3^D-point shape (9 in 2D, 27 in 3D). FP64, one thread per coarse cell, entries in
+// stencil-slot order.
+template <int D>
+__global__ void galerkin_kernel(LV<double> F, LV<double> C, double* Ac) {
+    constexpr int NS = D == 2 ? 9 : 27, NCH = 1 << D;
     for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < C.ncell; cc += gridDim.x * blockDim.x) {
-        const int I = cc % C.n[0], J = cc / C.n[0];
-        double acc[9];
+        int Q[3];
+        cell_coords(C, cc, Q);
+        double acc[NS];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) acc[k] = 0.0;
-        for (int ch = 0; ch < 4; ++ch) {
-            const int f0 = 2 * I + (ch & 1), f1 = 2 * J + (ch >> 1);
-            const int f = f0 + F.n[0] * f1;
-            for (int k = 0; k < 9; ++k) {
+        for (int k = 0; k < NS; ++k) acc[k] = 0.0;
+        for (int ch = 0; ch < NCH; ++ch) {
+            int fq[3] = {2 * Q[0] + (ch & 1), 2 * Q[1] + ((ch >> 1) & 1), D == 3 ? 2 * Q[2] + ((ch >> 2) & 1) : 0};
+            const int f = fq[0] + F.n[0] * (fq[1] + F.n[1] * fq[2]);
+            for (int k = 0; k < NS; ++k) {
                 const double a = F.A[k * F.ncell + f];
                 if (a == 0.0) continue;
-                const int g[2] = {f0 + koff(2, k, 0), f1 + koff(2, k, 1)};  // unwrapped
-                int p[2], sdir[2];
-                for (int ax = 0; ax < 2; ++ax) {
-                    p[ax] = g[ax] >> 1;  // floor(g / 2), also for g = -1
+                int g[3], p[3], sdir[3];
+                for (int ax = 0; ax < D; ++ax) {
+                    g[ax] = fq[ax] + koff(D, k, ax);  // unwrapped
+                    p[ax] = g[ax] >> 1;               // floor(g / 2), also for g = -1
                     sdir[ax] = (g[ax] & 1) ? 1 : -1;
                 }
-                double own[2] = {0.75, 0.75};  // the prolongation row of fine cell g
+                double own[3] = {0.75, 0.75, 0.75};  // the prolongation row of fine cell g
                 if (F.pw) {
-                    const int gw0 = (g[0] % F.n[0] + F.n[0]) % F.n[0], gw1 = (g[1] % F.n[1] + F.n[1]) % F.n[1];
-                    own[0] = F.pw[gw0 + F.n[0] * gw1];
-                    own[1] = F.pw[F.ncell + gw0 + F.n[0] * gw1];
+                    int gw[3] = {0, 0, 0};
+                    for (int ax = 0; ax < D; ++ax) gw[ax] = (g[ax] % F.n[ax] + F.n[ax]) % F.n[ax];
+                    const int gi = gw[0] + F.n[0] * (gw[1] + F.n[1] * gw[2]);
+                    for (int ax = 0; ax < D; ++ax) own[ax] = F.pw[ax * F.ncell + gi];
                 }
-                for (int o = 0; o < 4; ++o) {
+                for (int o = 0; o < NCH; ++o) {
                     double w = 1.0;
-                    int off[2];
-                    for (int ax = 0; ax < 2; ++ax) {
+                    int off[3] = {0, 0, 0};
+                    for (int ax = 0; ax < D; ++ax) {
                         const int src = p[ax] + (((o >> ax) & 1) ? sdir[ax] : 0);
                         w *= ((o >> ax) & 1) ? 1.0 - own[ax] : own[ax];
-                        const int base = ax == 0 ? I : J;
-                        off[ax] = src - base;
+                        off[ax] = src - Q[ax];
                         if (!C.per[ax] && (src < 0 || src >= C.n[ax])) {
                             off[ax] = 0;  // the ghost maps onto this boundary cell
                             const int side = src < 0 ? 0 : 1;
@@ -453,14 +487,15 @@ __global__ void galerkin2_kernel(LV<double> F, LV<double> C, double* Ac) {
                         }
                     }
                     int slot = 0;
-                    for (int k2 = 0; k2 < 9; ++k2)
-                        if (koff(2, k2, 0) == off[0] && koff(2, k2, 1) == off[1]) slot = k2;
+                    for (int k2 = 0; k2 < NS; ++k2)
+                        if (koff(D, k2, 0) == off[0] && koff(D, k2, 1) == off[1] && (D == 2 || koff(D, k2, 2) == off[2]))
+                            slot = k2;
                     acc[slot] += w * a;
                 }
             }
         }
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Ac[k * C.ncell + cc] = acc[k];
+        for (int k = 0; k < NS; ++k) Ac[k * C.ncell + cc] = acc[k];
     }
 }
 
@@ -469,40 +504,43 @@ __global__ void galerkin2_kernel(LV<double> F, LV<double> C, double* Ac) {
 // cell-centred 2:1 hierarchy: along each axis a fine cell is interpolated from its own
 // coarse parent C and the parent's neighbour N on the fine cell's side, with the weights of
 // the flux-continuous 1D solution between the two coarse centres: resistances from the fine
-// operator's couplings across faces, collapsed over the transverse direction (the sum of
-// the three entries linking the two columns of cells, as BoxMG collapses its stencils),
+// operator's couplings across faces, collapsed over the transverse directions (the sum of
+// the entries linking the two layers of cells, as BoxMG collapses its stencils),
 //   R1 = 1 / (2 g(f_other -> f))   (C's centre is the face between its two children),
 //   R2 = 1 / g(f -> n) + 1 / (2 g(n -> n_other))   (n, n_other: N's children, n next to f),
-// own-parent weight R2 / (R1 + R2); uniform couplings give bilinear's 3/4. The 2D weights
-// are the product of the axes' weights. Cells whose neighbour parent is outside a
-// non-periodic boundary, or whose couplings are not all positive, keep 3/4 (the ghost
-// rule of prolong_at then applies).
+// own-parent weight R2 / (R1 + R2); uniform couplings give bilinear's 3/4. The weights of a
+// cell are the product of its axes' weights. Cells whose neighbour parent is outside a
+// non-periodic boundary, or whose couplings are not all positive, keep 3/4 (the ghost rule
+// of prolong_at then applies).
+template <int D>
 __global__ void interp_weights_kernel(LV<double> F, double* pw, float* pw32) {
+    constexpr int NS = D == 2 ? 9 : 27;
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < F.ncell; f += gridDim.x * blockDim.x) {
-        const int q[2] = {f % F.n[0], f / F.n[0]};
-        for (int ax = 0; ax < 2; ++ax) {
+        int q[3];
+        cell_coords(F, f, q);
+        for (int ax = 0; ax < D; ++ax) {
             double w = 0.75;
-            const int s = (q[ax] & 1) ? 1 : -1;                // side of the neighbour parent
+            const int s = (q[ax] & 1) ? 1 : -1;  // side of the neighbour parent
             const int nc = F.n[ax] / 2;
-            const int pn = (q[ax] >> 1) + s;                    // neighbour parent (coarse index)
+            const int pn = (q[ax] >> 1) + s;      // neighbour parent (coarse index)
             const bool inside = F.per[ax] || (pn >= 0 && pn < nc);
             if (inside) {
                 // fine cells along the axis: f_other, f, n, n_other at offsets -s, 0, s, 2s
                 auto cell = [&](int d) {
-                    int c[2] = {q[0], q[1]};
+                    int c[3] = {q[0], q[1], q[2]};
                     c[ax] = ((c[ax] + d) % F.n[ax] + F.n[ax]) % F.n[ax];
-                    return c[0] + F.n[0] * c[1];
+                    return c[0] + F.n[0] * (c[1] + F.n[1] * c[2]);
                 };
-                // collapsed coupling from cell c towards +dir (dir = +-1) along ax
+                // collapsed coupling from cell c towards dir (+-1) along ax
                 auto coupling = [&](int c, int dir) {
                     double gsum = 0.0;
-                    for (int k = 1; k < 9; ++k)
-                        if (koff(2, k, ax) == dir) gsum -= F.A[k * F.ncell + c];
+                    for (int k = 1; k < NS; ++k)
+                        if (koff(D, k, ax) == dir) gsum -= F.A[k * F.ncell + c];
                     return gsum;
                 };
-                const double g1 = coupling(cell(-s), s);   // f_other -> f
-                const double g2 = coupling(f, s);           // f -> n
-                const double g3 = coupling(cell(s), s);     // n -> n_other
+                const double g1 = coupling(cell(-s), s);  // f_other -> f
+                const double g2 = coupling(f, s);          // f -> n
+                const double g3 = coupling(cell(s), s);    // n -> n_other
                 if (g1 > 0.0 && g2 > 0.0 && g3 > 0.0) {
                     const double R1 = 0.5 / g1, R2 = 1.0 / g2 + 0.5 / g3;
                     w = R2 / (R1 + R2);
@@ -580,21 +618,22 @@ __global__ void __launch_bounds__(512) coarse_cycle_kernel(LVSet S, int nu1, int
         }
     }
     __syncthreads();
-    // alternating zebra line relaxation (2D): lines along axis 0 then axis 1, each colour
-    // in turn (reverse order after the coarse-grid correction)
+    // alternating zebra line relaxation: lines along each axis in turn, each colour in turn
+    // (reverse order after the coarse-grid correction)
     auto line_sweep = [&](int l, bool reverse) {
-        if constexpr (D == 2) {
-            const LV<float>& L = V[l];
-            for (int st = 0; st < 2; ++st) {
-                const int axis = reverse ? 1 - st : st;
-                const int lines = L.n[1 - axis], per = L.per[1 - axis];
-                const int ncol = line_colours(lines, per);
-                for (int cc = 0; cc < ncol; ++cc) {
-                    const int col = reverse ? ncol - 1 - cc : cc;
-                    const int cnt = line_count(lines, per, col);
-                    for (int idx = tid; idx < cnt; idx += nt) line_solve<NPT>(L, axis, line_index(lines, col, idx));
-                    __syncthreads();
+        const LV<float>& L = V[l];
+        for (int st = 0; st < D; ++st) {
+            const int axis = reverse ? D - 1 - st : st;
+            int b, c, ncol;
+            line_axes(L, D, axis, b, c, ncol);
+            const int lines = L.ncell / L.n[axis];
+            for (int cc = 0; cc < ncol; ++cc) {
+                const int col = reverse ? ncol - 1 - cc : cc;
+                for (int idx = tid; idx < lines; idx += nt) {
+                    const int start = line_start(L, D, axis, idx, col);
+                    if (start >= 0) line_solve<D, NPT>(L, axis, start);
                 }
+                __syncthreads();
             }
         }
     };
@@ -975,7 +1014,7 @@ __device__ __forceinline__ int slot_of(int D, const int* o) {
         const int tab[9] = {5, 3, 6, 1, 0, 2, 7, 4, 8};
         return tab[(o[0] + 1) + 3 * (o[1] + 1)];
     }
-    for (int k = 0; k < 19; ++k)
+    for (int k = 0; k < 27; ++k)
         if (c_off3[k][0] == o[0] && c_off3[k][1] == o[1] && c_off3[k][2] == o[2]) return k;
     return -1;
 }
@@ -985,8 +1024,8 @@ __global__ void assemble_kernel(AsmParams P) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.ncell; c += gridDim.x * blockDim.x) {
         int q[3];
         cell_coords(L, c, q);
-        double a[19];
-        for (int k = 0; k < 19; ++k) a[k] = 0.0;
+        double a[27];
+        for (int k = 0; k < 27; ++k) a[k] = 0.0;
         double rb = 0.0;
         auto add = [&](int* o, double val) {
             // fold ghost targets on non-periodic axes (Dirichlet: -phi_in + 2 phi_b)
@@ -1163,11 +1202,12 @@ LV<R> make_lv(const cpic_run* r, int l, bool fp32) {
     L.ncell = (int)Lv.ncell;
     L.S = Lv.S;
     const bool cross = Lv.cross && !(fp32 && r->pc_face_only);
-    L.used = cross ? Lv.S : 2 * r->D + 1;
+    const int full = r->D == 2 ? 9 : (r->mg_coarse == CPIC_MG_COARSE_GALERKIN ? 27 : 19);
+    L.used = cross ? full : 2 * r->D + 1;
     L.ncol = cross ? (1 << r->D) : 2;
     L.lw = Lv.lw;
     L.pw = nullptr;
-    if (r->D == 2 && r->mg_interp == CPIC_MG_INTERP_OPERATOR && l + 1 < r->nlevels)
+    if (r->mg_interp == CPIC_MG_INTERP_OPERATOR && l + 1 < r->nlevels)
         L.pw = fp32 ? (const R*)(const void*)Lv.pw32 : (const R*)(const void*)Lv.pw;
     if (fp32) {
         L.A = (const R*)Lv.A32;
@@ -1193,7 +1233,7 @@ constexpr size_t CTA_SMEM_MAX = 200 * 1024;  // shared memory of the one-CTA coa
 LVSet make_set(const cpic_run* r) {
     LVSet S;
     S.nl = r->nlevels;
-    S.line = r->D == 2 && r->mg_smoother == CPIC_MG_SMOOTH_LINE ? 1 : 0;
+    S.line = r->mg_smoother == CPIC_MG_SMOOTH_LINE ? 1 : 0;
     for (int l = 0; l < r->nlevels; ++l) S.l[l] = make_lv<float>(r, l, true);
     // the one-CTA part starts at the first level of at most COARSE_CELLS cells from which
     // every coarser level fits the CTA's shared memory (stencil, inverse diagonal, x, b)
@@ -1232,6 +1272,8 @@ int dispatch_shape(const cpic_run* r, F f) {
     const bool cross = r->lev[0].cross != 0;
     if (r->D == 2) return cross ? f(std::integral_constant<int, 2>(), std::integral_constant<int, 9>())
                                 : f(std::integral_constant<int, 2>(), std::integral_constant<int, 5>());
+    if (r->mg_coarse == CPIC_MG_COARSE_GALERKIN)  // 27-point coarse levels
+        return f(std::integral_constant<int, 3>(), std::integral_constant<int, 27>());
     return cross ? f(std::integral_constant<int, 3>(), std::integral_constant<int, 19>())
                  : f(std::integral_constant<int, 3>(), std::integral_constant<int, 7>());
 }
@@ -1243,6 +1285,8 @@ int dispatch_vshape(const cpic_run* r, F f) {
     const bool cross = r->lev[0].cross != 0 && !r->pc_face_only;
     if (r->D == 2) return cross ? f(std::integral_constant<int, 2>(), std::integral_constant<int, 9>())
                                 : f(std::integral_constant<int, 2>(), std::integral_constant<int, 5>());
+    if (r->mg_coarse == CPIC_MG_COARSE_GALERKIN)
+        return f(std::integral_constant<int, 3>(), std::integral_constant<int, 27>());
     return cross ? f(std::integral_constant<int, 3>(), std::integral_constant<int, 19>())
                  : f(std::integral_constant<int, 3>(), std::integral_constant<int, 7>());
 }
@@ -1263,20 +1307,19 @@ int enqueue_vcycle(cpic_run* r, const LVSet& S) {
             CPIC_CHECK_LAUNCH();
             return CPIC_OK;
         };
-        // alternating zebra line relaxation (2D): one thread per line of a colour
+        // alternating zebra line relaxation: one thread per line (those of other colours
+        // return at once)
         auto line_smooth = [&](int l, bool reverse) -> int {
-            if constexpr (D == 2) {
-                const LV<float>& L = S.l[l];
-                for (int stp = 0; stp < 2; ++stp) {
-                    const int axis = reverse ? 1 - stp : stp;
-                    const int lines = L.n[1 - axis], per = L.per[1 - axis];
-                    const int ncol = line_colours(lines, per);
-                    for (int cc = 0; cc < ncol; ++cc) {
-                        const int col = reverse ? ncol - 1 - cc : cc;
-                        const int cnt = line_count(lines, per, col);
-                        line_kernel<NPT><<<(cnt + 63) / 64, 64, 0, st>>>(L, axis, col);
-                        CPIC_CHECK_LAUNCH();
-                    }
+            const LV<float>& L = S.l[l];
+            for (int stp = 0; stp < D; ++stp) {
+                const int axis = reverse ? D - 1 - stp : stp;
+                int b, c, ncol;
+                line_axes(L, D, axis, b, c, ncol);
+                const int lines = L.ncell / L.n[axis];
+                for (int cc = 0; cc < ncol; ++cc) {
+                    const int col = reverse ? ncol - 1 - cc : cc;
+                    line_kernel<D, NPT><<<(lines + 63) / 64, 64, 0, st>>>(L, axis, col, lines);
+                    CPIC_CHECK_LAUNCH();
                 }
             }
             return CPIC_OK;
@@ -1453,18 +1496,25 @@ int mg_setup(cpic_run* r) {
         P.bbc = l == 0 ? r->rhs_bc : nullptr;
         P.cross_flag = flag;
         P.cross_max = cmax;
-        const bool galerkin = r->D == 2 && r->mg_coarse == CPIC_MG_COARSE_GALERKIN;
-        if (l > 0 && r->D == 2 && r->mg_interp == CPIC_MG_INTERP_OPERATOR) {
+        const bool galerkin = r->mg_coarse == CPIC_MG_COARSE_GALERKIN;
+        if (l > 0 && r->mg_interp == CPIC_MG_INTERP_OPERATOR) {
             // the prolongation weights of the level above, from its (finished) operator
             LV<double> F = make_lv<double>(r, l - 1, false);
-            interp_weights_kernel<<<grid_blocks(F.ncell, 256), 256, 0, r->stream>>>(F, r->lev[l - 1].pw,
-                                                                                    r->lev[l - 1].pw32);
+            if (r->D == 2)
+                interp_weights_kernel<2><<<grid_blocks(F.ncell, 256), 256, 0, r->stream>>>(F, r->lev[l - 1].pw,
+                                                                                           r->lev[l - 1].pw32);
+            else
+                interp_weights_kernel<3><<<grid_blocks(F.ncell, 256), 256, 0, r->stream>>>(F, r->lev[l - 1].pw,
+                                                                                           r->lev[l - 1].pw32);
             CPIC_CHECK_LAUNCH();
         }
         if (galerkin && l > 0) {
-            // variational coarse operator from the level above (its full 9-point stencil)
+            // variational coarse operator from the level above (its full stencil)
             LV<double> F = make_lv<double>(r, l - 1, false);
-            galerkin2_kernel<<<grid_blocks(Lv.ncell, 256), 256, 0, r->stream>>>(F, P.L, Lv.A);
+            if (r->D == 2)
+                galerkin_kernel<2><<<grid_blocks(Lv.ncell, 256), 256, 0, r->stream>>>(F, P.L, Lv.A);
+            else
+                galerkin_kernel<3><<<grid_blocks(Lv.ncell, 256), 256, 0, r->stream>>>(F, P.L, Lv.A);
         } else {
             assemble_kernel<<<grid_blocks(Lv.ncell, 256), 256, 0, r->stream>>>(P);
         }
@@ -1480,8 +1530,8 @@ int mg_setup(cpic_run* r) {
         CPIC_CUDA(cudaMemcpyAsync(&hmax, cmax, sizeof(unsigned), cudaMemcpyDeviceToHost, r->stream));
         CPIC_CUDA(cudaStreamSynchronize(r->stream));
         Lv.cross = hflag;
-        // Galerkin coarse operators are 9-point: the V-cycle keeps every entry on every level
-        if (r->D == 2 && r->mg_coarse == CPIC_MG_COARSE_GALERKIN) Lv.cross = 1;
+        // Galerkin coarse operators are 9/27-point: the V-cycle keeps every entry on every level
+        if (r->mg_coarse == CPIC_MG_COARSE_GALERKIN) Lv.cross = 1;
         if (l == 0) {
             float ratio;
             memcpy(&ratio, &hmax, sizeof(ratio));
