@@ -402,8 +402,12 @@ int cpic_autotune(cpic_run* run, int trial_steps, cpic_tuning* out);
  * captured step graphs. */
 int cpic_set_push_tuning(cpic_run* run, int chunk, int tile);
 
-/* Writes the run's configuration, vertex map, injection sources, counters, potential and
- * live-slot particles to a file (synchronous). */
+/* Writes the run's configuration, vertex map, injection sources, counters, potential,
+ * conductor, magnetic field, gyro integrator, multigrid components and live-slot particles
+ * to a file (synchronous). A restored run continues bit for bit; a floating conductor's
+ * charge-free potential is solved again on restore with the saved multigrid components, so
+ * a run that changed its components after cpic_set_floating continues to the solve
+ * tolerance instead. */
 int cpic_checkpoint(cpic_run* run, const char* path);
 /* Creates a run from a checkpoint (arena/stream as in cpic_create); stepping it continues
  * the saved run exactly (particles, charge, potential and diagnostics bit for bit).

@@ -287,8 +287,10 @@ int cpic_restore(const char* path, void* arena, size_t arena_bytes, void* stream
     int mgs = CPIC_MG_SMOOTH_POINT;
     ok = ok && !st && rd(f, r->inj, CPIC_MAX_SPECIES) && rd(f, &ctr, 1) && rd(f, &since, 1) && rd(f, &fface, 1) &&
          rd(f, &fq0, 1) && rd(f, B0, 3) && rd(f, &gyro, 1) && rd(f, &mgc, 1) && rd(f, &mgi, 1) && rd(f, &mgs, 1);
+    // the multigrid components first: the conductor's psi is then solved as the saved run
+    // solved it when its components were set before cpic_set_floating
     if (ok && !st) st = cpic_set_multigrid(r, mgc, mgi, mgs);
-    if (ok && fface >= 0) st = cpic_set_floating(r, fface, fq0);  // psi and its flux sum, recomputed
+    if (ok && !st && fface >= 0) st = cpic_set_floating(r, fface, fq0);  // psi and its flux sum, recomputed
     if (ok && !st) st = cpic_set_magnetic_field(r, B0);
     if (ok && !st) st = cpic_set_gyro_integrator(r, gyro);
     ok = ok && !st && rd(f, phi.data(), phi.size());

@@ -94,8 +94,9 @@ def test_batch_remove_and_continue(cpic):
 
 def test_mixed_batch_equals_alone(cpic):
     """A batch whose 2D cylinder members share the persistent particle launch while a 3D
-    sphere and a magnetised 2D run (which cannot join it) push in their own branches: every
-    member ends bit-identical to the same run stepped alone (full cycles, across sorts)."""
+    sphere, a magnetised 2D run and an axisymmetric floating-sphere run with the cyclotronic
+    push (which cannot join it) push in their own branches: every member ends bit-identical
+    to the same run stepped alone (full cycles, across sorts)."""
     def makers():
         def sphere():
             w = wl.sphere(16, 12, 8, npart_per_species=4000, seed=44, inject=True)
@@ -106,7 +107,15 @@ def test_mixed_batch_equals_alone(cpic):
             w.B0 = (0.0, 0.0, 0.7)
             return cpic.run_from_workload(w, sort_interval=3)
 
-        return [lambda: _make(cpic, SPECS[0]), sphere, magnetized, lambda: _make(cpic, SPECS[2])]
+        def axisym_floating():  # Test C's kind of run: rings, cyclotronic push, floating sphere
+            w = wl.sphere_axisym(24, 24, npart_per_species=20_000, seed=45, dt=0.05)
+            w.B0 = (0.0, 5.0, 0.0)
+            w.gyro = "cyclotronic"
+            run = cpic.run_from_workload(w, sort_interval=2)
+            run.set_floating(0, 0.0)
+            return run
+
+        return [lambda: _make(cpic, SPECS[0]), sphere, magnetized, axisym_floating, lambda: _make(cpic, SPECS[2])]
 
     def state3(run):
         d = run.diag()
@@ -131,7 +140,7 @@ def test_mixed_batch_equals_alone(cpic):
     for r, ref in zip(runs, alone):
         got = state3(r)
         assert np.array_equal(got[0], ref[0])
-        for k in ("step", "n", "absorbed", "injected", "W_E", "W_K", "mg_cycles"):
+        for k in ("step", "n", "absorbed", "injected", "W_E", "W_K", "mg_cycles", "object_potential", "object_charge"):
             assert got[1][k] == ref[1][k], k
         for x, y in zip(got[2] + got[3], ref[2] + ref[3]):
             assert np.array_equal(x, y)

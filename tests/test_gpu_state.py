@@ -32,13 +32,23 @@ def _same(a, b):
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("case", ["cylinder", "sphere3d"])
+@pytest.mark.parametrize("case", ["cylinder", "sphere3d", "axisym_floating_cyclotronic"])
 def test_checkpoint_restore_continues_exactly(cpic, tmp_path, case):
+    """A restored run continues bit for bit: the 2D cylinder, the 3D sphere, and an
+    axisymmetric floating sphere with a field along the axis, the cyclotronic push and the
+    Galerkin / operator-induced / line-relaxation multigrid (every setting the file keeps)."""
     if case == "cylinder":
         w = wl.cylinder(n1=32, n2=64, npart_per_species=20_000, seed=61, inject=True)
-    else:
+    elif case == "sphere3d":
         w = wl.sphere(16, 16, 16, npart_per_species=20_000, seed=62)
+    else:
+        w = wl.sphere_axisym(24, 24, npart_per_species=20_000, seed=63, dt=0.05)
+        w.B0 = (0.0, 5.0, 0.0)
+        w.gyro = "cyclotronic"
     a = cpic.run_from_workload(w, sort_interval=3)
+    if case == "axisym_floating_cyclotronic":
+        a.set_multigrid("galerkin", "line", "operator")
+        a.set_floating(0, 0.0)
     a.initialize()
     a.step(5)
     path = os.path.join(tmp_path, "run.ckpt")
