@@ -223,6 +223,14 @@ int cpic_set_magnetic_field(cpic_run* run, const double* B);
 #define CPIC_GYRO_CYCLOTRONIC 1
 int cpic_set_gyro_integrator(cpic_run* run, int kind);
 
+/* Collection tally (Sec. III.C, Fig. 7: where on the object the particles are collected):
+ * counts[i] = particles of species sp removed at face `face` (0 or 1, the ends of axis 0)
+ * since the run started, by face cell i (2D: the cell index j along axis 1, n = n[1]; 3D:
+ * j + n[1] k, n = n[1] n[2]), taken at the particle's corrector point with the transverse
+ * indices clamped into the face. counts: host or device, n int64 values; CPIC_ERR_INVALID
+ * for a bad species, face or size. Synchronous. */
+int cpic_get_collection(cpic_run* run, int sp, int face, int64_t* counts, int64_t n);
+
 /* Floating conductor (Sec. III.A-B: the object collects the particles that reach it and
  * charges up to a floating potential; Figs. of the wall and sphere potential against time).
  * From now on the Dirichlet face `face` (0 or 1: the ends of axis 0, e.g. the object at

@@ -85,6 +85,10 @@ class OraclePIC:
         self.history = []
         self.injected = [0] * len(self.species)
         self._face_area = {}
+        # collection tally: particles removed at faces 0 / 1 per face cell (transverse indices
+        # of the corrector point, clamped into the face; 3D: j + n1 k)
+        ncol = self.n[1] * (self.n[2] if self.D == 3 else 1)
+        self.collect = np.zeros((len(self.species), 2, ncol), dtype=np.int64)
         self.B0 = getattr(wl, "B0", None)  # uniform magnetic field: Boris kick
         # the cyclotronic integrator (exact gyration) in place of the Boris step
         self.gyro = getattr(wl, "gyro", "boris") == "cyclotronic" and self.B0 is not None and bool(np.any(self.B0))
@@ -219,6 +223,13 @@ class OraclePIC:
                 sp.idx, sp.t, sp.v = idx.astype(np.int64, copy=False), t, v
                 continue
             sp.absorbed += np.bincount(face[~alive], minlength=2 * self.D)[: 2 * self.D]
+            for f in (0, 1):
+                hit = face == f
+                if np.any(hit):
+                    b = np.clip(idx[1][hit], 0, self.n[1] - 1)
+                    if self.D == 3:
+                        b = b + self.n[1] * np.clip(idx[2][hit], 0, self.n[2] - 1)
+                    self.collect[s, f] += np.bincount(b, minlength=self.collect.shape[2])
             sp.idx = np.compress(alive, idx, axis=1).astype(np.int64, copy=False)
             sp.t, sp.v = np.compress(alive, t, axis=1), np.compress(alive, v, axis=1)
         for (s, face, dens, vth, seed) in self.injection:

@@ -294,7 +294,7 @@ void replay_push(int D, const int* n, const int* pbc, long np, int* idx, float* 
         }
         face[p] = fc;
         for (int a = 0; a < D; ++a) {
-            idx[a * np + p] = fc < 0 ? cn[a] : -1;
+            idx[a * np + p] = cn[a]; /* removed particles keep their corrector cell */
             t[a * np + p] = tn[a];
         }
         for (int al = 0; al < 3; ++al) v[al * np + p] = vv[al];

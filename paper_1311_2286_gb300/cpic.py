@@ -153,6 +153,7 @@ _SIGS = {
     "cpic_load_particles": ([P, ctypes.c_int, ctypes.c_int64, P, P, P], ctypes.c_int),
     "cpic_get_particles": ([P, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), P, P, P], ctypes.c_int),
     "cpic_set_floating": ([P, ctypes.c_int, ctypes.c_double], ctypes.c_int),
+    "cpic_get_collection": ([P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int64], ctypes.c_int),
     "cpic_set_magnetic_field": ([P, P], ctypes.c_int),
     "cpic_set_gyro_integrator": ([P, ctypes.c_int], ctypes.c_int),
     "cpic_set_multigrid": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
@@ -418,6 +419,14 @@ class Run:
         """cpic_set_gyro_integrator: "boris" or "cyclotronic" (exact gyration in B0)."""
         k = {"boris": GYRO_BORIS, "cyclotronic": GYRO_CYCLOTRONIC}[kind] if isinstance(kind, str) else int(kind)
         check(load().cpic_set_gyro_integrator(self.h, k))
+
+    def collection(self, sp, face=0):
+        """cpic_get_collection: particles of species sp removed at face 0/1 so far, per face
+        cell (2D: along axis 1; 3D: j + n1 k)."""
+        n = self.cfg.n[1] * (self.cfg.n[2] if self.D == 3 else 1)
+        out = np.zeros(n, dtype=np.int64)
+        check(load().cpic_get_collection(self.h, sp, face, _ptr(out), n))
+        return out
 
     def set_floating(self, face=0, charge0=0.0):
         """cpic_set_floating: the face's conductor floats (Gauss's-law potential from its

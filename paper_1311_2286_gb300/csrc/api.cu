@@ -197,6 +197,8 @@ void plan(cpic_run* r, Planner& P) {
                         : (c.axisymmetric ? P.take<double>((size_t)2 * r->n[1]) : nullptr);
     r->R32 = c.axisymmetric ? P.take<float>((size_t)r->nvert) : nullptr;
     r->charge = P.take<unsigned long long>((size_t)c.n_species * r->ncell);
+    r->ncollect = D == 2 ? r->n[1] : r->n[1] * r->n[2];
+    r->collect = P.take<unsigned long long>((size_t)c.n_species * 2 * r->ncollect);
     r->charge_h = P.take<unsigned long long>((size_t)c.n_species * r->ncell_h);
     long long total = 0;
     for (int s = 0; s < c.n_species; ++s) {
@@ -868,6 +870,8 @@ int cpic_create(const cpic_config* cfg, void* arena, size_t arena_bytes, void* s
     if (e == cudaSuccess) e = cudaMemsetAsync(r->pb.cell[1], 0xff, sizeof(int) * r->pb.total, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->ticket, 0, sizeof(unsigned) * 4, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->kry, 0, sizeof(KrylovState), r->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(r->collect, 0, sizeof(unsigned long long) * cfg->n_species * 2 * r->ncollect, r->stream);
     if (e != cudaSuccess) {
         st = cuda_fail(e, "initial memset", __FILE__, __LINE__);
         if (r->own_memory) cudaFree(r->arena);
@@ -1057,6 +1061,19 @@ int cpic_set_gyro_integrator(cpic_run* r, int kind) {
     }
     r->gyro_kind = kind;
     invalidate_graphs(r);
+    return CPIC_OK;
+}
+
+int cpic_get_collection(cpic_run* r, int sp, int face, int64_t* counts, int64_t n) {
+    CHECK_RUN(r);
+    if (sp < 0 || sp >= r->cfg.n_species || (face != 0 && face != 1) || !counts || n != r->ncollect) {
+        set_error("get_collection: bad species, face, NULL array or size %lld (the face has %d cells)", (long long)n,
+                  r->ncollect);
+        return CPIC_ERR_INVALID;
+    }
+    CPIC_CUDA(cudaMemcpyAsync(counts, r->collect + ((size_t)sp * 2 + face) * r->ncollect,
+                              sizeof(unsigned long long) * r->ncollect, cudaMemcpyDefault, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
     return CPIC_OK;
 }
 

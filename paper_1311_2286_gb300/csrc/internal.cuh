@@ -106,6 +106,8 @@ struct PushParams {
     float bh[CPIC_MAX_SPECIES];    // Boris constants per species: half kick (float)(dt q/m / 2),
     float bt[CPIC_MAX_SPECIES][3]; // t = (float)(dt q/m B0 / 2),
     float bs[CPIC_MAX_SPECIES][3]; // s = (float)(2 t / (1 + |t|^2)) (t, s from FP64 values)
+    unsigned long long* collect;   // absorbed particles per [species][face 0/1][face cell]
+    int ncollect;                  // face cells of a face normal to axis 0
     int gyro;                      // cyclotronic integrator (exact gyration) instead of Boris
     float gb[3];                   // its unit field direction b (velocity components' basis)
     float gy[CPIC_MAX_SPECIES][4]; // per species cos th, sin th, sin th / th, (1 - cos th) / th
@@ -202,6 +204,8 @@ struct cpic_run {
     int mg_coarse;               // CPIC_MG_COARSE_*: rediscretised or Galerkin coarse operators
     int mg_smoother;             // CPIC_MG_SMOOTH_*: point or alternating zebra line Gauss-Seidel
     int mg_interp;               // CPIC_MG_INTERP_*: bilinear or operator-induced prolongation
+    unsigned long long* collect; // collection tally [species][face 0/1][face cell] (Fig. 7)
+    int ncollect;                // face cells of a face normal to axis 0: n1 (2D), n1 n2 (3D)
     int floating_face;           // face whose conductor floats (cpic_set_floating), -1: none
     double float_q0;             // its charge before any particle was collected
     double* psi;                 // potential of the unit-potential conductor in charge-free space

@@ -137,6 +137,17 @@ __device__ __forceinline__ float gather_scalar2(const PushParams& p, int v0, con
     return __fmaf_rn(w3, d, __fmaf_rn(w2, c, __fmaf_rn(w1, b, __fmul_rn(w0, a))));
 }
 
+// Collection tally (which part of the object collects the particles, Fig. 7): a particle
+// removed at a face normal to axis 0 counts in that face's cell at its corrector point,
+// the transverse indices clamped into the face (a particle that left through an edge).
+template <int D>
+__device__ __forceinline__ void collect_face(const PushParams& p, int s, int face, const int* cn) {
+    if (face != 0 && face != 1) return;
+    int idx = min(max(cn[1], 0), p.n[1] - 1);
+    if (D == 3) idx += p.n[1] * min(max(cn[2], 0), p.n[2] - 1);
+    atomicAdd(p.collect + ((long long)(2 * s + face)) * p.ncollect + idx, 1ull);
+}
+
 template <>
 struct Tab<3> {
     static __device__ __forceinline__ void gather(const PushParams& p, int v0, const float* t,

@@ -380,6 +380,7 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) particle_kernel(PushParam
             for (int al = 0; al < 3; ++al) vq[al][slot] = v[al];
         }
         tally.add(face);
+        if (active && face >= 0) collect_face<D>(p, s, face, cn);
         deposit_warp<D>(p, s, alive, cn, tn);
     }
     if (MODE == 0 && s_acc >= 0) tally.flush(p.ctr, s_acc);
@@ -449,6 +450,8 @@ PushParams make_push_params(cpic_run* r) {
     p.dt = (float)r->cfg.dt;
     p.K = r->K32;
     p.G = r->G32;
+    p.collect = r->collect;
+    p.ncollect = r->ncollect;
     p.R = r->D == 2 ? r->R32 : nullptr;
     p.pb = r->pb;
     p.charge = r->charge_h;

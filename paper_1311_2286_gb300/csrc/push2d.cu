@@ -368,6 +368,7 @@ __device__ __forceinline__ void push2d_run(const PushParams& p, int bid, int nb,
                     g2 += active && face == 2;
                     g3 += active && face == 3;
                     gbad += active && face == 6;
+                    if (active) collect_face<2>(p, s, face, cn);
                 }
                 // spec D: v_old . v_new as an FP32 fma chain, then round(x 2^24) to int64
                 const float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));

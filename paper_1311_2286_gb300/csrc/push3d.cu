@@ -509,7 +509,10 @@ __global__ void __launch_bounds__(P3_THREADS, 3) push3d_kernel(PushParams p) {
                 mover3<K0, K1, K2>(p, dtqm, cw, t, v, cn, tn, face, ke32);
                 ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
                 const bool alive = active && face < 0;
-                if (active && face >= 0) atomicAdd(&sh_gone[face], 1);  // rare: kept in shared memory
+                if (active && face >= 0) {  // rare
+                    atomicAdd(&sh_gone[face], 1);
+                    collect_face<3>(p, s, face, cn);
+                }
                 store_state3(active, cellp + slot, alive ? (cn[0] | (cn[1] << 10) | (cn[2] << 20)) : -1, tq0 + slot,
                              tq0 + T + slot, tq0 + 2 * T + slot, tn, vq0 + slot, vq0 + T + slot, vq0 + 2 * T + slot, v);
                 // a6: deposit
@@ -690,7 +693,10 @@ __global__ void __launch_bounds__(PD_THREADS, 4) push3d_direct_kernel(PushParams
             mover3<K0, K1, K2>(p, dtqm, cw, t, v, cn, tn, face, ke32);
             ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
             const bool alive = active && face < 0;
-            if (active && face >= 0) atomicAdd(&sh_gone[face], 1);
+            if (active && face >= 0) {  // rare
+                atomicAdd(&sh_gone[face], 1);
+                collect_face<3>(p, s, face, cn);
+            }
             store_state3(active, cellp + slot, alive ? (cn[0] | (cn[1] << 10) | (cn[2] << 20)) : -1, tq0 + slot,
                          tq0 + T + slot, tq0 + 2 * T + slot, tn, vq0 + slot, vq0 + T + slot, vq0 + 2 * T + slot, v);
             deposit_runs3(p, s, alive, cn, tn, wq);  // a6

@@ -6,7 +6,8 @@
 //   "CPICCKP1", u32 version, cpic_config, u64 nvert, f64 vertex map [nvert][D],
 //   InjectSpec[CPIC_MAX_SPECIES], DevCounters, i32 steps_since_sort, i32 floating face,
 //   f64 its initial charge, f64 B0[3], i32 gyro integrator, i32 multigrid coarse operator,
-//   i32 interpolation, i32 smoother, f64 phi [ncell],
+//   i32 interpolation, i32 smoother, u64 collection tally [species][2][face cells],
+//   f64 phi [ncell],
 //   per species: i64 count, i32 cell [count], f32 t [D][count], f32 v [3][count].
 // A restored run is created from the stored configuration and vertex map (the same metric
 // and multigrid hierarchy bit for bit), then takes the stored particles, counters, potential
@@ -22,10 +23,12 @@ namespace cpic {
 namespace {
 
 constexpr char kMagic[8] = {'C', 'P', 'I', 'C', 'C', 'K', 'P', '1'};
-constexpr unsigned kVersion = 4;  // 2: floating conductor, 3: magnetic field, 4: gyro integrator
+constexpr unsigned kVersion = 4;  // 2: floating conductor, 3: magnetic field, 4: gyro integrator,
+                                  // multigrid components and the collection tally
 
 size_t snapshot_bytes(const cpic_run* r) {
-    size_t b = sizeof(DevCounters) + sizeof(double) * (size_t)r->ncell;
+    size_t b = sizeof(DevCounters) + sizeof(double) * (size_t)r->ncell +
+               sizeof(unsigned long long) * (size_t)r->cfg.n_species * 2 * r->ncollect;
     for (int s = 0; s < r->cfg.n_species; ++s) b += (size_t)r->pb.capacity[s] * (4 + 4 * r->D + 12);
     return b + 256;
 }
@@ -44,6 +47,7 @@ int snapshot_copy(cpic_run* r, char* buf, bool save, int buffer) {
     };
     int st = cp(r->ctr, sizeof(DevCounters));
     if (!st) st = cp(r->lev[0].x, sizeof(double) * (size_t)r->ncell);
+    if (!st) st = cp(r->collect, sizeof(unsigned long long) * (size_t)r->cfg.n_species * 2 * r->ncollect);
     for (int s = 0; !st && s < r->cfg.n_species; ++s) {
         const long long b0 = r->pb.base[s], cap = r->pb.capacity[s];
         st = cp(r->pb.cell[buffer] + b0, sizeof(int) * cap);
@@ -198,6 +202,9 @@ int cpic_checkpoint(cpic_run* r, const char* path) {
     }
     const int D = r->D;
     std::vector<double> X((size_t)r->nvert * D), phi(r->ncell);
+    std::vector<unsigned long long> coll((size_t)r->cfg.n_species * 2 * r->ncollect);
+    CPIC_CUDA(cudaMemcpyAsync(coll.data(), r->collect, sizeof(unsigned long long) * coll.size(), cudaMemcpyDeviceToHost,
+                              r->stream));
     DevCounters ctr;
     CPIC_CUDA(cudaMemcpyAsync(X.data(), r->lev[0].X, sizeof(double) * X.size(), cudaMemcpyDeviceToHost, r->stream));
     CPIC_CUDA(cudaMemcpyAsync(phi.data(), r->lev[0].x, sizeof(double) * phi.size(), cudaMemcpyDeviceToHost, r->stream));
@@ -214,7 +221,7 @@ int cpic_checkpoint(cpic_run* r, const char* path) {
               wr(f, X.data(), X.size()) && wr(f, r->inj, CPIC_MAX_SPECIES) && wr(f, &ctr, 1) && wr(f, &since, 1) &&
               wr(f, &r->floating_face, 1) && wr(f, &r->float_q0, 1) && wr(f, r->B0, 3) && wr(f, &r->gyro_kind, 1) &&
               wr(f, &r->mg_coarse, 1) && wr(f, &r->mg_interp, 1) && wr(f, &r->mg_smoother, 1) &&
-              wr(f, phi.data(), phi.size());
+              wr(f, coll.data(), coll.size()) && wr(f, phi.data(), phi.size());
     const int b = ctr.cur;
     const long long T = r->pb.total;
     for (int s = 0; ok && s < r->cfg.n_species; ++s) {
@@ -293,7 +300,8 @@ int cpic_restore(const char* path, void* arena, size_t arena_bytes, void* stream
     if (ok && !st && fface >= 0) st = cpic_set_floating(r, fface, fq0);  // psi and its flux sum, recomputed
     if (ok && !st) st = cpic_set_magnetic_field(r, B0);
     if (ok && !st) st = cpic_set_gyro_integrator(r, gyro);
-    ok = ok && !st && rd(f, phi.data(), phi.size());
+    std::vector<unsigned long long> coll((size_t)cfg.n_species * 2 * r->ncollect);
+    ok = ok && !st && rd(f, coll.data(), coll.size()) && rd(f, phi.data(), phi.size());
     // particles into buffer 0, counters with cur = 0
     const long long T = r->pb.total;
     for (int s = 0; ok && s < cfg.n_species; ++s) {
@@ -318,7 +326,9 @@ int cpic_restore(const char* path, void* arena, size_t arena_bytes, void* stream
         ctr.cur = 0;
         for (int s = 0; s < CPIC_MAX_SPECIES; ++s) ctr.inject_ticket[s] = 0;
         ok = cudaMemcpy(r->ctr, &ctr, sizeof(ctr), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(r->lev[0].x, phi.data(), sizeof(double) * phi.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+             cudaMemcpy(r->lev[0].x, phi.data(), sizeof(double) * phi.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(r->collect, coll.data(), sizeof(unsigned long long) * coll.size(), cudaMemcpyHostToDevice) ==
+                 cudaSuccess;
         r->cur_host = 0;
         r->steps_since_sort = since;
     }

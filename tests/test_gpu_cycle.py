@@ -216,6 +216,11 @@ def test_sphere_axisym_cycle_matches_oracle(cpic, record_property, Bz):
     report = []
     _current_check(dev_abs, ora_abs, w, 1, SPH_STEPS, report)
     record_property("currents", report)
+    # collection tally (Fig. 7's diagnostic): per sphere and outer-face cell
+    for s in range(len(w.species)):
+        for f in (0, 1):
+            dev, ora = run.collection(s, f), pic.collect[s, f]
+            assert np.abs(dev - ora).sum() <= max(2, 0.005 * ora.sum()), (s, f, dev, ora)
     print("axisymmetric sphere: V(end) device %.6f oracle %.6f, mean %.6f / %.6f, max |dV| %.2e; W_E mean %.6e / %.6e"
           % (v[-1, 0], v[-1, 1], v[:, 0].mean(), v[:, 1].mean(), np.max(np.abs(v[:, 0] - v[:, 1])), we.mean(),
              we_ora.mean()))
@@ -224,26 +229,46 @@ def test_sphere_axisym_cycle_matches_oracle(cpic, record_property, Bz):
     run.close()
 
 
+def _polar_fraction(counts):
+    """Fraction of the sphere's collection with |cos delta| > 0.8, cos delta = cos[pi (1 -
+    eta)] at the face cell's centre (Fig. 7's axis); 0.2 for isotropic collection (the band
+    |cos delta| > 0.8 holds a fifth of the sphere's area)."""
+    n2 = counts.size
+    cd = np.cos(np.pi * (1.0 - (np.arange(n2) + 0.5) / n2))
+    tot = counts.sum()
+    return float(counts[np.abs(cd) > 0.8].sum()) / max(tot, 1), int(tot)
+
+
 def test_sphere_floating_potential_test_b(cpic):
     """Test B at the paper's size (Sec. III.B: 128 x 128, r1 = 1, r2 = 10, dt 0.1, plasma of
     density 1 and T_i = T_e, m_i/m_e = 1836, the sphere floating from zero charge, flux
     injection at r2), on the device alone with about 230 rings per cell per species: the
     sphere potential averaged over the last quarter of 4000 steps lies within 8% of the
     OML value -2.50 T_e that the paper's -2.54 is compared with (OML is approximate at
-    r1 = lambda_D; the paper's own agreement is 1.6%). Physics, not parity: the parity
-    of this path against the oracle is the test above."""
+    r1 = lambda_D; the paper's own agreement is 1.6%), and both species are collected
+    isotropically over the last tenth (Fig. 7: a fifth of the collection in |cos delta| >
+    0.8). Physics, not parity: the parity of this path against the oracle is the test
+    above."""
     n = 128
     w = wl.sphere_axisym(n, n, npart_per_species=230 * n * n, seed=8, dt=0.1, capacity_factor=1.6)
     run = cpic.run_from_workload(w, sort_interval=8)
     run.set_floating(0, 0.0)
     run.initialize()
     steps, vs = 4000, []
-    for _ in range(steps // 50):
+    for k in range(steps // 50):
         run.step(50)
         vs.append(run.diag()["object_potential"])
+        if k == (steps * 9 // 10) // 50 - 1:
+            c0 = [run.collection(s, 0) for s in range(2)]
     tail = float(np.mean(vs[-len(vs) // 4:]))
     print("Test B: sphere potential (last quarter of %d steps) %.4f T_e (OML -2.50, paper -2.54)" % (steps, tail))
     assert abs(tail / -2.50 - 1.0) <= 0.08, tail
+    # Fig. 7, unmagnetised: both species are collected isotropically over the last tenth
+    fr = [_polar_fraction(run.collection(s, 0) - c0[s]) for s in range(2)]
+    print("Test B collection over the last tenth: |cos delta| > 0.8 fraction electrons %.3f (%d), ions %.3f (%d)"
+          % (fr[0][0], fr[0][1], fr[1][0], fr[1][1]))
+    for f, n in fr:
+        assert abs(f - 0.2) <= 0.05 and n > 1000, fr
     run.close()
 
 
@@ -366,7 +391,10 @@ def test_sphere_floating_potential_test_c(cpic, Bz, expected):
     (averaged over the last sixth), and it finds them within about 10% of another code's
     -2.37 and -2.21; the sphere potential averaged over the last sixth here lies within
     10% of the paper's values (and the potential is less negative in the stronger field).
-    Physics, not parity: the parity of this path is the cyclotronic push and cycle tests."""
+    The collection over the last tenth (Fig. 7) is isotropic for the ions in both fields
+    and for the electrons in the weak one, and peaks at the poles for the electrons in the
+    moderate one. Physics, not parity: the parity of this path is the cyclotronic push and
+    cycle tests."""
     n = 128
     w = wl.sphere_axisym(n, n, npart_per_species=230 * n * n, seed=9, dt=0.05, capacity_factor=1.6)
     w.B0 = (0.0, Bz, 0.0)
@@ -375,10 +403,23 @@ def test_sphere_floating_potential_test_c(cpic, Bz, expected):
     run.set_floating(0, 0.0)
     run.initialize()
     steps, vs = 8000, []
-    for _ in range(steps // 50):
+    for k in range(steps // 50):
         run.step(50)
         vs.append(run.diag()["object_potential"])
+        if k == (steps * 9 // 10) // 50 - 1:
+            c0 = [run.collection(s, 0) for s in range(2)]
     tail = float(np.mean(vs[-len(vs) // 6:]))
+    fr = [_polar_fraction(run.collection(s, 0) - c0[s]) for s in range(2)]
+    print("Test C (B_z0 %.1f) collection over the last tenth: |cos delta| > 0.8 fraction electrons %.3f (%d), "
+          "ions %.3f (%d)" % (Bz, fr[0][0], fr[0][1], fr[1][0], fr[1][1]))
+    # Fig. 7: the ions (gyroradius above the sphere's radius) are collected isotropically in
+    # both fields, the electrons too in the weak field, while in the moderate field (electron
+    # gyroradius 0.05 r1) they reach the sphere mostly along the field, near the poles
+    assert abs(fr[1][0] - 0.2) <= 0.05, fr
+    if Bz < 5.0:
+        assert abs(fr[0][0] - 0.2) <= 0.05, fr
+    else:
+        assert fr[0][0] >= 0.27, fr
     print("Test C (B_z0 %.1f): sphere potential (last sixth of %d steps) %.4f T_e (paper %.2f)"
           % (Bz, steps, tail, expected))
     assert abs(tail / expected - 1.0) <= 0.10, tail

@@ -95,7 +95,7 @@ def test_vertex_field_bit_exact(cpic, case):
     run.close()
 
 
-def _push_case(cpic, w, phi, sort_first=False, tile=1):
+def _push_case(cpic, w, phi, sort_first=False, tile=1, with_collect=False):
     g, per = _geom(w)
     run = cpic.run_from_workload(w)
     run.set_push_tuning(0, tile)
@@ -108,9 +108,12 @@ def _push_case(cpic, w, phi, sort_first=False, tile=1):
     post = [run.particles(s) for s in range(len(w.species))]
     charge = [run.charge(s) for s in range(len(w.species))]
     d = run.diag()
+    collect = [[run.collection(s, f) for f in (0, 1)] for s in range(len(w.species))]
     run.close()
     G32 = gradient.vertex_gradient(phi, w.field_bc, w.field_bc_value).astype(np.float32)
     k32 = g.k.astype(np.float32)
+    if with_collect:
+        return g, per, pre, post, charge, d, k32, G32, collect
     return g, per, pre, post, charge, d, k32, G32
 
 
@@ -128,7 +131,7 @@ def test_push_bit_exact_vs_replay(cpic, case, sort_first, tile):
     phi = wl.random_field(rng, tuple(reversed(w.n)), 0.5)
     if case in DIRICHLET_AXIS0:
         phi = phi + np.linspace(-5, 0, w.n[0])
-    g, per, pre, post, charge, d, k32, G32 = _push_case(cpic, w, phi, sort_first, tile)
+    g, per, pre, post, charge, d, k32, G32, collect = _push_case(cpic, w, phi, sort_first, tile, with_collect=True)
     ke_total = 0.0
     D = w.dim
     for s, sp in enumerate(w.species):
@@ -148,6 +151,14 @@ def test_push_bit_exact_vs_replay(cpic, case, sort_first, tile):
             assert d["absorbed"][s][f] == int(np.sum(face == f)), (s, f)
         Cref = odep.deposit_fixed(i32[:, alive].astype(np.int64), t32[:, alive], w.n, per)
         assert np.array_equal(charge[s], Cref)
+        # collection tally: the removed particles of faces 0 / 1 by their corrector cell
+        for f in (0, 1):
+            hit = face == f
+            b = np.clip(i32[1][hit], 0, w.n[1] - 1)
+            if D == 3:
+                b = b + w.n[1] * np.clip(i32[2][hit], 0, w.n[2] - 1)
+            ncol = w.n[1] * (w.n[2] if D == 3 else 1)
+            assert np.array_equal(collect[s][f], np.bincount(b, minlength=ncol)), (s, f)
         ke_total += 0.5 * sp.m * sp.w * math.ldexp(float(int(kefp.sum())), -24)
         assert d["n"][s] == int(alive.sum())
     assert d["W_K"] == pytest.approx(ke_total, rel=1e-15, abs=1e-300)

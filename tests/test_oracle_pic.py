@@ -285,3 +285,31 @@ def test_upper_hybrid_frequency_with_uniform_b():
     amps = np.array(amps)
     wfreq = _frequency(amps - amps.mean(), 0.1)
     assert abs(wfreq / math.sqrt(2.0) - 1.0) < 0.02, wfreq
+
+
+def test_collection_tally_bins_by_the_transverse_cell():
+    """The collection tally (Fig. 7's diagnostic): particles placed in rows j of the first
+    column, moving into the object face with no field, are removed there in one step and
+    counted in exactly their rows; the tally sums to the absorbed count; particles moving
+    the other way are not counted."""
+    w = wl.cylinder(n1=16, n2=32, npart_per_species=1, seed=3, inject=False)
+    rows = np.array([0, 3, 3, 17, 31, 31, 31], dtype=np.int64)
+    m = rows.size
+    cell = (0 | (rows << 16)).astype(np.int32)
+    t = np.stack([np.full(m, 0.02), np.full(m, 0.5)]).astype(np.float32)
+    theta = 2.0 * np.pi * (rows + 0.5) / 32  # the annulus: theta = 2 pi eta
+    v = np.zeros((3, m), np.float32)
+    v[0], v[1] = -2.0 * np.cos(theta), -2.0 * np.sin(theta)  # radially inward: one step crosses r0
+    th1 = 2.0 * np.pi * 5.5 / 32  # a particle of the other species moving outward, mid-domain
+    keep = wl.ParticleSet(np.array([8 | (5 << 16)], np.int32), np.full((2, 1), 0.5, np.float32),
+                          np.array([[2.0 * np.cos(th1)], [2.0 * np.sin(th1)], [0.0]], np.float32))
+    w.particles = [wl.ParticleSet(cell, t, v), keep]
+    w.field_bc_value = [0.0] * 4  # no bias, and light macro-particles: a negligible field
+    for sp in w.species:
+        sp.w = 1e-9
+    pic = OraclePIC(w, "fp64")
+    pic.solve()
+    pic.step(solve=False)
+    np.testing.assert_array_equal(pic.collect[0, 0], np.bincount(rows, minlength=32))
+    assert pic.collect[0, 0].sum() == pic.species[0].absorbed[0] == m
+    assert pic.collect[1].sum() == 0 and pic.collect[0, 1].sum() == 0
