@@ -57,7 +57,6 @@ SRC3 = ["paper_1311_2286_gb300/csrc/push3d.cu", "paper_1311_2286_gb300/csrc/part
 SRC2 = ["paper_1311_2286_gb300/csrc/push2d.cu", "paper_1311_2286_gb300/csrc/particles.cuh"]
 PROFILE3 = "profiles/push3d_sphere_128cubed.md"
 PROFILE2 = "profiles/push2d_cylinder_512x1024_64M.md"
-PROFILE2_SMALL = "profiles/push2d_cylinder_128x256_4M.md"
 
 
 def sources_hash(files):
@@ -304,7 +303,8 @@ def cylinder_measurement(cpic, n1, n2, npart, steps, warmup, full_steps, stream,
     ph, pp = profiled_phases(run, min(steps, 20), lambda: run.step_particles(1), flush)
     push_ms = ph["push"][0] / max(ph["push"][1], 1)
     peak, kind = measured_peak()
-    roof = roofline(push_ms, pp, B2, peak, kind, profiled_traffic(profile, SRC2, pp),
+    # traffic only from a profile of this size class (the 128x256 state sits in L2)
+    roof = roofline(push_ms, pp, B2, peak, kind, profiled_traffic(profile, SRC2, pp) if profile else None,
                     "push2d_kernel<false,true> (fused gather/push/boundary/deposit, 2D)")
     out = {"value": ps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps, "particles": int(pp),
            "cells": n1 * n2, "setup_s": setup_s, "tuning": tuning, "roofline": roof,
@@ -755,7 +755,7 @@ def main():
     cyl = cyl64 = batched = served = None
     if args.cyl_particles > 0:
         cyl = cylinder_measurement(cpic, 128, 256, args.cyl_particles, max(args.steps, 100), args.warmup,
-                                   args.full_steps * 4, stream, flush, device_load=False, profile=PROFILE2_SMALL)
+                                   args.full_steps * 4, stream, flush, device_load=False, profile=None)
     if args.cyl64_particles > 0:
         cyl64 = cylinder_measurement(cpic, 512, 1024, args.cyl64_particles, args.steps, args.warmup, args.full_steps,
                                      stream, flush, device_load=True, profile=PROFILE2)
