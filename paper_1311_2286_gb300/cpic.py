@@ -506,15 +506,12 @@ class Run:
         return out.reshape(tuple(reversed(self.n)))
 
     def vertex_tables(self):
-        kw = 4 if self.D == 2 else 12
-        gw = 2 if self.D == 2 else 4
-        k = np.empty(self.nvert * kw, np.float32)
-        g = np.empty(self.nvert * gw, np.float32)
+        """cpic_get_vertex_tables: the mover's FP32 k and G, numpy vertex layout."""
+        k = np.empty(self.nvert * self.D * self.D, np.float32)
+        g = np.empty(self.nvert * self.D, np.float32)
         check(load().cpic_get_vertex_tables(self.h, _ptr(k), _ptr(g)))
         vshape = tuple(reversed([x + 1 for x in self.n]))
-        k = k.reshape(vshape + (kw,))[..., : self.D * self.D].reshape(vshape + (self.D, self.D))
-        g = g.reshape(vshape + (gw,))[..., : self.D]
-        return k, g
+        return k.reshape(vshape + (self.D, self.D)), g.reshape(vshape + (self.D,))
 
     def geometry(self):
         k = np.empty(self.nvert * self.D * self.D, np.float64)

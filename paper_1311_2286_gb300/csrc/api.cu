@@ -1302,11 +1302,34 @@ int cpic_get_charge(cpic_run* r, int sp, int64_t* counts) {
 
 int cpic_get_vertex_tables(cpic_run* r, float* k, float* g) {
     CHECK_RUN(r);
-    if (k)
-        CPIC_CUDA(cudaMemcpyAsync(k, r->K32, sizeof(float) * r->nvert * (r->D == 2 ? 4 : 12), cudaMemcpyDefault, r->stream));
-    if (g)
-        CPIC_CUDA(cudaMemcpyAsync(g, r->G32, sizeof(float) * r->nvert * (r->D == 2 ? 2 : 4), cudaMemcpyDefault, r->stream));
+    const int D = r->D;
+    const long long nv = r->nvert;
+    // the device tables are padded records (2D: k one float4, G one float2 per vertex; 3D: k
+    // and G in three float4 per vertex, G also as one float4); the output is unpadded
+    std::vector<float> kraw, graw;
+    if (k) {
+        kraw.resize((size_t)nv * (D == 2 ? 4 : 12));
+        CPIC_CUDA(cudaMemcpyAsync(kraw.data(), r->K32, sizeof(float) * kraw.size(), cudaMemcpyDeviceToHost, r->stream));
+    }
+    if (g) {
+        graw.resize((size_t)nv * (D == 2 ? 2 : 4));
+        CPIC_CUDA(cudaMemcpyAsync(graw.data(), r->G32, sizeof(float) * graw.size(), cudaMemcpyDeviceToHost, r->stream));
+    }
     CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    if (k) {
+        std::vector<float> out((size_t)nv * D * D);
+        for (long long v = 0; v < nv; ++v)
+            for (int q = 0; q < D * D; ++q)
+                out[(size_t)v * D * D + q] = kraw[(size_t)v * (D == 2 ? 4 : 12) + q];
+        CPIC_CUDA(cudaMemcpy(k, out.data(), sizeof(float) * out.size(), cudaMemcpyDefault));
+    }
+    if (g) {
+        std::vector<float> out((size_t)nv * D);
+        const int gw = D == 2 ? 2 : 4;
+        for (long long v = 0; v < nv; ++v)
+            for (int a = 0; a < D; ++a) out[(size_t)v * D + a] = graw[(size_t)v * gw + a];
+        CPIC_CUDA(cudaMemcpy(g, out.data(), sizeof(float) * out.size(), cudaMemcpyDefault));
+    }
     return CPIC_OK;
 }
 
