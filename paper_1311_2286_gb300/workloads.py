@@ -285,6 +285,36 @@ def langmuir_map2(n1=32, n2=32, eps=0.05, ppc=64, vth=0.05, amp=0.01, dt=0.1, se
     )
 
 
+def two_stream_map2(n1=64, n2=64, eps=0.05, ppc=256, v0=0.0975, vth=0.002, amp=1e-3, dt=0.05, seed=0):
+    """Two-stream configuration on the doubly periodic map2 square: two equal cold electron
+    beams (each half of the unit density) drifting at +v0 and -v0 along x through immobile
+    neutralising ions, with a small cos(2 pi x) density perturbation as the seed. The beams
+    are loaded as pairs at the same position (equal and opposite drift), so the seed is
+    the only initial current-free perturbation."""
+    rng = np.random.default_rng(seed)
+    half = n1 * n2 * ppc // 2
+    ps = load_map2(rng, n1, n2, eps, half, vth, amp=amp)
+    cell = np.concatenate([ps.cell, ps.cell])
+    t = np.concatenate([ps.t, ps.t], axis=1)
+    v = np.concatenate([ps.v, ps.v], axis=1).astype(np.float64)
+    v[0, :half] += v0
+    v[0, half:] -= v0
+    npart = 2 * half
+    return Workload(
+        name=f"two_stream_map2_{n1}x{n2}_eps{eps}",
+        dim=2,
+        n=(n1, n2),
+        vertices=map2_vertices(n1, n2, eps),
+        field_bc=[BC_PERIODIC] * 4,
+        field_bc_value=[0.0] * 4,
+        particle_bc=[PBC_PERIODIC] * 4,
+        dt=dt,
+        species=[Species(q=-1.0, m=1.0, w=1.0 / npart, vth=vth, capacity=npart)],
+        particles=[ParticleSet(cell, t, v.astype(np.float32))],
+        background=1.0,
+    )
+
+
 def cylinder(n1=128, n2=256, r0=1.0, R=40.0, npart_per_species=2_000_000, phi_obj=-5.0,
              mass_ratio=1836.0, dt=0.1, seed=1, inject=True, capacity_factor=1.5, host_particles=True):
     """2D cylinder in plasma on the log-polar annulus: object at xi = 0 held at phi_obj and

@@ -424,3 +424,72 @@ def test_sphere_floating_potential_test_c(cpic, Bz, expected):
           % (Bz, steps, tail, expected))
     assert abs(tail / expected - 1.0) <= 0.10, tail
     run.close()
+
+
+def test_landau_damping_rate(cpic):
+    """Landau damping (the paper's validation tests include it, Sec. III): a 5% density
+    perturbation with k lambda_D = 0.5 (wavelength the unit box, vth = 0.5 / 2 pi) on the
+    distorted map2 grid (eps 0.05), 64 x 64 cells, 1024 electrons per cell, dt 0.05, 400 full
+    cycles on the device. The field energy oscillates at 2 omega and decays as exp(2 gamma
+    t); the linear theory of a Maxwellian plasma gives omega = 1.4156, gamma = -0.1533 (in
+    omega_pe) at k lambda_D = 0.5. Peaks of W_E fitted between t = 4 (after the initial
+    transient) and t = 12 (before the thermal noise floor): omega within 3%, gamma within
+    10%."""
+    w = wl.langmuir_map2(64, 64, eps=0.05, ppc=1024, vth=0.5 / (2.0 * math.pi), amp=0.05, dt=0.05, seed=7)
+    run = cpic.run_from_workload(w, sort_interval=4, mg_rtol=1e-10, mg_max_cycles=100)
+    run.initialize()
+    we = [run.diag()["W_E"]]
+    for _ in range(400):
+        run.step(1)
+        we.append(run.diag()["W_E"])
+    run.close()
+    we = np.array(we)
+    t = np.arange(we.size) * w.dt
+    pk = [i for i in range(1, we.size - 1) if we[i] > we[i - 1] and we[i] >= we[i + 1]]
+    tp, wp = t[pk], we[pk]
+    lin = (tp > 4.0) & (tp < 12.0)
+    slope, _ = np.polyfit(tp[lin], np.log(wp[lin]), 1)
+    gamma = 0.5 * slope
+    omega = math.pi / np.mean(np.diff(tp[lin]))
+    print("Landau damping k lambda_D = 0.5: omega %.4f (theory 1.4156), gamma %.4f (theory -0.1533), %d peaks"
+          % (omega, gamma, int(lin.sum())))
+    assert abs(omega / 1.4156 - 1.0) <= 0.03, omega
+    assert abs(gamma / -0.1533 - 1.0) <= 0.10, gamma
+
+
+def test_two_stream_growth_rate(cpic):
+    """Two-stream instability (the paper's validation tests include it, Sec. III): two cold
+    electron beams at +-v0 with k v0 = 0.612 omega_pe for the box's mode (k = 2 pi), where
+    the cold two-beam dispersion relation 1 = (1/2)[1/(w - kv0)^2 + 1/(w + kv0)^2] has its
+    largest growth rate gamma = omega_pe / (2 sqrt 2) = 0.3536; distorted map2 grid (eps
+    0.05), 64 x 64 cells, 256 electrons per cell, dt 0.05, on the device. The field energy
+    grows as exp(2 gamma t) from the seeded perturbation until the beams trap (the seed
+    also excites the stable roots, which beat with the growing one early on); fitted over
+    W_E between 1% and 20% of its saturation maximum: gamma within 10%."""
+    w = wl.two_stream_map2(64, 64, eps=0.05, ppc=256, v0=0.612 / (2.0 * math.pi), vth=0.002, amp=1e-3, dt=0.05,
+                           seed=8)
+    run = cpic.run_from_workload(w, sort_interval=4, mg_rtol=1e-10, mg_max_cycles=100)
+    run.initialize()
+    we = [run.diag()["W_E"]]
+    for _ in range(500):
+        run.step(1)
+        we.append(run.diag()["W_E"])
+    run.close()
+    we = np.array(we)
+    t = np.arange(we.size) * w.dt
+    top = int(np.argmax(we))
+    # the last stretch before the maximum with W_E between 1% and 20% of it
+    stop = top
+    while stop > 0 and we[stop - 1] > 0.2 * we[top]:
+        stop -= 1
+    first = stop
+    while first > 0 and we[first - 1] > 0.01 * we[top]:
+        first -= 1
+    sel = np.zeros(we.size, bool)
+    sel[first:stop] = True
+    slope, _ = np.polyfit(t[sel], np.log(we[sel]), 1)
+    gamma = 0.5 * slope
+    print("two-stream: growth rate %.4f (theory 0.3536) over t = %.2f .. %.2f, W_E %.2e -> %.2e"
+          % (gamma, t[sel][0], t[sel][-1], we[0], we.max()))
+    assert sel.sum() >= 20
+    assert abs(gamma / 0.3536 - 1.0) <= 0.10, gamma
