@@ -191,7 +191,17 @@ int cpic_get_particles(cpic_run* run, int sp, int64_t room, int64_t* n, int32_t*
  * Faces normal to axis 0 (face 0 or 1) with absorbing particle boundaries, and the last
  * logical axis periodic or (2D) the run axisymmetric, whose face is then a surface of
  * revolution: segments drawn by ring area 2 pi r_mid |dX|, rate from the total. Otherwise
- * CPIC_ERR_INVALID. */
+ * CPIC_ERR_INVALID. A drift with an in-plane part (drift[0] or drift[1] nonzero) is a
+ * drifting Maxwellian source (Sec. III.A, the ions of the wall test), 2D only: per face
+ * segment j the inward drift u_j = drift . n_j (n_j the inward unit normal averaged over the
+ * segment's vertices) weighs the segment by its one-sided flux density
+ * Gamma(u_j) = vth/sqrt(2 pi) exp(-u_j^2/2 vth^2) + u_j/2 (1 + erf(u_j/(sqrt 2 vth))) times
+ * its length (or ring area); the rate is density sum_j Gamma(u_j) A_j dt / w; the normal
+ * speed follows the flux-weighted density v exp(-(v - u)^2/2 vth^2) on v > 0 (inverted by 64
+ * FP64 bisections), the tangential speed is Gaussian about the drift's tangential part, and
+ * drift[2] shifts the out-of-plane component. A 2D drift along z only keeps the resting
+ * flux and adds the drift to the drawn velocity; in 3D a nonzero drift returns
+ * CPIC_ERR_NOT_BUILT. */
 int cpic_set_injection(cpic_run* run, int sp, int face, double density, double vth,
                        const double* drift, uint64_t seed);
 

@@ -18,6 +18,18 @@ Readings (the paper gives no formulas):
     u = u_face + U4 dt (k v) (cell units, FP64, velocity already rounded to FP32); then the
     split (cell, FP32 offset) with the 1.0 -> next-cell rule, periodic wrap along the face;
     a particle whose partial push leaves the domain is dropped (not counted).
+A drifting Maxwellian (Sec. III.A: the ions of the wall test enter with a drift toward the
+wall), 2D faces: with u = drift . n the inward drift of a face point, the one-sided flux
+density of a Maxwellian of density 1 drifting at u along the normal is
+  Gamma(u) = vth / sqrt(2 pi) exp(-u^2 / 2 vth^2) + (u / 2) (1 + erf(u / (sqrt 2 vth))),
+so the rate is n sum_j Gamma(u_j) A_j dt / w over the face segments (u_j at the segment's
+midpoint normal, A_j its length, or its surface of revolution in an axisymmetric run), the
+segment is drawn by inverse CDF of Gamma(u_j) A_j (U0) and the offset along it is U5; the
+normal speed has the flux-weighted density v exp(-(v - u)^2 / 2 vth^2) on v > 0 and is drawn
+by inverse CDF, F(v) = 1 - U1, solved by 64 bisections of [0, max(u, 0) + 12 vth] in FP64;
+the tangential and out-of-plane components are the Gaussian ones above plus the drift's
+tangential and out-of-plane parts. With no drift this is the rule above (Gamma = vth /
+sqrt(2 pi), v = vth sqrt(-2 ln U1)), which stays the one used.
 3D (faces normal to axis 0 of a 3D map, e.g. the outer shell of the sphere runs):
   * face area: per face cell the quadrilateral area 1/2 |(X11 - X00) x (X01 - X10)| from its
     four vertices, summed in face-cell order (axis 1 fastest); the rate uses the total;
@@ -75,6 +87,59 @@ def rate_per_step(density, vth, area, dt, w):
     return (((density * vth) * INV_SQRT_2PI) * area) * dt / w
 
 
+def drift_flux(u, vth):
+    """One-sided flux density through a plane of a unit-density Maxwellian (thermal speed
+    vth) drifting at u along the plane's inward normal."""
+    return vth * INV_SQRT_2PI * math.exp(-u * u / (2.0 * vth * vth)) + 0.5 * u * (1.0 + math.erf(u / (math.sqrt(2.0) * vth)))
+
+
+def drift_normal_cdf(v, u, vth):
+    """CDF on v > 0 of the flux-weighted normal speed density v exp(-(v - u)^2 / 2 vth^2)."""
+    s2 = vth * vth
+    a = math.sqrt(0.5 * math.pi) * u * vth
+    e0 = math.exp(-u * u / (2.0 * s2))
+    erf0 = math.erf(u / (math.sqrt(2.0) * vth))
+    z = s2 * e0 + a * (1.0 + erf0)
+    f = s2 * (e0 - math.exp(-(v - u) * (v - u) / (2.0 * s2))) + a * (math.erf((v - u) / (math.sqrt(2.0) * vth)) + erf0)
+    return f / z
+
+
+def drift_normal_speed(q, u, vth):
+    """The normal speed with drift_normal_cdf(v) = q: 64 bisections of [0, max(u, 0) + 12 vth]."""
+    lo, hi = 0.0, max(u, 0.0) + 12.0 * vth
+    for _ in range(64):
+        mid = 0.5 * (lo + hi)
+        if drift_normal_cdf(mid, u, vth) < q:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def face_drift_weights_2d(X, k64, side, drift, vth, ring_areas=None):
+    """Per face segment (drifting injection): Gamma(u_j) A_j with u_j = drift . n_j, n_j the
+    inward unit normal from row 0 of k averaged over the segment's two vertices (FP64), A_j
+    the segment's length or its surface of revolution."""
+    n1 = X.shape[1] - 1
+    col = 0 if side == 0 else n1
+    m = X.shape[0] - 1
+    sgn = -1.0 if side == 1 else 1.0
+    out = np.empty(m)
+    for j in range(m):
+        kb = 0.5 * (k64[j, col] + k64[j + 1, col])
+        ga = kb[0]
+        gn = math.sqrt(ga[0] * ga[0] + ga[1] * ga[1])
+        nin = sgn * ga / gn
+        u = drift[0] * nin[0] + drift[1] * nin[1]
+        if ring_areas is not None:
+            a = float(ring_areas[j])
+        else:
+            d = X[j + 1, col] - X[j, col]
+            a = math.sqrt(d[0] * d[0] + d[1] * d[1])
+        out[j] = drift_flux(u, vth) * a
+    return out
+
+
 def count_at_step(rate, step):
     return int(math.floor((step + 1) * rate) - math.floor(step * rate))
 
@@ -93,17 +158,28 @@ def draws(count, step, species, seed):
     return np.concatenate(out, axis=1)  # (count, 8)
 
 
-def inject_2d(k64, n, side, count, step, species, seed, vth, drift, dt, ring_areas=None):
+def inject_2d(k64, n, side, count, step, species, seed, vth, drift, dt, ring_areas=None, drift_weights=None):
     """New particles on the face normal to axis 0 (side 0: xi = 0, side 1: xi = 1).
     k64: FP64 vertex table (N2+1, N1+1, a, alpha). Returns (idx (2, m), t32 (2, m),
     v32 (3, m), keep mask over the count draws). ring_areas (axisymmetric runs): the face
     segments' surfaces of revolution; the segment is then drawn by inverse CDF of those
     (the first whose inclusive prefix exceeds U0 * total), the offset along it is U5, the
     out-of-plane component is v_theta, and axis 1 is not periodic (a particle whose partial
-    push leaves it is dropped)."""
+    push leaves it is dropped). drift_weights (a drifting Maxwellian: face_drift_weights_2d):
+    the segment is drawn by inverse CDF of those, the offset along it from U5, and the normal
+    speed from the drifting flux-weighted distribution."""
     n1, n2 = n
     U = draws(count, step, species, seed)
-    if ring_areas is None:
+    drifting = drift_weights is not None
+    if drifting:
+        cdf = np.empty_like(drift_weights)
+        acc = 0.0
+        for i, x in enumerate(drift_weights):
+            acc += float(x)
+            cdf[i] = acc
+        j = np.minimum(np.searchsorted(cdf, U[:, 0] * acc, side="right"), n2 - 1).astype(np.int64)
+        s = U[:, 5]
+    elif ring_areas is None:
         u1 = U[:, 0] * n2
         j = np.floor(u1).astype(np.int64)
         j = np.minimum(j, n2 - 1)
@@ -123,13 +199,21 @@ def inject_2d(k64, n, side, count, step, species, seed, vth, drift, dt, ring_are
     sgn = -1.0 if side == 1 else 1.0
     nin = sgn * ga / gn[:, None]
     tau = np.stack([-nin[:, 1], nin[:, 0]], axis=1)
-    vn = vth * np.sqrt(-2.0 * np.log(U[:, 1]))
     rho = vth * np.sqrt(-2.0 * np.log(U[:, 2]))
     vt = rho * np.cos(2.0 * math.pi * U[:, 3])
     vz = rho * np.sin(2.0 * math.pi * U[:, 3])
     v = np.empty((3, count))
-    v[0] = vn * nin[:, 0] + vt * tau[:, 0] + drift[0]
-    v[1] = vn * nin[:, 1] + vt * tau[:, 1] + drift[1]
+    if drifting:
+        un = drift[0] * nin[:, 0] + drift[1] * nin[:, 1]
+        ut = drift[0] * tau[:, 0] + drift[1] * tau[:, 1]
+        vn = np.array([drift_normal_speed(1.0 - U[p, 1], un[p], vth) for p in range(count)])
+        vt = vt + ut
+        v[0] = vn * nin[:, 0] + vt * tau[:, 0]
+        v[1] = vn * nin[:, 1] + vt * tau[:, 1]
+    else:
+        vn = vth * np.sqrt(-2.0 * np.log(U[:, 1]))
+        v[0] = vn * nin[:, 0] + vt * tau[:, 0] + drift[0]
+        v[1] = vn * nin[:, 1] + vt * tau[:, 1] + drift[1]
     v[2] = vz + drift[2]
     v32 = v.astype(np.float32)
     vd = v32.astype(np.float64)
@@ -148,7 +232,7 @@ def inject_2d(k64, n, side, count, step, species, seed, vth, drift, dt, ring_are
         out_idx[a] = c.astype(np.int64)
         out_t[a] = f32
     if ring_areas is None:
-        out_idx[1] = np.mod(out_idx[1], n2)
+        out_idx[1] = np.mod(out_idx[1], n2)  # (a periodic face)
         keep = (out_idx[0] >= 0) & (out_idx[0] < n1)
     else:
         keep = (out_idx[0] >= 0) & (out_idx[0] < n1) & (out_idx[1] >= 0) & (out_idx[1] < n2)

@@ -232,9 +232,19 @@ class OraclePIC:
                     self.collect[s, f] += np.bincount(b, minlength=self.collect.shape[2])
             sp.idx = np.compress(alive, idx, axis=1).astype(np.int64, copy=False)
             sp.t, sp.v = np.compress(alive, t, axis=1), np.compress(alive, v, axis=1)
-        for (s, face, dens, vth, seed) in self.injection:
+        for inj in self.injection:
+            s, face, dens, vth, seed = inj[:5]
+            drift = tuple(inj[5]) if len(inj) > 5 else (0.0, 0.0, 0.0)
             sp = self.species[s]
             side = face % 2
+            dweights = None
+            if self.D == 2 and any(drift):  # a drifting Maxwellian: per-segment flux weights
+                key = ("drift", s, side)
+                if key not in self._face_area:
+                    rings = inject.face_ring_areas_2d(self.geom.X, side) if self.geom.axisym else None
+                    self._face_area[key] = inject.face_drift_weights_2d(self.geom.X, self.geom.k, side, drift, vth,
+                                                                        rings)
+                dweights = self._face_area[key]
             if side not in self._face_area:
                 if self.geom.axisym:
                     self._face_area[side] = inject.face_area_axisym(self.geom.X, side)
@@ -242,14 +252,20 @@ class OraclePIC:
                     self._face_area[side] = (inject.face_length_2d(self.geom.X, side) if self.D == 2
                                              else inject.face_area_3d(self.geom.X, side))
             area = self._face_area[side]
-            rate = inject.rate_per_step(dens, vth, area, self.dt, sp.w)
+            if dweights is not None:
+                tot = 0.0
+                for x in dweights:
+                    tot += float(x)
+                rate = dens * tot * self.dt / sp.w
+            else:
+                rate = inject.rate_per_step(dens, vth, area, self.dt, sp.w)
             cnt = inject.count_at_step(rate, self.step_index)
             if cnt == 0:
                 continue
             if self.D == 2:
                 rings = inject.face_ring_areas_2d(self.geom.X, side) if self.geom.axisym else None
                 idx, t32, v32, _ = inject.inject_2d(self.geom.k, self.n, side, cnt, self.step_index, s, seed,
-                                                    vth, (0.0, 0.0, 0.0), self.dt, ring_areas=rings)
+                                                    vth, drift, self.dt, ring_areas=rings, drift_weights=dweights)
             else:
                 idx, t32, v32, _ = inject.inject_3d(self.geom.X, self.geom.k, self.n, side, cnt, self.step_index, s,
                                                     seed, vth, (0.0, 0.0, 0.0), self.dt)

@@ -542,8 +542,9 @@ def run_from_workload(wl, sort_interval=0, analytic=None, mg_rtol=0.0, mg_max_cy
         run.set_map_analytic(*analytic)
     for s, ps in enumerate(wl.particles):
         run.load_particles(s, ps.cell, ps.t, ps.v)
-    for (s, face, dens, vth, seed) in wl.injection:
-        run.set_injection(s, face, dens, vth, seed)
+    for inj in wl.injection:
+        s, face, dens, vth, seed = inj[:5]
+        run.set_injection(s, face, dens, vth, seed, drift=inj[5] if len(inj) > 5 else None)
     if getattr(wl, "B0", None) is not None:
         run.set_magnetic_field(wl.B0)
         run.set_gyro_integrator(getattr(wl, "gyro", "boris"))

@@ -196,6 +196,7 @@ void plan(cpic_run* r, Planner& P) {
     r->fcdf = r->D == 3 ? P.take<double>((size_t)2 * r->n[1] * r->n[2])
                         : (c.axisymmetric ? P.take<double>((size_t)2 * r->n[1]) : nullptr);
     r->R32 = c.axisymmetric ? P.take<float>((size_t)r->nvert) : nullptr;
+    r->dcdf = D == 2 ? P.take<double>((size_t)CPIC_MAX_SPECIES * r->n[1]) : nullptr;
     r->charge = P.take<unsigned long long>((size_t)c.n_species * r->ncell);
     r->ncollect = D == 2 ? r->n[1] : r->n[1] * r->n[2];
     r->collect = P.take<unsigned long long>((size_t)c.n_species * 2 * r->ncollect);
@@ -409,6 +410,43 @@ bool stream_ordered_source(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged || at.type == cudaMemoryTypeHost;
 }
 
+// Drifting-Maxwellian injection (2D): per face segment j the inward unit normal from row 0
+// of k averaged over the segment's two vertices (FP64), the inward drift u_j = drift . n_j,
+// the one-sided flux density Gamma(u_j) = vth/sqrt(2 pi) exp(-u_j^2/2vth^2) + u_j/2 (1 +
+// erf(u_j/(sqrt 2 vth))) times the segment's length (or surface of revolution); inclusive
+// prefixes on the device (the segment draw), the total sets the rate.
+int drift_setup(cpic_run* r, int s) {
+    InjectSpec& q = r->inj[s];
+    const int n1 = r->n[0], m = r->n[1], nv0 = n1 + 1;
+    const int col = (q.face & 1) ? n1 : 0;
+    std::vector<double> X((size_t)r->nvert * 2), k((size_t)r->nvert * 4);
+    CPIC_CUDA(cudaMemcpyAsync(X.data(), r->lev[0].X, sizeof(double) * X.size(), cudaMemcpyDeviceToHost, r->stream));
+    CPIC_CUDA(cudaMemcpyAsync(k.data(), r->k64, sizeof(double) * k.size(), cudaMemcpyDeviceToHost, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    const double sgn = (q.face & 1) ? -1.0 : 1.0, vth = q.vth;
+    std::vector<double> cdf(m);
+    double acc = 0.0;
+    for (int j = 0; j < m; ++j) {
+        const size_t v0 = (size_t)col + (size_t)nv0 * j, v1 = v0 + nv0;
+        const double g0 = 0.5 * (k[v0 * 4 + 0] + k[v1 * 4 + 0]), g1 = 0.5 * (k[v0 * 4 + 1] + k[v1 * 4 + 1]);
+        const double gn = sqrt(g0 * g0 + g1 * g1);
+        const double n0 = sgn * g0 / gn, nn1 = sgn * g1 / gn;
+        const double u = q.drift[0] * n0 + q.drift[1] * nn1;
+        const double gam = vth * (1.0 / sqrt(2.0 * M_PI)) * exp(-u * u / (2.0 * vth * vth)) +
+                           0.5 * u * (1.0 + erf(u / (sqrt(2.0) * vth)));
+        const double dx = X[v1 * 2] - X[v0 * 2], dy = X[v1 * 2 + 1] - X[v0 * 2 + 1];
+        double a = sqrt(dx * dx + dy * dy);
+        if (r->cfg.axisymmetric) a = 2.0 * M_PI * (0.5 * (X[v0 * 2] + X[v1 * 2])) * a;
+        acc += gam * a;
+        cdf[j] = acc;
+    }
+    CPIC_CUDA(cudaMemcpyAsync(r->dcdf + (size_t)s * m, cdf.data(), sizeof(double) * m, cudaMemcpyHostToDevice, r->stream));
+    CPIC_CUDA(cudaStreamSynchronize(r->stream));
+    q.dtot = acc;
+    q.rate = q.density * acc * r->cfg.dt / r->cfg.w[s];
+    return CPIC_OK;
+}
+
 int after_map(cpic_run* r) {
     int st = launch_geometry(r);
     if (st) return st;
@@ -508,7 +546,12 @@ int after_map(cpic_run* r) {
     for (int s = 0; s < CPIC_MAX_SPECIES; ++s)
         if (r->inj[s].enabled) {
             const InjectSpec& q = r->inj[s];
-            r->inj[s].rate = (((q.density * q.vth) * (1.0 / sqrt(2.0 * M_PI))) * r->face_len[q.face & 1]) * r->cfg.dt / r->cfg.w[s];
+            if (q.drifting) {
+                if (int e = drift_setup(r, s)) return e;
+            } else {
+                r->inj[s].rate =
+                    (((q.density * q.vth) * (1.0 / sqrt(2.0 * M_PI))) * r->face_len[q.face & 1]) * r->cfg.dt / r->cfg.w[s];
+            }
         }
     return CPIC_OK;
 }
@@ -1137,6 +1180,11 @@ int cpic_set_injection(cpic_run* r, int sp, int face, double density, double vth
         set_error("set_injection: the last logical axis must be periodic (or the run axisymmetric)");
         return CPIC_ERR_INVALID;
     }
+    const bool inplane = drift && (drift[0] != 0.0 || drift[1] != 0.0 || (r->D == 3 && drift[2] != 0.0));
+    if (r->D == 3 && inplane) {
+        set_error("set_injection: a drifting Maxwellian flux is built for 2D faces only");
+        return CPIC_ERR_NOT_BUILT;
+    }
     InjectSpec& q = r->inj[sp];
     q.enabled = density > 0.0;
     q.face = face;
@@ -1144,7 +1192,16 @@ int cpic_set_injection(cpic_run* r, int sp, int face, double density, double vth
     q.vth = vth;
     for (int a = 0; a < 3; ++a) q.drift[a] = drift ? drift[a] : 0.0;
     q.seed = seed;
-    q.rate = r->map_set ? (((density * vth) * (1.0 / sqrt(2.0 * M_PI))) * r->face_len[face & 1]) * r->cfg.dt / r->cfg.w[sp] : 0.0;
+    q.drifting = inplane ? 1 : 0;
+    q.dtot = 0.0;
+    q.rate = 0.0;
+    if (r->map_set) {
+        if (q.drifting) {
+            if (int e = drift_setup(r, sp)) return e;
+        } else {
+            q.rate = (((density * vth) * (1.0 / sqrt(2.0 * M_PI))) * r->face_len[face & 1]) * r->cfg.dt / r->cfg.w[sp];
+        }
+    }
     invalidate_graphs(r);
     return CPIC_OK;
 }

@@ -39,7 +39,33 @@ struct InjectOne {
     float vth, drift[3];
     unsigned long long seed;
     int blocks;  // blocks covering this species' draws
+    int drifting;          // 2D drifting Maxwellian: segment by dcdf, bisected normal speed
+    const double* dcdf;    // its segment prefixes of Gamma(u_j) A_j
+    double dtot, vthd, dr[3];
 };
+
+// drifting Maxwellian: CDF on v > 0 of the flux-weighted normal speed density
+// v exp(-(v - u)^2 / 2 vth^2), and its inverse by 64 bisections of [0, max(u, 0) + 12 vth]
+// (FP64, the same steps as the reading's definition)
+__device__ double drift_normal_cdf(double v, double u, double vth) {
+    const double s2 = vth * vth;
+    const double a = sqrt(0.5 * M_PI) * u * vth;
+    const double e0 = exp(-u * u / (2.0 * s2));
+    const double erf0 = erf(u / (sqrt(2.0) * vth));
+    const double z = s2 * e0 + a * (1.0 + erf0);
+    const double f = s2 * (e0 - exp(-(v - u) * (v - u) / (2.0 * s2))) + a * (erf((v - u) / (sqrt(2.0) * vth)) + erf0);
+    return f / z;
+}
+
+__device__ double drift_normal_speed(double q, double u, double vth) {
+    double lo = 0.0, hi = (u > 0.0 ? u : 0.0) + 12.0 * vth;
+    for (int it = 0; it < 64; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (drift_normal_cdf(mid, u, vth) < q) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
 
 struct InjectParams {
     PushParams p;
@@ -127,7 +153,20 @@ __global__ void inject_kernel(InjectParams ip) {
             const float U0 = u01f(r0.x), U1 = u01f(r0.y), U2 = u01f(r0.z), U3 = u01f(r0.w), U4 = u01f(r1.x);
             int j;
             float sfr;
-            if (ip.axisym) {
+            if (sp.drifting) {
+                // drifting Maxwellian: the segment by inverse CDF of Gamma(u_j) A_j (FP64),
+                // the offset along it from U5
+                const double* cdf = sp.dcdf;
+                const double target = (((double)r0.x + 0.5) * 2.3283064365386962890625e-10) * sp.dtot;
+                int lo = 0, hi = n2 - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cdf[mid] > target) hi = mid;
+                    else lo = mid + 1;
+                }
+                j = lo;
+                sfr = u01f(r1.y);
+            } else if (ip.axisym) {
                 // axisymmetric: the segment by inverse CDF of the surfaces of revolution (FP64,
                 // as for the 3D face cells), the offset along it from U5
                 const double* cdf = ip.fcdf + (sp.side ? n2 : 0);
@@ -158,13 +197,27 @@ __global__ void inject_kernel(InjectParams ip) {
             const float nin0 = __fdiv_rn(sgn * kb[0], gn), nin1 = __fdiv_rn(sgn * kb[1], gn);
             const float tau0 = -nin1, tau1 = nin0;
             // flux-weighted normal speed, Gaussian tangential and z components (Box-Muller)
-            const float vn = sp.vth * sqrtf(-2.0f * logf(U1));
             const float rho = sp.vth * sqrtf(-2.0f * logf(U2));
             float sn, cs;
             sincospif(2.0f * U3, &sn, &cs);
-            const float vt = rho * cs, vz = rho * sn;
-            const float v0 = __fadd_rn(__fmaf_rn(vn, nin0, __fmul_rn(vt, tau0)), sp.drift[0]);
-            const float v1 = __fadd_rn(__fmaf_rn(vn, nin1, __fmul_rn(vt, tau1)), sp.drift[1]);
+            const float vz = rho * sn;
+            float v0, v1;
+            if (sp.drifting) {
+                // the normal speed of the drifting flux (inverse CDF at 1 - U1, FP64) and the
+                // drift's tangential part on the Gaussian tangential speed
+                const double un = sp.dr[0] * (double)nin0 + sp.dr[1] * (double)nin1;
+                const double ut = sp.dr[0] * (double)tau0 + sp.dr[1] * (double)tau1;
+                const double q = 1.0 - ((double)r0.y + 0.5) * 2.3283064365386962890625e-10;
+                const float vn = (float)drift_normal_speed(q, un, sp.vthd);
+                const float vt = __fadd_rn(rho * cs, (float)ut);
+                v0 = __fmaf_rn(vn, nin0, __fmul_rn(vt, tau0));
+                v1 = __fmaf_rn(vn, nin1, __fmul_rn(vt, tau1));
+            } else {
+                const float vn = sp.vth * sqrtf(-2.0f * logf(U1));
+                const float vt = rho * cs;
+                v0 = __fadd_rn(__fmaf_rn(vn, nin0, __fmul_rn(vt, tau0)), sp.drift[0]);
+                v1 = __fadd_rn(__fmaf_rn(vn, nin1, __fmul_rn(vt, tau1)), sp.drift[1]);
+            }
             const float v2 = __fadd_rn(vz, sp.drift[2]);
             // partial first push over a uniform fraction U4 of the step, on the split position
             const float fdt = __fmul_rn(U4, ip.dt);
@@ -322,6 +375,11 @@ int launch_inject(cpic_run* r) {
         o.vth = (float)sp.vth;
         for (int a = 0; a < 3; ++a) o.drift[a] = (float)sp.drift[a];
         o.seed = sp.seed;
+        o.drifting = sp.drifting;
+        o.dcdf = r->dcdf ? r->dcdf + (size_t)s * r->n[1] : nullptr;
+        o.dtot = sp.dtot;
+        o.vthd = sp.vth;
+        for (int a = 0; a < 3; ++a) o.dr[a] = sp.drift[a];
         long long maxc = (long long)ceil(sp.rate) + 1;
         long long b = (maxc + 255) / 256;
         if (b > 4LL * device_sm_count()) b = 4LL * device_sm_count();

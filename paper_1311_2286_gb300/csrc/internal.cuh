@@ -144,7 +144,9 @@ struct InjectSpec {
     int face;
     double density, vth, drift[3];
     unsigned long long seed;
-    double rate;  // particles per step
+    double rate;   // particles per step
+    int drifting;  // 2D, in-plane drift: the drifting-Maxwellian flux and normal speeds
+    double dtot;   // drifting: sum over the face segments of Gamma(u_j) A_j
 };
 
 }  // namespace cpic
@@ -169,6 +171,7 @@ struct cpic_run {
     float* R32;       // axisymmetric runs: vertex cylindrical radius x^1 (FP32), else nullptr
     double* rhs_bc;   // Dirichlet part of the right-hand side (finest)
     double* jcdf;     // inclusive prefix sums of the cell Jacobians (device loading)
+    double* dcdf;     // 2D drifting injection: per species, inclusive prefixes of Gamma(u_j) A_j
     double* fcdf;     // inclusive prefix sums of the face-cell areas of faces 0 and 1 (3D), or
                       // of the face segments' surfaces of revolution (axisymmetric 2D)
     unsigned long long* charge;  // [nsp][ncell] folded charge counts (what the field solve reads)

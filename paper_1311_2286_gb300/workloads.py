@@ -285,6 +285,40 @@ def langmuir_map2(n1=32, n2=32, eps=0.05, ppc=64, vth=0.05, amp=0.01, dt=0.1, se
     )
 
 
+def planar_wall(n1=128, n2=128, Lx=20.0, Ly=5.0, ppc=64, mass_ratio=1836.0, ion_drift=-2.1, dt=0.05, seed=12,
+                capacity_factor=1.6):
+    """The conducting planar wall of Sec. III.A (Test A, eq. (map3): x = Lx xi, y = Ly eta):
+    the wall at xi = 0 (absorbing; floating when the run says so, else grounded), phi = 0 at
+    xi = 1, eta periodic; the box starts empty and both species are injected at xi = 1 each
+    step from a unit-density plasma, electrons from a Maxwellian at rest, ions (T_i = T_e)
+    from one drifting at ion_drift ion thermal speeds along x (toward the wall). The weight
+    gives about ppc particles per cell and species at unit density."""
+    xi, eta = _logical_vertices((n1, n2))
+    XI, ETA = np.meshgrid(xi, eta, indexing="xy")
+    X = np.empty((n2 + 1, n1 + 1, 2))
+    X[..., 0] = Lx * XI
+    X[..., 1] = Ly * ETA
+    w = Lx * Ly / (ppc * n1 * n2)
+    vti = 1.0 / math.sqrt(mass_ratio)
+    cap = int(capacity_factor * ppc * n1 * n2)
+    sp = [Species(-1.0, 1.0, w, 1.0, cap), Species(1.0, mass_ratio, w, vti, cap)]
+    empty = [ParticleSet(np.zeros(0, np.int32), np.zeros((2, 0), np.float32), np.zeros((3, 0), np.float32))
+             for _ in sp]
+    return Workload(
+        name=f"planar_wall_{n1}x{n2}",
+        dim=2,
+        n=(n1, n2),
+        vertices=X,
+        field_bc=[BC_DIRICHLET, BC_DIRICHLET, BC_PERIODIC, BC_PERIODIC],
+        field_bc_value=[0.0, 0.0, 0.0, 0.0],
+        particle_bc=[PBC_ABSORB, PBC_ABSORB, PBC_PERIODIC, PBC_PERIODIC],
+        dt=dt,
+        species=sp,
+        particles=empty,
+        injection=[(0, 1, 1.0, 1.0, seed * 1000 + 1), (1, 1, 1.0, vti, seed * 1000 + 2, (ion_drift * vti, 0.0, 0.0))],
+    )
+
+
 def two_stream_map2(n1=64, n2=64, eps=0.05, ppc=256, v0=0.0975, vth=0.002, amp=1e-3, dt=0.05, seed=0):
     """Two-stream configuration on the doubly periodic map2 square: two equal cold electron
     beams (each half of the unit density) drifting at +v0 and -v0 along x through immobile

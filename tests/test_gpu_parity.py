@@ -622,6 +622,55 @@ def test_injection_matches_oracle(cpic):
     run.close()
 
 
+@pytest.mark.parametrize("case", ["planar_wall", "cylinder"])
+def test_drifting_injection_matches_oracle(cpic, case):
+    """a8 with a drifting Maxwellian (Sec. III.A, Test A's ion source): the rate from the
+    per-segment flux sum, the segment by inverse CDF of Gamma(u_j) A_j, the normal speed by
+    bisection of the drifting flux CDF, and the drift's tangential part agree with the oracle
+    (count exact; cells exact up to draws within rounding of a segment edge; values to FP32
+    arithmetic). On the cylinder the inward drift varies along the face, so the segment draw
+    is far from uniform."""
+    if case == "planar_wall":
+        w = wl.planar_wall(32, 16, ppc=400)
+        w.injection = [(0, 1, 10.0, 1.0, 71, (0.0, 0.4, 0.0)), (1, 1, 50.0, 1.0 / math.sqrt(1836.0), 72,
+                                                                 (-2.1 / math.sqrt(1836.0), 0.0, 0.0))]
+    else:
+        w = wl.cylinder(n1=32, n2=64, npart_per_species=1000, seed=9, inject=True, capacity_factor=8.0)
+        w.injection = [(0, 1, 400.0, 1.0, 73, (1.3, -0.6, 0.0)), (1, 1, 400.0, 0.5, 74, (-0.4, 0.9, 0.0))]
+    n1, n2 = w.n
+    g, _ = _geom(w)
+    run = cpic.run_from_workload(w)
+    run.vertex_field()
+    run.push()
+    before = [run.particles(s) for s in range(2)]
+    run.inject()
+    after = [run.particles(s) for s in range(2)]
+    d = run.diag()
+    for s, (s_, face, dens, vth, seed, drift) in enumerate(w.injection):
+        sp = w.species[s]
+        wts = inject.face_drift_weights_2d(w.vertices, g.k, 1, drift, vth)
+        assert wts.max() > wts.min() * (1.5 if case == "cylinder" else 0.999)
+        tot = 0.0
+        for x in wts:
+            tot += float(x)
+        rate = dens * tot * w.dt / sp.w
+        cnt = inject.count_at_step(rate, 0)
+        assert cnt > 500
+        idx, t32, v32, keep = inject.inject_2d(g.k, (n1, n2), 1, cnt, 0, s, seed, vth, drift, w.dt,
+                                               drift_weights=wts)
+        nb = before[s][0].shape[0]
+        ca, ta, va = after[s]
+        new_c, new_t, new_v = ca[nb:], ta[:, nb:], va[:, nb:]
+        assert new_c.shape[0] == int(keep.sum())
+        assert d["injected"][s] == int(keep.sum())
+        ref_cell = (idx[0] | (idx[1] << 16)).astype(np.int32)
+        ok = new_c == ref_cell
+        assert np.sum(~ok) <= max(1, cnt // 10000)
+        np.testing.assert_allclose(new_v[:, ok], v32[:, ok], rtol=2e-6, atol=2e-6 * vth)
+        np.testing.assert_allclose(new_t[:, ok], t32[:, ok], atol=1e-5)
+    run.close()
+
+
 def test_injection_3d_matches_oracle(cpic):
     """a8 in 3D (outer shell of the sphere): count from the face area, face cell by inverse
     CDF of the face-cell areas, offsets, velocities and partial push agree with the oracle

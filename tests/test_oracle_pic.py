@@ -313,3 +313,67 @@ def test_collection_tally_bins_by_the_transverse_cell():
     np.testing.assert_array_equal(pic.collect[0, 0], np.bincount(rows, minlength=32))
     assert pic.collect[0, 0].sum() == pic.species[0].absorbed[0] == m
     assert pic.collect[1].sum() == 0 and pic.collect[0, 1].sum() == 0
+
+
+@pytest.mark.parametrize("u_over_vth", [2.1, -0.7])
+def test_drifting_flux_by_brute_force(u_over_vth):
+    """Drifting Maxwellian injection (Sec. III.A's ions, drift 2.1 vth toward the wall): the
+    flux density Gamma(u) = vth/sqrt(2 pi) exp(-u^2/2vth^2) + u/2 (1 + erf(u/sqrt(2) vth))
+    equals the count of a drifting Maxwellian box's particles crossing a plane within dt
+    (within 4 sigma), and the normal speeds the injection draws (inverse CDF by bisection)
+    have the distribution of those crossing particles' speeds (two-sample Kolmogorov-Smirnov
+    distance below its 1e-3-level critical value); the in-plane tangential drift is added
+    to the Gaussian tangential speed."""
+    rng = np.random.default_rng(31)
+    vth, dt, dens, A = 0.9, 0.05, 2.0, 1.5
+    u = u_over_vth * vth
+    L = (abs(u) + 8.0 * vth) * dt
+    npart = 4_000_000
+    w = dens * L * A / npart
+    vx = u + vth * rng.standard_normal(npart)
+    x = -L * rng.random(npart)
+    hit = x + vx * dt > 0.0
+    crossed = int(hit.sum())
+    expected = dens * inject.drift_flux(u, vth) * A * dt / w
+    assert abs(crossed - expected) < 4.0 * math.sqrt(expected), (crossed, expected)
+    # injected normal speeds on the xi = 1 face of a uniform rectangle (inward normal -x):
+    # a drift (-u, 0.3, 0.2) is u along the inward normal
+    n = (8, 16)
+    X = np.zeros((n[1] + 1, n[0] + 1, 2))
+    X[..., 0] = np.linspace(0.0, 2.0, n[0] + 1)[None, :]
+    X[..., 1] = np.linspace(0.0, A, n[1] + 1)[:, None]
+    from oracle import geometry
+    g = geometry.build_geometry(X, [False, True])
+    drift = (-u, 0.3, 0.2)
+    wts = inject.face_drift_weights_2d(X, g.k, 1, drift, vth)
+    np.testing.assert_allclose(wts.sum(), inject.drift_flux(u, vth) * A, rtol=1e-12)
+    cnt = 40_000
+    idx, t32, v32, keep = inject.inject_2d(g.k, n, 1, cnt, 0, 0, 77, vth, drift, 1e-6, drift_weights=wts)
+    vn = -v32[0].astype(np.float64)
+    ref = np.sort(vx[hit])
+    got = np.sort(vn)
+    allv = np.concatenate([ref, got])
+    d = np.max(np.abs(np.searchsorted(ref, allv, side="right") / ref.size
+                      - np.searchsorted(got, allv, side="right") / got.size))
+    crit = 1.95 * math.sqrt((ref.size + got.size) / (ref.size * got.size))
+    assert d < crit, (d, crit)
+    assert abs(v32[1].mean() - 0.3) < 5 * vth / math.sqrt(cnt) and abs(v32[2].mean() - 0.2) < 5 * vth / math.sqrt(cnt)
+
+
+def test_planar_wall_early_spike():
+    """Test A (Sec. III.A) on a reduced 32 x 16 grid: the box fills from the source at
+    xi = 1, the fast electrons reach the floating wall first and drive it to the paper's
+    early minimum of about -5.7 T_e (within 10%) in the first 1600 steps; the ions have not
+    arrived yet, so the wall then still sits far below the -2.1 T_e steady state."""
+    w = wl.planar_wall(32, 16, ppc=32)
+    p = OraclePIC(w, "fp64", engine="c", threads=4)
+    p.set_floating(0, 0.0)
+    p.initialize()
+    vs = []
+    for _ in range(1600):
+        p.step()
+        vs.append(p.history[-1]["object_potential"])
+    vs = np.array(vs)
+    assert abs(vs.min() / -5.7 - 1.0) <= 0.10, vs.min()
+    assert vs[-100:].mean() < -4.0
+    assert p.injected[1] > 0 and p.history[-1]["n"][1] > 0
