@@ -216,7 +216,7 @@ void plan(cpic_run* r, Planner& P) {
         r->pb.v[b] = P.take<float>((size_t)3 * total);
     }
     r->ctr = P.take<DevCounters>(1);
-    r->red = P.take<double>(2 * 1024 + 8);
+    r->red = P.take<double>(3 * KRY_BLOCKS + 16);
     r->kry = P.take<KrylovState>(1);
     r->kv = P.take<double>((size_t)5 * r->ncell);
     r->ph32 = P.take<float>(r->ncell);

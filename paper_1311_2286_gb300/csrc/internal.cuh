@@ -65,7 +65,10 @@ struct DevCounters {
 };
 
 // Scalars and reduction partials of the Krylov solve (device).
-constexpr int KRY_BLOCKS = 256;
+// blocks of the operator passes over the finest level (the FP64 residual, the Krylov
+// products): up to one per eight rows of cells, so that these passes fill the GPU; each
+// block leaves its partial sums in a reduction array of this many entries
+constexpr int KRY_BLOCKS = 2048;
 struct KrylovState {
     double rho, alpha, omega, beta;
     int restart;       // the next direction step starts over: r_hat = r, p = r
@@ -197,7 +200,7 @@ struct cpic_run {
     bool singular;
     double sumJ;                 // sum of finest J_c (singular projection)
     double load_total;           // last entry of jcdf: sum J_c, or sum Omega_c J_c (axisymmetric)
-    double* red;                 // reduction scratch [2 * 1024 + 8]
+    double* red;                 // reduction scratch [3 * KRY_BLOCKS + 16]
     int solver;                  // CPIC_SOLVER_* of the stream solve
     int pc_face_only;            // the FP32 V-cycle uses the stencil's face entries only
     double B0[3];                // uniform magnetic field (cpic_set_magnetic_field)

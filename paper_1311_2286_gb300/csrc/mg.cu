@@ -34,8 +34,11 @@
 // s = r - alpha v; s^ = V(s); t = M s^, omega = (t, s) / (t, t); phi += alpha p^ + omega s^;
 // then r = b - M phi is recomputed in FP64 (not updated), so the stopping test sees the true
 // residual, and rho' = (r^, r), beta = (rho' / rho)(alpha / omega). A vanishing rho, alpha
-// or omega restarts the recurrence with r^ = p = r. The products with M are FP64 on the FP32
-// preconditioned vectors; phi is only ever changed by FP64 additions of those vectors.
+// or omega restarts the recurrence with r^ = p = r. The products M p^ and M s^ only choose
+// the step lengths alpha and omega: they are FP32 (the FP32 copy of the full operator, on
+// the FP32 preconditioned vectors; FP64 on GB300 runs at 1/64 of the FP32 rate), while phi
+// is only ever changed by FP64 additions of those vectors and the stopping test reads the
+// FP64 residual, so the result's accuracy does not depend on them.
 //
 // The residual kernel ends with a last-block reduction that decides whether to continue;
 // it writes the decision into a CUDA graph conditional handle, so inside a captured step
@@ -765,7 +768,7 @@ struct ResidualParams {
     const double* rh;   // shadow residual r^: (r^, r) is reduced when ks is set and !init
     KrylovState* ks;    // Krylov scalars to update, or null
     int init;           // first residual of a Krylov solve: start the recurrence
-    double* part;       // [3 * RED_BLOCKS]
+    double* part;       // [3 * gridDim.x]
     unsigned* ticket;
     DevCounters* ctr;
     int* done;
@@ -875,10 +878,12 @@ __global__ void bicg_direction_kernel(int n, const double* __restrict__ r, doubl
     }
 }
 
-// y = M x32 (FP64) over the finest level; mode 0: v = y, p^ = x32 kept, reduce (r^, v) ->
+// y = M x32 over the finest level with the FP32 copy of the full operator (every stencil
+// entry; on GB300 an FP64 product is bound by the FP64 rate, at about a third of the memory
+// rate), stored and reduced in FP64; mode 0: v = y, p^ = x32 kept, reduce (r^, v) ->
 // alpha = rho / (r^, v); mode 1: reduce (y, s), (y, y) -> omega = (t, s) / (t, t)
 template <int D, int NPT>
-__global__ void __launch_bounds__(256) bicg_matvec_kernel(LV<double> L, const float* __restrict__ x32, int mode,
+__global__ void __launch_bounds__(256) bicg_matvec_kernel(LV<float> L, const float* __restrict__ x32, int mode,
                                                            double* v, float* ph32, const double* __restrict__ w,
                                                            KrylovState* ks) {
     __shared__ double sh[96];
@@ -890,7 +895,7 @@ __global__ void __launch_bounds__(256) bicg_matvec_kernel(LV<double> L, const fl
         for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
             int q[3] = {i, j, k};
             int c = i + L.n[0] * row;
-            const double y = stencil_apply<D, NPT>(L, x32, c, q);
+            const double y = (double)stencil_apply<D, NPT>(L, x32, c, q);
             if (mode == 0) {
                 v[c] = y;
                 ph32[c] = x32[c];
@@ -1257,7 +1262,14 @@ size_t cta_smem_bytes(const LVSet& S) {
     return f * sizeof(float);
 }
 
-int* done_flag(cpic_run* r) { return reinterpret_cast<int*>(r->red + 3 * RED_BLOCKS + 2); }
+int* done_flag(cpic_run* r) { return reinterpret_cast<int*>(r->red + 3 * KRY_BLOCKS + 2); }
+
+// blocks of a pass over the finest level's rows of cells (kCellBlock: eight rows a block)
+int row_blocks(const cpic_run* r) {
+    const long long rows = (long long)r->lev[0].n[1] * (r->D == 3 ? r->lev[0].n[2] : 1);
+    const long long b = (rows + 7) / 8;
+    return (int)(b < 1 ? 1 : (b > KRY_BLOCKS ? KRY_BLOCKS : b));
+}
 
 const dim3 kCellBlock(32, 8, 1);
 
@@ -1396,7 +1408,7 @@ int enqueue_residual(cpic_run* r, double rtol, int max_cycles, int count_cycle, 
     P.use_handle = use_handle ? 1 : 0;
     P.handle = h;
     return dispatch_shape(r, [&](auto Dc, auto Nc) -> int {
-        residual_kernel<decltype(Dc)::value, decltype(Nc)::value><<<RED_BLOCKS, kCellBlock, 0, r->stream>>>(P);
+        residual_kernel<decltype(Dc)::value, decltype(Nc)::value><<<row_blocks(r), kCellBlock, 0, r->stream>>>(P);
         CPIC_CHECK_LAUNCH();
         return CPIC_OK;
     });
@@ -1419,10 +1431,10 @@ int enqueue_bicg_iteration(cpic_run* r, const LVSet& S, double rtol, int max_cyc
     CPIC_CHECK_LAUNCH();
     int e = enqueue_vcycle(r, S);
     if (e) return e;
-    LV<double> L0 = make_lv<double>(r, 0, false);
+    LV<float> L0 = make_lv<float>(r, 0, true);  // A32 holds every entry of the operator
     e = dispatch_shape(r, [&](auto Dc, auto Nc) -> int {
         bicg_matvec_kernel<decltype(Dc)::value, decltype(Nc)::value>
-            <<<KRY_BLOCKS, kCellBlock, 0, st>>>(L0, x32, 0, v, r->ph32, rh, r->kry);
+            <<<row_blocks(r), kCellBlock, 0, st>>>(L0, x32, 0, v, r->ph32, rh, r->kry);
         CPIC_CHECK_LAUNCH();
         return CPIC_OK;
     });
@@ -1433,7 +1445,7 @@ int enqueue_bicg_iteration(cpic_run* r, const LVSet& S, double rtol, int max_cyc
     if (e) return e;
     e = dispatch_shape(r, [&](auto Dc, auto Nc) -> int {
         bicg_matvec_kernel<decltype(Dc)::value, decltype(Nc)::value>
-            <<<KRY_BLOCKS, kCellBlock, 0, st>>>(L0, x32, 1, nullptr, nullptr, s, r->kry);
+            <<<row_blocks(r), kCellBlock, 0, st>>>(L0, x32, 1, nullptr, nullptr, s, r->kry);
         CPIC_CHECK_LAUNCH();
         return CPIC_OK;
     });
@@ -1477,8 +1489,8 @@ int enqueue_epilogue(cpic_run* r) {
 }  // namespace
 
 int mg_setup(cpic_run* r) {
-    int* flag = reinterpret_cast<int*>(r->red + 3 * RED_BLOCKS + 4);
-    unsigned* cmax = reinterpret_cast<unsigned*>(r->red + 3 * RED_BLOCKS + 6);
+    int* flag = reinterpret_cast<int*>(r->red + 3 * KRY_BLOCKS + 4);
+    unsigned* cmax = reinterpret_cast<unsigned*>(r->red + 3 * KRY_BLOCKS + 6);
     r->pc_face_only = 0;
     for (int l = 0; l < r->nlevels; ++l) {
         Level& Lv = r->lev[l];
