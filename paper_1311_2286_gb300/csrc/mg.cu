@@ -255,51 +255,59 @@ __device__ __forceinline__ void restrict_at(const LV<R>& F, const LV<R>& Cl, con
     Cl.x[C] = R(0);
 }
 
-template <typename R>
-__device__ __forceinline__ R coarse_value(const LV<R>& Cl, int* q) {
-    R sign = R(1);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (a >= Cl.D) break;
-        if (q[a] < 0 || q[a] >= Cl.n[a]) {
-            int side = q[a] < 0 ? 0 : 1;
-            if (Cl.per[a]) {
-                q[a] = q[a] < 0 ? q[a] + Cl.n[a] : q[a] - Cl.n[a];
-            } else {
-                q[a] = side == 0 ? 0 : Cl.n[a] - 1;
-                if (Cl.bc[2 * a + side] == CPIC_BC_DIRICHLET) sign = -sign;
-            }
-        }
-    }
-    return sign * Cl.x[lin(Cl, q)];
-}
-
+// Prolongation x_f += sum over the 2^D parents of w * x_parent: per axis the fine cell's own
+// parent (weight own, 3/4 when bilinear) and the parent on the fine cell's side (1 - own,
+// with the correction's ghost rules: periodic wrap, or else the boundary parent itself, its
+// sign flipped at a Dirichlet face). The per-axis offsets, signs
+// and weights are set up once and combined per parent: w = ((1 w_0) w_1) w_2 and the signed
+// parent value, accumulated over the parents in order.
 template <int D, typename R>
 __device__ __forceinline__ void prolong_at(const LV<R>& F, const LV<R>& Cl, const int* q) {
-    const int p[3] = {q[0] >> 1, q[1] >> 1, q[2] >> 1};
-    const int s[3] = {(q[0] & 1) ? 1 : -1, (q[1] & 1) ? 1 : -1, (q[2] & 1) ? 1 : -1};
     const int f = q[0] + F.n[0] * (q[1] + F.n[1] * q[2]);
     R own[3] = {R(0.75), R(0.75), R(0.75)};  // weight of the own parent per axis (bilinear: 3/4)
     if (F.pw)
 #pragma unroll
         for (int a = 0; a < D; ++a) own[a] = F.pw[a * F.ncell + f];
+    int off[3][2];
+    R sg[3][2], wt[3][2];
+    int stride = 1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const int pa = q[a] >> 1;
+        int nb = pa + ((q[a] & 1) ? 1 : -1);
+        R sign = R(1);
+        if (nb < 0 || nb >= Cl.n[a]) {
+            const int side = nb < 0 ? 0 : 1;
+            if (Cl.per[a]) {
+                nb = nb < 0 ? nb + Cl.n[a] : nb - Cl.n[a];
+            } else {
+                nb = side == 0 ? 0 : Cl.n[a] - 1;
+                if (Cl.bc[2 * a + side] == CPIC_BC_DIRICHLET) sign = -sign;
+            }
+        }
+        off[a][0] = pa * stride;
+        off[a][1] = nb * stride;
+        sg[a][0] = R(1);
+        sg[a][1] = sign;
+        wt[a][0] = own[a];
+        wt[a][1] = R(1) - own[a];
+        stride *= Cl.n[a];
+    }
     R acc = R(0);
 #pragma unroll
     for (int o = 0; o < (D == 2 ? 4 : 8); ++o) {
-        R w = R(1);
-        int qq[3] = {p[0], p[1], D == 3 ? p[2] : 0};
+        R w = R(1), sign = R(1);
+        int idx = 0;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            if ((o >> a) & 1) {
-                qq[a] += s[a];
-                w *= R(1) - own[a];
-            } else {
-                w *= own[a];
-            }
+            const int bit = (o >> a) & 1;
+            w *= wt[a][bit];
+            sign *= sg[a][bit];
+            idx += off[a][bit];
         }
-        acc += w * coarse_value(Cl, qq);
+        acc += w * (sign * Cl.x[idx]);
     }
-    F.x[q[0] + F.n[0] * (q[1] + F.n[1] * q[2])] += acc;
+    F.x[f] += acc;
 }
 
 // ------------------------------------------------------------------ line relaxation
