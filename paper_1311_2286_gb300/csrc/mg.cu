@@ -579,10 +579,36 @@ __global__ void smooth_kernel(LV<float> L, const float* __restrict__ dinv, int c
 }
 
 template <int D, int NPT>
-__global__ void restrict_kernel(LV<float> F, LV<float> Cl) {
-    int q[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(blockIdx.y * blockDim.y + threadIdx.y), (int)blockIdx.z};
-    if (q[0] >= Cl.n[0] || q[1] >= Cl.n[1] || q[2] >= Cl.n[2]) return;
-    restrict_at<D, NPT>(F, Cl, q);
+__global__ void __launch_bounds__(256) restrict_kernel(LV<float> F, LV<float> Cl) {
+    // one thread per fine cell (block RB_X x RB_Y x RB_Z fine cells): its residual goes to
+    // shared memory, then one thread per coarse cell of the block sums its 2^D children in
+    // restrict_at's order (children ch = 0 .. 2^D - 1, axis 0 fastest)
+    constexpr int BX = 32, BY = D == 3 ? 4 : 8, BZ = D == 3 ? 2 : 1;
+    __shared__ float rs[BX * BY * BZ];
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int t = tx + BX * (ty + BY * tz);
+    int q[3] = {(int)blockIdx.x * BX + tx, (int)blockIdx.y * BY + ty, D == 3 ? (int)blockIdx.z * BZ + tz : 0};
+    float r = 0.0f;
+    if (q[0] < F.n[0] && q[1] < F.n[1] && q[2] < F.n[2]) {
+        const int f = q[0] + F.n[0] * (q[1] + F.n[1] * q[2]);
+        r = F.b[f] - stencil_sum<D, NPT, 0>(F, f, q);
+    }
+    rs[t] = r;
+    __syncthreads();
+    constexpr int CX = BX / 2, CY = BY / 2, CZ = D == 3 ? BZ / 2 : 1;
+    if (t < CX * CY * CZ) {
+        const int ci = t % CX, cj = (t / CX) % CY, ck = t / (CX * CY);
+        const int qc[3] = {(int)blockIdx.x * CX + ci, (int)blockIdx.y * CY + cj, D == 3 ? (int)blockIdx.z * CZ + ck : 0};
+        if (qc[0] < Cl.n[0] && qc[1] < Cl.n[1] && qc[2] < Cl.n[2]) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int ch = 0; ch < (D == 2 ? 4 : 8); ++ch)
+                acc += rs[(2 * ci + (ch & 1)) + BX * ((2 * cj + ((ch >> 1) & 1)) + BY * (D == 3 ? 2 * ck + ((ch >> 2) & 1) : 0))];
+            const int C = qc[0] + Cl.n[0] * (qc[1] + Cl.n[1] * qc[2]);
+            Cl.b[C] = acc;
+            Cl.x[C] = 0.0f;
+        }
+    }
 }
 
 template <int D>
@@ -1354,7 +1380,11 @@ int enqueue_vcycle(cpic_run* r, const LVSet& S) {
                     if (int e = smooth(l, col)) return e;
             }
             const LV<float>& C = S.l[l + 1];
-            restrict_kernel<D, NPT><<<cell_grid(C.n[0], C.n[1], C.n[2]), kCellBlock, 0, st>>>(S.l[l], C);
+            const LV<float>& Fl = S.l[l];
+            const dim3 rb(32, D == 3 ? 4 : 8, D == 3 ? 2 : 1);
+            const dim3 rg((unsigned)((Fl.n[0] + 31) / 32), (unsigned)((Fl.n[1] + rb.y - 1) / rb.y),
+                          (unsigned)(D == 3 ? (Fl.n[2] + 1) / 2 : 1));
+            restrict_kernel<D, NPT><<<rg, rb, 0, st>>>(Fl, C);
             CPIC_CHECK_LAUNCH();
         }
         size_t smem = cta_smem_bytes(S);
