@@ -924,19 +924,79 @@ __global__ void __launch_bounds__(256) bicg_matvec_kernel(LV<float> L, const flo
     __shared__ bool last;
     double d0 = 0.0, d1 = 0.0, d2 = 0.0;
     const int nrows = L.n[1] * L.n[2];
-    for (int row = blockIdx.x * blockDim.y + threadIdx.y; row < nrows; row += gridDim.x * blockDim.y) {
-        int j = row % L.n[1], k = row / L.n[1];
-        for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
-            int q[3] = {i, j, k};
-            int c = i + L.n[0] * row;
-            const double y = (double)stencil_apply<D, NPT>(L, x32, c, q);
-            if (mode == 0) {
-                v[c] = y;
-                ph32[c] = x32[c];
-                d0 += w[c] * y;  // w = r^
-            } else {
-                d0 += y * w[c];  // w = s
-                d1 += y * y;
+    // one cell's product and its contributions to the reductions
+    auto emit = [&](int c, float yf) {
+        const double y = (double)yf;
+        if (mode == 0) {
+            v[c] = y;
+            ph32[c] = x32[c];
+            d0 += w[c] * y;  // w = r^
+        } else {
+            d0 += y * w[c];  // w = s
+            d1 += y * y;
+        }
+    };
+    if (L.n[0] % 4 == 0) {
+        // four consecutive cells along axis 0 per thread: each stencil entry of the four is one
+        // 16-byte load, and a neighbour row's four values one 16-byte load plus the value
+        // beyond the end the shifted entries need; the per-cell sums are stencil_apply's
+        const int n0 = L.n[0], q4 = n0 / 4;
+        for (int row = blockIdx.x * blockDim.y + threadIdx.y; row < nrows; row += gridDim.x * blockDim.y) {
+            const int j = row % L.n[1], k = row / L.n[1];
+            int lo[3], hi[3];
+            const int qq[3] = {0, j, k};
+#pragma unroll
+            for (int a = 1; a < D; ++a) {
+                lo[a] = qq[a] > 0 ? qq[a] - 1 : (L.per[a] ? L.n[a] - 1 : 0);
+                hi[a] = qq[a] + 1 < L.n[a] ? qq[a] + 1 : (L.per[a] ? 0 : L.n[a] - 1);
+            }
+            const int jy[3] = {n0 * lo[1], n0 * j, n0 * hi[1]};
+            int kz[3] = {0, 0, 0};
+            if (D == 3) {
+                const int pl = n0 * L.n[1];
+                kz[0] = pl * lo[2];
+                kz[1] = pl * k;
+                kz[2] = pl * hi[2];
+            }
+            for (int g = threadIdx.x; g < q4; g += blockDim.x) {
+                const int i0 = 4 * g;
+                const int il = i0 > 0 ? i0 - 1 : (L.per[0] ? n0 - 1 : 0);
+                const int ir = i0 + 4 < n0 ? i0 + 4 : (L.per[0] ? 0 : n0 - 1);
+                const int c = i0 + n0 * row;
+                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int e = 0; e < NPT; ++e) {
+                    const int dx = koff(D, e, 0);
+                    const int rb = jy[koff(D, e, 1) + 1] + (D == 3 ? kz[koff(D, e, 2) + 1] : 0);
+                    const float4 xm = *reinterpret_cast<const float4*>(x32 + rb + i0);
+                    float xs[4];
+                    if (dx == 0) {
+                        xs[0] = xm.x, xs[1] = xm.y, xs[2] = xm.z, xs[3] = xm.w;
+                    } else if (dx < 0) {
+                        // cell i0's left neighbour: wrapped, or i0 itself at a closed face
+                        xs[0] = i0 > 0 || L.per[0] ? x32[rb + il] : xm.x;
+                        xs[1] = xm.x, xs[2] = xm.y, xs[3] = xm.z;
+                    } else {
+                        xs[0] = xm.y, xs[1] = xm.z, xs[2] = xm.w;
+                        xs[3] = i0 + 4 < n0 || L.per[0] ? x32[rb + ir] : xm.w;
+                    }
+                    const float4 a4 = *reinterpret_cast<const float4*>(L.A + (size_t)e * L.ncell + c);
+                    acc[0] += a4.x * xs[0];
+                    acc[1] += a4.y * xs[1];
+                    acc[2] += a4.z * xs[2];
+                    acc[3] += a4.w * xs[3];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) emit(c + u, acc[u]);
+            }
+        }
+    } else {
+        for (int row = blockIdx.x * blockDim.y + threadIdx.y; row < nrows; row += gridDim.x * blockDim.y) {
+            int j = row % L.n[1], k = row / L.n[1];
+            for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
+                int q[3] = {i, j, k};
+                int c = i + L.n[0] * row;
+                emit(c, stencil_apply<D, NPT>(L, x32, c, q));
             }
         }
     }
