@@ -218,7 +218,7 @@ void plan(cpic_run* r, Planner& P) {
     r->ctr = P.take<DevCounters>(1);
     r->red = P.take<double>(3 * KRY_BLOCKS + 16);
     r->kry = P.take<KrylovState>(1);
-    r->kv = P.take<double>((size_t)5 * r->ncell);
+    r->kv = P.take<double>((size_t)2 * r->ncell + ((size_t)3 * r->ncell + 1) / 2);  // r, r^; FP32 p, v, s
     r->ph32 = P.take<float>(r->ncell);
     r->hist = P.take<int>((size_t)c.n_species * r->ncell);
     r->scan = P.take<long long>((size_t)c.n_species * r->ncell + 1);

@@ -34,11 +34,12 @@
 // s = r - alpha v; s^ = V(s); t = M s^, omega = (t, s) / (t, t); phi += alpha p^ + omega s^;
 // then r = b - M phi is recomputed in FP64 (not updated), so the stopping test sees the true
 // residual, and rho' = (r^, r), beta = (rho' / rho)(alpha / omega). A vanishing rho, alpha
-// or omega restarts the recurrence with r^ = p = r. The products M p^ and M s^ only choose
-// the step lengths alpha and omega: they are FP32 (the FP32 copy of the full operator, on
-// the FP32 preconditioned vectors; FP64 on GB300 runs at 1/64 of the FP32 rate), while phi
-// is only ever changed by FP64 additions of those vectors and the stopping test reads the
-// FP64 residual, so the result's accuracy does not depend on them.
+// or omega restarts the recurrence with r^ = p = r. The direction vectors p, v, s and the
+// products M p^ and M s^ only choose the search space and the step lengths alpha and omega:
+// they are FP32 (the products with the FP32 copy of the full operator; FP64 on GB300 runs at
+// 1/64 of the FP32 rate), while phi is only ever changed by FP64 additions of FP32 steps
+// and the stopping test reads the FP64 residual, so the result's accuracy does not depend
+// on them; the dot products accumulate in FP64.
 //
 // The residual kernel ends with a last-block reduction that decides whether to continue;
 // it writes the decision into a CUDA graph conditional handle, so inside a captured step
@@ -894,32 +895,34 @@ __global__ void update_kernel(double* phi, const float* e, int n) {
 
 // ---- BiCGStab steps (the scalars live in KrylovState; see the header comment)
 
-// p = r + beta (p - omega v), or p = r^ = r on a restart; the V-cycle's right-hand side float(p)
-__global__ void bicg_direction_kernel(int n, const double* __restrict__ r, double* rh, double* p, const double* v,
+// p = r + beta (p - omega v), or p = r^ = r on a restart; p is also the V-cycle's right-hand
+// side. The direction vectors p, v and s are FP32 (they only shape the Krylov space: the
+// residual and phi stay FP64), which keeps these passes off GB300's FP64 units.
+__global__ void bicg_direction_kernel(int n, const double* __restrict__ r, double* rh, float* p, const float* v,
                                       float* b32, const KrylovState* ks) {
-    const double beta = ks->beta, omega = ks->omega;
+    const float beta = (float)ks->beta, omega = (float)ks->omega;
     const bool restart = ks->restart != 0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        double pc;
+        float pc;
         if (restart) {
             rh[c] = r[c];
-            pc = r[c];
+            pc = (float)r[c];
         } else {
-            pc = r[c] + beta * (p[c] - omega * v[c]);
+            pc = (float)r[c] + beta * (p[c] - omega * v[c]);
         }
         p[c] = pc;
-        b32[c] = (float)pc;
+        b32[c] = pc;
     }
 }
 
 // y = M x32 over the finest level with the FP32 copy of the full operator (every stencil
 // entry; on GB300 an FP64 product is bound by the FP64 rate, at about a third of the memory
-// rate), stored and reduced in FP64; mode 0: v = y, p^ = x32 kept, reduce (r^, v) ->
+// rate), reduced in FP64; mode 0: v = y, p^ = x32 kept, reduce (r^, v) ->
 // alpha = rho / (r^, v); mode 1: reduce (y, s), (y, y) -> omega = (t, s) / (t, t)
 template <int D, int NPT>
 __global__ void __launch_bounds__(256) bicg_matvec_kernel(LV<float> L, const float* __restrict__ x32, int mode,
-                                                           double* v, float* ph32, const double* __restrict__ w,
-                                                           KrylovState* ks) {
+                                                           float* v, float* ph32, const double* __restrict__ wr,
+                                                           const float* __restrict__ ws, KrylovState* ks) {
     __shared__ double sh[96];
     __shared__ bool last;
     double d0 = 0.0, d1 = 0.0, d2 = 0.0;
@@ -928,11 +931,11 @@ __global__ void __launch_bounds__(256) bicg_matvec_kernel(LV<float> L, const flo
     auto emit = [&](int c, float yf) {
         const double y = (double)yf;
         if (mode == 0) {
-            v[c] = y;
+            v[c] = yf;
             ph32[c] = x32[c];
-            d0 += w[c] * y;  // w = r^
+            d0 += wr[c] * y;  // r^
         } else {
-            d0 += y * w[c];  // w = s
+            d0 += y * (double)ws[c];  // s
             d1 += y * y;
         }
     };
@@ -1031,23 +1034,23 @@ __global__ void __launch_bounds__(256) bicg_matvec_kernel(LV<float> L, const flo
     }
 }
 
-// s = r - alpha v; the V-cycle's right-hand side float(s)
-__global__ void bicg_s_kernel(int n, const double* __restrict__ r, const double* __restrict__ v, double* s,
+// s = r - alpha v (FP32), also the V-cycle's right-hand side
+__global__ void bicg_s_kernel(int n, const double* __restrict__ r, const float* __restrict__ v, float* s,
                               float* b32, const KrylovState* ks) {
-    const double alpha = ks->alpha;
+    const float alpha = (float)ks->alpha;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        const double sc = r[c] - alpha * v[c];
+        const float sc = (float)r[c] - alpha * v[c];
         s[c] = sc;
-        b32[c] = (float)sc;
+        b32[c] = sc;
     }
 }
 
-// phi += alpha p^ + omega s^
+// phi += alpha p^ + omega s^: the step formed in FP32, added to phi in FP64
 __global__ void bicg_update_kernel(int n, double* phi, const float* __restrict__ ph32, const float* __restrict__ sh32,
                                    const KrylovState* ks) {
-    const double alpha = ks->alpha, omega = ks->omega;
+    const float alpha = (float)ks->alpha, omega = (float)ks->omega;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
-        phi[c] += alpha * (double)ph32[c] + omega * (double)sh32[c];
+        phi[c] += (double)(alpha * ph32[c] + omega * sh32[c]);
 }
 
 // mode 1: (sum b, -); mode 2: (sum J phi, -)
@@ -1518,9 +1521,9 @@ int enqueue_bicg_iteration(cpic_run* r, const LVSet& S, double rtol, int max_cyc
     const int n = (int)r->ncell;
     double* rv = r->kv;
     double* rh = r->kv + r->ncell;
-    double* p = r->kv + 2 * r->ncell;
-    double* v = r->kv + 3 * r->ncell;
-    double* s = r->kv + 4 * r->ncell;
+    float* p = reinterpret_cast<float*>(r->kv + 2 * r->ncell);  // FP32 p, v, s after r, r^
+    float* v = p + r->ncell;
+    float* s = v + r->ncell;
     float* b32 = r->lev[0].b32;
     float* x32 = r->lev[0].x32;
     cudaStream_t st = r->stream;
@@ -1532,7 +1535,7 @@ int enqueue_bicg_iteration(cpic_run* r, const LVSet& S, double rtol, int max_cyc
     LV<float> L0 = make_lv<float>(r, 0, true);  // A32 holds every entry of the operator
     e = dispatch_shape(r, [&](auto Dc, auto Nc) -> int {
         bicg_matvec_kernel<decltype(Dc)::value, decltype(Nc)::value>
-            <<<row_blocks(r), kCellBlock, 0, st>>>(L0, x32, 0, v, r->ph32, rh, r->kry);
+            <<<row_blocks(r), kCellBlock, 0, st>>>(L0, x32, 0, v, r->ph32, rh, nullptr, r->kry);
         CPIC_CHECK_LAUNCH();
         return CPIC_OK;
     });
@@ -1543,7 +1546,7 @@ int enqueue_bicg_iteration(cpic_run* r, const LVSet& S, double rtol, int max_cyc
     if (e) return e;
     e = dispatch_shape(r, [&](auto Dc, auto Nc) -> int {
         bicg_matvec_kernel<decltype(Dc)::value, decltype(Nc)::value>
-            <<<row_blocks(r), kCellBlock, 0, st>>>(L0, x32, 1, nullptr, nullptr, s, r->kry);
+            <<<row_blocks(r), kCellBlock, 0, st>>>(L0, x32, 1, nullptr, nullptr, nullptr, s, r->kry);
         CPIC_CHECK_LAUNCH();
         return CPIC_OK;
     });
