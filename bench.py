@@ -259,7 +259,11 @@ def sphere_measurement(cpic, npart, steps, warmup, full_steps, stream, flush, e2
     kname = ("push3d_kernel<absorb,reflect,periodic> (fused gather/push/boundary, shared-tile deposit, 3D)" if tiled
              else "push3d_direct_kernel<absorb,reflect,periodic> (fused gather/push/boundary, per-warp deposit "
                   "transposition, 3D)")
-    roof = roofline(push_ms, pp, B3, peak, kind, profiled_traffic(PROFILE3, SRC3, pp), kname)
+    # with the direct kernel the sort leaves its gather to the next push, which then also reads
+    # each particle's 4-byte source index: 4 / S bytes more per particle-step on average
+    sint = tuning.get("sort_interval", 0) if isinstance(tuning, dict) else 0
+    bpp = B3 + (4.0 / sint if (not tiled and sint > 0) else 0.0)
+    roof = roofline(push_ms, pp, bpp, peak, kind, profiled_traffic(PROFILE3, SRC3, pp), kname)
     run.step(1)
     full_ms, full_ps, cyc = timed_steps(run, full_steps, lambda: run.step(1), flush, stream)
     e2e = end_to_end(run, cpic, e2e_steps) if e2e_steps > 0 else None
@@ -321,10 +325,48 @@ def cylinder_measurement(cpic, n1, n2, npart, steps, warmup, full_steps, stream,
     return out
 
 
+def gpu_local_cpus(dev):
+    """The CPUs of the GPU's own NUMA node (the local_cpulist of its PCI function) that this
+    process may run on, or None when that is unknown or no narrower than its affinity."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(dev), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout.strip().splitlines()[0]
+        dom, rest = out.split(":", 1)
+        bus = "%04x:%s" % (int(dom, 16), rest.lower())
+        with open("/sys/bus/pci/devices/%s/local_cpulist" % bus) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        have = os.sched_getaffinity(0)
+        cpus &= have
+        return cpus if cpus and cpus != have else None
+    except Exception:
+        return None
+
+
 def end_to_end(run, cpic, steps):
     """The value's metric through the public API with host buffers (pinned), copies
     included: per step, cpic_load_particles from host, cpic_step_particles,
-    cpic_get_particles into host, cpic_get_diag."""
+    cpic_get_particles into host, cpic_get_diag. The host side runs on the GPU's own NUMA
+    node when the system says which one that is (the pinned buffers are allocated there)."""
+    import torch
+
+    saved = os.sched_getaffinity(0)
+    local_cpus = gpu_local_cpus(torch.cuda.current_device())
+    if local_cpus:
+        os.sched_setaffinity(0, local_cpus)
+    try:
+        out = _end_to_end(run, cpic, steps)
+    finally:
+        os.sched_setaffinity(0, saved)
+    out["host_cpus"] = ("%d of %d cores, the GPU's NUMA node" % (len(local_cpus), len(saved)) if local_cpus
+                        else "process affinity (%d cores)" % len(saved))
+    return out
+
+
+def _end_to_end(run, cpic, steps):
     import ctypes
 
     import torch

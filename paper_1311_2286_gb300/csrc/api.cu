@@ -616,7 +616,7 @@ int enqueue_step_post(cpic_run* r, bool sort, bool fold) {
     return st;
 }
 
-int enqueue_step(cpic_run* r, bool sort, bool fold) {
+int enqueue_step(cpic_run* r, bool sort, bool fold, bool fused_sort = false) {
     int st = launch_vertex_field(r);
     if (st) return st;
     st = launch_push(r);
@@ -628,7 +628,7 @@ int enqueue_step(cpic_run* r, bool sort, bool fold) {
         if (st) return st;
     }
     if (sort) {
-        st = launch_sort(r);
+        st = launch_sort(r, fused_sort);
         if (st) return st;
     }
     return CPIC_OK;
@@ -669,7 +669,13 @@ int build_step_graph(cpic_run* r, int with_solve, int with_sort) {
         r->stream = saved;
         return cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
     }
-    st = enqueue_step(r, with_sort != 0, with_solve != 0);
+    // the graph is replayed in any order state: its push reads the device flag, and the host
+    // flag is managed around each replay (step_once), not by what capture enqueues
+    const bool pending = r->order_pending;
+    r->order_pending = false;
+    const bool fused = with_sort != 0 && push3d_fused_ok(r);
+    st = enqueue_step(r, with_sort != 0, with_solve != 0, fused);
+    r->order_pending = pending;
     if (!st && with_solve) {
         cudaStreamCaptureStatus cs;
         cudaGraph_t cg = nullptr;
@@ -697,11 +703,15 @@ int build_step_graph(cpic_run* r, int with_solve, int with_sort) {
     r->step_graph[with_solve][with_sort] = ex;
     r->step_graph_ok[with_solve][with_sort] = true;
     r->graph_kernels[with_solve][with_sort] = nk;
+    r->graph_sort_fused[with_solve][with_sort] = fused;
     return CPIC_OK;
 }
 
 int step_once(cpic_run* r, bool solve) {
     bool sort = r->cfg.sort_interval > 0 && r->steps_since_sort + 1 >= r->cfg.sort_interval;
+    if (r->order_pending && !push3d_fused_ok(r)) {
+        if (int e = resolve_order(r)) return e;
+    }
     if (!r->profiling) {
         const int wi = sort ? 1 : 0, ws = solve ? 1 : 0;
         if (!r->step_graph_ok[ws][wi]) {
@@ -710,6 +720,8 @@ int step_once(cpic_run* r, bool solve) {
         }
         CPIC_CUDA(cudaGraphLaunch(r->step_graph[ws][wi], r->stream));
         g_launches.fetch_add(r->graph_kernels[ws][wi], std::memory_order_relaxed);
+        // the replay's push took any pending order; a fused sort at its end leaves a new one
+        r->order_pending = sort && r->graph_sort_fused[ws][wi];
         ++r->steps_since_sort;
         if (sort) {
             r->cur_host ^= 1;
@@ -733,7 +745,7 @@ int step_once(cpic_run* r, bool solve) {
     });
     if (st) return st;
     if (r->cfg.sort_interval > 0 && ++r->steps_since_sort >= r->cfg.sort_interval) {
-        st = phase(r, CPIC_PHASE_SORT, [&] { return launch_sort(r); });
+        st = phase(r, CPIC_PHASE_SORT, [&] { return launch_sort(r, push3d_fused_ok(r)); });
         if (st) return st;
         r->cur_host ^= 1;
         r->steps_since_sort = 0;
@@ -845,6 +857,7 @@ int cpic_set_multigrid(cpic_run* r, int coarse, int interpolation, int smoother)
 
 int cpic_set_push_tuning(cpic_run* r, int chunk, int tile) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     if (chunk < 0 || chunk > (1 << 20) || (chunk % 256) != 0 || (tile != 0 && tile != 1)) {
         set_error("set_push_tuning: chunk must be 0 or a multiple of 256 up to 2^20, tile 0 or 1 (got %d, %d)", chunk,
                   tile);
@@ -953,6 +966,7 @@ int cpic_set_stream(cpic_run* r, void* stream) {
 
 int cpic_set_map_vertices(cpic_run* r, const double* xyz) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     if (!xyz) {
         set_error("xyz is NULL");
         return CPIC_ERR_INVALID;
@@ -963,6 +977,7 @@ int cpic_set_map_vertices(cpic_run* r, const double* xyz) {
 
 int cpic_set_map_analytic(cpic_run* r, int map_id, const double* params, int nparams) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     int need = map_id == CPIC_MAP_SHELL ? 3 : (map_id == CPIC_MAP_SINE ? 1 : 2);
     bool dim_ok = map_id == CPIC_MAP_SHELL ? r->D == 3 : r->D == 2;
     if (map_id < CPIC_MAP_SINE || map_id > CPIC_MAP_SHELL || !dim_ok || !params || nparams < need) {
@@ -976,6 +991,7 @@ int cpic_set_map_analytic(cpic_run* r, int map_id, const double* params, int npa
 
 int cpic_load_particles(cpic_run* r, int sp, int64_t n, const int32_t* cell, const float* t, const float* v) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     if (sp < 0 || sp >= r->cfg.n_species || n < 0 || n > r->pb.capacity[sp] || (n > 0 && (!cell || !t || !v))) {
         set_error("load_particles: bad species, count or pointers (n = %lld, capacity = %lld)", (long long)n,
                   sp >= 0 && sp < CPIC_MAX_SPECIES ? (long long)r->pb.capacity[sp] : -1ll);
@@ -1008,6 +1024,7 @@ int cpic_load_particles(cpic_run* r, int sp, int64_t n, const int32_t* cell, con
 
 int cpic_load_maxwellian(cpic_run* r, int sp, int64_t n, double vth, const double* drift, uint64_t seed) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     CHECK_MAP(r);
     if (sp < 0 || sp >= r->cfg.n_species || n < 0 || n > r->pb.capacity[sp] || !(vth >= 0.0)) {
         set_error("load_maxwellian: bad species, count (n = %lld) or vth", (long long)n);
@@ -1018,6 +1035,7 @@ int cpic_load_maxwellian(cpic_run* r, int sp, int64_t n, double vth, const doubl
 
 int cpic_get_particles(cpic_run* r, int sp, int64_t room, int64_t* n, int32_t* cell, float* t, float* v) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     if (sp < 0 || sp >= r->cfg.n_species || !n) {
         set_error("get_particles: bad species or NULL count");
         return CPIC_ERR_INVALID;
@@ -1078,6 +1096,7 @@ int cpic_get_particles(cpic_run* r, int sp, int64_t room, int64_t* n, int32_t* c
 
 int cpic_set_magnetic_field(cpic_run* r, const double* B) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     double b[3] = {0.0, 0.0, 0.0};
     if (B)
         for (int a = 0; a < 3; ++a) b[a] = B[a];
@@ -1098,6 +1117,7 @@ int cpic_set_magnetic_field(cpic_run* r, const double* B) {
 
 int cpic_set_gyro_integrator(cpic_run* r, int kind) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     if (kind != CPIC_GYRO_BORIS && kind != CPIC_GYRO_CYCLOTRONIC) {
         set_error("set_gyro_integrator: CPIC_GYRO_BORIS or CPIC_GYRO_CYCLOTRONIC");
         return CPIC_ERR_INVALID;
@@ -1208,6 +1228,7 @@ int cpic_set_injection(cpic_run* r, int sp, int face, double density, double vth
 
 int cpic_initialize(cpic_run* r) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     CHECK_MAP(r);
     int st = launch_deposit(r);
     if (!st) st = launch_fold(r);
@@ -1257,6 +1278,7 @@ int cpic_push(cpic_run* r) {
 
 int cpic_deposit(cpic_run* r) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     CHECK_MAP(r);
     int st = launch_deposit(r);
     return st ? st : launch_fold(r);
@@ -1264,12 +1286,14 @@ int cpic_deposit(cpic_run* r) {
 
 int cpic_kick(cpic_run* r, double fraction) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     CHECK_MAP(r);
     return launch_kick(r, fraction);
 }
 
 int cpic_inject(cpic_run* r) {
     CHECK_RUN(r);
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     CHECK_MAP(r);
     int st = launch_inject(r);
     return st ? st : launch_fold(r);

@@ -256,7 +256,9 @@ int cpic_batch_add(cpic_batch* b, cpic_run* r) {
         cudaStreamDestroy(s);
         return cuda_fail(e, "cudaEventCreate(join)", __FILE__, __LINE__);
     }
-    // the run's earlier work (load, initialise) is on its own stream: order the batch after it
+    // the run's earlier work (load, initialise, a pending sort order, which the batch's
+    // kernels do not read through) is on its own stream: order the batch after it
+    if (int st = resolve_order(r)) return st;
     CPIC_CUDA(cudaStreamSynchronize(r->stream));
     b->runs.push_back(r);
     b->branch.push_back(s);
@@ -316,6 +318,11 @@ int cpic_batch_step(cpic_batch* b, int nsteps, int with_solve) {
         return CPIC_ERR_INVALID;
     }
     if (b->runs.empty()) return CPIC_OK;
+    for (cpic_run* r : b->runs)  // a member stepped alone since it joined
+        if (r->order_pending) {
+            if (int st = resolve_order(r)) return st;
+            CPIC_CUDA(cudaStreamSynchronize(r->stream));
+        }
     for (int k = 0; k < nsteps; ++k) {
         std::string key(b->runs.size(), '0');
         for (size_t i = 0; i < b->runs.size(); ++i) {

@@ -62,6 +62,11 @@ struct DevCounters {
     double object_potential;
     double object_charge;
     double float_cpsi;
+    // 1: a sort's new order is pending: slot i of the other buffer's cell array holds the
+    // index (in the current buffer) of the particle that belongs in slot i, and the counts
+    // are already the sorted ones; the next fused 3D push reads through it and the step's
+    // finalisation flips the buffers (see launch_sort)
+    int perm;
 };
 
 // Scalars and reduction partials of the Krylov solve (device).
@@ -194,8 +199,10 @@ struct cpic_run {
     cudaGraphExec_t step_graph[2][2];  // [with field solve][with sort]
     bool step_graph_ok[2][2];
     int graph_kernels[2][2];           // kernel nodes launched by one replay
+    bool graph_sort_fused[2][2];       // the graph's sort leaves its order to the next push
     cudaStream_t capture_stream;
     int cluster_cs;              // cluster size of the cluster solver (0: not applicable)
+    bool order_pending;          // a fused sort's order may be pending on the device (DevCounters::perm)
     int dense_m;                 // coarsest unknowns (+1 row when singular)
     bool singular;
     double sumJ;                 // sum of finest J_c (singular projection)
@@ -277,7 +284,13 @@ int launch_load_maxwellian(cpic_run* r, int sp, long long n, double vth, const d
 // inject.cu
 int launch_inject(cpic_run* r);
 // sort.cu
-int launch_sort(cpic_run* r);
+// the cell sort; fused: leave the reordering to the next push (push3d's direct kernel reads
+// through the pending order; only when push3d_fused_ok), else gather now
+int launch_sort(cpic_run* r, bool fused = false);
+// carry out a pending sort order (gather; a no-op when none is pending): before anything
+// other than a fused 3D push touches the particles
+int resolve_order(cpic_run* r);
+bool push3d_fused_ok(const cpic_run* r);
 // mg.cu
 int mg_setup(cpic_run* r);
 int mg_solve(cpic_run* r, double rtol, int max_cycles, bool host_loop, int* cycles, double* res);

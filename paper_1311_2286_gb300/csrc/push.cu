@@ -432,8 +432,15 @@ __global__ void fold_kernel(FoldParams f) {
     }
 }
 
+// step count; a push that read through a pending sort order wrote the other buffer: flip
 __global__ void finalize_step_kernel(DevCounters* ctr) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) ctr->step += 1;
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        ctr->step += 1;
+        if (ctr->perm) {
+            ctr->cur = 1 - ctr->cur;
+            ctr->perm = 0;
+        }
+    }
 }
 
 }  // namespace
@@ -554,6 +561,15 @@ int launch_push_prep(cpic_run* r) {
 }
 
 int launch_push_kernel(cpic_run* r) {
+    // a pending sort order: the direct 3D kernel reads through it (its finalisation flips the
+    // buffers); any other kernel needs the particles gathered first
+    if (r->order_pending) {
+        if (push3d_fused_ok(r)) {
+            r->order_pending = false;
+        } else if (int e = resolve_order(r)) {
+            return e;
+        }
+    }
     // the specialised 2D kernel covers periodic and absorbing axes; reflecting ones take the
     // generic kernel
     bool reflect = false;

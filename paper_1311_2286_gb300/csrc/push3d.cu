@@ -627,6 +627,11 @@ __global__ void __launch_bounds__(PD_THREADS, 4) push3d_direct_kernel(PushParams
     __shared__ int sh_gone[8];  // removed particles of the chunk per face (6: non-finite)
     const DevCounters* ctr = p.ctr;
     const int cur = ctr->cur;
+    // a fused sort left its order pending: slot i of the other buffer's cell array holds the
+    // current-buffer index of the particle that belongs in slot i; read it from there and
+    // write the pushed state to slot i of the other buffer (the step's finalisation flips)
+    const bool perm = ctr->perm != 0;
+    const int dst = perm ? 1 - cur : cur;
     const int nsp = p.nsp;
     int cnt[CPIC_MAX_SPECIES];
     int total = 0;
@@ -654,9 +659,12 @@ __global__ void __launch_bounds__(PD_THREADS, 4) push3d_direct_kernel(PushParams
         const int lo = local * C;
         const int hi = min(lo + C, cnt[s]);
         const long long b0 = p.pb.base[s];
-        int* __restrict__ cellp = p.pb.cell[cur] + b0;
-        float* __restrict__ tq0 = p.pb.t[cur] + b0;
-        float* __restrict__ vq0 = p.pb.v[cur] + b0;
+        const int* cellp = p.pb.cell[cur] + b0;
+        const float* tq0 = p.pb.t[cur] + b0;
+        const float* vq0 = p.pb.v[cur] + b0;
+        int* cellq = p.pb.cell[dst] + b0;
+        float* tq1 = p.pb.t[dst] + b0;
+        float* vq1 = p.pb.v[dst] + b0;
         const float dtqm = p.dtqm[s];
         __syncthreads();  // the previous chunk's tallies are read
         if (threadIdx.x < 8) sh_gone[threadIdx.x] = 0;
@@ -667,11 +675,12 @@ __global__ void __launch_bounds__(PD_THREADS, 4) push3d_direct_kernel(PushParams
         int ncw = -1;
         float nt[3] = {0.f, 0.f, 0.f}, nv[3] = {0.f, 0.f, 0.f};
         if (i < hi) {
-            ncw = cellp[i];
+            const int src = perm ? cellq[i] : i;
+            ncw = cellp[src];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) nt[a] = tq0[a * T + i];
+            for (int a = 0; a < 3; ++a) nt[a] = tq0[a * T + src];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + i];
+            for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + src];
         }
         for (int base = lo; base < hi; base += PD_THREADS) {
             const int slot = i;
@@ -681,11 +690,12 @@ __global__ void __launch_bounds__(PD_THREADS, 4) push3d_direct_kernel(PushParams
             i += PD_THREADS;
             ncw = -1;
             if (i < hi) {
-                ncw = cellp[i];
+                const int src = perm ? cellq[i] : i;
+                ncw = cellp[src];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) nt[a] = tq0[a * T + i];
+                for (int a = 0; a < 3; ++a) nt[a] = tq0[a * T + src];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + i];
+                for (int a = 0; a < 3; ++a) nv[a] = vq0[a * T + src];
             }
             int cn[3], face;
             float tn[3], ke32;
@@ -697,8 +707,8 @@ __global__ void __launch_bounds__(PD_THREADS, 4) push3d_direct_kernel(PushParams
                 atomicAdd(&sh_gone[face], 1);
                 collect_face<3>(p, s, face, cn);
             }
-            store_state3(active, cellp + slot, alive ? (cn[0] | (cn[1] << 10) | (cn[2] << 20)) : -1, tq0 + slot,
-                         tq0 + T + slot, tq0 + 2 * T + slot, tn, vq0 + slot, vq0 + T + slot, vq0 + 2 * T + slot, v);
+            store_state3(active, cellq + slot, alive ? (cn[0] | (cn[1] << 10) | (cn[2] << 20)) : -1, tq1 + slot,
+                         tq1 + T + slot, tq1 + 2 * T + slot, tn, vq1 + slot, vq1 + T + slot, vq1 + 2 * T + slot, v);
             deposit_runs3(p, s, alive, cn, tn, wq);  // a6
         }
         ke = warp_sum_ll(ke);
@@ -771,6 +781,14 @@ int launch_push3d_t(cpic_run* r, const PushParams& p) {
 }
 
 }  // namespace
+
+// whether the 3D push the run takes is the direct kernel, which can read through a pending
+// sort order (so that the sort may leave its gather to it)
+bool push3d_fused_ok(const cpic_run* r) {
+    if (r->D != 3 || r->magnetized || r->push_tile) return false;
+    const int k0 = r->cfg.particle_bc[0], k1 = r->cfg.particle_bc[2], k2 = r->cfg.particle_bc[4];
+    return (k0 == K_ABS && k1 == K_REF && k2 == K_PER) || (k0 == K_PER && k1 == K_PER && k2 == K_PER);
+}
 
 // the specialised 3D kernel for the axis kinds it is instantiated for; CPIC_ERR_NOT_BUILT
 // for others (the caller then takes the generic kernel)

@@ -24,6 +24,7 @@ struct SortParams {
     int* hist;         // [nsp][ncell]
     long long* scan;   // [nsp * ncell + 1]
     unsigned* ticket;  // last-block counter of the gather (zero between sorts)
+    int flush;         // gather only if an order is pending (DevCounters::perm)
 };
 
 __device__ __forceinline__ long long cell_key(const SortParams& p, int cw) {
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(SC_THREADS) rank_kernel(SortParams p) {
 template <int D>
 __global__ void __launch_bounds__(256) gather_kernel(SortParams p) {
     __shared__ bool last;
+    if (p.flush && !p.ctr->perm) return;  // nothing pending (the same for every block)
     const int s = blockIdx.y;
     const long long n = p.scan[(long long)(s + 1) * p.ncell] - p.scan[(long long)s * p.ncell];
     const int cur = p.ctr->cur, nxt = 1 - cur;
@@ -366,11 +368,23 @@ __global__ void __launch_bounds__(256) gather_kernel(SortParams p) {
         p.ctr->alive[sp] = cnt;
     }
     p.ctr->cur = 1 - p.ctr->cur;
+    p.ctr->perm = 0;
 }
 
-}  // namespace
+// Fused sort: the live counts become the sorted ones and the order is left pending; the next
+// push reads slot i's particle from the index the rank pass stored in the other buffer, writes
+// it to slot i there, and the step's finalisation flips the buffers.
+__global__ void sort_fused_finish_kernel(SortParams p) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int sp = 0; sp < p.nsp; ++sp) {
+        const long long cnt = p.scan[(long long)(sp + 1) * p.ncell] - p.scan[(long long)sp * p.ncell];
+        p.ctr->count[sp] = cnt;
+        p.ctr->alive[sp] = cnt;
+    }
+    p.ctr->perm = 1;
+}
 
-int launch_sort(cpic_run* r) {
+SortParams sort_params(cpic_run* r) {
     SortParams p;
     p.D = r->D;
     for (int a = 0; a < 3; ++a) p.n[a] = a < r->D ? r->n[a] : 1;
@@ -381,6 +395,36 @@ int launch_sort(cpic_run* r) {
     p.hist = r->hist;
     p.scan = r->scan;
     p.ticket = r->ticket + 2;
+    p.flush = 0;
+    return p;
+}
+
+int launch_gather(cpic_run* r, const SortParams& p) {
+    int dev = 0, nsm = 0;
+    CPIC_CUDA(cudaGetDevice(&dev));
+    CPIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const dim3 ggrid((unsigned)(nsm * 8 / p.nsp > 0 ? nsm * 8 / p.nsp : 1), (unsigned)p.nsp);
+    if (p.D == 2)
+        gather_kernel<2><<<ggrid, 256, 0, r->stream>>>(p);
+    else
+        gather_kernel<3><<<ggrid, 256, 0, r->stream>>>(p);
+    CPIC_CHECK_LAUNCH();
+    return CPIC_OK;
+}
+
+}  // namespace
+
+int resolve_order(cpic_run* r) {
+    if (!r->order_pending) return CPIC_OK;
+    r->order_pending = false;
+    SortParams p = sort_params(r);
+    p.flush = 1;
+    return launch_gather(r, p);
+}
+
+int launch_sort(cpic_run* r, bool fused) {
+    if (int e = resolve_order(r)) return e;
+    SortParams p = sort_params(r);
     long long N = (long long)p.nsp * r->ncell;
     long long tot = 0;
     for (int s = 0; s < p.nsp; ++s) tot += r->pb.capacity[s] + 32;
@@ -405,16 +449,13 @@ int launch_sort(cpic_run* r) {
     else
         rank_kernel<3><<<(int)pblocks, 256, 0, r->stream>>>(p);
     CPIC_CHECK_LAUNCH();
-    int dev = 0, nsm = 0;
-    CPIC_CUDA(cudaGetDevice(&dev));
-    CPIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const dim3 ggrid((unsigned)(nsm * 8 / p.nsp > 0 ? nsm * 8 / p.nsp : 1), (unsigned)p.nsp);
-    if (p.D == 2)
-        gather_kernel<2><<<ggrid, 256, 0, r->stream>>>(p);
-    else
-        gather_kernel<3><<<ggrid, 256, 0, r->stream>>>(p);
-    CPIC_CHECK_LAUNCH();
-    return CPIC_OK;
+    if (fused) {
+        sort_fused_finish_kernel<<<1, 32, 0, r->stream>>>(p);
+        CPIC_CHECK_LAUNCH();
+        r->order_pending = true;
+        return CPIC_OK;
+    }
+    return launch_gather(r, p);
 }
 
 }  // namespace cpic

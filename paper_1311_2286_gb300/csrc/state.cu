@@ -93,6 +93,7 @@ int tune_trial(cpic_run* r, char* buf, int saved_cur, int trial_steps, cudaEvent
     *ms_per_step = ms / nsteps;
     if (!st) st = snapshot_copy(r, buf, false, saved_cur);  // particles back to their buffer
     r->cur_host = saved_cur;
+    r->order_pending = false;  // the snapshot was taken with the particles in slot order
     return st;
 }
 
@@ -103,6 +104,7 @@ int cpic_autotune(cpic_run* r, int trial_steps, cpic_tuning* out) {
         set_error("autotune: NULL run/out or trial_steps < 1");
         return CPIC_ERR_INVALID;
     }
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     if (!r->map_set) {
         set_error("autotune: the run has no map yet");
         return CPIC_ERR_STATE;
@@ -196,6 +198,7 @@ int cpic_checkpoint(cpic_run* r, const char* path) {
         set_error("checkpoint: NULL run or path");
         return CPIC_ERR_INVALID;
     }
+    if (int e = resolve_order(r)) return e;  // the particles in slot order
     if (!r->map_set) {
         set_error("checkpoint: the run has no map yet");
         return CPIC_ERR_STATE;
