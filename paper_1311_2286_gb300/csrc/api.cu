@@ -616,9 +616,18 @@ int enqueue_step_post(cpic_run* r, bool sort, bool fold) {
     return st;
 }
 
+// a fused sort step: the direct 3D push and the injection count the particles' new cells,
+// so the sort skips its histogram pass
+int begin_counted_step(cpic_run* r) {
+    r->count_hist = true;
+    CPIC_CUDA(cudaMemsetAsync(r->hist, 0, sizeof(int) * r->cfg.n_species * (size_t)r->ncell, r->stream));
+    return CPIC_OK;
+}
+
 int enqueue_step(cpic_run* r, bool sort, bool fold, bool fused_sort = false) {
     int st = launch_vertex_field(r);
     if (st) return st;
+    if (sort && fused_sort && (st = begin_counted_step(r))) return st;
     st = launch_push(r);
     if (st) return st;
     st = launch_inject(r);
@@ -676,6 +685,7 @@ int build_step_graph(cpic_run* r, int with_solve, int with_sort) {
     const bool fused = with_sort != 0 && push3d_fused_ok(r);
     st = enqueue_step(r, with_sort != 0, with_solve != 0, fused);
     r->order_pending = pending;
+    r->count_hist = false;
     if (!st && with_solve) {
         cudaStreamCaptureStatus cs;
         cudaGraph_t cg = nullptr;
@@ -731,8 +741,10 @@ int step_once(cpic_run* r, bool solve) {
     }
     // profiled path: the same work launched stream-ordered, bracketed by events; the push
     // phase holds the fused push kernel alone
+    const bool fused = sort && push3d_fused_ok(r);
     int st = phase(r, CPIC_PHASE_FIELD, [&] {
         int q = launch_vertex_field(r);
+        if (!q && fused) q = begin_counted_step(r);
         return q ? q : launch_push_prep(r);
     });
     if (st) return st;
@@ -745,7 +757,7 @@ int step_once(cpic_run* r, bool solve) {
     });
     if (st) return st;
     if (r->cfg.sort_interval > 0 && ++r->steps_since_sort >= r->cfg.sort_interval) {
-        st = phase(r, CPIC_PHASE_SORT, [&] { return launch_sort(r, push3d_fused_ok(r)); });
+        st = phase(r, CPIC_PHASE_SORT, [&] { return launch_sort(r, fused); });
         if (st) return st;
         r->cur_host ^= 1;
         r->steps_since_sort = 0;

@@ -346,6 +346,8 @@ __global__ void inject3d_kernel(InjectParams ip) {
             alive = c[0] >= 0 && c[0] < n1 && c[1] >= 0 && c[1] < n2;
             const long long slot = p.pb.base[s] + start + pi;
             p.pb.cell[cur][slot] = alive ? encode<3>(c) : -1;
+            if (p.hist && alive)  // the push builds this step's sort histogram: add the newcomers
+                atomicAdd(p.hist + (size_t)s * n1 * n2 * n3 + c[0] + (size_t)n1 * (c[1] + (size_t)n2 * c[2]), 1);
 #pragma unroll
             for (int a = 0; a < 3; ++a) p.pb.t[cur][a * T + slot] = tt[a];
 #pragma unroll

@@ -120,6 +120,8 @@ struct PushParams {
     float gb[3];                   // its unit field direction b (velocity components' basis)
     float gy[CPIC_MAX_SPECIES][4]; // per species cos th, sin th, sin th / th, (1 - cos th) / th
     int chunk;                     // particles per block chunk (0: one wave of blocks)
+    int* hist;                     // when set: count each kept particle's new cell here
+                                   // ([species][cell], the next sort's histogram)
     int tile;                      // 1: shared-memory deposit tile when the chunk fits
     DevCounters* ctr;
 };
@@ -203,6 +205,7 @@ struct cpic_run {
     cudaStream_t capture_stream;
     int cluster_cs;              // cluster size of the cluster solver (0: not applicable)
     bool order_pending;          // a fused sort's order may be pending on the device (DevCounters::perm)
+    bool count_hist;             // this step's direct 3D push and injection build the sort's histogram
     int dense_m;                 // coarsest unknowns (+1 row when singular)
     bool singular;
     double sumJ;                 // sum of finest J_c (singular projection)

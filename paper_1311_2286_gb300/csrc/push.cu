@@ -468,6 +468,7 @@ PushParams make_push_params(cpic_run* r) {
     p.origin = 1 + p.hs1 + p.hs2;
     p.ctr = r->ctr;
     p.chunk = r->push_chunk;
+    p.hist = r->count_hist ? r->hist : nullptr;
     p.tile = r->push_tile;
     set_boris_constants(r, &p, 1.0);
     return p;

@@ -707,6 +707,12 @@ __global__ void __launch_bounds__(PD_THREADS, 4) push3d_direct_kernel(PushParams
                 atomicAdd(&sh_gone[face], 1);
                 collect_face<3>(p, s, face, cn);
             }
+            if (p.hist) {  // the next sort's histogram: one atomic per run of equal cells
+                const int key = alive ? cn[0] + p.n[0] * (cn[1] + p.n[1] * cn[2]) : -1;
+                const unsigned peers = __match_any_sync(FULL, key);
+                if (key >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+                    atomicAdd(p.hist + (size_t)s * p.n[0] * p.n[1] * p.n[2] + key, (int)__popc(peers));
+            }
             store_state3(active, cellq + slot, alive ? (cn[0] | (cn[1] << 10) | (cn[2] << 20)) : -1, tq1 + slot,
                          tq1 + T + slot, tq1 + 2 * T + slot, tn, vq1 + slot, vq1 + T + slot, vq1 + 2 * T + slot, v);
             deposit_runs3(p, s, alive, cn, tn, wq);  // a6

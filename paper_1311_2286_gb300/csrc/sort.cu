@@ -431,9 +431,13 @@ int launch_sort(cpic_run* r, bool fused) {
     long long pblocks = (tot + 255) / 256;
     if (pblocks > 8LL * device_sm_count()) pblocks = 8LL * device_sm_count();
     if (pblocks < 1) pblocks = 1;
-    CPIC_CUDA(cudaMemsetAsync(r->hist, 0, sizeof(int) * N, r->stream));
-    hist_kernel<<<(int)pblocks, 256, 0, r->stream>>>(p);
-    CPIC_CHECK_LAUNCH();
+    if (r->count_hist) {
+        r->count_hist = false;  // the step's push and injection counted the cells
+    } else {
+        CPIC_CUDA(cudaMemsetAsync(r->hist, 0, sizeof(int) * N, r->stream));
+        hist_kernel<<<(int)pblocks, 256, 0, r->stream>>>(p);
+        CPIC_CHECK_LAUNCH();
+    }
     long long chunk = 4096;
     while ((N + chunk - 1) / chunk > SCAN_THREADS) chunk *= 2;
     int nb = (int)((N + chunk - 1) / chunk);
