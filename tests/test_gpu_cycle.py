@@ -2,8 +2,8 @@
 charge -> RHS, multigrid solve, diagnostics) against the oracle's cycle (oracle/pic.py,
 FP64 mover, exact b2 deposit, direct solve), run from the same particles.
 
-What is compared (the benchmark spec's run-level tolerances, Sec. II four-step cycle and the
-charging runs of Sec. III.A-B):
+What is compared (run-level tolerances for the Sec. II four-step cycle and the charging
+runs of Sec. III.A-B):
   * the start-up half kick (v^{-1/2}) and the state after one step: <= 1e-5 normwise
     (global xi and v) against FP64;
   * the device's field energy at every step against 1/2 sum_c phi_c Q_c evaluated here in
