@@ -128,3 +128,38 @@ def test_push_tuning_changes_no_result(cpic, chunk, tile):
         assert np.array_equal(ca[s], cb[s])
     for key in ("n", "absorbed", "W_K"):
         assert da[key] == db[key], key
+
+
+@pytest.mark.parametrize("interval", [1, 2, 3])
+def test_fused_sort_order_matches_gathered_sort(cpic, tmp_path, interval):
+    """The sort that leaves its gather to the next direct 3D push (and takes its histogram
+    from that step's push and injection) against the sort with its own histogram and gather
+    (the tiled push): the same particles (as sets), charge, counters and potential after
+    each stretch, with reads, a checkpoint, an explicit sort and a change of push kernel in
+    between, several of them while an order is pending, and a restored run continuing."""
+    def run_for(tile):
+        r = cpic.sphere_run_device(16, 12, 8, 20_000, sort_interval=interval, inject=True)
+        r.set_push_tuning(0, tile)
+        states = []
+        r.step(3)
+        states.append(_state(r, 2))
+        r.step_particles(interval)  # ends with a sort: with tile 0 its order is pending now
+        states.append(_state(r, 2))
+        path = str(tmp_path / ("run%d.ck" % tile))
+        r.checkpoint(path)
+        r.step(interval)
+        r.sort()
+        r.step(2)
+        states.append(_state(r, 2))
+        r.set_push_tuning(0, 1 - tile)  # the other push kernel from here on
+        r.step(interval + 1)
+        states.append(_state(r, 2))
+        r.close()
+        c = cpic.Run.restore(path)
+        c.step(interval + 2)
+        states.append(_state(c, 2))
+        c.close()
+        return states
+
+    for x, y in zip(run_for(0), run_for(1)):
+        _same(x, y)
