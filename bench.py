@@ -307,8 +307,11 @@ def cylinder_measurement(cpic, n1, n2, npart, steps, warmup, full_steps, stream,
     ph, pp = profiled_phases(run, min(steps, 20), lambda: run.step_particles(1), flush)
     push_ms = ph["push"][0] / max(ph["push"][1], 1)
     peak, kind = measured_peak()
-    # traffic only from a profile of this size class (the 128x256 state sits in L2)
-    roof = roofline(push_ms, pp, B2, peak, kind, profiled_traffic(profile, SRC2, pp) if profile else None,
+    # traffic only from a profile of this size class (the 128x256 state sits in L2); the push
+    # after a sort reads each particle's 4-byte source index (the sort leaves its gather to it)
+    sint = tuning.get("sort_interval", 0) if isinstance(tuning, dict) else 0
+    roof = roofline(push_ms, pp, B2 + (4.0 / sint if sint > 0 else 0.0), peak, kind,
+                    profiled_traffic(profile, SRC2, pp) if profile else None,
                     "push2d_kernel<false,true> (fused gather/push/boundary/deposit, 2D)")
     out = {"value": ps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps, "particles": int(pp),
            "cells": n1 * n2, "setup_s": setup_s, "tuning": tuning, "roofline": roof,

@@ -682,7 +682,7 @@ int build_step_graph(cpic_run* r, int with_solve, int with_sort) {
     // flag is managed around each replay (step_once), not by what capture enqueues
     const bool pending = r->order_pending;
     r->order_pending = false;
-    const bool fused = with_sort != 0 && push3d_fused_ok(r);
+    const bool fused = with_sort != 0 && push_fused_ok(r);
     st = enqueue_step(r, with_sort != 0, with_solve != 0, fused);
     r->order_pending = pending;
     r->count_hist = false;
@@ -719,7 +719,7 @@ int build_step_graph(cpic_run* r, int with_solve, int with_sort) {
 
 int step_once(cpic_run* r, bool solve) {
     bool sort = r->cfg.sort_interval > 0 && r->steps_since_sort + 1 >= r->cfg.sort_interval;
-    if (r->order_pending && !push3d_fused_ok(r)) {
+    if (r->order_pending && !push_fused_ok(r)) {
         if (int e = resolve_order(r)) return e;
     }
     if (!r->profiling) {
@@ -741,7 +741,7 @@ int step_once(cpic_run* r, bool solve) {
     }
     // profiled path: the same work launched stream-ordered, bracketed by events; the push
     // phase holds the fused push kernel alone
-    const bool fused = sort && push3d_fused_ok(r);
+    const bool fused = sort && push_fused_ok(r);
     int st = phase(r, CPIC_PHASE_FIELD, [&] {
         int q = launch_vertex_field(r);
         if (!q && fused) q = begin_counted_step(r);

@@ -233,6 +233,8 @@ __global__ void inject_kernel(InjectParams ip) {
             }
             long long slot = p.pb.base[s] + start + pi;
             p.pb.cell[cur][slot] = alive ? encode<2>(c) : -1;
+            if (p.hist && alive)  // the push builds this step's sort histogram: add the newcomers
+                atomicAdd(p.hist + (size_t)s * n1 * n2 + c[0] + (size_t)n1 * c[1], 1);
             p.pb.t[cur][slot] = tt[0];
             p.pb.t[cur][T + slot] = tt[1];
             p.pb.v[cur][slot] = v0;

@@ -287,13 +287,14 @@ int launch_load_maxwellian(cpic_run* r, int sp, long long n, double vth, const d
 // inject.cu
 int launch_inject(cpic_run* r);
 // sort.cu
-// the cell sort; fused: leave the reordering to the next push (push3d's direct kernel reads
-// through the pending order; only when push3d_fused_ok), else gather now
+// the cell sort; fused: leave the reordering to the next push (the direct 3D kernel and the
+// 2D kernel read through the pending order; only when push_fused_ok), else gather now
 int launch_sort(cpic_run* r, bool fused = false);
 // carry out a pending sort order (gather; a no-op when none is pending): before anything
 // other than a fused 3D push touches the particles
 int resolve_order(cpic_run* r);
-bool push3d_fused_ok(const cpic_run* r);
+bool push_fused_ok(const cpic_run* r);
+bool push3d_direct_taken(const cpic_run* r);
 // mg.cu
 int mg_setup(cpic_run* r);
 int mg_solve(cpic_run* r, double rtol, int max_cycles, bool host_loop, int* cycles, double* res);

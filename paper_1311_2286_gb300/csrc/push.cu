@@ -561,11 +561,23 @@ int launch_push_prep(cpic_run* r) {
     return CPIC_OK;
 }
 
+// whether the run's push kernel can read through a pending sort order and count the next
+// sort's histogram (so that the sort may leave its histogram and gather to the push): the
+// direct 3D kernel and the 2D kernel (periodic and absorbing axes, no field, Omega = 1)
+bool push_fused_ok(const cpic_run* r) {
+    if (r->magnetized) return false;
+    if (r->D == 3) return push3d_direct_taken(r);
+    if (r->cfg.axisymmetric) return false;
+    for (int f = 0; f < 4; ++f)
+        if (r->cfg.particle_bc[f] == CPIC_PBC_REFLECT) return false;
+    return true;
+}
+
 int launch_push_kernel(cpic_run* r) {
-    // a pending sort order: the direct 3D kernel reads through it (its finalisation flips the
-    // buffers); any other kernel needs the particles gathered first
+    // a pending sort order: the direct 3D kernel and the 2D kernel read through it (the step's
+    // finalisation flips the buffers); any other kernel needs the particles gathered first
     if (r->order_pending) {
-        if (push3d_fused_ok(r)) {
+        if (push_fused_ok(r)) {
             r->order_pending = false;
         } else if (int e = resolve_order(r)) {
             return e;

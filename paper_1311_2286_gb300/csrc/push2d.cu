@@ -145,6 +145,11 @@ __device__ __forceinline__ void push2d_run(const PushParams& p, int bid, int nb,
                                            int* red_min, int* red_max) {
     const DevCounters* ctr = p.ctr;
     const int cur = ctr->cur;
+    // a fused sort left its order pending: slot i of the other buffer's cell array holds the
+    // current-buffer index of the particle that belongs in slot i; read it from there and
+    // write the pushed state to slot i of the other buffer (the step's finalisation flips)
+    const bool perm = ctr->perm != 0;
+    const int dst = perm ? 1 - cur : cur;
     const int nsp = p.nsp;
     int cnt[CPIC_MAX_SPECIES];
     int total = 0;
@@ -176,12 +181,12 @@ __device__ __forceinline__ void push2d_run(const PushParams& p, int bid, int nb,
         const int lo = local * C;
         const int hi = min(lo + C, cnt[s]);
         const long long b0 = p.pb.base[s];
-        int* __restrict__ cellp = p.pb.cell[cur] + b0;
-        float* __restrict__ t0p = p.pb.t[cur] + b0;
-        float* __restrict__ t1p = t0p + T;
-        float* __restrict__ v0p = p.pb.v[cur] + b0;
-        float* __restrict__ v1p = v0p + T;
-        float* __restrict__ v2p = v1p + T;
+        const int* cellp = p.pb.cell[cur] + b0;  // read (through cellq's indices when perm)
+        const float* tp = p.pb.t[cur] + b0;
+        const float* vp = p.pb.v[cur] + b0;
+        int* cellq = p.pb.cell[dst] + b0;  // written
+        float* tq = p.pb.t[dst] + b0;
+        float* vq = p.pb.v[dst] + b0;
         const float dtqm = p.dtqm[s];
 
         // tile rows: the rows of the chunk's particles (sampled; the chunk is in cell order
@@ -192,7 +197,7 @@ __device__ __forceinline__ void push2d_run(const PushParams& p, int bid, int nb,
         tl.W = n0 + 2;
         {
             const int si = lo + (int)(((long long)(hi - lo - 1) * threadIdx.x) / (P2_THREADS - 1));
-            const int sc = cellp[si];
+            const int sc = cellp[perm ? cellq[si] : si];
             int rmin = sc >= 0 ? (sc >> 16) : 0x7fffffff, rmax = sc >= 0 ? (sc >> 16) : -1;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -227,12 +232,13 @@ __device__ __forceinline__ void push2d_run(const PushParams& p, int bid, int nb,
         int ncw = -1;
         float nt0 = 0.f, nt1 = 0.f, nv0_ = 0.f, nv1_ = 0.f, nv2_ = 0.f;
         if (i < hi) {
-            ncw = cellp[i];
-            nt0 = t0p[i];
-            nt1 = t1p[i];
-            nv0_ = v0p[i];
-            nv1_ = v1p[i];
-            nv2_ = v2p[i];
+            const int j = perm ? cellq[i] : i;
+            ncw = cellp[j];
+            nt0 = tp[j];
+            nt1 = tp[T + j];
+            nv0_ = vp[j];
+            nv1_ = vp[T + j];
+            nv2_ = vp[2 * T + j];
         }
         // the iteration loop, specialised on whether the chunk's tile is in use
         auto iterate = [&](auto tile_tag) {
@@ -245,12 +251,13 @@ __device__ __forceinline__ void push2d_run(const PushParams& p, int bid, int nb,
                 i += P2_THREADS;
                 ncw = -1;
                 if (i < hi) {
-                    ncw = cellp[i];
-                    nt0 = t0p[i];
-                    nt1 = t1p[i];
-                    nv0_ = v0p[i];
-                    nv1_ = v1p[i];
-                    nv2_ = v2p[i];
+                    const int j = perm ? cellq[i] : i;
+                    ncw = cellp[j];
+                    nt0 = tp[j];
+                    nt1 = tp[T + j];
+                    nv0_ = vp[j];
+                    nv1_ = vp[T + j];
+                    nv2_ = vp[2 * T + j];
                 }
                 const bool active = cw >= 0;
                 int c[2] = {active ? (cw & 0xFFFF) : 0, active ? (cw >> 16) : 0};
@@ -373,8 +380,14 @@ __device__ __forceinline__ void push2d_run(const PushParams& p, int bid, int nb,
                 // spec D: v_old . v_new as an FP32 fma chain, then round(x 2^24) to int64
                 const float ke32 = __fmaf_rn(vo2, v[2], __fmaf_rn(vo1, v[1], __fmul_rn(vo0, v[0])));
                 if (active) ke += __float2ll_rn(__fmul_rn(ke32, 16777216.0f));
-                store_state(active, cellp + slot, alive ? (cn[0] | (cn[1] << 16)) : -1, t0p + slot, tn[0], t1p + slot,
-                            tn[1], v0p + slot, v[0], v1p + slot, v[1], v2p + slot, v[2]);
+                if (p.hist) {  // the next sort's histogram: one atomic per run of equal cells
+                    const int key = alive ? cn[0] + n0 * cn[1] : -1;
+                    const unsigned peers = __match_any_sync(FULL, key);
+                    if (key >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+                        atomicAdd(p.hist + (size_t)s * n0 * n1 + key, (int)__popc(peers));
+                }
+                store_state(active, cellq + slot, alive ? (cn[0] | (cn[1] << 16)) : -1, tq + slot, tn[0],
+                            tq + T + slot, tn[1], vq + slot, v[0], vq + T + slot, v[1], vq + 2 * T + slot, v[2]);
                 // a6: deposit
                 if constexpr (TILE)
                     deposit_tile(p, tl, s, alive, cn, tn);

@@ -788,9 +788,8 @@ int launch_push3d_t(cpic_run* r, const PushParams& p) {
 
 }  // namespace
 
-// whether the 3D push the run takes is the direct kernel, which can read through a pending
-// sort order (so that the sort may leave its gather to it)
-bool push3d_fused_ok(const cpic_run* r) {
+// whether the 3D push the run takes is the direct kernel (see push_fused_ok)
+bool push3d_direct_taken(const cpic_run* r) {
     if (r->D != 3 || r->magnetized || r->push_tile) return false;
     const int k0 = r->cfg.particle_bc[0], k1 = r->cfg.particle_bc[2], k2 = r->cfg.particle_bc[4];
     return (k0 == K_ABS && k1 == K_REF && k2 == K_PER) || (k0 == K_PER && k1 == K_PER && k2 == K_PER);
