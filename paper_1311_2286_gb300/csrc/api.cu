@@ -608,16 +608,16 @@ int enqueue_step_pre(cpic_run* r, bool with_push) {
     return st;
 }
 
-int enqueue_step_post(cpic_run* r, bool sort, bool fold) {
+int enqueue_step_post(cpic_run* r, bool sort, bool fold, bool fused_sort) {
     int st = launch_finalize_step(r);
     if (!st) st = launch_inject(r);
     if (!st && fold) st = launch_fold(r);
-    if (!st && sort) st = launch_sort(r);
+    if (!st && sort) st = launch_sort(r, fused_sort);
     return st;
 }
 
-// a fused sort step: the direct 3D push and the injection count the particles' new cells,
-// so the sort skips its histogram pass
+// a fused sort step: the push and the injection count the particles' new cells, so the
+// sort skips its histogram pass
 int begin_counted_step(cpic_run* r) {
     r->count_hist = true;
     CPIC_CUDA(cudaMemsetAsync(r->hist, 0, sizeof(int) * r->cfg.n_species * (size_t)r->ncell, r->stream));

@@ -45,6 +45,7 @@ struct cpic_batch {
     struct Graph {
         cudaGraphExec_t exec = nullptr;
         int kernels = 0;
+        std::vector<char> fused;  // per member: its sort in this graph leaves the order pending
     };
     std::map<std::string, Graph> graphs;
     int mode = CPIC_BATCH_AUTO;  // cpic_batch_set_mode
@@ -111,6 +112,19 @@ int capture(cpic_batch* b, bool solve, const std::string& key, cpic_batch::Graph
     (void)solve;
     int st = persistent ? build_push_tables(b, &groups) : CPIC_OK;  // before the capture: it allocates
     if (st) return st;
+    // members that sort in this step and push with a kernel that reads through a pending
+    // order (not through the persistent batched push) sort with the fused order: their push
+    // counts the histogram and their next push does the gather. The graph runs in any order
+    // state (the kernels read the device flag); the host flags are managed around launches.
+    const size_t nr = b->runs.size();
+    out->fused.assign(nr, 0);
+    std::vector<char> pending(nr, 0);
+    for (size_t i = 0; i < nr; ++i) {
+        cpic_run* r = b->runs[i];
+        out->fused[i] = key[i] == '1' && push_fused_ok(r) && !(persistent && push2d_batchable(r));
+        pending[i] = r->order_pending;
+        r->order_pending = false;
+    }
     CPIC_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaEventRecord(b->fork, b->stream);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaEventRecord(fork)", __FILE__, __LINE__);
@@ -124,7 +138,8 @@ int capture(cpic_batch* b, bool solve, const std::string& key, cpic_batch::Graph
         }
         cudaStream_t saved = r->stream;
         r->stream = b->branch[i];
-        st = enqueue_step_pre(r, !persistent || !push2d_batchable(r));
+        if (out->fused[i]) st = begin_counted_step(r);
+        if (!st) st = enqueue_step_pre(r, !persistent || !push2d_batchable(r));
         r->stream = saved;
         if (st) break;
         e = cudaEventRecord(b->join_pre[i], b->branch[i]);
@@ -153,7 +168,7 @@ int capture(cpic_batch* b, bool solve, const std::string& key, cpic_batch::Graph
         }
         cudaStream_t saved = r->stream;
         r->stream = b->branch[i];
-        st = enqueue_step_post(r, key[i] == '1', solve);
+        st = enqueue_step_post(r, key[i] == '1', solve, out->fused[i] != 0);
         if (!st && solve) {
             cudaStreamCaptureStatus cs;
             cudaGraph_t cg = nullptr;
@@ -169,6 +184,10 @@ int capture(cpic_batch* b, bool solve, const std::string& key, cpic_batch::Graph
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->stream, &g);
+    for (size_t i = 0; i < nr; ++i) {
+        b->runs[i]->order_pending = pending[i] != 0;
+        b->runs[i]->count_hist = false;
+    }
     if (st) {
         if (g) cudaGraphDestroy(g);
         return st;
@@ -318,8 +337,9 @@ int cpic_batch_step(cpic_batch* b, int nsteps, int with_solve) {
         return CPIC_ERR_INVALID;
     }
     if (b->runs.empty()) return CPIC_OK;
-    for (cpic_run* r : b->runs)  // a member stepped alone since it joined
-        if (r->order_pending) {
+    const bool persistent = b->mode == CPIC_BATCH_PERSISTENT;
+    for (cpic_run* r : b->runs)  // a pending order the member's batched push does not take
+        if (r->order_pending && !(push_fused_ok(r) && !(persistent && push2d_batchable(r)))) {
             if (int st = resolve_order(r)) return st;
             CPIC_CUDA(cudaStreamSynchronize(r->stream));
         }
@@ -344,6 +364,8 @@ int cpic_batch_step(cpic_batch* b, int nsteps, int with_solve) {
         add_launches(it->second.kernels);
         for (size_t i = 0; i < b->runs.size(); ++i) {
             cpic_run* r = b->runs[i];
+            // the push took any pending order; a fused sort at the end leaves a new one
+            r->order_pending = key[i] == '1' && it->second.fused[i];
             if (key[i] == '1') {
                 r->cur_host ^= 1;
                 r->steps_since_sort = 0;

@@ -278,7 +278,9 @@ bool push2d_batchable(const cpic_run* r);
 // the zeroing of the deposit grid (and the push itself for runs that cannot join it); then
 // the step counter, injection, halo fold and sort
 int enqueue_step_pre(cpic_run* r, bool with_push);
-int enqueue_step_post(cpic_run* r, bool sort, bool fold);
+int enqueue_step_post(cpic_run* r, bool sort, bool fold, bool fused_sort = false);
+// a fused sort step: the push and the injection count the sort's histogram (zeroed here)
+int begin_counted_step(cpic_run* r);
 int launch_push3d(cpic_run* r, const PushParams& p);  // CPIC_ERR_NOT_BUILT: no specialisation
 // one PIC step without the field solve, enqueued on r->stream (also inside stream capture)
 int enqueue_step(cpic_run* r, bool sort, bool fold);
