@@ -377,3 +377,22 @@ def test_planar_wall_early_spike():
     assert abs(vs.min() / -5.7 - 1.0) <= 0.10, vs.min()
     assert vs[-100:].mean() < -4.0
     assert p.injected[1] > 0 and p.history[-1]["n"][1] > 0
+
+
+def test_drifting_flux_reduces_to_the_resting_flux():
+    """With no drift along the normal the drifting source is the resting one (closed forms):
+    Gamma(0) = vth / sqrt(2 pi), the normal-speed CDF is the Rayleigh CDF
+    1 - exp(-v^2 / 2 vth^2), so its inverse at q is vth sqrt(-2 ln(1 - q)); and for large
+    inward drift the flux tends to u (every particle crosses) and the normal speed to u."""
+    vth = 0.7
+    assert abs(inject.drift_flux(0.0, vth) - vth / math.sqrt(2.0 * math.pi)) < 1e-15
+    for v in (0.1, 0.5, 1.3, 3.0):
+        assert abs(inject.drift_normal_cdf(v, 0.0, vth) - (1.0 - math.exp(-v * v / (2.0 * vth * vth)))) < 1e-13
+    for q in (0.05, 0.3, 0.5, 0.9, 0.999):
+        want = vth * math.sqrt(-2.0 * math.log(1.0 - q))
+        assert abs(inject.drift_normal_speed(q, 0.0, vth) - want) < 1e-12 * max(want, 1.0)
+    u = 40.0 * vth
+    assert abs(inject.drift_flux(u, vth) / u - 1.0) < 1e-12
+    assert abs(inject.drift_normal_speed(0.5, u, vth) / u - 1.0) < 1e-2
+    # an outflowing drift (u < 0) still injects the inward tail, fewer the faster it flows out
+    assert 0.0 < inject.drift_flux(-2.0 * vth, vth) < inject.drift_flux(-1.0 * vth, vth) < inject.drift_flux(0.0, vth)
