@@ -272,7 +272,12 @@ int cpic_load_maxwellian(cpic_run* run, int sp, int64_t n, double vth, const dou
  * (standard leapfrog start-up for eq. (step1)). */
 int cpic_initialize(cpic_run* run);
 /* nsteps full PIC steps (Sec. II cycle): vertex field, push (+ deposit), injection, sort
- * every sort_interval steps, charge -> RHS, multigrid solve to mg_rtol, diagnostics. */
+ * every sort_interval steps, charge -> RHS, multigrid solve to mg_rtol, diagnostics.
+ * When the push is the direct 3D kernel or the 2D kernel, a sort takes its histogram from
+ * the step's push and injection and leaves its reordering to the next push, which reads
+ * each sorted slot's particle through the sort's index; every other call that touches the
+ * particles (reads, loads, injection, checkpoints, another push kernel) carries out such a
+ * pending order first, so the particles are always seen in sorted slot order. */
 int cpic_step(cpic_run* run, int nsteps);
 /* nsteps particle steps with the field held fixed: vertex field, push (+ deposit),
  * injection, sort every sort_interval steps; no charge -> RHS and no field solve. This is
