@@ -55,7 +55,7 @@ WORKLOAD = ("3D sphere in plasma: shell r=30^xi, theta in [pi/32, pi-pi/32] (spe
             "steps")
 SRC3 = ["paper_1311_2286_gb300/csrc/push3d.cu", "paper_1311_2286_gb300/csrc/particles.cuh"]
 SRC2 = ["paper_1311_2286_gb300/csrc/push2d.cu", "paper_1311_2286_gb300/csrc/particles.cuh"]
-PROFILE3 = "profiles/push3d_sphere_128cubed.md"
+PROFILE3 = "profiles/push3d_sphere_64cubed_headline_density.md"
 PROFILE2 = "profiles/push2d_cylinder_512x1024_64M.md"
 
 
@@ -230,7 +230,7 @@ def roofline(push_ms, particles, bpp, peak, kind, traffic, kernel):
             "particles_per_launch": particles, "push_ms": push_ms}
 
 
-def sphere_measurement(cpic, npart, steps, warmup, full_steps, stream, flush, e2e_steps, tuning=None):
+def sphere_measurement(cpic, npart, steps, warmup, full_steps, stream, flush, e2e_steps, tuning=None, cells=128):
     """The headline: fixed-field particle steps of the 3D sphere (autotuned sort interval,
     push chunking and deposit tiling), the push kernel's roofline, full cycles with the 3D
     multigrid solve, and the end-to-end figure through the public API."""
@@ -238,7 +238,7 @@ def sphere_measurement(cpic, npart, steps, warmup, full_steps, stream, flush, e2
 
     cs = ctypes_stream(stream)
     t0 = time.perf_counter()
-    run = cpic.sphere_run_device(128, 128, 128, npart, stream=cs, inject=True)
+    run = cpic.sphere_run_device(cells, cells, cells, npart, stream=cs, inject=True)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     if tuning is None:
@@ -729,6 +729,9 @@ def main():
     ap.add_argument("--full-steps", type=int, default=5, help="full PIC cycles (with the field solve) timed")
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--sphere-particles", type=int, default=32_000_000, help="per species (headline)")
+    ap.add_argument("--sphere-cells", type=int, default=128,
+                    help="cells per axis of the sphere run (128: the headline; smaller only to profile the "
+                         "headline's particle density on a smaller device footprint)")
     ap.add_argument("--cyl-particles", type=int, default=2_000_000, help="per species, 128x256 cylinder (0: skip)")
     ap.add_argument("--cyl64-particles", type=int, default=32_000_000,
                     help="per species, 512x1024 cylinder, the 2D HBM roofline run (0: skip)")
@@ -790,7 +793,7 @@ def main():
     torch.cuda.synchronize()
     fixed = tuple(int(x) for x in args.tuning.split(",")) if args.tuning else None
     head = sphere_measurement(cpic, args.sphere_particles, args.steps, args.warmup, args.full_steps, stream, flush,
-                              0 if args.no_e2e else args.e2e_steps, tuning=fixed)
+                              0 if args.no_e2e else args.e2e_steps, tuning=fixed, cells=args.sphere_cells)
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -822,7 +825,9 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD.format(S=tuning["sort_interval"]),
+            "config": {"workload": WORKLOAD.format(S=tuning["sort_interval"]) if args.sphere_cells == 128 else
+                       "%s (PROFILING SIZE: %d^3 cells, %d particles per species)" % (
+                           WORKLOAD.format(S=tuning["sort_interval"]), args.sphere_cells, args.sphere_particles),
                        "step": "fixed-field particle step (a1-a8, sort amortised)", "autotune": tuning,
                        "particles_per_gpu": 2 * args.sphere_particles, "cells": 128 ** 3,
                        "l2": "inputs (1.8 GB of particle state) larger than L2; L2 also flushed between timed steps "
